@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the per-pixel ray integration path.
+
+Workload: the twisted bar (single cubic B-spline block, 8x8x32 control points,
+parametrisation-quality scalar, Eq. 23) rendered at 1920x1080 with a
+perspective camera, plain FP32, RK tolerance 1e-5, ds = diag/128, K = 4.
+One step = one whole frame: face projection, ray/face intersection,
+depth sort + Alg. 2 pairing, and ODE integration with compositing.
+
+Prints one JSON line.  `value` is Mpixels/s over the whole job (all ranks),
+timed on the device with CUDA events per step; L2 is flushed (a 512 MiB
+write) between timed steps, outside the events.  `e2e` is the same metric
+through ivv_render_to_host (pinned host output, device->host copy inside).
+`--impl reference` times the FP64 CPU oracle on a bounded row sample.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixels/s & ms/frame at 1920x1080 vs plain FP32, at <=1e-3 max RGBA error"
+UNIT = "Mpixels/s"
+WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x1080 perspective, FP32"
+
+# Algorithmic FP32 flops of the integrator (cubic elements), counted per unit:
+F_RHS = 1283      # one W(p): 576-FMA sum-factorised phi+J, Bernstein basis, V, 3x3 adjugate solve
+F_STEP = 70       # stage combinations, clamps and error norm of one BS3(2) step attempt
+F_SAMPLE = 150    # K=4 supersampled TF lookups + Alg. 1 updates + Eq. 23 per sample
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_oracle_sample(scene, target_s=12.0, max_stride=64):
+    """Oracle Mpix/s on evenly spaced rows of the frame (rows at stride s,
+    halving s until one sample takes >= target_s / 3)."""
+    import oracle
+    vol = oracle.OracleVolume(scene.blocks, scene.scalar_mode)
+    W, H = scene.width, scene.height
+    stride = max_stride
+    best = None
+    cores = os.cpu_count() or 1
+    while True:
+        rows = list(range(stride // 2, H, stride))
+        t0 = time.perf_counter()
+        for y in rows:
+            oracle.render(scene, vol, window=(0, W, y, y + 1), n_threads=cores)
+        dt = time.perf_counter() - t0
+        best = (len(rows) * W, dt, stride, len(rows))
+        if dt >= target_s / 3 or stride == 1:
+            break
+        stride //= 2
+    px, dt, stride, nrows = best
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d rows at stride %d of the 1920x1080 frame (%d pixels), FP64 per-sample Newton, "
+                      "%.2f s" % (nrows, stride, px, dt)}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    from paper_1404_3363_gb300 import scenes
+    import oracle
+    sc = scenes.config(1)
+    vol = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    W, H = sc.width, sc.height
+    cores = os.cpu_count() or 1
+    stride = args.ref_stride
+    rows = list(range(stride // 2, H, stride))
+
+    def step():
+        for y in rows:
+            oracle.render(sc, vol, window=(0, W, y, y + 1), n_threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    px = len(rows) * W
+    value = px / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": H,
+                   "sample": "%d rows at stride %d per step" % (len(rows), stride)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d rows at stride %d of the frame (%d pixels) per step" % (len(rows), stride, px)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1404_3363_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1404_3363_gb300 import ivv, scenes
+
+    sc = scenes.config(1)
+    W, H = sc.width, sc.height
+    stream = torch.cuda.current_stream()
+    vol = ivv.volume_for(sc)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    # untimed instrumented replay: algorithmic work counts of this exact frame
+    vol.reset_stats()
+    vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS)
+    st = vol.stats()
+    flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
+                + st["samples"] * F_SAMPLE)
+
+    # parity spot check of this frame against the oracle (untimed)
+    max_err = None
+    if rank == 0 and not args.no_parity:
+        import oracle
+        img = out.cpu().numpy().astype(np.float64)
+        ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+        cov = np.argwhere(img[..., 3] > 0)
+        rng = np.random.default_rng(7)
+        pick = cov[rng.choice(len(cov), min(48, len(cov)), replace=False)] if len(cov) else []
+        max_err = 0.0
+        for y, x in pick:
+            ref = oracle.render(sc, ov, window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
+            max_err = max(max_err, float(np.abs(img[y, x] - ref).max()))
+
+    def frame(flags=0):
+        vol.render(sc.camera, sc.params, W, H, out=out, flags=flags)
+
+    for _ in range(args.warmup):
+        frame()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(_gpu_id_for_smi(local))
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_sum = {k: 0.0 for k in ivv.STAGES}
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        frame(ivv.FLAG_TIMING)
+        ev[i][1].record(stream)
+        for k, v in vol.stage_times().items():
+            stage_sum[k] += v
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * W * H / (ms * 1e-3) / 1e6
+    k5_ms = stage_sum["integrate"] / args.steps
+
+    # end to end through the C ABI with host buffers (device->host copy inside)
+    host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+    for _ in range(2):
+        vol.render_to_host(sc.camera, sc.params, W, H, host)
+    e2e_n = max(3, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        vol.render_to_host(sc.camera, sc.params, W, H, host)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_n
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    props = torch.cuda.get_device_properties(local)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_fp32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_k5 / (k5_ms * 1e-3) / 1e12 if k5_ms > 0 else 0.0
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = cpu_oracle_sample(sc)
+
+    if rank == 0:
+        import ctypes
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "rk_tol": sc.params.rk_tol,
+                       "ds": sc.params.ds, "supersample_k": sc.params.supersample_k,
+                       "l2": "flushed between steps (512 MiB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "stages_ms": {k: v / args.steps for k, v in stage_sum.items()},
+            "wall_s_timed_loop": t_wall,
+            "gpu_launches": 4 * args.steps,
+            "e2e": {"value": world * W * H / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                    "ms_per_frame": e2e_ms,
+                    "h2d_bytes_per_step": ctypes.sizeof(ivv.Camera) + ctypes.sizeof(ivv.RenderParams),
+                    "d2h_bytes_per_step": W * H * 16},
+            "roofline": {"bound": "alu", "kernel": "k5_integrate", "achieved": achieved, "peak": peak_fp32,
+                         "unit": "TFLOP/s", "frac": achieved / peak_fp32 if peak_fp32 else None,
+                         "traffic": None,
+                         "peak_note": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (max SM clock)"
+                                      % (props.multi_processor_count, sm_max),
+                         "flops_per_launch": flops_k5, "k5_ms": k5_ms},
+            "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
+                                        "fragments", "isect_tests", "isect_newton")},
+            "max_delta_p": st["max_delta_p"],
+            "parity_max_rgba_err_sampled": max_err,
+            "clocks": clocks,
+        }
+        if cpu_base:
+            line["cpu_baseline"] = cpu_base
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--ref-stride", type=int, default=96)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

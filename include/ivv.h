@@ -1,0 +1,250 @@
+/*
+ * ivv.h -- C ABI of the GB300 isogeometric volume ray integrator.
+ *
+ * Renders multi-block trivariate B-spline volumes (geometry phi, scalar rho on
+ * a common parameter domain P, Eq. 1 of Fuchs & Hjelmervik, "Interactive
+ * Isogeometric Volume Visualization with Pixel-Accurate Geometry", TVCG 2015)
+ * with the paper's three per-frame stages (§4):
+ *   1. intersections of every pixel ray with the 6 boundary surfaces of every
+ *      block (§4.1),
+ *   2. per-pixel depth-sorted fragment lists and blockwise entry/exit pairing
+ *      (§4.2, Alg. 2),
+ *   3. for each entry/exit pair, the pulled-back view-ray ODE p' = W(p),
+ *      J_phi(p) W = V(phi(p)) (§5.2, Eqs. 10-15), integrated by an embedded
+ *      Runge-Kutta pair with error control, with the transfer function and
+ *      front-to-back compositing with supersampling (§3.2.1, Alg. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - No function aborts, traps or prints.  Errors are returned as an
+ *     ivv_status; ivv_last_error() gives a thread-local message.
+ *   - Input arrays are copied at call time; the caller keeps ownership.
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()).  Streams are cudaStream_t passed as void*; NULL is the
+ *     legacy default stream.  Work is enqueued asynchronously on that stream;
+ *     only ivv_get_stats and the *_to_host entry point synchronise.
+ *   - A volume handle may be used from one host thread at a time.
+ *   - Images are float32 RGBA, row-major [height][width][4], row 0 at the
+ *     top; colour is the accumulated C_dst of Alg. 1 (background 0), A is the
+ *     accumulated opacity alpha_dst.
+ */
+#ifndef IVV_H
+#define IVV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IVV_OK = 0,
+  IVV_ERR_INVALID_ARG = 1,     /* bad pointer, size, knot vector, mode ...      */
+  IVV_ERR_CUDA = 2,            /* a CUDA runtime call failed                     */
+  IVV_ERR_OOM = 3,             /* device allocation failed                       */
+  IVV_ERR_ABUF_OVERFLOW = 4,   /* a pixel had more fragments/pairs than stored   */
+  IVV_ERR_NONCONVERGED = 5,    /* an iteration hit its cap (reported by stats)   */
+  IVV_ERR_DEGENERATE = 6,      /* det J <= 0 inside a block (assumption 4, §5)   */
+  IVV_ERR_UNSUPPORTED = 7,     /* e.g. degree > 3                                */
+  IVV_ERR_WORKSPACE = 8        /* caller workspace too small or misaligned       */
+} ivv_status;
+
+/* Scalar field rho (§1, §6.1): */
+enum {
+  IVV_SCALAR_CP = 0,        /* rho from the scalar control points              */
+  IVV_SCALAR_DETJ = 1,      /* rho = det J_phi, derived per sample              */
+  IVV_SCALAR_QUALITY = 2    /* rho = det J_phi / ||J_phi||_F  (Eq. 23)          */
+};
+
+/* Arithmetic of the ray stages: */
+enum {
+  IVV_PREC_FP32 = 0,    /* all kernels FP32                                       */
+  IVV_PREC_MIXED = 1,   /* FP32, plus FP64 Newton residual for grazing hits and
+                           an FP64 3x3 solve where |det J| < tau_det             */
+  IVV_PREC_FP64 = 2     /* all kernels FP64                                       */
+};
+
+enum {
+  IVV_FLAG_STATS = 1,    /* instrumented kernels: fill ivv_stats counters       */
+  IVV_FLAG_TIMING = 2    /* record CUDA events between the stages of the render */
+};
+
+/* Stages timed with IVV_FLAG_TIMING (indices into ivv_get_stage_times). */
+enum {
+  IVV_STAGE_PROJECT = 0,     /* face patch screen boxes                         */
+  IVV_STAGE_INTERSECT = 1,   /* ray/face intersections into fragment lists §4.1 */
+  IVV_STAGE_PAIR = 2,        /* depth sort and Alg. 2 pairing §4.2              */
+  IVV_STAGE_INTEGRATE = 3,   /* ODE integration and compositing §5.2, §3.2.1    */
+  IVV_N_STAGES = 4
+};
+
+typedef struct ivv_volume ivv_volume;     /* opaque, library-owned */
+
+/* One volume block (Eq. 1): a tensor-product B-spline of degrees degree[d]
+ * with n_cp[d] control points per direction d (0=u, 1=v, 2=w).
+ * knots[d]: n_cp[d] + degree[d] + 1 non-decreasing values, clamped (first and
+ *   last degree[d]+1 equal); they are normalised to [0,1] (the paper clamps
+ *   to [0,1]^3, §5.1 and §5.4).
+ * geom_cp: [n_cp[2]][n_cp[1]][n_cp[0]][3] doubles, u fastest.
+ * scalar_cp: [n_cp[2]][n_cp[1]][n_cp[0]] doubles; required for IVV_SCALAR_CP,
+ *   ignored otherwise. */
+typedef struct {
+  int degree[3];
+  int n_cp[3];
+  const double* knots[3];
+  const double* geom_cp;
+  const double* scalar_cp;
+} ivv_block_desc;
+
+/* Pinhole (ortho = 0) or orthographic (ortho = 1) camera.  The ray of pixel
+ * (x, y) of a W x H image passes through ndc = ((x+.5)/W*2-1, 1-(y+.5)/H*2):
+ * perspective: o = eye, d = normalize(f + ndc_x tan(fovy/2) (W/H) r
+ *                                      + ndc_y tan(fovy/2) u);
+ * orthographic: d = f, o = eye + ndc_x (h/2)(W/H) r + ndc_y (h/2) u,
+ * with f = normalize(target - eye), r = normalize(f x up), u = r x f. */
+typedef struct {
+  int ortho;
+  double eye[3], target[3], up[3];
+  double fovy_deg;
+  double ortho_height;
+} ivv_camera;
+
+/* Render parameters.  Pass NULL for the defaults in brackets.
+ * rk_tol       absolute local error bound (inf-norm, parameter space) of the
+ *              embedded Bogacki-Shampine 3(2) pair [1e-5]
+ * ds           sample distance along the ray in G arc length; <= 0 selects
+ *              diag/128, diag = diagonal of the control-point bounding box
+ *              (§3.2.1; samples s_j = j ds, last interval partial)
+ * supersample_k sub-samples per interval of the linearly interpolated scalar
+ *              (§3.2.1 supersampling) [4]
+ * c            weight of the perpendicular field V_perp (Eq. 10) [1]
+ * early_alpha  stop a pixel once alpha_dst >= early_alpha [1 - 1e-4]
+ * use_mlp_guess reserved, must be 0
+ * precision    IVV_PREC_* [FP32]
+ * flags        IVV_FLAG_* [0]
+ * x0, y0, full_width, full_height
+ *              render the window [x0, x0+width) x [y0, y0+height) of a
+ *              full_width x full_height image (0 = the window is the image) */
+typedef struct {
+  double rk_tol;
+  double ds;
+  int supersample_k;
+  double c;
+  double early_alpha;
+  int use_mlp_guess;
+  int precision;
+  int flags;
+  int x0, y0, full_width, full_height;
+} ivv_render_params;
+
+/* Counters of the last instrumented render (IVV_FLAG_STATS) plus overflow
+ * and cap counters of every render since the last ivv_reset_stats. */
+typedef struct {
+  unsigned long long rays;          /* pixels with >= 1 entry/exit pair        */
+  unsigned long long pairs;         /* entry/exit pairs integrated             */
+  unsigned long long fragments;     /* stored ray/face intersections           */
+  unsigned long long samples;       /* scalar samples s_j composited           */
+  unsigned long long rk_steps;      /* accepted RK steps                       */
+  unsigned long long rk_rejects;    /* rejected RK steps                       */
+  unsigned long long rhs_evals;     /* evaluations of W(p) in the integrator   */
+  unsigned long long isect_newton;  /* Newton iterations of ray/face solves    */
+  unsigned long long isect_tests;   /* ray/face pairs that passed the hull test */
+  unsigned long long fp64_solves;   /* FP64 fallbacks (mixed precision)        */
+  unsigned long long abuf_overflow; /* fragments dropped (list full)           */
+  unsigned long long pair_overflow; /* pairs dropped (list full)               */
+  unsigned long long unmatched;     /* records left unpaired by Alg. 2          */
+  unsigned long long step_cap;      /* pairs that hit the RK step cap          */
+  double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
+} ivv_stats;
+
+/* Build a volume from n_blocks blocks (§4: multi-block models): validate,
+ * normalise knots, Bezier-extract every block by knot insertion, elevate all
+ * blocks to a common degree P in {2, 3}, extract the 6 boundary faces of
+ * every block as Bezier face patches with outward orientation, check
+ * det J > 0 at sample points (§5 assumption 4), and upload to the device on
+ * `stream` (synchronised before return).  Returns IVV_ERR_DEGENERATE if
+ * det J <= 0 is found, IVV_ERR_UNSUPPORTED for degrees > 3. */
+ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int scalar_mode,
+                             void* stream, ivv_volume** out);
+
+/* Piecewise-linear transfer function (§3.1, Eq. 4): n_knots (2..256) knots
+ * r[i] ascending with r[0] = 0 and r[n-1] = 1; rgba [n][4]: emitted colour
+ * C_src and extinction weight A in [0,1].  Per sample, with
+ * x = clamp((rho - lo) / (hi - lo), 0, 1): alpha_src = 1 - exp(-sigma A xi),
+ * so Alg. 1's T = (1 - alpha_src)^(ds_i / xi) = exp(-sigma A ds_i).
+ * lo >= hi (or NaN) selects the default range: min/max of the scalar control
+ * points, or of the derived scalar over a 64^3 grid of sample points of every
+ * block.  Host arrays, copied. */
+ivv_status ivv_set_transfer_function(ivv_volume* vol, int n_knots, const float* r, const float* rgba,
+                                     float sigma, float lo, float hi);
+
+/* The scalar range in use (after ivv_set_transfer_function). */
+ivv_status ivv_get_scalar_range(const ivv_volume* vol, double* lo, double* hi);
+
+/* Bytes of device workspace ivv_render needs for a width x height window at
+ * the given precision (fragment lists, pair lists, queues, counters). */
+ivv_status ivv_workspace_size(const ivv_volume* vol, int width, int height, int precision,
+                              size_t* bytes);
+
+/* Render a width x height window into out_rgba (device, caller-owned,
+ * [height][width][4] float32).  workspace: device buffer of at least
+ * ivv_workspace_size bytes, 256-byte aligned; NULL makes the library use a
+ * buffer it owns (grown with cudaMalloc outside of any stream capture).
+ * All work is enqueued on `stream`; nothing is synchronised. */
+ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
+                      int width, int height, float* out_rgba, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* As ivv_render, but out_rgba_host is host memory (pinned for full speed);
+ * the image is rendered into library-owned device memory, copied back with
+ * cudaMemcpyAsync on `stream`, and the stream is synchronised. */
+ivv_status ivv_render_to_host(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
+                              int width, int height, float* out_rgba_host, void* stream);
+
+/* Stages 1-2 only (§4.1, §4.2): the per-pixel entry/exit pairs in
+ * front-to-back order.  Device outputs, caller-owned:
+ *   pair_count [height*width] int32,
+ *   pairs      [max_pairs][height*width][8] float32 per pixel and slot:
+ *              (p_in.u, p_in.v, p_in.w, t_in, p_out.u, p_out.v, p_out.w, t_out)
+ *              (FP32 and MIXED; FP64 precision is rejected here),
+ *   pair_block [max_pairs][height*width] int32.
+ * max_pairs must be >= 1; pairs beyond it are dropped and counted. */
+ivv_status ivv_render_pairs(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
+                            int width, int height, int max_pairs, int* pair_count, float* pairs,
+                            int* pair_block, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Spline evaluation on the device (Eq. 1 with the Bezier-extracted blocks):
+ * p [n][3] device float32 parameter points of one block; outputs (device,
+ * any may be NULL): phi [n][3], jac [n][3][3] (jac[r][c] = d phi_r/d p_c),
+ * rho [n] (per the volume's scalar mode). */
+ivv_status ivv_eval_points(ivv_volume* vol, int block, int n, const float* p, float* phi,
+                           float* jac, float* rho, void* stream);
+
+/* Host-only FP64 evaluation of the library's own representation of a
+ * volume description (Bezier elements after knot insertion and degree
+ * elevation, Eq. 1): no device is used.  p [n][3] parameter points of block
+ * `block` in [0,1]^3; outputs (any may be NULL): phi [n][3], jac [n][3][3],
+ * rho [n] per scalar_mode.  Runs the whole host preparation, so it validates
+ * a description exactly as ivv_create_volume would. */
+ivv_status ivv_host_eval(const ivv_block_desc* blocks, int n_blocks, int scalar_mode, int block, int n,
+                         const double* p, double* phi, double* jac, double* rho);
+
+/* Milliseconds of each stage of the last render made with IVV_FLAG_TIMING
+ * (ms[IVV_N_STAGES], CUDA events on the render stream); synchronises that
+ * stream.  Returns IVV_ERR_INVALID_ARG if no timed render was made. */
+ivv_status ivv_get_stage_times(ivv_volume* vol, float* ms);
+
+/* Counters (see ivv_stats); synchronises the stream of the last render. */
+ivv_status ivv_get_stats(ivv_volume* vol, ivv_stats* out);
+ivv_status ivv_reset_stats(ivv_volume* vol);
+
+/* Volume facts: blocks, Bezier elements, face patches, common degree P. */
+ivv_status ivv_volume_info(const ivv_volume* vol, int* n_blocks, int* n_elements, int* n_faces,
+                           int* degree);
+
+const char* ivv_last_error(void);
+void ivv_destroy_volume(ivv_volume* vol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IVV_H */

@@ -172,9 +172,12 @@ class OracleVolume:
         return N, dN
 
     def scalar_range(self, n=64):
-        lo, hi = C.c_double(), C.c_double()
-        lib().orc_scalar_range(self.h, n, C.byref(lo), C.byref(hi))
-        return lo.value, hi.value
+        cache = self.__dict__.setdefault("_range_cache", {})
+        if n not in cache:
+            lo, hi = C.c_double(), C.c_double()
+            lib().orc_scalar_range(self.h, n, C.byref(lo), C.byref(hi))
+            cache[n] = (lo.value, hi.value)
+        return cache[n]
 
     def hits(self, o, d, cap=256):
         out = (Hit * cap)()

@@ -1080,7 +1080,7 @@ int orc_trace_pair(void* v, const orc_tf* t, const orc_params* prm, const double
 }
 
 // Render pixels [x0,x1) x [y0,y1) of a W x H image into out[(y-y0)][(x-x0)][4].
-// n_threads worker threads split the rows.  Returns 0.
+// n_threads worker threads take chunks of 16 pixels.  Returns 0.
 int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* prm, int W, int H,
                int x0, int x1, int y0, int y1, int n_threads, double* out, orc_pixel_stats* stats) {
   Volume* V = (Volume*)v;
@@ -1092,16 +1092,19 @@ int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* 
   Camera cam;
   std::memcpy(&cam, c, sizeof(cam));
   const int w = x1 - x0, h = y1 - y0;
-  std::atomic<int> next(0);
+  const long npx = (long)w * h;
+  const long chunk = 16;                           // pixels per work item
+  std::atomic<long> next(0);
   auto work = [&]() {
     for (;;) {
-      const int row = next.fetch_add(1);
-      if (row >= h) break;
-      for (int i = 0; i < w; ++i) {
+      const long c0 = next.fetch_add(chunk);
+      if (c0 >= npx) break;
+      for (long q = c0; q < c0 + chunk && q < npx; ++q) {
+        const int row = (int)(q / w), i = (int)(q % w);
         PixelStats st;
-        render_pixel(*V, tf, P, cam, W, H, x0 + i, y0 + row, out + ((size_t)row * w + i) * 4, st);
+        render_pixel(*V, tf, P, cam, W, H, x0 + i, y0 + row, out + (size_t)q * 4, st);
         if (stats) {
-          orc_pixel_stats& s = stats[(size_t)row * w + i];
+          orc_pixel_stats& s = stats[q];
           s.npairs = st.npairs; s.unmatched = st.unmatched; s.newton_fail = st.newton_fail;
           s.nsamples = st.nsamples; s.rk_steps = st.rk_steps;
         }

@@ -1,0 +1,369 @@
+// Host preparation of a multi-block B-spline volume (once per volume, not per
+// frame).  Validates the input, normalises knots to [0,1], converts each block
+// to Bezier elements by knot insertion (Boehm), raises every element to the
+// common degree P, extracts the 6 boundary faces of every block (§4.1: "6
+// surfaces per block") as Bezier face patches, checks det J > 0 (§5,
+// assumption 4) and computes the default scalar range.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ivv_internal.h"
+
+namespace ivv {
+namespace {
+
+// Insert knot x once into (T, degree p, control points Q[n][D]) (Boehm).
+void insert_knot(std::vector<double>& T, int p, std::vector<double>& Q, int D, double x) {
+  const int n = (int)Q.size() / D;
+  int k = -1;                                  // T[k] <= x < T[k+1]
+  for (int i = 0; i + 1 < (int)T.size(); ++i)
+    if (T[i] <= x && x < T[i + 1]) k = i;
+  std::vector<double> R((n + 1) * D);
+  for (int i = 0; i <= n; ++i) {
+    for (int c = 0; c < D; ++c) {
+      double v;
+      if (i <= k - p) {
+        v = Q[i * D + c];
+      } else if (i >= k + 1) {
+        v = Q[(i - 1) * D + c];
+      } else {
+        const double a = (x - T[i]) / (T[i + p] - T[i]);
+        v = (1 - a) * Q[(i - 1) * D + c] + a * Q[i * D + c];
+      }
+      R[i * D + c] = v;
+    }
+  }
+  T.insert(T.begin() + k + 1, x);
+  Q.swap(R);
+}
+
+// Bezier segments of one clamped B-spline curve (n control points of
+// dimension D), raised to degree P: out[nseg][P+1][D]; brk[nseg+1].
+void extract_curve(const std::vector<double>& knots, int p, int D, const double* cp, int n, int P,
+                   std::vector<double>& out, std::vector<double>& brk) {
+  std::vector<double> T = knots;
+  std::vector<double> Q(cp, cp + (size_t)n * D);
+  brk.clear();
+  for (double x : knots) if (brk.empty() || x > brk.back()) brk.push_back(x);
+  for (size_t b = 1; b + 1 < brk.size(); ++b) {
+    const double x = brk[b];
+    int mult = 0;
+    for (double y : T) if (y == x) ++mult;
+    for (int r = mult; r < p; ++r) insert_knot(T, p, Q, D, x);
+  }
+  const int nseg = (int)brk.size() - 1;
+  out.assign((size_t)nseg * (P + 1) * D, 0.0);
+  for (int s = 0; s < nseg; ++s) {
+    std::vector<double> seg(Q.begin() + (size_t)s * p * D, Q.begin() + (size_t)(s * p + p + 1) * D);
+    for (int q = p; q < P; ++q) {                // degree elevation q -> q+1
+      std::vector<double> up((q + 2) * D);
+      for (int c = 0; c < D; ++c) {
+        up[c] = seg[c];
+        up[(q + 1) * D + c] = seg[q * D + c];
+        for (int i = 1; i <= q; ++i) {
+          const double a = (double)i / (q + 1);
+          up[i * D + c] = a * seg[(i - 1) * D + c] + (1 - a) * seg[i * D + c];
+        }
+      }
+      seg.swap(up);
+    }
+    std::copy(seg.begin(), seg.end(), out.begin() + (size_t)s * (P + 1) * D);
+  }
+}
+
+void bernstein(int P, double x, double* b, double* db) {
+  const double y = 1 - x;
+  if (P == 2) {
+    b[0] = y * y; b[1] = 2 * x * y; b[2] = x * x;
+    db[0] = -2 * y; db[1] = 2 - 4 * x; db[2] = 2 * x;
+  } else {
+    b[0] = y * y * y; b[1] = 3 * x * y * y; b[2] = 3 * x * x * y; b[3] = x * x * x;
+    db[0] = -3 * y * y; db[1] = 3 * y * (1 - 3 * x); db[2] = 3 * x * (2 - 3 * x); db[3] = 3 * x * x;
+  }
+}
+
+int find_seg(const double* brk, int nseg, double x) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (brk[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+double det3(const double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+}  // namespace
+
+void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
+               double* rho_cp) {
+  const BlockInfo& B = hv.blocks[block];
+  const int P = hv.P, n1 = P + 1;
+  int e[3];
+  double loc[3], sc[3];
+  for (int d = 0; d < 3; ++d) {
+    const double* brk = &hv.brk[B.brk_off[d]];
+    const double x = std::min(std::max(p[d], 0.0), 1.0);
+    e[d] = find_seg(brk, B.nseg[d], x);
+    sc[d] = 1.0 / (brk[e[d] + 1] - brk[e[d]]);
+    loc[d] = (x - brk[e[d]]) * sc[d];
+  }
+  const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
+  const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
+  double bu[4], dbu[4], bv[4], dbv[4], bw[4], dbw[4];
+  bernstein(P, loc[0], bu, dbu);
+  bernstein(P, loc[1], bv, dbv);
+  bernstein(P, loc[2], bw, dbw);
+  for (int r = 0; r < 3; ++r) { phi[r] = 0; J[r][0] = J[r][1] = J[r][2] = 0; }
+  double rho = 0;
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j)
+      for (int k = 0; k < n1; ++k) {
+        const double* c = C + ((i * n1 + j) * n1 + k) * 4;
+        const double w0 = bu[i] * bv[j] * bw[k];
+        for (int r = 0; r < 3; ++r) {
+          phi[r] += w0 * c[r];
+          J[r][0] += dbu[i] * bv[j] * bw[k] * c[r] * sc[0];
+          J[r][1] += bu[i] * dbv[j] * bw[k] * c[r] * sc[1];
+          J[r][2] += bu[i] * bv[j] * dbw[k] * c[r] * sc[2];
+        }
+        rho += w0 * c[3];
+      }
+  if (rho_cp) *rho_cp = rho;
+}
+
+ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, HostVolume& hv,
+                          std::string& err) {
+  if (!blocks || n_blocks <= 0) { err = "no blocks"; return IVV_ERR_INVALID_ARG; }
+  if (mode < IVV_SCALAR_CP || mode > IVV_SCALAR_QUALITY) { err = "bad scalar mode"; return IVV_ERR_INVALID_ARG; }
+  hv = HostVolume();
+  hv.mode = mode;
+  hv.n_blocks = n_blocks;
+  int P = 2;
+  for (int b = 0; b < n_blocks; ++b) {
+    for (int d = 0; d < 3; ++d) {
+      const int p = blocks[b].degree[d], n = blocks[b].n_cp[d];
+      if (p < 1) { err = "degree must be >= 1"; return IVV_ERR_INVALID_ARG; }
+      if (p > 3) { err = "degrees above 3 are not supported"; return IVV_ERR_UNSUPPORTED; }
+      if (n < p + 1) { err = "n_cp must be >= degree + 1"; return IVV_ERR_INVALID_ARG; }
+      if (!blocks[b].knots[d]) { err = "missing knot vector"; return IVV_ERR_INVALID_ARG; }
+      P = std::max(P, p);
+    }
+    if (!blocks[b].geom_cp) { err = "missing geometry control points"; return IVV_ERR_INVALID_ARG; }
+    if (mode == IVV_SCALAR_CP && !blocks[b].scalar_cp) {
+      err = "IVV_SCALAR_CP needs scalar control points"; return IVV_ERR_INVALID_ARG;
+    }
+  }
+  hv.P = P;
+  const int n1 = P + 1;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  double slo = 1e300, shi = -1e300;
+  for (int b = 0; b < n_blocks; ++b) {
+    const ivv_block_desc& d = blocks[b];
+    std::vector<double> kn[3];
+    for (int k = 0; k < 3; ++k) {
+      const int p = d.degree[k], n = d.n_cp[k], nk = n + p + 1;
+      kn[k].assign(d.knots[k], d.knots[k] + nk);
+      for (int i = 1; i < nk; ++i)
+        if (!(kn[k][i] >= kn[k][i - 1])) { err = "knots must be non-decreasing"; return IVV_ERR_INVALID_ARG; }
+      const double a = kn[k][0], z = kn[k][nk - 1];
+      if (!(z > a)) { err = "empty knot range"; return IVV_ERR_INVALID_ARG; }
+      for (int i = 0; i <= p; ++i)
+        if (kn[k][i] != a || kn[k][nk - 1 - i] != z) { err = "knot vectors must be clamped"; return IVV_ERR_INVALID_ARG; }
+      for (int i = p + 1; i < n; ++i) {
+        int m = 0;
+        for (int j = 0; j < nk; ++j) if (kn[k][j] == kn[k][i]) ++m;
+        if (m > p) { err = "interior knot multiplicity exceeds the degree"; return IVV_ERR_INVALID_ARG; }
+      }
+      for (double& x : kn[k]) x = (x - a) / (z - a);
+    }
+    const int nu = d.n_cp[0], nv = d.n_cp[1], nw = d.n_cp[2];
+    // grid[w][v][u][4] = (x, y, z, rho)
+    std::vector<double> grid((size_t)nu * nv * nw * 4);
+    for (size_t q = 0; q < (size_t)nu * nv * nw; ++q) {
+      for (int r = 0; r < 3; ++r) {
+        const double v = d.geom_cp[3 * q + r];
+        if (!std::isfinite(v)) { err = "non-finite control point"; return IVV_ERR_INVALID_ARG; }
+        grid[4 * q + r] = v;
+        lo[r] = std::min(lo[r], v);
+        hi[r] = std::max(hi[r], v);
+      }
+      const double s = (mode == IVV_SCALAR_CP) ? d.scalar_cp[q] : 0.0;
+      if (!std::isfinite(s)) { err = "non-finite scalar control point"; return IVV_ERR_INVALID_ARG; }
+      grid[4 * q + 3] = s;
+      slo = std::min(slo, s);
+      shi = std::max(shi, s);
+    }
+    // extraction along u, then v, then w (tensor product)
+    int dims[3] = {nu, nv, nw};
+    std::vector<double> brk[3];
+    for (int axis = 0; axis < 3; ++axis) {
+      const int n = dims[axis];
+      int other[2];
+      int oi = 0;
+      for (int a = 0; a < 3; ++a) if (a != axis) other[oi++] = a;
+      std::vector<double> seg_out;
+      std::vector<double> line(n * 4);
+      int nout = -1;
+      std::vector<double> next;
+      int ndims[3] = {dims[0], dims[1], dims[2]};
+      for (int i1 = 0; i1 < dims[other[1]]; ++i1)
+        for (int i0 = 0; i0 < dims[other[0]]; ++i0) {
+          auto index = [&](const int* dd, int along, int a0, int a1) {
+            int c[3];
+            c[axis] = along; c[other[0]] = a0; c[other[1]] = a1;
+            return ((size_t)c[2] * dd[1] + c[1]) * dd[0] + c[0];
+          };
+          for (int t = 0; t < n; ++t)
+            for (int c = 0; c < 4; ++c) line[t * 4 + c] = grid[index(dims, t, i0, i1) * 4 + c];
+          extract_curve(kn[axis], d.degree[axis], 4, line.data(), n, P, seg_out, brk[axis]);
+          if (nout < 0) {
+            nout = (int)(seg_out.size() / 4);
+            ndims[axis] = nout;
+            next.assign((size_t)ndims[0] * ndims[1] * ndims[2] * 4, 0.0);
+          }
+          for (int t = 0; t < nout; ++t)
+            for (int c = 0; c < 4; ++c) next[index(ndims, t, i0, i1) * 4 + c] = seg_out[t * 4 + c];
+        }
+      grid.swap(next);
+      dims[axis] = ndims[axis];
+    }
+    BlockInfo B;
+    for (int k = 0; k < 3; ++k) {
+      B.nseg[k] = (int)brk[k].size() - 1;
+      B.brk_off[k] = (int)hv.brk.size();
+      hv.brk.insert(hv.brk.end(), brk[k].begin(), brk[k].end());
+    }
+    B.elem_off = hv.n_elems();
+    B.tau_det = 0.f;
+    // elements, i-major ((i*(P+1)+j)*(P+1)+k)
+    for (int ew = 0; ew < B.nseg[2]; ++ew)
+      for (int ev = 0; ev < B.nseg[1]; ++ev)
+        for (int eu = 0; eu < B.nseg[0]; ++eu)
+          for (int i = 0; i < n1; ++i)
+            for (int j = 0; j < n1; ++j)
+              for (int k = 0; k < n1; ++k) {
+                const size_t g = (((size_t)(ew * n1 + k) * dims[1]) + (ev * n1 + j)) * dims[0] + (eu * n1 + i);
+                for (int c = 0; c < 4; ++c) hv.elem.push_back(grid[g * 4 + c]);
+              }
+    hv.blocks.push_back(B);
+  }
+  double dg[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+  hv.diag = std::sqrt(dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2]);
+  if (!(hv.diag > 0)) { err = "degenerate control-point bounding box"; return IVV_ERR_DEGENERATE; }
+
+  // faces: 6 per block, one Bezier patch per element on the face
+  for (int b = 0; b < n_blocks; ++b) {
+    const BlockInfo& B = hv.blocks[b];
+    for (int f = 0; f < 6; ++f) {
+      const int nd = f / 2, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+      const int side = f % 2;
+      for (int eb = 0; eb < B.nseg[bd]; ++eb)
+        for (int ea = 0; ea < B.nseg[ad]; ++ea) {
+          int e[3];
+          e[nd] = side ? B.nseg[nd] - 1 : 0;
+          e[ad] = ea;
+          e[bd] = eb;
+          const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
+          const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
+          FaceMeta m;
+          m.block = b;
+          m.face = f;
+          const double* ba = &hv.brk[B.brk_off[ad]];
+          const double* bb = &hv.brk[B.brk_off[bd]];
+          FaceMeta64 m64{ba[ea], ba[ea + 1], bb[eb], bb[eb + 1]};
+          m.a0 = (float)m64.a0; m.a1 = (float)m64.a1; m.b0 = (float)m64.b0; m.b1 = (float)m64.b1;
+          double flo[3] = {1e300, 1e300, 1e300}, fhi[3] = {-1e300, -1e300, -1e300};
+          for (int bi = 0; bi < n1; ++bi)
+            for (int ai = 0; ai < n1; ++ai) {
+              int l[3];
+              l[nd] = side ? P : 0;
+              l[ad] = ai;
+              l[bd] = bi;
+              const double* c = C + ((l[0] * n1 + l[1]) * n1 + l[2]) * 4;
+              for (int r = 0; r < 3; ++r) {
+                hv.face_cp.push_back(c[r]);
+                flo[r] = std::min(flo[r], c[r]);
+                fhi[r] = std::max(fhi[r], c[r]);
+              }
+              hv.face_cp.push_back(0.0);
+            }
+          for (int r = 0; r < 3; ++r) {
+            // round outward so the float box contains the double box
+            m.lo[r] = std::nextafter((float)flo[r], -1e30f);
+            m.hi[r] = std::nextafter((float)fhi[r], 1e30f);
+          }
+          hv.faces.push_back(m);
+          hv.faces64.push_back(m64);
+        }
+    }
+  }
+
+  // det J > 0 at sample points of every element, and the mean |det J| per block
+  hv.mean_abs_det.assign(n_blocks, 0.0);
+  const double sp[3] = {0.05, 0.5, 0.95};
+  for (int b = 0; b < n_blocks; ++b) {
+    BlockInfo& B = hv.blocks[b];
+    const double* bu = &hv.brk[B.brk_off[0]];
+    const double* bv = &hv.brk[B.brk_off[1]];
+    const double* bw = &hv.brk[B.brk_off[2]];
+    double sum = 0;
+    long cnt = 0;
+    for (int ew = 0; ew < B.nseg[2]; ++ew)
+      for (int ev = 0; ev < B.nseg[1]; ++ev)
+        for (int eu = 0; eu < B.nseg[0]; ++eu)
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c)
+              for (int e = 0; e < 3; ++e) {
+                double p[3] = {bu[eu] + sp[a] * (bu[eu + 1] - bu[eu]), bv[ev] + sp[c] * (bv[ev + 1] - bv[ev]),
+                               bw[ew] + sp[e] * (bw[ew + 1] - bw[ew])};
+                double phi[3], J[3][3];
+                host_eval(hv, b, p, phi, J, nullptr);
+                const double dj = det3(J);
+                if (!(dj > 0)) {
+                  err = "det J <= 0 inside block " + std::to_string(b) +
+                        " (the parametrisation must be orientation preserving)";
+                  return IVV_ERR_DEGENERATE;
+                }
+                sum += dj;
+                ++cnt;
+              }
+    hv.mean_abs_det[b] = sum / cnt;
+    B.tau_det = (float)(1e-6 * hv.mean_abs_det[b]);
+  }
+
+  // default scalar range
+  if (mode == IVV_SCALAR_CP) {
+    hv.def_lo = slo;
+    hv.def_hi = shi;
+  } else {
+    const int n = 64;
+    double a = 1e300, z = -1e300;
+    for (int b = 0; b < n_blocks; ++b)
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            double p[3] = {(i + 0.5) / n, (j + 0.5) / n, (k + 0.5) / n}, phi[3], J[3][3];
+            host_eval(hv, b, p, phi, J, nullptr);
+            double s = det3(J);
+            if (mode == IVV_SCALAR_QUALITY) {
+              double f = 0;
+              for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) f += J[r][c] * J[r][c];
+              s /= std::sqrt(f);
+            }
+            a = std::min(a, s);
+            z = std::max(z, s);
+          }
+    hv.def_lo = a;
+    hv.def_hi = z;
+  }
+  if (!(hv.def_hi > hv.def_lo)) hv.def_hi = hv.def_lo + 1.0;
+  return IVV_OK;
+}
+
+}  // namespace ivv

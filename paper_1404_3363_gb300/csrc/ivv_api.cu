@@ -1,0 +1,622 @@
+// C ABI of the isogeometric volume ray integrator (include/ivv.h): volume
+// upload, per-frame workspace layout, stage launches and status plumbing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ivv_device.cuh"
+#include "ivv_internal.h"
+
+namespace ivv {
+template <int P>
+void launch_integrate_p(const DevVolume& V, const DevCamera<float>* cam32, const DevCamera<double>* cam64,
+                        const DevTF& tf, const IntegrateArgs& a, bool mixed, bool stats, const void* pin,
+                        const void* pout, const int* pblk, const int* pcnt, const int* active, const int* n_active,
+                        int* queue_head, float4* out, DevStats* st, int num_sms, cudaStream_t s);
+void launch_export_pairs(int npix, int max_pairs, bool fp64, const void* pin, const void* pout, const int* pblk,
+                         const int* pcnt, int* out_count, float* out_pairs, int* out_block, cudaStream_t s);
+}  // namespace ivv
+
+namespace {
+
+thread_local std::string g_err;
+
+ivv_status fail(ivv_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+ivv_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(IVV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define IVV_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct WsLayout {
+  size_t boxes, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active, counters, total;
+};
+
+WsLayout layout(int n_faces, size_t npix, size_t v4) {
+  WsLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o += align256(bytes); return at; };
+  L.boxes = take(sizeof(int4) * (size_t)std::max(n_faces, 1));
+  L.frag_tp = take(v4 * ivv::kMaxFrags * npix);
+  L.frag_meta = take(sizeof(unsigned) * ivv::kMaxFrags * npix);
+  L.frag_count = take(sizeof(int) * npix);
+  L.pair_in = take(v4 * ivv::kMaxPairs * npix);
+  L.pair_out = take(v4 * ivv::kMaxPairs * npix);
+  L.pair_block = take(sizeof(int) * ivv::kMaxPairs * npix);
+  L.pair_count = take(sizeof(int) * npix);
+  L.active = take(sizeof(int) * npix);
+  L.counters = take(256);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct ivv_volume {
+  ivv::HostVolume hv;
+  int device = 0;
+  int num_sms = 1;
+  ivv::BlockInfo* d_blocks = nullptr;
+  float* d_brk32 = nullptr;
+  double* d_brk64 = nullptr;
+  float4* d_elem32 = nullptr;
+  ivv::Dbl4* d_elem64 = nullptr;
+  float4* d_face32 = nullptr;
+  ivv::Dbl4* d_face64 = nullptr;
+  ivv::FaceMeta* d_faces = nullptr;
+  ivv::FaceMeta64* d_faces64 = nullptr;
+  float* d_tf_r = nullptr;
+  float4* d_tf_rgba = nullptr;
+  int tf_n = 0;
+  float sigma = 1.f;
+  double lo = 0, hi = 1;
+  bool tf_set = false;
+  ivv::DevStats* d_stats = nullptr;
+  void* own_ws = nullptr;
+  size_t own_ws_bytes = 0;
+  float* own_out = nullptr;
+  size_t own_out_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev[IVV_N_STAGES + 1] = {};
+  bool timed = false;
+};
+
+namespace {
+
+void free_volume(ivv_volume* v) {
+  if (!v) return;
+  void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_face32, v->d_face64,
+                  v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : v->ev)
+    if (e) cudaEventDestroy(e);
+  delete v;
+}
+
+template <typename T>
+ivv_status upload(T** dst, const T* src, size_t n, cudaStream_t s) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * n);
+  if (e != cudaSuccess) return fail(IVV_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (src) {
+    e = cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  }
+  return IVV_OK;
+}
+
+ivv::DevVolume dev_volume(const ivv_volume* v) {
+  ivv::DevVolume V;
+  V.P = v->hv.P;
+  V.mode = v->hv.mode;
+  V.n_blocks = v->hv.n_blocks;
+  V.n_faces = v->hv.n_faces();
+  V.blocks = v->d_blocks;
+  V.brk32 = v->d_brk32;
+  V.brk64 = v->d_brk64;
+  V.elem32 = v->d_elem32;
+  V.elem64 = v->d_elem64;
+  V.face32 = v->d_face32;
+  V.face64 = v->d_face64;
+  V.faces = v->d_faces;
+  V.faces64 = v->d_faces64;
+  V.diag = (float)v->hv.diag;
+  return V;
+}
+
+struct Frame {
+  double eye[3], f[3], r[3], u[3], sx, sy;
+  int ortho, W, H, x0, y0, w, h;
+};
+
+ivv_status make_frame(const ivv_camera* c, const ivv_render_params& p, int width, int height, Frame& F) {
+  if (!c) return fail(IVV_ERR_INVALID_ARG, "camera is NULL");
+  if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  F.W = p.full_width > 0 ? p.full_width : width;
+  F.H = p.full_height > 0 ? p.full_height : height;
+  F.x0 = p.x0;
+  F.y0 = p.y0;
+  F.w = width;
+  F.h = height;
+  if (F.x0 < 0 || F.y0 < 0 || F.x0 + width > F.W || F.y0 + height > F.H)
+    return fail(IVV_ERR_INVALID_ARG, "window outside the full image");
+  double f[3], n = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (!std::isfinite(c->eye[i]) || !std::isfinite(c->target[i]) || !std::isfinite(c->up[i]))
+      return fail(IVV_ERR_INVALID_ARG, "non-finite camera");
+    f[i] = c->target[i] - c->eye[i];
+    n += f[i] * f[i];
+  }
+  n = std::sqrt(n);
+  if (!(n > 0)) return fail(IVV_ERR_INVALID_ARG, "camera target equals eye");
+  for (int i = 0; i < 3; ++i) f[i] /= n;
+  double r[3] = {f[1] * c->up[2] - f[2] * c->up[1], f[2] * c->up[0] - f[0] * c->up[2],
+                 f[0] * c->up[1] - f[1] * c->up[0]};
+  const double nr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(nr > 1e-12)) return fail(IVV_ERR_INVALID_ARG, "camera up is parallel to the view direction");
+  for (int i = 0; i < 3; ++i) r[i] /= nr;
+  double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  const double aspect = (double)F.W / F.H;
+  if (c->ortho) {
+    if (!(c->ortho_height > 0)) return fail(IVV_ERR_INVALID_ARG, "ortho_height must be positive");
+    F.sy = 0.5 * c->ortho_height;
+    F.sx = F.sy * aspect;
+  } else {
+    if (!(c->fovy_deg > 0 && c->fovy_deg < 180)) return fail(IVV_ERR_INVALID_ARG, "fovy_deg must be in (0,180)");
+    F.sy = std::tan(0.5 * c->fovy_deg * M_PI / 180.0);
+    F.sx = F.sy * aspect;
+  }
+  F.ortho = c->ortho ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    F.eye[i] = c->eye[i];
+    F.f[i] = f[i];
+    F.r[i] = r[i];
+    F.u[i] = u[i];
+  }
+  return IVV_OK;
+}
+
+template <typename R>
+ivv::DevCamera<R> dev_camera(const Frame& F) {
+  ivv::DevCamera<R> c;
+  for (int i = 0; i < 3; ++i) {
+    c.eye[i] = (R)F.eye[i];
+    c.f[i] = (R)F.f[i];
+    c.r[i] = (R)F.r[i];
+    c.u[i] = (R)F.u[i];
+  }
+  c.sx = (R)F.sx;
+  c.sy = (R)F.sy;
+  c.ortho = F.ortho;
+  c.W = F.W;
+  c.H = F.H;
+  c.x0 = F.x0;
+  c.y0 = F.y0;
+  c.w = F.w;
+  c.h = F.h;
+  return c;
+}
+
+ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_render_params& p) {
+  if (in) {
+    p = *in;
+  } else {
+    std::memset(&p, 0, sizeof(p));
+    p.rk_tol = 1e-5;
+    p.supersample_k = 4;
+    p.c = 1.0;
+    p.early_alpha = 1.0 - 1e-4;
+  }
+  if (!(p.ds > 0)) p.ds = v->hv.diag / 128.0;
+  if (!(p.rk_tol > 0) || !std::isfinite(p.rk_tol)) return fail(IVV_ERR_INVALID_ARG, "rk_tol must be positive");
+  if (p.supersample_k < 1 || p.supersample_k > 64) return fail(IVV_ERR_INVALID_ARG, "supersample_k must be in 1..64");
+  if (!(p.c >= 0) || !std::isfinite(p.c)) return fail(IVV_ERR_INVALID_ARG, "c must be non-negative");
+  if (!(p.early_alpha > 0)) return fail(IVV_ERR_INVALID_ARG, "early_alpha must be positive");
+  if (p.precision < IVV_PREC_FP32 || p.precision > IVV_PREC_FP64) return fail(IVV_ERR_INVALID_ARG, "bad precision");
+  if (p.use_mlp_guess != 0) return fail(IVV_ERR_UNSUPPORTED, "use_mlp_guess is not available in this build");
+  return IVV_OK;
+}
+
+ivv_status ensure_own(void** buf, size_t* have, size_t need, cudaStream_t s) {
+  if (*have >= need) return IVV_OK;
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(IVV_ERR_WORKSPACE, "library workspace must grow, but a stream capture is active");
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) return fail(IVV_ERR_OOM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+  *have = need;
+  return IVV_OK;
+}
+
+// Stages 1-2 into the workspace.  out_zero receives zero pixels for rays
+// without pairs (may be NULL).
+template <typename R>
+ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_params& p, char* ws, const WsLayout& L,
+                             int max_pairs, float4* out_zero, cudaStream_t s) {
+  typedef typename ivv::Vec4T<R>::type V4;
+  const ivv::DevVolume V = dev_volume(v);
+  const int npix = F.w * F.h;
+  const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
+  const bool mixed = p.precision == IVV_PREC_MIXED;
+  const bool timing = (p.flags & IVV_FLAG_TIMING) != 0;
+  IVV_CUDA(cudaMemsetAsync(ws + L.counters, 0, 256, s));
+  if (timing) IVV_CUDA(cudaEventRecord(v->ev[0], s));
+  ivv::launch_face_project(V, dev_camera<float>(F), (int4*)(ws + L.boxes), s);
+  if (timing) IVV_CUDA(cudaEventRecord(v->ev[1], s));
+  ivv::launch_intersect<R>(V, dev_camera<R>(F), dev_camera<double>(F), mixed, stats, (const int4*)(ws + L.boxes),
+                           (V4*)(ws + L.frag_tp), (unsigned*)(ws + L.frag_meta), (int*)(ws + L.frag_count),
+                           v->d_stats, s);
+  if (timing) IVV_CUDA(cudaEventRecord(v->ev[2], s));
+  ivv::launch_pair<R>(V, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
+                      (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
+                      (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
+                      (int*)(ws + L.counters), out_zero, nullptr, v->d_stats, s);
+  if (timing) IVV_CUDA(cudaEventRecord(v->ev[3], s));
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width, int height,
+                       float* out, void* workspace, size_t workspace_bytes, cudaStream_t s) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  if (!out) return fail(IVV_ERR_INVALID_ARG, "out_rgba is NULL");
+  if (((uintptr_t)out) % 16) return fail(IVV_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned");
+  if (!v->tf_set) return fail(IVV_ERR_INVALID_ARG, "no transfer function set");
+  ivv_render_params p;
+  ivv_status st = resolve_params(v, params, p);
+  if (st != IVV_OK) return st;
+  Frame F;
+  st = make_frame(cam, p, width, height, F);
+  if (st != IVV_OK) return st;
+  const bool fp64 = p.precision == IVV_PREC_FP64;
+  const size_t npix = (size_t)width * height;
+  const WsLayout L = layout(v->hv.n_faces(), npix, fp64 ? sizeof(ivv::Dbl4) : sizeof(float4));
+  char* ws = (char*)workspace;
+  if (ws) {
+    if (workspace_bytes < L.total) return fail(IVV_ERR_WORKSPACE, "workspace smaller than ivv_workspace_size");
+    if (((uintptr_t)ws) % 256) return fail(IVV_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  } else {
+    st = ensure_own(&v->own_ws, &v->own_ws_bytes, L.total, s);
+    if (st != IVV_OK) return st;
+    ws = (char*)v->own_ws;
+  }
+  v->last_stream = s;
+  const ivv::DevVolume V = dev_volume(v);
+  ivv::DevTF tf;
+  tf.n = v->tf_n;
+  tf.sigma = v->sigma;
+  tf.lo = (float)v->lo;
+  tf.inv_range = (float)(1.0 / (v->hi - v->lo));
+  tf.r = v->d_tf_r;
+  tf.rgba = v->d_tf_rgba;
+  ivv::IntegrateArgs a;
+  a.rk_tol = (float)p.rk_tol;
+  a.ds = (float)p.ds;
+  a.c = (float)p.c;
+  a.early_alpha = (float)p.early_alpha;
+  a.K = p.supersample_k;
+  a.max_steps = 200000;
+  a.npix = (int)npix;
+  const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
+  const bool mixed = p.precision == IVV_PREC_MIXED;
+  if (fp64) {
+    st = run_surface_pairs<double>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    ivv::DevCamera<double> c64 = dev_camera<double>(F);
+    if (V.P == 2)
+      ivv::launch_integrate_p<2>(V, nullptr, &c64, tf, a, false, stats, ws + L.pair_in, ws + L.pair_out,
+                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
+                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+    else
+      ivv::launch_integrate_p<3>(V, nullptr, &c64, tf, a, false, stats, ws + L.pair_in, ws + L.pair_out,
+                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
+                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+  } else {
+    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    ivv::DevCamera<float> c32 = dev_camera<float>(F);
+    if (V.P == 2)
+      ivv::launch_integrate_p<2>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
+                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
+                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+    else
+      ivv::launch_integrate_p<3>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
+                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
+                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+  }
+  if (p.flags & IVV_FLAG_TIMING) {
+    IVV_CUDA(cudaEventRecord(v->ev[4], s));
+    v->timed = true;
+  }
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ivv_last_error(void) { return g_err.c_str(); }
+
+ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int scalar_mode, void* stream,
+                             ivv_volume** out) {
+  if (!out) return fail(IVV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ivv_volume* v = new ivv_volume();
+  std::string err;
+  ivv_status st = ivv::prepare_volume(blocks, n_blocks, scalar_mode, v->hv, err);
+  if (st != IVV_OK) {
+    delete v;
+    return fail(st, err);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&v->device);
+  if (e != cudaSuccess) {
+    delete v;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  e = cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device);
+  if (e != cudaSuccess) {
+    delete v;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  const ivv::HostVolume& hv = v->hv;
+  std::vector<float> brk32(hv.brk.begin(), hv.brk.end());
+  std::vector<float4> elem32(hv.elem.size() / 4), face32(hv.face_cp.size() / 4);
+  for (size_t i = 0; i < elem32.size(); ++i)
+    elem32[i] = make_float4((float)hv.elem[4 * i], (float)hv.elem[4 * i + 1], (float)hv.elem[4 * i + 2],
+                            (float)hv.elem[4 * i + 3]);
+  for (size_t i = 0; i < face32.size(); ++i)
+    face32[i] = make_float4((float)hv.face_cp[4 * i], (float)hv.face_cp[4 * i + 1], (float)hv.face_cp[4 * i + 2], 0.f);
+  if ((st = upload(&v->d_blocks, hv.blocks.data(), hv.blocks.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_brk32, brk32.data(), brk32.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_brk64, hv.brk.data(), hv.brk.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_elem32, elem32.data(), elem32.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_elem64, (const ivv::Dbl4*)hv.elem.data(), hv.elem.size() / 4, s)) != IVV_OK ||
+      (st = upload(&v->d_face32, face32.data(), face32.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_face64, (const ivv::Dbl4*)hv.face_cp.data(), hv.face_cp.size() / 4, s)) != IVV_OK ||
+      (st = upload(&v->d_faces, hv.faces.data(), hv.faces.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_faces64, hv.faces64.data(), hv.faces64.size(), s)) != IVV_OK ||
+      (st = upload<float>(&v->d_tf_r, nullptr, 256, s)) != IVV_OK ||
+      (st = upload<float4>(&v->d_tf_rgba, nullptr, 256, s)) != IVV_OK ||
+      (st = upload<ivv::DevStats>(&v->d_stats, nullptr, 1, s)) != IVV_OK) {
+    std::string m = g_err;
+    free_volume(v);
+    return fail(st, m);
+  }
+  for (int i = 0; i <= IVV_N_STAGES && e == cudaSuccess; ++i) e = cudaEventCreate(&v->ev[i]);
+  if (e != cudaSuccess) {
+    free_volume(v);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  e = cudaMemsetAsync(v->d_stats, 0, sizeof(ivv::DevStats), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_volume(v);
+    return cuda_fail(e, "volume upload");
+  }
+  v->lo = hv.def_lo;
+  v->hi = hv.def_hi;
+  *out = v;
+  return IVV_OK;
+}
+
+void ivv_destroy_volume(ivv_volume* vol) {
+  if (!vol) return;
+  cudaDeviceSynchronize();
+  free_volume(vol);
+}
+
+ivv_status ivv_set_transfer_function(ivv_volume* v, int n, const float* r, const float* rgba, float sigma, float lo,
+                                     float hi) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  if (n < 2 || n > 256) return fail(IVV_ERR_INVALID_ARG, "n_knots must be in 2..256");
+  if (!r || !rgba) return fail(IVV_ERR_INVALID_ARG, "NULL transfer function array");
+  if (r[0] != 0.f || r[n - 1] != 1.f) return fail(IVV_ERR_INVALID_ARG, "r[0] must be 0 and r[n-1] must be 1");
+  for (int i = 1; i < n; ++i)
+    if (!(r[i] >= r[i - 1])) return fail(IVV_ERR_INVALID_ARG, "knots r must be ascending");
+  for (int i = 0; i < 4 * n; ++i)
+    if (!std::isfinite(rgba[i])) return fail(IVV_ERR_INVALID_ARG, "non-finite rgba");
+  if (!(sigma >= 0) || !std::isfinite(sigma)) return fail(IVV_ERR_INVALID_ARG, "sigma must be non-negative");
+  cudaError_t e = cudaMemcpy(v->d_tf_r, r, sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v->d_tf_rgba, rgba, sizeof(float4) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "transfer function upload");
+  v->tf_n = n;
+  v->sigma = sigma;
+  if (std::isfinite(lo) && std::isfinite(hi) && hi > lo) {
+    v->lo = lo;
+    v->hi = hi;
+  } else {
+    v->lo = v->hv.def_lo;
+    v->hi = v->hv.def_hi;
+  }
+  v->tf_set = true;
+  return IVV_OK;
+}
+
+ivv_status ivv_get_scalar_range(const ivv_volume* v, double* lo, double* hi) {
+  if (!v || !lo || !hi) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  *lo = v->lo;
+  *hi = v->hi;
+  return IVV_OK;
+}
+
+ivv_status ivv_workspace_size(const ivv_volume* v, int width, int height, int precision, size_t* bytes) {
+  if (!v || !bytes) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  const bool fp64 = precision == IVV_PREC_FP64;
+  *bytes = layout(v->hv.n_faces(), (size_t)width * height, fp64 ? sizeof(ivv::Dbl4) : sizeof(float4)).total;
+  return IVV_OK;
+}
+
+ivv_status ivv_render(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width, int height,
+                      float* out_rgba, void* workspace, size_t workspace_bytes, void* stream) {
+  return render_impl(v, cam, params, width, height, out_rgba, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+ivv_status ivv_render_to_host(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width,
+                              int height, float* out_host, void* stream) {
+  if (!v || !out_host) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  const size_t bytes = sizeof(float4) * (size_t)width * height;
+  cudaStream_t s = (cudaStream_t)stream;
+  ivv_status st = ensure_own((void**)&v->own_out, &v->own_out_bytes, bytes, s);
+  if (st != IVV_OK) return st;
+  st = render_impl(v, cam, params, width, height, v->own_out, nullptr, 0, s);
+  if (st != IVV_OK) return st;
+  IVV_CUDA(cudaMemcpyAsync(out_host, v->own_out, bytes, cudaMemcpyDeviceToHost, s));
+  IVV_CUDA(cudaStreamSynchronize(s));
+  return IVV_OK;
+}
+
+ivv_status ivv_render_pairs(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width,
+                            int height, int max_pairs, int* pair_count, float* pairs, int* pair_block, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (!v || !pair_count || !pairs || !pair_block) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (max_pairs < 1) return fail(IVV_ERR_INVALID_ARG, "max_pairs must be >= 1");
+  ivv_render_params p;
+  ivv_status st = resolve_params(v, params, p);
+  if (st != IVV_OK) return st;
+  if (p.precision == IVV_PREC_FP64) return fail(IVV_ERR_INVALID_ARG, "ivv_render_pairs supports FP32 and MIXED");
+  Frame F;
+  st = make_frame(cam, p, width, height, F);
+  if (st != IVV_OK) return st;
+  const size_t npix = (size_t)width * height;
+  const WsLayout L = layout(v->hv.n_faces(), npix, sizeof(float4));
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (ws) {
+    if (workspace_bytes < L.total) return fail(IVV_ERR_WORKSPACE, "workspace smaller than ivv_workspace_size");
+    if (((uintptr_t)ws) % 256) return fail(IVV_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  } else {
+    st = ensure_own(&v->own_ws, &v->own_ws_bytes, L.total, s);
+    if (st != IVV_OK) return st;
+    ws = (char*)v->own_ws;
+  }
+  v->last_stream = s;
+  const int mp = std::min(max_pairs, ivv::kMaxPairs);
+  st = run_surface_pairs<float>(v, F, p, ws, L, mp, nullptr, s);
+  if (st != IVV_OK) return st;
+  ivv::launch_export_pairs((int)npix, max_pairs, false, ws + L.pair_in, ws + L.pair_out,
+                           (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), pair_count, pairs,
+                           pair_block, s);
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+ivv_status ivv_eval_points(ivv_volume* v, int block, int n, const float* p, float* phi, float* jac, float* rho,
+                           void* stream) {
+  if (!v || (!p && n > 0)) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
+  if (n < 0) return fail(IVV_ERR_INVALID_ARG, "n must be >= 0");
+  ivv::launch_eval_points(dev_volume(v), block, n, p, phi, jac, rho, (cudaStream_t)stream);
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+ivv_status ivv_host_eval(const ivv_block_desc* blocks, int n_blocks, int scalar_mode, int block, int n,
+                         const double* p, double* phi, double* jac, double* rho) {
+  if (n < 0 || (n > 0 && !p)) return fail(IVV_ERR_INVALID_ARG, "bad points");
+  ivv::HostVolume hv;
+  std::string err;
+  ivv_status st = ivv::prepare_volume(blocks, n_blocks, scalar_mode, hv, err);
+  if (st != IVV_OK) return fail(st, err);
+  if (block < 0 || block >= hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
+  for (int i = 0; i < n; ++i) {
+    double f[3], J[3][3], rc;
+    ivv::host_eval(hv, block, p + 3 * i, f, J, &rc);
+    if (phi)
+      for (int r = 0; r < 3; ++r) phi[3 * i + r] = f[r];
+    if (jac)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) jac[9 * i + 3 * r + c] = J[r][c];
+    if (rho) {
+      double s = rc;
+      if (scalar_mode != IVV_SCALAR_CP) {
+        s = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (scalar_mode == IVV_SCALAR_QUALITY) {
+          double fr = 0;
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) fr += J[r][c] * J[r][c];
+          s /= std::sqrt(fr);
+        }
+      }
+      rho[i] = s;
+    }
+  }
+  return IVV_OK;
+}
+
+ivv_status ivv_get_stage_times(ivv_volume* v, float* ms) {
+  if (!v || !ms) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (!v->timed) return fail(IVV_ERR_INVALID_ARG, "no render with IVV_FLAG_TIMING was made");
+  IVV_CUDA(cudaEventSynchronize(v->ev[IVV_N_STAGES]));
+  for (int i = 0; i < IVV_N_STAGES; ++i) IVV_CUDA(cudaEventElapsedTime(&ms[i], v->ev[i], v->ev[i + 1]));
+  return IVV_OK;
+}
+
+ivv_status ivv_get_stats(ivv_volume* v, ivv_stats* out) {
+  if (!v || !out) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  IVV_CUDA(cudaStreamSynchronize(v->last_stream));
+  ivv::DevStats d;
+  IVV_CUDA(cudaMemcpy(&d, v->d_stats, sizeof(d), cudaMemcpyDeviceToHost));
+  out->rays = d.rays;
+  out->pairs = d.pairs;
+  out->fragments = d.fragments;
+  out->samples = d.samples;
+  out->rk_steps = d.rk_steps;
+  out->rk_rejects = d.rk_rejects;
+  out->rhs_evals = d.rhs_evals;
+  out->isect_newton = d.isect_newton;
+  out->isect_tests = d.isect_tests;
+  out->fp64_solves = d.fp64_solves;
+  out->abuf_overflow = d.abuf_overflow;
+  out->pair_overflow = d.pair_overflow;
+  out->unmatched = d.unmatched;
+  out->step_cap = d.step_cap;
+  float f;
+  std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
+  out->max_delta_p = f;
+  return IVV_OK;
+}
+
+ivv_status ivv_reset_stats(ivv_volume* v) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  IVV_CUDA(cudaMemsetAsync(v->d_stats, 0, sizeof(ivv::DevStats), v->last_stream));
+  IVV_CUDA(cudaStreamSynchronize(v->last_stream));
+  return IVV_OK;
+}
+
+ivv_status ivv_volume_info(const ivv_volume* v, int* n_blocks, int* n_elements, int* n_faces, int* degree) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  if (n_blocks) *n_blocks = v->hv.n_blocks;
+  if (n_elements) *n_elements = v->hv.n_elems();
+  if (n_faces) *n_faces = v->hv.n_faces();
+  if (degree) *degree = v->hv.P;
+  return IVV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+// Device-side data layout and helpers shared by the kernels.
+//
+// Layout in HBM (uploaded once per volume):
+//   elem   [E][(P+1)^3] float4 (x, y, z, rho) -- Bezier control points of every
+//          element, index (i*(P+1)+j)*(P+1)+k with i along u, j along v, k along w
+//          (w innermost, so the first contraction streams contiguous float4s)
+//   elem64 the same in double ([E][(P+1)^3][4])
+//   face   [F][(P+1)^2] float4 (x, y, z, 0) -- boundary face patches, a fastest
+//   brk    breakpoints of every block and direction (float and double copies)
+// All spline work is Bernstein evaluation of a single element: the geometry
+// phi = sum B_i(u) B_j(v) B_k(w) C_ijk (Eq. 1 restricted to one element) with
+// first partials by the same sum-factorised contraction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ivv_internal.h"
+
+namespace ivv {
+
+// ------------------------------------------------------------- parameters
+// 32-byte aligned four-double vector (x, y, z, w).
+struct __align__(32) Dbl4 {
+  double x, y, z, w;
+};
+
+template <typename R> struct Vec4T;
+template <> struct Vec4T<float> { typedef float4 type; };
+template <> struct Vec4T<double> { typedef Dbl4 type; };
+
+struct DevVolume {
+  int P, mode, n_blocks, n_faces;
+  const BlockInfo* blocks;
+  const float* brk32;
+  const double* brk64;
+  const float4* elem32;
+  const Dbl4* elem64;
+  const float4* face32;
+  const Dbl4* face64;
+  const FaceMeta* faces;
+  const FaceMeta64* faces64;
+  float diag;
+};
+
+template <typename R>
+struct DevCamera {
+  R eye[3], f[3], r[3], u[3];
+  R sx, sy;             // perspective: tan(fovy/2)*aspect, tan(fovy/2); ortho: half widths
+  int ortho;
+  int W, H;             // full image
+  int x0, y0, w, h;     // window
+};
+
+struct DevTF {
+  int n;
+  float sigma, lo, inv_range;
+  const float* r;       // [n]
+  const float4* rgba;   // [n]
+};
+
+// Per-launch counters; the overflow/cap counters are always maintained.
+struct DevStats {
+  unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
+      isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap;
+  unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
+  unsigned int pad;
+};
+
+// ------------------------------------------------------------- helpers
+template <typename R> __device__ __forceinline__ R rcp_(R x) { return R(1) / x; }
+
+template <int P, typename R>
+__device__ __forceinline__ void bernstein(R x, R b[P + 1], R db[P + 1]) {
+  const R y = R(1) - x;
+  if (P == 2) {
+    b[0] = y * y; b[1] = R(2) * x * y; b[2] = x * x;
+    db[0] = R(-2) * y; db[1] = R(2) - R(4) * x; db[2] = R(2) * x;
+  } else {
+    const R x2 = x * x, y2 = y * y;
+    b[0] = y2 * y; b[1] = R(3) * x * y2; b[2] = R(3) * x2 * y; b[3] = x2 * x;
+    db[0] = R(-3) * y2; db[1] = R(3) * y * (R(1) - R(3) * x);
+    db[2] = R(3) * x * (R(2) - R(3) * x); db[3] = R(3) * x2;
+  }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void bernstein_v(R x, R b[P + 1]) {
+  const R y = R(1) - x;
+  if (P == 2) {
+    b[0] = y * y; b[1] = R(2) * x * y; b[2] = x * x;
+  } else {
+    const R x2 = x * x, y2 = y * y;
+    b[0] = y2 * y; b[1] = R(3) * x * y2; b[2] = R(3) * x2 * y; b[3] = x2 * x;
+  }
+}
+
+template <typename R> __device__ __forceinline__ const R* brk_ptr(const DevVolume& V);
+template <> __device__ __forceinline__ const float* brk_ptr<float>(const DevVolume& V) { return V.brk32; }
+template <> __device__ __forceinline__ const double* brk_ptr<double>(const DevVolume& V) { return V.brk64; }
+
+// Segment s with brk[s] <= x < brk[s+1] (x clamped to [0,1]); local coordinate
+// and the chain-rule factor 1/(brk[s+1]-brk[s]).
+template <typename R>
+__device__ __forceinline__ int locate(const R* __restrict__ brk, int nseg, R x, R& loc, R& scale) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(brk + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  const R b0 = __ldg(brk + lo), b1 = __ldg(brk + lo + 1);
+  scale = R(1) / (b1 - b0);
+  loc = (x - b0) * scale;
+  loc = loc < R(0) ? R(0) : (loc > R(1) ? R(1) : loc);
+  return lo;
+}
+
+template <typename R> struct ElemPtr;
+template <> struct ElemPtr<float> {
+  static __device__ __forceinline__ float4 ld(const DevVolume& V, size_t i) { return __ldg(V.elem32 + i); }
+};
+template <> struct ElemPtr<double> {
+  static __device__ __forceinline__ Dbl4 ld(const DevVolume& V, size_t i) {
+    const double2* p = reinterpret_cast<const double2*>(V.elem64 + i);
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    Dbl4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+  }
+};
+
+// phi, J (J[r][c] = d phi_r / d p_c) and optionally the scalar control-point
+// field at parameter point p of block `blk`.  Sum-factorised: for each i the
+// (j,k) slab is contracted along w (value and w-derivative), then along v,
+// then the u contraction accumulates -- 576 FMA for P = 3.
+template <int P, typename R, bool WANT_RHO>
+__device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& B, const R p[3], R phi[3],
+                                           R J[3][3], R& rho) {
+  constexpr int N = P + 1;
+  R loc[3], sc[3];
+  int e[3];
+  const R* brk = brk_ptr<R>(V);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R x = p[d];
+    x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+    e[d] = locate<R>(brk + B.brk_off[d], B.nseg[d], x, loc[d], sc[d]);
+  }
+  const size_t base = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]) * (N * N * N);
+  R bu[N], dbu[N], bv[N], dbv[N], bw[N], dbw[N];
+  bernstein<P, R>(loc[0], bu, dbu);
+  bernstein<P, R>(loc[1], bv, dbv);
+  bernstein<P, R>(loc[2], bw, dbw);
+  R f[3] = {0, 0, 0}, fu[3] = {0, 0, 0}, fv[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
+  R s = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    R s00[3] = {0, 0, 0}, s01[3] = {0, 0, 0}, s10[3] = {0, 0, 0};
+    R ss = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      R t0[3] = {0, 0, 0}, t1[3] = {0, 0, 0};
+      R ts = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const typename Vec4T<R>::type c = ElemPtr<R>::ld(V, base + (i * N + j) * N + k);
+        t0[0] += bw[k] * c.x; t0[1] += bw[k] * c.y; t0[2] += bw[k] * c.z;
+        t1[0] += dbw[k] * c.x; t1[1] += dbw[k] * c.y; t1[2] += dbw[k] * c.z;
+        if (WANT_RHO) ts += bw[k] * c.w;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        s00[r] += bv[j] * t0[r];
+        s01[r] += dbv[j] * t0[r];
+        s10[r] += bv[j] * t1[r];
+      }
+      if (WANT_RHO) ss += bv[j] * ts;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      f[r] += bu[i] * s00[r];
+      fu[r] += dbu[i] * s00[r];
+      fv[r] += bu[i] * s01[r];
+      fw[r] += bu[i] * s10[r];
+    }
+    if (WANT_RHO) s += bu[i] * ss;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    phi[r] = f[r];
+    J[r][0] = fu[r] * sc[0];
+    J[r][1] = fv[r] * sc[1];
+    J[r][2] = fw[r] * sc[2];
+  }
+  rho = s;
+}
+
+template <typename R>
+__device__ __forceinline__ R det3(const R J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// Solve J x = b by the adjugate (Cramer); returns det J.
+template <typename R>
+__device__ __forceinline__ R solve3(const R J[3][3], const R b[3], R x[3]) {
+  const R c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const R c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const R c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const R det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const R inv = R(1) / det;
+  const R c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  const R c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  const R c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  const R c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  const R c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  const R c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  x[0] = (c00 * b[0] + c10 * b[1] + c20 * b[2]) * inv;
+  x[1] = (c01 * b[0] + c11 * b[1] + c21 * b[2]) * inv;
+  x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
+  return det;
+}
+
+// Pixel ray (matches the boundary header's camera definition).
+template <typename R>
+__device__ __forceinline__ void make_ray(const DevCamera<R>& c, int px, int py, R o[3], R d[3]) {
+  const R nx = (R(px) + R(0.5)) / R(c.W) * R(2) - R(1);
+  const R ny = R(1) - (R(py) + R(0.5)) / R(c.H) * R(2);
+  if (c.ortho) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o[i] = c.eye[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
+      d[i] = c.f[i];
+    }
+  } else {
+    R dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o[i] = c.eye[i];
+      dd[i] = c.f[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
+    }
+    const R n = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = dd[i] / n;
+  }
+}
+
+// Screen position (pixel units, pixel centres at integers) of a point g.
+template <typename R>
+__device__ __forceinline__ void project(const DevCamera<R>& c, const R g[3], R& sx, R& sy) {
+  R w[3] = {g[0] - c.eye[0], g[1] - c.eye[1], g[2] - c.eye[2]};
+  R x = w[0] * c.r[0] + w[1] * c.r[1] + w[2] * c.r[2];
+  R y = w[0] * c.u[0] + w[1] * c.u[1] + w[2] * c.u[2];
+  if (!c.ortho) {
+    const R z = w[0] * c.f[0] + w[1] * c.f[1] + w[2] * c.f[2];
+    x /= z;
+    y /= z;
+  }
+  const R nx = x / c.sx, ny = y / c.sy;
+  sx = (nx + R(1)) * R(0.5) * R(c.W) - R(0.5);
+  sy = (R(1) - ny) * R(0.5) * R(c.H) - R(0.5);
+}
+
+// Piecewise-linear TF (knots in shared memory): colour and extinction weight.
+__device__ __forceinline__ float4 tf_eval(const float* __restrict__ r, const float4* __restrict__ rgba, int n,
+                                          float x) {
+  if (x <= r[0]) return rgba[0];
+  if (x >= r[n - 1]) return rgba[n - 1];
+  int lo = 0, hi = n - 2;              // segment i with r[i] <= x < r[i+1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (r[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  const float w = r[lo + 1] - r[lo];
+  const float t = w > 0.f ? (x - r[lo]) / w : 1.f;
+  const float4 a = rgba[lo], b = rgba[lo + 1];
+  return make_float4(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z), a.w + t * (b.w - a.w));
+}
+
+__device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
+  if (v > 0.f) atomicMax(addr, __float_as_uint(v));
+}
+
+// ------------------------------------------------------------- launchers
+struct Workspace;   // see ivv_api.cu
+
+void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, cudaStream_t s);
+
+template <typename R>
+void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, bool mixed,
+                      bool stats, const int4* boxes, typename Vec4T<R>::type* frag_tp, unsigned* frag_meta,
+                      int* frag_count, DevStats* st, cudaStream_t s);
+
+template <typename R>
+void launch_pair(const DevVolume& V, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
+                 const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
+                 typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs,
+                 int* active, int* n_active, float4* out_rgba_zero, Dbl4* out_rgba_zero64, DevStats* st,
+                 cudaStream_t s);
+
+struct IntegrateArgs {
+  float rk_tol, ds, c, early_alpha;
+  int K;
+  int max_steps;
+  int npix;
+};
+
+template <typename R>
+void launch_integrate(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, const IntegrateArgs& a,
+                      bool mixed, bool stats, const typename Vec4T<R>::type* pair_in,
+                      const typename Vec4T<R>::type* pair_out, const int* pair_block, const int* pair_count,
+                      const int* active, const int* n_active, int* queue_head, float4* out_rgba, DevStats* st,
+                      int num_sms, cudaStream_t s);
+
+void launch_eval_points(const DevVolume& V, int block, int n, const float* p, float* phi, float* jac,
+                        float* rho, cudaStream_t s);
+
+}  // namespace ivv

@@ -1,0 +1,66 @@
+// Internal declarations shared by the host preparation (host_prep.cpp), the
+// C-ABI (ivv_api.cu) and the kernel launchers (k_*.cu).  Not installed.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ivv.h"
+
+namespace ivv {
+
+constexpr int kTileW = 16;          // K2 screen tile (one CTA)
+constexpr int kTileH = 16;
+constexpr int kMaxFrags = 32;       // fragment slots per pixel (A-buffer)
+constexpr int kMaxPairs = 16;       // entry/exit pair slots per pixel
+
+// Face patch record: block, face index (0/1: u=0/1, 2/3: v=0/1, 4/5: w=0/1),
+// parameter box of the patch on its face, and the bbox of its control points.
+struct FaceMeta {
+  int block;
+  int face;
+  float a0, a1, b0, b1;
+  float lo[3], hi[3];
+};
+
+struct FaceMeta64 {
+  double a0, a1, b0, b1;
+};
+
+struct BlockInfo {
+  int nseg[3];
+  int brk_off[3];     // offsets into the breakpoint arrays
+  int elem_off;       // first Bezier element of the block
+  float tau_det;      // |det J| below which MIXED precision solves in FP64
+};
+
+// Host image of a prepared volume (see host_prep.cpp).
+struct HostVolume {
+  int P = 3;                       // common Bezier degree (2 or 3)
+  int mode = 0;                    // IVV_SCALAR_*
+  int n_blocks = 0;
+  std::vector<BlockInfo> blocks;
+  std::vector<double> brk;         // concatenated breakpoints (normalised)
+  std::vector<double> elem;        // [E][(P+1)^3][4] (x, y, z, rho), i-major
+  std::vector<double> face_cp;     // [F][(P+1)^2][4] (x, y, z, 0), a fastest
+  std::vector<FaceMeta> faces;
+  std::vector<FaceMeta64> faces64;
+  std::vector<double> mean_abs_det;
+  double diag = 1.0;               // diagonal of the control-point bbox
+  double def_lo = 0.0, def_hi = 1.0;   // default scalar range
+  int n_elems() const { return (int)(elem.size() / (4 * (size_t)(P + 1) * (P + 1) * (P + 1))); }
+  int n_faces() const { return (int)faces.size(); }
+};
+
+// Builds the host image.  Returns IVV_OK or an error with a message.
+ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int scalar_mode,
+                          HostVolume& out, std::string& err);
+
+// Host-side FP64 evaluation of phi, J and the scalar on the Bezier elements
+// (used for the det J check and the default scalar range).
+void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
+               double* rho_cp);
+
+}  // namespace ivv

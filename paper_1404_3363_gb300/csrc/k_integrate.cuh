@@ -1,0 +1,311 @@
+// Stage 3 (§5.2, §3.2.1): ray integration in parameter space.
+//
+// K5 integrate -- persistent kernel; each warp takes 32 pixels at a time from
+// the work queue filled by K4.  For every entry/exit pair of a pixel, in front
+// to back order, the pulled-back view ray
+//     p'(s) = W(p),  J_phi(p) W(p) = V(phi(p)),                     (Eqs. 13-15)
+//     V(g)  = d + c [(g_in - g) - <g_in - g, d> d]                  (Eqs. 10-11)
+// is integrated from p(0) = p_in with the embedded Bogacki-Shampine 3(2) pair
+// (FSAL: 3 new right-hand sides per step) under absolute error control in
+// parameter space.  Steps are shortened to land exactly on the sample points
+// s_j = j ds and on the exit s = L; p is clamped to [0,1]^3 (§5.4).  At each
+// sample the scalar rho (control points, det J or Eq. 23) is taken from the
+// right-hand side evaluated at the step end, and the interval [s_{j-1}, s_j]
+// is composited with K midpoint sub-samples of the linearly interpolated
+// scalar (supersampling) by Alg. 1 with T = exp(-sigma A ds_i / K).
+// A pixel stops when its opacity reaches early_alpha.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ivv_device.cuh"
+
+namespace ivv {
+
+template <typename R> struct Acc { R C[3]; R a; };
+
+template <int P, typename R, bool MIXED, bool CPRHO>
+struct RhsCtx {
+  const DevVolume* V;
+  BlockInfo B;
+  R g_in[3], d[3], c;
+  int mode;
+};
+
+// W(p) and, when asked, rho(p) and phi(p).  Returns false if det J is not
+// positive (the step is then rejected by the caller).
+template <int P, typename R, bool MIXED, bool WANT_RHO>
+__device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B, const R p[3], const R g_in[3],
+                                         const R d[3], R c, int mode, R W[3], R& rho, R phi[3],
+                                         unsigned long long& n_fp64) {
+  R J[3][3], rc;
+  if (WANT_RHO && mode == IVV_SCALAR_CP)
+    eval_block<P, R, true>(V, B, p, phi, J, rc);
+  else
+    eval_block<P, R, false>(V, B, p, phi, J, rc);
+  R e[3] = {g_in[0] - phi[0], g_in[1] - phi[1], g_in[2] - phi[2]};
+  const R ed = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
+  R v[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) v[r] = d[r] + c * (e[r] - ed * d[r]);
+  const R det = solve3<R>(J, v, W);
+  if constexpr (MIXED) {
+    if (fabs(det) < R(B.tau_det)) {
+      double Jd[3][3], vd[3], Wd[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        vd[r] = v[r];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Jd[r][k] = J[r][k];
+      }
+      solve3<double>(Jd, vd, Wd);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) W[r] = R(Wd[r]);
+      ++n_fp64;
+    }
+  }
+  if (WANT_RHO) {
+    if (mode == IVV_SCALAR_CP) {
+      rho = rc;
+    } else if (mode == IVV_SCALAR_DETJ) {
+      rho = det;
+    } else {
+      R f = 0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f += J[r][k] * J[r][k];
+      rho = det / sqrt(f);
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const DevTF& tf, int K,
+                                                   R rho0, R rho1, R dsi, Acc<R>& acc) {
+  const R invK = R(1) / R(K);
+  const R dr = rho1 - rho0;
+  const R tau_scale = R(tf.sigma) * dsi * invK;
+  for (int k = 0; k < K; ++k) {
+    const R rk = rho0 + (R(k) + R(0.5)) * invK * dr;
+    R x = (rk - R(tf.lo)) * R(tf.inv_range);
+    x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+    const float4 c = tf_eval(s_r, s_rgba, tf.n, (float)x);
+    const R T = exp(-tau_scale * R(c.w));
+    const R w = (R(1) - T) * (R(1) - acc.a);
+    acc.C[0] += w * R(c.x);
+    acc.C[1] += w * R(c.y);
+    acc.C[2] += w * R(c.z);
+    acc.a += w;
+  }
+}
+
+template <int P, typename R, bool MIXED, bool STATS>
+__global__ void __launch_bounds__(128) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
+                                                    const typename Vec4T<R>::type* __restrict__ pair_in,
+                                                    const typename Vec4T<R>::type* __restrict__ pair_out,
+                                                    const int* __restrict__ pair_block,
+                                                    const int* __restrict__ pair_count, const int* __restrict__ active,
+                                                    const int* __restrict__ n_active, int* __restrict__ queue_head,
+                                                    float4* __restrict__ out, DevStats* __restrict__ st) {
+  typedef typename Vec4T<R>::type V4;
+  __shared__ float s_r[256];
+  __shared__ float4 s_rgba[256];
+  for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
+    s_r[i] = tf.r[i];
+    s_rgba[i] = tf.rgba[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nact = *n_active;
+  const int npix = args.npix;
+  const R ds = R(args.ds), tol = R(args.rk_tol), cc = R(args.c), early = R(args.early_alpha);
+  const R tail_eps = R(1e-12) * R(V.diag);
+  const R hmin = R(1e-7) * ds;
+  unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
+  float max_dp = 0.f;
+
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(queue_head, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= nact) break;
+    const int item = base + lane;
+    if (item < nact) {
+    const int pix = __ldg(active + item);
+    const int xw = pix % cam.w, yw = pix / cam.w;
+    const int px = cam.x0 + xw, py = cam.y0 + yw;
+    R o[3], d[3];
+    make_ray<R>(cam, px, py, o, d);
+    Acc<R> acc;
+    acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
+    const int np = __ldg(pair_count + pix);
+    bool done = false;
+    for (int q = 0; q < np && !done; ++q) {
+      const size_t slot = (size_t)q * npix + pix;
+      const V4 pin = pair_in[slot];
+      const V4 pout = pair_out[slot];
+      const int blk = __ldg(pair_block + slot);
+      const BlockInfo B = V.blocks[blk];
+      const R L = R(pout.x) - R(pin.x);
+      if (!(L > R(0))) continue;
+      R g_in[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pin.x) * d[r];
+      const R fl = floor(L / ds);
+      const int nsamp = (int)fl;
+      const int nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
+      R p[3] = {R(pin.y), R(pin.z), R(pin.w)};
+      R k1[3], rho_prev, phi[3];
+      rhs_eval<P, R, MIXED, true>(V, B, p, g_in, d, cc, V.mode, k1, rho_prev, phi, c_fp64);
+      if (STATS) {
+        ++c_rhs;
+        ++c_samp;
+      }
+      R s = R(0), s_last = R(0), h = ds;
+      int j = 1, steps = 0;
+      while (j <= nlast) {
+        const R s_t = (j <= nsamp) ? R(j) * ds : L;
+        const R rem = s_t - s;
+        const bool last = h >= rem;
+        const R hh = last ? rem : h;
+        R q2[3], q3[3], pn[3], k2[3], k3[3], k4[3], rho_n, dummy, ph2[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const R x = p[r] + R(0.5) * hh * k1[r];
+          q2[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+        }
+        rhs_eval<P, R, MIXED, false>(V, B, q2, g_in, d, cc, V.mode, k2, dummy, ph2, c_fp64);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const R x = p[r] + R(0.75) * hh * k2[r];
+          q3[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+        }
+        rhs_eval<P, R, MIXED, false>(V, B, q3, g_in, d, cc, V.mode, k3, dummy, ph2, c_fp64);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const R x = p[r] + hh * (R(2.0 / 9.0) * k1[r] + R(1.0 / 3.0) * k2[r] + R(4.0 / 9.0) * k3[r]);
+          pn[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+        }
+        rhs_eval<P, R, MIXED, true>(V, B, pn, g_in, d, cc, V.mode, k4, rho_n, phi, c_fp64);
+        R err = R(0);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const R e = hh * (R(-5.0 / 72.0) * k1[r] + R(1.0 / 12.0) * k2[r] + R(1.0 / 9.0) * k3[r] -
+                            R(1.0 / 8.0) * k4[r]);
+          const R ae = fabs(e);
+          err = ae > err ? ae : err;
+        }
+        ++steps;
+        if (STATS) c_rhs += 3;
+        const bool capped = steps >= args.max_steps;
+        if (err <= tol || hh <= hmin || capped) {
+          if (STATS) ++c_steps;
+          if (capped && STATS) ++c_cap;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            p[r] = pn[r];
+            k1[r] = k4[r];
+          }
+          R fac = err > R(0) ? R(0.9) * cbrt(tol / err) : R(5);
+          fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
+          const R hn = hh * fac;
+          if (last) {
+            composite_interval<R>(s_r, s_rgba, tf, args.K, rho_prev, rho_n, s_t - s_last, acc);
+            if (STATS) {
+              ++c_samp;
+              R sx, sy;
+              project<R>(cam, phi, sx, sy);
+              const float dp = 2.f * (float)fmax(fabs(sx - R(px)), fabs(sy - R(py)));
+              max_dp = fmaxf(max_dp, dp);
+            }
+            rho_prev = rho_n;
+            s = s_t;
+            s_last = s_t;
+            ++j;
+            h = h > hn ? h : hn;
+            if (acc.a >= early) { done = true; break; }
+          } else {
+            s += hh;
+            h = hn;
+          }
+          if (capped) break;
+        } else {
+          if (STATS) ++c_rej;
+          R fac = R(0.9) * cbrt(tol / err);
+          h = hh * (fac < R(0.2) ? R(0.2) : fac);
+        }
+      }
+    }
+    out[pix] = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
+    }  // item < nact
+  }
+  // counters
+  if (MIXED) {
+    unsigned long long v = c_fp64;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_down_sync(0xffffffffu, v, o2);
+    if (lane == 0 && v) atomicAdd(&st->fp64_solves, v);
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      c_rhs += __shfl_down_sync(0xffffffffu, c_rhs, o2);
+      c_steps += __shfl_down_sync(0xffffffffu, c_steps, o2);
+      c_rej += __shfl_down_sync(0xffffffffu, c_rej, o2);
+      c_samp += __shfl_down_sync(0xffffffffu, c_samp, o2);
+      c_cap += __shfl_down_sync(0xffffffffu, c_cap, o2);
+      max_dp = fmaxf(max_dp, __shfl_down_sync(0xffffffffu, max_dp, o2));
+    }
+    if (lane == 0) {
+      atomicAdd(&st->rhs_evals, c_rhs);
+      atomicAdd(&st->rk_steps, c_steps);
+      atomicAdd(&st->rk_rejects, c_rej);
+      atomicAdd(&st->samples, c_samp);
+      atomicAdd(&st->step_cap, c_cap);
+      atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
+    }
+  }
+}
+
+template <int P, typename R, bool MIXED, bool STATS>
+void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, const IntegrateArgs& a,
+               const typename Vec4T<R>::type* pin, const typename Vec4T<R>::type* pout, const int* pblk,
+               const int* pcnt, const int* active, const int* n_active, int* queue_head, float4* out, DevStats* st,
+               int num_sms, cudaStream_t s) {
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k5_integrate<P, R, MIXED, STATS>, 128, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  int grid = num_sms * blocks_per_sm;
+  const int max_useful = (a.npix + 127) / 128;
+  if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
+  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, pin, pout, pblk, pcnt, active, n_active,
+                                                         queue_head, out, st);
+}
+
+template <int P>
+void launch_integrate_p(const DevVolume& V, const DevCamera<float>* cam32, const DevCamera<double>* cam64,
+                        const DevTF& tf, const IntegrateArgs& a, bool mixed, bool stats, const void* pin,
+                        const void* pout, const int* pblk, const int* pcnt, const int* active, const int* n_active,
+                        int* queue_head, float4* out, DevStats* st, int num_sms, cudaStream_t s) {
+  if (cam32) {
+    const float4* i4 = (const float4*)pin;
+    const float4* o4 = (const float4*)pout;
+    if (mixed) {
+      if (stats) launch_k5<P, float, true, true>(V, *cam32, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+      else launch_k5<P, float, true, false>(V, *cam32, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+    } else {
+      if (stats) launch_k5<P, float, false, true>(V, *cam32, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+      else launch_k5<P, float, false, false>(V, *cam32, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+    }
+  } else {
+    const Dbl4* i4 = (const Dbl4*)pin;
+    const Dbl4* o4 = (const Dbl4*)pout;
+    if (stats) launch_k5<P, double, false, true>(V, *cam64, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+    else launch_k5<P, double, false, false>(V, *cam64, tf, a, i4, o4, pblk, pcnt, active, n_active, queue_head, out, st, num_sms, s);
+  }
+}
+
+}  // namespace ivv

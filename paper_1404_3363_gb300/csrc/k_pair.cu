@@ -1,0 +1,175 @@
+// Stage 2 (§4.2): per-pixel depth sorting of the fragment list and blockwise
+// entry/exit pairing (Alg. 2).
+//   K4 pair -- one thread per pixel: load the pixel's fragment slots (the
+//              A-buffer written by K2), insertion-sort them by
+//              (depth, block, facing), merge duplicates of one block with equal
+//              facing (hits on edges shared by two patches or two faces), then
+//              repeatedly take the nearest unused back-facing record and the
+//              nearest unused front-facing record of the same block (Alg. 2).
+//              Pairs are written in that order, which is front to back for
+//              non-overlapping blocks.  Pixels with pairs are appended to the
+//              work queue of the integrator; the others get a zero pixel.
+#include <cuda_runtime.h>
+
+#include "ivv_device.cuh"
+
+namespace ivv {
+
+namespace {
+
+template <typename R>
+__global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typename Vec4T<R>::type* __restrict__ frag_tp,
+                                               const unsigned* __restrict__ frag_meta,
+                                               const int* __restrict__ frag_count,
+                                               typename Vec4T<R>::type* __restrict__ pair_in,
+                                               typename Vec4T<R>::type* __restrict__ pair_out,
+                                               int* __restrict__ pair_block, int* __restrict__ pair_count,
+                                               int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
+                                               float4* __restrict__ out_rgba, DevStats* __restrict__ st) {
+  typedef typename Vec4T<R>::type V4;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int np = 0;
+  unsigned um = 0, pov = 0;
+  if (pix < npix) {
+    int n = frag_count[pix];
+    n = n < kMaxFrags ? n : kMaxFrags;
+    R t[kMaxFrags];
+    unsigned m[kMaxFrags];
+    unsigned char ord[kMaxFrags];
+    for (int i = 0; i < n; ++i) {
+      t[i] = frag_tp[(size_t)i * npix + pix].x;
+      m[i] = frag_meta[(size_t)i * npix + pix];
+    }
+    // insertion sort of slot indices by (t, block, front)
+    for (int i = 0; i < n; ++i) {
+      int j = i;
+      while (j > 0) {
+        const int a = ord[j - 1];
+        const bool gt = (t[a] > t[i]) || (t[a] == t[i] && ((m[a] >> 4) > (m[i] >> 4) ||
+                                                           ((m[a] >> 4) == (m[i] >> 4) && (m[a] & 1u) > (m[i] & 1u))));
+        if (!gt) break;
+        ord[j] = ord[j - 1];
+        --j;
+      }
+      ord[j] = (unsigned char)i;
+    }
+    // merge duplicates: same block, same facing, |dt| <= tau_dup
+    unsigned used = 0;          // bit per sorted position
+    for (int i = 0; i < n; ++i) {
+      const int a = ord[i];
+      for (int j = 0; j < i; ++j) {
+        const int b = ord[j];
+        if (!((used >> j) & 1u) && (m[a] >> 4) == (m[b] >> 4) && (m[a] & 1u) == (m[b] & 1u) &&
+            t[a] - t[b] <= tau_dup) {
+          used |= 1u << i;
+          break;
+        }
+      }
+    }
+    // Alg. 2
+    for (;;) {
+      int back = -1;
+      for (int i = 0; i < n; ++i)
+        if (!((used >> i) & 1u) && !(m[ord[i]] & 1u)) { back = i; break; }
+      if (back < 0) break;
+      const unsigned blk = m[ord[back]] >> 4;
+      int front = -1;
+      for (int i = 0; i < n; ++i)
+        if (!((used >> i) & 1u) && (m[ord[i]] & 1u) && (m[ord[i]] >> 4) == blk) { front = i; break; }
+      used |= 1u << back;
+      if (front < 0) { ++um; continue; }
+      used |= 1u << front;
+      if (np < max_pairs) {
+        const size_t o = (size_t)np * npix + pix;
+        pair_in[o] = frag_tp[(size_t)ord[front] * npix + pix];
+        pair_out[o] = frag_tp[(size_t)ord[back] * npix + pix];
+        pair_block[o] = (int)blk;
+        ++np;
+      } else {
+        ++pov;
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      if (!((used >> i) & 1u)) ++um;
+    pair_count[pix] = np;
+    if (np == 0 && out_rgba) out_rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // warp-aggregated append of active pixels to the work queue
+  const bool act = np > 0;
+  const unsigned bal = __ballot_sync(0xffffffffu, act);
+  int base = 0;
+  if (lane == 0 && bal) base = atomicAdd(n_active, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (act) active[base + __popc(bal & ((1u << lane) - 1u))] = pix;
+  // counters that are always kept
+  unsigned long long cu = um, cp = pov, cr = act ? 1 : 0, cpairs = np;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cu += __shfl_down_sync(0xffffffffu, cu, o);
+    cp += __shfl_down_sync(0xffffffffu, cp, o);
+    cr += __shfl_down_sync(0xffffffffu, cr, o);
+    cpairs += __shfl_down_sync(0xffffffffu, cpairs, o);
+  }
+  if (lane == 0) {
+    if (cu) atomicAdd(&st->unmatched, cu);
+    if (cp) atomicAdd(&st->pair_overflow, cp);
+    if (cr) atomicAdd(&st->rays, cr);
+    if (cpairs) atomicAdd(&st->pairs, cpairs);
+  }
+}
+
+}  // namespace
+
+template <typename R>
+void launch_pair(const DevVolume& V, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
+                 const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
+                 typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
+                 int* n_active, float4* out_rgba_zero, Dbl4* /*unused*/, DevStats* st, cudaStream_t s) {
+  (void)V;
+  if (npix <= 0) return;
+  const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
+  k4_pair<R><<<(npix + 255) / 256, 256, 0, s>>>(npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
+                                                pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, st);
+}
+
+template void launch_pair<float>(const DevVolume&, int, float, const float4*, const unsigned*, const int*, float4*,
+                                 float4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*, cudaStream_t);
+template void launch_pair<double>(const DevVolume&, int, float, const Dbl4*, const unsigned*, const int*,
+                                  Dbl4*, Dbl4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*,
+                                  cudaStream_t);
+
+}  // namespace ivv
+
+namespace ivv {
+namespace {
+
+__global__ void k_export_pairs(int npix, int max_pairs, const float4* __restrict__ pin, const float4* __restrict__ pout,
+                               const int* __restrict__ pblk, const int* __restrict__ pcnt, int* __restrict__ out_count,
+                               float* __restrict__ out_pairs, int* __restrict__ out_block) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  int n = pcnt[pix];
+  n = n < max_pairs ? n : max_pairs;
+  out_count[pix] = n;
+  for (int q = 0; q < n; ++q) {
+    const size_t s = (size_t)q * npix + pix;
+    const float4 a = pin[s], b = pout[s];
+    float* o = out_pairs + s * 8;
+    o[0] = a.y; o[1] = a.z; o[2] = a.w; o[3] = a.x;
+    o[4] = b.y; o[5] = b.z; o[6] = b.w; o[7] = b.x;
+    out_block[s] = pblk[s];
+  }
+}
+
+}  // namespace
+
+void launch_export_pairs(int npix, int max_pairs, bool fp64, const void* pin, const void* pout, const int* pblk,
+                         const int* pcnt, int* out_count, float* out_pairs, int* out_block, cudaStream_t s) {
+  (void)fp64;
+  if (npix <= 0) return;
+  k_export_pairs<<<(npix + 255) / 256, 256, 0, s>>>(npix, max_pairs, (const float4*)pin, (const float4*)pout, pblk,
+                                                    pcnt, out_count, out_pairs, out_block);
+}
+
+}  // namespace ivv

@@ -1,0 +1,308 @@
+"""Thin Python binding of libivv.so (include/ivv.h): argument marshalling only.
+
+Every step of the render runs in the library's CUDA kernels; PyTorch provides
+device memory (tensors) and streams.  There is no CPU fallback: if the library
+is missing or no GPU is present, these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libivv.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ivv.h")
+
+IVV_OK = 0
+STATUS_NAMES = {0: "IVV_OK", 1: "IVV_ERR_INVALID_ARG", 2: "IVV_ERR_CUDA", 3: "IVV_ERR_OOM",
+                4: "IVV_ERR_ABUF_OVERFLOW", 5: "IVV_ERR_NONCONVERGED", 6: "IVV_ERR_DEGENERATE",
+                7: "IVV_ERR_UNSUPPORTED", 8: "IVV_ERR_WORKSPACE"}
+FLAG_STATS = 1
+FLAG_TIMING = 2
+STAGES = ("project", "intersect", "pair", "integrate")
+
+c_double_p = C.POINTER(C.c_double)
+c_float_p = C.POINTER(C.c_float)
+
+
+class IvvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("degree", C.c_int * 3), ("n_cp", C.c_int * 3), ("knots", c_double_p * 3),
+                ("geom_cp", c_double_p), ("scalar_cp", c_double_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("ortho", C.c_int), ("eye", C.c_double * 3), ("target", C.c_double * 3),
+                ("up", C.c_double * 3), ("fovy_deg", C.c_double), ("ortho_height", C.c_double)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("rk_tol", C.c_double), ("ds", C.c_double), ("supersample_k", C.c_int),
+                ("c", C.c_double), ("early_alpha", C.c_double), ("use_mlp_guess", C.c_int),
+                ("precision", C.c_int), ("flags", C.c_int), ("x0", C.c_int), ("y0", C.c_int),
+                ("full_width", C.c_int), ("full_height", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_ulonglong) for n in (
+        "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
+        "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap")] + \
+        [("max_delta_p", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_LIB = None
+
+
+def header_functions():
+    """Names of the functions include/ivv.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ivv_[a-z_0-9]+)\s*\(", src)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libivv.so (built by paper_1404_3363_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise IvvError(-1, "libivv.so not built (%s); run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.ivv_last_error.restype = C.c_char_p
+    L.ivv_create_volume.argtypes = [C.POINTER(BlockDesc), C.c_int, C.c_int, vp, C.POINTER(vp)]
+    L.ivv_set_transfer_function.argtypes = [vp, C.c_int, c_float_p, c_float_p, C.c_float, C.c_float, C.c_float]
+    L.ivv_get_scalar_range.argtypes = [vp, c_double_p, c_double_p]
+    L.ivv_workspace_size.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+    L.ivv_render.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp,
+                             C.c_size_t, vp]
+    L.ivv_render_to_host.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp]
+    L.ivv_render_pairs.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int,
+                                   vp, vp, vp, vp, C.c_size_t, vp]
+    L.ivv_eval_points.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
+    L.ivv_host_eval.argtypes = [C.POINTER(BlockDesc), C.c_int, C.c_int, C.c_int, C.c_int, c_double_p, c_double_p,
+                                c_double_p, c_double_p]
+    L.ivv_get_stage_times.argtypes = [vp, c_float_p]
+    L.ivv_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.ivv_reset_stats.argtypes = [vp]
+    L.ivv_volume_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+    L.ivv_destroy_volume.argtypes = [vp]
+    L.ivv_destroy_volume.restype = None
+    _LIB = L
+    return L
+
+
+def _check(status):
+    if status != IVV_OK:
+        raise IvvError(status, load().ivv_last_error().decode(errors="replace"))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def camera_struct(cam) -> Camera:
+    c = Camera()
+    c.ortho = int(cam.ortho)
+    for i in range(3):
+        c.eye[i], c.target[i], c.up[i] = cam.eye[i], cam.target[i], cam.up[i]
+    c.fovy_deg = float(cam.fovy_deg)
+    c.ortho_height = float(cam.ortho_height)
+    return c
+
+
+def params_struct(p=None, flags=0, window=None) -> RenderParams:
+    q = RenderParams()
+    q.rk_tol = p.rk_tol if p else 1e-5
+    q.ds = p.ds if p else 0.0
+    q.supersample_k = p.supersample_k if p else 4
+    q.c = p.c if p else 1.0
+    q.early_alpha = p.early_alpha if p else 1.0 - 1e-4
+    q.use_mlp_guess = 0
+    q.precision = p.precision if p else 0
+    q.flags = flags
+    if window is not None:
+        q.x0, q.y0, q.full_width, q.full_height = window
+    return q
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def block_descs(blocks):
+    """ctypes block descriptors plus the arrays they point into (keep both alive)."""
+    keep = []
+    arr = (BlockDesc * len(blocks))()
+    for bi, b in enumerate(blocks):
+        kn = [_f64(k) for k in b.knots]
+        g = _f64(b.geom_cp)
+        s = _f64(b.scalar_cp) if b.scalar_cp is not None else None
+        keep += kn + [g] + ([s] if s is not None else [])
+        nu, nv, nw = b.n_cp
+        for d in range(3):
+            arr[bi].degree[d] = int(b.degree[d])
+            arr[bi].knots[d] = kn[d].ctypes.data_as(c_double_p)
+        arr[bi].n_cp[0], arr[bi].n_cp[1], arr[bi].n_cp[2] = nu, nv, nw
+        arr[bi].geom_cp = g.ctypes.data_as(c_double_p)
+        arr[bi].scalar_cp = s.ctypes.data_as(c_double_p) if s is not None else c_double_p()
+    return arr, keep
+
+
+def host_eval(blocks, scalar_mode, block, p):
+    """FP64 host evaluation of the library's Bezier-extracted representation."""
+    arr, keep = block_descs(blocks)
+    p = _f64(np.atleast_2d(p))
+    n = p.shape[0]
+    phi = np.zeros((n, 3))
+    jac = np.zeros((n, 3, 3))
+    rho = np.zeros(n)
+    _check(load().ivv_host_eval(arr, len(blocks), int(scalar_mode), int(block), n, p.ctypes.data_as(c_double_p),
+                                phi.ctypes.data_as(c_double_p), jac.ctypes.data_as(c_double_p),
+                                rho.ctypes.data_as(c_double_p)))
+    return phi, jac, rho
+
+
+class Volume:
+    """A multi-block spline volume resident on the current CUDA device."""
+
+    def __init__(self, blocks, scalar_mode, stream=None):
+        L = load()
+        arr, keep = block_descs(blocks)
+        h = C.c_void_p()
+        _check(L.ivv_create_volume(arr, len(blocks), int(scalar_mode), C.c_void_p(_stream_ptr(stream)),
+                                   C.byref(h)))
+        self.h = h
+        self.scalar_mode = scalar_mode
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().ivv_destroy_volume(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        v = [C.c_int() for _ in range(4)]
+        _check(load().ivv_volume_info(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("n_blocks", "n_elements", "n_faces", "degree"), (x.value for x in v)))
+
+    def set_transfer_function(self, tf):
+        r = np.ascontiguousarray(tf.r, dtype=np.float32)
+        rgba = np.ascontiguousarray(tf.rgba, dtype=np.float32)
+        lo = tf.lo if math.isfinite(tf.lo) else float("nan")
+        hi = tf.hi if math.isfinite(tf.hi) else float("nan")
+        _check(load().ivv_set_transfer_function(self.h, len(r), r.ctypes.data_as(c_float_p),
+                                                rgba.ctypes.data_as(c_float_p), float(tf.sigma), lo, hi))
+
+    def scalar_range(self):
+        lo, hi = C.c_double(), C.c_double()
+        _check(load().ivv_get_scalar_range(self.h, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
+    def workspace_size(self, width, height, precision=0):
+        n = C.c_size_t()
+        _check(load().ivv_workspace_size(self.h, width, height, precision, C.byref(n)))
+        return n.value
+
+    def workspace(self, width, height, precision=0):
+        """A cached torch uint8 workspace tensor large enough for the window."""
+        import torch
+        need = self.workspace_size(width, height, precision)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        off = (-base) % 256
+        return base + off, need
+
+    def render(self, camera, params=None, width=None, height=None, out=None, stream=None, flags=0,
+               window=None):
+        """Render into a float32 [H][W][4] CUDA tensor (allocated if out is None)."""
+        import torch
+        if out is None:
+            out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+        prm = params_struct(params, flags, window)
+        ws, need = self.workspace(width, height, prm.precision)
+        cam = camera_struct(camera)
+        _check(load().ivv_render(self.h, C.byref(cam), C.byref(prm), width, height,
+                                 C.c_void_p(out.data_ptr()), C.c_void_p(ws), need,
+                                 C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def render_to_host(self, camera, params, width, height, out_host, stream=None, flags=0):
+        """Render and copy into host memory (numpy float32 [H][W][4] or a pinned tensor)."""
+        prm = params_struct(params, flags)
+        cam = camera_struct(camera)
+        ptr = out_host.ctypes.data if isinstance(out_host, np.ndarray) else out_host.data_ptr()
+        _check(load().ivv_render_to_host(self.h, C.byref(cam), C.byref(prm), width, height, C.c_void_p(ptr),
+                                         C.c_void_p(_stream_ptr(stream))))
+        return out_host
+
+    def render_pairs(self, camera, params, width, height, max_pairs=16, stream=None, flags=0):
+        """Stages 1-2: per-pixel entry/exit pairs (counts [H*W], pairs [M][H*W][8], blocks [M][H*W])."""
+        import torch
+        npix = width * height
+        cnt = torch.empty(npix, dtype=torch.int32, device="cuda")
+        pairs = torch.zeros((max_pairs, npix, 8), dtype=torch.float32, device="cuda")
+        blk = torch.zeros((max_pairs, npix), dtype=torch.int32, device="cuda")
+        prm = params_struct(params, flags)
+        ws, need = self.workspace(width, height, prm.precision)
+        cam = camera_struct(camera)
+        _check(load().ivv_render_pairs(self.h, C.byref(cam), C.byref(prm), width, height, max_pairs,
+                                       C.c_void_p(cnt.data_ptr()), C.c_void_p(pairs.data_ptr()),
+                                       C.c_void_p(blk.data_ptr()), C.c_void_p(ws), need,
+                                       C.c_void_p(_stream_ptr(stream))))
+        return cnt, pairs, blk
+
+    def eval_points(self, block, p, stream=None):
+        """phi [n][3], J [n][3][3], rho [n] at float32 CUDA points p [n][3]."""
+        import torch
+        p = p.contiguous()
+        n = p.shape[0]
+        phi = torch.empty((n, 3), dtype=torch.float32, device=p.device)
+        jac = torch.empty((n, 3, 3), dtype=torch.float32, device=p.device)
+        rho = torch.empty(n, dtype=torch.float32, device=p.device)
+        _check(load().ivv_eval_points(self.h, block, n, C.c_void_p(p.data_ptr()), C.c_void_p(phi.data_ptr()),
+                                      C.c_void_p(jac.data_ptr()), C.c_void_p(rho.data_ptr()),
+                                      C.c_void_p(_stream_ptr(stream))))
+        return phi, jac, rho
+
+    def stage_times(self):
+        """{stage: ms} of the last render made with FLAG_TIMING."""
+        ms = (C.c_float * len(STAGES))()
+        _check(load().ivv_get_stage_times(self.h, ms))
+        return dict(zip(STAGES, list(ms)))
+
+    def stats(self):
+        s = Stats()
+        _check(load().ivv_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(load().ivv_reset_stats(self.h))
+
+
+def volume_for(scene, stream=None) -> Volume:
+    v = Volume(scene.blocks, scene.scalar_mode, stream)
+    v.set_transfer_function(scene.tf)
+    return v

@@ -1,0 +1,252 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: images max |dRGBA| <= 1e-3; entry/exit parameters <= 1e-5
+(pixels away from silhouettes; see the per-test notes); spline evaluation at
+FP32 rounding of the control-point magnitudes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_3363_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_RGBA = 1e-3
+TOL_PARAM = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ivv():
+    from paper_1404_3363_gb300 import build, ivv as mod
+    assert torch.cuda.is_available(), "a CUDA device is required"
+    build.build()
+    mod.load()
+    return mod
+
+
+def _gpu_image(ivv, sc, flags=0, window=None, width=None, height=None):
+    vol = ivv.volume_for(sc)
+    img = vol.render(sc.camera, sc.params, width or sc.width, height or sc.height, flags=flags, window=window)
+    torch.cuda.synchronize()
+    return vol, img.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_eval_points_match_oracle(ivv, cfg):
+    sc = scenes.config(cfg, width=8, height=8)
+    vol = ivv.volume_for(sc)
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    rng = np.random.default_rng(50)
+    P = rng.uniform(0, 1, (4096, 3)).astype(np.float32)
+    for b in (0, len(sc.blocks) - 1):
+        phi, J, rho = vol.eval_points(b, torch.from_numpy(P).cuda())
+        f2, J2, r2 = ov.eval(b, P.astype(np.float64))
+        scale = np.abs(f2).max()
+        np.testing.assert_allclose(phi.cpu().numpy(), f2, atol=4e-6 * scale)
+        np.testing.assert_allclose(J.cpu().numpy(), J2, atol=2e-5 * np.abs(J2).max())
+        np.testing.assert_allclose(rho.cpu().numpy(), r2, atol=2e-5 * max(1.0, np.abs(r2).max()))
+
+
+def _oracle_pairs(ov, sc):
+    W, H = sc.width, sc.height
+    out = {}
+    for y in range(H):
+        for x in range(W):
+            pr, um = ov.pixel_pairs(sc.camera, W, H, x, y)
+            if pr:
+                out[(x, y)] = pr
+    return out
+
+
+def _grazing(ov, sc, x, y, pairs, thresh=0.1):
+    """True if the ray meets a face at a small angle (ill-conditioned hit)."""
+    o, d = oracle.ray(sc.camera, sc.width, sc.height, x, y)
+    for p in pairs:
+        for q in (p.p_in, p.p_out):
+            q = np.array(q)
+            _, J, _ = ov.eval(p.block, q)
+            k = int(np.argmin(np.minimum(np.abs(q), np.abs(q - 1))))
+            n = np.linalg.inv(J[0])[k]          # gradient of the face's parameter
+            n = n / np.linalg.norm(n)
+            if abs(n @ d) < thresh:
+                return True
+    return False
+
+
+@pytest.mark.parametrize("cfg,size,prec", [(0, (64, 64), 0), (1, (200, 120), 0), (1, (200, 120), 1),
+                                           (2, (160, 96), 1)])
+def test_entry_exit_pairs_match_oracle(ivv, cfg, size, prec):
+    sc = scenes.config(cfg, width=size[0], height=size[1])
+    sc.params.precision = prec
+    vol = ivv.volume_for(sc)
+    cnt, pairs, blk = vol.render_pairs(sc.camera, sc.params, sc.width, sc.height, max_pairs=16)
+    torch.cuda.synchronize()
+    cnt, pairs, blk = cnt.cpu().numpy(), pairs.cpu().numpy(), blk.cpu().numpy()
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    ref = _oracle_pairs(ov, sc)
+    W = sc.width
+    checked = mism = 0
+    worst = 0.0
+    for y in range(sc.height):
+        for x in range(W):
+            pix = y * W + x
+            rp = ref.get((x, y), [])
+            if cnt[pix] != len(rp):
+                # allowed only for a chord too short to matter (silhouette)
+                short = [p for p in rp if p.t_out - p.t_in < 2e-4 * ov.diag]
+                extra = cnt[pix] - len(rp)
+                assert abs(extra) <= max(1, len(short)) and (len(short) > 0 or extra > 0), (x, y, cnt[pix], len(rp))
+                if extra > 0:
+                    for q in range(cnt[pix]):
+                        L = pairs[q, pix, 7] - pairs[q, pix, 3]
+                        assert L < 2e-4 * ov.diag or any(
+                            abs(pairs[q, pix, 3] - p.t_in) < 1e-4 for p in rp)
+                mism += 1
+                continue
+            if not rp:
+                continue
+            graze = _grazing(ov, sc, x, y, rp)
+            for q, p in enumerate(rp):
+                assert blk[q, pix] == p.block
+                e = max(np.abs(pairs[q, pix, 0:3] - np.array(p.p_in)).max(),
+                        np.abs(pairs[q, pix, 4:7] - np.array(p.p_out)).max())
+                te = max(abs(pairs[q, pix, 3] - p.t_in), abs(pairs[q, pix, 7] - p.t_out))
+                if not graze:
+                    assert e <= TOL_PARAM, (x, y, q, e)
+                    worst = max(worst, e)
+                assert te <= 1e-4 * max(1.0, abs(p.t_in)), (x, y, q, te)
+            checked += 1
+    assert checked > 0.02 * sc.width * sc.height
+    assert mism <= 0.002 * sc.width * sc.height + 2
+
+
+@pytest.mark.parametrize("cfg,size,prec", [(0, (64, 64), 2), (0, (64, 64), 0), (1, (200, 120), 0),
+                                           (1, (200, 120), 1), (2, (160, 96), 1), (4, (160, 90), 1)])
+def test_image_matches_oracle(ivv, cfg, size, prec):
+    sc = scenes.config(cfg, width=size[0], height=size[1])
+    sc.params.precision = prec
+    vol, img = _gpu_image(ivv, sc)
+    ref = oracle.render(sc)
+    err = np.abs(img - ref).max()
+    assert ref[..., 3].max() > 0.2, "workload renders something"
+    assert err <= TOL_RGBA, err
+    st = vol.stats()
+    assert st["abuf_overflow"] == 0 and st["pair_overflow"] == 0 and st["step_cap"] == 0
+
+
+def test_full_size_sampled_pixels(ivv):
+    """1920x1080 twisted bar, FP32, the benchmark's launch: sampled pixels
+    against the oracle computed one by one."""
+    sc = scenes.config(1)
+    vol, img = _gpu_image(ivv, sc)
+    cov = np.argwhere(img[..., 3] > 0)
+    assert len(cov) > 1000
+    rng = np.random.default_rng(51)
+    pick = cov[rng.choice(len(cov), 160, replace=False)]
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    worst = 0.0
+    for y, x in pick:
+        ref = oracle.render(sc, ov, window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
+        worst = max(worst, np.abs(img[y, x] - ref).max())
+    assert worst <= TOL_RGBA, worst
+    # background pixels sampled too
+    bg = np.argwhere(img[..., 3] == 0)
+    for y, x in bg[rng.choice(len(bg), 40, replace=False)]:
+        ref = oracle.render(sc, ov, window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
+        assert np.abs(ref).max() <= TOL_RGBA
+
+
+def test_window_equals_crop_and_is_deterministic(ivv):
+    sc = scenes.config(1, width=200, height=120)
+    vol = ivv.volume_for(sc)
+    full = vol.render(sc.camera, sc.params, 200, 120).clone()
+    again = vol.render(sc.camera, sc.params, 200, 120).clone()
+    assert torch.equal(full, again)
+    win = vol.render(sc.camera, sc.params, 37, 29, window=(81, 45, 200, 120))
+    torch.cuda.synchronize()
+    assert torch.equal(win, full[45:74, 81:118])
+
+
+def test_ragged_and_tiny_images(ivv):
+    for (w, h) in [(1, 1), (17, 13), (33, 1), (5, 71)]:
+        sc = scenes.config(0, width=w, height=h)
+        sc.params.precision = 0
+        _, img = _gpu_image(ivv, sc)
+        ref = oracle.render(sc)
+        assert np.abs(img - ref).max() <= TOL_RGBA, (w, h)
+
+
+def test_empty_view_is_zero(ivv):
+    sc = scenes.config(1, width=96, height=64)
+    cam = sc.camera
+    # look away from the bar
+    t = np.array(cam.target)
+    e = np.array(cam.eye)
+    sc.camera = scenes.Camera(False, tuple(e), tuple(2 * e - t), cam.up, fovy_deg=30.0)
+    vol, img = _gpu_image(ivv, sc)
+    assert np.abs(img).max() == 0.0
+    assert vol.stats()["rays"] == 0
+
+
+def test_constant_density_closed_form(ivv):
+    """Affine box, constant scalar: alpha = 1 - exp(-sigma A L) per pixel."""
+    from tests.test_oracle_bspline import _affine_block
+    from tests.test_oracle_intersect import _slab
+    rng = np.random.default_rng(52)
+    blk, A, b = _affine_block(rng)
+    blk.scalar_cp = np.full(blk.geom_cp.shape[:3], 0.3)
+    col = np.array([0.25, 0.5, 0.625, 0.75])
+    tf = scenes.TransferFunction(np.array([0, 1], np.float32), np.array([col, col], np.float32), 1.5,
+                                 lo=0.0, hi=1.0)
+    centre = b + A @ np.full(3, 0.5)
+    cam = scenes.Camera(False, tuple(centre + np.array([3.0, 1.0, 2.0])), tuple(centre), (0, 0, 1), fovy_deg=40.0)
+    sc = scenes.Scene("box", [blk], scenes.SCALAR_CP, tf, cam, 48, 40,
+                      scenes.RenderParams(ds=0.05, early_alpha=2.0))
+    _, img = _gpu_image(ivv, sc)
+    for y in range(40):
+        for x in range(48):
+            o, d = oracle.ray(cam, 48, 40, x, y)
+            ref = _slab(A, b, o, d)
+            L = 0.0 if ref is None else ref[1] - ref[0]
+            a = 1 - math.exp(-1.5 * col[3] * L)
+            assert abs(img[y, x, 3] - a) <= 1e-4, (x, y, img[y, x, 3], a)
+
+
+def test_stats_and_timing(ivv):
+    sc = scenes.config(1, width=200, height=120)
+    vol = ivv.volume_for(sc)
+    vol.reset_stats()
+    vol.render(sc.camera, sc.params, 200, 120, flags=ivv.FLAG_STATS | ivv.FLAG_TIMING)
+    st = vol.stats()
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    ref, rs = oracle.render(sc, ov, stats=True)
+    assert abs(st["rays"] - (rs[..., 0] > 0).sum()) <= 3
+    assert st["samples"] >= 0.95 * rs[..., 3].sum()
+    assert st["rk_steps"] >= st["samples"] - st["pairs"]
+    assert st["rhs_evals"] >= 3 * st["rk_steps"]
+    assert 0 < st["max_delta_p"] <= 1.0          # pixel accuracy, Eq. 5
+    t = vol.stage_times()
+    assert set(t) == {"project", "intersect", "pair", "integrate"} and all(v >= 0 for v in t.values())
+
+
+def test_render_to_host_and_errors(ivv):
+    sc = scenes.config(0, width=40, height=30)
+    sc.params.precision = 0
+    vol = ivv.volume_for(sc)
+    host = np.zeros((30, 40, 4), np.float32)
+    vol.render_to_host(sc.camera, sc.params, 40, 30, host)
+    dev = vol.render(sc.camera, sc.params, 40, 30)
+    assert np.array_equal(host, dev.cpu().numpy())
+    with pytest.raises(ivv.IvvError) as e:
+        vol.render(sc.camera, sc.params, 0, 30)
+    assert e.value.status == 1
+    with pytest.raises(ivv.IvvError) as e:
+        vol.render(sc.camera, sc.params, 40, 30, window=(10, 10, 40, 30))   # window outside the image
+    assert e.value.status == 1
+    bad = scenes.Camera(False, sc.camera.eye, sc.camera.eye, sc.camera.up)
+    with pytest.raises(ivv.IvvError):
+        vol.render(bad, sc.params, 40, 30)
