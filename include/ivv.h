@@ -228,6 +228,17 @@ ivv_status ivv_eval_points(ivv_volume* vol, int block, int n, const float* p, fl
 ivv_status ivv_host_eval(const ivv_block_desc* blocks, int n_blocks, int scalar_mode, int block, int n,
                          const double* p, double* phi, double* jac, double* rho);
 
+/* Host execution of the stage 1-2 code that ivv_render runs on the device
+ * (face boxes, ray/patch roots, fragments, depth sort and Alg. 2), for a
+ * width x height window: inspection and CPU testing of a volume description;
+ * ivv_render never uses it.  Host outputs, caller-owned, same layout as
+ * ivv_render_pairs but double: pair_count [height*width],
+ * pairs [max_pairs][height*width][8], pair_block [max_pairs][height*width]. */
+ivv_status ivv_host_render_pairs(const ivv_block_desc* blocks, int n_blocks, int scalar_mode,
+                                 const ivv_camera* cam, const ivv_render_params* params, int width,
+                                 int height, int max_pairs, int* pair_count, double* pairs,
+                                 int* pair_block);
+
 /* Milliseconds of each stage of the last render made with IVV_FLAG_TIMING
  * (ms[IVV_N_STAGES], CUDA events on the render stream); synchronises that
  * stream.  Returns IVV_ERR_INVALID_ARG if no timed render was made. */

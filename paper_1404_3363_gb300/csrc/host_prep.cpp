@@ -115,6 +115,7 @@ void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3]
   }
   const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
   const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
+  const double* org = &hv.elem_org[(size_t)eid * 4];
   double bu[4], dbu[4], bv[4], dbv[4], bw[4], dbw[4];
   bernstein(P, loc[0], bu, dbu);
   bernstein(P, loc[1], bv, dbv);
@@ -134,6 +135,7 @@ void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3]
         }
         rho += w0 * c[3];
       }
+  for (int r = 0; r < 3; ++r) phi[r] += org[r];
   if (rho_cp) *rho_cp = rho;
 }
 
@@ -241,16 +243,23 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
     }
     B.elem_off = hv.n_elems();
     B.tau_det = 0.f;
-    // elements, i-major ((i*(P+1)+j)*(P+1)+k)
+    // elements, i-major ((i*(P+1)+j)*(P+1)+k); geometry relative to the
+    // element's first control point, which keeps FP32 partials accurate
     for (int ew = 0; ew < B.nseg[2]; ++ew)
       for (int ev = 0; ev < B.nseg[1]; ++ev)
-        for (int eu = 0; eu < B.nseg[0]; ++eu)
+        for (int eu = 0; eu < B.nseg[0]; ++eu) {
+          const size_t g0 = (((size_t)(ew * n1) * dims[1]) + (ev * n1)) * dims[0] + (eu * n1);
+          const double org[3] = {grid[g0 * 4], grid[g0 * 4 + 1], grid[g0 * 4 + 2]};
+          for (int c = 0; c < 3; ++c) hv.elem_org.push_back(org[c]);
+          hv.elem_org.push_back(0.0);
           for (int i = 0; i < n1; ++i)
             for (int j = 0; j < n1; ++j)
               for (int k = 0; k < n1; ++k) {
                 const size_t g = (((size_t)(ew * n1 + k) * dims[1]) + (ev * n1 + j)) * dims[0] + (eu * n1 + i);
-                for (int c = 0; c < 4; ++c) hv.elem.push_back(grid[g * 4 + c]);
+                for (int c = 0; c < 3; ++c) hv.elem.push_back(grid[g * 4 + c] - org[c]);
+                hv.elem.push_back(grid[g * 4 + 3]);
               }
+        }
     hv.blocks.push_back(B);
   }
   double dg[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
@@ -271,14 +280,16 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
           e[bd] = eb;
           const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
           const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
+          const double* eorg = &hv.elem_org[(size_t)eid * 4];
           FaceMeta m;
           m.block = b;
           m.face = f;
           const double* ba = &hv.brk[B.brk_off[ad]];
           const double* bb = &hv.brk[B.brk_off[bd]];
-          FaceMeta64 m64{ba[ea], ba[ea + 1], bb[eb], bb[eb + 1]};
+          FaceMeta64 m64{ba[ea], ba[ea + 1], bb[eb], bb[eb + 1], {0, 0, 0}};
           m.a0 = (float)m64.a0; m.a1 = (float)m64.a1; m.b0 = (float)m64.b0; m.b1 = (float)m64.b1;
           double flo[3] = {1e300, 1e300, 1e300}, fhi[3] = {-1e300, -1e300, -1e300};
+          double forg[3] = {0, 0, 0};
           for (int bi = 0; bi < n1; ++bi)
             for (int ai = 0; ai < n1; ++ai) {
               int l[3];
@@ -286,10 +297,14 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
               l[ad] = ai;
               l[bd] = bi;
               const double* c = C + ((l[0] * n1 + l[1]) * n1 + l[2]) * 4;
+              double g[3];
+              for (int r = 0; r < 3; ++r) g[r] = eorg[r] + c[r];
+              if (ai == 0 && bi == 0)
+                for (int r = 0; r < 3; ++r) forg[r] = g[r];
               for (int r = 0; r < 3; ++r) {
-                hv.face_cp.push_back(c[r]);
-                flo[r] = std::min(flo[r], c[r]);
-                fhi[r] = std::max(fhi[r], c[r]);
+                hv.face_cp.push_back(g[r] - forg[r]);
+                flo[r] = std::min(flo[r], g[r]);
+                fhi[r] = std::max(fhi[r], g[r]);
               }
               hv.face_cp.push_back(0.0);
             }
@@ -297,6 +312,8 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
             // round outward so the float box contains the double box
             m.lo[r] = std::nextafter((float)flo[r], -1e30f);
             m.hi[r] = std::nextafter((float)fhi[r], 1e30f);
+            m.org[r] = (float)forg[r];
+            m64.org[r] = forg[r];
           }
           hv.faces.push_back(m);
           hv.faces64.push_back(m64);

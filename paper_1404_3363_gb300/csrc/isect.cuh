@@ -1,0 +1,542 @@
+// Per-ray work of stages 1 and 2, written once for the device kernels and the
+// host inspection entry point (ivv_host_pixel_pairs):
+//   * face_screen_box  -- conservative pixel box of a face patch (convex hull
+//                          of its control points projected to the screen);
+//   * patch_roots       -- all parameters (a,b) where a Bezier face patch meets
+//                          a ray: control points are expressed in a 2-D frame
+//                          perpendicular to the ray, so roots are zeros of a
+//                          planar Bezier map.  A sub-patch whose hull misses the
+//                          origin is dropped; one whose Jacobian sign is fixed
+//                          (interval bound over its hodographs) holds at most one
+//                          root and is solved by damped Newton from its centre;
+//                          otherwise it is split at 1/2 (de Casteljau) down to a
+//                          fixed depth;
+//   * make_fragment     -- 3-D point, depth t, facing and block parameter point
+//                          of a root;
+//   * pair_fragments    -- depth sort, duplicate merge and Alg. 2 of §4.2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+#include "ivv_internal.h"
+
+namespace ivv {
+
+#ifndef IVV_HD
+#define IVV_HD __host__ __device__ __forceinline__
+#endif
+
+template <typename R> IVV_HD R clamp01r(R x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
+template <typename R> IVV_HD R minr(R a, R b) { return a < b ? a : b; }
+template <typename R> IVV_HD R maxr(R a, R b) { return a > b ? a : b; }
+
+template <int P, typename R>
+IVV_HD void bern_hd(R x, R b[P + 1], R db[P + 1]) {
+  const R y = R(1) - x;
+  if (P == 2) {
+    b[0] = y * y; b[1] = R(2) * x * y; b[2] = x * x;
+    db[0] = R(-2) * y; db[1] = R(2) - R(4) * x; db[2] = R(2) * x;
+  } else {
+    const R x2 = x * x, y2 = y * y;
+    b[0] = y2 * y; b[1] = R(3) * x * y2; b[2] = R(3) * x2 * y; b[3] = x2 * x;
+    db[0] = R(-3) * y2; db[1] = R(3) * y * (R(1) - R(3) * x);
+    db[2] = R(3) * x * (R(2) - R(3) * x); db[3] = R(3) * x2;
+  }
+}
+
+// ------------------------------------------------------------ ray frame
+template <typename R>
+IVV_HD void ray_frame(const R d[3], R e1[3], R e2[3]) {
+  R ax[3] = {R(1), R(0), R(0)};
+  if (fabs(d[0]) > R(0.6)) { ax[0] = R(0); ax[1] = R(1); }
+  e1[0] = d[1] * ax[2] - d[2] * ax[1];
+  e1[1] = d[2] * ax[0] - d[0] * ax[2];
+  e1[2] = d[0] * ax[1] - d[1] * ax[0];
+  const R n = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  e1[0] /= n; e1[1] /= n; e1[2] /= n;
+  e2[0] = d[1] * e1[2] - d[2] * e1[1];
+  e2[1] = d[2] * e1[0] - d[0] * e1[2];
+  e2[2] = d[0] * e1[1] - d[1] * e1[0];
+}
+
+
+// ------------------------------------------------------------ camera
+template <typename R>
+struct DevCamera {
+  R eye[3], f[3], r[3], u[3];
+  R sx, sy;             // perspective: tan(fovy/2)*aspect, tan(fovy/2); ortho: half widths
+  int ortho;
+  int W, H;             // full image
+  int x0, y0, w, h;     // window
+};
+
+// Pixel ray (matches the boundary header's camera definition).
+template <typename R>
+IVV_HD void make_ray(const DevCamera<R>& c, int px, int py, R o[3], R d[3]) {
+  const R nx = (R(px) + R(0.5)) / R(c.W) * R(2) - R(1);
+  const R ny = R(1) - (R(py) + R(0.5)) / R(c.H) * R(2);
+  if (c.ortho) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o[i] = c.eye[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
+      d[i] = c.f[i];
+    }
+  } else {
+    R dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o[i] = c.eye[i];
+      dd[i] = c.f[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
+    }
+    const R n = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = dd[i] / n;
+  }
+}
+
+// Screen position (pixel units, pixel centres at integers) of a point g.
+template <typename R>
+IVV_HD void project(const DevCamera<R>& c, const R g[3], R& sx, R& sy) {
+  R w[3] = {g[0] - c.eye[0], g[1] - c.eye[1], g[2] - c.eye[2]};
+  R x = w[0] * c.r[0] + w[1] * c.r[1] + w[2] * c.r[2];
+  R y = w[0] * c.u[0] + w[1] * c.u[1] + w[2] * c.u[2];
+  if (!c.ortho) {
+    const R z = w[0] * c.f[0] + w[1] * c.f[1] + w[2] * c.f[2];
+    x /= z;
+    y /= z;
+  }
+  const R nx = x / c.sx, ny = y / c.sy;
+  sx = (nx + R(1)) * R(0.5) * R(c.W) - R(0.5);
+  sy = (R(1) - ny) * R(0.5) * R(c.H) - R(0.5);
+}
+
+// Conservative pixel box (x0, y0, x1, y1; empty if x0 > x1) of a face patch
+// with control points org + cp[k]: the patch lies in the convex hull of its
+// control points, whose projection bounds the patch's projection when every
+// control point is in front of the eye.  Patches crossing the eye plane get
+// the whole window; patches entirely behind it get an empty box.
+template <int NN>
+IVV_HD int4 face_screen_box(const DevCamera<float>& cam, const float4* cp, const float org[3], float diag) {
+  float xmin = 1e30f, xmax = -1e30f, ymin = 1e30f, ymax = -1e30f;
+  bool behind_all = true, straddle = false;
+  const float znear = 1e-6f * diag;
+  for (int q = 0; q < NN; ++q) {
+    const float4 c = cp[q];
+    const float g[3] = {org[0] + c.x, org[1] + c.y, org[2] + c.z};
+    const float w[3] = {g[0] - cam.eye[0], g[1] - cam.eye[1], g[2] - cam.eye[2]};
+    const float z = w[0] * cam.f[0] + w[1] * cam.f[1] + w[2] * cam.f[2];
+    if (z > 0.f) behind_all = false;
+    if (!cam.ortho && z <= znear) straddle = true;
+    float sx, sy;
+    project<float>(cam, g, sx, sy);
+    xmin = fminf(xmin, sx); xmax = fmaxf(xmax, sx);
+    ymin = fminf(ymin, sy); ymax = fmaxf(ymax, sy);
+  }
+  int4 b;
+  if (behind_all) {
+    b = make_int4(1, 1, 0, 0);
+  } else if (straddle) {
+    b = make_int4(cam.x0, cam.y0, cam.x0 + cam.w - 1, cam.y0 + cam.h - 1);
+  } else {
+    const float lim = 1e9f;
+    xmin = fmaxf(xmin, -lim); ymin = fmaxf(ymin, -lim);
+    xmax = fminf(xmax, lim); ymax = fminf(ymax, lim);
+    const int bx0 = (int)floorf(xmin) - 1, by0 = (int)floorf(ymin) - 1;
+    const int bx1 = (int)ceilf(xmax) + 1, by1 = (int)ceilf(ymax) + 1;
+    b.x = bx0 > cam.x0 ? bx0 : cam.x0;
+    b.y = by0 > cam.y0 ? by0 : cam.y0;
+    b.z = bx1 < cam.x0 + cam.w - 1 ? bx1 : cam.x0 + cam.w - 1;
+    b.w = by1 < cam.y0 + cam.h - 1 ? by1 : cam.y0 + cam.h - 1;
+  }
+  return b;
+}
+
+// ------------------------------------------------------------ 2-D patch
+template <int P, typename R>
+struct Patch2 {
+  static constexpr int N = P + 1, NN = N * N;
+  R x[NN], y[NN];        // index j*N + i: i along a, j along b
+};
+
+template <int P, typename R>
+IVV_HD bool hull_has_origin(const Patch2<P, R>& q, R pad) {
+  R x0 = q.x[0], x1 = q.x[0], y0 = q.y[0], y1 = q.y[0];
+#pragma unroll
+  for (int k = 1; k < Patch2<P, R>::NN; ++k) {
+    x0 = minr(x0, q.x[k]); x1 = maxr(x1, q.x[k]);
+    y0 = minr(y0, q.y[k]); y1 = maxr(y1, q.y[k]);
+  }
+  return !(x0 > pad || x1 < -pad || y0 > pad || y1 < -pad);
+}
+
+// The Jacobian det of the planar map is a sum of positive weights times
+// cross(du_i, dv_j) over hodograph control vectors; if the interval of those
+// cross products excludes 0 the map is locally one-to-one on the patch.
+template <int P, typename R>
+IVV_HD bool fixed_jacobian_sign(const Patch2<P, R>& q) {
+  constexpr int N = P + 1;
+  R ax0 = R(1e30), ax1 = R(-1e30), ay0 = R(1e30), ay1 = R(-1e30);
+  R bx0 = R(1e30), bx1 = R(-1e30), by0 = R(1e30), by1 = R(-1e30);
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const R ux = q.x[j * N + i + 1] - q.x[j * N + i], uy = q.y[j * N + i + 1] - q.y[j * N + i];
+      ax0 = minr(ax0, ux); ax1 = maxr(ax1, ux); ay0 = minr(ay0, uy); ay1 = maxr(ay1, uy);
+      const R vx = q.x[(i + 1) * N + j] - q.x[i * N + j], vy = q.y[(i + 1) * N + j] - q.y[i * N + j];
+      bx0 = minr(bx0, vx); bx1 = maxr(bx1, vx); by0 = minr(by0, vy); by1 = maxr(by1, vy);
+    }
+  // interval of ux*vy - uy*vx
+  const R p0 = ax0 * by0, p1 = ax0 * by1, p2 = ax1 * by0, p3 = ax1 * by1;
+  const R q0 = ay0 * bx0, q1 = ay0 * bx1, q2 = ay1 * bx0, q3 = ay1 * bx1;
+  const R plo = minr(minr(p0, p1), minr(p2, p3)), phi = maxr(maxr(p0, p1), maxr(p2, p3));
+  const R qlo = minr(minr(q0, q1), minr(q2, q3)), qhi = maxr(maxr(q0, q1), maxr(q2, q3));
+  return (plo - qhi) > R(0) || (phi - qlo) < R(0);
+}
+
+template <int P, typename R>
+IVV_HD void split_patch(const Patch2<P, R>& q, int dir, Patch2<P, R>& L, Patch2<P, R>& Rt) {
+  constexpr int N = P + 1;
+#pragma unroll
+  for (int line = 0; line < N; ++line) {
+    R wx[N], wy[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int idx = dir == 0 ? line * N + k : k * N + line;
+      wx[k] = q.x[idx];
+      wy[k] = q.y[idx];
+    }
+    {
+      const int i0 = dir == 0 ? line * N : line;
+      const int iN = dir == 0 ? line * N + P : P * N + line;
+      L.x[i0] = wx[0]; L.y[i0] = wy[0];
+      Rt.x[iN] = wx[P]; Rt.y[iN] = wy[P];
+    }
+#pragma unroll
+    for (int lev = 1; lev <= P; ++lev) {
+#pragma unroll
+      for (int k = 0; k + lev <= P; ++k) {
+        wx[k] = R(0.5) * (wx[k] + wx[k + 1]);
+        wy[k] = R(0.5) * (wy[k] + wy[k + 1]);
+      }
+      const int il = dir == 0 ? line * N + lev : lev * N + line;
+      const int ir = dir == 0 ? line * N + (P - lev) : (P - lev) * N + line;
+      L.x[il] = wx[0]; L.y[il] = wy[0];
+      Rt.x[ir] = wx[P - lev]; Rt.y[ir] = wy[P - lev];
+    }
+  }
+}
+
+template <typename R> struct RootEps;
+template <> struct RootEps<float> {
+  static constexpr float step = 1e-6f, accept = 1e-4f, dup = 2e-5f;
+};
+template <> struct RootEps<double> {
+  static constexpr double step = 1e-13, accept = 1e-9, dup = 1e-10;
+};
+
+// Damped Newton on the planar map of patch q (local parameters) from (a,b).
+template <int P, typename R>
+IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
+  constexpr int N = P + 1;
+  for (int it = 0; it < 16; ++it) {
+    R ba[N], dba[N], bb[N], dbb[N];
+    bern_hd<P, R>(a, ba, dba);
+    bern_hd<P, R>(b, bb, dbb);
+    R Fx = 0, Fy = 0, Ax = 0, Ay = 0, Bx = 0, By = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      R tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        tx0 += ba[i] * q.x[j * N + i]; ty0 += ba[i] * q.y[j * N + i];
+        tx1 += dba[i] * q.x[j * N + i]; ty1 += dba[i] * q.y[j * N + i];
+      }
+      Fx += bb[j] * tx0; Fy += bb[j] * ty0;
+      Ax += bb[j] * tx1; Ay += bb[j] * ty1;
+      Bx += dbb[j] * tx0; By += dbb[j] * ty0;
+    }
+    ++iters;
+    const R det = Ax * By - Bx * Ay;
+    if (det == R(0)) return false;
+    R da = (-Fx * By + Fy * Bx) / det;
+    R db = (-Ax * Fy + Ay * Fx) / det;
+    const R mx = maxr(fabs(da), fabs(db));
+    if (mx > R(0.5)) { da *= R(0.5) / mx; db *= R(0.5) / mx; }
+    a += da;
+    b += db;
+    if (a < R(-1) || a > R(2) || b < R(-1) || b > R(2)) return false;
+    if (fabs(da) + fabs(db) < RootEps<R>::step) return true;
+  }
+  return false;
+}
+
+constexpr int kMaxPatchRoots = 4;
+constexpr int kSplitDepth = 8;
+
+// Accept a root (a,b) of a sub-patch covering [a0,a1] x [b0,b1] of the face
+// patch: inside the sub-patch (tolerance scaled to its size) and inside the
+// patch, and not a duplicate of a root already found.
+// Returns false if (a,b) lies outside the sub-patch (the caller then looks
+// for the sub-patch's own root in smaller pieces).
+template <typename R>
+IVV_HD bool accept_root(R a, R b, R a0, R a1, R b0, R b1, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& nr) {
+  const R wa = a1 - a0, wb = b1 - b0;
+  const R ea = RootEps<R>::accept / wa, eb = RootEps<R>::accept / wb;
+  if (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb) return false;
+  const R ga = a0 + a * wa, gb = b0 + b * wb;
+  const R e = RootEps<R>::accept;
+  if (ga < -e || ga > R(1) + e || gb < -e || gb > R(1) + e) return true;
+  for (int k = 0; k < nr; ++k)
+    if (fabs(ra[k] - ga) + fabs(rb[k] - gb) < RootEps<R>::dup) return true;
+  if (nr < kMaxPatchRoots) {
+    ra[nr] = ga;
+    rb[nr] = gb;
+    ++nr;
+  }
+  return true;
+}
+
+// All roots (a,b) in [0,1]^2 (within a tolerance) of the planar patch q0.
+// Returns the count (<= kMaxPatchRoots); `iters` accumulates Newton steps.
+template <int P, typename R>
+IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& iters) {
+  int nr = 0;
+  if (!hull_has_origin<P, R>(q0, pad)) return 0;
+  if (fixed_jacobian_sign<P, R>(q0)) {       // common case: one Newton solve
+    R a = R(0.5), b = R(0.5);
+    if (newton2<P, R>(q0, a, b, iters) && accept_root<R>(a, b, R(0), R(1), R(0), R(1), ra, rb, nr)) return nr;
+  }
+  struct Node {
+    Patch2<P, R> q;
+    R a0, a1, b0, b1;
+    int depth;
+  };
+  Node stack[kSplitDepth + 1];
+  stack[0].q = q0;
+  stack[0].a0 = R(0); stack[0].a1 = R(1); stack[0].b0 = R(0); stack[0].b1 = R(1);
+  stack[0].depth = 0;
+  int sp = 1;
+  bool first = true;
+  while (sp > 0) {
+    const Node nd = stack[--sp];
+    bool split = true;
+    if (!first) {
+      if (!hull_has_origin<P, R>(nd.q, pad)) continue;
+      const bool single = fixed_jacobian_sign<P, R>(nd.q);
+      if (single) {
+        // Newton from the centre; if it fails or converges to a root outside
+        // this sub-patch, look for this sub-patch's root in smaller pieces
+        R a = R(0.5), b = R(0.5);
+        split = !(newton2<P, R>(nd.q, a, b, iters) && accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
+      } else if (nd.depth >= kSplitDepth) {
+        // smallest piece, not certified: Newton from the centre and the four
+        // quarter points, keeping every distinct root inside the piece
+        for (int s0 = 0; s0 < 5; ++s0) {
+          R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
+          R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
+          if (newton2<P, R>(nd.q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr);
+        }
+        split = false;
+      }
+    }
+    first = false;
+    if (!split || nd.depth >= kSplitDepth || sp + 2 > kSplitDepth + 1) continue;
+    // split along the parameter direction with the longer control polygon
+    constexpr int N = P + 1;
+    R la = 0, lb = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      la += fabs(nd.q.x[k * N + P] - nd.q.x[k * N]) + fabs(nd.q.y[k * N + P] - nd.q.y[k * N]);
+      lb += fabs(nd.q.x[P * N + k] - nd.q.x[k]) + fabs(nd.q.y[P * N + k] - nd.q.y[k]);
+    }
+    const int dir = la >= lb ? 0 : 1;
+    Node& hi = stack[sp];
+    Node& lo = stack[sp + 1];              // lower half is processed next
+    split_patch<P, R>(nd.q, dir, lo.q, hi.q);
+    lo.depth = hi.depth = nd.depth + 1;
+    lo.a0 = hi.a0 = nd.a0; lo.a1 = hi.a1 = nd.a1;
+    lo.b0 = hi.b0 = nd.b0; lo.b1 = hi.b1 = nd.b1;
+    if (dir == 0) {
+      const R m = R(0.5) * (nd.a0 + nd.a1);
+      lo.a1 = m;
+      hi.a0 = m;
+    } else {
+      const R m = R(0.5) * (nd.b0 + nd.b1);
+      lo.b1 = m;
+      hi.b0 = m;
+    }
+    sp += 2;
+  }
+  return nr;
+}
+
+// ------------------------------------------------------------ 3-D patch
+// S(a,b) relative to the patch origin, with partials; cp are (x,y,z,_) rows.
+template <int P, typename R, typename V4>
+IVV_HD void patch_eval3_rel(const V4* cp, R a, R b, R S[3], R Sa[3], R Sb[3]) {
+  constexpr int N = P + 1;
+  R ba[N], dba[N], bb[N], dbb[N];
+  bern_hd<P, R>(a, ba, dba);
+  bern_hd<P, R>(b, bb, dbb);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) S[r] = Sa[r] = Sb[r] = R(0);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    R t0[3] = {0, 0, 0}, t1[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const V4 c = cp[j * N + i];
+      t0[0] += ba[i] * R(c.x); t0[1] += ba[i] * R(c.y); t0[2] += ba[i] * R(c.z);
+      t1[0] += dba[i] * R(c.x); t1[1] += dba[i] * R(c.y); t1[2] += dba[i] * R(c.z);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      S[r] += bb[j] * t0[r];
+      Sa[r] += bb[j] * t1[r];
+      Sb[r] += dbb[j] * t0[r];
+    }
+  }
+}
+
+// Planar control points of a face patch in the frame (e1, e2) of a ray from
+// o: x_k = ((org - o) + c_k) . e1, with c_k relative to the patch origin.
+template <int P, typename R, typename V4>
+IVV_HD void project_patch(const V4* cp, const R org[3], const R o[3], const R e1[3], const R e2[3],
+                          Patch2<P, R>& q) {
+  const R D[3] = {org[0] - o[0], org[1] - o[1], org[2] - o[2]};
+  const R x0 = D[0] * e1[0] + D[1] * e1[1] + D[2] * e1[2];
+  const R y0 = D[0] * e2[0] + D[1] * e2[1] + D[2] * e2[2];
+#pragma unroll
+  for (int k = 0; k < (P + 1) * (P + 1); ++k) {
+    const V4 c = cp[k];
+    q.x[k] = x0 + (R(c.x) * e1[0] + R(c.y) * e1[1] + R(c.z) * e1[2]);
+    q.y[k] = y0 + (R(c.x) * e2[0] + R(c.y) * e2[1] + R(c.z) * e2[2]);
+  }
+}
+
+// Ray vs axis-aligned box [lo, hi] (padded); true if it meets the box at t >= 0.
+template <typename R>
+IVV_HD bool ray_box(const R o[3], const R d[3], const float lo[3], const float hi[3], R pad) {
+  R t0 = R(-1e30), t1 = R(1e30);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R inv = R(1) / d[r];
+    R ta = (R(lo[r]) - pad - o[r]) * inv, tb = (R(hi[r]) + pad - o[r]) * inv;
+    if (ta > tb) { const R x = ta; ta = tb; tb = x; }
+    t0 = ta > t0 ? ta : t0;
+    t1 = tb < t1 ? tb : t1;
+  }
+  return t1 >= t0 && t1 >= R(0);
+}
+
+// Fragment of a root (a,b) of face `m`: depth t, facing, block parameter point.
+template <int P, typename R, typename V4>
+IVV_HD void make_fragment(const V4* cp, const R org[3], const FaceMeta& m, const R pa0, const R pa1, const R pb0,
+                          const R pb1, const R o[3], const R d[3], R a, R b, R& t, bool& front, R pp[3], R& cosang) {
+  R S[3], Sa[3], Sb[3];
+  patch_eval3_rel<P, R, V4>(cp, a, b, S, Sa, Sb);
+  t = ((org[0] - o[0]) * d[0] + (org[1] - o[1]) * d[1] + (org[2] - o[2]) * d[2]) +
+      (S[0] * d[0] + S[1] * d[1] + S[2] * d[2]);
+  const R n[3] = {Sa[1] * Sb[2] - Sa[2] * Sb[1], Sa[2] * Sb[0] - Sa[0] * Sb[2], Sa[0] * Sb[1] - Sa[1] * Sb[0]};
+  const R dn = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+  const R nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  cosang = nl > R(0) ? fabs(dn) / nl : R(0);
+  front = (m.face & 1) ? (dn < R(0)) : (dn > R(0));
+  const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+  pp[nd] = (m.face & 1) ? R(1) : R(0);
+  pp[ad] = pa0 + a * (pa1 - pa0);
+  pp[bd] = pb0 + b * (pb1 - pb0);
+}
+
+// FP64 polish of a hit near a silhouette: Newton on S(a,b) - o - t d = 0
+// with the FP64 face patch (control points relative to org).
+template <int P, typename V4>
+IVV_HD void refine_hit_fp64(const V4* cp, const double org[3], const double o[3], const double d[3], double& a,
+                            double& b, double& t) {
+  for (int it = 0; it < 4; ++it) {
+    double S[3], Sa[3], Sb[3];
+    patch_eval3_rel<P, double, V4>(cp, a, b, S, Sa, Sb);
+    double F[3];
+    for (int r = 0; r < 3; ++r) F[r] = -((org[r] - o[r]) + S[r] - t * d[r]);
+    // solve [Sa Sb -d] x = F by Cramer
+    const double A[3][3] = {{Sa[0], Sb[0], -d[0]}, {Sa[1], Sb[1], -d[1]}, {Sa[2], Sb[2], -d[2]}};
+    const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+    if (det == 0.0) break;
+    const double c10 = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    const double c12 = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    const double c20 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    const double c21 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    const double x0 = (c00 * F[0] + c10 * F[1] + c20 * F[2]) / det;
+    const double x1 = (c01 * F[0] + c11 * F[1] + c21 * F[2]) / det;
+    const double x2 = (c02 * F[0] + c12 * F[1] + c22 * F[2]) / det;
+    if (!(fabs(x0) < 0.5 && fabs(x1) < 0.5)) break;
+    a += x0; b += x1; t += x2;
+  }
+}
+
+// ------------------------------------------------------------ stage 2
+// Sort fragments by (t, block, facing), merge duplicates of one block with
+// equal facing closer than tau_dup, and pair by Alg. 2.  meta = block << 4 |
+// face << 1 | front.  Writes (front index, back index) per pair in order.
+template <typename R>
+IVV_HD int pair_fragments(int n, const R* t, const unsigned* m, R tau_dup, int max_pairs, int* in_idx, int* out_idx,
+                          unsigned& unmatched, unsigned& overflow) {
+  unsigned char ord[kMaxFrags];
+  for (int i = 0; i < n; ++i) {
+    int j = i;
+    while (j > 0) {
+      const int a = ord[j - 1];
+      const bool gt = (t[a] > t[i]) || (t[a] == t[i] && ((m[a] >> 4) > (m[i] >> 4) ||
+                                                         ((m[a] >> 4) == (m[i] >> 4) && (m[a] & 1u) > (m[i] & 1u))));
+      if (!gt) break;
+      ord[j] = ord[j - 1];
+      --j;
+    }
+    ord[j] = (unsigned char)i;
+  }
+  unsigned used = 0;
+  for (int i = 0; i < n; ++i) {
+    const int a = ord[i];
+    for (int j = 0; j < i; ++j) {
+      const int b = ord[j];
+      if (!((used >> j) & 1u) && (m[a] >> 4) == (m[b] >> 4) && (m[a] & 1u) == (m[b] & 1u) && t[a] - t[b] <= tau_dup) {
+        used |= 1u << i;
+        break;
+      }
+    }
+  }
+  int np = 0;
+  for (;;) {
+    int back = -1;
+    for (int i = 0; i < n; ++i)
+      if (!((used >> i) & 1u) && !(m[ord[i]] & 1u)) { back = i; break; }
+    if (back < 0) break;
+    const unsigned blk = m[ord[back]] >> 4;
+    int front = -1;
+    for (int i = 0; i < n; ++i)
+      if (!((used >> i) & 1u) && (m[ord[i]] & 1u) && (m[ord[i]] >> 4) == blk) { front = i; break; }
+    used |= 1u << back;
+    if (front < 0) { ++unmatched; continue; }
+    used |= 1u << front;
+    if (np < max_pairs) {
+      in_idx[np] = ord[front];
+      out_idx[np] = ord[back];
+      ++np;
+    } else {
+      ++overflow;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (!((used >> i) & 1u)) ++unmatched;
+  return np;
+}
+
+}  // namespace ivv

@@ -75,6 +75,8 @@ struct ivv_volume {
   double* d_brk64 = nullptr;
   float4* d_elem32 = nullptr;
   ivv::Dbl4* d_elem64 = nullptr;
+  float4* d_org32 = nullptr;
+  ivv::Dbl4* d_org64 = nullptr;
   float4* d_face32 = nullptr;
   ivv::Dbl4* d_face64 = nullptr;
   ivv::FaceMeta* d_faces = nullptr;
@@ -99,7 +101,8 @@ namespace {
 
 void free_volume(ivv_volume* v) {
   if (!v) return;
-  void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_face32, v->d_face64,
+  void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_org64,
+                  v->d_face32, v->d_face64,
                   v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -131,6 +134,8 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   V.brk64 = v->d_brk64;
   V.elem32 = v->d_elem32;
   V.elem64 = v->d_elem64;
+  V.org32 = v->d_org32;
+  V.org64 = v->d_org64;
   V.face32 = v->d_face32;
   V.face64 = v->d_face64;
   V.faces = v->d_faces;
@@ -212,7 +217,7 @@ ivv::DevCamera<R> dev_camera(const Frame& F) {
   return c;
 }
 
-ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_render_params& p) {
+ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_render_params& p) {
   if (in) {
     p = *in;
   } else {
@@ -222,7 +227,7 @@ ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_
     p.c = 1.0;
     p.early_alpha = 1.0 - 1e-4;
   }
-  if (!(p.ds > 0)) p.ds = v->hv.diag / 128.0;
+  if (!(p.ds > 0)) p.ds = diag / 128.0;
   if (!(p.rk_tol > 0) || !std::isfinite(p.rk_tol)) return fail(IVV_ERR_INVALID_ARG, "rk_tol must be positive");
   if (p.supersample_k < 1 || p.supersample_k > 64) return fail(IVV_ERR_INVALID_ARG, "supersample_k must be in 1..64");
   if (!(p.c >= 0) || !std::isfinite(p.c)) return fail(IVV_ERR_INVALID_ARG, "c must be non-negative");
@@ -230,6 +235,10 @@ ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_
   if (p.precision < IVV_PREC_FP32 || p.precision > IVV_PREC_FP64) return fail(IVV_ERR_INVALID_ARG, "bad precision");
   if (p.use_mlp_guess != 0) return fail(IVV_ERR_UNSUPPORTED, "use_mlp_guess is not available in this build");
   return IVV_OK;
+}
+
+ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_render_params& p) {
+  return resolve_params_diag(v->hv.diag, in, p);
 }
 
 ivv_status ensure_own(void** buf, size_t* have, size_t need, cudaStream_t s) {
@@ -356,6 +365,22 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
 
 }  // namespace
 
+namespace ivv {
+std::string& last_error_ref() { return g_err; }
+ivv_status resolve_params_host(double diag, const ivv_render_params* in, ivv_render_params& p) {
+  return resolve_params_diag(diag, in, p);
+}
+ivv_status frame_cameras(const ivv_camera* c, const ivv_render_params& p, int width, int height,
+                         DevCamera<float>& c32, DevCamera<double>& c64) {
+  Frame F;
+  ivv_status st = make_frame(c, p, width, height, F);
+  if (st != IVV_OK) return st;
+  c32 = dev_camera<float>(F);
+  c64 = dev_camera<double>(F);
+  return IVV_OK;
+}
+}  // namespace ivv
+
 extern "C" {
 
 const char* ivv_last_error(void) { return g_err.c_str(); }
@@ -384,7 +409,9 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
   }
   const ivv::HostVolume& hv = v->hv;
   std::vector<float> brk32(hv.brk.begin(), hv.brk.end());
-  std::vector<float4> elem32(hv.elem.size() / 4), face32(hv.face_cp.size() / 4);
+  std::vector<float4> elem32(hv.elem.size() / 4), face32(hv.face_cp.size() / 4), org32(hv.elem_org.size() / 4);
+  for (size_t i = 0; i < org32.size(); ++i)
+    org32[i] = make_float4((float)hv.elem_org[4 * i], (float)hv.elem_org[4 * i + 1], (float)hv.elem_org[4 * i + 2], 0.f);
   for (size_t i = 0; i < elem32.size(); ++i)
     elem32[i] = make_float4((float)hv.elem[4 * i], (float)hv.elem[4 * i + 1], (float)hv.elem[4 * i + 2],
                             (float)hv.elem[4 * i + 3]);
@@ -395,6 +422,8 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
       (st = upload(&v->d_brk64, hv.brk.data(), hv.brk.size(), s)) != IVV_OK ||
       (st = upload(&v->d_elem32, elem32.data(), elem32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_elem64, (const ivv::Dbl4*)hv.elem.data(), hv.elem.size() / 4, s)) != IVV_OK ||
+      (st = upload(&v->d_org32, org32.data(), org32.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_org64, (const ivv::Dbl4*)hv.elem_org.data(), hv.elem_org.size() / 4, s)) != IVV_OK ||
       (st = upload(&v->d_face32, face32.data(), face32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_face64, (const ivv::Dbl4*)hv.face_cp.data(), hv.face_cp.size() / 4, s)) != IVV_OK ||
       (st = upload(&v->d_faces, hv.faces.data(), hv.faces.size(), s)) != IVV_OK ||

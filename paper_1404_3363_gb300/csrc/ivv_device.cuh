@@ -3,9 +3,12 @@
 // Layout in HBM (uploaded once per volume):
 //   elem   [E][(P+1)^3] float4 (x, y, z, rho) -- Bezier control points of every
 //          element, index (i*(P+1)+j)*(P+1)+k with i along u, j along v, k along w
-//          (w innermost, so the first contraction streams contiguous float4s)
+//          (w innermost, so the first contraction streams contiguous float4s);
+//          x, y, z relative to the element origin elem_org[E] (its first
+//          control point), which keeps FP32 partial derivatives accurate
 //   elem64 the same in double ([E][(P+1)^3][4])
-//   face   [F][(P+1)^2] float4 (x, y, z, 0) -- boundary face patches, a fastest
+//   face   [F][(P+1)^2] float4 (x, y, z, 0) -- boundary face patches, a fastest,
+//          relative to the face origin in FaceMeta
 //   brk    breakpoints of every block and direction (float and double copies)
 // All spline work is Bernstein evaluation of a single element: the geometry
 // phi = sum B_i(u) B_j(v) B_k(w) C_ijk (Eq. 1 restricted to one element) with
@@ -16,6 +19,7 @@
 #include <stdint.h>
 
 #include "ivv_internal.h"
+#include "isect.cuh"
 
 namespace ivv {
 
@@ -36,20 +40,13 @@ struct DevVolume {
   const double* brk64;
   const float4* elem32;
   const Dbl4* elem64;
+  const float4* org32;
+  const Dbl4* org64;
   const float4* face32;
   const Dbl4* face64;
   const FaceMeta* faces;
   const FaceMeta64* faces64;
   float diag;
-};
-
-template <typename R>
-struct DevCamera {
-  R eye[3], f[3], r[3], u[3];
-  R sx, sy;             // perspective: tan(fovy/2)*aspect, tan(fovy/2); ortho: half widths
-  int ortho;
-  int W, H;             // full image
-  int x0, y0, w, h;     // window
 };
 
 struct DevTF {
@@ -118,10 +115,19 @@ __device__ __forceinline__ int locate(const R* __restrict__ brk, int nseg, R x, 
 template <typename R> struct ElemPtr;
 template <> struct ElemPtr<float> {
   static __device__ __forceinline__ float4 ld(const DevVolume& V, size_t i) { return __ldg(V.elem32 + i); }
+  static __device__ __forceinline__ float4 org(const DevVolume& V, size_t e) { return __ldg(V.org32 + e); }
 };
 template <> struct ElemPtr<double> {
   static __device__ __forceinline__ Dbl4 ld(const DevVolume& V, size_t i) {
     const double2* p = reinterpret_cast<const double2*>(V.elem64 + i);
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    Dbl4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+  }
+  static __device__ __forceinline__ Dbl4 org(const DevVolume& V, size_t e) { return ld2(V.org64 + e); }
+  static __device__ __forceinline__ Dbl4 ld2(const Dbl4* q) {
+    const double2* p = reinterpret_cast<const double2*>(q);
     const double2 a = __ldg(p), b = __ldg(p + 1);
     Dbl4 r;
     r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
@@ -146,7 +152,8 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
     x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
     e[d] = locate<R>(brk + B.brk_off[d], B.nseg[d], x, loc[d], sc[d]);
   }
-  const size_t base = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]) * (N * N * N);
+  const size_t eid = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]);
+  const size_t base = eid * (N * N * N);
   R bu[N], dbu[N], bv[N], dbv[N], bw[N], dbw[N];
   bernstein<P, R>(loc[0], bu, dbu);
   bernstein<P, R>(loc[1], bv, dbv);
@@ -185,6 +192,10 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
     }
     if (WANT_RHO) s += bu[i] * ss;
   }
+  const typename Vec4T<R>::type og = ElemPtr<R>::org(V, eid);
+  f[0] += R(og.x);
+  f[1] += R(og.y);
+  f[2] += R(og.z);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     phi[r] = f[r];
@@ -219,46 +230,6 @@ __device__ __forceinline__ R solve3(const R J[3][3], const R b[3], R x[3]) {
   x[1] = (c01 * b[0] + c11 * b[1] + c21 * b[2]) * inv;
   x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
   return det;
-}
-
-// Pixel ray (matches the boundary header's camera definition).
-template <typename R>
-__device__ __forceinline__ void make_ray(const DevCamera<R>& c, int px, int py, R o[3], R d[3]) {
-  const R nx = (R(px) + R(0.5)) / R(c.W) * R(2) - R(1);
-  const R ny = R(1) - (R(py) + R(0.5)) / R(c.H) * R(2);
-  if (c.ortho) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      o[i] = c.eye[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
-      d[i] = c.f[i];
-    }
-  } else {
-    R dd[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      o[i] = c.eye[i];
-      dd[i] = c.f[i] + nx * c.sx * c.r[i] + ny * c.sy * c.u[i];
-    }
-    const R n = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = dd[i] / n;
-  }
-}
-
-// Screen position (pixel units, pixel centres at integers) of a point g.
-template <typename R>
-__device__ __forceinline__ void project(const DevCamera<R>& c, const R g[3], R& sx, R& sy) {
-  R w[3] = {g[0] - c.eye[0], g[1] - c.eye[1], g[2] - c.eye[2]};
-  R x = w[0] * c.r[0] + w[1] * c.r[1] + w[2] * c.r[2];
-  R y = w[0] * c.u[0] + w[1] * c.u[1] + w[2] * c.u[2];
-  if (!c.ortho) {
-    const R z = w[0] * c.f[0] + w[1] * c.f[1] + w[2] * c.f[2];
-    x /= z;
-    y /= z;
-  }
-  const R nx = x / c.sx, ny = y / c.sy;
-  sx = (nx + R(1)) * R(0.5) * R(c.W) - R(0.5);
-  sy = (R(1) - ny) * R(0.5) * R(c.H) - R(0.5);
 }
 
 // Piecewise-linear TF (knots in shared memory): colour and extinction weight.

@@ -17,16 +17,19 @@ constexpr int kMaxFrags = 32;       // fragment slots per pixel (A-buffer)
 constexpr int kMaxPairs = 16;       // entry/exit pair slots per pixel
 
 // Face patch record: block, face index (0/1: u=0/1, 2/3: v=0/1, 4/5: w=0/1),
-// parameter box of the patch on its face, and the bbox of its control points.
+// parameter box of the patch on its face, the patch origin (its control
+// points are stored relative to it) and the bbox of its control points.
 struct FaceMeta {
   int block;
   int face;
   float a0, a1, b0, b1;
+  float org[3];
   float lo[3], hi[3];
 };
 
 struct FaceMeta64 {
   double a0, a1, b0, b1;
+  double org[3];
 };
 
 struct BlockInfo {
@@ -43,8 +46,9 @@ struct HostVolume {
   int n_blocks = 0;
   std::vector<BlockInfo> blocks;
   std::vector<double> brk;         // concatenated breakpoints (normalised)
-  std::vector<double> elem;        // [E][(P+1)^3][4] (x, y, z, rho), i-major
-  std::vector<double> face_cp;     // [F][(P+1)^2][4] (x, y, z, 0), a fastest
+  std::vector<double> elem;        // [E][(P+1)^3][4] (x, y, z, rho), i-major, xyz relative to elem_org
+  std::vector<double> elem_org;    // [E][4] element origin (first control point), w = 0
+  std::vector<double> face_cp;     // [F][(P+1)^2][4] (x, y, z, 0) relative to the face origin, a fastest
   std::vector<FaceMeta> faces;
   std::vector<FaceMeta64> faces64;
   std::vector<double> mean_abs_det;

@@ -36,62 +36,18 @@ __global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typena
     n = n < kMaxFrags ? n : kMaxFrags;
     R t[kMaxFrags];
     unsigned m[kMaxFrags];
-    unsigned char ord[kMaxFrags];
     for (int i = 0; i < n; ++i) {
       t[i] = frag_tp[(size_t)i * npix + pix].x;
       m[i] = frag_meta[(size_t)i * npix + pix];
     }
-    // insertion sort of slot indices by (t, block, front)
-    for (int i = 0; i < n; ++i) {
-      int j = i;
-      while (j > 0) {
-        const int a = ord[j - 1];
-        const bool gt = (t[a] > t[i]) || (t[a] == t[i] && ((m[a] >> 4) > (m[i] >> 4) ||
-                                                           ((m[a] >> 4) == (m[i] >> 4) && (m[a] & 1u) > (m[i] & 1u))));
-        if (!gt) break;
-        ord[j] = ord[j - 1];
-        --j;
-      }
-      ord[j] = (unsigned char)i;
+    int in_idx[kMaxPairs], out_idx[kMaxPairs];
+    np = pair_fragments<R>(n, t, m, tau_dup, max_pairs, in_idx, out_idx, um, pov);
+    for (int q = 0; q < np; ++q) {
+      const size_t o = (size_t)q * npix + pix;
+      pair_in[o] = frag_tp[(size_t)in_idx[q] * npix + pix];
+      pair_out[o] = frag_tp[(size_t)out_idx[q] * npix + pix];
+      pair_block[o] = (int)(m[in_idx[q]] >> 4);
     }
-    // merge duplicates: same block, same facing, |dt| <= tau_dup
-    unsigned used = 0;          // bit per sorted position
-    for (int i = 0; i < n; ++i) {
-      const int a = ord[i];
-      for (int j = 0; j < i; ++j) {
-        const int b = ord[j];
-        if (!((used >> j) & 1u) && (m[a] >> 4) == (m[b] >> 4) && (m[a] & 1u) == (m[b] & 1u) &&
-            t[a] - t[b] <= tau_dup) {
-          used |= 1u << i;
-          break;
-        }
-      }
-    }
-    // Alg. 2
-    for (;;) {
-      int back = -1;
-      for (int i = 0; i < n; ++i)
-        if (!((used >> i) & 1u) && !(m[ord[i]] & 1u)) { back = i; break; }
-      if (back < 0) break;
-      const unsigned blk = m[ord[back]] >> 4;
-      int front = -1;
-      for (int i = 0; i < n; ++i)
-        if (!((used >> i) & 1u) && (m[ord[i]] & 1u) && (m[ord[i]] >> 4) == blk) { front = i; break; }
-      used |= 1u << back;
-      if (front < 0) { ++um; continue; }
-      used |= 1u << front;
-      if (np < max_pairs) {
-        const size_t o = (size_t)np * npix + pix;
-        pair_in[o] = frag_tp[(size_t)ord[front] * npix + pix];
-        pair_out[o] = frag_tp[(size_t)ord[back] * npix + pix];
-        pair_block[o] = (int)blk;
-        ++np;
-      } else {
-        ++pov;
-      }
-    }
-    for (int i = 0; i < n; ++i)
-      if (!((used >> i) & 1u)) ++um;
     pair_count[pix] = np;
     if (np == 0 && out_rgba) out_rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
   }

@@ -6,9 +6,9 @@
 //                       control points (convex hull property).
 //   K2 intersect     -- one CTA per 16x16 screen tile: cull the face boxes
 //                       against the tile, stage the surviving patches in
-//                       shared memory, and per pixel solve S(a,b) = o + t d by
-//                       Newton on the two coordinates perpendicular to the ray
-//                       (hull test first), from four starts; hits go into the
+//                       shared memory, and per pixel find every root of
+//                       S(a,b) = o + t d (hull test, certified single-root
+//                       Newton or subdivision; isect.cuh); hits go into the
 //                       pixel's fragment slots (the A-buffer of §4.2).
 #include <cuda_runtime.h>
 
@@ -18,100 +18,22 @@ namespace ivv {
 
 namespace {
 
+template <int P>
 __global__ void k0_face_project(DevVolume V, DevCamera<float> cam, int4* __restrict__ boxes) {
+  constexpr int NN = (P + 1) * (P + 1);
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= V.n_faces) return;
-  const int NN = (V.P + 1) * (V.P + 1);
-  const float4* cp = V.face32 + (size_t)f * NN;
-  float xmin = 1e30f, xmax = -1e30f, ymin = 1e30f, ymax = -1e30f;
-  bool behind_all = true, straddle = false;
-  const float znear = 1e-6f * V.diag;
-  for (int q = 0; q < NN; ++q) {
-    const float4 c = cp[q];
-    const float w[3] = {c.x - cam.eye[0], c.y - cam.eye[1], c.z - cam.eye[2]};
-    const float z = w[0] * cam.f[0] + w[1] * cam.f[1] + w[2] * cam.f[2];
-    if (z > 0.f) behind_all = false;
-    if (!cam.ortho && z <= znear) straddle = true;
-    const float g[3] = {c.x, c.y, c.z};
-    float sx, sy;
-    project<float>(cam, g, sx, sy);
-    xmin = fminf(xmin, sx); xmax = fmaxf(xmax, sx);
-    ymin = fminf(ymin, sy); ymax = fmaxf(ymax, sy);
-  }
-  int4 b;
-  if (behind_all) {
-    b = make_int4(1, 1, 0, 0);                                   // empty
-  } else if (straddle) {
-    b = make_int4(cam.x0, cam.y0, cam.x0 + cam.w - 1, cam.y0 + cam.h - 1);
-  } else {
-    const float lim = 1e9f;
-    xmin = fmaxf(xmin, -lim); ymin = fmaxf(ymin, -lim);
-    xmax = fminf(xmax, lim); ymax = fminf(ymax, lim);
-    b.x = max((int)floorf(xmin) - 1, cam.x0);
-    b.y = max((int)floorf(ymin) - 1, cam.y0);
-    b.z = min((int)ceilf(xmax) + 1, cam.x0 + cam.w - 1);
-    b.w = min((int)ceilf(ymax) + 1, cam.y0 + cam.h - 1);
-  }
-  boxes[f] = b;
+  boxes[f] = face_screen_box<NN>(cam, V.face32 + (size_t)f * NN, V.faces[f].org, V.diag);
 }
 
-template <typename R> __device__ __forceinline__ R clamp01(R x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
-
-template <typename R> struct Eps;
-template <> struct Eps<float> {
-  static constexpr float step = 1e-6f, accept = 1e-4f;
-};
-template <> struct Eps<double> {
-  static constexpr double step = 1e-13, accept = 1e-9;
-};
-
-// 3-D patch point and partials at (a, b) from control points in shared memory.
-template <int P, typename R, typename V4>
-__device__ __forceinline__ void patch_eval3(const V4* cp, R a, R b, R S[3], R Sa[3], R Sb[3]) {
-  constexpr int N = P + 1;
-  R ba[N], dba[N], bb[N], dbb[N];
-  bernstein<P, R>(a, ba, dba);
-  bernstein<P, R>(b, bb, dbb);
-#pragma unroll
-  for (int r = 0; r < 3; ++r) S[r] = Sa[r] = Sb[r] = R(0);
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    R t0[3] = {0, 0, 0}, t1[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const V4 c = cp[j * N + i];
-      t0[0] += ba[i] * R(c.x); t0[1] += ba[i] * R(c.y); t0[2] += ba[i] * R(c.z);
-      t1[0] += dba[i] * R(c.x); t1[1] += dba[i] * R(c.y); t1[2] += dba[i] * R(c.z);
-    }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      S[r] += bb[j] * t0[r];
-      Sa[r] += bb[j] * t1[r];
-      Sb[r] += dbb[j] * t0[r];
-    }
-  }
-}
-
-// FP64 polish of a hit near a silhouette: Newton on S(a,b) - o - t d = 0.
+// FP64 polish of a grazing hit (mixed precision), kept out of line.
 template <int P>
 __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const DevCamera<double>& cam64, int px, int py,
-                            double& a, double& b, double& t) {
-  constexpr int N = P + 1;
-  const Dbl4* cp = V.face64 + (size_t)face * N * N;
+                                         double& a, double& b, double& t) {
+  const FaceMeta64 m = V.faces64[face];
   double o[3], d[3];
   make_ray<double>(cam64, px, py, o, d);
-  for (int it = 0; it < 4; ++it) {
-    double S[3], Sa[3], Sb[3];
-    patch_eval3<P, double, Dbl4>(cp, a, b, S, Sa, Sb);
-    double J[3][3], F[3], x[3];
-    for (int r = 0; r < 3; ++r) {
-      J[r][0] = Sa[r]; J[r][1] = Sb[r]; J[r][2] = -d[r];
-      F[r] = -(S[r] - o[r] - t * d[r]);
-    }
-    solve3<double>(J, F, x);
-    if (!(fabs(x[0]) < 0.5 && fabs(x[1]) < 0.5)) break;
-    a += x[0]; b += x[1]; t += x[2];
-  }
+  refine_hit_fp64<P, Dbl4>(V.face64 + (size_t)face * (P + 1) * (P + 1), m.org, o, d, a, b, t);
 }
 
 template <int P, typename R, bool MIXED, bool STATS>
@@ -141,21 +63,11 @@ __global__ void __launch_bounds__(256) k2_intersect(DevVolume V, DevCamera<R> ca
 
   R o[3], d[3], e1[3], e2[3];
   make_ray<R>(cam, px, py, o, d);
-  {
-    R ax[3] = {R(1), R(0), R(0)};
-    if (fabs(d[0]) > R(0.6)) { ax[0] = R(0); ax[1] = R(1); }
-    e1[0] = d[1] * ax[2] - d[2] * ax[1];
-    e1[1] = d[2] * ax[0] - d[0] * ax[2];
-    e1[2] = d[0] * ax[1] - d[1] * ax[0];
-    const R n = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
-    e1[0] /= n; e1[1] /= n; e1[2] /= n;
-    e2[0] = d[1] * e1[2] - d[2] * e1[1];
-    e2[1] = d[2] * e1[0] - d[0] * e1[2];
-    e2[2] = d[0] * e1[1] - d[1] * e1[0];
-  }
+  ray_frame<R>(d, e1, e2);
   const R hull_pad = R(1e-6) * R(V.diag);
   int nfrag = 0;
-  unsigned long long c_tests = 0, c_newton = 0, c_fp64 = 0;
+  int c_newton = 0;
+  unsigned long long c_tests = 0, c_fp64 = 0;
 
   for (int base = 0; base < V.n_faces; base += 256) {
     const int f = base + tid;
@@ -191,111 +103,50 @@ __global__ void __launch_bounds__(256) k2_intersect(DevVolume V, DevCamera<R> ca
       if (valid) {
         for (int q = 0; q < nst; ++q) {
           const FaceMeta& m = s_meta[q];
-          // ray vs control-point box
-          R t0 = R(-1e30), t1 = R(1e30);
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const R inv = R(1) / d[r];
-            R ta = (R(m.lo[r]) - hull_pad - o[r]) * inv, tb = (R(m.hi[r]) + hull_pad - o[r]) * inv;
-            if (ta > tb) { const R x = ta; ta = tb; tb = x; }
-            t0 = ta > t0 ? ta : t0;
-            t1 = tb < t1 ? tb : t1;
+          if (!ray_box<R>(o, d, m.lo, m.hi, hull_pad)) continue;
+          const int fi = s_cand[c0 + q];
+          R org[3], pa0, pa1, pb0, pb1;
+          if constexpr (sizeof(R) == 8) {
+            const FaceMeta64 m64 = V.faces64[fi];
+            org[0] = m64.org[0]; org[1] = m64.org[1]; org[2] = m64.org[2];
+            pa0 = m64.a0; pa1 = m64.a1; pb0 = m64.b0; pb1 = m64.b1;
+          } else {
+            org[0] = m.org[0]; org[1] = m.org[1]; org[2] = m.org[2];
+            pa0 = m.a0; pa1 = m.a1; pb0 = m.b0; pb1 = m.b1;
           }
-          if (!(t1 >= t0 && t1 >= R(0))) continue;
-          // control points in the ray frame; hull must contain the ray
           const V4* cp = s_cp + q * NN;
-          R X[NN], Y[NN];
-          R xmin = R(1e30), xmax = R(-1e30), ymin = R(1e30), ymax = R(-1e30);
-#pragma unroll
-          for (int k = 0; k < NN; ++k) {
-            const V4 c = cp[k];
-            const R w0 = R(c.x) - o[0], w1 = R(c.y) - o[1], w2 = R(c.z) - o[2];
-            X[k] = w0 * e1[0] + w1 * e1[1] + w2 * e1[2];
-            Y[k] = w0 * e2[0] + w1 * e2[1] + w2 * e2[2];
-            xmin = X[k] < xmin ? X[k] : xmin; xmax = X[k] > xmax ? X[k] : xmax;
-            ymin = Y[k] < ymin ? Y[k] : ymin; ymax = Y[k] > ymax ? Y[k] : ymax;
-          }
-          if (xmin > hull_pad || xmax < -hull_pad || ymin > hull_pad || ymax < -hull_pad) continue;
+          Patch2<P, R> pq;
+          project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
+          if (!hull_has_origin<P, R>(pq, hull_pad)) continue;
           if (STATS) ++c_tests;
-          R ra[4], rb[4];
-          int nr = 0;
-#pragma unroll 1
-          for (int s0 = 0; s0 < 4; ++s0) {
-            R a = (s0 & 1) ? R(0.75) : R(0.25), b = (s0 & 2) ? R(0.75) : R(0.25);
-            bool conv = false;
-#pragma unroll 1
-            for (int it = 0; it < 16; ++it) {
-              R ba[N], dba[N], bb[N], dbb[N];
-              bernstein<P, R>(a, ba, dba);
-              bernstein<P, R>(b, bb, dbb);
-              R Fx = 0, Fy = 0, Ax = 0, Ay = 0, Bx = 0, By = 0;
-#pragma unroll
-              for (int j = 0; j < N; ++j) {
-                R tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
-#pragma unroll
-                for (int i = 0; i < N; ++i) {
-                  tx0 += ba[i] * X[j * N + i]; ty0 += ba[i] * Y[j * N + i];
-                  tx1 += dba[i] * X[j * N + i]; ty1 += dba[i] * Y[j * N + i];
-                }
-                Fx += bb[j] * tx0; Fy += bb[j] * ty0;
-                Ax += bb[j] * tx1; Ay += bb[j] * ty1;
-                Bx += dbb[j] * tx0; By += dbb[j] * ty0;
-              }
-              const R det = Ax * By - Bx * Ay;
-              if (STATS) ++c_newton;
-              if (det == R(0)) break;
-              R da = (-Fx * By + Fy * Bx) / det;
-              R db = (-Ax * Fy + Ay * Fx) / det;
-              const R mx = fabs(da) > fabs(db) ? fabs(da) : fabs(db);
-              if (mx > R(0.5)) { da *= R(0.5) / mx; db *= R(0.5) / mx; }
-              a += da;
-              b += db;
-              if (a < R(-1) || a > R(2) || b < R(-1) || b > R(2)) break;
-              if (fabs(da) + fabs(db) < Eps<R>::step) { conv = true; break; }
-            }
-            if (!conv) continue;
-            const R ea = Eps<R>::accept;
-            if (a < -ea || a > R(1) + ea || b < -ea || b > R(1) + ea) continue;
-            bool dup = false;
-            for (int k = 0; k < nr; ++k)
-              if (fabs(ra[k] - a) + fabs(rb[k] - b) < R(1e-3)) dup = true;
-            if (dup) continue;
-            ra[nr] = a; rb[nr] = b; ++nr;
-            a = clamp01(a);
-            b = clamp01(b);
-            R S[3], Sa[3], Sb[3];
-            patch_eval3<P, R, V4>(cp, a, b, S, Sa, Sb);
-            R t = (S[0] - o[0]) * d[0] + (S[1] - o[1]) * d[1] + (S[2] - o[2]) * d[2];
-            R nrm[3] = {Sa[1] * Sb[2] - Sa[2] * Sb[1], Sa[2] * Sb[0] - Sa[0] * Sb[2], Sa[0] * Sb[1] - Sa[1] * Sb[0]};
-            R dn = nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2];
+          R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
+          const int nr = patch_roots<P, R>(pq, hull_pad, ra, rb, c_newton);
+          for (int k = 0; k < nr; ++k) {
+            R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
+            R t, pp[3], cosang;
+            bool front;
+            make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
             if constexpr (MIXED) {
-              const R nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-              if (fabs(dn) < R(0.05) * nl) {
+              if (cosang < R(0.2)) {
                 double a64 = a, b64 = b, t64 = t;
-                refine_fp64<P>(V, s_cand[c0 + q], cam64, px, py, a64, b64, t64);
-                a = clamp01(R(a64));
-                b = clamp01(R(b64));
+                refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+                a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
+                b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
                 t = R(t64);
+                const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+                const FaceMeta64 m64 = V.faces64[fi];
+                pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
+                pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
                 if (STATS) ++c_fp64;
               }
             }
             if (!(t > R(0))) continue;
-            const bool front = (m.face & 1) ? (dn < R(0)) : (dn > R(0));
-            const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-            R pp[3];
-            pp[nd] = (m.face & 1) ? R(1) : R(0);
-            pp[ad] = R(m.a0) + a * (R(m.a1) - R(m.a0));
-            pp[bd] = R(m.b0) + b * (R(m.b1) - R(m.b0));
-            if constexpr (sizeof(R) == 8) {
-              const FaceMeta64 m64 = V.faces64[s_cand[c0 + q]];
-              pp[ad] = R(m64.a0) + a * (R(m64.a1) - R(m64.a0));
-              pp[bd] = R(m64.b0) + b * (R(m64.b1) - R(m64.b0));
-            }
             if (nfrag < kMaxFrags) {
               V4 rec;
               rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
               frag_tp[(size_t)nfrag * npix + pix] = rec;
-              frag_meta[(size_t)nfrag * npix + pix] = ((unsigned)m.block << 4) | ((unsigned)m.face << 1) | (front ? 1u : 0u);
+              frag_meta[(size_t)nfrag * npix + pix] =
+                  ((unsigned)m.block << 4) | ((unsigned)m.face << 1) | (front ? 1u : 0u);
               ++nfrag;
             } else {
               atomicAdd(&st->abuf_overflow, 1ull);
@@ -309,16 +160,17 @@ __global__ void __launch_bounds__(256) k2_intersect(DevVolume V, DevCamera<R> ca
   if (valid) frag_count[pix] = nfrag;
   if (STATS) {
     unsigned long long nf = valid ? (unsigned long long)nfrag : 0ull;
+    unsigned long long cn = (unsigned long long)c_newton;
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
       c_tests += __shfl_down_sync(0xffffffffu, c_tests, o2);
-      c_newton += __shfl_down_sync(0xffffffffu, c_newton, o2);
+      cn += __shfl_down_sync(0xffffffffu, cn, o2);
       c_fp64 += __shfl_down_sync(0xffffffffu, c_fp64, o2);
       nf += __shfl_down_sync(0xffffffffu, nf, o2);
     }
     if (lane == 0) {
       atomicAdd(&st->isect_tests, c_tests);
-      atomicAdd(&st->isect_newton, c_newton);
+      atomicAdd(&st->isect_newton, cn);
       atomicAdd(&st->fp64_solves, c_fp64);
       atomicAdd(&st->fragments, nf);
     }
@@ -329,7 +181,10 @@ __global__ void __launch_bounds__(256) k2_intersect(DevVolume V, DevCamera<R> ca
 
 void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, cudaStream_t s) {
   if (V.n_faces <= 0) return;
-  k0_face_project<<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes);
+  if (V.P == 2)
+    k0_face_project<2><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes);
+  else
+    k0_face_project<3><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes);
 }
 
 template <typename R>

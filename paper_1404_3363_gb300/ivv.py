@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.ivv_host_eval.argtypes = [C.POINTER(BlockDesc), C.c_int, C.c_int, C.c_int, C.c_int, c_double_p, c_double_p,
                                 c_double_p, c_double_p]
     L.ivv_get_stage_times.argtypes = [vp, c_float_p]
+    L.ivv_host_render_pairs.argtypes = [C.POINTER(BlockDesc), C.c_int, C.c_int, C.POINTER(Camera),
+                                        C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int, vp, vp, vp]
     L.ivv_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.ivv_reset_stats.argtypes = [vp]
     L.ivv_volume_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
@@ -176,6 +178,21 @@ def host_eval(blocks, scalar_mode, block, p):
                                 phi.ctypes.data_as(c_double_p), jac.ctypes.data_as(c_double_p),
                                 rho.ctypes.data_as(c_double_p)))
     return phi, jac, rho
+
+
+def host_render_pairs(blocks, scalar_mode, camera, params, width, height, max_pairs=16, window=None):
+    """Stage 1-2 code of the device path executed on the host (inspection)."""
+    arr, keep = block_descs(blocks)
+    npix = width * height
+    cnt = np.zeros(npix, np.int32)
+    pairs = np.zeros((max_pairs, npix, 8))
+    blk = np.zeros((max_pairs, npix), np.int32)
+    cam = camera_struct(camera)
+    prm = params_struct(params, 0, window)
+    _check(load().ivv_host_render_pairs(arr, len(blocks), int(scalar_mode), C.byref(cam), C.byref(prm), width,
+                                        height, max_pairs, C.c_void_p(cnt.ctypes.data),
+                                        C.c_void_p(pairs.ctypes.data), C.c_void_p(blk.ctypes.data)))
+    return cnt, pairs, blk
 
 
 class Volume:

@@ -47,81 +47,26 @@ def test_eval_points_match_oracle(ivv, cfg):
         f2, J2, r2 = ov.eval(b, P.astype(np.float64))
         scale = np.abs(f2).max()
         np.testing.assert_allclose(phi.cpu().numpy(), f2, atol=4e-6 * scale)
-        np.testing.assert_allclose(J.cpu().numpy(), J2, atol=2e-5 * np.abs(J2).max())
+        np.testing.assert_allclose(J.cpu().numpy(), J2, atol=3e-6 * np.abs(J2).max())
         np.testing.assert_allclose(rho.cpu().numpy(), r2, atol=2e-5 * max(1.0, np.abs(r2).max()))
 
 
-def _oracle_pairs(ov, sc):
-    W, H = sc.width, sc.height
-    out = {}
-    for y in range(H):
-        for x in range(W):
-            pr, um = ov.pixel_pairs(sc.camera, W, H, x, y)
-            if pr:
-                out[(x, y)] = pr
-    return out
-
-
-def _grazing(ov, sc, x, y, pairs, thresh=0.1):
-    """True if the ray meets a face at a small angle (ill-conditioned hit)."""
-    o, d = oracle.ray(sc.camera, sc.width, sc.height, x, y)
-    for p in pairs:
-        for q in (p.p_in, p.p_out):
-            q = np.array(q)
-            _, J, _ = ov.eval(p.block, q)
-            k = int(np.argmin(np.minimum(np.abs(q), np.abs(q - 1))))
-            n = np.linalg.inv(J[0])[k]          # gradient of the face's parameter
-            n = n / np.linalg.norm(n)
-            if abs(n @ d) < thresh:
-                return True
-    return False
-
-
 @pytest.mark.parametrize("cfg,size,prec", [(0, (64, 64), 0), (1, (200, 120), 0), (1, (200, 120), 1),
-                                           (2, (160, 96), 1)])
+                                           (2, (160, 96), 1), (4, (160, 90), 1)])
 def test_entry_exit_pairs_match_oracle(ivv, cfg, size, prec):
+    """Stages 1-2 on the GPU: per pixel the oracle's pair count and block, and
+    entry/exit parameters within 1e-5 (FP32: hits within 0.2 of grazing get
+    2e-4; MIXED refines those in FP64 and is held to 1e-5 everywhere)."""
+    from tests.test_library_cpu import compare_pairs
     sc = scenes.config(cfg, width=size[0], height=size[1])
     sc.params.precision = prec
     vol = ivv.volume_for(sc)
     cnt, pairs, blk = vol.render_pairs(sc.camera, sc.params, sc.width, sc.height, max_pairs=16)
     torch.cuda.synchronize()
-    cnt, pairs, blk = cnt.cpu().numpy(), pairs.cpu().numpy(), blk.cpu().numpy()
+    cnt, pairs, blk = cnt.cpu().numpy(), pairs.cpu().numpy().astype(np.float64), blk.cpu().numpy()
     ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
-    ref = _oracle_pairs(ov, sc)
-    W = sc.width
-    checked = mism = 0
-    worst = 0.0
-    for y in range(sc.height):
-        for x in range(W):
-            pix = y * W + x
-            rp = ref.get((x, y), [])
-            if cnt[pix] != len(rp):
-                # allowed only for a chord too short to matter (silhouette)
-                short = [p for p in rp if p.t_out - p.t_in < 2e-4 * ov.diag]
-                extra = cnt[pix] - len(rp)
-                assert abs(extra) <= max(1, len(short)) and (len(short) > 0 or extra > 0), (x, y, cnt[pix], len(rp))
-                if extra > 0:
-                    for q in range(cnt[pix]):
-                        L = pairs[q, pix, 7] - pairs[q, pix, 3]
-                        assert L < 2e-4 * ov.diag or any(
-                            abs(pairs[q, pix, 3] - p.t_in) < 1e-4 for p in rp)
-                mism += 1
-                continue
-            if not rp:
-                continue
-            graze = _grazing(ov, sc, x, y, rp)
-            for q, p in enumerate(rp):
-                assert blk[q, pix] == p.block
-                e = max(np.abs(pairs[q, pix, 0:3] - np.array(p.p_in)).max(),
-                        np.abs(pairs[q, pix, 4:7] - np.array(p.p_out)).max())
-                te = max(abs(pairs[q, pix, 3] - p.t_in), abs(pairs[q, pix, 7] - p.t_out))
-                if not graze:
-                    assert e <= TOL_PARAM, (x, y, q, e)
-                    worst = max(worst, e)
-                assert te <= 1e-4 * max(1.0, abs(p.t_in)), (x, y, q, te)
-            checked += 1
+    checked, worst = compare_pairs(ov, sc, cnt, pairs, blk, TOL_PARAM, graze_cos=0.2 if prec == 0 else -1.0)
     assert checked > 0.02 * sc.width * sc.height
-    assert mism <= 0.002 * sc.width * sc.height + 2
 
 
 @pytest.mark.parametrize("cfg,size,prec", [(0, (64, 64), 2), (0, (64, 64), 0), (1, (200, 120), 0),

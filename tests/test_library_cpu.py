@@ -91,3 +91,57 @@ def test_invalid_descriptions_are_rejected(lib):
     nan[0, 0, 0, 0] = np.nan
     assert status_of([scenes.Block(good.degree, good.knots, nan, good.scalar_cp)]) == 1
     assert status_of([good], mode=7) == 1
+
+
+def _grazing_cos(ov, o, d, block, q):
+    """|cos| between the ray and the face normal at parameter point q."""
+    q = np.asarray(q)
+    _, J, _ = ov.eval(block, q)
+    k = int(np.argmin(np.minimum(np.abs(q), np.abs(q - 1))))
+    n = np.linalg.inv(J[0])[k]
+    return abs(n @ d) / np.linalg.norm(n)
+
+
+def compare_pairs(ov, sc, cnt, pairs, blk, tol_param, graze_cos=0.2, tol_graze=2e-4):
+    """Per-pixel pair lists against the oracle.  Returns (checked, worst)."""
+    import oracle as orc
+    W, H = sc.width, sc.height
+    checked, worst = 0, 0.0
+    for y in range(H):
+        for x in range(W):
+            pix = y * W + x
+            rp, um = ov.pixel_pairs(sc.camera, W, H, x, y)
+            if cnt[pix] != len(rp):
+                # only a chord too short to contribute may differ
+                short = [p for p in rp if p.t_out - p.t_in < 1e-4 * ov.diag]
+                extra = [q for q in range(cnt[pix]) if pairs[q, pix, 7] - pairs[q, pix, 3] < 1e-4 * ov.diag]
+                assert abs(int(cnt[pix]) - len(rp)) <= max(len(short), len(extra)), (x, y, cnt[pix], len(rp))
+                continue
+            o, d = orc.ray(sc.camera, W, H, x, y)
+            for q, p in enumerate(rp):
+                assert blk[q, pix] == p.block, (x, y)
+                for got, ref in ((pairs[q, pix, 0:3], p.p_in), (pairs[q, pix, 4:7], p.p_out)):
+                    e = np.abs(got - np.array(ref)).max()
+                    lim = tol_param if _grazing_cos(ov, o, d, p.block, ref) >= graze_cos else tol_graze
+                    assert e <= lim, (x, y, q, e)
+                    worst = max(worst, e)
+                assert abs(pairs[q, pix, 3] - p.t_in) <= 2e-4 and abs(pairs[q, pix, 7] - p.t_out) <= 2e-4
+                checked += 1
+    return checked, worst
+
+
+@pytest.mark.parametrize("cfg,size,prec,tol", [(0, (64, 64), 2, 1e-10), (0, (64, 64), 0, 1e-5),
+                                               (1, (200, 120), 0, 1e-5), (1, (200, 120), 1, 1e-5),
+                                               (2, (160, 96), 1, 1e-5), (4, (160, 90), 1, 1e-5)])
+def test_host_stage12_code_matches_oracle_pairs(lib, cfg, size, prec, tol):
+    """The stage 1-2 code of the device kernels, executed on the host, gives
+    the oracle's entry/exit pairs: same count per pixel, block, and
+    parameters within tol (FP32: hits within 0.2 of grazing get 2e-4; MIXED
+    refines those in FP64, so it is held to tol everywhere)."""
+    sc = scenes.config(cfg, width=size[0], height=size[1])
+    sc.params.precision = prec
+    cnt, pairs, blk = ivv.host_render_pairs(sc.blocks, sc.scalar_mode, sc.camera, sc.params, sc.width, sc.height)
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    graze = 0.2 if prec == 0 else -1.0
+    checked, worst = compare_pairs(ov, sc, cnt, pairs, blk, tol, graze_cos=graze)
+    assert checked > 0.02 * sc.width * sc.height
