@@ -196,39 +196,6 @@ IVV_HD bool fixed_jacobian_sign(const Patch2<P, R>& q) {
   return (plo - qhi) > R(0) || (phi - qlo) < R(0);
 }
 
-template <int P, typename R>
-IVV_HD void split_patch(const Patch2<P, R>& q, int dir, Patch2<P, R>& L, Patch2<P, R>& Rt) {
-  constexpr int N = P + 1;
-#pragma unroll
-  for (int line = 0; line < N; ++line) {
-    R wx[N], wy[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int idx = dir == 0 ? line * N + k : k * N + line;
-      wx[k] = q.x[idx];
-      wy[k] = q.y[idx];
-    }
-    {
-      const int i0 = dir == 0 ? line * N : line;
-      const int iN = dir == 0 ? line * N + P : P * N + line;
-      L.x[i0] = wx[0]; L.y[i0] = wy[0];
-      Rt.x[iN] = wx[P]; Rt.y[iN] = wy[P];
-    }
-#pragma unroll
-    for (int lev = 1; lev <= P; ++lev) {
-#pragma unroll
-      for (int k = 0; k + lev <= P; ++k) {
-        wx[k] = R(0.5) * (wx[k] + wx[k + 1]);
-        wy[k] = R(0.5) * (wy[k] + wy[k + 1]);
-      }
-      const int il = dir == 0 ? line * N + lev : lev * N + line;
-      const int ir = dir == 0 ? line * N + (P - lev) : (P - lev) * N + line;
-      L.x[il] = wx[0]; L.y[il] = wy[0];
-      Rt.x[ir] = wx[P - lev]; Rt.y[ir] = wy[P - lev];
-    }
-  }
-}
-
 template <typename R> struct RootEps;
 template <> struct RootEps<float> {
   static constexpr float step = 1e-6f, accept = 1e-4f, dup = 2e-5f;
@@ -241,6 +208,7 @@ template <> struct RootEps<double> {
 template <int P, typename R>
 IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
   constexpr int N = P + 1;
+#pragma unroll 1
   for (int it = 0; it < 16; ++it) {
     R ba[N], dba[N], bb[N], dbb[N];
     bern_hd<P, R>(a, ba, dba);
@@ -267,7 +235,7 @@ IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
     if (mx > R(0.5)) { da *= R(0.5) / mx; db *= R(0.5) / mx; }
     a += da;
     b += db;
-    if (a < R(-1) || a > R(2) || b < R(-1) || b > R(2)) return false;
+    if (a < R(-0.5) || a > R(1.5) || b < R(-0.5) || b > R(1.5)) return false;
     if (fabs(da) + fabs(db) < RootEps<R>::step) return true;
   }
   return false;
@@ -299,67 +267,108 @@ IVV_HD bool accept_root(R a, R b, R a0, R a1, R b0, R b1, R ra[kMaxPatchRoots], 
   return true;
 }
 
-// All roots (a,b) in [0,1]^2 (within a tolerance) of the planar patch q0.
-// Returns the count (<= kMaxPatchRoots); `iters` accumulates Newton steps.
+// Sub-patch of q covering [a0,a1] x [b0,b1] (de Casteljau: split at the
+// upper end, then split the left part at the relative lower end).
 template <int P, typename R>
-IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& iters) {
-  int nr = 0;
-  if (!hull_has_origin<P, R>(q0, pad)) return 0;
-  if (fixed_jacobian_sign<P, R>(q0)) {       // common case: one Newton solve
-    R a = R(0.5), b = R(0.5);
-    if (newton2<P, R>(q0, a, b, iters) && accept_root<R>(a, b, R(0), R(1), R(0), R(1), ra, rb, nr)) return nr;
+IVV_HD void sub_patch(const Patch2<P, R>& q, R a0, R a1, R b0, R b1, Patch2<P, R>& out) {
+  constexpr int N = P + 1;
+  out = q;
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    const R t0 = dir == 0 ? a0 : b0, t1 = dir == 0 ? a1 : b1;
+    const R s = t1 > R(0) ? t0 / t1 : R(0);
+#pragma unroll
+    for (int line = 0; line < N; ++line) {
+      R wx[N], wy[N], lx[N], ly[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int idx = dir == 0 ? line * N + k : k * N + line;
+        wx[k] = out.x[idx];
+        wy[k] = out.y[idx];
+      }
+      // left part of the split at t1
+      lx[0] = wx[0]; ly[0] = wy[0];
+#pragma unroll
+      for (int lev = 1; lev <= P; ++lev) {
+#pragma unroll
+        for (int k = 0; k + lev <= P; ++k) {
+          wx[k] = wx[k] + t1 * (wx[k + 1] - wx[k]);
+          wy[k] = wy[k] + t1 * (wy[k + 1] - wy[k]);
+        }
+        lx[lev] = wx[0]; ly[lev] = wy[0];
+      }
+      // right part of the split of that at s
+      R rx[N], ry[N];
+      rx[P] = lx[P]; ry[P] = ly[P];
+#pragma unroll
+      for (int lev = 1; lev <= P; ++lev) {
+#pragma unroll
+        for (int k = 0; k + lev <= P; ++k) {
+          lx[k] = lx[k] + s * (lx[k + 1] - lx[k]);
+          ly[k] = ly[k] + s * (ly[k + 1] - ly[k]);
+        }
+        rx[P - lev] = lx[P - lev]; ry[P - lev] = ly[P - lev];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int idx = dir == 0 ? line * N + k : k * N + line;
+        out.x[idx] = rx[k];
+        out.y[idx] = ry[k];
+      }
+    }
   }
-  struct Node {
-    Patch2<P, R> q;
+}
+
+// Subdivision search for the roots of q0 (rare path: patches whose single
+// root is not certified).  The stack keeps parameter boxes only; each piece
+// is re-extracted from q0.
+template <int P, typename R>
+__host__ __device__ __noinline__ int patch_roots_split(const Patch2<P, R>* q0p, R pad, R* ra, R* rb, int& iters) {
+  struct Box {
     R a0, a1, b0, b1;
     int depth;
   };
-  Node stack[kSplitDepth + 1];
-  stack[0].q = q0;
+  const Patch2<P, R>& q0 = *q0p;
+  Box stack[kSplitDepth + 1];
   stack[0].a0 = R(0); stack[0].a1 = R(1); stack[0].b0 = R(0); stack[0].b1 = R(1);
   stack[0].depth = 0;
-  int sp = 1;
-  bool first = true;
+  int sp = 1, nr = 0;
   while (sp > 0) {
-    const Node nd = stack[--sp];
+    const Box nd = stack[--sp];
+    Patch2<P, R> q;
+    sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
+    if (!hull_has_origin<P, R>(q, pad)) continue;
     bool split = true;
-    if (!first) {
-      if (!hull_has_origin<P, R>(nd.q, pad)) continue;
-      const bool single = fixed_jacobian_sign<P, R>(nd.q);
-      if (single) {
-        // Newton from the centre; if it fails or converges to a root outside
-        // this sub-patch, look for this sub-patch's root in smaller pieces
-        R a = R(0.5), b = R(0.5);
-        split = !(newton2<P, R>(nd.q, a, b, iters) && accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
-      } else if (nd.depth >= kSplitDepth) {
-        // smallest piece, not certified: Newton from the centre and the four
-        // quarter points, keeping every distinct root inside the piece
-        for (int s0 = 0; s0 < 5; ++s0) {
-          R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
-          R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
-          if (newton2<P, R>(nd.q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr);
-        }
-        split = false;
+    if (fixed_jacobian_sign<P, R>(q)) {
+      // Newton from the centre; if it fails or converges to a root outside
+      // this piece, look for the piece's root in smaller pieces
+      R a = R(0.5), b = R(0.5);
+      split = !(newton2<P, R>(q, a, b, iters) && accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
+    } else if (nd.depth >= kSplitDepth) {
+      // smallest piece, not certified: Newton from the centre and the four
+      // quarter points, keeping every distinct root inside the piece
+      for (int s0 = 0; s0 < 5; ++s0) {
+        R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
+        R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
+        if (newton2<P, R>(q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr);
       }
+      split = false;
     }
-    first = false;
     if (!split || nd.depth >= kSplitDepth || sp + 2 > kSplitDepth + 1) continue;
     // split along the parameter direction with the longer control polygon
     constexpr int N = P + 1;
     R la = 0, lb = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      la += fabs(nd.q.x[k * N + P] - nd.q.x[k * N]) + fabs(nd.q.y[k * N + P] - nd.q.y[k * N]);
-      lb += fabs(nd.q.x[P * N + k] - nd.q.x[k]) + fabs(nd.q.y[P * N + k] - nd.q.y[k]);
+      la += fabs(q.x[k * N + P] - q.x[k * N]) + fabs(q.y[k * N + P] - q.y[k * N]);
+      lb += fabs(q.x[P * N + k] - q.x[k]) + fabs(q.y[P * N + k] - q.y[k]);
     }
-    const int dir = la >= lb ? 0 : 1;
-    Node& hi = stack[sp];
-    Node& lo = stack[sp + 1];              // lower half is processed next
-    split_patch<P, R>(nd.q, dir, lo.q, hi.q);
+    Box& hi = stack[sp];
+    Box& lo = stack[sp + 1];               // lower half is processed next
+    lo = nd;
+    hi = nd;
     lo.depth = hi.depth = nd.depth + 1;
-    lo.a0 = hi.a0 = nd.a0; lo.a1 = hi.a1 = nd.a1;
-    lo.b0 = hi.b0 = nd.b0; lo.b1 = hi.b1 = nd.b1;
-    if (dir == 0) {
+    if (la >= lb) {
       const R m = R(0.5) * (nd.a0 + nd.a1);
       lo.a1 = m;
       hi.a0 = m;
@@ -371,6 +380,28 @@ IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb
     sp += 2;
   }
   return nr;
+}
+
+// All roots (a,b) in [0,1]^2 (within a tolerance) of the planar patch q0,
+// whose hull is known to contain the origin.  Returns the count
+// (<= kMaxPatchRoots); `iters` accumulates Newton steps.
+template <int P, typename R>
+IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& iters) {
+  if (fixed_jacobian_sign<P, R>(q0)) {
+    // one-to-one patch (common case): Newton from the centre; a solution
+    // outside the patch gets one restart from the nearest patch point
+    int nr = 0;
+    R a = R(0.5), b = R(0.5);
+#pragma unroll 1
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (!newton2<P, R>(q0, a, b, iters)) break;
+      if (accept_root<R>(a, b, R(0), R(1), R(0), R(1), ra, rb, nr)) return nr;
+      if (attempt == 1) return 0;
+      a = clamp01r(a);
+      b = clamp01r(b);
+    }
+  }
+  return patch_roots_split<P, R>(&q0, pad, ra, rb, iters);
 }
 
 // ------------------------------------------------------------ 3-D patch

@@ -37,7 +37,7 @@ __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const Dev
 }
 
 template <int P, typename R, bool MIXED, bool STATS>
-__global__ void __launch_bounds__(256) k2_intersect(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
+__global__ void __launch_bounds__(256, 2) k2_intersect(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
                                                     const int4* __restrict__ boxes,
                                                     typename Vec4T<R>::type* __restrict__ frag_tp,
                                                     unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
