@@ -108,7 +108,7 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
       }
       int in_idx[kMaxPairs], out_idx[kMaxPairs];
       unsigned um = 0, pov = 0;
-      const int np = pair_fragments<R>(n, tt, mm, tau, std::min(max_pairs, (int)kMaxPairs), in_idx, out_idx, um, pov);
+      const int np = pair_fragments<R>(n, tt, mm, pp_all, tau, std::min(max_pairs, (int)kMaxPairs), in_idx, out_idx, um, pov);
       pair_count[pix] = np;
       for (int q = 0; q < np; ++q) {
         double* o8 = pairs + ((size_t)q * npix + pix) * 8;

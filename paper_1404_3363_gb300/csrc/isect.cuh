@@ -517,16 +517,28 @@ IVV_HD void refine_hit_fp64(const V4* cp, const double org[3], const double o[3]
 // Sort fragments by (t, block, facing), merge duplicates of one block with
 // equal facing closer than tau_dup, and pair by Alg. 2.  meta = block << 4 |
 // face << 1 | front.  Writes (front index, back index) per pair in order.
+// Strict order of fragments: depth, block, facing, face, then parameters
+// (so the result never depends on the order fragments were appended).
 template <typename R>
-IVV_HD int pair_fragments(int n, const R* t, const unsigned* m, R tau_dup, int max_pairs, int* in_idx, int* out_idx,
-                          unsigned& unmatched, unsigned& overflow) {
+IVV_HD bool frag_less(R ta, unsigned ma, const R* pa, R tb, unsigned mb, const R* pb) {
+  if (ta != tb) return ta < tb;
+  if ((ma >> 4) != (mb >> 4)) return (ma >> 4) < (mb >> 4);
+  if ((ma & 1u) != (mb & 1u)) return (ma & 1u) < (mb & 1u);
+  if (ma != mb) return ma < mb;
+  if (pa[0] != pb[0]) return pa[0] < pb[0];
+  if (pa[1] != pb[1]) return pa[1] < pb[1];
+  return pa[2] < pb[2];
+}
+
+template <typename R>
+IVV_HD int pair_fragments(int n, const R* t, const unsigned* m, const R (*pp)[3], R tau_dup, int max_pairs,
+                          int* in_idx, int* out_idx, unsigned& unmatched, unsigned& overflow) {
   unsigned char ord[kMaxFrags];
   for (int i = 0; i < n; ++i) {
     int j = i;
     while (j > 0) {
       const int a = ord[j - 1];
-      const bool gt = (t[a] > t[i]) || (t[a] == t[i] && ((m[a] >> 4) > (m[i] >> 4) ||
-                                                         ((m[a] >> 4) == (m[i] >> 4) && (m[a] & 1u) > (m[i] & 1u))));
+      const bool gt = frag_less<R>(t[i], m[i], pp[i], t[a], m[a], pp[a]);
       if (!gt) break;
       ord[j] = ord[j - 1];
       --j;

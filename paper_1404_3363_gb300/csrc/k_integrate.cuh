@@ -24,16 +24,7 @@ namespace ivv {
 
 template <typename R> struct Acc { R C[3]; R a; };
 
-template <int P, typename R, bool MIXED, bool CPRHO>
-struct RhsCtx {
-  const DevVolume* V;
-  BlockInfo B;
-  R g_in[3], d[3], c;
-  int mode;
-};
-
-// W(p) and, when asked, rho(p) and phi(p).  Returns false if det J is not
-// positive (the step is then rejected by the caller).
+// W(p) = J_phi(p)^-1 V(phi(p)) and, when asked, rho(p) and phi(p).
 template <int P, typename R, bool MIXED, bool WANT_RHO>
 __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B, const R p[3], const R g_in[3],
                                          const R d[3], R c, int mode, R W[3], R& rho, R phi[3],
@@ -80,6 +71,10 @@ __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B,
   }
 }
 
+template <typename R> __device__ __forceinline__ R fast_exp(R x);
+template <> __device__ __forceinline__ float fast_exp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double fast_exp<double>(double x) { return exp(x); }
+
 template <typename R>
 __device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const DevTF& tf, int K,
                                                    R rho0, R rho1, R dsi, Acc<R>& acc) {
@@ -91,7 +86,7 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
     R x = (rk - R(tf.lo)) * R(tf.inv_range);
     x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
     const float4 c = tf_eval(s_r, s_rgba, tf.n, (float)x);
-    const R T = exp(-tau_scale * R(c.w));
+    const R T = fast_exp<R>(-tau_scale * R(c.w));
     const R w = (R(1) - T) * (R(1) - acc.a);
     acc.C[0] += w * R(c.x);
     acc.C[1] += w * R(c.y);
@@ -100,14 +95,18 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
   }
 }
 
+// One lane's position in the integration of its current pixel.
+//   stage 0: start of a pair (evaluate W at p_in), 1..3: the three new
+//   right-hand sides of a Bogacki-Shampine step at q2, q3 and the step end.
 template <int P, typename R, bool MIXED, bool STATS>
-__global__ void __launch_bounds__(128) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
-                                                    const typename Vec4T<R>::type* __restrict__ pair_in,
-                                                    const typename Vec4T<R>::type* __restrict__ pair_out,
-                                                    const int* __restrict__ pair_block,
-                                                    const int* __restrict__ pair_count, const int* __restrict__ active,
-                                                    const int* __restrict__ n_active, int* __restrict__ queue_head,
-                                                    float4* __restrict__ out, DevStats* __restrict__ st) {
+__global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
+                                                       const typename Vec4T<R>::type* __restrict__ pair_in,
+                                                       const typename Vec4T<R>::type* __restrict__ pair_out,
+                                                       const int* __restrict__ pair_block,
+                                                       const int* __restrict__ pair_count,
+                                                       const int* __restrict__ active, const int* __restrict__ n_active,
+                                                       int* __restrict__ queue_head, float4* __restrict__ out,
+                                                       DevStats* __restrict__ st) {
   typedef typename Vec4T<R>::type V4;
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
@@ -125,120 +124,181 @@ __global__ void __launch_bounds__(128) k5_integrate(DevVolume V, DevCamera<R> ca
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
   float max_dp = 0.f;
 
+  // lane state
+  int pix = -1;           // -1: needs a pixel; -2: queue drained
+  int q = 0, np = 0, stage = 0, j = 0, nsamp = 0, nlast = 0, steps = 0, blk = 0;
+  R o[3], d[3], g_in[3], p[3], k1[3], k2[3], k3[3], pn[3];
+  R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0;
+  bool last = false;
+  Acc<R> acc;
+
   for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(queue_head, 32);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= nact) break;
-    const int item = base + lane;
-    if (item < nact) {
-    const int pix = __ldg(active + item);
-    const int xw = pix % cam.w, yw = pix / cam.w;
-    const int px = cam.x0 + xw, py = cam.y0 + yw;
-    R o[3], d[3];
-    make_ray<R>(cam, px, py, o, d);
-    Acc<R> acc;
-    acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
-    const int np = __ldg(pair_count + pix);
-    bool done = false;
-    for (int q = 0; q < np && !done; ++q) {
-      const size_t slot = (size_t)q * npix + pix;
-      const V4 pin = pair_in[slot];
-      const V4 pout = pair_out[slot];
-      const int blk = __ldg(pair_block + slot);
-      const BlockInfo B = V.blocks[blk];
-      const R L = R(pout.x) - R(pin.x);
-      if (!(L > R(0))) continue;
-      R g_in[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pin.x) * d[r];
-      const R fl = floor(L / ds);
-      const int nsamp = (int)fl;
-      const int nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
-      R p[3] = {R(pin.y), R(pin.z), R(pin.w)};
-      R k1[3], rho_prev, phi[3];
-      rhs_eval<P, R, MIXED, true>(V, B, p, g_in, d, cc, V.mode, k1, rho_prev, phi, c_fp64);
-      if (STATS) {
-        ++c_rhs;
-        ++c_samp;
-      }
-      R s = R(0), s_last = R(0), h = ds;
-      int j = 1, steps = 0;
-      while (j <= nlast) {
-        const R s_t = (j <= nsamp) ? R(j) * ds : L;
-        const R rem = s_t - s;
-        const bool last = h >= rem;
-        const R hh = last ? rem : h;
-        R q2[3], q3[3], pn[3], k2[3], k3[3], k4[3], rho_n, dummy, ph2[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const R x = p[r] + R(0.5) * hh * k1[r];
-          q2[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-        }
-        rhs_eval<P, R, MIXED, false>(V, B, q2, g_in, d, cc, V.mode, k2, dummy, ph2, c_fp64);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const R x = p[r] + R(0.75) * hh * k2[r];
-          q3[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-        }
-        rhs_eval<P, R, MIXED, false>(V, B, q3, g_in, d, cc, V.mode, k3, dummy, ph2, c_fp64);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const R x = p[r] + hh * (R(2.0 / 9.0) * k1[r] + R(1.0 / 3.0) * k2[r] + R(4.0 / 9.0) * k3[r]);
-          pn[r] = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-        }
-        rhs_eval<P, R, MIXED, true>(V, B, pn, g_in, d, cc, V.mode, k4, rho_n, phi, c_fp64);
-        R err = R(0);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const R e = hh * (R(-5.0 / 72.0) * k1[r] + R(1.0 / 12.0) * k2[r] + R(1.0 / 9.0) * k3[r] -
-                            R(1.0 / 8.0) * k4[r]);
-          const R ae = fabs(e);
-          err = ae > err ? ae : err;
-        }
-        ++steps;
-        if (STATS) c_rhs += 3;
-        const bool capped = steps >= args.max_steps;
-        if (err <= tol || hh <= hmin || capped) {
-          if (STATS) ++c_steps;
-          if (capped && STATS) ++c_cap;
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            p[r] = pn[r];
-            k1[r] = k4[r];
-          }
-          R fac = err > R(0) ? R(0.9) * cbrt(tol / err) : R(5);
-          fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
-          const R hn = hh * fac;
-          if (last) {
-            composite_interval<R>(s_r, s_rgba, tf, args.K, rho_prev, rho_n, s_t - s_last, acc);
-            if (STATS) {
-              ++c_samp;
-              R sx, sy;
-              project<R>(cam, phi, sx, sy);
-              const float dp = 2.f * (float)fmax(fabs(sx - R(px)), fabs(sy - R(py)));
-              max_dp = fmaxf(max_dp, dp);
-            }
-            rho_prev = rho_n;
-            s = s_t;
-            s_last = s_t;
-            ++j;
-            h = h > hn ? h : hn;
-            if (acc.a >= early) { done = true; break; }
-          } else {
-            s += hh;
-            h = hn;
-          }
-          if (capped) break;
+    // ---- refill lanes that finished their pixel
+    const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
+    if (need) {
+      int base = 0;
+      const int leader = __ffs(need) - 1;
+      if (lane == leader) base = atomicAdd(queue_head, __popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (pix == -1) {
+        const int item = base + __popc(need & ((1u << lane) - 1u));
+        if (item < nact) {
+          pix = __ldg(active + item);
+          const int xw = pix % cam.w, yw = pix / cam.w;
+          make_ray<R>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
+          acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
+          np = __ldg(pair_count + pix);
+          q = -1;
+          stage = 0;
         } else {
-          if (STATS) ++c_rej;
-          R fac = R(0.9) * cbrt(tol / err);
-          h = hh * (fac < R(0.2) ? R(0.2) : fac);
+          pix = -2;
         }
       }
     }
-    out[pix] = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
-    }  // item < nact
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) break;
+
+    // ---- choose this lane's evaluation point
+    bool live = pix >= 0;
+    if (live && stage == 0) {
+      // advance to the next pair with a positive length, or finish the pixel
+      bool found = false;
+      while (!found && ++q < np) {
+        const size_t slot = (size_t)q * npix + pix;
+        const V4 pi = pair_in[slot];
+        const V4 po = pair_out[slot];
+        L = R(po.x) - R(pi.x);
+        if (!(L > R(0))) continue;
+        blk = __ldg(pair_block + slot);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pi.x) * d[r];
+        p[0] = R(pi.y); p[1] = R(pi.z); p[2] = R(pi.w);
+        const R fl = floor(L / ds);
+        nsamp = (int)fl;
+        nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
+        s = s_last = R(0);
+        h = ds;
+        j = 1;
+        steps = 0;
+        found = true;
+      }
+      if (!found) {
+        out[pix] = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
+        pix = -1;
+        live = false;
+      }
+    }
+    R x[3];
+    if (live) {
+      if (stage == 0) {
+        x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
+      } else if (stage == 1) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = p[r] + R(0.5) * hh * k1[r];
+      } else if (stage == 2) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = p[r] + R(0.75) * hh * k2[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = pn[r];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[r] = x[r] < R(0) ? R(0) : (x[r] > R(1) ? R(1) : x[r]);
+    } else {
+      x[0] = x[1] = x[2] = R(0.5);
+    }
+    // ---- the one right-hand side of this iteration (converged across lanes)
+    R W[3], rho, phi[3];
+    {
+      const BlockInfo B = V.blocks[live ? blk : 0];
+      rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
+    }
+    if (!live) continue;
+    if (STATS) ++c_rhs;
+    // ---- advance the lane's state
+    if (stage == 0) {
+      k1[0] = W[0]; k1[1] = W[1]; k1[2] = W[2];
+      rho_prev = rho;
+      if (STATS) ++c_samp;
+    } else if (stage == 1) {
+      k2[0] = W[0]; k2[1] = W[1]; k2[2] = W[2];
+    } else if (stage == 2) {
+      k3[0] = W[0]; k3[1] = W[1]; k3[2] = W[2];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        pn[r] = p[r] + hh * (R(2.0 / 9.0) * k1[r] + R(1.0 / 3.0) * k2[r] + R(4.0 / 9.0) * k3[r]);
+    } else {
+      R err = R(0);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const R e = hh * (R(-5.0 / 72.0) * k1[r] + R(1.0 / 12.0) * k2[r] + R(1.0 / 9.0) * k3[r] - R(1.0 / 8.0) * W[r]);
+        const R ae = fabs(e);
+        err = ae > err ? ae : err;
+      }
+      ++steps;
+      const bool capped = steps >= args.max_steps;
+      if (err <= tol || hh <= hmin || capped) {
+        if (STATS) {
+          ++c_steps;
+          if (capped) ++c_cap;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          p[r] = x[r];
+          k1[r] = W[r];
+        }
+        R fac = err > R(0) ? R(0.9) * cbrt(tol / err) : R(5);
+        fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
+        const R hn = hh * fac;
+        bool pair_done = capped;
+        if (last) {
+          const R s_t = (j <= nsamp) ? R(j) * ds : L;
+          composite_interval<R>(s_r, s_rgba, tf, args.K, rho_prev, rho, s_t - s_last, acc);
+          if (STATS) {
+            ++c_samp;
+            R sx, sy;
+            project<R>(cam, phi, sx, sy);
+            const int xw = pix % cam.w, yw = pix / cam.w;
+            const float dp = 2.f * (float)fmax(fabs(sx - R(cam.x0 + xw)), fabs(sy - R(cam.y0 + yw)));
+            max_dp = fmaxf(max_dp, dp);
+          }
+          rho_prev = rho;
+          s = s_t;
+          s_last = s_t;
+          ++j;
+          h = h > hn ? h : hn;
+          if (acc.a >= early) {
+            pair_done = true;
+            q = np;              // early termination ends the pixel
+          }
+          if (j > nlast) pair_done = true;
+        } else {
+          s += hh;
+          h = hn;
+        }
+        if (pair_done) {
+          stage = 0;
+          continue;
+        }
+      } else {
+        if (STATS) ++c_rej;
+        const R fac = R(0.9) * cbrt(tol / err);
+        h = hh * (fac < R(0.2) ? R(0.2) : fac);
+      }
+    }
+    // ---- set up the next stage (a new step after stage 0 or 3)
+    if (stage == 0 || stage == 3) {
+      if (j > nlast) {             // zero-length remainder: pair done
+        stage = 0;
+        continue;
+      }
+      const R s_t = (j <= nsamp) ? R(j) * ds : L;
+      const R rem = s_t - s;
+      last = h >= rem;
+      hh = last ? rem : h;
+      stage = 1;
+    } else {
+      ++stage;
+    }
   }
   // counters
   if (MIXED) {

@@ -34,14 +34,18 @@ __global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typena
   if (pix < npix) {
     int n = frag_count[pix];
     n = n < kMaxFrags ? n : kMaxFrags;
-    R t[kMaxFrags];
+    R t[kMaxFrags], pp[kMaxFrags][3];
     unsigned m[kMaxFrags];
     for (int i = 0; i < n; ++i) {
-      t[i] = frag_tp[(size_t)i * npix + pix].x;
+      const V4 f = frag_tp[(size_t)i * npix + pix];
+      t[i] = f.x;
+      pp[i][0] = f.y;
+      pp[i][1] = f.z;
+      pp[i][2] = f.w;
       m[i] = frag_meta[(size_t)i * npix + pix];
     }
     int in_idx[kMaxPairs], out_idx[kMaxPairs];
-    np = pair_fragments<R>(n, t, m, tau_dup, max_pairs, in_idx, out_idx, um, pov);
+    np = pair_fragments<R>(n, t, m, pp, tau_dup, max_pairs, in_idx, out_idx, um, pov);
     for (int q = 0; q < np; ++q) {
       const size_t o = (size_t)q * npix + pix;
       pair_in[o] = frag_tp[(size_t)in_idx[q] * npix + pix];
