@@ -243,6 +243,13 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
     }
     B.elem_off = hv.n_elems();
     B.tau_det = 0.f;
+    B.uniform = 0;
+    for (int k = 0; k < 3; ++k) {
+      bool uni = true;
+      for (int i = 0; i <= B.nseg[k]; ++i)
+        if (std::fabs(brk[k][i] - (double)i / B.nseg[k]) > 1e-12) uni = false;
+      if (uni) B.uniform |= 1 << k;
+    }
     // elements, i-major ((i*(P+1)+j)*(P+1)+k); geometry relative to the
     // element's first control point, which keeps FP32 partials accurate
     for (int ew = 0; ew < B.nseg[2]; ++ew)

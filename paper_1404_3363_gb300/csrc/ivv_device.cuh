@@ -150,7 +150,16 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
   for (int d = 0; d < 3; ++d) {
     R x = p[d];
     x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-    e[d] = locate<R>(brk + B.brk_off[d], B.nseg[d], x, loc[d], sc[d]);
+    if ((B.uniform >> d) & 1) {            // uniform knots: O(1) element lookup
+      const R xs = x * R(B.nseg[d]);
+      int k = (int)xs;
+      k = k < B.nseg[d] - 1 ? k : B.nseg[d] - 1;
+      e[d] = k;
+      loc[d] = xs - R(k);
+      sc[d] = R(B.nseg[d]);
+    } else {
+      e[d] = locate<R>(brk + B.brk_off[d], B.nseg[d], x, loc[d], sc[d]);
+    }
   }
   const size_t eid = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]);
   const size_t base = eid * (N * N * N);
@@ -233,15 +242,19 @@ __device__ __forceinline__ R solve3(const R J[3][3], const R b[3], R x[3]) {
 }
 
 // Piecewise-linear TF (knots in shared memory): colour and extinction weight.
-__device__ __forceinline__ float4 tf_eval(const float* __restrict__ r, const float4* __restrict__ rgba, int n,
-                                          float x) {
+// seg[i] (kTfTable entries) is the last segment starting at or below
+// i / kTfTable, so the segment of x is found from seg[floor(x kTfTable)] by a
+// short forward scan.
+constexpr int kTfTable = 256;
+
+__device__ __forceinline__ float4 tf_eval(const float* __restrict__ r, const float4* __restrict__ rgba,
+                                          const unsigned char* __restrict__ seg, int n, float x) {
   if (x <= r[0]) return rgba[0];
   if (x >= r[n - 1]) return rgba[n - 1];
-  int lo = 0, hi = n - 2;              // segment i with r[i] <= x < r[i+1]
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (r[mid] <= x) lo = mid; else hi = mid - 1;
-  }
+  int c = (int)(x * (float)kTfTable);
+  c = c < kTfTable - 1 ? c : kTfTable - 1;
+  int lo = seg[c];                     // segment i with r[i] <= x < r[i+1]
+  while (lo < n - 2 && r[lo + 1] <= x) ++lo;
   const float w = r[lo + 1] - r[lo];
   const float t = w > 0.f ? (x - r[lo]) / w : 1.f;
   const float4 a = rgba[lo], b = rgba[lo + 1];

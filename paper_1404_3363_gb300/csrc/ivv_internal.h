@@ -37,6 +37,7 @@ struct BlockInfo {
   int brk_off[3];     // offsets into the breakpoint arrays
   int elem_off;       // first Bezier element of the block
   float tau_det;      // |det J| below which MIXED precision solves in FP64
+  int uniform;        // bit d set: breakpoints of direction d are i / nseg[d]
 };
 
 // Host image of a prepared volume (see host_prep.cpp).

@@ -71,13 +71,17 @@ __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B,
   }
 }
 
+template <typename R> __device__ __forceinline__ R pow_third(R x);
+template <> __device__ __forceinline__ float pow_third<float>(float x) { return exp2f(__log2f(x) * (1.f / 3.f)); }
+template <> __device__ __forceinline__ double pow_third<double>(double x) { return cbrt(x); }
+
 template <typename R> __device__ __forceinline__ R fast_exp(R x);
 template <> __device__ __forceinline__ float fast_exp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double fast_exp<double>(double x) { return exp(x); }
 
 template <typename R>
-__device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const DevTF& tf, int K,
-                                                   R rho0, R rho1, R dsi, Acc<R>& acc) {
+__device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const unsigned char* s_seg,
+                                                   const DevTF& tf, int K, R rho0, R rho1, R dsi, Acc<R>& acc) {
   const R invK = R(1) / R(K);
   const R dr = rho1 - rho0;
   const R tau_scale = R(tf.sigma) * dsi * invK;
@@ -85,7 +89,7 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
     const R rk = rho0 + (R(k) + R(0.5)) * invK * dr;
     R x = (rk - R(tf.lo)) * R(tf.inv_range);
     x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-    const float4 c = tf_eval(s_r, s_rgba, tf.n, (float)x);
+    const float4 c = tf_eval(s_r, s_rgba, s_seg, tf.n, (float)x);
     const R T = fast_exp<R>(-tau_scale * R(c.w));
     const R w = (R(1) - T) * (R(1) - acc.a);
     acc.C[0] += w * R(c.x);
@@ -110,9 +114,17 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   typedef typename Vec4T<R>::type V4;
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
+  __shared__ unsigned char s_seg[kTfTable];
   for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
     s_r[i] = tf.r[i];
     s_rgba[i] = tf.rgba[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
+    const float x = (float)i / (float)kTfTable;
+    int k = 0;
+    while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
+    s_seg[i] = (unsigned char)k;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -127,6 +139,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   // lane state
   int pix = -1;           // -1: needs a pixel; -2: queue drained
   int q = 0, np = 0, stage = 0, j = 0, nsamp = 0, nlast = 0, steps = 0, blk = 0;
+  BlockInfo B = V.blocks[0];
   R o[3], d[3], g_in[3], p[3], k1[3], k2[3], k3[3], pn[3];
   R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0;
   bool last = false;
@@ -169,6 +182,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         L = R(po.x) - R(pi.x);
         if (!(L > R(0))) continue;
         blk = __ldg(pair_block + slot);
+        B = V.blocks[blk];
 #pragma unroll
         for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pi.x) * d[r];
         p[0] = R(pi.y); p[1] = R(pi.z); p[2] = R(pi.w);
@@ -208,10 +222,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     }
     // ---- the one right-hand side of this iteration (converged across lanes)
     R W[3], rho, phi[3];
-    {
-      const BlockInfo B = V.blocks[live ? blk : 0];
-      rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
-    }
+    rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
     if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
@@ -246,13 +257,13 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
           p[r] = x[r];
           k1[r] = W[r];
         }
-        R fac = err > R(0) ? R(0.9) * cbrt(tol / err) : R(5);
+        R fac = err > R(0) ? R(0.9) * pow_third<R>(tol / err) : R(5);
         fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
         const R hn = hh * fac;
         bool pair_done = capped;
         if (last) {
           const R s_t = (j <= nsamp) ? R(j) * ds : L;
-          composite_interval<R>(s_r, s_rgba, tf, args.K, rho_prev, rho, s_t - s_last, acc);
+          composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rho, s_t - s_last, acc);
           if (STATS) {
             ++c_samp;
             R sx, sy;
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         }
       } else {
         if (STATS) ++c_rej;
-        const R fac = R(0.9) * cbrt(tol / err);
+        const R fac = R(0.9) * pow_third<R>(tol / err);
         h = hh * (fac < R(0.2) ? R(0.2) : fac);
       }
     }
