@@ -194,6 +194,29 @@ ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_p
                       int width, int height, float* out_rgba, void* workspace,
                       size_t workspace_bytes, void* stream);
 
+/* Render a small window without allocating device memory.  For callers that
+ * cannot call cudaMalloc at render time: code recording a CUDA graph (device
+ * allocation cannot be captured), real-time or plug-in hosts whose memory is
+ * owned by a pool or budget of their own, and threads that must not risk the
+ * implicit device synchronisation an allocation may cause.  The paper has no
+ * counterpart; this is a deployment variant of ivv_render.
+ * The per-frame workspace lives in a file-scope device array of 12 MiB
+ * (IVV_NOALLOC_SCRATCH_BYTES), enough for a 64 x 64 window at any precision
+ * with up to 16384 face patches; every GPU that loads the library keeps that
+ * array until the process exits.  Larger windows return IVV_ERR_WORKSPACE
+ * with the required size in ivv_last_error(); use ivv_render for them.
+ * The volume (created earlier) and out_rgba (device, caller-owned,
+ * [height][width][4] float32) are the caller's.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls share
+ * the one array, whose contents persist between calls (everything a frame
+ * needs zeroed is cleared by the frame itself), so calls that overlap on the
+ * GPU -- on different streams or from different threads -- race: serialise
+ * them. */
+#define IVV_NOALLOC_SCRATCH_BYTES (12u << 20)
+ivv_status ivv_render_noalloc(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
+                              int width, int height, float* out_rgba, void* stream);
+
 /* As ivv_render, but out_rgba_host is host memory (pinned for full speed);
  * the image is rendered into library-owned device memory, copied back with
  * cudaMemcpyAsync on `stream`, and the stream is synchronised. */

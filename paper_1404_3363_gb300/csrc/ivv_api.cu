@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "ivv_device.cuh"
@@ -518,6 +519,59 @@ ivv_status ivv_render_to_host(ivv_volume* v, const ivv_camera* cam, const ivv_re
   IVV_CUDA(cudaMemcpyAsync(out_host, v->own_out, bytes, cudaMemcpyDeviceToHost, s));
   IVV_CUDA(cudaStreamSynchronize(s));
   return IVV_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- no-alloc
+// Fixed scratch for ivv_render_noalloc: the per-frame workspace (fragment
+// lists, pairs, queue, counters) of a small window lives in this file-scope
+// device array instead of memory the caller or the library allocates.  Each
+// GPU that loads the library holds it until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;   // 12 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands for it, so the address is looked up once per
+// device (with that device current) and cached.
+ivv_status noalloc_scratch(void** out) {
+  int dev = 0;
+  IVV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(IVV_ERR_UNSUPPORTED, "device index too large for the scratch table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    IVV_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return IVV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ivv_status ivv_render_noalloc(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width,
+                              int height, float* out_rgba, void* stream) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  const int precision = params ? params->precision : IVV_PREC_FP32;
+  const size_t need = layout(v->hv.n_faces(), (size_t)width * height,
+                             precision == IVV_PREC_FP64 ? sizeof(ivv::Dbl4) : sizeof(float4)).total;
+  if (need > kNoAllocScratchBytes)
+    return fail(IVV_ERR_WORKSPACE, "window needs " + std::to_string(need) + " bytes of scratch; ivv_render_noalloc has " +
+                                       std::to_string(kNoAllocScratchBytes) + " (use ivv_render for larger windows)");
+  void* scratch = nullptr;
+  ivv_status st = noalloc_scratch(&scratch);
+  if (st != IVV_OK) return st;
+  return render_impl(v, cam, params, width, height, out_rgba, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
 }
 
 ivv_status ivv_render_pairs(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width,

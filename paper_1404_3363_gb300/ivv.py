@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.ivv_render.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp,
                              C.c_size_t, vp]
     L.ivv_render_to_host.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp]
+    L.ivv_render_noalloc.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp]
     L.ivv_render_pairs.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int,
                                    vp, vp, vp, vp, C.c_size_t, vp]
     L.ivv_eval_points.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -264,6 +265,15 @@ class Volume:
         _check(load().ivv_render(self.h, C.byref(cam), C.byref(prm), width, height,
                                  C.c_void_p(out.data_ptr()), C.c_void_p(ws), need,
                                  C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def render_noalloc(self, camera, params, width, height, out, stream=None, flags=0):
+        """Render a small window into the caller's float32 [H][W][4] CUDA tensor
+        without any device allocation (the library's fixed scratch array)."""
+        prm = params_struct(params, flags)
+        cam = camera_struct(camera)
+        _check(load().ivv_render_noalloc(self.h, C.byref(cam), C.byref(prm), width, height,
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
         return out
 
     def render_to_host(self, camera, params, width, height, out_host, stream=None, flags=0):
