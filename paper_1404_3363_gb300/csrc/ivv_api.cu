@@ -324,6 +324,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
   a.early_alpha = (float)p.early_alpha;
   a.K = p.supersample_k;
   a.max_steps = 200000;
+  a.max_step_samples = 8;
   a.npix = (int)npix;
   const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
   const bool mixed = p.precision == IVV_PREC_MIXED;

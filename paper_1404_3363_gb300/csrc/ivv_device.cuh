@@ -286,6 +286,7 @@ struct IntegrateArgs {
   float rk_tol, ds, c, early_alpha;
   int K;
   int max_steps;
+  int max_step_samples;   // longest RK step, in sample distances
   int npix;
 };
 

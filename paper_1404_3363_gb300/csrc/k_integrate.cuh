@@ -71,6 +71,12 @@ __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B,
   }
 }
 
+// s + hh, snapped to L when the step reaches the end of the pair.
+template <typename R> __device__ __forceinline__ R last_end(R s, R hh, R L) {
+  const R e = s + hh;
+  return e >= L ? L : e;
+}
+
 template <typename R> __device__ __forceinline__ R pow_third(R x);
 template <> __device__ __forceinline__ float pow_third<float>(float x) { return exp2f(__log2f(x) * (1.f / 3.f)); }
 template <> __device__ __forceinline__ double pow_third<double>(double x) { return cbrt(x); }
@@ -100,8 +106,12 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
 }
 
 // One lane's position in the integration of its current pixel.
-//   stage 0: start of a pair (evaluate W at p_in), 1..3: the three new
-//   right-hand sides of a Bogacki-Shampine step at q2, q3 and the step end.
+//   stage 0: start of a pair (evaluate W and rho at p_in);
+//   stages 1..3: the three new right-hand sides of a Bogacki-Shampine step
+//   (at q2, q3 and the step end); after an accepted step the samples s_j that
+//   fall inside it are visited in order:
+//   stage 4: rho at the dense-output point p(s_j) (cubic Hermite through the
+//   step's end points and slopes, third order like the pair itself).
 template <int P, typename R, bool MIXED, bool STATS>
 __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
                                                        const typename Vec4T<R>::type* __restrict__ pair_in,
@@ -133,16 +143,16 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   const R ds = R(args.ds), tol = R(args.rk_tol), cc = R(args.c), early = R(args.early_alpha);
   const R tail_eps = R(1e-12) * R(V.diag);
   const R hmin = R(1e-7) * ds;
+  const R hmax = R(args.max_step_samples) * ds;
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
   float max_dp = 0.f;
 
   // lane state
   int pix = -1;           // -1: needs a pixel; -2: queue drained
-  int q = 0, np = 0, stage = 0, j = 0, nsamp = 0, nlast = 0, steps = 0, blk = 0;
+  int q = 0, np = 0, stage = 0, j = 0, nsamp = 0, nlast = 0, steps = 0;
   BlockInfo B = V.blocks[0];
-  R o[3], d[3], g_in[3], p[3], k1[3], k2[3], k3[3], pn[3];
-  R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0;
-  bool last = false;
+  R o[3], d[3], g_in[3], p[3], k1[3], k2[3], k3[3], pn[3], p0[3], k0[3];
+  R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0, rho_end = 0, s0 = 0;
   Acc<R> acc;
 
   for (;;) {
@@ -181,8 +191,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         const V4 po = pair_out[slot];
         L = R(po.x) - R(pi.x);
         if (!(L > R(0))) continue;
-        blk = __ldg(pair_block + slot);
-        B = V.blocks[blk];
+        B = V.blocks[__ldg(pair_block + slot)];
 #pragma unroll
         for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pi.x) * d[r];
         p[0] = R(pi.y); p[1] = R(pi.z); p[2] = R(pi.w);
@@ -211,9 +220,17 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
       } else if (stage == 2) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) x[r] = p[r] + R(0.75) * hh * k2[r];
-      } else {
+      } else if (stage == 3) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) x[r] = pn[r];
+      } else {
+        // cubic Hermite dense output on the accepted step [s0, s] (length hh)
+        const R th = ((j <= nsamp ? R(j) * ds : L) - s0) / hh;
+        const R t2 = th * th, t3 = t2 * th;
+        const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + th;
+        const R h01 = R(3) * t2 - R(2) * t3, h11 = t3 - t2;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = h00 * p0[r] + h10 * hh * k0[r] + h01 * p[r] + h11 * hh * k1[r];
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = x[r] < R(0) ? R(0) : (x[r] > R(1) ? R(1) : x[r]);
@@ -226,6 +243,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
+    bool sample = false;        // rho / phi belong to sample s_j
     if (stage == 0) {
       k1[0] = W[0]; k1[1] = W[1]; k1[2] = W[2];
       rho_prev = rho;
@@ -237,7 +255,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
 #pragma unroll
       for (int r = 0; r < 3; ++r)
         pn[r] = p[r] + hh * (R(2.0 / 9.0) * k1[r] + R(1.0 / 3.0) * k2[r] + R(4.0 / 9.0) * k3[r]);
-    } else {
+    } else if (stage == 3) {
       R err = R(0);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -254,61 +272,93 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
+          p0[r] = p[r];
+          k0[r] = k1[r];
           p[r] = x[r];
           k1[r] = W[r];
         }
+        s0 = s;
+        s = last_end(s, hh, L);
+        rho_end = rho;
         R fac = err > R(0) ? R(0.9) * pow_third<R>(tol / err) : R(5);
         fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
-        const R hn = hh * fac;
-        bool pair_done = capped;
-        if (last) {
-          const R s_t = (j <= nsamp) ? R(j) * ds : L;
-          composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rho, s_t - s_last, acc);
-          if (STATS) {
-            ++c_samp;
-            R sx, sy;
-            project<R>(cam, phi, sx, sy);
-            const int xw = pix % cam.w, yw = pix / cam.w;
-            const float dp = 2.f * (float)fmax(fabs(sx - R(cam.x0 + xw)), fabs(sy - R(cam.y0 + yw)));
-            max_dp = fmaxf(max_dp, dp);
-          }
-          rho_prev = rho;
-          s = s_t;
-          s_last = s_t;
-          ++j;
-          h = h > hn ? h : hn;
-          if (acc.a >= early) {
-            pair_done = true;
-            q = np;              // early termination ends the pixel
-          }
-          if (j > nlast) pair_done = true;
-        } else {
-          s += hh;
-          h = hn;
-        }
-        if (pair_done) {
+        h = hh * fac;
+        if (capped) {
           stage = 0;
           continue;
         }
+        stage = 4;           // visit the samples inside (s0, s]
       } else {
         if (STATS) ++c_rej;
         const R fac = R(0.9) * pow_third<R>(tol / err);
         h = hh * (fac < R(0.2) ? R(0.2) : fac);
       }
+    } else {
+      sample = true;         // stage 4: rho at an interior sample point
     }
-    // ---- set up the next stage (a new step after stage 0 or 3)
-    if (stage == 0 || stage == 3) {
-      if (j > nlast) {             // zero-length remainder: pair done
-        stage = 0;
+    // ---- samples inside the accepted step: composite those that lie at or
+    //      before the step end (the end itself reuses the step-end rho)
+    if (stage == 4) {
+      for (;;) {
+        if (j > nlast) break;
+        const R s_t = (j <= nsamp) ? R(j) * ds : L;
+        R rj;
+        if (sample) {
+          rj = rho;
+          sample = false;
+        } else if (s_t >= s) {
+          if (s_t > s) break;          // beyond this step
+          rj = rho_end;                // the step ends on this sample
+          phi[0] = phi[0];
+        } else {
+          break;                       // needs a dense-output evaluation
+        }
+        composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rj, s_t - s_last, acc);
+        if (STATS) {
+          ++c_samp;
+          R sx, sy;
+          project<R>(cam, phi, sx, sy);
+          const int xw = pix % cam.w, yw = pix / cam.w;
+          const float dp = 2.f * (float)fmax(fabs(sx - R(cam.x0 + xw)), fabs(sy - R(cam.y0 + yw)));
+          max_dp = fmaxf(max_dp, dp);
+        }
+        rho_prev = rj;
+        s_last = s_t;
+        ++j;
+        if (acc.a >= early) {
+          q = np;                      // early termination ends the pixel
+          j = nlast + 1;
+        }
+      }
+      if (j > nlast) {
+        stage = 0;                     // pair done
         continue;
       }
       const R s_t = (j <= nsamp) ? R(j) * ds : L;
-      const R rem = s_t - s;
-      last = h >= rem;
-      hh = last ? rem : h;
+      if (s_t < s) continue;           // stage 4 again: next interior sample
+      // ---- next step
+      const R rem = L - s;
+      hh = h < hmax ? h : hmax;
+      hh = hh < rem ? hh : rem;
       stage = 1;
-    } else {
+      continue;
+    }
+    if (stage == 0) {
+      if (j > nlast) {                 // zero-length remainder: pair done
+        continue;
+      }
+      const R rem = L - s;
+      hh = h < hmax ? h : hmax;
+      hh = hh < rem ? hh : rem;
+      stage = 1;
+    } else if (stage == 1 || stage == 2) {
       ++stage;
+    } else {
+      // rejected step (stage 3): retry with the smaller h
+      const R rem = L - s;
+      hh = h < hmax ? h : hmax;
+      hh = hh < rem ? hh : rem;
+      stage = 1;
     }
   }
   // counters
