@@ -45,9 +45,10 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
       const int tx = xw / kTileW, ty = yw / kTileH;
       const int rx0 = c32.x0 + tx * kTileW, ry0 = c32.y0 + ty * kTileH;
       const int rx1 = std::min(rx0 + kTileW - 1, c32.x0 + w - 1), ry1 = std::min(ry0 + kTileH - 1, c32.y0 + h - 1);
-      R o[3], d[3], e1[3], e2[3];
+      R o[3], d[3], e1[3], e2[3], inv_d[3];
       make_ray<R>(cam, px, py, o, d);
       ray_frame<R>(d, e1, e2);
+      for (int r = 0; r < 3; ++r) inv_d[r] = R(1) / d[r];
       R tt[kMaxFrags], pp_all[kMaxFrags][3];
       unsigned mm[kMaxFrags];
       int n = 0, iters = 0;
@@ -55,7 +56,7 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
         const int4 b = boxes[f];
         if (!(b.x <= rx1 && b.z >= rx0 && b.y <= ry1 && b.w >= ry0)) continue;
         const FaceMeta& m = hv.faces[f];
-        if (!ray_box<R>(o, d, m.lo, m.hi, hull_pad)) continue;
+        if (!ray_box<R>(o, inv_d, m.lo, m.hi, hull_pad)) continue;
         const FaceMeta64& m64 = hv.faces64[f];
         R org[3], pa0, pa1, pb0, pb1;
         if constexpr (sizeof(R) == 8) {

@@ -448,13 +448,14 @@ IVV_HD void project_patch(const V4* cp, const R org[3], const R o[3], const R e1
   }
 }
 
-// Ray vs axis-aligned box [lo, hi] (padded); true if it meets the box at t >= 0.
+// Ray vs axis-aligned box [lo, hi] (padded); true if it meets the box at
+// t >= 0.  inv_d = 1 / d per component.
 template <typename R>
-IVV_HD bool ray_box(const R o[3], const R d[3], const float lo[3], const float hi[3], R pad) {
+IVV_HD bool ray_box(const R o[3], const R inv_d[3], const float lo[3], const float hi[3], R pad) {
   R t0 = R(-1e30), t1 = R(1e30);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const R inv = R(1) / d[r];
+    const R inv = inv_d[r];
     R ta = (R(lo[r]) - pad - o[r]) * inv, tb = (R(hi[r]) + pad - o[r]) * inv;
     if (ta > tb) { const R x = ta; ta = tb; tb = x; }
     t0 = ta > t0 ? ta : t0;

@@ -70,8 +70,10 @@ __global__ void __launch_bounds__(256, 2) k2_intersect(DevVolume V, DevCamera<R>
   const int rx0 = cam.x0 + tx * kTileW, ry0 = cam.y0 + ty * kTileH;
   const int rx1 = min(rx0 + kTileW - 1, cam.x0 + cam.w - 1), ry1 = min(ry0 + kTileH - 1, cam.y0 + cam.h - 1);
 
-  R o[3], d[3];
+  R o[3], d[3], inv_d[3];
   make_ray<R>(cam, px, py, o, d);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) inv_d[r] = R(1) / d[r];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     s_o[tid][r] = o[r];
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256, 2) k2_intersect(DevVolume V, DevCamera<R>
         if (valid) {
           const int4 b = s_box[q];
           pass = px >= b.x && px <= b.z && py >= b.y && py <= b.w &&
-                 ray_box<R>(o, d, s_meta[q].lo, s_meta[q].hi, hull_pad);
+                 ray_box<R>(o, inv_d, s_meta[q].lo, s_meta[q].hi, hull_pad);
         }
         const unsigned wb = __ballot_sync(0xffffffffu, pass);
         if (wb) {

@@ -170,9 +170,11 @@ def test_stats_and_timing(ivv):
     ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
     ref, rs = oracle.render(sc, ov, stats=True)
     assert abs(st["rays"] - (rs[..., 0] > 0).sum()) <= 3
-    assert st["samples"] >= 0.95 * rs[..., 3].sum()
-    assert st["rk_steps"] >= st["samples"] - st["pairs"]
-    assert st["rhs_evals"] >= 3 * st["rk_steps"]
+    assert abs(st["samples"] - rs[..., 3].sum()) <= 0.01 * rs[..., 3].sum()
+    # every accepted or rejected step costs three right-hand sides; pair starts
+    # and dense-output samples add one each
+    assert st["rhs_evals"] >= 3 * (st["rk_steps"] + st["rk_rejects"]) + st["pairs"]
+    assert st["rk_steps"] > 0
     assert 0 < st["max_delta_p"] <= 1.0          # pixel accuracy, Eq. 5
     t = vol.stage_times()
     assert set(t) == {"project", "intersect", "pair", "integrate"} and all(v >= 0 for v in t.values())
