@@ -29,10 +29,15 @@ METRIC = "Mpixels/s & ms/frame at 1920x1080 vs plain FP32, at <=1e-3 max RGBA er
 UNIT = "Mpixels/s"
 WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x1080 perspective, FP32"
 
-# Algorithmic FP32 flops of the integrator (cubic elements), counted per unit:
+# Algorithmic FP32 flops per unit (cubic elements):
+# integrator (K5)
 F_RHS = 1283      # one W(p): 576-FMA sum-factorised phi+J, Bernstein basis, V, 3x3 adjugate solve
 F_STEP = 70       # stage combinations, clamps and error norm of one BS3(2) step attempt
 F_SAMPLE = 150    # K=4 supersampled TF lookups + Alg. 1 updates + Eq. 23 per sample
+# ray/patch intersection (K2)
+F_HULL = 260      # patch control points into the ray frame (16 x 6 FMA) + hull + Jacobian-sign test
+F_NEWTON = 230    # one 2-D Newton iteration on a bicubic patch (value, 2 partials, 2x2 solve)
+F_FRAG = 220      # 3-D point, partials and facing of a root
 
 
 def _env_int(name, default):
@@ -117,6 +122,22 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu counters, or
+    None if its sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as f:
+            rec = json.load(f)[kernel]
+        m = hashlib.sha256()
+        for name in rec["src_files"]:
+            with open(os.path.join(ROOT, "paper_1404_3363_gb300", "csrc", name), "rb") as f:
+                m.update(f.read())
+        return rec["dram_bytes_per_launch"] if m.hexdigest()[:16] == rec["src_sha"] else None
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def cpu_oracle_sample(scene, target_s=12.0, max_stride=64):
@@ -212,6 +233,7 @@ def run_ours(args):
     st = vol.stats()
     flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
                 + st["samples"] * F_SAMPLE)
+    flops_k2 = st["isect_tests"] * F_HULL + st["isect_newton"] * F_NEWTON + st["fragments"] * F_FRAG
 
     # parity spot check of this frame against the oracle (untimed)
     max_err = None
@@ -261,6 +283,7 @@ def run_ours(args):
         dist.barrier()
     value = world * W * H / (ms * 1e-3) / 1e6
     k5_ms = stage_sum["integrate"] / args.steps
+    k2_ms = stage_sum["intersect"] / args.steps
 
     # end to end through the C ABI with host buffers (device->host copy inside)
     host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
@@ -280,7 +303,17 @@ def run_ours(args):
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_fp32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = flops_k5 / (k5_ms * 1e-3) / 1e12 if k5_ms > 0 else 0.0
+    peak_note = ("FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (max SM clock)"
+                 % (props.multi_processor_count, sm_max))
+
+    def roof(kernel, flops, ms):
+        achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp32 if peak_fp32 else None, "traffic": _ncu_traffic(kernel),
+                "peak_note": peak_note, "flops_per_launch": flops, "ms_per_launch": ms}
+
+    roofs = sorted([roof("k2_intersect", flops_k2, k2_ms), roof("k5_integrate", flops_k5, k5_ms)],
+                   key=lambda r: -r["ms_per_launch"])
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -303,12 +336,8 @@ def run_ours(args):
                     "ms_per_frame": e2e_ms,
                     "h2d_bytes_per_step": ctypes.sizeof(ivv.Camera) + ctypes.sizeof(ivv.RenderParams),
                     "d2h_bytes_per_step": W * H * 16},
-            "roofline": {"bound": "alu", "kernel": "k5_integrate", "achieved": achieved, "peak": peak_fp32,
-                         "unit": "TFLOP/s", "frac": achieved / peak_fp32 if peak_fp32 else None,
-                         "traffic": None,
-                         "peak_note": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (max SM clock)"
-                                      % (props.multi_processor_count, sm_max),
-                         "flops_per_launch": flops_k5, "k5_ms": k5_ms},
+            "roofline": roofs[0],
+            "roofline_kernels": roofs,
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
                                         "fragments", "isect_tests", "isect_newton")},
             "max_delta_p": st["max_delta_p"],
