@@ -56,7 +56,7 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
         const int4 b = boxes[f];
         if (!(b.x <= rx1 && b.z >= rx0 && b.y <= ry1 && b.w >= ry0)) continue;
         const FaceMeta& m = hv.faces[f];
-        if (!ray_box<R>(o, inv_d, m.lo, m.hi, hull_pad)) continue;
+        if (!ray_box<R>(o, inv_d, m.lo, m.hi, hull_pad) || !ray_obb<R>(o, d, m, R(4) * hull_pad)) continue;
         const FaceMeta64& m64 = hv.faces64[f];
         R org[3], pa0, pa1, pb0, pb1;
         if constexpr (sizeof(R) == 8) {

@@ -98,6 +98,57 @@ double det3(const double J[3][3]) {
          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
 }
 
+// Oriented bounding box of a face patch's control points (relative to org):
+// axes from the patch tangents at its centre, extents from the control
+// points, padded by a relative 1e-6 so the FP32 copy stays conservative.
+void face_obb(const double* cp, int P, const double org[3], FaceMeta& m) {
+  const int n1 = P + 1;
+  double b[4], db[4];
+  bernstein(P, 0.5, b, db);
+  double Sa[3] = {0, 0, 0}, Sb[3] = {0, 0, 0};
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n1; ++i)
+      for (int r = 0; r < 3; ++r) {
+        Sa[r] += db[i] * b[j] * cp[(j * n1 + i) * 4 + r];
+        Sb[r] += b[i] * db[j] * cp[(j * n1 + i) * 4 + r];
+      }
+  auto norm = [](double* v) {
+    const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (n > 0) for (int r = 0; r < 3; ++r) v[r] /= n;
+    return n;
+  };
+  double ax[3][3];
+  for (int r = 0; r < 3; ++r) ax[0][r] = Sa[r];
+  double nrm[3] = {Sa[1] * Sb[2] - Sa[2] * Sb[1], Sa[2] * Sb[0] - Sa[0] * Sb[2], Sa[0] * Sb[1] - Sa[1] * Sb[0]};
+  if (norm(ax[0]) == 0 || norm(nrm) == 0) {           // degenerate: axis-aligned box
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 3; ++r) ax[a][r] = a == r ? 1.0 : 0.0;
+  } else {
+    for (int r = 0; r < 3; ++r) ax[2][r] = nrm[r];
+    ax[1][0] = ax[2][1] * ax[0][2] - ax[2][2] * ax[0][1];
+    ax[1][1] = ax[2][2] * ax[0][0] - ax[2][0] * ax[0][2];
+    ax[1][2] = ax[2][0] * ax[0][1] - ax[2][1] * ax[0][0];
+    norm(ax[1]);
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, ext = 0;
+  for (int k = 0; k < n1 * n1; ++k)
+    for (int a = 0; a < 3; ++a) {
+      const double x = ax[a][0] * cp[k * 4] + ax[a][1] * cp[k * 4 + 1] + ax[a][2] * cp[k * 4 + 2];
+      lo[a] = std::min(lo[a], x);
+      hi[a] = std::max(hi[a], x);
+    }
+  for (int a = 0; a < 3; ++a) ext = std::max(ext, hi[a] - lo[a]);
+  for (int r = 0; r < 3; ++r) {
+    double c = org[r];
+    for (int a = 0; a < 3; ++a) c += ax[a][r] * 0.5 * (lo[a] + hi[a]);
+    m.obb_c[r] = (float)c;
+  }
+  for (int a = 0; a < 3; ++a) {
+    for (int r = 0; r < 3; ++r) m.obb_ax[a][r] = (float)ax[a][r];
+    m.obb_h[a] = (float)(0.5 * (hi[a] - lo[a]) + 1e-6 * ext + 1e-6 * std::fabs(org[0] + org[1] + org[2]));
+  }
+}
+
 }  // namespace
 
 void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
@@ -322,6 +373,7 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
             m.org[r] = (float)forg[r];
             m64.org[r] = forg[r];
           }
+          face_obb(&hv.face_cp[hv.face_cp.size() - (size_t)n1 * n1 * 4], P, forg, m);
           hv.faces.push_back(m);
           hv.faces64.push_back(m64);
         }

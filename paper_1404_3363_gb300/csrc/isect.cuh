@@ -464,6 +464,30 @@ IVV_HD bool ray_box(const R o[3], const R inv_d[3], const float lo[3], const flo
   return t1 >= t0 && t1 >= R(0);
 }
 
+// Ray vs the oriented box of a face patch (padded); true if it meets the box
+// at t >= 0.
+template <typename R>
+IVV_HD bool ray_obb(const R o[3], const R d[3], const FaceMeta& m, R pad) {
+  const R w[3] = {o[0] - R(m.obb_c[0]), o[1] - R(m.obb_c[1]), o[2] - R(m.obb_c[2])};
+  R t0 = R(-1e30), t1 = R(1e30);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R oa = R(m.obb_ax[a][0]) * w[0] + R(m.obb_ax[a][1]) * w[1] + R(m.obb_ax[a][2]) * w[2];
+    const R da = R(m.obb_ax[a][0]) * d[0] + R(m.obb_ax[a][1]) * d[1] + R(m.obb_ax[a][2]) * d[2];
+    const R hw = R(m.obb_h[a]) + pad;
+    if (fabs(da) < R(1e-30)) {
+      if (oa < -hw || oa > hw) return false;
+      continue;
+    }
+    const R inv = R(1) / da;
+    R ta = (-hw - oa) * inv, tb = (hw - oa) * inv;
+    if (ta > tb) { const R x = ta; ta = tb; tb = x; }
+    t0 = ta > t0 ? ta : t0;
+    t1 = tb < t1 ? tb : t1;
+  }
+  return t1 >= t0 && t1 >= R(0);
+}
+
 // Fragment of a root (a,b) of face `m`: depth t, facing, block parameter point.
 template <int P, typename R, typename V4>
 IVV_HD void make_fragment(const V4* cp, const R org[3], const FaceMeta& m, const R pa0, const R pa1, const R pb0,

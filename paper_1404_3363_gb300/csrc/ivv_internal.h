@@ -12,7 +12,7 @@
 namespace ivv {
 
 constexpr int kTileW = 16;          // K2 screen tile (one CTA)
-constexpr int kTileH = 16;
+constexpr int kTileH = 8;
 constexpr int kMaxFrags = 32;       // fragment slots per pixel (A-buffer)
 constexpr int kMaxPairs = 16;       // entry/exit pair slots per pixel
 
@@ -25,6 +25,11 @@ struct FaceMeta {
   float a0, a1, b0, b1;
   float org[3];
   float lo[3], hi[3];
+  // oriented box of the control points: centre, axes (rows: tangent a,
+  // its orthogonal complement in the tangent plane, normal), half extents
+  float obb_c[3];
+  float obb_ax[3][3];
+  float obb_h[3];
 };
 
 struct FaceMeta64 {

@@ -4,7 +4,7 @@
 // directly:
 //   K0 face_project  -- conservative screen box of each face patch from its
 //                       control points (convex hull property).
-//   K2 intersect     -- one CTA per 16x16 screen tile: cull the face boxes
+//   K2 intersect     -- one CTA per 16x8 screen tile: cull the face boxes
 //                       against the tile and stage the surviving patches in
 //                       shared memory; every pixel tests its ray against each
 //                       staged patch's screen box and bounding box and queues
@@ -41,7 +41,7 @@ __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const Dev
 }
 
 template <int P, typename R, bool MIXED, bool STATS>
-__global__ void __launch_bounds__(256, 2) k2_intersect(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
+__global__ void __launch_bounds__(kTileW * kTileH, 4) k2_intersect(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
                                                        const int4* __restrict__ boxes,
                                                        typename Vec4T<R>::type* __restrict__ frag_tp,
                                                        unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(256, 2) k2_intersect(DevVolume V, DevCamera<R>
         if (valid) {
           const int4 b = s_box[q];
           pass = px >= b.x && px <= b.z && py >= b.y && py <= b.w &&
-                 ray_box<R>(o, inv_d, s_meta[q].lo, s_meta[q].hi, hull_pad);
+                 ray_box<R>(o, inv_d, s_meta[q].lo, s_meta[q].hi, hull_pad) &&
+                 ray_obb<R>(o, d, s_meta[q], R(4) * hull_pad);
         }
         const unsigned wb = __ballot_sync(0xffffffffu, pass);
         if (wb) {
@@ -245,7 +246,7 @@ void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCame
   const int tiles = ((cam.w + kTileW - 1) / kTileW) * ((cam.h + kTileH - 1) / kTileH);
   if (tiles <= 0) return;
 #define IVV_K2(PP, MM, SS) \
-  k2_intersect<PP, R, MM, SS><<<tiles, 256, 0, s>>>(V, cam, cam64, boxes, frag_tp, frag_meta, frag_count, st)
+  k2_intersect<PP, R, MM, SS><<<tiles, kTileW * kTileH, 0, s>>>(V, cam, cam64, boxes, frag_tp, frag_meta, frag_count, st)
   if constexpr (sizeof(R) == 4) {
     if (V.P == 2) {
       if (mixed) { if (stats) IVV_K2(2, true, true); else IVV_K2(2, true, false); }
