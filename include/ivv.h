@@ -118,12 +118,19 @@ typedef struct {
  *              (§3.2.1 supersampling) [4]
  * c            weight of the perpendicular field V_perp (Eq. 10) [1]
  * early_alpha  stop a pixel once alpha_dst >= early_alpha [1 - 1e-4]
- * use_mlp_guess reserved, must be 0
+ * use_mlp_guess IVV_GUESS_* initial guess of the RF method; must be
+ *              IVV_GUESS_CENTER (0) with the ODE method [0]
  * precision    IVV_PREC_* [FP32]
  * flags        IVV_FLAG_* [0]
  * x0, y0, full_width, full_height
  *              render the window [x0, x0+width) x [y0, y0+height) of a
- *              full_width x full_height image (0 = the window is the image) */
+ *              full_width x full_height image (0 = the window is the image)
+ * method       IVV_METHOD_* [ODE]; RF supports FP32 precision only, reads
+ *              back the sample count (one stream synchronisation) and keeps
+ *              its sample buffers (40 bytes per sample) in library memory
+ * rf_tol       RF stopping rule: ||phi(p) - g|| <= rf_tol times the half width
+ *              of the pixel at the sample's depth (the paper stops at the
+ *              pixel frustum, rf_tol = 1) [0.05] */
 typedef struct {
   double rk_tol;
   double ds;
@@ -134,7 +141,23 @@ typedef struct {
   int precision;
   int flags;
   int x0, y0, full_width, full_height;
+  int method;
+  double rf_tol;
 } ivv_render_params;
+
+/* Preimage methods of stage 3 (§5): */
+enum {
+  IVV_METHOD_ODE = 0,   /* pulled-back view-ray ODE, embedded RK (§5.2)         */
+  IVV_METHOD_RF = 1     /* per-sample Newton root finding (§5.1), all samples in
+                           parallel from an initial guess chosen by use_mlp_guess */
+};
+
+/* Initial guesses of the RF method (use_mlp_guess): */
+enum {
+  IVV_GUESS_CENTER = 0, /* parameter centre (1/2, 1/2, 1/2) of the block         */
+  IVV_GUESS_MLP = 1,    /* the block's trained network (ivv_train_guess)         */
+  IVV_GUESS_CHORD = 2   /* p_in + (s / L)(p_out - p_in) along the pair            */
+};
 
 /* Counters of the last instrumented render (IVV_FLAG_STATS) plus overflow
  * and cap counters of every render since the last ivv_reset_stats. */
@@ -153,6 +176,8 @@ typedef struct {
   unsigned long long pair_overflow; /* pairs dropped (list full)               */
   unsigned long long unmatched;     /* records left unpaired by Alg. 2          */
   unsigned long long step_cap;      /* pairs that hit the RK step cap          */
+  unsigned long long rf_newton_iters; /* RF: Newton iterations over all samples */
+  unsigned long long rf_unconverged;  /* RF: samples that missed the tolerance  */
   double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
 } ivv_stats;
 
@@ -266,6 +291,51 @@ ivv_status ivv_host_render_pairs(const ivv_block_desc* blocks, int n_blocks, int
  * (ms[IVV_N_STAGES], CUDA events on the render stream); synchronises that
  * stream.  Returns IVV_ERR_INVALID_ARG if no timed render was made. */
 ivv_status ivv_get_stage_times(ivv_volume* vol, float* ms);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial guess of the inverse geometry map (not in the paper).
+ * Per block, a 3-64-64-3 perceptron (ReLU) maps g_hat = (g - c) * inv_h, the
+ * world point normalised to the block's control-point box, to a parameter
+ * guess p_hat.  Parameters are one flat float vector of IVV_GUESS_PARAMS
+ * values: W1 [64][3], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3].
+ * ------------------------------------------------------------------------- */
+#define IVV_GUESS_PARAMS 4611
+
+typedef struct {
+  int samples_per_block;   /* forward-map samples per block [1 << 20]        */
+  int epochs;              /* passes over the samples [8]                     */
+  int batch;               /* mini-batch size, multiple of 128 [8192]         */
+  float lr;                /* Adam learning rate, cosine-decayed to lr/10 [3e-3] */
+  unsigned long long seed; /* sample and initialisation seed [1]              */
+} ivv_guess_train_params;
+
+/* Train every block's network on the device: samples p uniform in [0,1]^3
+ * (counter-based hash of (seed, block, index)), targets from g = phi(p)
+ * evaluated by the library's spline kernels; Adam on the mean squared error.
+ * final_loss (host, [n_blocks], may be NULL) receives each block's mean loss
+ * over its first 65536 samples after training.  Allocates its sample buffers
+ * (samples_per_block * 32 bytes) for the duration of the call; synchronises
+ * `stream`. */
+ivv_status ivv_train_guess(ivv_volume* vol, const ivv_guess_train_params* params, float* final_loss,
+                           void* stream);
+
+/* Tensor-core inference (FP16 weights, FP32 accumulation): g [n][4] device
+ * floats (x, y, z, ignored) of points in the blocks block_of [n] (device
+ * int32); p_out [n][4] device floats (p_hat, 0).  Needs trained or set
+ * weights (IVV_ERR_INVALID_ARG otherwise). */
+ivv_status ivv_guess_points(ivv_volume* vol, int n, const float* g, const int* block_of, float* p_out,
+                            void* stream);
+
+/* One forward/backward pass of the training kernel (no update) on caller
+ * samples of one block: x_hat [n][4] and p [n][4] device floats (normalised
+ * inputs and targets).  grad (host, [IVV_GUESS_PARAMS]) and loss (host)
+ * receive the gradient and value of the mean squared error.  Synchronises. */
+ivv_status ivv_guess_loss_grad(ivv_volume* vol, int block, int n, const float* x_hat, const float* p,
+                               float* grad, float* loss, void* stream);
+
+/* Host copies of one block's parameters and normalisation (c[3], inv_h). */
+ivv_status ivv_get_guess_weights(ivv_volume* vol, int block, float* params, float* c, float* inv_h);
+ivv_status ivv_set_guess_weights(ivv_volume* vol, int block, const float* params);
 
 /* Counters (see ivv_stats); synchronises the stream of the last render. */
 ivv_status ivv_get_stats(ivv_volume* vol, ivv_stats* out);

@@ -11,6 +11,8 @@
 
 #include "ivv_device.cuh"
 #include "ivv_internal.h"
+#include "mlp.cuh"
+#include <random>
 
 namespace ivv {
 template <int P>
@@ -96,6 +98,17 @@ struct ivv_volume {
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[IVV_N_STAGES + 1] = {};
   bool timed = false;
+  // learned initial guess
+  float* d_theta = nullptr;        // [n_blocks][kMlpParams]
+  float* d_adam_m = nullptr;
+  float* d_adam_v = nullptr;
+  __half* d_theta16 = nullptr;
+  ivv::MlpNorm* d_norms = nullptr;
+  std::vector<ivv::MlpNorm> norms;
+  bool guess_ready = false;
+  // RF sample buffers (grown on demand)
+  void* rf_buf = nullptr;
+  size_t rf_bytes = 0;
 };
 
 namespace {
@@ -109,6 +122,9 @@ void free_volume(ivv_volume* v) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : v->ev)
     if (e) cudaEventDestroy(e);
+  void* g[] = {v->d_theta, v->d_adam_m, v->d_adam_v, v->d_theta16, v->d_norms, v->rf_buf};
+  for (void* p : g)
+    if (p) cudaFree(p);
   delete v;
 }
 
@@ -228,13 +244,20 @@ ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_ren
     p.c = 1.0;
     p.early_alpha = 1.0 - 1e-4;
   }
+  if (!(p.rf_tol > 0)) p.rf_tol = 0.05;
   if (!(p.ds > 0)) p.ds = diag / 128.0;
   if (!(p.rk_tol > 0) || !std::isfinite(p.rk_tol)) return fail(IVV_ERR_INVALID_ARG, "rk_tol must be positive");
   if (p.supersample_k < 1 || p.supersample_k > 64) return fail(IVV_ERR_INVALID_ARG, "supersample_k must be in 1..64");
   if (!(p.c >= 0) || !std::isfinite(p.c)) return fail(IVV_ERR_INVALID_ARG, "c must be non-negative");
   if (!(p.early_alpha > 0)) return fail(IVV_ERR_INVALID_ARG, "early_alpha must be positive");
   if (p.precision < IVV_PREC_FP32 || p.precision > IVV_PREC_FP64) return fail(IVV_ERR_INVALID_ARG, "bad precision");
-  if (p.use_mlp_guess != 0) return fail(IVV_ERR_UNSUPPORTED, "use_mlp_guess is not available in this build");
+  if (p.method != IVV_METHOD_ODE && p.method != IVV_METHOD_RF) return fail(IVV_ERR_INVALID_ARG, "bad method");
+  if (p.use_mlp_guess < IVV_GUESS_CENTER || p.use_mlp_guess > IVV_GUESS_CHORD)
+    return fail(IVV_ERR_INVALID_ARG, "bad initial-guess mode");
+  if (p.method == IVV_METHOD_ODE && p.use_mlp_guess != IVV_GUESS_CENTER)
+    return fail(IVV_ERR_INVALID_ARG, "initial guesses apply to the RF method");
+  if (p.method == IVV_METHOD_RF && p.precision != IVV_PREC_FP32)
+    return fail(IVV_ERR_UNSUPPORTED, "the RF method runs in FP32 precision");
   return IVV_OK;
 }
 
@@ -328,6 +351,52 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
   a.npix = (int)npix;
   const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
   const bool mixed = p.precision == IVV_PREC_MIXED;
+  if (p.method == IVV_METHOD_RF) {
+    if (p.use_mlp_guess == IVV_GUESS_MLP && !v->guess_ready)
+      return fail(IVV_ERR_INVALID_ARG, "IVV_GUESS_MLP needs ivv_train_guess or ivv_set_guess_weights first");
+    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    const float4* pin = (const float4*)(ws + L.pair_in);
+    const float4* pout = (const float4*)(ws + L.pair_out);
+    const int* pblk = (const int*)(ws + L.pair_block);
+    const int* pcnt = (const int*)(ws + L.pair_count);
+    const int* act = (const int*)(ws + L.active);
+    int* counters = (int*)(ws + L.counters);
+    int* cnt = (int*)(ws + L.frag_count);             // fragment lists are dead after stage 2
+    int* off = (int*)(ws + L.frag_meta);
+    int* sums = off + npix;
+    const float tail_eps = (float)(1e-12 * v->hv.diag);
+    ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms, s);
+    ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+    int total = 0;
+    IVV_CUDA(cudaMemcpyAsync(&total, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IVV_CUDA(cudaStreamSynchronize(s));
+    const size_t per = 2 * sizeof(float4) + sizeof(int) + sizeof(float);
+    const size_t cap_n = (size_t)std::max(total, 1);
+    st = ensure_own(&v->rf_buf, &v->rf_bytes, cap_n * per + 1024, s);
+    if (st != IVV_OK) return st;
+    char* rb = (char*)v->rf_buf;
+    float4* sg = (float4*)rb;
+    float4* sp = sg + cap_n;
+    int* sblk = (int*)(sp + cap_n);
+    float* srho = (float*)(sblk + cap_n);
+    ivv::DevCamera<float> c32 = dev_camera<float>(F);
+    ivv::launch_rf_expand(c32, pin, pout, pblk, pcnt, act, counters, off, (int)npix, (float)p.ds, tail_eps,
+                          p.use_mlp_guess, total, sg, sblk, sp, v->num_sms, s);
+    if (p.use_mlp_guess == IVV_GUESS_MLP)
+      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->num_sms, s);
+    if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
+    ivv::launch_rf_newton(V, c32, (float)p.rf_tol, counters + 2, sg, sblk, sp, srho, v->d_stats, stats, v->num_sms, s);
+    ivv::launch_rf_composite(tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act, counters, off,
+                             (int)npix, (float)p.ds, tail_eps, total, sg, srho, (float4*)out, v->d_stats, stats,
+                             v->num_sms, s);
+    if (p.flags & IVV_FLAG_TIMING) {
+      IVV_CUDA(cudaEventRecord(v->ev[4], s));
+      v->timed = true;
+    }
+    IVV_CUDA(cudaGetLastError());
+    return IVV_OK;
+  }
   if (fp64) {
     st = run_surface_pairs<double>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;
@@ -450,6 +519,42 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
   }
   v->lo = hv.def_lo;
   v->hi = hv.def_hi;
+  // per-block input normalisation of the guess network: control-point box
+  for (int b = 0; b < n_blocks; ++b) {
+    const ivv_block_desc& d = blocks[b];
+    const size_t ncp = (size_t)d.n_cp[0] * d.n_cp[1] * d.n_cp[2];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t q = 0; q < ncp; ++q)
+      for (int r = 0; r < 3; ++r) {
+        lo[r] = std::min(lo[r], d.geom_cp[3 * q + r]);
+        hi[r] = std::max(hi[r], d.geom_cp[3 * q + r]);
+      }
+    ivv::MlpNorm nm;
+    double hw = 0;
+    for (int r = 0; r < 3; ++r) {
+      nm.c[r] = (float)(0.5 * (lo[r] + hi[r]));
+      hw = std::max(hw, 0.5 * (hi[r] - lo[r]));
+    }
+    nm.inv_h = (float)(1.0 / (hw > 0 ? hw : 1.0));
+    v->norms.push_back(nm);
+  }
+  {
+    const size_t np = (size_t)n_blocks * ivv::kMlpParams;
+    if ((st = upload<float>(&v->d_theta, nullptr, np, s)) != IVV_OK ||
+        (st = upload<float>(&v->d_adam_m, nullptr, np, s)) != IVV_OK ||
+        (st = upload<float>(&v->d_adam_v, nullptr, np, s)) != IVV_OK ||
+        (st = upload<__half>(&v->d_theta16, nullptr, np, s)) != IVV_OK ||
+        (st = upload(&v->d_norms, v->norms.data(), v->norms.size(), s)) != IVV_OK) {
+      std::string m = g_err;
+      free_volume(v);
+      return fail(st, m);
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      free_volume(v);
+      return cuda_fail(e, "guess buffers");
+    }
+  }
   *out = v;
   return IVV_OK;
 }
@@ -620,6 +725,159 @@ ivv_status ivv_eval_points(ivv_volume* v, int block, int n, const float* p, floa
   return IVV_OK;
 }
 
+// ---------------------------------------------------------------- guess
+ivv_status ivv_train_guess(ivv_volume* v, const ivv_guess_train_params* in, float* final_loss, void* stream) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  ivv_guess_train_params p;
+  if (in) {
+    p = *in;
+  } else {
+    p.samples_per_block = 1 << 20;
+    p.epochs = 8;
+    p.batch = 8192;
+    p.lr = 3e-3f;
+    p.seed = 1;
+  }
+  if (p.samples_per_block < 128 || p.epochs < 1 || p.batch < 128 || p.batch % 128 || !(p.lr > 0))
+    return fail(IVV_ERR_INVALID_ARG, "bad training parameters");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int S = p.samples_per_block;
+  const int nb = v->hv.n_blocks;
+  const int ctas = ivv::mlp_train_ctas(std::max(p.batch, std::min(S, 65536)));
+  float4 *xs = nullptr, *ps = nullptr;
+  float *partial = nullptr, *partial_loss = nullptr, *grad = nullptr, *loss = nullptr;
+  auto cleanup = [&]() {
+    void* q[] = {xs, ps, partial, partial_loss, grad, loss};
+    for (void* x : q)
+      if (x) cudaFree(x);
+  };
+  cudaError_t e = cudaMalloc(&xs, sizeof(float4) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&ps, sizeof(float4) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&partial, sizeof(float) * (size_t)ctas * ivv::kMlpParams);
+  if (e == cudaSuccess) e = cudaMalloc(&partial_loss, sizeof(float) * ctas);
+  if (e == cudaSuccess) e = cudaMalloc(&grad, sizeof(float) * ivv::kMlpParams);
+  if (e == cudaSuccess) e = cudaMalloc(&loss, sizeof(float));
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(IVV_ERR_OOM, std::string("training buffers: ") + cudaGetErrorString(e));
+  }
+  const ivv::DevVolume V = dev_volume(v);
+  const long steps = (long)p.epochs * std::max(1, S / p.batch);
+  for (int b = 0; b < nb; ++b) {
+    // He-style initialisation, seeded per block
+    std::mt19937_64 rng(p.seed * 1000003ull + (unsigned long long)b);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<float> th(ivv::kMlpParams, 0.f);
+    for (int i = 0; i < ivv::kMlpH * 3; ++i) th[ivv::kOffW1 + i] = (float)(nd(rng) * std::sqrt(2.0 / 3.0));
+    for (int i = 0; i < ivv::kMlpH * ivv::kMlpH; ++i) th[ivv::kOffW2 + i] = (float)(nd(rng) * std::sqrt(2.0 / ivv::kMlpH));
+    for (int i = 0; i < 3 * ivv::kMlpH; ++i) th[ivv::kOffW3 + i] = (float)(nd(rng) * std::sqrt(1.0 / ivv::kMlpH));
+    for (int i = 0; i < 3; ++i) th[ivv::kOffB3 + i] = 0.5f;
+    float* tb = v->d_theta + (size_t)b * ivv::kMlpParams;
+    float* mb = v->d_adam_m + (size_t)b * ivv::kMlpParams;
+    float* vb = v->d_adam_v + (size_t)b * ivv::kMlpParams;
+    __half* hb = v->d_theta16 + (size_t)b * ivv::kMlpParams;
+    e = cudaMemcpyAsync(tb, th.data(), sizeof(float) * ivv::kMlpParams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mb, 0, sizeof(float) * ivv::kMlpParams, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vb, 0, sizeof(float) * ivv::kMlpParams, s);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "guess init");
+    }
+    ivv::launch_mlp_samples(V, v->norms[b], b, S, p.seed, xs, ps, s);
+    for (long k = 1; k <= steps; ++k) {
+      const int first = (int)(((k - 1) * (long)p.batch) % S);
+      const double frac = (double)k / steps;
+      const float lr = (float)(p.lr * (0.1 + 0.9 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+      e = ivv::launch_mlp_fwd_bwd(tb, xs, ps, S, first, p.batch, 1.f / p.batch, partial, partial_loss, s);
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "mlp_fwd_bwd");
+      }
+      ivv::launch_mlp_reduce(partial, partial_loss, ivv::mlp_train_ctas(p.batch), grad, loss, s);
+      ivv::launch_mlp_adam(tb, mb, vb, grad, lr, (int)k, hb, s);
+    }
+    if (final_loss) {
+      const int n = std::min(S, 65536);
+      e = ivv::launch_mlp_fwd_bwd(tb, xs, ps, S, 0, n, 1.f / n, partial, partial_loss, s);
+      if (e == cudaSuccess) {
+        ivv::launch_mlp_reduce(partial, partial_loss, ivv::mlp_train_ctas(n), grad, loss, s);
+        e = cudaMemcpyAsync(final_loss + b, loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+      }
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "final loss");
+      }
+    }
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "training");
+  v->guess_ready = true;
+  return IVV_OK;
+}
+
+ivv_status ivv_guess_points(ivv_volume* v, int n, const float* g, const int* block_of, float* p_out, void* stream) {
+  if (!v || n < 0 || (n > 0 && (!g || !block_of || !p_out))) return fail(IVV_ERR_INVALID_ARG, "bad argument");
+  if (!v->guess_ready) return fail(IVV_ERR_INVALID_ARG, "the guess network is neither trained nor set");
+  if (((uintptr_t)g) % 16 || ((uintptr_t)p_out) % 16) return fail(IVV_ERR_INVALID_ARG, "g and p_out must be 16-byte aligned");
+  if (n == 0) return IVV_OK;
+  ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->num_sms,
+                        (cudaStream_t)stream);
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+ivv_status ivv_guess_loss_grad(ivv_volume* v, int block, int n, const float* x_hat, const float* p, float* grad,
+                               float* loss, void* stream) {
+  if (!v || !x_hat || !p || !grad || !loss || n <= 0) return fail(IVV_ERR_INVALID_ARG, "bad argument");
+  if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ctas = ivv::mlp_train_ctas(n);
+  float *partial = nullptr, *partial_loss = nullptr, *dgrad = nullptr, *dloss = nullptr;
+  cudaError_t e = cudaMalloc(&partial, sizeof(float) * (size_t)ctas * ivv::kMlpParams);
+  if (e == cudaSuccess) e = cudaMalloc(&partial_loss, sizeof(float) * ctas);
+  if (e == cudaSuccess) e = cudaMalloc(&dgrad, sizeof(float) * ivv::kMlpParams);
+  if (e == cudaSuccess) e = cudaMalloc(&dloss, sizeof(float));
+  if (e == cudaSuccess)
+    e = ivv::launch_mlp_fwd_bwd(v->d_theta + (size_t)block * ivv::kMlpParams, (const float4*)x_hat, (const float4*)p,
+                                n, 0, n, 1.f / n, partial, partial_loss, s);
+  if (e == cudaSuccess) {
+    ivv::launch_mlp_reduce(partial, partial_loss, ctas, dgrad, dloss, s);
+    e = cudaMemcpyAsync(grad, dgrad, sizeof(float) * ivv::kMlpParams, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dloss, sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  void* q[] = {partial, partial_loss, dgrad, dloss};
+  for (void* x : q)
+    if (x) cudaFree(x);
+  if (e != cudaSuccess) return cuda_fail(e, "guess loss/grad");
+  return IVV_OK;
+}
+
+ivv_status ivv_get_guess_weights(ivv_volume* v, int block, float* params, float* c, float* inv_h) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
+  if (params)
+    IVV_CUDA(cudaMemcpy(params, v->d_theta + (size_t)block * ivv::kMlpParams, sizeof(float) * ivv::kMlpParams,
+                        cudaMemcpyDeviceToHost));
+  if (c)
+    for (int r = 0; r < 3; ++r) c[r] = v->norms[block].c[r];
+  if (inv_h) *inv_h = v->norms[block].inv_h;
+  return IVV_OK;
+}
+
+ivv_status ivv_set_guess_weights(ivv_volume* v, int block, const float* params) {
+  if (!v || !params) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
+  float* tb = v->d_theta + (size_t)block * ivv::kMlpParams;
+  IVV_CUDA(cudaMemcpy(tb, params, sizeof(float) * ivv::kMlpParams, cudaMemcpyHostToDevice));
+  ivv::launch_mlp_to_half(tb, v->d_theta16 + (size_t)block * ivv::kMlpParams, ivv::kMlpParams, nullptr);
+  IVV_CUDA(cudaDeviceSynchronize());
+  v->guess_ready = true;
+  return IVV_OK;
+}
+
 ivv_status ivv_host_eval(const ivv_block_desc* blocks, int n_blocks, int scalar_mode, int block, int n,
                          const double* p, double* phi, double* jac, double* rho) {
   if (n < 0 || (n > 0 && !p)) return fail(IVV_ERR_INVALID_ARG, "bad points");
@@ -681,6 +939,8 @@ ivv_status ivv_get_stats(ivv_volume* v, ivv_stats* out) {
   out->pair_overflow = d.pair_overflow;
   out->unmatched = d.unmatched;
   out->step_cap = d.step_cap;
+  out->rf_newton_iters = d.rf_newton_iters;
+  out->rf_unconverged = d.rf_unconverged;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;

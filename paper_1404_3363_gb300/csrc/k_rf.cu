@@ -1,0 +1,388 @@
+// Root-finding ray integration (§5.1, Eqs. 6-7), batched over all samples of
+// all rays.  Because each sample's preimage is solved from its own initial
+// guess, the samples of a ray are independent and the work is spread one
+// thread per sample:
+//   R1 rf_count     -- samples per active pixel (over its pairs)
+//   R2 scan         -- exclusive scan of the counts (per-CTA scan, scan of the
+//                      CTA sums, add-back)
+//   R3 rf_expand    -- each sample's point g_j = o + (t_in + s_j) d, its block
+//                      and an initial guess: the block's parameter centre, or
+//                      the chord guess p_in + (s_j / L)(p_out - p_in); the
+//                      learned guess overwrites it (K6 in k_mlp.cu)
+//   R4 rf_newton    -- damped Newton on F(p) = phi(p) - g_j with a halving
+//                      line search and clamping to [0,1]^3, stopped when ||F||
+//                      is below rf_tol times the half width of the pixel at the
+//                      sample's depth (the paper's pixel-accuracy criterion);
+//                      the scalar at the converged point
+//   R5 rf_composite -- per pixel, Alg. 1 with supersampling over its samples
+//                      in front-to-back order, early termination
+#include <cuda_runtime.h>
+
+#include "ivv_device.cuh"
+
+namespace ivv {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+
+struct PairView {
+  float L, t_in;
+  float pin[3], pout[3];
+  int blk;
+  int nsamp, nlast;
+};
+
+__device__ __forceinline__ bool load_pair(const float4* pair_in, const float4* pair_out, const int* pair_block,
+                                          size_t slot, float ds, float tail_eps, PairView& v) {
+  const float4 pi = pair_in[slot], po = pair_out[slot];
+  v.L = po.x - pi.x;
+  if (!(v.L > 0.f)) return false;
+  v.t_in = pi.x;
+  v.pin[0] = pi.y; v.pin[1] = pi.z; v.pin[2] = pi.w;
+  v.pout[0] = po.y; v.pout[1] = po.z; v.pout[2] = po.w;
+  v.blk = pair_block[slot];
+  const float fl = floorf(v.L / ds);
+  v.nsamp = (int)fl;
+  v.nlast = v.nsamp + ((v.L - fl * ds > tail_eps) ? 1 : 0);
+  return true;
+}
+
+__global__ void k_rf_count(const float4* __restrict__ pair_in, const float4* __restrict__ pair_out,
+                           const int* __restrict__ pair_block, const int* __restrict__ pair_count,
+                           const int* __restrict__ active, const int* __restrict__ n_active, int npix, float ds,
+                           float tail_eps, int* __restrict__ cnt) {
+  const int nact = *n_active;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    int c = 0;
+    for (int q = 0; q < np; ++q) {
+      PairView v;
+      if (load_pair(pair_in, pair_out, pair_block, (size_t)q * npix + pix, ds, tail_eps, v)) c += v.nlast + 1;
+    }
+    cnt[item] = c;
+  }
+}
+
+// exclusive scan within each CTA of kScanBlock items; CTA totals to sums[]
+__global__ void __launch_bounds__(kScanBlock) k_scan_local(const int* __restrict__ in, const int* __restrict__ n_ptr,
+                                                           int* __restrict__ out, int* __restrict__ sums) {
+  __shared__ int warp_tot[kScanBlock / 32];
+  const int n = *n_ptr;
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  if (blockIdx.x * kScanBlock >= n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x = i < n ? in[i] : 0;
+  int v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_tot[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_tot[lane] = w;
+  }
+  __syncthreads();
+  const int incl = v + (warp > 0 ? warp_tot[warp - 1] : 0);
+  if (i < n) out[i] = incl - x;
+  if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = incl;
+}
+
+// exclusive scan of the CTA sums (one CTA, chunks of kScanBlock) and total
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* __restrict__ sums, const int* __restrict__ n_ptr,
+                                                          int cap, int* __restrict__ total) {
+  __shared__ int warp_tot[kScanBlock / 32];
+  __shared__ int carry;
+  const int n = (*n_ptr + kScanBlock - 1) / kScanBlock;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    const int x = i < n ? sums[i] : 0;
+    int v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int w = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const int incl = v + (warp > 0 ? warp_tot[warp - 1] : 0);
+    const int c = carry;
+    if (i < n) sums[i] = c + incl - x;
+    __syncthreads();
+    if (threadIdx.x == kScanBlock - 1) carry = c + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry < cap ? carry : cap;
+  if (threadIdx.x == 0 && carry > cap) total[1] = carry - cap;   // overflow count
+}
+
+__global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ n_ptr, const int* __restrict__ sums) {
+  const int n = *n_ptr;
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  if (i < n) out[i] += sums[blockIdx.x];
+}
+
+__global__ void k_rf_expand(DevCamera<float> cam, const float4* __restrict__ pair_in,
+                            const float4* __restrict__ pair_out, const int* __restrict__ pair_block,
+                            const int* __restrict__ pair_count, const int* __restrict__ active,
+                            const int* __restrict__ n_active, const int* __restrict__ off, int npix, float ds,
+                            float tail_eps, int guess, int cap, float4* __restrict__ sg, int* __restrict__ sblk,
+                            float4* __restrict__ sp) {
+  const int nact = *n_active;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int xw = pix % cam.w, yw = pix / cam.w;
+    float o[3], d[3];
+    make_ray<float>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
+    const int np = pair_count[pix];
+    int k = off[item];
+    for (int q = 0; q < np; ++q) {
+      PairView v;
+      if (!load_pair(pair_in, pair_out, pair_block, (size_t)q * npix + pix, ds, tail_eps, v)) continue;
+      for (int j = 0; j <= v.nlast; ++j, ++k) {
+        if (k >= cap) return;
+        const float s = j <= v.nsamp ? (float)j * ds : v.L;
+        const float t = v.t_in + s;
+        sg[k] = make_float4(o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2], s);
+        sblk[k] = v.blk;
+        float p[3];
+        if (guess == 2) {
+          const float a = s / v.L;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) p[r] = v.pin[r] + a * (v.pout[r] - v.pin[r]);
+        } else {
+          p[0] = p[1] = p[2] = 0.5f;
+        }
+        sp[k] = make_float4(p[0], p[1], p[2], 0.f);
+      }
+    }
+  }
+}
+
+template <int P, bool STATS>
+__global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float> cam, float rf_tol,
+                                                   const int* __restrict__ n_ptr, const float4* __restrict__ sg,
+                                                   const int* __restrict__ sblk, const float4* __restrict__ sp,
+                                                   float* __restrict__ srho, DevStats* __restrict__ st) {
+  const int n = *n_ptr;
+  unsigned long long c_it = 0, c_ev = 0, c_fail = 0;
+  // half width of a pixel per unit depth (perspective) or absolute (ortho)
+  const float px_half = cam.sy / (float)cam.H;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 g4 = sg[i];
+    const float g[3] = {g4.x, g4.y, g4.z};
+    const BlockInfo B = V.blocks[sblk[i]];
+    float depth = 1.f;
+    if (!cam.ortho)
+      depth = (g[0] - cam.eye[0]) * cam.f[0] + (g[1] - cam.eye[1]) * cam.f[1] + (g[2] - cam.eye[2]) * cam.f[2];
+    const float tol = rf_tol * px_half * depth;
+    const float4 p4 = sp[i];
+    float p[3] = {fminf(fmaxf(p4.x, 0.f), 1.f), fminf(fmaxf(p4.y, 0.f), 1.f), fminf(fmaxf(p4.z, 0.f), 1.f)};
+    float phi[3], J[3][3], rc;
+    eval_block<P, float, true>(V, B, p, phi, J, rc);
+    if (STATS) ++c_ev;
+    float F[3] = {phi[0] - g[0], phi[1] - g[1], phi[2] - g[2]};
+    float nF = sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    int it = 0;
+    for (; it < 16 && nF > tol; ++it) {
+      float dx[3];
+      const float rhs[3] = {-F[0], -F[1], -F[2]};
+      solve3<float>(J, rhs, dx);
+      float lam = 1.f;
+      bool moved = false;
+      for (int ls = 0; ls < 6; ++ls) {
+        float q[3], fq[3], Jq[3][3], rq;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) q[r] = fminf(fmaxf(p[r] + lam * dx[r], 0.f), 1.f);
+        eval_block<P, float, true>(V, B, q, fq, Jq, rq);
+        if (STATS) ++c_ev;
+        const float G[3] = {fq[0] - g[0], fq[1] - g[1], fq[2] - g[2]};
+        const float nG = sqrtf(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+        if (nG < nF || ls == 5) {
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            p[r] = q[r];
+            F[r] = G[r];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) J[r][c] = Jq[r][c];
+          }
+          rc = rq;
+          moved = nG < nF;
+          nF = nG;
+          break;
+        }
+        lam *= 0.5f;
+      }
+      if (!moved) break;
+    }
+    if (STATS) {
+      c_it += it;
+      if (nF > tol) ++c_fail;
+    }
+    float rho = rc;
+    if (V.mode != IVV_SCALAR_CP) {
+      rho = det3<float>(J);
+      if (V.mode == IVV_SCALAR_QUALITY) {
+        float f = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) f += J[r][c] * J[r][c];
+        rho /= sqrtf(f);
+      }
+    }
+    srho[i] = rho;
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c_it += __shfl_down_sync(0xffffffffu, c_it, o);
+      c_ev += __shfl_down_sync(0xffffffffu, c_ev, o);
+      c_fail += __shfl_down_sync(0xffffffffu, c_fail, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&st->rf_newton_iters, c_it);
+      atomicAdd(&st->rhs_evals, c_ev);
+      atomicAdd(&st->rf_unconverged, c_fail);
+    }
+  }
+}
+
+__global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __restrict__ pair_in,
+                               const float4* __restrict__ pair_out, const int* __restrict__ pair_block,
+                               const int* __restrict__ pair_count, const int* __restrict__ active,
+                               const int* __restrict__ n_active, const int* __restrict__ off, int npix, float ds,
+                               float tail_eps, int cap, const float4* __restrict__ sg, const float* __restrict__ srho,
+                               float4* __restrict__ out, DevStats* __restrict__ st, bool stats) {
+  __shared__ float s_r[256];
+  __shared__ float4 s_rgba[256];
+  __shared__ unsigned char s_seg[kTfTable];
+  for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
+    s_r[i] = tf.r[i];
+    s_rgba[i] = tf.rgba[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
+    const float x = (float)i / (float)kTfTable;
+    int k = 0;
+    while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
+    s_seg[i] = (unsigned char)k;
+  }
+  __syncthreads();
+  const int nact = *n_active;
+  unsigned long long c_samp = 0;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    int k = off[item];
+    float C[3] = {0.f, 0.f, 0.f}, a = 0.f;
+    bool done = false;
+    for (int q = 0; q < np && !done; ++q) {
+      PairView v;
+      if (!load_pair(pair_in, pair_out, pair_block, (size_t)q * npix + pix, ds, tail_eps, v)) continue;
+      float rho_prev = 0.f, s_prev = 0.f;
+      for (int j = 0; j <= v.nlast; ++j, ++k) {
+        if (k >= cap) {
+          done = true;
+          break;
+        }
+        const float rho = srho[k];
+        const float s = sg[k].w;
+        ++c_samp;
+        if (j > 0 && !done) {
+          const float invK = 1.f / (float)K;
+          const float dr = rho - rho_prev;
+          const float tau = tf.sigma * (s - s_prev) * invK;
+          for (int kk = 0; kk < K; ++kk) {
+            float x = (rho_prev + ((float)kk + 0.5f) * invK * dr - tf.lo) * tf.inv_range;
+            x = fminf(fmaxf(x, 0.f), 1.f);
+            const float4 c = tf_eval(s_r, s_rgba, s_seg, tf.n, x);
+            const float T = __expf(-tau * c.w);
+            const float w = (1.f - T) * (1.f - a);
+            C[0] += w * c.x;
+            C[1] += w * c.y;
+            C[2] += w * c.z;
+            a += w;
+          }
+          if (a >= early) done = true;
+        }
+        rho_prev = rho;
+        s_prev = s;
+      }
+    }
+    out[pix] = make_float4(C[0], C[1], C[2], a);
+  }
+  if (stats) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c_samp += __shfl_down_sync(0xffffffffu, c_samp, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&st->samples, c_samp);
+  }
+}
+
+}  // namespace
+
+void launch_rf_count(const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
+                     const int* n_active, int npix, float ds, float tail_eps, int* cnt, int num_sms, cudaStream_t s) {
+  k_rf_count<<<num_sms * 8, 256, 0, s>>>(pin, pout, pblk, pcnt, active, n_active, npix, ds, tail_eps, cnt);
+}
+
+void launch_rf_scan(const int* cnt, const int* n_active, int npix, int* off, int* sums, int cap, int* total,
+                    cudaStream_t s) {
+  const int blocks = (npix + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<blocks, kScanBlock, 0, s>>>(cnt, n_active, off, sums);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(sums, n_active, cap, total);
+  k_scan_add<<<blocks, kScanBlock, 0, s>>>(off, n_active, sums);
+}
+
+void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const float4* pout, const int* pblk,
+                      const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
+                      float tail_eps, int guess, int cap, float4* sg, int* sblk, float4* sp, int num_sms,
+                      cudaStream_t s) {
+  k_rf_expand<<<num_sms * 8, 256, 0, s>>>(cam, pin, pout, pblk, pcnt, active, n_active, off, npix, ds, tail_eps,
+                                          guess, cap, sg, sblk, sp);
+}
+
+void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, const int* n_ptr,
+                      const float4* sg, const int* sblk, const float4* sp, float* srho, DevStats* st, bool stats,
+                      int num_sms, cudaStream_t s) {
+  const int grid = num_sms * 16;
+  if (V.P == 2) {
+    if (stats) k_rf_newton<2, true><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+    else k_rf_newton<2, false><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+  } else {
+    if (stats) k_rf_newton<3, true><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+    else k_rf_newton<3, false><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+  }
+}
+
+void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
+                         const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
+                         float tail_eps, int cap, const float4* sg, const float* srho, float4* out, DevStats* st,
+                         bool stats, int num_sms, cudaStream_t s) {
+  k_rf_composite<<<num_sms * 8, 128, 0, s>>>(tf, K, early, pin, pout, pblk, pcnt, active, n_active, off, npix, ds,
+                                             tail_eps, cap, sg, srho, out, st, stats);
+}
+
+}  // namespace ivv

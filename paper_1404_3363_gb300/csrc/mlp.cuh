@@ -1,0 +1,41 @@
+// Layout and launchers of the learned initial-guess network (k_mlp.cu).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "ivv_device.cuh"
+
+namespace ivv {
+
+constexpr int kMlpH = 64;
+// flat parameter vector: W1 [64][3], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3]
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpH * 3;
+constexpr int kOffW2 = kOffB1 + kMlpH;
+constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
+constexpr int kOffW3 = kOffB2 + kMlpH;
+constexpr int kOffB3 = kOffW3 + 3 * kMlpH;
+constexpr int kMlpParams = kOffB3 + 3;      // 4611
+
+// Input normalisation of a block: g_hat = (g - c) * inv_h.
+struct MlpNorm {
+  float c[3];
+  float inv_h;
+};
+
+void launch_mlp_samples(const DevVolume& V, const MlpNorm& norm, int block, int S, unsigned long long seed,
+                        float4* x_out, float4* p_out, cudaStream_t s);
+size_t mlp_train_smem();
+int mlp_train_ctas(int n);
+cudaError_t launch_mlp_fwd_bwd(const float* theta, const float4* xs, const float4* ps, int S, int first, int n,
+                               float scale, float* partial, float* partial_loss, cudaStream_t s);
+void launch_mlp_reduce(const float* partial, const float* partial_loss, int nparts, float* grad, float* loss,
+                       cudaStream_t s);
+void launch_mlp_adam(float* theta, float* m, float* v, const float* grad, float lr, int step, __half* theta16,
+                     cudaStream_t s);
+void launch_mlp_to_half(const float* theta, __half* theta16, int n, cudaStream_t s);
+void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
+                      int n_static, float4* p_out, int num_sms, cudaStream_t s);
+
+}  // namespace ivv

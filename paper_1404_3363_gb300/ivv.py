@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "IVV_OK", 1: "IVV_ERR_INVALID_ARG", 2: "IVV_ERR_CUDA", 3: "IV
                 7: "IVV_ERR_UNSUPPORTED", 8: "IVV_ERR_WORKSPACE"}
 FLAG_STATS = 1
 FLAG_TIMING = 2
+GUESS_PARAMS = 4611
 STAGES = ("project", "intersect", "pair", "integrate")
 
 c_double_p = C.POINTER(C.c_double)
@@ -45,17 +46,27 @@ class Camera(C.Structure):
                 ("up", C.c_double * 3), ("fovy_deg", C.c_double), ("ortho_height", C.c_double)]
 
 
+METHOD_ODE, METHOD_RF = 0, 1
+GUESS_CENTER, GUESS_MLP, GUESS_CHORD = 0, 1, 2
+
+
 class RenderParams(C.Structure):
     _fields_ = [("rk_tol", C.c_double), ("ds", C.c_double), ("supersample_k", C.c_int),
                 ("c", C.c_double), ("early_alpha", C.c_double), ("use_mlp_guess", C.c_int),
                 ("precision", C.c_int), ("flags", C.c_int), ("x0", C.c_int), ("y0", C.c_int),
-                ("full_width", C.c_int), ("full_height", C.c_int)]
+                ("full_width", C.c_int), ("full_height", C.c_int), ("method", C.c_int), ("rf_tol", C.c_double)]
+
+
+class GuessTrainParams(C.Structure):
+    _fields_ = [("samples_per_block", C.c_int), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
+                ("seed", C.c_ulonglong)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in (
         "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
-        "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap")] + \
+        "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap",
+    "rf_newton_iters", "rf_unconverged")] + \
         [("max_delta_p", C.c_double)]
 
     def as_dict(self):
@@ -98,6 +109,11 @@ def load(path: str = LIB_PATH):
     L.ivv_get_stage_times.argtypes = [vp, c_float_p]
     L.ivv_host_render_pairs.argtypes = [C.POINTER(BlockDesc), C.c_int, C.c_int, C.POINTER(Camera),
                                         C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int, vp, vp, vp]
+    L.ivv_train_guess.argtypes = [vp, C.POINTER(GuessTrainParams), c_float_p, vp]
+    L.ivv_guess_points.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.ivv_guess_loss_grad.argtypes = [vp, C.c_int, C.c_int, vp, vp, c_float_p, c_float_p, vp]
+    L.ivv_get_guess_weights.argtypes = [vp, C.c_int, c_float_p, c_float_p, c_float_p]
+    L.ivv_set_guess_weights.argtypes = [vp, C.c_int, c_float_p]
     L.ivv_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.ivv_reset_stats.argtypes = [vp]
     L.ivv_volume_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
@@ -133,8 +149,10 @@ def params_struct(p=None, flags=0, window=None) -> RenderParams:
     q.supersample_k = p.supersample_k if p else 4
     q.c = p.c if p else 1.0
     q.early_alpha = p.early_alpha if p else 1.0 - 1e-4
-    q.use_mlp_guess = 0
+    q.use_mlp_guess = getattr(p, "use_mlp_guess", 0) if p else 0
     q.precision = p.precision if p else 0
+    q.method = getattr(p, "method", 0) if p else 0
+    q.rf_tol = getattr(p, "rf_tol", 0.05) if p else 0.05
     q.flags = flags
     if window is not None:
         q.x0, q.y0, q.full_width, q.full_height = window
@@ -319,6 +337,48 @@ class Volume:
         ms = (C.c_float * len(STAGES))()
         _check(load().ivv_get_stage_times(self.h, ms))
         return dict(zip(STAGES, list(ms)))
+
+    # ---- learned initial guess
+    def train_guess(self, samples_per_block=1 << 20, epochs=8, batch=8192, lr=3e-3, seed=1, stream=None):
+        """Train every block's guess network on the device; returns the final
+        mean squared error per block."""
+        nb = self.info()["n_blocks"]
+        out = (C.c_float * nb)()
+        prm = GuessTrainParams(samples_per_block, epochs, batch, lr, seed)
+        _check(load().ivv_train_guess(self.h, C.byref(prm), out, C.c_void_p(_stream_ptr(stream))))
+        return list(out)
+
+    def guess_points(self, g4, block_of, stream=None):
+        """Tensor-core guess p_hat [n][4] for CUDA tensors g4 [n][4] (float32)
+        and block_of [n] (int32)."""
+        import torch
+        g4 = g4.contiguous()
+        block_of = block_of.contiguous()
+        out = torch.empty_like(g4)
+        _check(load().ivv_guess_points(self.h, g4.shape[0], C.c_void_p(g4.data_ptr()), C.c_void_p(block_of.data_ptr()),
+                                       C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def guess_loss_grad(self, block, x4, p4, stream=None):
+        """(loss, gradient) of the device training kernel on one batch."""
+        grad = np.zeros(GUESS_PARAMS, np.float32)
+        loss = C.c_float()
+        _check(load().ivv_guess_loss_grad(self.h, block, x4.shape[0], C.c_void_p(x4.contiguous().data_ptr()),
+                                          C.c_void_p(p4.contiguous().data_ptr()), grad.ctypes.data_as(c_float_p),
+                                          C.byref(loss), C.c_void_p(_stream_ptr(stream))))
+        return loss.value, grad
+
+    def get_guess_weights(self, block):
+        w = np.zeros(GUESS_PARAMS, np.float32)
+        c = np.zeros(3, np.float32)
+        ih = C.c_float()
+        _check(load().ivv_get_guess_weights(self.h, block, w.ctypes.data_as(c_float_p), c.ctypes.data_as(c_float_p),
+                                            C.byref(ih)))
+        return w, c, ih.value
+
+    def set_guess_weights(self, block, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().ivv_set_guess_weights(self.h, block, w.ctypes.data_as(c_float_p)))
 
     def stats(self):
         s = Stats()

@@ -91,6 +91,8 @@ class RenderParams:
     early_alpha: float = 1.0 - 1e-4
     precision: int = PRECISION_FP32
     use_mlp_guess: int = 0
+    method: int = 0            # 0: ODE (§5.2), 1: per-sample root finding (§5.1)
+    rf_tol: float = 0.05       # RF stop: fraction of the pixel half width
 
 
 @dataclasses.dataclass
