@@ -294,9 +294,9 @@ ivv_status ivv_get_stage_times(ivv_volume* vol, float* ms);
 
 /* ---------------------------------------------------------------------------
  * Learned initial guess of the inverse geometry map (not in the paper).
- * Per block, a 3-64-64-3 perceptron (ReLU) maps g_hat = (g - c) * inv_h, the
- * world point normalised to the block's control-point box, to a parameter
- * guess p_hat.  Parameters are one flat float vector of IVV_GUESS_PARAMS
+ * Per block, a 3-64-64-3 perceptron (ReLU) maps g_hat = (g - c) * inv_h (per
+ * axis), the world point normalised to the block's control-point box
+ * [-1,1]^3, to a parameter guess p_hat.  Parameters are one flat float vector of IVV_GUESS_PARAMS
  * values: W1 [64][3], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3].
  * ------------------------------------------------------------------------- */
 #define IVV_GUESS_PARAMS 4611
@@ -304,7 +304,7 @@ ivv_status ivv_get_stage_times(ivv_volume* vol, float* ms);
 typedef struct {
   int samples_per_block;   /* forward-map samples per block [1 << 20]        */
   int epochs;              /* passes over the samples [8]                     */
-  int batch;               /* mini-batch size, multiple of 128 [8192]         */
+  int batch;               /* mini-batch size, multiple of 128 [4096]         */
   float lr;                /* Adam learning rate, cosine-decayed to lr/10 [3e-3] */
   unsigned long long seed; /* sample and initialisation seed [1]              */
 } ivv_guess_train_params;
@@ -333,7 +333,7 @@ ivv_status ivv_guess_points(ivv_volume* vol, int n, const float* g, const int* b
 ivv_status ivv_guess_loss_grad(ivv_volume* vol, int block, int n, const float* x_hat, const float* p,
                                float* grad, float* loss, void* stream);
 
-/* Host copies of one block's parameters and normalisation (c[3], inv_h). */
+/* Host copies of one block's parameters and normalisation (c[3], inv_h[3]). */
 ivv_status ivv_get_guess_weights(ivv_volume* vol, int block, float* params, float* c, float* inv_h);
 ivv_status ivv_set_guess_weights(ivv_volume* vol, int block, const float* params);
 

@@ -530,12 +530,13 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
         hi[r] = std::max(hi[r], d.geom_cp[3 * q + r]);
       }
     ivv::MlpNorm nm;
-    double hw = 0;
+    double hmax = 0;
+    for (int r = 0; r < 3; ++r) hmax = std::max(hmax, 0.5 * (hi[r] - lo[r]));
     for (int r = 0; r < 3; ++r) {
       nm.c[r] = (float)(0.5 * (lo[r] + hi[r]));
-      hw = std::max(hw, 0.5 * (hi[r] - lo[r]));
+      const double hw = std::max(0.5 * (hi[r] - lo[r]), 1e-6 * hmax);
+      nm.inv_h[r] = (float)(1.0 / (hw > 0 ? hw : 1.0));
     }
-    nm.inv_h = (float)(1.0 / (hw > 0 ? hw : 1.0));
     v->norms.push_back(nm);
   }
   {
@@ -734,7 +735,7 @@ ivv_status ivv_train_guess(ivv_volume* v, const ivv_guess_train_params* in, floa
   } else {
     p.samples_per_block = 1 << 20;
     p.epochs = 8;
-    p.batch = 8192;
+    p.batch = 4096;
     p.lr = 3e-3f;
     p.seed = 1;
   }
@@ -861,9 +862,10 @@ ivv_status ivv_get_guess_weights(ivv_volume* v, int block, float* params, float*
   if (params)
     IVV_CUDA(cudaMemcpy(params, v->d_theta + (size_t)block * ivv::kMlpParams, sizeof(float) * ivv::kMlpParams,
                         cudaMemcpyDeviceToHost));
-  if (c)
-    for (int r = 0; r < 3; ++r) c[r] = v->norms[block].c[r];
-  if (inv_h) *inv_h = v->norms[block].inv_h;
+  for (int r = 0; r < 3; ++r) {
+    if (c) c[r] = v->norms[block].c[r];
+    if (inv_h) inv_h[r] = v->norms[block].inv_h[r];
+  }
   return IVV_OK;
 }
 

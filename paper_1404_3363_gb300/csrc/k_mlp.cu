@@ -1,6 +1,6 @@
 // Learned initial guess for the inverse geometry map (not in the paper): per
 // block, a 3-64-64-3 perceptron with ReLU hidden layers maps a world point
-// normalised to the block's control-point box, g_hat = (g - c) / h, to a
+// normalised to the block's control-point box, g_hat = (g - c) / h per axis, to a
 // parameter-space guess p_hat.  It is trained on samples of the forward map
 // the method itself evaluates (p uniform in [0,1]^3, g = phi(p)).
 //
@@ -51,8 +51,8 @@ __global__ void k_mlp_samples(DevVolume V, MlpNorm norm, int block, int S, unsig
   const BlockInfo B = V.blocks[block];
   float phi[3], J[3][3], rho;
   eval_block<P, float, false>(V, B, p, phi, J, rho);
-  x_out[i] = make_float4((phi[0] - norm.c[0]) * norm.inv_h, (phi[1] - norm.c[1]) * norm.inv_h,
-                         (phi[2] - norm.c[2]) * norm.inv_h, 0.f);
+  x_out[i] = make_float4((phi[0] - norm.c[0]) * norm.inv_h[0], (phi[1] - norm.c[1]) * norm.inv_h[1],
+                         (phi[2] - norm.c[2]) * norm.inv_h[2], 0.f);
   p_out[i] = make_float4(p[0], p[1], p[2], 0.f);
 }
 
@@ -278,11 +278,13 @@ __global__ void __launch_bounds__(32 * kInferWarps) k_mlp_infer(const __half* __
       float x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
       if (r0 < n) {
         const float4 a = g[r0];
-        x0[0] = (a.x - nm.c[0]) * nm.inv_h; x0[1] = (a.y - nm.c[1]) * nm.inv_h; x0[2] = (a.z - nm.c[2]) * nm.inv_h;
+        x0[0] = (a.x - nm.c[0]) * nm.inv_h[0]; x0[1] = (a.y - nm.c[1]) * nm.inv_h[1];
+        x0[2] = (a.z - nm.c[2]) * nm.inv_h[2];
       }
       if (r1 < n) {
         const float4 a = g[r1];
-        x1[0] = (a.x - nm.c[0]) * nm.inv_h; x1[1] = (a.y - nm.c[1]) * nm.inv_h; x1[2] = (a.z - nm.c[2]) * nm.inv_h;
+        x1[0] = (a.x - nm.c[0]) * nm.inv_h[0]; x1[1] = (a.y - nm.c[1]) * nm.inv_h[1];
+        x1[2] = (a.z - nm.c[2]) * nm.inv_h[2];
       }
       // layer 1 on the FP32 pipe, written as A fragments of layer 2 (K = 64)
       unsigned A[4][4];

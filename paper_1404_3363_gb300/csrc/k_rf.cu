@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
     float depth = 1.f;
     if (!cam.ortho)
       depth = (g[0] - cam.eye[0]) * cam.f[0] + (g[1] - cam.eye[1]) * cam.f[1] + (g[2] - cam.eye[2]) * cam.f[2];
-    const float tol = rf_tol * px_half * depth;
+    // stop at the pixel-accuracy tolerance, but not below FP32 resolution
+    const float tol = fmaxf(rf_tol * px_half * depth, 2e-7f * (fabsf(g[0]) + fabsf(g[1]) + fabsf(g[2]) + V.diag));
     const float4 p4 = sp[i];
     float p[3] = {fminf(fmaxf(p4.x, 0.f), 1.f), fminf(fmaxf(p4.y, 0.f), 1.f), fminf(fmaxf(p4.z, 0.f), 1.f)};
     float phi[3], J[3][3], rc;

@@ -18,10 +18,11 @@ constexpr int kOffW3 = kOffB2 + kMlpH;
 constexpr int kOffB3 = kOffW3 + 3 * kMlpH;
 constexpr int kMlpParams = kOffB3 + 3;      // 4611
 
-// Input normalisation of a block: g_hat = (g - c) * inv_h.
+// Input normalisation of a block: g_hat_r = (g_r - c_r) * inv_h_r, mapping
+// the block's control-point box to [-1, 1]^3.
 struct MlpNorm {
   float c[3];
-  float inv_h;
+  float inv_h[3];
 };
 
 void launch_mlp_samples(const DevVolume& V, const MlpNorm& norm, int block, int S, unsigned long long seed,

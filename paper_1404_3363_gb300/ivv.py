@@ -339,7 +339,7 @@ class Volume:
         return dict(zip(STAGES, list(ms)))
 
     # ---- learned initial guess
-    def train_guess(self, samples_per_block=1 << 20, epochs=8, batch=8192, lr=3e-3, seed=1, stream=None):
+    def train_guess(self, samples_per_block=1 << 20, epochs=8, batch=4096, lr=3e-3, seed=1, stream=None):
         """Train every block's guess network on the device; returns the final
         mean squared error per block."""
         nb = self.info()["n_blocks"]
@@ -371,10 +371,10 @@ class Volume:
     def get_guess_weights(self, block):
         w = np.zeros(GUESS_PARAMS, np.float32)
         c = np.zeros(3, np.float32)
-        ih = C.c_float()
+        ih = np.zeros(3, np.float32)
         _check(load().ivv_get_guess_weights(self.h, block, w.ctypes.data_as(c_float_p), c.ctypes.data_as(c_float_p),
-                                            C.byref(ih)))
-        return w, c, ih.value
+                                            ih.ctypes.data_as(c_float_p)))
+        return w, c, ih
 
     def set_guess_weights(self, block, w):
         w = np.ascontiguousarray(w, dtype=np.float32)

@@ -37,6 +37,7 @@ def _render(ivv, vol, sc, method, guess, flags=0):
 def test_rf_images_match_oracle(ivv, cfg, size):
     sc = scenes.config(cfg, width=size[0], height=size[1])
     sc.params.precision = scenes.PRECISION_FP32
+    sc.params.rf_tol = 1e-3          # 1e-3 of a pixel half width: image parity, not only pixel accuracy
     vol = ivv.volume_for(sc)
     ref = oracle.render(sc)
     for guess in (ivv.GUESS_CHORD, ivv.GUESS_CENTER):
@@ -48,9 +49,10 @@ def test_rf_images_match_oracle(ivv, cfg, size):
 def test_learned_guess_gains_over_plain_newton(ivv):
     sc = scenes.config(1, width=200, height=120)
     sc.params.precision = scenes.PRECISION_FP32
+    sc.params.rf_tol = 1e-3
     vol = ivv.volume_for(sc)
-    losses = vol.train_guess(samples_per_block=1 << 18, epochs=6, batch=8192, lr=3e-3, seed=3)
-    assert losses[0] < 2e-4
+    losses = vol.train_guess(samples_per_block=1 << 17, epochs=24, batch=2048, lr=3e-3, seed=3)
+    assert losses[0] < 1e-4
     ref = oracle.render(sc)
     iters = {}
     for guess in (ivv.GUESS_CENTER, ivv.GUESS_MLP, ivv.GUESS_CHORD):
