@@ -326,6 +326,17 @@ ivv_status ivv_train_guess(ivv_volume* vol, const ivv_guess_train_params* params
 ivv_status ivv_guess_points(ivv_volume* vol, int n, const float* g, const int* block_of, float* p_out,
                             void* stream);
 
+/* Inverse geometry map of world points (§5.1, Eq. 6 solved per point): g
+ * [n][4] device floats (x, y, z, ignored) lying in blocks block_of [n]
+ * (device int32); damped Newton with a halving line search from the initial
+ * guess `guess` (IVV_GUESS_CENTER or IVV_GUESS_MLP) until ||phi(p) - g|| <=
+ * tol (not below FP32 resolution).  p_out [n][4] device floats receives
+ * (p, ||phi(p) - g||); iters [n] device int32 (may be NULL) the Newton
+ * iterations used, or -1 - iterations where the tolerance was not reached.
+ * Enqueued on `stream`. */
+ivv_status ivv_invert_points(ivv_volume* vol, int n, const float* g, const int* block_of, int guess, float tol,
+                             float* p_out, int* iters, void* stream);
+
 /* One forward/backward pass of the training kernel (no update) on caller
  * samples of one block: x_hat [n][4] and p [n][4] device floats (normalised
  * inputs and targets).  grad (host, [IVV_GUESS_PARAMS]) and loss (host)

@@ -91,6 +91,7 @@ struct ivv_volume {
   double lo = 0, hi = 1;
   bool tf_set = false;
   ivv::DevStats* d_stats = nullptr;
+  int* d_count = nullptr;          // device copy of a point count (point location)
   void* own_ws = nullptr;
   size_t own_ws_bytes = 0;
   float* own_out = nullptr;
@@ -116,7 +117,7 @@ namespace {
 void free_volume(ivv_volume* v) {
   if (!v) return;
   void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_org64,
-                  v->d_face32, v->d_face64,
+                  v->d_count, v->d_face32, v->d_face64,
                   v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -386,7 +387,8 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     if (p.use_mlp_guess == IVV_GUESS_MLP)
       ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->num_sms, s);
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
-    ivv::launch_rf_newton(V, c32, (float)p.rf_tol, counters + 2, sg, sblk, sp, srho, v->d_stats, stats, v->num_sms, s);
+    ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,
+                          stats, v->num_sms, s);
     ivv::launch_rf_composite(tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act, counters, off,
                              (int)npix, (float)p.ds, tail_eps, total, sg, srho, (float4*)out, v->d_stats, stats,
                              v->num_sms, s);
@@ -501,7 +503,8 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
       (st = upload(&v->d_faces64, hv.faces64.data(), hv.faces64.size(), s)) != IVV_OK ||
       (st = upload<float>(&v->d_tf_r, nullptr, 256, s)) != IVV_OK ||
       (st = upload<float4>(&v->d_tf_rgba, nullptr, 256, s)) != IVV_OK ||
-      (st = upload<ivv::DevStats>(&v->d_stats, nullptr, 1, s)) != IVV_OK) {
+      (st = upload<ivv::DevStats>(&v->d_stats, nullptr, 1, s)) != IVV_OK ||
+      (st = upload<int>(&v->d_count, nullptr, 4, s)) != IVV_OK) {
     std::string m = g_err;
     free_volume(v);
     return fail(st, m);
@@ -825,6 +828,29 @@ ivv_status ivv_guess_points(ivv_volume* v, int n, const float* g, const int* blo
   if (n == 0) return IVV_OK;
   ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->num_sms,
                         (cudaStream_t)stream);
+  IVV_CUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+ivv_status ivv_invert_points(ivv_volume* v, int n, const float* g, const int* block_of, int guess, float tol,
+                             float* p_out, int* iters, void* stream) {
+  if (!v || n < 0 || (n > 0 && (!g || !block_of || !p_out))) return fail(IVV_ERR_INVALID_ARG, "bad argument");
+  if (guess != IVV_GUESS_CENTER && guess != IVV_GUESS_MLP) return fail(IVV_ERR_INVALID_ARG, "bad guess mode");
+  if (guess == IVV_GUESS_MLP && !v->guess_ready) return fail(IVV_ERR_INVALID_ARG, "the guess network is not trained");
+  if (!(tol > 0)) return fail(IVV_ERR_INVALID_ARG, "tol must be positive");
+  if (((uintptr_t)g) % 16 || ((uintptr_t)p_out) % 16) return fail(IVV_ERR_INVALID_ARG, "g and p_out must be 16-byte aligned");
+  if (n == 0) return IVV_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  IVV_CUDA(cudaMemcpyAsync(v->d_count, &n, sizeof(int), cudaMemcpyHostToDevice, s));
+  if (guess == IVV_GUESS_MLP)
+    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->num_sms, s);
+  else
+    ivv::launch_fill_center((float4*)p_out, n, s);
+  ivv::DevCamera<float> cam{};
+  cam.H = 1;
+  cam.ortho = 1;
+  ivv::launch_rf_newton(dev_volume(v), cam, 0.f, tol, v->d_count, (const float4*)g, block_of, (const float4*)p_out,
+                        nullptr, (float4*)p_out, iters, v->d_stats, false, v->num_sms, s);
   IVV_CUDA(cudaGetLastError());
   return IVV_OK;
 }

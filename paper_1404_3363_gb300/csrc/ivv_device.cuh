@@ -301,6 +301,7 @@ void launch_integrate(const DevVolume& V, const DevCamera<R>& cam, const DevTF& 
 void launch_eval_points(const DevVolume& V, int block, int n, const float* p, float* phi, float* jac,
                         float* rho, cudaStream_t s);
 
+void launch_fill_center(float4* p, int n, cudaStream_t s);
 void launch_rf_count(const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
                      const int* n_active, int npix, float ds, float tail_eps, int* cnt, int num_sms, cudaStream_t s);
 void launch_rf_scan(const int* cnt, const int* n_active, int npix, int* off, int* sums, int cap, int* total,
@@ -309,9 +310,9 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
                       const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                       float tail_eps, int guess, int cap, float4* sg, int* sblk, float4* sp, int num_sms,
                       cudaStream_t s);
-void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, const int* n_ptr,
-                      const float4* sg, const int* sblk, const float4* sp, float* srho, DevStats* st, bool stats,
-                      int num_sms, cudaStream_t s);
+void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
+                      const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
+                      DevStats* st, bool stats, int num_sms, cudaStream_t s);
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                          float tail_eps, int cap, const float4* sg, const float* srho, float4* out, DevStats* st,

@@ -181,11 +181,14 @@ __global__ void k_rf_expand(DevCamera<float> cam, const float4* __restrict__ pai
   }
 }
 
+// abs_tol > 0: fixed stopping tolerance (point location); otherwise the
+// pixel-accuracy rule of the camera.  p_out / it_out are optional.
 template <int P, bool STATS>
-__global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float> cam, float rf_tol,
+__global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float> cam, float rf_tol, float abs_tol,
                                                    const int* __restrict__ n_ptr, const float4* __restrict__ sg,
                                                    const int* __restrict__ sblk, const float4* __restrict__ sp,
-                                                   float* __restrict__ srho, DevStats* __restrict__ st) {
+                                                   float* __restrict__ srho, float4* __restrict__ p_out,
+                                                   int* __restrict__ it_out, DevStats* __restrict__ st) {
   const int n = *n_ptr;
   unsigned long long c_it = 0, c_ev = 0, c_fail = 0;
   // half width of a pixel per unit depth (perspective) or absolute (ortho)
@@ -194,11 +197,17 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
     const float4 g4 = sg[i];
     const float g[3] = {g4.x, g4.y, g4.z};
     const BlockInfo B = V.blocks[sblk[i]];
-    float depth = 1.f;
-    if (!cam.ortho)
-      depth = (g[0] - cam.eye[0]) * cam.f[0] + (g[1] - cam.eye[1]) * cam.f[1] + (g[2] - cam.eye[2]) * cam.f[2];
-    // stop at the pixel-accuracy tolerance, but not below FP32 resolution
-    const float tol = fmaxf(rf_tol * px_half * depth, 2e-7f * (fabsf(g[0]) + fabsf(g[1]) + fabsf(g[2]) + V.diag));
+    float tol;
+    if (abs_tol > 0.f) {
+      tol = abs_tol;
+    } else {
+      float depth = 1.f;
+      if (!cam.ortho)
+        depth = (g[0] - cam.eye[0]) * cam.f[0] + (g[1] - cam.eye[1]) * cam.f[1] + (g[2] - cam.eye[2]) * cam.f[2];
+      tol = rf_tol * px_half * depth;
+    }
+    // never below FP32 resolution of the coordinates
+    tol = fmaxf(tol, 2e-7f * (fabsf(g[0]) + fabsf(g[1]) + fabsf(g[2]) + V.diag));
     const float4 p4 = sp[i];
     float p[3] = {fminf(fmaxf(p4.x, 0.f), 1.f), fminf(fmaxf(p4.y, 0.f), 1.f), fminf(fmaxf(p4.z, 0.f), 1.f)};
     float phi[3], J[3][3], rc;
@@ -242,6 +251,8 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
       c_it += it;
       if (nF > tol) ++c_fail;
     }
+    if (p_out) p_out[i] = make_float4(p[0], p[1], p[2], nF);
+    if (it_out) it_out[i] = nF <= tol ? it : -1 - it;
     float rho = rc;
     if (V.mode != IVV_SCALAR_CP) {
       rho = det3<float>(J);
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
         rho /= sqrtf(f);
       }
     }
-    srho[i] = rho;
+    if (srho) srho[i] = rho;
   }
   if (STATS) {
 #pragma unroll
@@ -344,6 +355,17 @@ __global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __res
 
 }  // namespace
 
+namespace {
+__global__ void k_fill_center(float4* __restrict__ p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = make_float4(0.5f, 0.5f, 0.5f, 0.f);
+}
+}  // namespace
+
+void launch_fill_center(float4* p, int n, cudaStream_t s) {
+  if (n > 0) k_fill_center<<<(n + 255) / 256, 256, 0, s>>>(p, n);
+}
+
 void launch_rf_count(const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
                      const int* n_active, int npix, float ds, float tail_eps, int* cnt, int num_sms, cudaStream_t s) {
   k_rf_count<<<num_sms * 8, 256, 0, s>>>(pin, pout, pblk, pcnt, active, n_active, npix, ds, tail_eps, cnt);
@@ -365,17 +387,18 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
                                           guess, cap, sg, sblk, sp);
 }
 
-void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, const int* n_ptr,
-                      const float4* sg, const int* sblk, const float4* sp, float* srho, DevStats* st, bool stats,
-                      int num_sms, cudaStream_t s) {
+void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
+                      const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
+                      DevStats* st, bool stats, int num_sms, cudaStream_t s) {
   const int grid = num_sms * 16;
+#define IVV_RFN(PP, SS) \
+  k_rf_newton<PP, SS><<<grid, 128, 0, s>>>(V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, p_out, it_out, st)
   if (V.P == 2) {
-    if (stats) k_rf_newton<2, true><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
-    else k_rf_newton<2, false><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+    if (stats) IVV_RFN(2, true); else IVV_RFN(2, false);
   } else {
-    if (stats) k_rf_newton<3, true><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
-    else k_rf_newton<3, false><<<grid, 128, 0, s>>>(V, cam, rf_tol, n_ptr, sg, sblk, sp, srho, st);
+    if (stats) IVV_RFN(3, true); else IVV_RFN(3, false);
   }
+#undef IVV_RFN
 }
 
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,

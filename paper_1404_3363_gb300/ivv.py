@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
                                         C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int, vp, vp, vp]
     L.ivv_train_guess.argtypes = [vp, C.POINTER(GuessTrainParams), c_float_p, vp]
     L.ivv_guess_points.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.ivv_invert_points.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_float, vp, vp, vp]
     L.ivv_guess_loss_grad.argtypes = [vp, C.c_int, C.c_int, vp, vp, c_float_p, c_float_p, vp]
     L.ivv_get_guess_weights.argtypes = [vp, C.c_int, c_float_p, c_float_p, c_float_p]
     L.ivv_set_guess_weights.argtypes = [vp, C.c_int, c_float_p]
@@ -358,6 +359,19 @@ class Volume:
         _check(load().ivv_guess_points(self.h, g4.shape[0], C.c_void_p(g4.data_ptr()), C.c_void_p(block_of.data_ptr()),
                                        C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
         return out
+
+    def invert_points(self, g4, block_of, guess=0, tol=1e-5, stream=None):
+        """(p [n][4] with the final residual in column 3, iterations [n]) of the
+        batched Newton inversion from the chosen initial guess."""
+        import torch
+        g4 = g4.contiguous()
+        block_of = block_of.contiguous()
+        out = torch.empty_like(g4)
+        its = torch.empty(g4.shape[0], dtype=torch.int32, device=g4.device)
+        _check(load().ivv_invert_points(self.h, g4.shape[0], C.c_void_p(g4.data_ptr()), C.c_void_p(block_of.data_ptr()),
+                                        int(guess), float(tol), C.c_void_p(out.data_ptr()), C.c_void_p(its.data_ptr()),
+                                        C.c_void_p(_stream_ptr(stream))))
+        return out, its
 
     def guess_loss_grad(self, block, x4, p4, stream=None):
         """(loss, gradient) of the device training kernel on one batch."""
