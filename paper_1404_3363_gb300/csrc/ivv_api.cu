@@ -100,7 +100,7 @@ struct ivv_volume {
   cudaEvent_t ev[IVV_N_STAGES + 1] = {};
   bool timed = false;
   // learned initial guess
-  float* d_theta = nullptr;        // [n_blocks][kMlpParams]
+  float* d_theta = nullptr;        // [n_blocks][kMlpStride]
   float* d_adam_m = nullptr;
   float* d_adam_v = nullptr;
   __half* d_theta16 = nullptr;
@@ -543,7 +543,7 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
     v->norms.push_back(nm);
   }
   {
-    const size_t np = (size_t)n_blocks * ivv::kMlpParams;
+    const size_t np = (size_t)n_blocks * ivv::kMlpStride;
     if ((st = upload<float>(&v->d_theta, nullptr, np, s)) != IVV_OK ||
         (st = upload<float>(&v->d_adam_m, nullptr, np, s)) != IVV_OK ||
         (st = upload<float>(&v->d_adam_v, nullptr, np, s)) != IVV_OK ||
@@ -776,10 +776,10 @@ ivv_status ivv_train_guess(ivv_volume* v, const ivv_guess_train_params* in, floa
     for (int i = 0; i < ivv::kMlpH * ivv::kMlpH; ++i) th[ivv::kOffW2 + i] = (float)(nd(rng) * std::sqrt(2.0 / ivv::kMlpH));
     for (int i = 0; i < 3 * ivv::kMlpH; ++i) th[ivv::kOffW3 + i] = (float)(nd(rng) * std::sqrt(1.0 / ivv::kMlpH));
     for (int i = 0; i < 3; ++i) th[ivv::kOffB3 + i] = 0.5f;
-    float* tb = v->d_theta + (size_t)b * ivv::kMlpParams;
-    float* mb = v->d_adam_m + (size_t)b * ivv::kMlpParams;
-    float* vb = v->d_adam_v + (size_t)b * ivv::kMlpParams;
-    __half* hb = v->d_theta16 + (size_t)b * ivv::kMlpParams;
+    float* tb = v->d_theta + (size_t)b * ivv::kMlpStride;
+    float* mb = v->d_adam_m + (size_t)b * ivv::kMlpStride;
+    float* vb = v->d_adam_v + (size_t)b * ivv::kMlpStride;
+    __half* hb = v->d_theta16 + (size_t)b * ivv::kMlpStride;
     e = cudaMemcpyAsync(tb, th.data(), sizeof(float) * ivv::kMlpParams, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mb, 0, sizeof(float) * ivv::kMlpParams, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(vb, 0, sizeof(float) * ivv::kMlpParams, s);
@@ -867,7 +867,7 @@ ivv_status ivv_guess_loss_grad(ivv_volume* v, int block, int n, const float* x_h
   if (e == cudaSuccess) e = cudaMalloc(&dgrad, sizeof(float) * ivv::kMlpParams);
   if (e == cudaSuccess) e = cudaMalloc(&dloss, sizeof(float));
   if (e == cudaSuccess)
-    e = ivv::launch_mlp_fwd_bwd(v->d_theta + (size_t)block * ivv::kMlpParams, (const float4*)x_hat, (const float4*)p,
+    e = ivv::launch_mlp_fwd_bwd(v->d_theta + (size_t)block * ivv::kMlpStride, (const float4*)x_hat, (const float4*)p,
                                 n, 0, n, 1.f / n, partial, partial_loss, s);
   if (e == cudaSuccess) {
     ivv::launch_mlp_reduce(partial, partial_loss, ctas, dgrad, dloss, s);
@@ -886,7 +886,7 @@ ivv_status ivv_get_guess_weights(ivv_volume* v, int block, float* params, float*
   if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
   if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
   if (params)
-    IVV_CUDA(cudaMemcpy(params, v->d_theta + (size_t)block * ivv::kMlpParams, sizeof(float) * ivv::kMlpParams,
+    IVV_CUDA(cudaMemcpy(params, v->d_theta + (size_t)block * ivv::kMlpStride, sizeof(float) * ivv::kMlpParams,
                         cudaMemcpyDeviceToHost));
   for (int r = 0; r < 3; ++r) {
     if (c) c[r] = v->norms[block].c[r];
@@ -898,9 +898,9 @@ ivv_status ivv_get_guess_weights(ivv_volume* v, int block, float* params, float*
 ivv_status ivv_set_guess_weights(ivv_volume* v, int block, const float* params) {
   if (!v || !params) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
   if (block < 0 || block >= v->hv.n_blocks) return fail(IVV_ERR_INVALID_ARG, "block out of range");
-  float* tb = v->d_theta + (size_t)block * ivv::kMlpParams;
+  float* tb = v->d_theta + (size_t)block * ivv::kMlpStride;
   IVV_CUDA(cudaMemcpy(tb, params, sizeof(float) * ivv::kMlpParams, cudaMemcpyHostToDevice));
-  ivv::launch_mlp_to_half(tb, v->d_theta16 + (size_t)block * ivv::kMlpParams, ivv::kMlpParams, nullptr);
+  ivv::launch_mlp_to_half(tb, v->d_theta16 + (size_t)block * ivv::kMlpStride, ivv::kMlpParams, nullptr);
   IVV_CUDA(cudaDeviceSynchronize());
   v->guess_ready = true;
   return IVV_OK;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(32 * kInferWarps) k_mlp_infer(const __half* __
       if (!want) break;
       const int src = __ffs(want) - 1;
       todo_b = __shfl_sync(0xffffffffu, !done0 ? b0 : b1, src);
-      const __half* th = theta16_all + (size_t)todo_b * kMlpParams;
+      const __half* th = theta16_all + (size_t)todo_b * kMlpStride;
       const MlpNorm nm = norms[todo_b];
       float x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
       if (r0 < n) {

@@ -17,6 +17,11 @@ constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
 constexpr int kOffW3 = kOffB2 + kMlpH;
 constexpr int kOffB3 = kOffW3 + 3 * kMlpH;
 constexpr int kMlpParams = kOffB3 + 3;      // 4611
+// per-block stride of the parameter arrays on the device: a multiple of 8 so
+// every block's FP16 copy starts on a 16-byte boundary (the inference kernel
+// reads weight pairs as 32-bit words)
+constexpr int kMlpStride = (kMlpParams + 7) / 8 * 8;   // 4616
+static_assert(kMlpStride % 8 == 0 && kOffW2 % 2 == 0 && kOffW3 % 2 == 0, "FP16 weight pairs must stay word aligned");
 
 // Input normalisation of a block: g_hat_r = (g_r - c_r) * inv_h_r, mapping
 // the block's control-point box to [-1, 1]^3.
