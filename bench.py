@@ -165,6 +165,20 @@ def cpu_oracle_sample(scene, target_s=12.0, max_stride=64):
                       "%.2f s" % (nrows, stride, px, dt)}
 
 
+def aggregate_ranks(ms_local, pixels_per_rank, dist=None, device=None):
+    """Whole-job Mpixels/s: every rank renders its own frame (replicas, weak
+    scaling); the job time is the slowest rank's.  Returns (value, ms_max)."""
+    ms = float(ms_local)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device or "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * pixels_per_rank / (ms * 1e-3) / 1e6, ms
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -276,12 +290,9 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    value, ms = aggregate_ranks(ms, W * H, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * W * H / (ms * 1e-3) / 1e6
     k5_ms = stage_sum["integrate"] / args.steps
     k2_ms = stage_sum["intersect"] / args.steps
 
@@ -294,10 +305,7 @@ def run_ours(args):
     for _ in range(e2e_n):
         vol.render_to_host(sc.camera, sc.params, W, H, host)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_n
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value, e2e_ms = aggregate_ranks(e2e_ms, W * H, dist, "cuda")
 
     props = torch.cuda.get_device_properties(local)
     peaks = _peaks()
@@ -332,7 +340,7 @@ def run_ours(args):
             "stages_ms": {k: v / args.steps for k, v in stage_sum.items()},
             "wall_s_timed_loop": t_wall,
             "gpu_launches": 4 * args.steps,
-            "e2e": {"value": world * W * H / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+            "e2e": {"value": e2e_value, "unit": UNIT,
                     "ms_per_frame": e2e_ms,
                     "h2d_bytes_per_step": ctypes.sizeof(ivv.Camera) + ctypes.sizeof(ivv.RenderParams),
                     "d2h_bytes_per_step": W * H * 16},
