@@ -29,6 +29,22 @@ METRIC = "Mpixels/s & ms/frame at 1920x1080 vs plain FP32, at <=1e-3 max RGBA er
 UNIT = "Mpixels/s"
 WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x1080 perspective, FP32"
 
+# --workload: the default is the headline frame above; the others are the
+# remaining workloads of the method, each printed as its own line.
+WORKLOADS = {
+    "bar1080": (1, 0, WORKLOAD),
+    "beam1080": (2, 1, "bent beam, 16 cubic blocks 6x6x12 cp (C0), Gaussian-sum scalar, 1920x1080 perspective, "
+                       "mixed precision"),
+    "beam1080-fp32": (2, 0, "bent beam, 16 cubic blocks 6x6x12 cp (C0), Gaussian-sum scalar, 1920x1080 "
+                            "perspective, FP32"),
+    "backstep4k": (4, 1, "backward-facing step, 3 quadratic/cubic blocks 64x16x16 cp, shear-layer scalar, "
+                         "64-knot TF, 3840x2160, rk_tol 1e-6, mixed precision"),
+    "backstep4k-fp32": (4, 0, "backward-facing step, 3 quadratic/cubic blocks 64x16x16 cp, shear-layer scalar, "
+                              "64-knot TF, 3840x2160, rk_tol 1e-6, FP32"),
+    "batch64": (None, 0, "64 requests over the twisted cube, twisted bar and bent beam, sizes uniform over "
+                         "{256,512,768,1024}^2, seeded cameras and TFs, FP32, one CUDA graph"),
+}
+
 # Algorithmic FP32 flops per unit (cubic elements):
 # integrator (K5)
 F_RHS = 1283      # one W(p): 576-FMA sum-factorised phi+J, Bernstein basis, V, 3x3 adjugate solve
@@ -140,7 +156,7 @@ def _ncu_traffic(kernel):
         return None
 
 
-def cpu_oracle_sample(scene, target_s=12.0, max_stride=64):
+def cpu_oracle_sample(scene, target_s=12.0, max_stride=64, label="1920x1080 frame"):
     """Oracle Mpix/s on evenly spaced rows of the frame (rows at stride s,
     halving s until one sample takes >= target_s / 3)."""
     import oracle
@@ -161,8 +177,8 @@ def cpu_oracle_sample(scene, target_s=12.0, max_stride=64):
         stride //= 2
     px, dt, stride, nrows = best
     return {"value": px / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d rows at stride %d of the 1920x1080 frame (%d pixels), FP64 per-sample Newton, "
-                      "%.2f s" % (nrows, stride, px, dt)}
+            "sample": "%d rows at stride %d of the %s (%d pixels), FP64 per-sample Newton, "
+                      "%.2f s" % (nrows, stride, label, px, dt)}
 
 
 def aggregate_ranks(ms_local, pixels_per_rank, dist=None, device=None):
@@ -234,7 +250,9 @@ def run_ours(args):
     libbuild.build()
     from paper_1404_3363_gb300 import ivv, scenes
 
-    sc = scenes.config(1)
+    cfg, prec, workload = WORKLOADS[args.workload]
+    sc = scenes.config(cfg)
+    sc.params.precision = prec
     W, H = sc.width, sc.height
     stream = torch.cuda.current_stream()
     vol = ivv.volume_for(sc)
@@ -325,15 +343,15 @@ def run_ours(args):
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = cpu_oracle_sample(sc)
+        cpu_base = cpu_oracle_sample(sc, label="%dx%d frame" % (W, H))
 
     if rank == 0:
         import ctypes
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": W, "height": H, "rk_tol": sc.params.rk_tol,
+            "vs_baseline": None, "dtype": "f32" if prec == 0 else "f32+f64", "data": "synthetic",
+            "config": {"workload": workload, "width": W, "height": H, "rk_tol": sc.params.rk_tol,
                        "ds": sc.params.ds, "supersample_k": sc.params.supersample_k,
                        "l2": "flushed between steps (512 MiB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -359,6 +377,123 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """The 64-request batch: one CUDA graph per step (K0, K2, K4, K5 launches
+    over all requests), launch shapes from the autotuner's cache."""
+    import numpy as np
+    import torch
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1404_3363_gb300 import autotune, build as libbuild
+    libbuild.build()
+    from paper_1404_3363_gb300 import ivv, scenes
+
+    vols, reqs = scenes.batch_requests()
+    gpu = [ivv.volume_for(v) for v in vols]
+    items = [(gpu[q.volume], q.camera, q.width, q.height, q.tf) for q in reqs]
+    b = ivv.Batch(items)
+    npix = b.info()["n_pixels"]
+    tuning, tune_ms, tune_src = autotune.tuned(b, items)
+    stream = torch.cuda.current_stream()
+
+    b.reset_stats()
+    b.render(flags=ivv.FLAG_STATS)
+    st = b.stats()
+    flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
+                + st["samples"] * F_SAMPLE)
+    b.render(flags=ivv.FLAG_TIMING)
+    stages = b.stage_times()
+
+    max_err = None
+    if rank == 0 and not args.no_parity:
+        import oracle
+        b.render()
+        torch.cuda.synchronize()
+        orc = [oracle.OracleVolume(v.blocks, v.scalar_mode) for v in vols]
+        rng = np.random.default_rng(7)
+        max_err = 0.0
+        for q, out in list(zip(reqs, b.outputs))[::4]:
+            img = out.cpu().numpy()
+            cov = np.argwhere(img[..., 3] > 0)
+            if not len(cov):
+                continue
+            y, x = cov[rng.integers(len(cov))]
+            sc = vols[q.volume]
+            sc = type(sc)(sc.name, sc.blocks, sc.scalar_mode, q.tf, q.camera, q.width, q.height,
+                          scenes.RenderParams())
+            ref = oracle.render(sc, orc[q.volume], window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
+            max_err = max(max_err, float(np.abs(img[y, x].astype(np.float64) - ref).max()))
+
+    for _ in range(args.warmup):
+        b.render()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(_gpu_id_for_smi(local))
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        b.render()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = sum(x.elapsed_time(y) for x, y in ev) / args.steps
+    value, ms = aggregate_ranks(ms, npix, dist, "cuda")
+
+    # end to end: graph replay plus every request's image copied to pinned host memory
+    hosts = [torch.empty(o.shape, dtype=torch.float32, pin_memory=True) for o in b.outputs]
+    e2e_n = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        b.render()
+        for h_, o in zip(hosts, b.outputs):
+            h_.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_n
+    e2e_value, e2e_ms = aggregate_ranks(e2e_ms, npix, dist, "cuda")
+
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    peak_fp32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    k5_ms = stages["integrate"]
+    achieved = flops_k5 / (k5_ms * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch64"][2], "requests": len(reqs), "pixels": npix,
+                       "tuning": tuning, "tuning_source": tune_src, "autotune_ms": tune_ms,
+                       "l2": "inputs larger than L2 (%.1f GB workspace)" % (b.info()["workspace_bytes"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "stages_ms_timed_render": stages,
+            "gpu_launches": 4 * args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_batch": e2e_ms, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": npix * 16},
+            "roofline": {"bound": "alu", "kernel": "k5_integrate (batched)", "achieved": achieved,
+                         "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                         "flops_per_launch": flops_k5, "ms_per_launch": k5_ms},
+            "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
+                                        "fragments")},
+            "parity_max_rgba_err_sampled": max_err,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,11 +503,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--ref-stride", type=int, default=96)
+    ap.add_argument("--workload", default="bar1080", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -356,6 +356,99 @@ ivv_status ivv_reset_stats(ivv_volume* vol);
 ivv_status ivv_volume_info(const ivv_volume* vol, int* n_blocks, int* n_elements, int* n_faces,
                            int* degree);
 
+/* ---------------------------------------------------------------------
+ * Batched rendering: many views of several volumes, of uneven image sizes,
+ * in one launch per stage, replayed from a captured CUDA graph.
+ *
+ * At creation every distinct volume of the batch is copied into one device
+ * pool (blocks, Bezier elements, face patches and breakpoints concatenated
+ * with rebased offsets), so a ray of any request finds its geometry through
+ * the pool's block table alone.  The stages then run once over the whole
+ * batch: K0 over every (request, face), K2 over every screen tile of every
+ * request, K4 over every pixel, and the persistent K5 over one work queue
+ * that spans all requests, so rays of short and long requests share the
+ * machine until the last one finishes.  The library owns the workspace
+ * (about 640 bytes of fragment slots and 600 bytes of pair slots per pixel).
+ * The volumes may be destroyed after creation; all of them must share the
+ * common degree P (IVV_ERR_UNSUPPORTED otherwise). */
+typedef struct ivv_batch ivv_batch;       /* opaque, library-owned */
+
+#define IVV_BATCH_TF_MAX 64               /* knots of a per-request TF     */
+#define IVV_BATCH_MAX_REQUESTS 4096
+
+/* One render request.
+ * volume      a created volume; its data is copied at ivv_batch_create
+ * camera      see ivv_camera; may be changed later by ivv_batch_set_camera
+ * width, height  image size; the whole image is rendered
+ * tf_n, tf_r, tf_rgba, tf_sigma, scalar_lo, scalar_hi
+ *             the request's transfer function with the meaning of
+ *             ivv_set_transfer_function (tf_n <= IVV_BATCH_TF_MAX knots);
+ *             tf_r == NULL takes the volume's current transfer function and
+ *             range, scalar_lo >= scalar_hi the volume's default range
+ * out_rgba    device pointer, caller-owned, [height][width][4] float32,
+ *             16-byte aligned; written by every ivv_batch_render */
+typedef struct {
+  const ivv_volume* volume;
+  ivv_camera camera;
+  int width, height;
+  int tf_n;
+  const float* tf_r;
+  const float* tf_rgba;
+  float tf_sigma;
+  double scalar_lo, scalar_hi;
+  float* out_rgba;
+} ivv_request;
+
+/* Launch shapes chosen by the autotuner.
+ * tile_w, tile_h   K2 screen tile (one CTA): 8x8, 16x8 or 16x16 [16x8]
+ * k5_ctas_per_sm   resident CTAs of the persistent K5 per SM, 1..4 [4]
+ * step_samples     the step batch: the longest RK step, in sample distances
+ *                  (samples inside a step come from dense output), one of
+ *                  4, 8, 16 [8] */
+typedef struct {
+  int tile_w, tile_h;
+  int k5_ctas_per_sm;
+  int step_samples;
+} ivv_batch_tuning;
+
+/* Build a batch of n requests (1..IVV_BATCH_MAX_REQUESTS) rendered with the
+ * shared parameters `params` (NULL: defaults; method ODE, precision FP32 or
+ * MIXED, no window; ds <= 0 gives each request its volume's diag/128).
+ * Uploads the pool and the request table on `stream` and synchronises it. */
+ivv_status ivv_batch_create(const ivv_request* requests, int n, const ivv_render_params* params, void* stream,
+                            ivv_batch** out);
+
+/* Render every request of the batch on `stream`.  flags = 0 replays the
+ * batch's CUDA graph (captured on the first call and again after a tuning
+ * change); IVV_FLAG_STATS and/or IVV_FLAG_TIMING launch the same stages
+ * directly, with counters (ivv_batch_get_stats) or per-stage events
+ * (ivv_batch_get_stage_times). */
+ivv_status ivv_batch_render(ivv_batch* batch, int flags, void* stream);
+
+/* Replace the camera of request i (enqueued on `stream`; the graph reads the
+ * request table from device memory, so no re-capture is needed). */
+ivv_status ivv_batch_set_camera(ivv_batch* batch, int i, const ivv_camera* camera, void* stream);
+
+ivv_status ivv_batch_set_tuning(ivv_batch* batch, const ivv_batch_tuning* tuning);
+ivv_status ivv_batch_get_tuning(const ivv_batch* batch, ivv_batch_tuning* tuning);
+
+/* Time the candidate launch shapes on this batch (reps timed renders each,
+ * after one warm-up, CUDA events on `stream`): the K2 tile shape by the
+ * surface stage's time, then the K5 CTAs per SM and step batch by the
+ * integration stage's time.  Applies and returns the fastest; *best_ms is the
+ * frame time with it.  Synchronises `stream`. */
+ivv_status ivv_batch_autotune(ivv_batch* batch, int reps, ivv_batch_tuning* best, float* best_ms, void* stream);
+
+/* Counters of the batch (see ivv_stats); synchronises the last stream. */
+ivv_status ivv_batch_get_stats(ivv_batch* batch, ivv_stats* out);
+ivv_status ivv_batch_reset_stats(ivv_batch* batch);
+/* Stage times of the last IVV_FLAG_TIMING render, as ivv_get_stage_times. */
+ivv_status ivv_batch_get_stage_times(ivv_batch* batch, float* ms);
+/* Requests, total pixels, library workspace bytes, whether a graph exists. */
+ivv_status ivv_batch_info(const ivv_batch* batch, int* n_requests, long long* n_pixels, size_t* workspace_bytes,
+                          int* graph_ready);
+void ivv_batch_destroy(ivv_batch* batch);
+
 const char* ivv_last_error(void);
 void ivv_destroy_volume(ivv_volume* vol);
 

@@ -295,6 +295,7 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
     B.elem_off = hv.n_elems();
     B.tau_det = 0.f;
     B.uniform = 0;
+    B.mode = mode;
     for (int k = 0; k < 3; ++k) {
       bool uni = true;
       for (int i = 0; i <= B.nseg[k]; ++i)

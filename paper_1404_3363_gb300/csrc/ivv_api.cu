@@ -12,6 +12,7 @@
 #include "ivv_device.cuh"
 #include "ivv_internal.h"
 #include "mlp.cuh"
+#include "volume.h"
 #include <random>
 
 namespace ivv {
@@ -22,6 +23,7 @@ void launch_integrate_p(const DevVolume& V, const DevCamera<float>* cam32, const
                         int* queue_head, float4* out, DevStats* st, int num_sms, cudaStream_t s);
 void launch_export_pairs(int npix, int max_pairs, bool fp64, const void* pin, const void* pout, const int* pblk,
                          const int* pcnt, int* out_count, float* out_pairs, int* out_block, cudaStream_t s);
+void stats_to_public(const DevStats& d, ivv_stats* out);
 }  // namespace ivv
 
 namespace {
@@ -69,48 +71,6 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
 
 }  // namespace
 
-struct ivv_volume {
-  ivv::HostVolume hv;
-  int device = 0;
-  int num_sms = 1;
-  ivv::BlockInfo* d_blocks = nullptr;
-  float* d_brk32 = nullptr;
-  double* d_brk64 = nullptr;
-  float4* d_elem32 = nullptr;
-  ivv::Dbl4* d_elem64 = nullptr;
-  float4* d_org32 = nullptr;
-  ivv::Dbl4* d_org64 = nullptr;
-  float4* d_face32 = nullptr;
-  ivv::Dbl4* d_face64 = nullptr;
-  ivv::FaceMeta* d_faces = nullptr;
-  ivv::FaceMeta64* d_faces64 = nullptr;
-  float* d_tf_r = nullptr;
-  float4* d_tf_rgba = nullptr;
-  int tf_n = 0;
-  float sigma = 1.f;
-  double lo = 0, hi = 1;
-  bool tf_set = false;
-  ivv::DevStats* d_stats = nullptr;
-  int* d_count = nullptr;          // device copy of a point count (point location)
-  void* own_ws = nullptr;
-  size_t own_ws_bytes = 0;
-  float* own_out = nullptr;
-  size_t own_out_bytes = 0;
-  cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[IVV_N_STAGES + 1] = {};
-  bool timed = false;
-  // learned initial guess
-  float* d_theta = nullptr;        // [n_blocks][kMlpStride]
-  float* d_adam_m = nullptr;
-  float* d_adam_v = nullptr;
-  __half* d_theta16 = nullptr;
-  ivv::MlpNorm* d_norms = nullptr;
-  std::vector<ivv::MlpNorm> norms;
-  bool guess_ready = false;
-  // RF sample buffers (grown on demand)
-  void* rf_buf = nullptr;
-  size_t rf_bytes = 0;
-};
 
 namespace {
 
@@ -584,6 +544,8 @@ ivv_status ivv_set_transfer_function(ivv_volume* v, int n, const float* r, const
   if (e == cudaSuccess) e = cudaMemcpy(v->d_tf_rgba, rgba, sizeof(float4) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "transfer function upload");
   v->tf_n = n;
+  v->tf_r_host.assign(r, r + n);
+  v->tf_rgba_host.assign(rgba, rgba + 4 * n);
   v->sigma = sigma;
   if (std::isfinite(lo) && std::isfinite(hi) && hi > lo) {
     v->lo = lo;
@@ -953,6 +915,14 @@ ivv_status ivv_get_stats(ivv_volume* v, ivv_stats* out) {
   IVV_CUDA(cudaStreamSynchronize(v->last_stream));
   ivv::DevStats d;
   IVV_CUDA(cudaMemcpy(&d, v->d_stats, sizeof(d), cudaMemcpyDeviceToHost));
+  ivv::stats_to_public(d, out);
+  return IVV_OK;
+}
+
+}  // extern "C"
+
+namespace ivv {
+void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->rays = d.rays;
   out->pairs = d.pairs;
   out->fragments = d.fragments;
@@ -972,8 +942,10 @@ ivv_status ivv_get_stats(ivv_volume* v, ivv_stats* out) {
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;
-  return IVV_OK;
 }
+}  // namespace ivv
+
+extern "C" {
 
 ivv_status ivv_reset_stats(ivv_volume* v) {
   if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");

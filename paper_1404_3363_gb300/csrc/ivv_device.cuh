@@ -262,6 +262,50 @@ __device__ __forceinline__ float4 tf_eval(const float* __restrict__ r, const flo
   return make_float4(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z), a.w + t * (b.w - a.w));
 }
 
+// ------------------------------------------------------------- batches
+// One request of a batch.  The batch's pixels are numbered request after
+// request: request rq owns pixels pix0[rq] .. pix0[rq+1]-1 (row-major within
+// its image); its K2 tiles (of the tuned tile shape) are tile0[rq] ..
+// tile0[rq+1]-1, row-major over the image; its volume's faces are face0 .. face0 + n_faces - 1 of the batch's pool and their
+// screen boxes for this camera start at box0.
+struct DevRequest {
+  DevCamera<float> cam;
+  DevCamera<double> cam64;
+  int face0, n_faces, box0;
+  float diag;          // control-point bbox diagonal of the volume
+  float ds;            // sample distance
+  float4* out;         // caller-owned RGBA image
+};
+
+// The request's transfer function; seg as in tf_eval.
+constexpr int kBatchTfMax = IVV_BATCH_TF_MAX;
+struct DevTFSlot {
+  float r[kBatchTfMax];
+  float4 rgba[kBatchTfMax];
+  unsigned char seg[kTfTable];
+  int n;
+  float sigma, lo, inv_range;
+};
+
+struct BatchArgs {
+  const DevRequest* req;   // [nreq]
+  const int* pix0;         // [nreq + 1] first pixel of each request, then the total
+  const int* tile0;        // [nreq + 1] first K2 tile of each request, then the total
+  const DevTFSlot* tf;     // [nreq]
+  int nreq;
+};
+
+// The request rq with first[rq] <= x < first[rq + 1] (first ascending).
+__device__ __forceinline__ int batch_find(const int* __restrict__ first, int nreq, int x) {
+  int lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int batch_request(const BatchArgs& ba, int pix) { return batch_find(ba.pix0, ba.nreq, pix); }
+
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
   if (v > 0.f) atomicMax(addr, __float_as_uint(v));
 }
@@ -297,6 +341,20 @@ void launch_integrate(const DevVolume& V, const DevCamera<R>& cam, const DevTF& 
                       const typename Vec4T<R>::type* pair_out, const int* pair_block, const int* pair_count,
                       const int* active, const int* n_active, int* queue_head, float4* out_rgba, DevStats* st,
                       int num_sms, cudaStream_t s);
+
+void launch_batch_pair(const BatchArgs& ba, int npix, const float4* frag_tp, const unsigned* frag_meta,
+                       const int* frag_count, float4* pair_in, float4* pair_out, int* pair_block, int* pair_count,
+                       int* active, int* n_active, DevStats* st, cudaStream_t s);
+void launch_batch_face_project(const DevVolume& V, const BatchArgs& ba, int max_faces, int4* boxes, cudaStream_t s);
+// tile_w x tile_h in {8x8, 16x8, 16x16}; returns false for another shape.
+bool launch_batch_intersect(const DevVolume& V, const BatchArgs& ba, int tiles, int tile_w, int tile_h, bool mixed,
+                            bool stats, const int4* boxes, float4* frag_tp, unsigned* frag_meta, int* frag_count,
+                            size_t stride, DevStats* st, cudaStream_t s);
+void launch_batch_integrate(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a, bool mixed, bool stats,
+                            const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
+                            const int* active, const int* n_active, int* queue_head, DevStats* st, int grid,
+                            cudaStream_t s);
+int batch_integrate_max_ctas_per_sm(int P, bool mixed, bool stats);
 
 void launch_eval_points(const DevVolume& V, int block, int n, const float* p, float* phi, float* jac,
                         float* rho, cudaStream_t s);

@@ -43,6 +43,7 @@ struct BlockInfo {
   int elem_off;       // first Bezier element of the block
   float tau_det;      // |det J| below which MIXED precision solves in FP64
   int uniform;        // bit d set: breakpoints of direction d are i / nseg[d]
+  int mode;           // IVV_SCALAR_* of the block's volume
 };
 
 // Host image of a prepared volume (see host_prep.cpp).

@@ -105,6 +105,15 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
   }
 }
 
+// Pixel-accuracy error Delta P (Eq. 5) of the world point phi for pixel
+// (xw, yw) of the window of cam: twice the larger screen offset, in pixels.
+template <typename R, typename RC>
+__device__ __forceinline__ float pixel_error(const DevCamera<RC>& cam, const R phi[3], int xw, int yw) {
+  RC sx, sy, ph[3] = {RC(phi[0]), RC(phi[1]), RC(phi[2])};
+  project<RC>(cam, ph, sx, sy);
+  return 2.f * (float)fmax(fabs(sx - RC(cam.x0 + xw)), fabs(sy - RC(cam.y0 + yw)));
+}
+
 // One lane's position in the integration of its current pixel.
 //   stage 0: start of a pair (evaluate W and rho at p_in);
 //   stages 1..3: the three new right-hand sides of a Bogacki-Shampine step
@@ -112,8 +121,14 @@ __device__ __forceinline__ void composite_interval(const float* s_r, const float
 //   fall inside it are visited in order:
 //   stage 4: rho at the dense-output point p(s_j) (cubic Hermite through the
 //   step's end points and slopes, third order like the pair itself).
-template <int P, typename R, bool MIXED, bool STATS>
+//
+// BATCH: the queue holds pixels of every request of a batch (BatchArgs); a
+// lane looks up its pixel's request when it takes the pixel and from then on
+// uses that request's camera, sample distance, transfer function slot and
+// image; the block table of the batch's pool carries each block's scalar mode.
+template <int P, typename R, bool MIXED, bool STATS, bool BATCH = false>
 __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
+                                                       BatchArgs ba,
                                                        const typename Vec4T<R>::type* __restrict__ pair_in,
                                                        const typename Vec4T<R>::type* __restrict__ pair_out,
                                                        const int* __restrict__ pair_block,
@@ -125,25 +140,29 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
   __shared__ unsigned char s_seg[kTfTable];
-  for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
-    s_r[i] = tf.r[i];
-    s_rgba[i] = tf.rgba[i];
+  if constexpr (!BATCH) {
+    for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
+      s_r[i] = tf.r[i];
+      s_rgba[i] = tf.rgba[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
+      const float x = (float)i / (float)kTfTable;
+      int k = 0;
+      while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
+      s_seg[i] = (unsigned char)k;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
-    const float x = (float)i / (float)kTfTable;
-    int k = 0;
-    while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
-    s_seg[i] = (unsigned char)k;
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   const int npix = args.npix;
-  const R ds = R(args.ds), tol = R(args.rk_tol), cc = R(args.c), early = R(args.early_alpha);
-  const R tail_eps = R(1e-12) * R(V.diag);
-  const R hmin = R(1e-7) * ds;
-  const R hmax = R(args.max_step_samples) * ds;
+  const R tol = R(args.rk_tol), cc = R(args.c), early = R(args.early_alpha);
+  R ds = R(args.ds);
+  R tail_eps = R(1e-12) * R(V.diag);
+  R hmin = R(1e-7) * ds;
+  R hmax = R(args.max_step_samples) * ds;
+  int rq = 0;             // BATCH: request of the lane's pixel
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
   float max_dp = 0.f;
 
@@ -167,8 +186,20 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         const int item = base + __popc(need & ((1u << lane) - 1u));
         if (item < nact) {
           pix = __ldg(active + item);
-          const int xw = pix % cam.w, yw = pix / cam.w;
-          make_ray<R>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
+          if constexpr (BATCH) {
+            rq = batch_request(ba, pix);
+            const DevRequest& rr = ba.req[rq];
+            const int loc = pix - __ldg(ba.pix0 + rq);
+            const int xw = loc % rr.cam.w, yw = loc / rr.cam.w;
+            make_ray<R>(rr.cam, rr.cam.x0 + xw, rr.cam.y0 + yw, o, d);
+            ds = R(rr.ds);
+            tail_eps = R(1e-12) * R(rr.diag);
+            hmin = R(1e-7) * ds;
+            hmax = R(args.max_step_samples) * ds;
+          } else {
+            const int xw = pix % cam.w, yw = pix / cam.w;
+            make_ray<R>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
+          }
           acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
           np = __ldg(pair_count + pix);
           q = -1;
@@ -205,7 +236,11 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         found = true;
       }
       if (!found) {
-        out[pix] = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
+        const float4 res = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
+        if constexpr (BATCH)
+          ba.req[rq].out[pix - __ldg(ba.pix0 + rq)] = res;
+        else
+          out[pix] = res;
         pix = -1;
         live = false;
       }
@@ -239,7 +274,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     }
     // ---- the one right-hand side of this iteration (converged across lanes)
     R W[3], rho, phi[3];
-    rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
+    rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
     if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
@@ -313,13 +348,27 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         } else {
           break;                       // needs a dense-output evaluation
         }
-        composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rj, s_t - s_last, acc);
+        if constexpr (BATCH) {
+          const DevTFSlot& ts = ba.tf[rq];
+          DevTF t2;
+          t2.n = ts.n;
+          t2.sigma = ts.sigma;
+          t2.lo = ts.lo;
+          t2.inv_range = ts.inv_range;
+          composite_interval<R>(ts.r, ts.rgba, ts.seg, t2, args.K, rho_prev, rj, s_t - s_last, acc);
+        } else {
+          composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rj, s_t - s_last, acc);
+        }
         if (STATS) {
           ++c_samp;
-          R sx, sy;
-          project<R>(cam, phi, sx, sy);
-          const int xw = pix % cam.w, yw = pix / cam.w;
-          const float dp = 2.f * (float)fmax(fabs(sx - R(cam.x0 + xw)), fabs(sy - R(cam.y0 + yw)));
+          float dp;
+          if constexpr (BATCH) {
+            const DevCamera<float>& cm = ba.req[rq].cam;
+            const int loc = pix - __ldg(ba.pix0 + rq);
+            dp = pixel_error<R>(cm, phi, loc % cm.w, loc / cm.w);
+          } else {
+            dp = pixel_error<R>(cam, phi, pix % cam.w, pix / cam.w);
+          }
           max_dp = fmaxf(max_dp, dp);
         }
         rho_prev = rj;
@@ -402,7 +451,8 @@ void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, con
   int grid = num_sms * blocks_per_sm;
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
-  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, pin, pout, pblk, pcnt, active, n_active,
+  BatchArgs none{};
+  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, pin, pout, pblk, pcnt, active, n_active,
                                                          queue_head, out, st);
 }
 

@@ -17,52 +17,54 @@ namespace ivv {
 
 namespace {
 
+// Sorting and pairing of the fragments of pixel `pix` (slot index
+// slot * stride + pix); returns the number of pairs written.  A pixel
+// without pairs gets a zero RGBA in *zero_out (if not NULL).
 template <typename R>
-__global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typename Vec4T<R>::type* __restrict__ frag_tp,
-                                               const unsigned* __restrict__ frag_meta,
-                                               const int* __restrict__ frag_count,
-                                               typename Vec4T<R>::type* __restrict__ pair_in,
-                                               typename Vec4T<R>::type* __restrict__ pair_out,
-                                               int* __restrict__ pair_block, int* __restrict__ pair_count,
-                                               int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
-                                               float4* __restrict__ out_rgba, DevStats* __restrict__ st) {
+__device__ __forceinline__ int pair_pixel(size_t pix, size_t stride, R tau_dup,
+                                          const typename Vec4T<R>::type* __restrict__ frag_tp,
+                                          const unsigned* __restrict__ frag_meta, const int* __restrict__ frag_count,
+                                          typename Vec4T<R>::type* __restrict__ pair_in,
+                                          typename Vec4T<R>::type* __restrict__ pair_out, int* __restrict__ pair_block,
+                                          int* __restrict__ pair_count, int max_pairs, float4* zero_out,
+                                          unsigned& um, unsigned& pov) {
   typedef typename Vec4T<R>::type V4;
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  int np = 0;
-  unsigned um = 0, pov = 0;
-  if (pix < npix) {
-    int n = frag_count[pix];
-    n = n < kMaxFrags ? n : kMaxFrags;
-    R t[kMaxFrags], pp[kMaxFrags][3];
-    unsigned m[kMaxFrags];
-    for (int i = 0; i < n; ++i) {
-      const V4 f = frag_tp[(size_t)i * npix + pix];
-      t[i] = f.x;
-      pp[i][0] = f.y;
-      pp[i][1] = f.z;
-      pp[i][2] = f.w;
-      m[i] = frag_meta[(size_t)i * npix + pix];
-    }
-    int in_idx[kMaxPairs], out_idx[kMaxPairs];
-    np = pair_fragments<R>(n, t, m, pp, tau_dup, max_pairs, in_idx, out_idx, um, pov);
-    for (int q = 0; q < np; ++q) {
-      const size_t o = (size_t)q * npix + pix;
-      pair_in[o] = frag_tp[(size_t)in_idx[q] * npix + pix];
-      pair_out[o] = frag_tp[(size_t)out_idx[q] * npix + pix];
-      pair_block[o] = (int)(m[in_idx[q]] >> 4);
-    }
-    pair_count[pix] = np;
-    if (np == 0 && out_rgba) out_rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int n = frag_count[pix];
+  n = n < kMaxFrags ? n : kMaxFrags;
+  R t[kMaxFrags], pp[kMaxFrags][3];
+  unsigned m[kMaxFrags];
+  for (int i = 0; i < n; ++i) {
+    const V4 f = frag_tp[(size_t)i * stride + pix];
+    t[i] = f.x;
+    pp[i][0] = f.y;
+    pp[i][1] = f.z;
+    pp[i][2] = f.w;
+    m[i] = frag_meta[(size_t)i * stride + pix];
   }
-  // warp-aggregated append of active pixels to the work queue
+  int in_idx[kMaxPairs], out_idx[kMaxPairs];
+  const int np = pair_fragments<R>(n, t, m, pp, tau_dup, max_pairs, in_idx, out_idx, um, pov);
+  for (int q = 0; q < np; ++q) {
+    const size_t o = (size_t)q * stride + pix;
+    pair_in[o] = frag_tp[(size_t)in_idx[q] * stride + pix];
+    pair_out[o] = frag_tp[(size_t)out_idx[q] * stride + pix];
+    pair_block[o] = (int)(m[in_idx[q]] >> 4);
+  }
+  pair_count[pix] = np;
+  if (np == 0 && zero_out) *zero_out = make_float4(0.f, 0.f, 0.f, 0.f);
+  return np;
+}
+
+// Warp-aggregated append of the active pixels to the integrator's queue and
+// the counters that every render keeps.
+__device__ __forceinline__ void pair_epilogue(int pix, int np, unsigned um, unsigned pov, int* __restrict__ active,
+                                              int* __restrict__ n_active, DevStats* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
   const bool act = np > 0;
   const unsigned bal = __ballot_sync(0xffffffffu, act);
   int base = 0;
   if (lane == 0 && bal) base = atomicAdd(n_active, __popc(bal));
   base = __shfl_sync(0xffffffffu, base, 0);
   if (act) active[base + __popc(bal & ((1u << lane) - 1u))] = pix;
-  // counters that are always kept
   unsigned long long cu = um, cp = pov, cr = act ? 1 : 0, cpairs = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -79,6 +81,46 @@ __global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typena
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typename Vec4T<R>::type* __restrict__ frag_tp,
+                                               const unsigned* __restrict__ frag_meta,
+                                               const int* __restrict__ frag_count,
+                                               typename Vec4T<R>::type* __restrict__ pair_in,
+                                               typename Vec4T<R>::type* __restrict__ pair_out,
+                                               int* __restrict__ pair_block, int* __restrict__ pair_count,
+                                               int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
+                                               float4* __restrict__ out_rgba, DevStats* __restrict__ st) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  int np = 0;
+  unsigned um = 0, pov = 0;
+  if (pix < npix)
+    np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
+                       pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
+  pair_epilogue(pix, np, um, pov, active, n_active, st);
+}
+
+// Batched form: pixel `pix` of the batch's pixel space belongs to request
+// rq with pix0[rq] <= pix < pix0[rq + 1]; its duplicate tolerance follows
+// the request's volume and its empty-pixel zero goes to the request's image.
+__global__ void __launch_bounds__(256) kb4_pair(BatchArgs ba, int npix, const float4* __restrict__ frag_tp,
+                                                const unsigned* __restrict__ frag_meta,
+                                                const int* __restrict__ frag_count, float4* __restrict__ pair_in,
+                                                float4* __restrict__ pair_out, int* __restrict__ pair_block,
+                                                int* __restrict__ pair_count, int* __restrict__ active,
+                                                int* __restrict__ n_active, DevStats* __restrict__ st) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  int np = 0;
+  unsigned um = 0, pov = 0;
+  if (pix < npix) {
+    const int rq = batch_request(ba, pix);
+    const DevRequest& q = ba.req[rq];
+    const float tau = 1e-5f * q.diag;
+    np = pair_pixel<float>(pix, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
+                           pair_count, kMaxPairs, q.out + (pix - __ldg(ba.pix0 + rq)), um, pov);
+  }
+  pair_epilogue(pix, np, um, pov, active, n_active, st);
+}
+
 }  // namespace
 
 template <typename R>
@@ -91,6 +133,14 @@ void launch_pair(const DevVolume& V, int npix, float diag, const typename Vec4T<
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
   k4_pair<R><<<(npix + 255) / 256, 256, 0, s>>>(npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
                                                 pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, st);
+}
+
+void launch_batch_pair(const BatchArgs& ba, int npix, const float4* frag_tp, const unsigned* frag_meta,
+                       const int* frag_count, float4* pair_in, float4* pair_out, int* pair_block, int* pair_count,
+                       int* active, int* n_active, DevStats* st, cudaStream_t s) {
+  if (npix <= 0) return;
+  kb4_pair<<<(npix + 255) / 256, 256, 0, s>>>(ba, npix, frag_tp, frag_meta, frag_count, pair_in, pair_out,
+                                             pair_block, pair_count, active, n_active, st);
 }
 
 template void launch_pair<float>(const DevVolume&, int, float, const float4*, const unsigned*, const int*, float4*,

@@ -62,6 +62,19 @@ class GuessTrainParams(C.Structure):
                 ("seed", C.c_ulonglong)]
 
 
+class Request(C.Structure):
+    _fields_ = [("volume", C.c_void_p), ("camera", Camera), ("width", C.c_int), ("height", C.c_int),
+                ("tf_n", C.c_int), ("tf_r", c_float_p), ("tf_rgba", c_float_p), ("tf_sigma", C.c_float),
+                ("scalar_lo", C.c_double), ("scalar_hi", C.c_double), ("out_rgba", C.c_void_p)]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("k5_ctas_per_sm", C.c_int), ("step_samples", C.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class Stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in (
         "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
@@ -120,6 +133,19 @@ def load(path: str = LIB_PATH):
     L.ivv_volume_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
     L.ivv_destroy_volume.argtypes = [vp]
     L.ivv_destroy_volume.restype = None
+    L.ivv_batch_create.argtypes = [C.POINTER(Request), C.c_int, C.POINTER(RenderParams), vp, C.POINTER(vp)]
+    L.ivv_batch_render.argtypes = [vp, C.c_int, vp]
+    L.ivv_batch_set_camera.argtypes = [vp, C.c_int, C.POINTER(Camera), vp]
+    L.ivv_batch_set_tuning.argtypes = [vp, C.POINTER(BatchTuning)]
+    L.ivv_batch_get_tuning.argtypes = [vp, C.POINTER(BatchTuning)]
+    L.ivv_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(BatchTuning), c_float_p, vp]
+    L.ivv_batch_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.ivv_batch_reset_stats.argtypes = [vp]
+    L.ivv_batch_get_stage_times.argtypes = [vp, c_float_p]
+    L.ivv_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_size_t),
+                                 C.POINTER(C.c_int)]
+    L.ivv_batch_destroy.argtypes = [vp]
+    L.ivv_batch_destroy.restype = None
     _LIB = L
     return L
 
@@ -407,3 +433,96 @@ def volume_for(scene, stream=None) -> Volume:
     v = Volume(scene.blocks, scene.scalar_mode, stream)
     v.set_transfer_function(scene.tf)
     return v
+
+
+class Batch:
+    """Many render requests rendered together (one launch per stage, replayed
+    from a CUDA graph).  items: sequence of (volume, camera, width, height, tf)
+    with tf a TransferFunction or None (the volume's own); outputs are float32
+    [H][W][4] CUDA tensors in self.outputs (given ones are used as they are)."""
+
+    def __init__(self, items, params=None, outputs=None, stream=None):
+        import torch
+        L = load()
+        n = len(items)
+        reqs = (Request * n)()
+        keep = []
+        self.outputs = []
+        for i, (vol, cam, w, h, tf) in enumerate(items):
+            out = outputs[i] if outputs is not None else torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+            self.outputs.append(out)
+            q = reqs[i]
+            q.volume = vol.h.value
+            q.camera = camera_struct(cam)
+            q.width, q.height = int(w), int(h)
+            q.out_rgba = out.data_ptr()
+            if tf is not None:
+                r = np.ascontiguousarray(tf.r, dtype=np.float32)
+                rgba = np.ascontiguousarray(tf.rgba, dtype=np.float32)
+                keep += [r, rgba]
+                q.tf_n = len(r)
+                q.tf_r = r.ctypes.data_as(c_float_p)
+                q.tf_rgba = rgba.ctypes.data_as(c_float_p)
+                q.tf_sigma = float(tf.sigma)
+                q.scalar_lo = tf.lo if math.isfinite(tf.lo) else float("nan")
+                q.scalar_hi = tf.hi if math.isfinite(tf.hi) else float("nan")
+        prm = params_struct(params)
+        h = C.c_void_p()
+        _check(L.ivv_batch_create(reqs, n, C.byref(prm), C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().ivv_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, flags=0, stream=None):
+        _check(load().ivv_batch_render(self.h, int(flags), C.c_void_p(_stream_ptr(stream))))
+        return self.outputs
+
+    def set_camera(self, i, camera, stream=None):
+        cam = camera_struct(camera)
+        _check(load().ivv_batch_set_camera(self.h, int(i), C.byref(cam), C.c_void_p(_stream_ptr(stream))))
+
+    @property
+    def tuning(self):
+        t = BatchTuning()
+        _check(load().ivv_batch_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    @tuning.setter
+    def tuning(self, d):
+        t = BatchTuning(int(d["tile_w"]), int(d["tile_h"]), int(d["k5_ctas_per_sm"]), int(d["step_samples"]))
+        _check(load().ivv_batch_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, reps=3, stream=None):
+        """Time the candidate launch shapes; applies and returns (tuning, ms per frame)."""
+        t = BatchTuning()
+        ms = C.c_float()
+        _check(load().ivv_batch_autotune(self.h, int(reps), C.byref(t), C.byref(ms),
+                                         C.c_void_p(_stream_ptr(stream))))
+        return t.as_dict(), ms.value
+
+    def stats(self):
+        s = Stats()
+        _check(load().ivv_batch_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(load().ivv_batch_reset_stats(self.h))
+
+    def stage_times(self):
+        ms = (C.c_float * len(STAGES))()
+        _check(load().ivv_batch_get_stage_times(self.h, ms))
+        return dict(zip(STAGES, list(ms)))
+
+    def info(self):
+        n, px, ws, g = C.c_int(), C.c_longlong(), C.c_size_t(), C.c_int()
+        _check(load().ivv_batch_info(self.h, C.byref(n), C.byref(px), C.byref(ws), C.byref(g)))
+        return {"n_requests": n.value, "n_pixels": px.value, "workspace_bytes": ws.value, "graph_ready": bool(g.value)}

@@ -93,6 +93,23 @@ def test_invalid_descriptions_are_rejected(lib):
     assert status_of([good], mode=7) == 1
 
 
+def test_batch_entry_points_reject_null_arguments(lib):
+    """The batch calls validate their arguments before any CUDA call."""
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.ivv_batch_create(None, 1, None, None, C.byref(out)) == 1
+    assert lib.ivv_batch_create(None, 1, None, None, None) == 1
+    reqs = (ivv.Request * 1)()
+    assert lib.ivv_batch_create(reqs, 0, None, None, C.byref(out)) == 1          # n < 1
+    assert lib.ivv_batch_create(reqs, 1, None, None, C.byref(out)) == 1          # NULL volume
+    assert out.value is None
+    assert lib.ivv_batch_render(None, 0, None) == 1
+    assert lib.ivv_batch_set_tuning(None, None) == 1
+    assert lib.ivv_batch_info(None, None, None, None, None) == 1
+    assert b"NULL" in lib.ivv_last_error() or b"batch" in lib.ivv_last_error()
+    lib.ivv_batch_destroy(None)
+
+
 def _grazing_cos(ov, o, d, block, q):
     """|cos| between the ray and the face normal at parameter point q."""
     q = np.asarray(q)
