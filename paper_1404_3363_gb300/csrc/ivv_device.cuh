@@ -140,6 +140,13 @@ template <> struct ElemPtr<double> {
 // field at parameter point p of block `blk`.  Sum-factorised: for each i the
 // (j,k) slab is contracted along w (value and w-derivative), then along v,
 // then the u contraction accumulates -- 576 FMA for P = 3.
+template <int P, bool WANT_RHO>
+__device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
+                                               const float dbu[P + 1], const float bv[P + 1],
+                                               const float dbv[P + 1], const float bw[P + 1],
+                                               const float dbw[P + 1], float f[3], float fu[3], float fv[3],
+                                               float fw[3], float& rho);
+
 template <int P, typename R, bool WANT_RHO>
 __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& B, const R p[3], R phi[3],
                                            R J[3][3], R& rho) {
@@ -170,6 +177,9 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
   bernstein<P, R>(loc[2], bw, dbw);
   R f[3] = {0, 0, 0}, fu[3] = {0, 0, 0}, fv[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
   R s = 0;
+  if constexpr (sizeof(R) == 4) {
+    contract_f32x2<P, WANT_RHO>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw, s);
+  } else {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     R s00[3] = {0, 0, 0}, s01[3] = {0, 0, 0}, s10[3] = {0, 0, 0};
@@ -202,6 +212,7 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
     }
     if (WANT_RHO) s += bu[i] * ss;
   }
+  }
   const typename Vec4T<R>::type og = ElemPtr<R>::org(V, eid);
   f[0] += R(og.x);
   f[1] += R(og.y);
@@ -214,6 +225,60 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
     J[r][2] = fw[r] * sc[2];
   }
   rho = s;
+}
+
+// FP32 form of the contraction above on paired lanes (__ffma2_rn: two fused
+// multiply-adds per instruction): (x, y) and (z, rho) of each control point
+// travel together through the w, v and u contractions; the second lane of the
+// (z, rho) pair of a derivative is not needed and costs nothing.
+template <int P, bool WANT_RHO>
+__device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
+                                               const float dbu[P + 1], const float bv[P + 1],
+                                               const float dbv[P + 1], const float bw[P + 1],
+                                               const float dbw[P + 1], float f[3], float fu[3], float fv[3],
+                                               float fw[3], float& rho) {
+  constexpr int N = P + 1;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 fxy = z2, fzr = z2, fuxy = z2, fuzr = z2, fvxy = z2, fvzr = z2, fwxy = z2, fwzr = z2;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    float2 s00xy = z2, s00zr = z2, s01xy = z2, s01zr = z2, s10xy = z2, s10zr = z2;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float2 t0xy = z2, t0zr = z2, t1xy = z2, t1zr = z2;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float4 c = __ldg(cp + (i * N + j) * N + k);
+        const float2 cxy = make_float2(c.x, c.y), czr = make_float2(c.z, WANT_RHO ? c.w : 0.f);
+        const float2 b = make_float2(bw[k], bw[k]), db = make_float2(dbw[k], dbw[k]);
+        t0xy = __ffma2_rn(b, cxy, t0xy);
+        t0zr = __ffma2_rn(b, czr, t0zr);
+        t1xy = __ffma2_rn(db, cxy, t1xy);
+        t1zr = __ffma2_rn(db, czr, t1zr);
+      }
+      const float2 b = make_float2(bv[j], bv[j]), db = make_float2(dbv[j], dbv[j]);
+      s00xy = __ffma2_rn(b, t0xy, s00xy);
+      s00zr = __ffma2_rn(b, t0zr, s00zr);
+      s01xy = __ffma2_rn(db, t0xy, s01xy);
+      s01zr = __ffma2_rn(db, t0zr, s01zr);
+      s10xy = __ffma2_rn(b, t1xy, s10xy);
+      s10zr = __ffma2_rn(b, t1zr, s10zr);
+    }
+    const float2 b = make_float2(bu[i], bu[i]), db = make_float2(dbu[i], dbu[i]);
+    fxy = __ffma2_rn(b, s00xy, fxy);
+    fzr = __ffma2_rn(b, s00zr, fzr);
+    fuxy = __ffma2_rn(db, s00xy, fuxy);
+    fuzr = __ffma2_rn(db, s00zr, fuzr);
+    fvxy = __ffma2_rn(b, s01xy, fvxy);
+    fvzr = __ffma2_rn(b, s01zr, fvzr);
+    fwxy = __ffma2_rn(b, s10xy, fwxy);
+    fwzr = __ffma2_rn(b, s10zr, fwzr);
+  }
+  f[0] = fxy.x; f[1] = fxy.y; f[2] = fzr.x;
+  fu[0] = fuxy.x; fu[1] = fuxy.y; fu[2] = fuzr.x;
+  fv[0] = fvxy.x; fv[1] = fvxy.y; fv[2] = fvzr.x;
+  fw[0] = fwxy.x; fw[1] = fwxy.y; fw[2] = fwzr.x;
+  rho = fzr.y;
 }
 
 template <typename R>
