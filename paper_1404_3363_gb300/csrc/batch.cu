@@ -233,6 +233,7 @@ ivv::BatchArgs batch_args(const ivv_batch* b) {
   a.req = b->d_req;
   a.pix0 = b->d_pix0;
   a.tile0 = b->d_tile0[shape_index(b->tune.tile_w, b->tune.tile_h)];
+  a.tile16 = b->d_tile0[shape_index(16, 16)];
   a.tf = b->d_tf;
   a.nreq = b->nreq;
   return a;
@@ -257,7 +258,7 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
                                    b->d_stats, s))
     return bfail(IVV_ERR_INVALID_ARG, "unsupported K2 tile shape");
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[2], s));
-  ivv::launch_batch_pair(ba, npix, (const float4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
+  ivv::launch_batch_pair(ba, b->tiles[shape_index(16, 16)], npix, (const float4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                          (const int*)(ws + L.frag_count), (float4*)(ws + L.pair_in), (float4*)(ws + L.pair_out),
                          (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), (int*)(ws + L.active),
                          (int*)(ws + L.counters), b->d_stats, s);

@@ -259,7 +259,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
                            (V4*)(ws + L.frag_tp), (unsigned*)(ws + L.frag_meta), (int*)(ws + L.frag_count),
                            v->d_stats, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[2], s));
-  ivv::launch_pair<R>(V, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
+  ivv::launch_pair<R>(V, F.w, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                       (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
                       (int*)(ws + L.counters), out_zero, nullptr, v->d_stats, s);

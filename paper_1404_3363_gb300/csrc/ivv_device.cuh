@@ -356,6 +356,7 @@ struct BatchArgs {
   const DevRequest* req;   // [nreq]
   const int* pix0;         // [nreq + 1] first pixel of each request, then the total
   const int* tile0;        // [nreq + 1] first K2 tile of each request, then the total
+  const int* tile16;       // [nreq + 1] the same for 16x16 tiles (K4's pixel order)
   const DevTFSlot* tf;     // [nreq]
   int nreq;
 };
@@ -386,7 +387,7 @@ void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCame
                       int* frag_count, DevStats* st, cudaStream_t s);
 
 template <typename R>
-void launch_pair(const DevVolume& V, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
+void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs,
                  int* active, int* n_active, float4* out_rgba_zero, Dbl4* out_rgba_zero64, DevStats* st,
@@ -407,7 +408,7 @@ void launch_integrate(const DevVolume& V, const DevCamera<R>& cam, const DevTF& 
                       const int* active, const int* n_active, int* queue_head, float4* out_rgba, DevStats* st,
                       int num_sms, cudaStream_t s);
 
-void launch_batch_pair(const BatchArgs& ba, int npix, const float4* frag_tp, const unsigned* frag_meta,
+void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
                        const int* frag_count, float4* pair_in, float4* pair_out, int* pair_block, int* pair_count,
                        int* active, int* n_active, DevStats* st, cudaStream_t s);
 void launch_batch_face_project(const DevVolume& V, const BatchArgs& ba, int max_faces, int4* boxes, cudaStream_t s);

@@ -81,8 +81,18 @@ __device__ __forceinline__ void pair_epilogue(int pix, int np, unsigned um, unsi
   }
 }
 
+// Pixel of thread threadIdx.x of 16x16 tile (tx, ty): warp w covers the 8x4
+// block at (8 (w & 1), 4 (w >> 1)) of the tile.  Pixels are queued in this
+// order, so the 32 lanes of an integrator warp start on a compact pixel block
+// whose rays cross the same elements (shared control-point loads).
+__device__ __forceinline__ void tile_pixel(int tx, int ty, int& x, int& y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  x = tx * 16 + (warp & 1) * 8 + (lane & 7);
+  y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typename Vec4T<R>::type* __restrict__ frag_tp,
+__global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const typename Vec4T<R>::type* __restrict__ frag_tp,
                                                const unsigned* __restrict__ frag_meta,
                                                const int* __restrict__ frag_count,
                                                typename Vec4T<R>::type* __restrict__ pair_in,
@@ -90,10 +100,13 @@ __global__ void __launch_bounds__(256) k4_pair(int npix, R tau_dup, const typena
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
                                                float4* __restrict__ out_rgba, DevStats* __restrict__ st) {
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tiles_x = (w + 15) / 16;
+  int x, y;
+  tile_pixel(blockIdx.x % tiles_x, blockIdx.x / tiles_x, x, y);
+  const int pix = y * w + x;
   int np = 0;
   unsigned um = 0, pov = 0;
-  if (pix < npix)
+  if (x < w && pix < npix)
     np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
                        pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
   pair_epilogue(pix, np, um, pov, active, n_active, st);
@@ -108,12 +121,16 @@ __global__ void __launch_bounds__(256) kb4_pair(BatchArgs ba, int npix, const fl
                                                 float4* __restrict__ pair_out, int* __restrict__ pair_block,
                                                 int* __restrict__ pair_count, int* __restrict__ active,
                                                 int* __restrict__ n_active, DevStats* __restrict__ st) {
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rq = batch_find(ba.tile16, ba.nreq, blockIdx.x);
+  const DevRequest& q = ba.req[rq];
+  const int t = blockIdx.x - __ldg(ba.tile16 + rq);
+  const int tiles_x = (q.cam.w + 15) / 16;
+  int x, y;
+  tile_pixel(t % tiles_x, t / tiles_x, x, y);
+  const int pix = __ldg(ba.pix0 + rq) + y * q.cam.w + x;
   int np = 0;
   unsigned um = 0, pov = 0;
-  if (pix < npix) {
-    const int rq = batch_request(ba, pix);
-    const DevRequest& q = ba.req[rq];
+  if (x < q.cam.w && y < q.cam.h) {
     const float tau = 1e-5f * q.diag;
     np = pair_pixel<float>(pix, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
                            pair_count, kMaxPairs, q.out + (pix - __ldg(ba.pix0 + rq)), um, pov);
@@ -124,28 +141,30 @@ __global__ void __launch_bounds__(256) kb4_pair(BatchArgs ba, int npix, const fl
 }  // namespace
 
 template <typename R>
-void launch_pair(const DevVolume& V, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
+void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
                  int* n_active, float4* out_rgba_zero, Dbl4* /*unused*/, DevStats* st, cudaStream_t s) {
   (void)V;
   if (npix <= 0) return;
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
-  k4_pair<R><<<(npix + 255) / 256, 256, 0, s>>>(npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
+  if (w <= 0) return;
+  const int h = npix / w;
+  k4_pair<R><<<((w + 15) / 16) * ((h + 15) / 16), 256, 0, s>>>(w, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
                                                 pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, st);
 }
 
-void launch_batch_pair(const BatchArgs& ba, int npix, const float4* frag_tp, const unsigned* frag_meta,
+void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
                        const int* frag_count, float4* pair_in, float4* pair_out, int* pair_block, int* pair_count,
                        int* active, int* n_active, DevStats* st, cudaStream_t s) {
-  if (npix <= 0) return;
-  kb4_pair<<<(npix + 255) / 256, 256, 0, s>>>(ba, npix, frag_tp, frag_meta, frag_count, pair_in, pair_out,
+  if (npix <= 0 || tiles16 <= 0) return;
+  kb4_pair<<<tiles16, 256, 0, s>>>(ba, npix, frag_tp, frag_meta, frag_count, pair_in, pair_out,
                                              pair_block, pair_count, active, n_active, st);
 }
 
-template void launch_pair<float>(const DevVolume&, int, float, const float4*, const unsigned*, const int*, float4*,
+template void launch_pair<float>(const DevVolume&, int, int, float, const float4*, const unsigned*, const int*, float4*,
                                  float4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*, cudaStream_t);
-template void launch_pair<double>(const DevVolume&, int, float, const Dbl4*, const unsigned*, const int*,
+template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*, const unsigned*, const int*,
                                   Dbl4*, Dbl4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*,
                                   cudaStream_t);
 
