@@ -77,7 +77,7 @@ BatchLayout batch_layout(size_t n_boxes, size_t npix) {
   L.pair_block = take(sizeof(int) * ivv::kMaxPairs * npix);
   L.pair_count = take(sizeof(int) * npix);
   L.active = take(sizeof(int) * npix);
-  L.counters = take(256);
+  L.counters = take(ivv::kCountersBytes);
   L.total = o;
   return L;
 }
@@ -247,7 +247,7 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
   char* ws = b->ws;
   const int npix = (int)b->npix;
   const bool mixed = b->p.precision == IVV_PREC_MIXED;
-  IVV_BCUDA(cudaMemsetAsync(ws + L.counters, 0, 256, s));
+  IVV_BCUDA(cudaMemsetAsync(ws + L.counters, 0, ivv::kCountersBytes, s));
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[0], s));
   ivv::launch_batch_face_project(V, ba, b->max_faces, (int4*)(ws + L.boxes), s);
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[1], s));
@@ -278,7 +278,7 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
   ivv::launch_batch_integrate(V, ba, a, mixed, stats, (const float4*)(ws + L.pair_in),
                               (const float4*)(ws + L.pair_out), (const int*)(ws + L.pair_block),
                               (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
-                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + 1, b->d_stats, grid, s);
+                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff, b->d_stats, grid, s);
   if (timing) {
     IVV_BCUDA(cudaEventRecord(b->ev[4], s));
     b->timed = true;

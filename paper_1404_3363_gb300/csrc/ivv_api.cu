@@ -64,7 +64,7 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
   L.pair_block = take(sizeof(int) * ivv::kMaxPairs * npix);
   L.pair_count = take(sizeof(int) * npix);
   L.active = take(sizeof(int) * npix);
-  L.counters = take(256);
+  L.counters = take(ivv::kCountersBytes);
   L.total = o;
   return L;
 }
@@ -251,7 +251,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
   const bool mixed = p.precision == IVV_PREC_MIXED;
   const bool timing = (p.flags & IVV_FLAG_TIMING) != 0;
-  IVV_CUDA(cudaMemsetAsync(ws + L.counters, 0, 256, s));
+  IVV_CUDA(cudaMemsetAsync(ws + L.counters, 0, ivv::kCountersBytes, s));
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[0], s));
   ivv::launch_face_project(V, dev_camera<float>(F), (int4*)(ws + L.boxes), s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[1], s));
@@ -367,12 +367,12 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
       ivv::launch_integrate_p<2>(V, nullptr, &c64, tf, a, false, stats, ws + L.pair_in, ws + L.pair_out,
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
     else
       ivv::launch_integrate_p<3>(V, nullptr, &c64, tf, a, false, stats, ws + L.pair_in, ws + L.pair_out,
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
   } else {
     st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;
@@ -381,12 +381,12 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
       ivv::launch_integrate_p<2>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
     else
       ivv::launch_integrate_p<3>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + 1, (float4*)out, v->d_stats, v->num_sms, s);
+                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
   }
   if (p.flags & IVV_FLAG_TIMING) {
     IVV_CUDA(cudaEventRecord(v->ev[4], s));

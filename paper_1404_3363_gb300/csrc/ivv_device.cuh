@@ -249,7 +249,7 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const float4 c = __ldg(cp + (i * N + j) * N + k);
-        const float2 cxy = make_float2(c.x, c.y), czr = make_float2(c.z, WANT_RHO ? c.w : 0.f);
+        const float2 cxy = make_float2(c.x, c.y), czr = make_float2(c.z, c.w);
         const float2 b = make_float2(bw[k], bw[k]), db = make_float2(dbw[k], dbw[k]);
         t0xy = __ffma2_rn(b, cxy, t0xy);
         t0zr = __ffma2_rn(b, czr, t0zr);
@@ -371,6 +371,35 @@ __device__ __forceinline__ int batch_find(const int* __restrict__ first, int nre
   return lo;
 }
 __device__ __forceinline__ int batch_request(const BatchArgs& ba, int pix) { return batch_find(ba.pix0, ba.nreq, pix); }
+
+// As tf_eval for an unclamped normalised scalar x, also returning the piece
+// of the TF that x falls in: -1 for x <= r[0] and n-1 for x >= r[n-1] (the
+// constant ends), otherwise the segment i with r[i] <= x < r[i+1].
+__device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const float4* __restrict__ rgba,
+                                              const unsigned char* __restrict__ seg, int n, float x, int& piece) {
+  if (x <= r[0]) {
+    piece = -1;
+    return rgba[0];
+  }
+  if (x >= r[n - 1]) {
+    piece = n - 1;
+    return rgba[n - 1];
+  }
+  int c = (int)(x * (float)kTfTable);
+  c = c < kTfTable - 1 ? c : kTfTable - 1;
+  int lo = seg[c];
+  while (lo < n - 2 && r[lo + 1] <= x) ++lo;
+  piece = lo;
+  const float w = r[lo + 1] - r[lo];
+  const float t = w > 0.f ? __fdividef(x - r[lo], w) : 1.f;
+  const float4 a = rgba[lo], b = rgba[lo + 1];
+  return make_float4(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z), a.w + t * (b.w - a.w));
+}
+
+// Counters block of a render: [0] active pixels, [2] RF sample total, [3]
+// spare; the integrator's queue head at kQueueHeadOff.
+constexpr int kQueueHeadOff = 1;
+constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
   if (v > 0.f) atomicMax(addr, __float_as_uint(v));

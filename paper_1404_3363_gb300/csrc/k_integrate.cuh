@@ -85,17 +85,36 @@ template <typename R> __device__ __forceinline__ R fast_exp(R x);
 template <> __device__ __forceinline__ float fast_exp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double fast_exp<double>(double x) { return exp(x); }
 
+// Alg. 1 over the interval [s_{j-1}, s_j] of length dsi with K midpoint
+// sub-samples of the linearly interpolated scalar (§3.2.1 supersampling).
+// The TF is piecewise linear in the normalised scalar and constant outside
+// [r_0, r_{n-1}]; when both interval ends fall into the same piece, the K
+// sub-sample colours are the same linear interpolation of the two end
+// colours, so two TF lookups serve all K sub-samples.
 template <typename R>
 __device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const unsigned char* s_seg,
                                                    const DevTF& tf, int K, R rho0, R rho1, R dsi, Acc<R>& acc) {
   const R invK = R(1) / R(K);
   const R dr = rho1 - rho0;
   const R tau_scale = R(tf.sigma) * dsi * invK;
+  const R x0 = (rho0 - R(tf.lo)) * R(tf.inv_range), x1 = (rho1 - R(tf.lo)) * R(tf.inv_range);
+  int g0, g1;
+  const float4 c0 = tf_eval_seg(s_r, s_rgba, s_seg, tf.n, (float)x0, g0);
+  const float4 c1 = tf_eval_seg(s_r, s_rgba, s_seg, tf.n, (float)x1, g1);
+  const bool same = g0 == g1;
   for (int k = 0; k < K; ++k) {
-    const R rk = rho0 + (R(k) + R(0.5)) * invK * dr;
-    R x = (rk - R(tf.lo)) * R(tf.inv_range);
-    x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-    const float4 c = tf_eval(s_r, s_rgba, s_seg, tf.n, (float)x);
+    const R fk = (R(k) + R(0.5)) * invK;
+    float4 c;
+    if (same) {
+      const float f = (float)fk;
+      c = make_float4(c0.x + f * (c1.x - c0.x), c0.y + f * (c1.y - c0.y), c0.z + f * (c1.z - c0.z),
+                      c0.w + f * (c1.w - c0.w));
+    } else {
+      const R rk = rho0 + fk * dr;
+      R x = (rk - R(tf.lo)) * R(tf.inv_range);
+      x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+      c = tf_eval(s_r, s_rgba, s_seg, tf.n, (float)x);
+    }
     const R T = fast_exp<R>(-tau_scale * R(c.w));
     const R w = (R(1) - T) * (R(1) - acc.a);
     acc.C[0] += w * R(c.x);
@@ -156,6 +175,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   }
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
+  if (nact == 0) return;
   const int npix = args.npix;
   const R tol = R(args.rk_tol), cc = R(args.c), early = R(args.early_alpha);
   R ds = R(args.ds);
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
           q = -1;
           stage = 0;
         } else {
-          pix = -2;
+          pix = -2;                    // the queue is drained
         }
       }
     }
