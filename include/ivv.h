@@ -178,6 +178,7 @@ typedef struct {
   unsigned long long step_cap;      /* pairs that hit the RK step cap          */
   unsigned long long rf_newton_iters; /* RF: Newton iterations over all samples */
   unsigned long long rf_unconverged;  /* RF: samples that missed the tolerance  */
+  unsigned long long isect_items;   /* (pixel, patch) candidates after the box tests */
   double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
 } ivv_stats;
 
@@ -368,13 +369,13 @@ ivv_status ivv_volume_info(const ivv_volume* vol, int* n_blocks, int* n_elements
  * request, K4 over every pixel, and the persistent K5 over one work queue
  * that spans all requests, so rays of short and long requests share the
  * machine until the last one finishes.  The library owns the workspace
- * (about 640 bytes of fragment slots and 600 bytes of pair slots per pixel).
+ * (about 1.4 KB per pixel: fragment slots, stage-1 items and pair slots).
  * The volumes may be destroyed after creation; all of them must share the
  * common degree P (IVV_ERR_UNSUPPORTED otherwise). */
 typedef struct ivv_batch ivv_batch;       /* opaque, library-owned */
 
 #define IVV_BATCH_TF_MAX 64               /* knots of a per-request TF     */
-#define IVV_BATCH_MAX_REQUESTS 4096
+#define IVV_BATCH_MAX_REQUESTS 4096      /* and fewer than 2^27 pixels in all */
 
 /* One render request.
  * volume      a created volume; its data is copied at ivv_batch_create
@@ -400,7 +401,8 @@ typedef struct {
 } ivv_request;
 
 /* Launch shapes chosen by the autotuner.
- * tile_w, tile_h   K2 screen tile (one CTA): 8x8, 16x8 or 16x16 [16x8]
+ * tile_w, tile_h   K2 culling tile (one warp, one lane per pixel): 8x4, 4x8
+ *                  or 16x2 [8x4]
  * k5_ctas_per_sm   resident CTAs of the persistent K5 per SM, 1..4 [4]
  * step_samples     the step batch: the longest RK step, in sample distances
  *                  (samples inside a step come from dense output), one of
@@ -433,7 +435,7 @@ ivv_status ivv_batch_set_tuning(ivv_batch* batch, const ivv_batch_tuning* tuning
 ivv_status ivv_batch_get_tuning(const ivv_batch* batch, ivv_batch_tuning* tuning);
 
 /* Time the candidate launch shapes on this batch (reps timed renders each,
- * after one warm-up, CUDA events on `stream`): the K2 tile shape by the
+ * after one warm-up, CUDA events on `stream`): the K2 culling tile by the
  * surface stage's time, then the K5 CTAs per SM and step batch by the
  * integration stage's time.  Applies and returns the fastest; *best_ms is the
  * frame time with it.  Synchronises `stream`. */

@@ -52,23 +52,30 @@ ivv_status bcuda(cudaError_t e, const char* what) {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// The K2 tile shapes the batch kernels are built for.
-constexpr int kShapes[3][2] = {{16, 8}, {8, 8}, {16, 16}};
+// Tile shapes with a tile table: the K2a warp tiles the batch kernels are
+// built for (the first kNumWarpShapes), then K4's 16x16 pixel order.
+constexpr int kNumWarpShapes = 3;
+constexpr int kNumShapes = 4;
+constexpr int kShapes[kNumShapes][2] = {{8, 4}, {4, 8}, {16, 2}, {16, 16}};
+constexpr int kShape16 = 3;
 int shape_index(int tw, int th) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < kNumWarpShapes; ++i)
     if (kShapes[i][0] == tw && kShapes[i][1] == th) return i;
   return -1;
 }
 
 struct BatchLayout {
-  size_t boxes, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active, counters, total;
+  size_t boxes, gboxes, items, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
+      counters, total;
 };
 
-BatchLayout batch_layout(size_t n_boxes, size_t npix) {
+BatchLayout batch_layout(size_t n_boxes, size_t n_gboxes, size_t npix) {
   BatchLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o += a256(bytes); return at; };
   L.boxes = take(sizeof(int4) * std::max<size_t>(n_boxes, 1));
+  L.gboxes = take(sizeof(int4) * std::max<size_t>(n_gboxes, 1));
+  L.items = take(sizeof(int2) * ivv::kItemsPerPixel * npix);
   L.frag_tp = take(sizeof(float4) * ivv::kMaxFrags * npix);
   L.frag_meta = take(sizeof(unsigned) * ivv::kMaxFrags * npix);
   L.frag_count = take(sizeof(int) * npix);
@@ -91,8 +98,8 @@ struct ivv_batch {
   long long npix = 0;
   std::vector<ivv::DevRequest> hreq;
   std::vector<ivv::BlockInfo> blocks;
-  int n_faces = 0, max_faces = 0, n_boxes = 0;
-  int tiles[3] = {0, 0, 0};                 // K2 tiles of the batch per shape
+  int n_faces = 0, max_faces = 0, n_boxes = 0, n_gboxes = 0;
+  int tiles[kNumShapes] = {};               // tiles of the batch per shape
   // pool
   ivv::BlockInfo* d_blocks = nullptr;
   float* d_brk32 = nullptr;
@@ -106,14 +113,14 @@ struct ivv_batch {
   // tables
   ivv::DevRequest* d_req = nullptr;
   int* d_pix0 = nullptr;
-  int* d_tile0[3] = {nullptr, nullptr, nullptr};
+  int* d_tile0[kNumShapes] = {};
   ivv::DevTFSlot* d_tf = nullptr;
   ivv::DevStats* d_stats = nullptr;
   // workspace
   BatchLayout L{};
   char* ws = nullptr;
   // launch shapes, graph, timing
-  ivv_batch_tuning tune{16, 8, 4, 8};
+  ivv_batch_tuning tune{8, 4, 4, 8};
   int k5_max_ctas[2] = {1, 1};              // occupancy limit without / with statistics
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -137,7 +144,7 @@ void free_batch(ivv_batch* b) {
   drop_graph(b);
   void* ptrs[] = {b->d_blocks, b->d_brk32, b->d_brk64, b->d_elem32, b->d_org32, b->d_face32, b->d_face64,
                   b->d_faces, b->d_faces64, b->d_req, b->d_pix0, b->d_tile0[0], b->d_tile0[1], b->d_tile0[2],
-                  b->d_tf, b->d_stats, b->ws};
+                  b->d_tile0[3], b->d_tf, b->d_stats, b->ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : b->ev)
@@ -233,7 +240,7 @@ ivv::BatchArgs batch_args(const ivv_batch* b) {
   a.req = b->d_req;
   a.pix0 = b->d_pix0;
   a.tile0 = b->d_tile0[shape_index(b->tune.tile_w, b->tune.tile_h)];
-  a.tile16 = b->d_tile0[shape_index(16, 16)];
+  a.tile16 = b->d_tile0[kShape16];
   a.tf = b->d_tf;
   a.nreq = b->nreq;
   return a;
@@ -248,17 +255,24 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
   const int npix = (int)b->npix;
   const bool mixed = b->p.precision == IVV_PREC_MIXED;
   IVV_BCUDA(cudaMemsetAsync(ws + L.counters, 0, ivv::kCountersBytes, s));
+  ivv::SurfaceWs sw;
+  sw.boxes = (int4*)(ws + L.boxes);
+  sw.gboxes = (int4*)(ws + L.gboxes);
+  sw.items = (int2*)(ws + L.items);
+  sw.cap = (int)std::min<long long>((long long)ivv::kItemsPerPixel * b->npix, 0x7fffffffll);
+  sw.n_items = (int*)(ws + L.counters) + ivv::kItemCounter;
+  sw.frag_tp = ws + L.frag_tp;
+  sw.frag_meta = (unsigned*)(ws + L.frag_meta);
+  sw.frag_count = (int*)(ws + L.frag_count);
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[0], s));
-  ivv::launch_batch_face_project(V, ba, b->max_faces, (int4*)(ws + L.boxes), s);
+  ivv::launch_batch_face_project(V, ba, b->max_faces, sw, s);
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[1], s));
   const int si = shape_index(b->tune.tile_w, b->tune.tile_h);
-  if (!ivv::launch_batch_intersect(V, ba, b->tiles[si], b->tune.tile_w, b->tune.tile_h, mixed, stats,
-                                   (const int4*)(ws + L.boxes), (float4*)(ws + L.frag_tp),
-                                   (unsigned*)(ws + L.frag_meta), (int*)(ws + L.frag_count), (size_t)npix,
-                                   b->d_stats, s))
+  if (si < 0 || !ivv::launch_batch_intersect(V, ba, b->tiles[si], b->tune.tile_w, b->tune.tile_h, mixed, stats, sw,
+                                             (size_t)npix, b->d_stats, b->num_sms, s))
     return bfail(IVV_ERR_INVALID_ARG, "unsupported K2 tile shape");
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[2], s));
-  ivv::launch_batch_pair(ba, b->tiles[shape_index(16, 16)], npix, (const float4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
+  ivv::launch_batch_pair(ba, b->tiles[kShape16], npix, (const float4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                          (const int*)(ws + L.frag_count), (float4*)(ws + L.pair_in), (float4*)(ws + L.pair_out),
                          (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), (int*)(ws + L.active),
                          (int*)(ws + L.counters), b->d_stats, s);
@@ -382,9 +396,9 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
     n_elem += (size_t)hv.n_elems();
     n_brk += hv.brk.size();
   }
-  if (b->blocks.size() >= (1u << 27)) {
+  if (b->blocks.size() >= (1u << 27) || faces.size() >= (1u << ivv::kBatchFaceBits)) {
     free_batch(b);
-    return bfail(IVV_ERR_UNSUPPORTED, "too many blocks in one batch");
+    return bfail(IVV_ERR_UNSUPPORTED, "a batch's volumes hold fewer than 2^27 blocks and 2^20 face patches");
   }
   b->n_faces = (int)faces.size();
   if ((st = balloc(&b->d_blocks, b->blocks.size())) != IVV_OK || (st = balloc(&b->d_brk32, n_brk)) != IVV_OK ||
@@ -423,10 +437,10 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
 
   // ---- request records, transfer-function slots, pixel and tile tables
   std::vector<ivv::DevTFSlot> slots(n);
-  std::vector<int> pix0(n + 1), tile0[3];
-  for (int k = 0; k < 3; ++k) tile0[k].assign(n + 1, 0);
+  std::vector<int> pix0(n + 1), tile0[kNumShapes];
+  for (int k = 0; k < kNumShapes; ++k) tile0[k].assign(n + 1, 0);
   b->hreq.resize(n);
-  long long pix = 0, tl[3] = {0, 0, 0}, box = 0;
+  long long pix = 0, tl[kNumShapes] = {}, box = 0, gbox = 0;
   ivv_render_params pw = p;
   for (int i = 0; i < n; ++i) {
     const ivv_request& r = req[i];
@@ -441,40 +455,44 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
     q.face0 = face_base[vol_of[i]];
     q.n_faces = v->hv.n_faces();
     q.box0 = (int)box;
+    q.gbox0 = (int)gbox;
     q.diag = (float)v->hv.diag;
     q.ds = (float)(ds_given ? params->ds : v->hv.diag / 128.0);
     q.out = (float4*)r.out_rgba;
     b->max_faces = std::max(b->max_faces, q.n_faces);
     pix0[i] = (int)pix;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kNumShapes; ++k) {
       tile0[k][i] = (int)tl[k];
       tl[k] += (long long)((r.width + kShapes[k][0] - 1) / kShapes[k][0]) * ((r.height + kShapes[k][1] - 1) / kShapes[k][1]);
     }
     pix += (long long)r.width * r.height;
     box += q.n_faces;
-    if (pix >= (1ll << 31) || tl[1] >= (1ll << 31)) {
+    gbox += (q.n_faces + ivv::kGroup - 1) / ivv::kGroup;
+    if (pix * ivv::kItemsPerPixel >= (1ll << 31) || tl[1] >= (1ll << 31)) {
       free_batch(b);
-      return bfail(IVV_ERR_UNSUPPORTED, "a batch holds fewer than 2^31 pixels");
+      return bfail(IVV_ERR_UNSUPPORTED, "a batch holds fewer than 2^27 pixels");
     }
   }
   pix0[n] = (int)pix;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kNumShapes; ++k) {
     tile0[k][n] = (int)tl[k];
     b->tiles[k] = (int)tl[k];
   }
   b->npix = pix;
   b->n_boxes = (int)box;
-  b->L = batch_layout((size_t)box, (size_t)pix);
+  b->n_gboxes = (int)gbox;
+  b->L = batch_layout((size_t)box, (size_t)gbox, (size_t)pix);
   if ((st = balloc(&b->d_req, n)) != IVV_OK || (st = balloc(&b->d_pix0, n + 1)) != IVV_OK ||
       (st = balloc(&b->d_tile0[0], n + 1)) != IVV_OK || (st = balloc(&b->d_tile0[1], n + 1)) != IVV_OK ||
-      (st = balloc(&b->d_tile0[2], n + 1)) != IVV_OK || (st = balloc(&b->d_tf, n)) != IVV_OK ||
+      (st = balloc(&b->d_tile0[2], n + 1)) != IVV_OK || (st = balloc(&b->d_tile0[3], n + 1)) != IVV_OK ||
+      (st = balloc(&b->d_tf, n)) != IVV_OK ||
       (st = balloc(&b->d_stats, 1)) != IVV_OK || (st = balloc(&b->ws, b->L.total)) != IVV_OK) {
     free_batch(b);
     return st;
   }
   e = cudaMemcpyAsync(b->d_req, b->hreq.data(), sizeof(ivv::DevRequest) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_pix0, pix0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+  for (int k = 0; k < kNumShapes && e == cudaSuccess; ++k)
     e = cudaMemcpyAsync(b->d_tile0[k], tile0[k].data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_tf, slots.data(), sizeof(ivv::DevTFSlot) * n, cudaMemcpyHostToDevice, s);
@@ -558,10 +576,10 @@ ivv_status ivv_batch_autotune(ivv_batch* b, int reps, ivv_batch_tuning* best, fl
   drop_graph(b);
   ivv_batch_tuning cur = b->tune, win = cur;
   float best_t = 1e30f;
-  for (const auto& sh : kShapes) {               // K2 tile shape by the surface stage
+  for (int k = 0; k < kNumWarpShapes; ++k) {     // K2a warp tile by the surface stage
     ivv_batch_tuning t = cur;
-    t.tile_w = sh[0];
-    t.tile_h = sh[1];
+    t.tile_w = kShapes[k][0];
+    t.tile_h = kShapes[k][1];
     float ms;
     const ivv_status st = stage_ms(t, 1, 2, ms);
     if (st != IVV_OK) return st;

@@ -229,8 +229,9 @@ IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
     ++iters;
     const R det = Ax * By - Bx * Ay;
     if (det == R(0)) return false;
-    R da = (-Fx * By + Fy * Bx) / det;
-    R db = (-Ax * Fy + Ay * Fx) / det;
+    const R inv = R(1) / det;
+    R da = (-Fx * By + Fy * Bx) * inv;
+    R db = (-Ax * Fy + Ay * Fx) * inv;
     const R mx = maxr(fabs(da), fabs(db));
     if (mx > R(0.5)) { da *= R(0.5) / mx; db *= R(0.5) / mx; }
     a += da;
@@ -243,6 +244,44 @@ IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
 
 constexpr int kMaxPatchRoots = 4;
 constexpr int kSplitDepth = 8;
+
+// Starting point for Newton on patch q: the zero of the bilinear map through
+// its four corners (which lie on the patch), c00 + a e + b f + a b g = 0 with
+// e = c10 - c00, f = c01 - c00, g = c11 - c10 - c01 + c00.  Eliminating a
+// (cross product with e + b g) leaves k2 b^2 + k1 b + k0 = 0; a follows from
+// the better conditioned component.  Falls back to the centre when the
+// quadratic has no usable root; the result is clamped to [0,1]^2.
+template <int P, typename R>
+IVV_HD void bilinear_start(const Patch2<P, R>& q, R& a, R& b) {
+  constexpr int N = P + 1;
+  const R c00x = q.x[0], c00y = q.y[0], c10x = q.x[P], c10y = q.y[P];
+  const R c01x = q.x[P * N], c01y = q.y[P * N], c11x = q.x[P * N + P], c11y = q.y[P * N + P];
+  const R ex = c10x - c00x, ey = c10y - c00y, fx = c01x - c00x, fy = c01y - c00y;
+  const R gx = c11x - c10x - c01x + c00x, gy = c11y - c10y - c01y + c00y;
+  const R k2 = fx * gy - fy * gx;
+  const R k1 = (c00x * gy - c00y * gx) + (fx * ey - fy * ex);
+  const R k0 = c00x * ey - c00y * ex;
+  a = b = R(0.5);
+  R bb;
+  const R scale = fabs(k1) + fabs(k0) + R(1e-30);
+  if (fabs(k2) <= R(1e-6) * scale) {
+    if (k1 == R(0)) return;
+    bb = -k0 / k1;
+  } else {
+    const R disc = k1 * k1 - R(4) * k2 * k0;
+    if (!(disc >= R(0))) return;
+    const R sq = sqrt(disc);
+    const R q1 = R(-0.5) * (k1 + (k1 >= R(0) ? sq : -sq));       // stable pair of roots
+    const R r1 = q1 / k2, r2 = q1 != R(0) ? k0 / q1 : r1;
+    const R d1 = fabs(r1 - clamp01r(r1)), d2 = fabs(r2 - clamp01r(r2));
+    bb = d1 <= d2 ? r1 : r2;
+  }
+  const R dx = ex + bb * gx, dy = ey + bb * gy;
+  const R aa = fabs(dx) >= fabs(dy) ? -(c00x + bb * fx) / dx : -(c00y + bb * fy) / dy;
+  if (!(aa == aa) || !(bb == bb) || fabs(aa) > R(1e30)) return;
+  a = clamp01r(aa);
+  b = clamp01r(bb);
+}
 
 // Accept a root (a,b) of a sub-patch covering [a0,a1] x [b0,b1] of the face
 // patch: inside the sub-patch (tolerance scaled to its size) and inside the
@@ -388,10 +427,11 @@ __host__ __device__ __noinline__ int patch_roots_split(const Patch2<P, R>* q0p, 
 template <int P, typename R>
 IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& iters) {
   if (fixed_jacobian_sign<P, R>(q0)) {
-    // one-to-one patch (common case): Newton from the centre; a solution
-    // outside the patch gets one restart from the nearest patch point
+    // one-to-one patch (common case): Newton from the bilinear start; a
+    // solution outside the patch gets one restart from the nearest patch point
     int nr = 0;
-    R a = R(0.5), b = R(0.5);
+    R a, b;
+    bilinear_start<P, R>(q0, a, b);
 #pragma unroll 1
     for (int attempt = 0; attempt < 2; ++attempt) {
       if (!newton2<P, R>(q0, a, b, iters)) break;

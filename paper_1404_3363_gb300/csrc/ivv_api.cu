@@ -48,7 +48,8 @@ ivv_status cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
-  size_t boxes, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active, counters, total;
+  size_t boxes, gboxes, items, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
+      counters, total;
 };
 
 WsLayout layout(int n_faces, size_t npix, size_t v4) {
@@ -56,6 +57,8 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o += align256(bytes); return at; };
   L.boxes = take(sizeof(int4) * (size_t)std::max(n_faces, 1));
+  L.gboxes = take(sizeof(int4) * (size_t)std::max((n_faces + 31) / 32, 1));
+  L.items = take(sizeof(int2) * ivv::kItemsPerPixel * npix);
   L.frag_tp = take(v4 * ivv::kMaxFrags * npix);
   L.frag_meta = take(sizeof(unsigned) * ivv::kMaxFrags * npix);
   L.frag_count = take(sizeof(int) * npix);
@@ -252,12 +255,19 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   const bool mixed = p.precision == IVV_PREC_MIXED;
   const bool timing = (p.flags & IVV_FLAG_TIMING) != 0;
   IVV_CUDA(cudaMemsetAsync(ws + L.counters, 0, ivv::kCountersBytes, s));
+  ivv::SurfaceWs sw;
+  sw.boxes = (int4*)(ws + L.boxes);
+  sw.gboxes = (int4*)(ws + L.gboxes);
+  sw.items = (int2*)(ws + L.items);
+  sw.cap = (int)std::min<size_t>((size_t)ivv::kItemsPerPixel * npix, 0x7fffffff);
+  sw.n_items = (int*)(ws + L.counters) + ivv::kItemCounter;
+  sw.frag_tp = ws + L.frag_tp;
+  sw.frag_meta = (unsigned*)(ws + L.frag_meta);
+  sw.frag_count = (int*)(ws + L.frag_count);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[0], s));
-  ivv::launch_face_project(V, dev_camera<float>(F), (int4*)(ws + L.boxes), s);
+  ivv::launch_face_project(V, dev_camera<float>(F), sw.boxes, sw.gboxes, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[1], s));
-  ivv::launch_intersect<R>(V, dev_camera<R>(F), dev_camera<double>(F), mixed, stats, (const int4*)(ws + L.boxes),
-                           (V4*)(ws + L.frag_tp), (unsigned*)(ws + L.frag_meta), (int*)(ws + L.frag_count),
-                           v->d_stats, s);
+  ivv::launch_intersect<R>(V, dev_camera<R>(F), dev_camera<double>(F), mixed, stats, sw, v->d_stats, v->num_sms, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[2], s));
   ivv::launch_pair<R>(V, F.w, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
@@ -939,6 +949,7 @@ void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->step_cap = d.step_cap;
   out->rf_newton_iters = d.rf_newton_iters;
   out->rf_unconverged = d.rf_unconverged;
+  out->isect_items = d.isect_items;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;

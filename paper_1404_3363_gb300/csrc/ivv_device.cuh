@@ -60,7 +60,7 @@ struct DevTF {
 struct DevStats {
   unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
       isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap, rf_newton_iters,
-      rf_unconverged;
+      rf_unconverged, isect_items;
   unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
   unsigned int pad;
 };
@@ -330,13 +330,14 @@ __device__ __forceinline__ float4 tf_eval(const float* __restrict__ r, const flo
 // ------------------------------------------------------------- batches
 // One request of a batch.  The batch's pixels are numbered request after
 // request: request rq owns pixels pix0[rq] .. pix0[rq+1]-1 (row-major within
-// its image); its K2 tiles (of the tuned tile shape) are tile0[rq] ..
-// tile0[rq+1]-1, row-major over the image; its volume's faces are face0 .. face0 + n_faces - 1 of the batch's pool and their
-// screen boxes for this camera start at box0.
+// its image); its K2a warp tiles (of the tuned shape) are tile0[rq] ..
+// tile0[rq+1]-1, row-major over the image; its volume's faces are face0 ..
+// face0 + n_faces - 1 of the batch's pool, their screen boxes for this camera
+// start at box0 and their group boxes at gbox0.
 struct DevRequest {
   DevCamera<float> cam;
   DevCamera<double> cam64;
-  int face0, n_faces, box0;
+  int face0, n_faces, box0, gbox0;
   float diag;          // control-point bbox diagonal of the volume
   float ds;            // sample distance
   float4* out;         // caller-owned RGBA image
@@ -397,8 +398,9 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
 }
 
 // Counters block of a render: [0] active pixels, [2] RF sample total, [3]
-// spare; the integrator's queue head at kQueueHeadOff.
+// spare, [4] stage-1 items; the integrator's queue head at kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
+constexpr int kItemCounter = 4;
 constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
@@ -408,12 +410,28 @@ __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, floa
 // ------------------------------------------------------------- launchers
 struct Workspace;   // see ivv_api.cu
 
-void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, cudaStream_t s);
+// Stage-1 buffers of a render: face screen boxes [F], group boxes [ceil(F/32)],
+// the (pixel, patch) item list (cap entries, count at *n_items) and the
+// A-buffer (frag_tp / frag_meta slot-major, frag_count per pixel).
+constexpr int kItemsPerPixel = 16;   // capacity of the (pixel, patch) list per pixel
+constexpr int kBatchFaceBits = 20;   // batch items: request << 20 | pool patch
+constexpr int kGroup = 32;           // patches per group box
+struct SurfaceWs {
+  int4* boxes;
+  int4* gboxes;
+  int2* items;
+  int cap;
+  int* n_items;
+  void* frag_tp;
+  unsigned* frag_meta;
+  int* frag_count;
+};
+
+void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, int4* gboxes, cudaStream_t s);
 
 template <typename R>
 void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, bool mixed,
-                      bool stats, const int4* boxes, typename Vec4T<R>::type* frag_tp, unsigned* frag_meta,
-                      int* frag_count, DevStats* st, cudaStream_t s);
+                      bool stats, const SurfaceWs& w, DevStats* st, int num_sms, cudaStream_t s);
 
 template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
@@ -440,11 +458,14 @@ void launch_integrate(const DevVolume& V, const DevCamera<R>& cam, const DevTF& 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
                        const int* frag_count, float4* pair_in, float4* pair_out, int* pair_block, int* pair_count,
                        int* active, int* n_active, DevStats* st, cudaStream_t s);
-void launch_batch_face_project(const DevVolume& V, const BatchArgs& ba, int max_faces, int4* boxes, cudaStream_t s);
-// tile_w x tile_h in {8x8, 16x8, 16x16}; returns false for another shape.
+void launch_batch_face_project(const DevVolume& V, const BatchArgs& ba, int max_faces, const SurfaceWs& w,
+                               cudaStream_t s);
+// K2a warp tile tile_w x tile_h in {8x4, 4x8, 16x2}; tiles = the batch's
+// count of such tiles (ba.tile0 holds their prefix); returns false for
+// another shape.
 bool launch_batch_intersect(const DevVolume& V, const BatchArgs& ba, int tiles, int tile_w, int tile_h, bool mixed,
-                            bool stats, const int4* boxes, float4* frag_tp, unsigned* frag_meta, int* frag_count,
-                            size_t stride, DevStats* st, cudaStream_t s);
+                            bool stats, const SurfaceWs& w, size_t stride, DevStats* st, int num_sms,
+                            cudaStream_t s);
 void launch_batch_integrate(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a, bool mixed, bool stats,
                             const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
                             const int* active, const int* n_active, int* queue_head, DevStats* st, int grid,

@@ -1,10 +1,11 @@
-// Stage 1 (§4.1): intersections of every pixel ray with the boundary surfaces
-// of every block.  The paper rasterises a view-dependent pixel-accurate
-// tessellation; here every ray is intersected with the Bezier face patches
-// directly (device bodies in k_surface.cuh):
-//   K0 face_project  -- conservative screen box of each face patch.
-//   K2 intersect     -- one CTA per 16x8 screen tile; fragments go to the
-//                       pixel's A-buffer slots (§4.2).
+// Stage 1 (§4.1) of a single frame: intersections of every pixel ray with the
+// boundary surfaces of every block (device bodies in k_surface.cuh):
+//   K0  k0_face_project -- screen boxes of the face patches and of groups of
+//       32 patches.
+//   K2a k2a_cull        -- one warp per 8x4 tile: culling and per-pixel
+//       bounding-box tests; (pixel, patch) items to a global list.
+//   K2b k2b_roots       -- one thread per item: hull test, roots, fragments
+//       into the pixel's A-buffer slots (§4.2).
 #include <cuda_runtime.h>
 
 #include "k_surface.cuh"
@@ -13,62 +14,106 @@ namespace ivv {
 
 namespace {
 
+constexpr int kCullWarps = 8;        // warps (8x4 tiles) per K2a CTA
+constexpr int kRootsThreads = 128;
+
 template <int P>
-__global__ void k0_face_project(DevVolume V, DevCamera<float> cam, int4* __restrict__ boxes) {
+__global__ void k0_face_project(DevVolume V, DevCamera<float> cam, int4* __restrict__ boxes,
+                                int4* __restrict__ gboxes) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= V.n_faces) return;
-  boxes[f] = face_box<P>(V, cam, f, V.diag);
+  project_faces<P>(V, cam, f, V.n_faces, 0, V.diag, boxes, gboxes);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kCullWarps) k2a_cull(DevVolume V, DevCamera<R> cam,
+                                                            const int4* __restrict__ boxes,
+                                                            const int4* __restrict__ gboxes, int2* __restrict__ items,
+                                                            int cap, int* __restrict__ n_items,
+                                                            int* __restrict__ frag_count, DevStats* __restrict__ st) {
+  const int tiles_x = (cam.w + 7) / 8;
+  const int tiles = tiles_x * ((cam.h + 3) / 4);
+  const int t = blockIdx.x * kCullWarps + (threadIdx.x >> 5);
+  if (t >= tiles) return;                      // whole warps
+  cull_warp_tile<R, 8, 4>(V, cam, t % tiles_x, t / tiles_x, 0, V.n_faces, boxes, gboxes, V.diag, 0, 0, items, cap,
+                          n_items, frag_count, st);
 }
 
 template <int P, typename R, bool MIXED, bool STATS>
-__global__ void __launch_bounds__(kTileW * kTileH, 4) k2_intersect(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
-                                                       const int4* __restrict__ boxes,
-                                                       typename Vec4T<R>::type* __restrict__ frag_tp,
-                                                       unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
-                                                       DevStats* __restrict__ st) {
-  const int tiles_x = (cam.w + kTileW - 1) / kTileW;
-  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-  k2_tile<P, R, MIXED, STATS, kTileW, kTileH>(V, cam, cam64, tx, ty, 0, V.n_faces, boxes, V.diag, 0,
-                                              (size_t)cam.w * cam.h, frag_tp, frag_meta, frag_count, st);
+__global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCamera<R> cam,
+                                                              DevCamera<double> cam64,
+                                                              const int2* __restrict__ items,
+                                                              const int* __restrict__ n_items, int cap,
+                                                              typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                              unsigned* __restrict__ frag_meta,
+                                                              int* __restrict__ frag_count,
+                                                              DevStats* __restrict__ st) {
+  const int n = min(*n_items, cap);
+  const size_t stride = (size_t)cam.w * cam.h;
+  unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
+  int c_newton = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int2 it = __ldg(items + i);
+    const int xw = it.x % cam.w, yw = it.x / cam.w;
+    const int px = cam.x0 + xw, py = cam.y0 + yw;
+    R o[3], d[3];
+    make_ray<R>(cam, px, py, o, d);
+    roots_item<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
+                                   frag_count, st, c_tests, c_newton, c_fp64, c_frag);
+  }
+  roots_counters<STATS>(c_tests, c_newton, c_fp64, c_frag, n, st);
+}
+
+template <int P, typename R, bool MIXED, bool STATS>
+void launch_k2b(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, const SurfaceWs& w,
+                DevStats* st, int num_sms, cudaStream_t s) {
+  typedef typename Vec4T<R>::type V4;
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2b_roots<P, R, MIXED, STATS>, kRootsThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  k2b_roots<P, R, MIXED, STATS><<<num_sms * per_sm, kRootsThreads, 0, s>>>(
+      V, cam, cam64, w.items, w.n_items, w.cap, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
 }
 
 }  // namespace
 
-void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, cudaStream_t s) {
+void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, int4* gboxes,
+                         cudaStream_t s) {
   if (V.n_faces <= 0) return;
   if (V.P == 2)
-    k0_face_project<2><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes);
+    k0_face_project<2><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes, gboxes);
   else
-    k0_face_project<3><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes);
+    k0_face_project<3><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes, gboxes);
 }
 
 template <typename R>
 void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, bool mixed,
-                      bool stats, const int4* boxes, typename Vec4T<R>::type* frag_tp, unsigned* frag_meta,
-                      int* frag_count, DevStats* st, cudaStream_t s) {
-  const int tiles = ((cam.w + kTileW - 1) / kTileW) * ((cam.h + kTileH - 1) / kTileH);
+                      bool stats, const SurfaceWs& w, DevStats* st, int num_sms, cudaStream_t s) {
+  const int tiles = ((cam.w + 7) / 8) * ((cam.h + 3) / 4);
   if (tiles <= 0) return;
-#define IVV_K2(PP, MM, SS) \
-  k2_intersect<PP, R, MM, SS><<<tiles, kTileW * kTileH, 0, s>>>(V, cam, cam64, boxes, frag_tp, frag_meta, frag_count, st)
+  k2a_cull<R><<<(tiles + kCullWarps - 1) / kCullWarps, 32 * kCullWarps, 0, s>>>(
+      V, cam, w.boxes, w.gboxes, w.items, w.cap, w.n_items, w.frag_count, st);
+#define IVV_K2B(PP, MM, SS) launch_k2b<PP, R, MM, SS>(V, cam, cam64, w, st, num_sms, s)
   if constexpr (sizeof(R) == 4) {
     if (V.P == 2) {
-      if (mixed) { if (stats) IVV_K2(2, true, true); else IVV_K2(2, true, false); }
-      else { if (stats) IVV_K2(2, false, true); else IVV_K2(2, false, false); }
+      if (mixed) { if (stats) IVV_K2B(2, true, true); else IVV_K2B(2, true, false); }
+      else { if (stats) IVV_K2B(2, false, true); else IVV_K2B(2, false, false); }
     } else {
-      if (mixed) { if (stats) IVV_K2(3, true, true); else IVV_K2(3, true, false); }
-      else { if (stats) IVV_K2(3, false, true); else IVV_K2(3, false, false); }
+      if (mixed) { if (stats) IVV_K2B(3, true, true); else IVV_K2B(3, true, false); }
+      else { if (stats) IVV_K2B(3, false, true); else IVV_K2B(3, false, false); }
     }
   } else {
     (void)mixed;
-    if (V.P == 2) { if (stats) IVV_K2(2, false, true); else IVV_K2(2, false, false); }
-    else { if (stats) IVV_K2(3, false, true); else IVV_K2(3, false, false); }
+    if (V.P == 2) { if (stats) IVV_K2B(2, false, true); else IVV_K2B(2, false, false); }
+    else { if (stats) IVV_K2B(3, false, true); else IVV_K2B(3, false, false); }
   }
-#undef IVV_K2
+#undef IVV_K2B
 }
 
 template void launch_intersect<float>(const DevVolume&, const DevCamera<float>&, const DevCamera<double>&, bool,
-                                      bool, const int4*, float4*, unsigned*, int*, DevStats*, cudaStream_t);
+                                      bool, const SurfaceWs&, DevStats*, int, cudaStream_t);
 template void launch_intersect<double>(const DevVolume&, const DevCamera<double>&, const DevCamera<double>&, bool,
-                                       bool, const int4*, Dbl4*, unsigned*, int*, DevStats*, cudaStream_t);
+                                       bool, const SurfaceWs&, DevStats*, int, cudaStream_t);
 
 }  // namespace ivv

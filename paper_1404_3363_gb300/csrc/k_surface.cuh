@@ -1,17 +1,23 @@
 // Stage 1 (§4.1) device bodies shared by the single-frame kernels
-// (k_surface.cu) and the batched kernels (k_batch.cu).
-//   face_box    -- conservative screen box of one face patch from its control
-//                  points (convex hull property).
-//   k2_tile     -- one CTA per TW x TH screen tile: cull the face boxes
-//                  against the tile and stage the surviving patches in shared
-//                  memory; every pixel tests its ray against each staged
-//                  patch's screen box and bounding box and queues the
-//                  survivors in a tile work list, which all threads then drain
-//                  densely: every root of S(a,b) = o + t d (hull test,
-//                  certified single-root Newton or subdivision; isect.cuh)
-//                  becomes a fragment appended to the pixel's slots through a
-//                  per-pixel atomic counter in shared memory (the A-buffer of
-//                  §4.2).
+// (k_surface.cu) and the batched kernels (k_batch.cu).  The paper rasterises
+// a view-dependent pixel-accurate tessellation of the boundary surfaces; here
+// every pixel ray is intersected with the Bezier face patches directly, in
+// three steps:
+//   K0  face_box / group box -- conservative screen box of each face patch
+//       from its control points (convex hull property) and the union box of
+//       each group of 32 consecutive patches (neighbours on one block face).
+//   K2a cull_warp_tile -- one warp per 8x4-pixel tile (one lane per pixel):
+//       group boxes, then patch boxes against the tile, then each lane's own
+//       ray against the patch's screen box, bounding box and oriented box;
+//       survivors are appended as (pixel, patch) items to a global list,
+//       patch by patch, so that consecutive items share a patch.
+//   K2b roots_item -- one thread per item: the patch's control points in the
+//       ray's frame, hull test, every root of S(a,b) = o + t d (certified
+//       single-root Newton or subdivision; isect.cuh), and each root appended
+//       as a fragment to the pixel's slots through a per-pixel atomic counter
+//       (the A-buffer of §4.2).
+// No step waits on another warp: K2a is short and light, K2b carries the
+// register-heavy root finding without barriers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +32,37 @@ __device__ __forceinline__ int4 face_box(const DevVolume& V, const DevCamera<flo
   return face_screen_box<NN>(cam, V.face32 + (size_t)f * NN, V.faces[f].org, diag);
 }
 
+__device__ __forceinline__ bool box_nonempty(int4 b) { return b.x <= b.z && b.y <= b.w; }
+__device__ __forceinline__ bool box_meets(int4 b, int x0, int y0, int x1, int y1) {
+  return b.x <= x1 && b.z >= x0 && b.y <= y1 && b.w >= y0;
+}
+
+// Screen box of local patch f (face0 + f of V) into boxes[f]; lane 0 of each
+// warp writes the union of its 32 patches' boxes into gboxes[f / 32].  All 32
+// lanes of the warp must call it (f = 32-aligned warp base + lane).
+template <int P>
+__device__ __forceinline__ void project_faces(const DevVolume& V, const DevCamera<float>& cam, int f, int nface,
+                                              int face0, float diag, int4* __restrict__ boxes,
+                                              int4* __restrict__ gboxes) {
+  int4 b = make_int4(1, 1, 0, 0);
+  if (f < nface) {
+    b = face_box<P>(V, cam, face0 + f, diag);
+    boxes[f] = b;
+  }
+  const bool ok = box_nonempty(b);
+  int x0 = ok ? b.x : 0x7fffffff, y0 = ok ? b.y : 0x7fffffff;
+  int x1 = ok ? b.z : -0x7fffffff, y1 = ok ? b.w : -0x7fffffff;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+  }
+  if ((threadIdx.x & 31) == 0 && f < nface)
+    gboxes[f / kGroup] = x0 <= x1 ? make_int4(x0, y0, x1, y1) : make_int4(1, 1, 0, 0);
+}
+
 // FP64 polish of a grazing hit (mixed precision), kept out of line.
 template <int P>
 __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const DevCamera<double>& cam64, int px, int py,
@@ -36,196 +73,161 @@ __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const Dev
   refine_hit_fp64<P, Dbl4>(V.face64 + (size_t)face * (P + 1) * (P + 1), m.org, o, d, a, b, t);
 }
 
-// Fragments of tile (tx, ty) of the window of `cam`.  Faces face0 ..
-// face0+nface-1 of V are candidates; boxes[f] is the screen box of face
-// face0+f.  Pixel (xw, yw) of the window writes its slots at index
-// slot * stride + pix0 + yw * cam.w + xw and its count at pix0 + yw * cam.w + xw.
-template <int P, typename R, bool MIXED, bool STATS, int TW, int TH>
-__device__ __forceinline__ void k2_tile(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64,
-                                        int tx, int ty, int face0, int nface, const int4* __restrict__ boxes,
-                                        float diag, size_t pix0, size_t stride,
-                                        typename Vec4T<R>::type* __restrict__ frag_tp,
-                                        unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
-                                        DevStats* __restrict__ st) {
-  typedef typename Vec4T<R>::type V4;
-  constexpr int N = P + 1, NN = N * N;
-  constexpr int CH = 32;                       // face patches staged per round
-  constexpr int kThreads = TW * TH;            // one thread per tile pixel
-  static_assert(kThreads % 32 == 0 && kThreads <= 1024, "tile must be whole warps");
-  __shared__ int s_cand[kThreads];
-  __shared__ int s_wcnt[kThreads / 32];
-  __shared__ V4 s_cp[CH * NN];
-  __shared__ FaceMeta s_meta[CH];
-  __shared__ int4 s_box[CH];
-  __shared__ R s_o[kThreads][3], s_d[kThreads][3];
-  __shared__ unsigned short s_work[kThreads * CH];   // (pixel << 5) | staged face
-  __shared__ int s_nwork;
-  __shared__ int s_count[kThreads];                  // fragments per tile pixel
-  (void)N;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int xw = tx * TW + (tid % TW), yw = ty * TH + (tid / TW);
+// K2a body: tile (tx, ty) of TW x TH = 32 pixels of the window of cam, one
+// lane per pixel; candidate patches face0 .. face0+nface-1 (their boxes and
+// group boxes for this camera in boxes / gboxes).  Items carry the pixel's
+// index pix0 + yw * cam.w + xw and tag | (the patch's index in V) (batches
+// put the request into the high bits of tag).  Zeroes the fragment counters
+// of the tile's pixels.
+template <typename R, int TW, int TH>
+__device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCamera<R>& cam, int tx, int ty, int face0,
+                                               int nface, const int4* __restrict__ boxes,
+                                               const int4* __restrict__ gboxes, float diag, int pix0, int tag,
+                                               int2* __restrict__ items, int cap, int* __restrict__ n_items,
+                                               int* __restrict__ frag_count, DevStats* __restrict__ st) {
+  static_assert(TW * TH == 32, "one lane per pixel");
+  const int lane = threadIdx.x & 31;
+  const int xw = tx * TW + (lane % TW), yw = ty * TH + (lane / TW);
   const bool valid = xw < cam.w && yw < cam.h;
   const int px = cam.x0 + xw, py = cam.y0 + yw;
+  const int pix = pix0 + yw * cam.w + xw;
+  if (valid) frag_count[pix] = 0;
   const int rx0 = cam.x0 + tx * TW, ry0 = cam.y0 + ty * TH;
   const int rx1 = min(rx0 + TW - 1, cam.x0 + cam.w - 1), ry1 = min(ry0 + TH - 1, cam.y0 + cam.h - 1);
-
   R o[3], d[3], inv_d[3];
   make_ray<R>(cam, px, py, o, d);
 #pragma unroll
   for (int r = 0; r < 3; ++r) inv_d[r] = R(1) / d[r];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    s_o[tid][r] = o[r];
-    s_d[tid][r] = d[r];
-  }
-  s_count[tid] = 0;
-  if (tid == 0) s_nwork = 0;
-  const R hull_pad = R(1e-6) * R(diag);
-  int c_newton = 0;
-  unsigned long long c_tests = 0, c_fp64 = 0;
-
-  for (int base = 0; base < nface; base += kThreads) {
-    // ---- faces whose screen box meets the tile, in index order
-    const int f = base + tid;
-    bool keep = false;
-    int4 fb = make_int4(1, 1, 0, 0);
-    if (f < nface) {
-      fb = __ldg(boxes + f);
-      keep = fb.x <= rx1 && fb.z >= rx0 && fb.y <= ry1 && fb.w >= ry0;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_wcnt[warp] = __popc(bal);
-    __syncthreads();
-    int off = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      const int c = s_wcnt[w];
-      off += (w < warp) ? c : 0;
-      total += c;
-    }
-    if (keep) s_cand[off + __popc(bal & ((1u << lane) - 1u))] = f;
-    __syncthreads();
-    for (int c0 = 0; c0 < total; c0 += CH) {
-      const int nst = min(CH, total - c0);
-      for (int q = tid; q < nst * NN; q += kThreads) {
-        const int fi = face0 + s_cand[c0 + q / NN];
-        if constexpr (sizeof(R) == 4) {
-          s_cp[q] = __ldg(V.face32 + (size_t)fi * NN + (q % NN));
-        } else {
-          s_cp[q] = V.face64[(size_t)fi * NN + (q % NN)];
-        }
-      }
-      for (int q = tid; q < nst; q += kThreads) {
-        s_meta[q] = V.faces[face0 + s_cand[c0 + q]];
-        s_box[q] = __ldg(boxes + s_cand[c0 + q]);
-      }
-      __syncthreads();
-      // ---- cheap per-pixel tests; survivors go to the tile's work list
-      for (int q = 0; q < nst; ++q) {
+  const R pad = R(1e-6) * R(diag);
+  const int ngroups = (nface + kGroup - 1) / kGroup;
+  unsigned dropped = 0;
+  for (int g0 = 0; g0 < ngroups; g0 += 32) {
+    const int g = g0 + lane;
+    const bool ghit = g < ngroups && box_meets(__ldg(gboxes + g), rx0, ry0, rx1, ry1);
+    unsigned gm = __ballot_sync(0xffffffffu, ghit);
+    while (gm) {
+      const int gg = g0 + __ffs(gm) - 1;
+      gm &= gm - 1;
+      const int f = gg * kGroup + lane;
+      int4 fb = make_int4(1, 1, 0, 0);
+      if (f < nface) fb = __ldg(boxes + f);
+      unsigned fm = __ballot_sync(0xffffffffu, box_meets(fb, rx0, ry0, rx1, ry1));
+      while (fm) {
+        const int fl = __ffs(fm) - 1;
+        fm &= fm - 1;
+        const int4 b = make_int4(__shfl_sync(0xffffffffu, fb.x, fl), __shfl_sync(0xffffffffu, fb.y, fl),
+                                 __shfl_sync(0xffffffffu, fb.z, fl), __shfl_sync(0xffffffffu, fb.w, fl));
+        const int fi = face0 + gg * kGroup + fl;
         bool pass = false;
-        if (valid) {
-          const int4 b = s_box[q];
-          pass = px >= b.x && px <= b.z && py >= b.y && py <= b.w &&
-                 ray_box<R>(o, inv_d, s_meta[q].lo, s_meta[q].hi, hull_pad) &&
-                 ray_obb<R>(o, d, s_meta[q], R(4) * hull_pad);
+        if (valid && px >= b.x && px <= b.z && py >= b.y && py <= b.w) {
+          const FaceMeta& m = V.faces[fi];
+          pass = ray_box<R>(o, inv_d, m.lo, m.hi, pad) && ray_obb<R>(o, d, m, R(4) * pad);
         }
-        const unsigned wb = __ballot_sync(0xffffffffu, pass);
-        if (wb) {
-          int wbase = 0;
-          if (lane == 0) wbase = atomicAdd(&s_nwork, __popc(wb));
-          wbase = __shfl_sync(0xffffffffu, wbase, 0);
-          if (pass) s_work[wbase + __popc(wb & ((1u << lane) - 1u))] = (unsigned short)((tid << 5) | q);
-        }
-      }
-      __syncthreads();
-      // ---- ray/patch roots, one (pixel, face) item per thread
-      const int nwork = s_nwork;
-      for (int w = tid; w < nwork; w += kThreads) {
-        const int item = s_work[w];
-        const int pl = item >> 5, qf = item & 31;
-        const FaceMeta& m = s_meta[qf];
-        R ro[3], rd[3], e1[3], e2[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          ro[r] = s_o[pl][r];
-          rd[r] = s_d[pl][r];
-        }
-        ray_frame<R>(rd, e1, e2);
-        const int fi = face0 + s_cand[c0 + qf];
-        R org[3], pa0, pa1, pb0, pb1;
-        if constexpr (sizeof(R) == 8) {
-          const FaceMeta64 m64 = V.faces64[fi];
-          org[0] = m64.org[0]; org[1] = m64.org[1]; org[2] = m64.org[2];
-          pa0 = m64.a0; pa1 = m64.a1; pb0 = m64.b0; pb1 = m64.b1;
-        } else {
-          org[0] = m.org[0]; org[1] = m.org[1]; org[2] = m.org[2];
-          pa0 = m.a0; pa1 = m.a1; pb0 = m.b0; pb1 = m.b1;
-        }
-        const V4* cp = s_cp + qf * NN;
-        Patch2<P, R> pq;
-        project_patch<P, R, V4>(cp, org, ro, e1, e2, pq);
-        if (!hull_has_origin<P, R>(pq, hull_pad)) continue;
-        if (STATS) ++c_tests;
-        R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
-        const int nr = patch_roots<P, R>(pq, hull_pad, ra, rb, c_newton);
-        const int ppx = rx0 + (pl % TW), ppy = ry0 + (pl / TW);
-        const size_t ppix = pix0 + (size_t)((ppy - cam.y0) * cam.w + (ppx - cam.x0));
-        for (int k = 0; k < nr; ++k) {
-          R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
-          R t, pp[3], cosang;
-          bool front;
-          make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, ro, rd, a, b, t, front, pp, cosang);
-          if constexpr (MIXED) {
-            if (cosang < R(0.2)) {
-              double a64 = a, b64 = b, t64 = t;
-              refine_fp64<P>(V, fi, cam64, ppx, ppy, a64, b64, t64);
-              a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
-              b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
-              t = R(t64);
-              const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-              const FaceMeta64 m64 = V.faces64[fi];
-              pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
-              pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
-              if (STATS) ++c_fp64;
-            }
-          }
-          if (!(t > R(0))) continue;
-          const int slot = atomicAdd(&s_count[pl], 1);
-          if (slot < kMaxFrags) {
-            V4 rec;
-            rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
-            frag_tp[(size_t)slot * stride + ppix] = rec;
-            frag_meta[(size_t)slot * stride + ppix] =
-                ((unsigned)m.block << 4) | ((unsigned)m.face << 1) | (front ? 1u : 0u);
-          } else {
-            atomicAdd(&st->abuf_overflow, 1ull);
+        const unsigned pm = __ballot_sync(0xffffffffu, pass);
+        if (pm) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(n_items, __popc(pm));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const int at = base + __popc(pm & ((1u << lane) - 1u));
+          if (pass) {
+            if (at < cap)
+              items[at] = make_int2(pix, tag | fi);
+            else
+              ++dropped;
           }
         }
       }
-      __syncthreads();
-      if (tid == 0) s_nwork = 0;
-      __syncthreads();
     }
   }
-  const int nfrag = min(s_count[tid], kMaxFrags);
-  if (valid) frag_count[pix0 + (size_t)(yw * cam.w + xw)] = nfrag;
-  if (STATS) {
-    unsigned long long nf = valid ? (unsigned long long)nfrag : 0ull;
-    unsigned long long cn = (unsigned long long)c_newton;
+  if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
+}
+
+// K2b body: item (pixel, patch) with the pixel's ray (o, d) for pixel
+// (px, py) of cam64's image; fragments at slot * stride + pix.
+template <int P, typename R, bool MIXED, bool STATS>
+__device__ __forceinline__ void roots_item(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
+                                           int px, int py, const R o[3], const R d[3], float diag, size_t stride,
+                                           typename Vec4T<R>::type* __restrict__ frag_tp,
+                                           unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
+                                           DevStats* __restrict__ st, unsigned long long& c_tests, int& c_newton,
+                                           unsigned long long& c_fp64, unsigned long long& c_frag) {
+  typedef typename Vec4T<R>::type V4;
+  constexpr int NN = (P + 1) * (P + 1);
+  const R pad = R(1e-6) * R(diag);
+  R e1[3], e2[3];
+  ray_frame<R>(d, e1, e2);
+  const FaceMeta& m = V.faces[fi];
+  R org[3], pa0, pa1, pb0, pb1;
+  const V4* cp;
+  if constexpr (sizeof(R) == 8) {
+    const FaceMeta64 m64 = V.faces64[fi];
+    org[0] = m64.org[0]; org[1] = m64.org[1]; org[2] = m64.org[2];
+    pa0 = m64.a0; pa1 = m64.a1; pb0 = m64.b0; pb1 = m64.b1;
+    cp = V.face64 + (size_t)fi * NN;
+  } else {
+    org[0] = m.org[0]; org[1] = m.org[1]; org[2] = m.org[2];
+    pa0 = m.a0; pa1 = m.a1; pb0 = m.b0; pb1 = m.b1;
+    cp = V.face32 + (size_t)fi * NN;
+  }
+  Patch2<P, R> pq;
+  project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
+  if (!hull_has_origin<P, R>(pq, pad)) return;
+  if (STATS) ++c_tests;
+  R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
+  const int nr = patch_roots<P, R>(pq, pad, ra, rb, c_newton);
+  const int face = m.face, block = m.block;
+  for (int k = 0; k < nr; ++k) {
+    R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
+    R t, pp[3], cosang;
+    bool front;
+    make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
+    if constexpr (MIXED) {
+      if (cosang < R(0.2)) {
+        double a64 = a, b64 = b, t64 = t;
+        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
+        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
+        t = R(t64);
+        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+        const FaceMeta64 m64 = V.faces64[fi];
+        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
+        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        if (STATS) ++c_fp64;
+      }
+    }
+    if (!(t > R(0))) continue;
+    const int slot = atomicAdd(frag_count + pix, 1);
+    if (slot < kMaxFrags) {
+      V4 rec;
+      rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
+      frag_tp[(size_t)slot * stride + pix] = rec;
+      frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
+      if (STATS) ++c_frag;
+    } else {
+      atomicAdd(&st->abuf_overflow, 1ull);
+    }
+  }
+}
+
+// Counters of K2b, one atomic per warp; n = items of the launch.
+template <bool STATS>
+__device__ __forceinline__ void roots_counters(unsigned long long c_tests, int c_newton, unsigned long long c_fp64,
+                                               unsigned long long c_frag, int n, DevStats* __restrict__ st) {
+  if (!STATS) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->isect_items, (unsigned long long)n);
+  unsigned long long cn = (unsigned long long)c_newton;
 #pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-      c_tests += __shfl_down_sync(0xffffffffu, c_tests, o2);
-      cn += __shfl_down_sync(0xffffffffu, cn, o2);
-      c_fp64 += __shfl_down_sync(0xffffffffu, c_fp64, o2);
-      nf += __shfl_down_sync(0xffffffffu, nf, o2);
-    }
-    if (lane == 0) {
-      atomicAdd(&st->isect_tests, c_tests);
-      atomicAdd(&st->isect_newton, cn);
-      atomicAdd(&st->fp64_solves, c_fp64);
-      atomicAdd(&st->fragments, nf);
-    }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    c_tests += __shfl_down_sync(0xffffffffu, c_tests, o2);
+    cn += __shfl_down_sync(0xffffffffu, cn, o2);
+    c_fp64 += __shfl_down_sync(0xffffffffu, c_fp64, o2);
+    c_frag += __shfl_down_sync(0xffffffffu, c_frag, o2);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&st->isect_tests, c_tests);
+    atomicAdd(&st->isect_newton, cn);
+    atomicAdd(&st->fp64_solves, c_fp64);
+    atomicAdd(&st->fragments, c_frag);
   }
 }
 

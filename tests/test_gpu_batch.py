@@ -108,8 +108,8 @@ def test_tile_shapes_give_identical_images(ivv, pool):
     b = _batch(ivv, gpu, small)
     base = [o.clone() for o in b.render()]
     t = b.tuning
-    assert (t["tile_w"], t["tile_h"], t["step_samples"]) == (16, 8, 8)
-    for tw, th in [(8, 8), (16, 16), (16, 8)]:
+    assert (t["tile_w"], t["tile_h"], t["step_samples"]) == (8, 4, 8)
+    for tw, th in [(4, 8), (16, 2), (8, 4)]:
         b.tuning = dict(t, tile_w=tw, tile_h=th)
         outs = b.render()
         torch.cuda.synchronize()
@@ -165,7 +165,7 @@ def test_autotune_picks_a_valid_shape(ivv, pool):
     small = _small(reqs, [(128, 96), (96, 128)], 6)
     b = _batch(ivv, gpu, small)
     best, ms = b.autotune(reps=1)
-    assert (best["tile_w"], best["tile_h"]) in [(16, 8), (8, 8), (16, 16)]
+    assert (best["tile_w"], best["tile_h"]) in [(8, 4), (4, 8), (16, 2)]
     assert best["step_samples"] in (4, 8, 16) and 1 <= best["k5_ctas_per_sm"] <= 4
     assert ms > 0 and b.tuning == best and b.info()["graph_ready"]
     outs = b.render()
@@ -218,7 +218,7 @@ def test_batch_argument_errors(ivv, pool):
         ivv.Batch([item], outputs=[bad])
     b = ivv.Batch([item])
     with pytest.raises(ivv.IvvError):
-        b.tuning = dict(b.tuning, tile_w=32)
+        b.tuning = dict(b.tuning, tile_w=16, tile_h=8)
     with pytest.raises(ivv.IvvError):
         b.tuning = dict(b.tuning, step_samples=5)
     with pytest.raises(ivv.IvvError):

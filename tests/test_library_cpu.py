@@ -93,6 +93,31 @@ def test_invalid_descriptions_are_rejected(lib):
     assert status_of([good], mode=7) == 1
 
 
+def _header_struct_fields(name):
+    import re
+    src = open(ivv.HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # declarator names: identifiers followed by an optional [n] and a comma or the end
+        names = re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])?\s*(?:,|$)", decl)
+        out += [n for n in names if n not in ("const", "double", "float", "int", "unsigned", "long", "void")]
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("ivv_stats", "Stats"), ("ivv_render_params", "RenderParams"),
+                                          ("ivv_camera", "Camera"), ("ivv_request", "Request"),
+                                          ("ivv_batch_tuning", "BatchTuning")])
+def test_binding_structs_match_header(cname, pyname):
+    """ctypes mirrors of the header's structs: same fields in the same order."""
+    fields = [n for n, _ in getattr(ivv, pyname)._fields_]
+    assert fields == _header_struct_fields(cname), cname
+
+
 def test_batch_entry_points_reject_null_arguments(lib):
     """The batch calls validate their arguments before any CUDA call."""
     import ctypes as C
