@@ -396,11 +396,18 @@ def run_batch(args):
     from paper_1404_3363_gb300 import ivv, scenes
 
     vols, reqs = scenes.batch_requests()
+    if args.only_volume is not None:
+        reqs = [q for q in reqs if q.volume == args.only_volume]
+    if args.requests:
+        reqs = reqs[:args.requests]
     gpu = [ivv.volume_for(v) for v in vols]
     items = [(gpu[q.volume], q.camera, q.width, q.height, q.tf) for q in reqs]
     b = ivv.Batch(items)
     npix = b.info()["n_pixels"]
-    tuning, tune_ms, tune_src = autotune.tuned(b, items)
+    if args.no_autotune:
+        tuning, tune_ms, tune_src = b.tuning, None, "default"
+    else:
+        tuning, tune_ms, tune_src = autotune.tuned(b, items)
     stream = torch.cuda.current_stream()
 
     b.reset_stats()
@@ -473,7 +480,9 @@ def run_batch(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch64"][2], "requests": len(reqs), "pixels": npix,
+            "config": {"workload": WORKLOADS["batch64"][2] + (
+                           "" if len(reqs) == 64 else " (subset: %d requests)" % len(reqs)),
+                       "requests": len(reqs), "pixels": npix,
                        "tuning": tuning, "tuning_source": tune_src, "autotune_ms": tune_ms,
                        "l2": "inputs larger than L2 (%.1f GB workspace)" % (b.info()["workspace_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -504,6 +513,9 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--ref-stride", type=int, default=96)
     ap.add_argument("--workload", default="bar1080", choices=sorted(WORKLOADS))
+    ap.add_argument("--requests", type=int, default=0, help="batch64: keep the first N requests (0: all)")
+    ap.add_argument("--only-volume", type=int, default=None, help="batch64: keep the requests of one volume")
+    ap.add_argument("--no-autotune", action="store_true", help="batch64: default launch shapes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

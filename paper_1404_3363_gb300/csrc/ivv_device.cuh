@@ -398,9 +398,11 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
 }
 
 // Counters block of a render: [0] active pixels, [2] RF sample total, [3]
-// spare, [4] stage-1 items; the integrator's queue head at kQueueHeadOff.
+// spare, [4] stage-1 items, [5] their hand-out head; the integrator's queue
+// head at kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
 constexpr int kItemCounter = 4;
+constexpr int kItemHead = 5;         // next stage-1 item to hand out (K2b)
 constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {

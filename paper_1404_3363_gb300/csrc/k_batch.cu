@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(32 * kCullWarps) kb2a_cull(DevVolume V, BatchA
 template <int P, bool MIXED, bool STATS>
 __global__ void __launch_bounds__(kRootsThreads, 4) kb2b_roots(DevVolume V, BatchArgs ba,
                                                                const int2* __restrict__ items,
-                                                               const int* __restrict__ n_items, int cap,
+                                                               int* __restrict__ n_items, int cap,
                                                                float4* __restrict__ frag_tp,
                                                                unsigned* __restrict__ frag_meta,
                                                                int* __restrict__ frag_count, size_t stride,
@@ -53,7 +53,11 @@ __global__ void __launch_bounds__(kRootsThreads, 4) kb2b_roots(DevVolume V, Batc
   const int n = min(*n_items, cap);
   unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (;;) {                                   // warps take 32 consecutive items at a time
+    const int base = take_items(n_items, n);
+    if (base >= n) break;
+    const int i = base + (int)(threadIdx.x & 31);
+    if (i >= n) continue;
     const int2 it = __ldg(items + i);
     const int rq = (int)((unsigned)it.y >> kBatchFaceBits);
     const int fi = it.y & ((1 << kBatchFaceBits) - 1);

@@ -42,7 +42,7 @@ template <int P, typename R, bool MIXED, bool STATS>
 __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCamera<R> cam,
                                                               DevCamera<double> cam64,
                                                               const int2* __restrict__ items,
-                                                              const int* __restrict__ n_items, int cap,
+                                                              int* __restrict__ n_items, int cap,
                                                               typename Vec4T<R>::type* __restrict__ frag_tp,
                                                               unsigned* __restrict__ frag_meta,
                                                               int* __restrict__ frag_count,
@@ -51,7 +51,11 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCa
   const size_t stride = (size_t)cam.w * cam.h;
   unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (;;) {                                   // warps take 32 consecutive items at a time
+    const int base = take_items(n_items, n);
+    if (base >= n) break;
+    const int i = base + (int)(threadIdx.x & 31);
+    if (i >= n) continue;
     const int2 it = __ldg(items + i);
     const int xw = it.x % cam.w, yw = it.x / cam.w;
     const int px = cam.x0 + xw, py = cam.y0 + yw;

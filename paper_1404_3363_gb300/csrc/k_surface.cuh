@@ -209,6 +209,16 @@ __device__ __forceinline__ void roots_item(const DevVolume& V, const DevCamera<d
   }
 }
 
+// Next 32 consecutive items for the calling warp (all lanes call it), from
+// the hand-out head at n_items[kItemHead - kItemCounter]; returns the first
+// or n when none are left.
+__device__ __forceinline__ int take_items(int* __restrict__ n_items, int n) {
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = atomicAdd(n_items + (kItemHead - kItemCounter), 32);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base < n ? base : n;
+}
+
 // Counters of K2b, one atomic per warp; n = items of the launch.
 template <bool STATS>
 __device__ __forceinline__ void roots_counters(unsigned long long c_tests, int c_newton, unsigned long long c_fp64,
