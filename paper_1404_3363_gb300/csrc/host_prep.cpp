@@ -101,6 +101,39 @@ double det3(const double J[3][3]) {
 // Oriented bounding box of a face patch's control points (relative to org):
 // axes from the patch tangents at its centre, extents from the control
 // points, padded by a relative 1e-6 so the FP32 copy stays conservative.
+// Control points of the piece [t0, t1] of a Bezier curve of degree P with
+// points c[0..P] (3-D, stride `stride` doubles between points), in place:
+// de Casteljau at t1 keeps the left part, then at t0 / t1 keeps the right one.
+void bezier_sub_curve(double* c, int P, int stride, double t0, double t1) {
+  double w[4][3], l[4][3];
+  for (int k = 0; k <= P; ++k)
+    for (int r = 0; r < 3; ++r) w[k][r] = c[k * stride + r];
+  for (int r = 0; r < 3; ++r) l[0][r] = w[0][r];
+  for (int lev = 1; lev <= P; ++lev) {
+    for (int k = 0; k + lev <= P; ++k)
+      for (int r = 0; r < 3; ++r) w[k][r] += t1 * (w[k + 1][r] - w[k][r]);
+    for (int r = 0; r < 3; ++r) l[lev][r] = w[0][r];
+  }
+  const double s = t1 > 0 ? t0 / t1 : 0.0;
+  double out[4][3];
+  for (int r = 0; r < 3; ++r) out[P][r] = l[P][r];
+  for (int lev = 1; lev <= P; ++lev) {
+    for (int k = 0; k + lev <= P; ++k)
+      for (int r = 0; r < 3; ++r) l[k][r] += s * (l[k + 1][r] - l[k][r]);
+    for (int r = 0; r < 3; ++r) out[P - lev][r] = l[P - lev][r];
+  }
+  for (int k = 0; k <= P; ++k)
+    for (int r = 0; r < 3; ++r) c[k * stride + r] = out[k][r];
+}
+
+// The sub-patch [a0,a1] x [b0,b1] of a tensor-product Bezier patch with
+// control net net[(bi * (P+1) + ai) * 3 + r], in place.
+void bezier_sub_patch(double* net, int P, double a0, double a1, double b0, double b1) {
+  const int n1 = P + 1;
+  for (int bi = 0; bi < n1; ++bi) bezier_sub_curve(net + (size_t)bi * n1 * 3, P, 3, a0, a1);
+  for (int ai = 0; ai < n1; ++ai) bezier_sub_curve(net + (size_t)ai * 3, P, n1 * 3, b0, b1);
+}
+
 void face_obb(const double* cp, int P, const double org[3], FaceMeta& m) {
   const int n1 = P + 1;
   double b[4], db[4];
@@ -325,7 +358,10 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
   hv.diag = std::sqrt(dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2]);
   if (!(hv.diag > 0)) { err = "degenerate control-point bounding box"; return IVV_ERR_DEGENERATE; }
 
-  // faces: 6 per block, one Bezier patch per element on the face
+  // faces: 6 per block, one Bezier patch per element on the face; a patch
+  // whose control net spans more than diag/6 is cut into k x k sub-patches
+  // (k <= 4, exact de Casteljau extraction) so that every patch is small
+  // against the volume (tight culling boxes, near-planar Newton problems)
   for (int b = 0; b < n_blocks; ++b) {
     const BlockInfo& B = hv.blocks[b];
     for (int f = 0; f < 6; ++f) {
@@ -340,15 +376,9 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
           const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
           const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
           const double* eorg = &hv.elem_org[(size_t)eid * 4];
-          FaceMeta m;
-          m.block = b;
-          m.face = f;
-          const double* ba = &hv.brk[B.brk_off[ad]];
-          const double* bb = &hv.brk[B.brk_off[bd]];
-          FaceMeta64 m64{ba[ea], ba[ea + 1], bb[eb], bb[eb + 1], {0, 0, 0}};
-          m.a0 = (float)m64.a0; m.a1 = (float)m64.a1; m.b0 = (float)m64.b0; m.b1 = (float)m64.b1;
-          double flo[3] = {1e300, 1e300, 1e300}, fhi[3] = {-1e300, -1e300, -1e300};
-          double forg[3] = {0, 0, 0};
+          // the element's face net, absolute, index bi * n1 + ai
+          std::vector<double> net((size_t)n1 * n1 * 3);
+          double nlo[3] = {1e300, 1e300, 1e300}, nhi[3] = {-1e300, -1e300, -1e300};
           for (int bi = 0; bi < n1; ++bi)
             for (int ai = 0; ai < n1; ++ai) {
               int l[3];
@@ -356,27 +386,53 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
               l[ad] = ai;
               l[bd] = bi;
               const double* c = C + ((l[0] * n1 + l[1]) * n1 + l[2]) * 4;
-              double g[3];
-              for (int r = 0; r < 3; ++r) g[r] = eorg[r] + c[r];
-              if (ai == 0 && bi == 0)
-                for (int r = 0; r < 3; ++r) forg[r] = g[r];
               for (int r = 0; r < 3; ++r) {
-                hv.face_cp.push_back(g[r] - forg[r]);
-                flo[r] = std::min(flo[r], g[r]);
-                fhi[r] = std::max(fhi[r], g[r]);
+                const double g = eorg[r] + c[r];
+                net[((size_t)bi * n1 + ai) * 3 + r] = g;
+                nlo[r] = std::min(nlo[r], g);
+                nhi[r] = std::max(nhi[r], g);
               }
-              hv.face_cp.push_back(0.0);
             }
-          for (int r = 0; r < 3; ++r) {
-            // round outward so the float box contains the double box
-            m.lo[r] = std::nextafter((float)flo[r], -1e30f);
-            m.hi[r] = std::nextafter((float)fhi[r], 1e30f);
-            m.org[r] = (float)forg[r];
-            m64.org[r] = forg[r];
-          }
-          face_obb(&hv.face_cp[hv.face_cp.size() - (size_t)n1 * n1 * 4], P, forg, m);
-          hv.faces.push_back(m);
-          hv.faces64.push_back(m64);
+          const double ndiag = std::sqrt((nhi[0] - nlo[0]) * (nhi[0] - nlo[0]) + (nhi[1] - nlo[1]) * (nhi[1] - nlo[1]) +
+                                         (nhi[2] - nlo[2]) * (nhi[2] - nlo[2]));
+          const int k = std::max(1, std::min(4, (int)std::ceil(ndiag / (hv.diag / 6.0) - 1e-9)));
+          const double* ba = &hv.brk[B.brk_off[ad]];
+          const double* bb = &hv.brk[B.brk_off[bd]];
+          for (int sb = 0; sb < k; ++sb)
+            for (int sa = 0; sa < k; ++sa) {
+              std::vector<double> sub = net;
+              if (k > 1) bezier_sub_patch(sub.data(), P, (double)sa / k, (double)(sa + 1) / k, (double)sb / k,
+                                          (double)(sb + 1) / k);
+              FaceMeta m;
+              m.block = b;
+              m.face = f;
+              const double a0 = ba[ea] + (ba[ea + 1] - ba[ea]) * sa / k, a1 = ba[ea] + (ba[ea + 1] - ba[ea]) * (sa + 1) / k;
+              const double b0 = bb[eb] + (bb[eb + 1] - bb[eb]) * sb / k, b1 = bb[eb] + (bb[eb + 1] - bb[eb]) * (sb + 1) / k;
+              FaceMeta64 m64{sa == 0 ? ba[ea] : a0, sa == k - 1 ? ba[ea + 1] : a1, sb == 0 ? bb[eb] : b0,
+                             sb == k - 1 ? bb[eb + 1] : b1, {0, 0, 0}};
+              m.a0 = (float)m64.a0; m.a1 = (float)m64.a1; m.b0 = (float)m64.b0; m.b1 = (float)m64.b1;
+              double flo[3] = {1e300, 1e300, 1e300}, fhi[3] = {-1e300, -1e300, -1e300};
+              double forg[3] = {sub[0], sub[1], sub[2]};
+              for (int q = 0; q < n1 * n1; ++q) {
+                for (int r = 0; r < 3; ++r) {
+                  const double g = sub[(size_t)q * 3 + r];
+                  hv.face_cp.push_back(g - forg[r]);
+                  flo[r] = std::min(flo[r], g);
+                  fhi[r] = std::max(fhi[r], g);
+                }
+                hv.face_cp.push_back(0.0);
+              }
+              for (int r = 0; r < 3; ++r) {
+                // round outward so the float box contains the double box
+                m.lo[r] = std::nextafter((float)flo[r], -1e30f);
+                m.hi[r] = std::nextafter((float)fhi[r], 1e30f);
+                m.org[r] = (float)forg[r];
+                m64.org[r] = forg[r];
+              }
+              face_obb(&hv.face_cp[hv.face_cp.size() - (size_t)n1 * n1 * 4], P, forg, m);
+              hv.faces.push_back(m);
+              hv.faces64.push_back(m64);
+            }
         }
     }
   }
