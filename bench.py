@@ -365,7 +365,7 @@ def run_ours(args):
             "roofline": roofs[0],
             "roofline_kernels": roofs,
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
-                                        "fragments", "isect_items", "isect_tests", "isect_newton")},
+                                        "fragments", "isect_items", "isect_split", "isect_tests", "isect_newton")},
             "max_delta_p": st["max_delta_p"],
             "parity_max_rgba_err_sampled": max_err,
             "clocks": clocks,
@@ -494,7 +494,7 @@ def run_batch(args):
                          "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
                          "flops_per_launch": flops_k5, "ms_per_launch": k5_ms},
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
-                                        "fragments", "isect_items", "isect_tests", "isect_newton")},
+                                        "fragments", "isect_items", "isect_split", "isect_tests", "isect_newton")},
             "parity_max_rgba_err_sampled": max_err,
             "clocks": clocks,
         }

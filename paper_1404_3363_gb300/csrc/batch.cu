@@ -65,7 +65,7 @@ int shape_index(int tw, int th) {
 }
 
 struct BatchLayout {
-  size_t boxes, gboxes, items, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
+  size_t boxes, gboxes, items, slow, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
       counters, total;
 };
 
@@ -76,6 +76,7 @@ BatchLayout batch_layout(size_t n_boxes, size_t n_gboxes, size_t npix) {
   L.boxes = take(sizeof(int4) * std::max<size_t>(n_boxes, 1));
   L.gboxes = take(sizeof(int4) * std::max<size_t>(n_gboxes, 1));
   L.items = take(sizeof(int2) * ivv::kItemsPerPixel * npix);
+  L.slow = take(sizeof(int) * ivv::kItemsPerPixel * npix);
   L.frag_tp = take(sizeof(float4) * ivv::kMaxFrags * npix);
   L.frag_meta = take(sizeof(unsigned) * ivv::kMaxFrags * npix);
   L.frag_count = take(sizeof(int) * npix);
@@ -259,6 +260,7 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
   sw.boxes = (int4*)(ws + L.boxes);
   sw.gboxes = (int4*)(ws + L.gboxes);
   sw.items = (int2*)(ws + L.items);
+  sw.slow = (int*)(ws + L.slow);
   sw.cap = (int)std::min<long long>((long long)ivv::kItemsPerPixel * b->npix, 0x7fffffffll);
   sw.n_items = (int*)(ws + L.counters) + ivv::kItemCounter;
   sw.frag_tp = ws + L.frag_tp;

@@ -421,26 +421,37 @@ __host__ __device__ __noinline__ int patch_roots_split(const Patch2<P, R>* q0p, 
   return nr;
 }
 
+// The common case of the root search of patch_roots: a one-to-one patch
+// (fixed Jacobian sign) holds at most one root, found by Newton from the
+// bilinear start; a solution outside the patch gets one restart from the
+// nearest patch point.  Returns false when the patch needs the subdivision
+// search (sign not fixed, or Newton broke down); otherwise nr roots are in
+// ra, rb.
+template <int P, typename R>
+IVV_HD bool patch_roots_fast(const Patch2<P, R>& q0, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& nr,
+                             int& iters) {
+  nr = 0;
+  if (!fixed_jacobian_sign<P, R>(q0)) return false;
+  R a, b;
+  bilinear_start<P, R>(q0, a, b);
+#pragma unroll 1
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (!newton2<P, R>(q0, a, b, iters)) return false;
+    if (accept_root<R>(a, b, R(0), R(1), R(0), R(1), ra, rb, nr)) return true;
+    if (attempt == 1) return true;       // converged twice outside: no root
+    a = clamp01r(a);
+    b = clamp01r(b);
+  }
+  return true;
+}
+
 // All roots (a,b) in [0,1]^2 (within a tolerance) of the planar patch q0,
 // whose hull is known to contain the origin.  Returns the count
 // (<= kMaxPatchRoots); `iters` accumulates Newton steps.
 template <int P, typename R>
 IVV_HD int patch_roots(const Patch2<P, R>& q0, R pad, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& iters) {
-  if (fixed_jacobian_sign<P, R>(q0)) {
-    // one-to-one patch (common case): Newton from the bilinear start; a
-    // solution outside the patch gets one restart from the nearest patch point
-    int nr = 0;
-    R a, b;
-    bilinear_start<P, R>(q0, a, b);
-#pragma unroll 1
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      if (!newton2<P, R>(q0, a, b, iters)) break;
-      if (accept_root<R>(a, b, R(0), R(1), R(0), R(1), ra, rb, nr)) return nr;
-      if (attempt == 1) return 0;
-      a = clamp01r(a);
-      b = clamp01r(b);
-    }
-  }
+  int nr;
+  if (patch_roots_fast<P, R>(q0, ra, rb, nr, iters)) return nr;
   return patch_roots_split<P, R>(&q0, pad, ra, rb, iters);
 }
 

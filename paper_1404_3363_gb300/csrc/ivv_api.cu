@@ -48,7 +48,7 @@ ivv_status cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
-  size_t boxes, gboxes, items, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
+  size_t boxes, gboxes, items, slow, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
       counters, total;
 };
 
@@ -59,6 +59,7 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
   L.boxes = take(sizeof(int4) * (size_t)std::max(n_faces, 1));
   L.gboxes = take(sizeof(int4) * (size_t)std::max((n_faces + 31) / 32, 1));
   L.items = take(sizeof(int2) * ivv::kItemsPerPixel * npix);
+  L.slow = take(sizeof(int) * ivv::kItemsPerPixel * npix);
   L.frag_tp = take(v4 * ivv::kMaxFrags * npix);
   L.frag_meta = take(sizeof(unsigned) * ivv::kMaxFrags * npix);
   L.frag_count = take(sizeof(int) * npix);
@@ -259,6 +260,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   sw.boxes = (int4*)(ws + L.boxes);
   sw.gboxes = (int4*)(ws + L.gboxes);
   sw.items = (int2*)(ws + L.items);
+  sw.slow = (int*)(ws + L.slow);
   sw.cap = (int)std::min<size_t>((size_t)ivv::kItemsPerPixel * npix, 0x7fffffff);
   sw.n_items = (int*)(ws + L.counters) + ivv::kItemCounter;
   sw.frag_tp = ws + L.frag_tp;
@@ -950,6 +952,7 @@ void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->rf_newton_iters = d.rf_newton_iters;
   out->rf_unconverged = d.rf_unconverged;
   out->isect_items = d.isect_items;
+  out->isect_split = d.isect_split;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;

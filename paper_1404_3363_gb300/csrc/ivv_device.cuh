@@ -60,7 +60,7 @@ struct DevTF {
 struct DevStats {
   unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
       isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap, rf_newton_iters,
-      rf_unconverged, isect_items;
+      rf_unconverged, isect_items, isect_split;
   unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
   unsigned int pad;
 };
@@ -398,11 +398,13 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
 }
 
 // Counters block of a render: [0] active pixels, [2] RF sample total, [3]
-// spare, [4] stage-1 items, [5] their hand-out head; the integrator's queue
-// head at kQueueHeadOff.
+// spare, [4] stage-1 items, [5] their hand-out head, [6] deferred items, [7]
+// their hand-out head; the integrator's queue head at kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
 constexpr int kItemCounter = 4;
 constexpr int kItemHead = 5;         // next stage-1 item to hand out (K2b)
+constexpr int kSlowCounter = 6;      // items deferred to the subdivision search
+constexpr int kSlowHead = 7;         // next deferred item to hand out (K2c)
 constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
@@ -422,6 +424,7 @@ struct SurfaceWs {
   int4* boxes;
   int4* gboxes;
   int2* items;
+  int* slow;          // [cap] items deferred to the subdivision search
   int cap;
   int* n_items;
   void* frag_tp;

@@ -45,12 +45,12 @@ __global__ void __launch_bounds__(32 * kCullWarps) kb2a_cull(DevVolume V, BatchA
 template <int P, bool MIXED, bool STATS>
 __global__ void __launch_bounds__(kRootsThreads, 4) kb2b_roots(DevVolume V, BatchArgs ba,
                                                                const int2* __restrict__ items,
-                                                               int* __restrict__ n_items, int cap,
-                                                               float4* __restrict__ frag_tp,
+                                                               int* __restrict__ slow, int* __restrict__ n_items,
+                                                               int cap, float4* __restrict__ frag_tp,
                                                                unsigned* __restrict__ frag_meta,
                                                                int* __restrict__ frag_count, size_t stride,
                                                                DevStats* __restrict__ st) {
-  const int n = min(*n_items, cap);
+  const int n = min(n_items[0], cap);
   unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
   for (;;) {                                   // warps take 32 consecutive items at a time
@@ -67,22 +67,98 @@ __global__ void __launch_bounds__(kRootsThreads, 4) kb2b_roots(DevVolume V, Batc
     const int px = q.cam.x0 + xw, py = q.cam.y0 + yw;
     float o[3], d[3];
     make_ray<float>(q.cam, px, py, o, d);
-    roots_item<P, float, MIXED, STATS>(V, q.cam64, it.x, fi, px, py, o, d, q.diag, stride, frag_tp, frag_meta,
-                                       frag_count, st, c_tests, c_newton, c_fp64, c_frag);
+    if (!roots_item<P, float, MIXED, STATS>(V, q.cam64, it.x, fi, px, py, o, d, q.diag, stride, frag_tp,
+                                                   frag_meta, frag_count, st, c_tests, c_newton, c_fp64, c_frag))
+      defer_item(i, slow, cap, n_items);
   }
-  roots_counters<STATS>(c_tests, c_newton, c_fp64, c_frag, n, st);
+  roots_counters<STATS, false>(c_tests, c_newton, c_fp64, c_frag, n, st);
+}
+
+template <int P, bool MIXED, bool STATS>
+__global__ void __launch_bounds__(kRootsThreads) kb2c_split(DevVolume V, BatchArgs ba, const int2* __restrict__ items,
+                                                            const int* __restrict__ slow, int* __restrict__ n_items,
+                                                            int cap, int warp_max, float4* __restrict__ frag_tp,
+                                                            unsigned* __restrict__ frag_meta,
+                                                            int* __restrict__ frag_count, size_t stride,
+                                                            DevStats* __restrict__ st) {
+  __shared__ SplitSmem<float> s_split[kRootsThreads / 32];
+  SplitSmem<float>& sm = s_split[threadIdx.x >> 5];
+  const int n = min(n_items[kSlowCounter - kItemCounter], cap);
+  if (n > warp_max) return;
+  unsigned long long c_fp64 = 0, c_frag = 0;
+  int c_newton = 0;
+  unsigned dropped = 0;
+  for (;;) {
+    int k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= n) break;
+    const int2 it = __ldg(items + __ldg(slow + k));
+    const int rq = (int)((unsigned)it.y >> kBatchFaceBits);
+    const int fi = it.y & ((1 << kBatchFaceBits) - 1);
+    const DevRequest& q = ba.req[rq];
+    const int loc = it.x - __ldg(ba.pix0 + rq);
+    const int xw = loc % q.cam.w, yw = loc / q.cam.w;
+    const int px = q.cam.x0 + xw, py = q.cam.y0 + yw;
+    float o[3], d[3];
+    make_ray<float>(q.cam, px, py, o, d);
+    split_item_warp<P, float, MIXED, STATS>(V, q.cam64, it.x, fi, px, py, o, d, q.diag, stride, frag_tp, frag_meta,
+                                            frag_count, st, sm, c_newton, c_fp64, c_frag, dropped);
+  }
+  if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
+  roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
+}
+
+template <int P, bool MIXED, bool STATS>
+__global__ void __launch_bounds__(kRootsThreads, 4) kb2c_thread(DevVolume V, BatchArgs ba,
+                                                                const int2* __restrict__ items,
+                                                                const int* __restrict__ slow,
+                                                                int* __restrict__ n_items, int cap, int warp_max,
+                                                                float4* __restrict__ frag_tp,
+                                                                unsigned* __restrict__ frag_meta,
+                                                                int* __restrict__ frag_count, size_t stride,
+                                                                DevStats* __restrict__ st) {
+  const int n = min(n_items[kSlowCounter - kItemCounter], cap);
+  if (n <= warp_max) return;
+  unsigned long long c_fp64 = 0, c_frag = 0;
+  int c_newton = 0;
+  for (;;) {
+    const int base = take_items(n_items, n, kSlowHead);
+    if (base >= n) break;
+    const int k = base + (int)(threadIdx.x & 31);
+    if (k >= n) continue;
+    const int2 it = __ldg(items + __ldg(slow + k));
+    const int rq = (int)((unsigned)it.y >> kBatchFaceBits);
+    const int fi = it.y & ((1 << kBatchFaceBits) - 1);
+    const DevRequest& q = ba.req[rq];
+    const int loc = it.x - __ldg(ba.pix0 + rq);
+    const int xw = loc % q.cam.w, yw = loc / q.cam.w;
+    const int px = q.cam.x0 + xw, py = q.cam.y0 + yw;
+    float o[3], d[3];
+    make_ray<float>(q.cam, px, py, o, d);
+    split_item_thread<P, float, MIXED, STATS>(V, q.cam64, it.x, fi, px, py, o, d, q.diag, stride, frag_tp,
+                                              frag_meta, frag_count, st, c_newton, c_fp64, c_frag);
+  }
+  roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
 }
 
 template <int P, bool MIXED, bool STATS>
 void launch_kb2b(const DevVolume& V, const BatchArgs& ba, const SurfaceWs& w, size_t stride, DevStats* st,
                  int num_sms, cudaStream_t s) {
-  static int per_sm = -1;
-  if (per_sm < 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb2b_roots<P, MIXED, STATS>, kRootsThreads, 0);
-    if (per_sm < 1) per_sm = 1;
+  static int per_sm[3] = {-1, -1, -1};
+  if (per_sm[0] < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], kb2b_roots<P, MIXED, STATS>, kRootsThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], kb2c_split<P, MIXED, STATS>, kRootsThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], kb2c_thread<P, MIXED, STATS>, kRootsThreads, 0);
+    for (int& x : per_sm) x = x < 1 ? 1 : x;
   }
-  kb2b_roots<P, MIXED, STATS><<<num_sms * per_sm, kRootsThreads, 0, s>>>(
-      V, ba, w.items, w.n_items, w.cap, (float4*)w.frag_tp, w.frag_meta, w.frag_count, stride, st);
+  const int warp_max = kSplitWaves * num_sms * per_sm[1] * (kRootsThreads / 32);
+  kb2b_roots<P, MIXED, STATS><<<num_sms * per_sm[0], kRootsThreads, 0, s>>>(
+      V, ba, w.items, w.slow, w.n_items, w.cap, (float4*)w.frag_tp, w.frag_meta, w.frag_count, stride, st);
+  kb2c_split<P, MIXED, STATS><<<num_sms * per_sm[1], kRootsThreads, 0, s>>>(
+      V, ba, w.items, w.slow, w.n_items, w.cap, warp_max, (float4*)w.frag_tp, w.frag_meta, w.frag_count, stride, st);
+  kb2c_thread<P, MIXED, STATS><<<num_sms * per_sm[2], kRootsThreads, 0, s>>>(
+      V, ba, w.items, w.slow, w.n_items, w.cap, warp_max, (float4*)w.frag_tp, w.frag_meta, w.frag_count, stride, st);
 }
 
 template <int TW, int TH>

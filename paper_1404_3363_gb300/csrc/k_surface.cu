@@ -4,8 +4,13 @@
 //       32 patches.
 //   K2a k2a_cull        -- one warp per 8x4 tile: culling and per-pixel
 //       bounding-box tests; (pixel, patch) items to a global list.
-//   K2b k2b_roots       -- one thread per item: hull test, roots, fragments
-//       into the pixel's A-buffer slots (§4.2).
+//   K2b k2b_roots       -- one thread per item: hull test, roots of the
+//       certified one-to-one patches, fragments into the pixel's A-buffer
+//       slots (§4.2); items whose patch needs the subdivision search are
+//       deferred to
+//   K2c k2c_split / k2c_thread -- the subdivision search of the deferred
+//       items: a warp per item, level by level across its lanes, while they
+//       fit a few waves of warps; a thread per item beyond that.
 #include <cuda_runtime.h>
 
 #include "k_surface.cuh"
@@ -38,20 +43,22 @@ __global__ void __launch_bounds__(32 * kCullWarps) k2a_cull(DevVolume V, DevCame
                           n_items, frag_count, st);
 }
 
+// K2b: every item on the certified fast path, the others deferred to the
+// list `slow`.  Warps take 32 consecutive items at a time.
 template <int P, typename R, bool MIXED, bool STATS>
 __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCamera<R> cam,
                                                               DevCamera<double> cam64,
                                                               const int2* __restrict__ items,
-                                                              int* __restrict__ n_items, int cap,
-                                                              typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                              int* __restrict__ slow, int* __restrict__ n_items,
+                                                              int cap, typename Vec4T<R>::type* __restrict__ frag_tp,
                                                               unsigned* __restrict__ frag_meta,
                                                               int* __restrict__ frag_count,
                                                               DevStats* __restrict__ st) {
-  const int n = min(*n_items, cap);
+  const int n = min(n_items[0], cap);
   const size_t stride = (size_t)cam.w * cam.h;
   unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
-  for (;;) {                                   // warps take 32 consecutive items at a time
+  for (;;) {
     const int base = take_items(n_items, n);
     if (base >= n) break;
     const int i = base + (int)(threadIdx.x & 31);
@@ -61,23 +68,100 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCa
     const int px = cam.x0 + xw, py = cam.y0 + yw;
     R o[3], d[3];
     make_ray<R>(cam, px, py, o, d);
-    roots_item<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
-                                   frag_count, st, c_tests, c_newton, c_fp64, c_frag);
+    if (!roots_item<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp,
+                                               frag_meta, frag_count, st, c_tests, c_newton, c_fp64, c_frag))
+      defer_item(i, slow, cap, n_items);
   }
-  roots_counters<STATS>(c_tests, c_newton, c_fp64, c_frag, n, st);
+  roots_counters<STATS, false>(c_tests, c_newton, c_fp64, c_frag, n, st);
+}
+
+// K2c: the deferred items' subdivision search.  With at most `warp_max`
+// deferred items (they fit a few waves of warps) each gets a whole warp
+// (split_item_warp, short latency); with more, one thread each
+// (k2c_thread, throughput).  Both kernels are launched; the one whose case
+// does not hold returns at once.
+template <int P, typename R, bool MIXED, bool STATS>
+__global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamera<R> cam, DevCamera<double> cam64,
+                                                           const int2* __restrict__ items,
+                                                           const int* __restrict__ slow, int* __restrict__ n_items,
+                                                           int cap, int warp_max,
+                                                           typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                           unsigned* __restrict__ frag_meta,
+                                                           int* __restrict__ frag_count, DevStats* __restrict__ st) {
+  __shared__ SplitSmem<R> s_split[kRootsThreads / 32];
+  SplitSmem<R>& sm = s_split[threadIdx.x >> 5];
+  const int n = min(n_items[kSlowCounter - kItemCounter], cap);
+  if (n > warp_max) return;
+  const size_t stride = (size_t)cam.w * cam.h;
+  unsigned long long c_fp64 = 0, c_frag = 0;
+  int c_newton = 0;
+  unsigned dropped = 0;
+  for (;;) {
+    int k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= n) break;
+    const int2 it = __ldg(items + __ldg(slow + k));
+    const int xw = it.x % cam.w, yw = it.x / cam.w;
+    const int px = cam.x0 + xw, py = cam.y0 + yw;
+    R o[3], d[3];
+    make_ray<R>(cam, px, py, o, d);
+    split_item_warp<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
+                                        frag_count, st, sm, c_newton, c_fp64, c_frag, dropped);
+  }
+  if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
+  roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
+}
+
+template <int P, typename R, bool MIXED, bool STATS>
+__global__ void __launch_bounds__(kRootsThreads, 4) k2c_thread(DevVolume V, DevCamera<R> cam,
+                                                               DevCamera<double> cam64,
+                                                               const int2* __restrict__ items,
+                                                               const int* __restrict__ slow,
+                                                               int* __restrict__ n_items, int cap, int warp_max,
+                                                               typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                               unsigned* __restrict__ frag_meta,
+                                                               int* __restrict__ frag_count,
+                                                               DevStats* __restrict__ st) {
+  const int n = min(n_items[kSlowCounter - kItemCounter], cap);
+  if (n <= warp_max) return;
+  const size_t stride = (size_t)cam.w * cam.h;
+  unsigned long long c_fp64 = 0, c_frag = 0;
+  int c_newton = 0;
+  for (;;) {
+    const int base = take_items(n_items, n, kSlowHead);
+    if (base >= n) break;
+    const int k = base + (int)(threadIdx.x & 31);
+    if (k >= n) continue;
+    const int2 it = __ldg(items + __ldg(slow + k));
+    const int xw = it.x % cam.w, yw = it.x / cam.w;
+    const int px = cam.x0 + xw, py = cam.y0 + yw;
+    R o[3], d[3];
+    make_ray<R>(cam, px, py, o, d);
+    split_item_thread<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
+                                          frag_count, st, c_newton, c_fp64, c_frag);
+  }
+  roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
 }
 
 template <int P, typename R, bool MIXED, bool STATS>
 void launch_k2b(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, const SurfaceWs& w,
                 DevStats* st, int num_sms, cudaStream_t s) {
   typedef typename Vec4T<R>::type V4;
-  static int per_sm = -1;
-  if (per_sm < 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2b_roots<P, R, MIXED, STATS>, kRootsThreads, 0);
-    if (per_sm < 1) per_sm = 1;
+  static int per_sm[3] = {-1, -1, -1};
+  if (per_sm[0] < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k2b_roots<P, R, MIXED, STATS>, kRootsThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k2c_split<P, R, MIXED, STATS>, kRootsThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k2c_thread<P, R, MIXED, STATS>, kRootsThreads, 0);
+    for (int& x : per_sm) x = x < 1 ? 1 : x;
   }
-  k2b_roots<P, R, MIXED, STATS><<<num_sms * per_sm, kRootsThreads, 0, s>>>(
-      V, cam, cam64, w.items, w.n_items, w.cap, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
+  const int warp_max = kSplitWaves * num_sms * per_sm[1] * (kRootsThreads / 32);
+  k2b_roots<P, R, MIXED, STATS><<<num_sms * per_sm[0], kRootsThreads, 0, s>>>(
+      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
+  k2c_split<P, R, MIXED, STATS><<<num_sms * per_sm[1], kRootsThreads, 0, s>>>(
+      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
+  k2c_thread<P, R, MIXED, STATS><<<num_sms * per_sm[2], kRootsThreads, 0, s>>>(
+      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
 }
 
 }  // namespace

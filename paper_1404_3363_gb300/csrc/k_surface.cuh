@@ -143,9 +143,11 @@ __device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCame
 }
 
 // K2b body: item (pixel, patch) with the pixel's ray (o, d) for pixel
-// (px, py) of cam64's image; fragments at slot * stride + pix.
+// (px, py) of cam64's image; fragments at slot * stride + pix.  Takes the
+// certified fast path only and returns false when the item needs the
+// subdivision search (K2c).
 template <int P, typename R, bool MIXED, bool STATS>
-__device__ __forceinline__ void roots_item(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
+__device__ __forceinline__ bool roots_item(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
                                            int px, int py, const R o[3], const R d[3], float diag, size_t stride,
                                            typename Vec4T<R>::type* __restrict__ frag_tp,
                                            unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
@@ -171,10 +173,278 @@ __device__ __forceinline__ void roots_item(const DevVolume& V, const DevCamera<d
   }
   Patch2<P, R> pq;
   project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
-  if (!hull_has_origin<P, R>(pq, pad)) return;
+  if (!hull_has_origin<P, R>(pq, pad)) return true;
   if (STATS) ++c_tests;
   R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
-  const int nr = patch_roots<P, R>(pq, pad, ra, rb, c_newton);
+  int nr;
+  if (!patch_roots_fast<P, R>(pq, ra, rb, nr, c_newton)) return false;
+  const int face = m.face, block = m.block;
+  for (int k = 0; k < nr; ++k) {
+    R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
+    R t, pp[3], cosang;
+    bool front;
+    make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
+    if constexpr (MIXED) {
+      if (cosang < R(0.2)) {
+        double a64 = a, b64 = b, t64 = t;
+        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
+        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
+        t = R(t64);
+        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+        const FaceMeta64 m64 = V.faces64[fi];
+        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
+        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        if (STATS) ++c_fp64;
+      }
+    }
+    if (!(t > R(0))) continue;
+    const int slot = atomicAdd(frag_count + pix, 1);
+    if (slot < kMaxFrags) {
+      V4 rec;
+      rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
+      frag_tp[(size_t)slot * stride + pix] = rec;
+      frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
+      if (STATS) ++c_frag;
+    } else {
+      atomicAdd(&st->abuf_overflow, 1ull);
+    }
+  }
+  return true;
+}
+
+// ---- K2c: subdivision search of one item by a whole warp, level by level.
+// The same parameter boxes as patch_roots_split (isect.cuh) are visited, in
+// breadth-first order: at each level every lane takes boxes of the level,
+// drops those whose hull misses the origin, solves certified boxes by Newton
+// from their centre (a root outside the box splits it further), runs the
+// multi-start Newton on uncertified boxes at the deepest level and splits
+// the rest along the longer control polygon.  Roots are gathered in shared
+// memory and merged by lane 0 (duplicates within the merge distance).
+constexpr int kBfsCap = 128;         // boxes per level
+constexpr int kSplitWaves = 4;       // warp-per-item search while the items fit this many waves
+constexpr int kRootCap = 16;         // gathered roots before merging
+
+template <typename R>
+struct SplitBox {
+  R a0, a1, b0, b1;
+  int depth;
+};
+
+template <typename R>
+struct SplitSmem {
+  SplitBox<R> box[2][kBfsCap];
+  R ra[kRootCap], rb[kRootCap];
+  int n[2];
+  int nr;
+};
+
+// Root (a, b) local to box nd: kept if inside the box (tolerance scaled to
+// its size) and the patch; returns false if outside the box.
+template <typename R>
+__device__ __forceinline__ bool gather_root(const SplitBox<R>& nd, R a, R b, SplitSmem<R>& sm) {
+  const R wa = nd.a1 - nd.a0, wb = nd.b1 - nd.b0;
+  const R ea = RootEps<R>::accept / wa, eb = RootEps<R>::accept / wb;
+  if (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb) return false;
+  const R ga = nd.a0 + a * wa, gb = nd.b0 + b * wb;
+  const R e = RootEps<R>::accept;
+  if (ga < -e || ga > R(1) + e || gb < -e || gb > R(1) + e) return true;
+  const int r = atomicAdd(&sm.nr, 1);
+  if (r < kRootCap) {
+    sm.ra[r] = ga;
+    sm.rb[r] = gb;
+  }
+  return true;
+}
+
+// All lanes of the warp call it; returns the merged roots in sm.ra/rb[0..n)
+// (n <= kMaxPatchRoots, the same on every lane).
+template <int P, typename R>
+__device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, SplitSmem<R>& sm, int& iters,
+                                                unsigned& dropped) {
+  constexpr int N = P + 1;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sm.box[0][0] = SplitBox<R>{R(0), R(1), R(0), R(1), 0};
+    sm.n[0] = 1;
+    sm.n[1] = 0;
+    sm.nr = 0;
+  }
+  __syncwarp();
+  int cur = 0;
+#pragma unroll 1
+  for (int level = 0; level <= kSplitDepth; ++level) {
+    const int n = min(sm.n[cur], kBfsCap);
+    if (n == 0) break;
+#pragma unroll 1
+    for (int k = lane; k < n; k += 32) {
+      const SplitBox<R> nd = sm.box[cur][k];
+      Patch2<P, R> q;
+      sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
+      if (!hull_has_origin<P, R>(q, pad)) continue;
+      bool split = true;
+      if (fixed_jacobian_sign<P, R>(q)) {
+        R a = R(0.5), b = R(0.5);
+        split = !(newton2<P, R>(q, a, b, iters) && gather_root<R>(nd, a, b, sm));
+      } else if (nd.depth >= kSplitDepth) {
+#pragma unroll 1
+        for (int s0 = 0; s0 < 5; ++s0) {
+          R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
+          R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
+          if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm);
+        }
+        split = false;
+      }
+      if (!split || nd.depth >= kSplitDepth) continue;
+      R la = 0, lb = 0;
+#pragma unroll
+      for (int t = 0; t < N; ++t) {
+        la += fabs(q.x[t * N + P] - q.x[t * N]) + fabs(q.y[t * N + P] - q.y[t * N]);
+        lb += fabs(q.x[P * N + t] - q.x[t]) + fabs(q.y[P * N + t] - q.y[t]);
+      }
+      SplitBox<R> lo = nd, hi = nd;
+      lo.depth = hi.depth = nd.depth + 1;
+      if (la >= lb) {
+        const R m = R(0.5) * (nd.a0 + nd.a1);
+        lo.a1 = m;
+        hi.a0 = m;
+      } else {
+        const R m = R(0.5) * (nd.b0 + nd.b1);
+        lo.b1 = m;
+        hi.b0 = m;
+      }
+      const int at = atomicAdd(&sm.n[cur ^ 1], 2);
+      if (at + 2 <= kBfsCap) {
+        sm.box[cur ^ 1][at] = lo;
+        sm.box[cur ^ 1][at + 1] = hi;
+      } else {
+        ++dropped;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) sm.n[cur] = 0;
+    __syncwarp();
+    cur ^= 1;
+  }
+  // merge duplicates (lane 0), keep at most kMaxPatchRoots
+  if (lane == 0) {
+    const int m = min(sm.nr, kRootCap);
+    int kept = 0;
+    for (int r = 0; r < m && kept < kMaxPatchRoots; ++r) {
+      bool dup = false;
+      for (int k = 0; k < kept; ++k)
+        if (fabs(sm.ra[k] - sm.ra[r]) + fabs(sm.rb[k] - sm.rb[r]) < RootEps<R>::dup) dup = true;
+      if (!dup) {
+        sm.ra[kept] = sm.ra[r];
+        sm.rb[kept] = sm.rb[r];
+        ++kept;
+      }
+    }
+    sm.nr = kept;
+  }
+  __syncwarp();
+  return sm.nr;
+}
+
+// K2c body for one deferred item (all lanes of the warp, same item): the
+// warp search, then one lane per root writes its fragment.
+template <int P, typename R, bool MIXED, bool STATS>
+__device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
+                                                int px, int py, const R o[3], const R d[3], float diag, size_t stride,
+                                                typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
+                                                DevStats* __restrict__ st, SplitSmem<R>& sm, int& c_newton,
+                                                unsigned long long& c_fp64, unsigned long long& c_frag,
+                                                unsigned& dropped) {
+  typedef typename Vec4T<R>::type V4;
+  constexpr int NN = (P + 1) * (P + 1);
+  const R pad = R(1e-6) * R(diag);
+  R e1[3], e2[3];
+  ray_frame<R>(d, e1, e2);
+  const FaceMeta& m = V.faces[fi];
+  R org[3], pa0, pa1, pb0, pb1;
+  const V4* cp;
+  if constexpr (sizeof(R) == 8) {
+    const FaceMeta64 m64 = V.faces64[fi];
+    org[0] = m64.org[0]; org[1] = m64.org[1]; org[2] = m64.org[2];
+    pa0 = m64.a0; pa1 = m64.a1; pb0 = m64.b0; pb1 = m64.b1;
+    cp = V.face64 + (size_t)fi * NN;
+  } else {
+    org[0] = m.org[0]; org[1] = m.org[1]; org[2] = m.org[2];
+    pa0 = m.a0; pa1 = m.a1; pb0 = m.b0; pb1 = m.b1;
+    cp = V.face32 + (size_t)fi * NN;
+  }
+  Patch2<P, R> pq;
+  project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
+  const int nr = split_roots_warp<P, R>(pq, pad, sm, c_newton, dropped);
+  const int lane = threadIdx.x & 31;
+  if (lane < nr) {
+    R a = clamp01r(sm.ra[lane]), b = clamp01r(sm.rb[lane]);
+    R t, pp[3], cosang;
+    bool front;
+    make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
+    const int face = m.face, block = m.block;
+    if constexpr (MIXED) {
+      if (cosang < R(0.2)) {
+        double a64 = a, b64 = b, t64 = t;
+        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
+        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
+        t = R(t64);
+        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+        const FaceMeta64 m64 = V.faces64[fi];
+        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
+        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        if (STATS) ++c_fp64;
+      }
+    }
+    if (t > R(0)) {
+      const int slot = atomicAdd(frag_count + pix, 1);
+      if (slot < kMaxFrags) {
+        V4 rec;
+        rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
+        frag_tp[(size_t)slot * stride + pix] = rec;
+        frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
+        if (STATS) ++c_frag;
+      } else {
+        atomicAdd(&st->abuf_overflow, 1ull);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// K2c body, one thread per deferred item (many deferred items): the
+// depth-first subdivision search of isect.cuh, then the fragments.
+template <int P, typename R, bool MIXED, bool STATS>
+__device__ __forceinline__ void split_item_thread(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
+                                                  int px, int py, const R o[3], const R d[3], float diag,
+                                                  size_t stride, typename Vec4T<R>::type* __restrict__ frag_tp,
+                                                  unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
+                                                  DevStats* __restrict__ st, int& c_newton,
+                                                  unsigned long long& c_fp64, unsigned long long& c_frag) {
+  typedef typename Vec4T<R>::type V4;
+  constexpr int NN = (P + 1) * (P + 1);
+  const R pad = R(1e-6) * R(diag);
+  R e1[3], e2[3];
+  ray_frame<R>(d, e1, e2);
+  const FaceMeta& m = V.faces[fi];
+  R org[3], pa0, pa1, pb0, pb1;
+  const V4* cp;
+  if constexpr (sizeof(R) == 8) {
+    const FaceMeta64 m64 = V.faces64[fi];
+    org[0] = m64.org[0]; org[1] = m64.org[1]; org[2] = m64.org[2];
+    pa0 = m64.a0; pa1 = m64.a1; pb0 = m64.b0; pb1 = m64.b1;
+    cp = V.face64 + (size_t)fi * NN;
+  } else {
+    org[0] = m.org[0]; org[1] = m.org[1]; org[2] = m.org[2];
+    pa0 = m.a0; pa1 = m.a1; pb0 = m.b0; pb1 = m.b1;
+    cp = V.face32 + (size_t)fi * NN;
+  }
+  Patch2<P, R> pq;
+  project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
+  R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
+  const int nr = patch_roots_split<P, R>(&pq, pad, ra, rb, c_newton);
   const int face = m.face, block = m.block;
   for (int k = 0; k < nr; ++k) {
     R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
@@ -209,22 +479,31 @@ __device__ __forceinline__ void roots_item(const DevVolume& V, const DevCamera<d
   }
 }
 
+// Appends item i to the list of items that need the subdivision search
+// (count at n_items[kSlowCounter - kItemCounter]).
+__device__ __forceinline__ void defer_item(int i, int* __restrict__ slow, int cap, int* __restrict__ n_items) {
+  const int k = atomicAdd(n_items + (kSlowCounter - kItemCounter), 1);
+  if (k < cap) slow[k] = i;
+}
+
 // Next 32 consecutive items for the calling warp (all lanes call it), from
 // the hand-out head at n_items[kItemHead - kItemCounter]; returns the first
 // or n when none are left.
-__device__ __forceinline__ int take_items(int* __restrict__ n_items, int n) {
+__device__ __forceinline__ int take_items(int* __restrict__ n_items, int n, int head = kItemHead) {
   int base = 0;
-  if ((threadIdx.x & 31) == 0) base = atomicAdd(n_items + (kItemHead - kItemCounter), 32);
+  if ((threadIdx.x & 31) == 0) base = atomicAdd(n_items + (head - kItemCounter), 32);
   base = __shfl_sync(0xffffffffu, base, 0);
   return base < n ? base : n;
 }
 
-// Counters of K2b, one atomic per warp; n = items of the launch.
-template <bool STATS>
+// Counters of K2b / K2c, one atomic per warp; n = items of the launch
+// (K2b: all items, K2c: items that needed the subdivision search).
+template <bool STATS, bool SPLIT>
 __device__ __forceinline__ void roots_counters(unsigned long long c_tests, int c_newton, unsigned long long c_fp64,
                                                unsigned long long c_frag, int n, DevStats* __restrict__ st) {
   if (!STATS) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->isect_items, (unsigned long long)n);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(SPLIT ? &st->isect_split : &st->isect_items, (unsigned long long)n);
   unsigned long long cn = (unsigned long long)c_newton;
 #pragma unroll
   for (int o2 = 16; o2 > 0; o2 >>= 1) {
