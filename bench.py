@@ -33,6 +33,7 @@ WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x
 # remaining workloads of the method, each printed as its own line.
 WORKLOADS = {
     "bar1080": (1, 0, WORKLOAD),
+    "cube64-fp64": (0, 2, "twisted cube, 1 cubic Bezier element, 64x64 orthographic, rk_tol 1e-8, FP64"),
     "beam1080": (2, 1, "bent beam, 16 cubic blocks 6x6x12 cp (C0), Gaussian-sum scalar, 1920x1080 perspective, "
                        "mixed precision"),
     "beam1080-fp32": (2, 0, "bent beam, 16 cubic blocks 6x6x12 cp (C0), Gaussian-sum scalar, 1920x1080 "
@@ -350,7 +351,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 0 else "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "f32+f64", 2: "f64"}[prec], "data": "synthetic",
             "config": {"workload": workload, "width": W, "height": H, "rk_tol": sc.params.rk_tol,
                        "ds": sc.params.ds, "supersample_k": sc.params.supersample_k,
                        "l2": "flushed between steps (512 MiB write outside the timed events)",
