@@ -10,8 +10,10 @@ Functions follow the paper (Fuchs & Hjelmervik, TVCG 2015):
   hits / pairs   §4.1 intersections, §4.2 Alg. 2 pairing
   invert         §5.1 Newton (RF) with QR, clamping and line search
   composite      §3.2.1 Alg. 1 with supersampling
-  render         the whole per-pixel path, per-sample RF (method 0) or
-                 RKF45 on the pulled-back ODE of §5.2 (method 1)
+  render         the whole per-pixel path, per-sample RF (method 0),
+                 RKF45 on the pulled-back ODE of §5.2 (method 1) or one step
+                 per sample interval of the fixed-step RK family of §5.3
+                 (FIXED_* methods)
   table1         §5.3 Table 1 harness (fixed-step RK family / RF)
 """
 from __future__ import annotations
@@ -25,6 +27,13 @@ import numpy as np
 from . import build as _build
 
 _LIB = None
+
+# render methods: per-sample root finding, RKF45 with error control, and the
+# fixed-step explicit RK family of §5.3 (one step per sample interval)
+METHOD_RF = 0
+METHOD_RKF45 = 1
+FIXED_EULER, FIXED_MIDPOINT, FIXED_KUTTA3, FIXED_RK4, FIXED_RK4_38, FIXED_FEHLBERG5 = 11, 12, 13, 14, 15, 16
+FIXED_ORDER = {11: 1, 12: 2, 13: 3, 14: 4, 15: 4, 16: 5}
 
 c_double_p = C.POINTER(C.c_double)
 

@@ -705,10 +705,13 @@ void composite_interval(const TF& tf, int K, double early, double rho0, double r
 
 struct Params {
   double ds; int K; double c; double early;
-  int method;          // 0 = RF per sample, 1 = RKF45 ODE
+  int method;          // 0 = RF per sample, 1 = RKF45 ODE, 10 + k = fixed-step tableau k (one step per interval)
   double newton_tol;   // relative to diag
   double rk_tol;
 };
+
+struct Tableau { int s; double a[6][6]; double b[6]; };
+Tableau tableau(int method);
 
 struct PixelStats { int npairs = 0, unmatched = 0, newton_fail = 0, nsamples = 0, rk_steps = 0; };
 
@@ -742,6 +745,33 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
       int it = invert_point(b, g, p, P.newton_tol * V.diag, 50, q);
       if (it < 0) ++st.newton_fail;
       for (int r = 0; r < 3; ++r) p[r] = q[r];
+    } else if (P.method >= 11 && P.method <= 16) {
+      // one step of a fixed-step explicit method (the paper's RK family,
+      // §5.3) from s_{j-1} to s_j; stage points and the result clamped to
+      // [0,1]^3 (§5.4)
+      const Tableau T = tableau(P.method - 10);
+      const double hh = s[j] - s[j - 1];
+      double k[6][3];
+      bool ok = true;
+      for (int st2 = 0; st2 < T.s && ok; ++st2) {
+        double q[3];
+        for (int r = 0; r < 3; ++r) {
+          double acc2 = p[r];
+          for (int m = 0; m < st2; ++m) acc2 += hh * T.a[st2][m] * k[m][r];
+          q[r] = std::min(std::max(acc2, 0.0), 1.0);
+        }
+        ok = ode_rhs(b, q, g_in, d, P.c, k[st2]);
+      }
+      if (!ok) {
+        ++st.newton_fail;
+      } else {
+        for (int r = 0; r < 3; ++r) {
+          double acc2 = p[r];
+          for (int st2 = 0; st2 < T.s; ++st2) acc2 += hh * T.b[st2] * k[st2][r];
+          p[r] = std::min(std::max(acc2, 0.0), 1.0);
+        }
+        ++st.rk_steps;
+      }
     } else {
       // integrate the pulled-back ODE from s_{j-1} to s_j with RKF45
       double sc = s[j - 1];
@@ -819,8 +849,6 @@ void t1_rhs(const double p[3], const double g_in[3], const double d[3], double c
   for (int r = 0; r < 3; ++r) Vv[r] = d[r] + c * (e[r] - ed * d[r]);
   qr_solve3(J, Vv, W);
 }
-
-struct Tableau { int s; double a[6][6]; double b[6]; };
 
 Tableau tableau(int method) {
   Tableau T;
