@@ -130,7 +130,10 @@ typedef struct {
  *              its sample buffers (40 bytes per sample) in library memory
  * rf_tol       RF stopping rule: ||phi(p) - g|| <= rf_tol times the half width
  *              of the pixel at the sample's depth (the paper stops at the
- *              pixel frustum, rf_tol = 1) [0.05] */
+ *              pixel frustum, rf_tol = 1) [0.05]
+ * rk_method    IVV_RK_* integrator of the ODE method [IVV_RK_BS32]; the
+ *              fixed-step family (§5.3) takes one step per sample interval
+ *              (rk_tol unused) and runs in FP32 or MIXED precision */
 typedef struct {
   double rk_tol;
   double ds;
@@ -143,7 +146,19 @@ typedef struct {
   int x0, y0, full_width, full_height;
   int method;
   double rf_tol;
+  int rk_method;
 } ivv_render_params;
+
+/* Integrators of the ODE method (rk_method): */
+enum {
+  IVV_RK_BS32 = 0,      /* embedded Bogacki-Shampine 3(2), error control, dense output */
+  IVV_RK_EULER = 1,     /* fixed step: explicit Euler (the paper's RK1)         */
+  IVV_RK_MIDPOINT = 2,  /* fixed step: explicit midpoint (RK2)                  */
+  IVV_RK_KUTTA3 = 3,    /* fixed step: Kutta's third-order method (RK3)         */
+  IVV_RK_RK4 = 4,       /* fixed step: classic fourth-order Runge-Kutta (RK4)   */
+  IVV_RK_RK4_38 = 5,    /* fixed step: Kutta's 3/8 rule (RK4 3/8)               */
+  IVV_RK_FEHLBERG5 = 6  /* fixed step: Fehlberg's pair, fifth-order weights (RKF) */
+};
 
 /* Preimage methods of stage 3 (§5): */
 enum {

@@ -223,11 +223,63 @@ ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_ren
     return fail(IVV_ERR_INVALID_ARG, "initial guesses apply to the RF method");
   if (p.method == IVV_METHOD_RF && p.precision != IVV_PREC_FP32)
     return fail(IVV_ERR_UNSUPPORTED, "the RF method runs in FP32 precision");
+  if (p.rk_method < IVV_RK_BS32 || p.rk_method > IVV_RK_FEHLBERG5) return fail(IVV_ERR_INVALID_ARG, "bad rk_method");
+  if (p.rk_method != IVV_RK_BS32 && p.method != IVV_METHOD_ODE)
+    return fail(IVV_ERR_INVALID_ARG, "rk_method applies to the ODE method");
+  if (p.rk_method != IVV_RK_BS32 && p.precision == IVV_PREC_FP64)
+    return fail(IVV_ERR_UNSUPPORTED, "the fixed-step integrators run in FP32 or MIXED precision");
   return IVV_OK;
 }
 
 ivv_status resolve_params(const ivv_volume* v, const ivv_render_params* in, ivv_render_params& p) {
   return resolve_params_diag(v->hv.diag, in, p);
+}
+
+// Tableaux of the fixed-step family (published coefficients: Euler;
+// explicit midpoint; Kutta 1901 third order; classic RK4; Kutta's 3/8 rule;
+// Fehlberg 1969 4(5) nodes with the fifth-order weights).
+ivv::RkTableau rk_tableau(int method) {
+  ivv::RkTableau T;
+  std::memset(&T, 0, sizeof(T));
+  switch (method) {
+    case IVV_RK_EULER:
+      T.s = 1; T.b[0] = 1.f;
+      break;
+    case IVV_RK_MIDPOINT:
+      T.s = 2; T.a[1][0] = 0.5f; T.b[1] = 1.f;
+      break;
+    case IVV_RK_KUTTA3:
+      T.s = 3; T.a[1][0] = 0.5f; T.a[2][0] = -1.f; T.a[2][1] = 2.f;
+      T.b[0] = 1.f / 6; T.b[1] = 2.f / 3; T.b[2] = 1.f / 6;
+      break;
+    case IVV_RK_RK4:
+      T.s = 4; T.a[1][0] = 0.5f; T.a[2][1] = 0.5f; T.a[3][2] = 1.f;
+      T.b[0] = 1.f / 6; T.b[1] = 1.f / 3; T.b[2] = 1.f / 3; T.b[3] = 1.f / 6;
+      break;
+    case IVV_RK_RK4_38:
+      T.s = 4; T.a[1][0] = 1.f / 3; T.a[2][0] = -1.f / 3; T.a[2][1] = 1.f;
+      T.a[3][0] = 1.f; T.a[3][1] = -1.f; T.a[3][2] = 1.f;
+      T.b[0] = 1.f / 8; T.b[1] = 3.f / 8; T.b[2] = 3.f / 8; T.b[3] = 1.f / 8;
+      break;
+    case IVV_RK_FEHLBERG5: {
+      T.s = 6;
+      const double a[6][5] = {{0, 0, 0, 0, 0},
+                              {1.0 / 4, 0, 0, 0, 0},
+                              {3.0 / 32, 9.0 / 32, 0, 0, 0},
+                              {1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197, 0, 0},
+                              {439.0 / 216, -8.0, 3680.0 / 513, -845.0 / 4104, 0},
+                              {-8.0 / 27, 2.0, -3544.0 / 2565, 1859.0 / 4104, -11.0 / 40}};
+      const double b[6] = {16.0 / 135, 0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50, 2.0 / 55};
+      for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 5; ++j) T.a[i][j] = (float)a[i][j];
+        T.b[i] = (float)b[i];
+      }
+      break;
+    }
+    default:
+      T.s = 0;
+  }
+  return T;
 }
 
 ivv_status ensure_own(void** buf, size_t* have, size_t need, cudaStream_t s) {
@@ -385,6 +437,23 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
                                  (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
+  } else if (p.rk_method != IVV_RK_BS32) {
+    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    const ivv::DevCamera<float> c32 = dev_camera<float>(F);
+    const ivv::RkTableau T = rk_tableau(p.rk_method);
+    const float4* pin = (const float4*)(ws + L.pair_in);
+    const float4* pout = (const float4*)(ws + L.pair_out);
+    if (V.P == 2)
+      ivv::launch_fixed_p<2>(V, c32, tf, a, T, mixed, stats, pin, pout, (const int*)(ws + L.pair_block),
+                             (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                             (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
+                             (float4*)out, v->d_stats, v->num_sms, s);
+    else
+      ivv::launch_fixed_p<3>(V, c32, tf, a, T, mixed, stats, pin, pout, (const int*)(ws + L.pair_block),
+                             (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                             (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
+                             (float4*)out, v->d_stats, v->num_sms, s);
   } else {
     st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;

@@ -477,6 +477,21 @@ void launch_batch_integrate(const DevVolume& V, const BatchArgs& ba, const Integ
                             cudaStream_t s);
 int batch_integrate_max_ctas_per_sm(int P, bool mixed, bool stats);
 
+// Explicit Runge-Kutta tableau of the fixed-step integrators, at most
+// kRkStagesMax stages (a strictly lower triangular).
+constexpr int kRkStagesMax = 6;
+struct RkTableau {
+  int s;
+  float a[kRkStagesMax][kRkStagesMax];
+  float b[kRkStagesMax];
+};
+
+template <int P>
+void launch_fixed_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, const IntegrateArgs& a,
+                    const RkTableau& T, bool mixed, bool stats, const float4* pin, const float4* pout,
+                    const int* pblk, const int* pcnt, const int* active, const int* n_active, int* queue_head,
+                    float4* out, DevStats* st, int num_sms, cudaStream_t s);
+
 void launch_eval_points(const DevVolume& V, int block, int n, const float* p, float* phi, float* jac,
                         float* rho, cudaStream_t s);
 

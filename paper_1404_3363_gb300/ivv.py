@@ -24,6 +24,8 @@ STATUS_NAMES = {0: "IVV_OK", 1: "IVV_ERR_INVALID_ARG", 2: "IVV_ERR_CUDA", 3: "IV
 FLAG_STATS = 1
 FLAG_TIMING = 2
 GUESS_PARAMS = 4611
+# ODE integrators (rk_method): error-controlled BS3(2) and the fixed-step family
+RK_BS32, RK_EULER, RK_MIDPOINT, RK_KUTTA3, RK_RK4, RK_RK4_38, RK_FEHLBERG5 = range(7)
 STAGES = ("project", "intersect", "pair", "integrate")
 
 c_double_p = C.POINTER(C.c_double)
@@ -54,7 +56,8 @@ class RenderParams(C.Structure):
     _fields_ = [("rk_tol", C.c_double), ("ds", C.c_double), ("supersample_k", C.c_int),
                 ("c", C.c_double), ("early_alpha", C.c_double), ("use_mlp_guess", C.c_int),
                 ("precision", C.c_int), ("flags", C.c_int), ("x0", C.c_int), ("y0", C.c_int),
-                ("full_width", C.c_int), ("full_height", C.c_int), ("method", C.c_int), ("rf_tol", C.c_double)]
+                ("full_width", C.c_int), ("full_height", C.c_int), ("method", C.c_int), ("rf_tol", C.c_double),
+                ("rk_method", C.c_int)]
 
 
 class GuessTrainParams(C.Structure):
@@ -180,6 +183,7 @@ def params_struct(p=None, flags=0, window=None) -> RenderParams:
     q.precision = p.precision if p else 0
     q.method = getattr(p, "method", 0) if p else 0
     q.rf_tol = getattr(p, "rf_tol", 0.05) if p else 0.05
+    q.rk_method = getattr(p, "rk_method", 0) if p else 0
     q.flags = flags
     if window is not None:
         q.x0, q.y0, q.full_width, q.full_height = window
