@@ -15,6 +15,8 @@ Functions follow the paper (Fuchs & Hjelmervik, TVCG 2015):
                  per sample interval of the fixed-step RK family of §5.3
                  (FIXED_* methods)
   table1         §5.3 Table 1 harness (fixed-step RK family / RF)
+Cutting and near-clip planes (§5.5) act on the depth-sorted intersections
+before compositing (render with params.near_clip / params.cut_planes).
 """
 from __future__ import annotations
 
@@ -57,7 +59,8 @@ class _TF(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("ds", C.c_double), ("supersample_k", C.c_int), ("c", C.c_double),
                 ("early_alpha", C.c_double), ("method", C.c_int),
-                ("newton_tol", C.c_double), ("rk_tol", C.c_double)]
+                ("newton_tol", C.c_double), ("rk_tol", C.c_double),
+                ("near_clip", C.c_double), ("n_cut", C.c_int), ("cut", (C.c_double * 4) * 4)]
 
 
 class Hit(C.Structure):
@@ -255,6 +258,13 @@ def params_struct(p, diag, method=0, newton_tol=1e-13, rk_tol=1e-12):
     q.method = method
     q.newton_tol = newton_tol
     q.rk_tol = rk_tol
+    q.near_clip = getattr(p, "near_clip", 0.0)
+    planes = list(getattr(p, "cut_planes", ()))
+    assert len(planes) <= 4
+    q.n_cut = len(planes)
+    for k, pl in enumerate(planes):
+        for c in range(4):
+            q.cut[k][c] = float(pl[c])
     return q
 
 

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <limits>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -708,6 +709,9 @@ struct Params {
   int method;          // 0 = RF per sample, 1 = RKF45 ODE, 10 + k = fixed-step tableau k (one step per interval)
   double newton_tol;   // relative to diag
   double rk_tol;
+  double near_clip;    // > 0: near plane at this distance along the view direction
+  int n_cut;           // cutting planes: points g with n.g + w > 0 are cut away
+  double cut[4][4];
 };
 
 struct Tableau { int s; double a[6][6]; double b[6]; };
@@ -810,13 +814,101 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
   }
 }
 
+// Cutting and near-clip planes (§5.5) on the depth-sorted intersections of
+// one ray, before compositing.  Near plane: hits nearer than it are dropped,
+// and a block whose nearest remaining hit is an exit gets an entry on the
+// plane (the eye side of the plane lies inside that block).  Cutting plane:
+// every entry/exit segment is shortened to the part with n.g + w <= 0.  An
+// end that moves onto a plane gets its parameter point by Newton (§5.1) from
+// the chord between the segment's original ends (from the exit for a new
+// entry); a segment whose new end does not invert inside its block is
+// dropped.
+std::vector<Pair> clip_pairs(const Volume& V, const Params& P, const Camera& cam, const double o[3],
+                             const double d[3], std::vector<Hit> hits, int* unmatched) {
+  const double NaN = std::numeric_limits<double>::quiet_NaN();
+  double t_near = 0;
+  if (P.near_clip > 0) {
+    double f[3] = {cam.target[0] - cam.eye[0], cam.target[1] - cam.eye[1], cam.target[2] - cam.eye[2]};
+    const double nf = norm3(f);
+    for (int r = 0; r < 3; ++r) f[r] /= nf;
+    t_near = P.near_clip / dot3(d, f);
+    std::vector<Hit> kept;
+    for (const Hit& h : hits)
+      if (h.t >= t_near) kept.push_back(h);
+    hits.swap(kept);
+    const size_t n0 = hits.size();
+    for (size_t i = 0; i < n0; ++i) {
+      bool nearest = true;
+      for (size_t k = 0; k < n0; ++k)
+        if (hits[k].block == hits[i].block && (hits[k].t < hits[i].t || (hits[k].t == hits[i].t && k < i)))
+          nearest = false;
+      if (nearest && !hits[i].front) {
+        Hit e = hits[i];
+        e.t = t_near;
+        e.front = 1;
+        e.face = -1;
+        for (int r = 0; r < 3; ++r) e.p[r] = NaN;          // solved below
+        hits.push_back(e);
+      }
+    }
+  }
+  std::vector<Pair> pairs = pair_hits(hits, unmatched);
+  std::vector<Pair> out;
+  const double tol = P.newton_tol * V.diag;
+  for (Pair pr : pairs) {
+    const double t_in0 = pr.t_in, t_out0 = pr.t_out;
+    double t0 = pr.t_in, t1 = pr.t_out;
+    for (int k = 0; k < P.n_cut; ++k) {
+      const double* c = P.cut[k];
+      const double fo = c[0] * o[0] + c[1] * o[1] + c[2] * o[2] + c[3];
+      const double fd = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
+      if (fd == 0) {
+        if (fo > 0) t1 = t0 - 1;                           // all of the segment is cut away
+        continue;
+      }
+      const double tc = -fo / fd;
+      if (fd > 0) t1 = std::min(t1, tc);
+      else t0 = std::max(t0, tc);
+    }
+    if (!(t1 > t0)) continue;
+    const bool new_in = std::isnan(pr.p_in[0]) || t0 > t_in0, new_out = t1 < t_out0;
+    const Block& b = V.blocks[pr.block];
+    bool ok = true;
+    double pin[3], pout[3];
+    for (int r = 0; r < 3; ++r) { pin[r] = pr.p_in[r]; pout[r] = pr.p_out[r]; }
+    if (new_in) {
+      double g[3], guess[3];
+      for (int r = 0; r < 3; ++r) g[r] = o[r] + t0 * d[r];
+      const double w = (t_out0 > t_in0) ? (t0 - t_in0) / (t_out0 - t_in0) : 0.0;
+      for (int r = 0; r < 3; ++r)
+        guess[r] = std::isnan(pr.p_in[0]) ? pr.p_out[r] : pr.p_in[r] + w * (pr.p_out[r] - pr.p_in[r]);
+      ok = invert_point(b, g, guess, tol, 100, pin) >= 0;
+    }
+    if (ok && new_out) {
+      double g[3], guess[3];
+      for (int r = 0; r < 3; ++r) g[r] = o[r] + t1 * d[r];
+      const double w = (t_out0 > t_in0) ? (t1 - t_in0) / (t_out0 - t_in0) : 1.0;
+      for (int r = 0; r < 3; ++r)
+        guess[r] = std::isnan(pr.p_in[0]) ? pr.p_out[r] : pr.p_in[r] + w * (pr.p_out[r] - pr.p_in[r]);
+      ok = invert_point(b, g, guess, tol, 100, pout) >= 0;
+    }
+    if (!ok) continue;
+    pr.t_in = t0;
+    pr.t_out = t1;
+    for (int r = 0; r < 3; ++r) { pr.p_in[r] = pin[r]; pr.p_out[r] = pout[r]; }
+    out.push_back(pr);
+  }
+  return out;
+}
+
 void render_pixel(const Volume& V, const TF& tf, const Params& P, const Camera& cam, int W, int H,
                   int x, int y, double out[4], PixelStats& st) {
   double o[3], d[3];
   make_ray(cam, W, H, x, y, o, d);
   std::vector<Hit> hits = ray_hits(V, o, d);
   int um = 0;
-  std::vector<Pair> pairs = pair_hits(hits, &um);
+  std::vector<Pair> pairs = (P.near_clip > 0 || P.n_cut > 0) ? clip_pairs(V, P, cam, o, d, hits, &um)
+                                                              : pair_hits(hits, &um);
   st.npairs = (int)pairs.size();
   st.unmatched = um;
   Accum acc;
@@ -906,6 +998,7 @@ typedef struct {
 typedef struct {
   double ds; int supersample_k; double c; double early_alpha;
   int method; double newton_tol; double rk_tol;
+  double near_clip; int n_cut; double cut[4][4];
 } orc_params;
 
 typedef struct { double t; double p[3]; int block, face, front; } orc_hit;
@@ -1094,7 +1187,7 @@ int orc_trace_pair(void* v, const orc_tf* t, const orc_params* prm, const double
   tf.r.assign(t->r, t->r + t->n_knots);
   tf.rgba.assign(t->rgba, t->rgba + 4 * t->n_knots);
   tf.sigma = t->sigma; tf.lo = t->lo; tf.hi = t->hi;
-  Params P{prm->ds, prm->supersample_k, prm->c, 2.0, prm->method, prm->newton_tol, prm->rk_tol};
+  Params P{prm->ds, prm->supersample_k, prm->c, 2.0, prm->method, prm->newton_tol, prm->rk_tol, 0.0, 0, {}};
   Pair p;
   p.block = pr->block; p.t_in = pr->t_in; p.t_out = pr->t_out;
   for (int r = 0; r < 3; ++r) { p.p_in[r] = pr->p_in[r]; p.p_out[r] = pr->p_out[r]; }
@@ -1116,7 +1209,10 @@ int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* 
   tf.r.assign(t->r, t->r + t->n_knots);
   tf.rgba.assign(t->rgba, t->rgba + 4 * t->n_knots);
   tf.sigma = t->sigma; tf.lo = t->lo; tf.hi = t->hi;
-  Params P{prm->ds, prm->supersample_k, prm->c, prm->early_alpha, prm->method, prm->newton_tol, prm->rk_tol};
+  Params P{prm->ds, prm->supersample_k, prm->c, prm->early_alpha, prm->method, prm->newton_tol, prm->rk_tol,
+           prm->near_clip, prm->n_cut < 0 ? 0 : (prm->n_cut > 4 ? 4 : prm->n_cut), {}};
+  for (int k = 0; k < P.n_cut; ++k)
+    for (int c = 0; c < 4; ++c) P.cut[k][c] = prm->cut[k][c];
   Camera cam;
   std::memcpy(&cam, c, sizeof(cam));
   const int w = x1 - x0, h = y1 - y0;
