@@ -133,7 +133,19 @@ typedef struct {
  *              pixel frustum, rf_tol = 1) [0.05]
  * rk_method    IVV_RK_* integrator of the ODE method [IVV_RK_BS32]; the
  *              fixed-step family (§5.3) takes one step per sample interval
- *              (rk_tol unused) and runs in FP32 or MIXED precision */
+ *              (rk_tol unused) and runs in FP32 or MIXED precision
+ * near_clip    > 0: near plane at this distance from the eye along the view
+ *              direction (§5.5): intersections in front of it are dropped
+ *              and a block whose nearest remaining intersection is an exit
+ *              (the plane cuts through the block) is entered on the plane [0]
+ * n_cut_planes, cut_planes
+ *              up to IVV_MAX_CUT_PLANES cutting planes (§5.5), plane k as
+ *              (n_x, n_y, n_z, w): the part of the volume with n.g + w > 0 is
+ *              cut away, i.e. every entry/exit segment of a ray is shortened
+ *              to n.g + w <= 0 [none].  An end point that moves onto a plane
+ *              gets its parameter point by Newton (§5.1) from the chord of
+ *              the segment; an entry on the near plane that does not invert
+ *              inside its block drops its segment. */
 typedef struct {
   double rk_tol;
   double ds;
@@ -147,7 +159,12 @@ typedef struct {
   int method;
   double rf_tol;
   int rk_method;
+  double near_clip;
+  int n_cut_planes;
+  double cut_planes[4][4];
 } ivv_render_params;
+
+#define IVV_MAX_CUT_PLANES 4
 
 /* Integrators of the ODE method (rk_method): */
 enum {

@@ -351,6 +351,8 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
   if (p.precision == IVV_PREC_FP64) return bfail(IVV_ERR_UNSUPPORTED, "batches run in FP32 or MIXED precision");
   if (p.x0 || p.y0 || p.full_width || p.full_height)
     return bfail(IVV_ERR_INVALID_ARG, "batches render whole images (no window)");
+  if (p.near_clip > 0 || p.n_cut_planes > 0)
+    return bfail(IVV_ERR_UNSUPPORTED, "batches render without cutting or near-clip planes");
   p.flags = 0;
 
   ivv_batch* b = new ivv_batch();

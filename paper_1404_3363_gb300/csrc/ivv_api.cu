@@ -228,6 +228,15 @@ ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_ren
     return fail(IVV_ERR_INVALID_ARG, "rk_method applies to the ODE method");
   if (p.rk_method != IVV_RK_BS32 && p.precision == IVV_PREC_FP64)
     return fail(IVV_ERR_UNSUPPORTED, "the fixed-step integrators run in FP32 or MIXED precision");
+  if (!(p.near_clip >= 0) || !std::isfinite(p.near_clip)) return fail(IVV_ERR_INVALID_ARG, "near_clip must be >= 0");
+  if (p.n_cut_planes < 0 || p.n_cut_planes > IVV_MAX_CUT_PLANES)
+    return fail(IVV_ERR_INVALID_ARG, "n_cut_planes must be in 0..IVV_MAX_CUT_PLANES");
+  for (int k = 0; k < p.n_cut_planes; ++k) {
+    const double* c = p.cut_planes[k];
+    if (!(std::isfinite(c[0]) && std::isfinite(c[1]) && std::isfinite(c[2]) && std::isfinite(c[3])))
+      return fail(IVV_ERR_INVALID_ARG, "non-finite cutting plane");
+    if (!(c[0] * c[0] + c[1] * c[1] + c[2] * c[2] > 0)) return fail(IVV_ERR_INVALID_ARG, "cutting plane normal is zero");
+  }
   return IVV_OK;
 }
 
@@ -323,10 +332,23 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[1], s));
   ivv::launch_intersect<R>(V, dev_camera<R>(F), dev_camera<double>(F), mixed, stats, sw, v->d_stats, v->num_sms, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[2], s));
+  ivv::ClipArgs<R> clip;
+  std::memset(&clip, 0, sizeof(clip));
+  clip.on = (p.near_clip > 0 || p.n_cut_planes > 0) ? 1 : 0;
+  clip.near = (R)p.near_clip;
+  for (int r = 0; r < 3; ++r) clip.f[r] = (R)F.f[r];
+  clip.n_cut = p.n_cut_planes;
+  for (int k = 0; k < p.n_cut_planes; ++k)
+    for (int c = 0; c < 4; ++c) clip.cut[k][c] = (R)p.cut_planes[k][c];
+  clip.cam = dev_camera<R>(F);
   ivv::launch_pair<R>(V, F.w, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                       (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
-                      (int*)(ws + L.counters), out_zero, nullptr, v->d_stats, s);
+                      (int*)(ws + L.counters), out_zero, clip, v->d_stats, s);
+  if (clip.on)
+    ivv::launch_clip_solve<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
+                              (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                              (const int*)(ws + L.counters), v->d_stats, v->num_sms, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[3], s));
   IVV_CUDA(cudaGetLastError());
   return IVV_OK;

@@ -438,11 +438,32 @@ template <typename R>
 void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, bool mixed,
                       bool stats, const SurfaceWs& w, DevStats* st, int num_sms, cudaStream_t s);
 
+// Cutting and near-clip planes (§5.5) applied by K4 to the depth-sorted
+// intersections of each pixel.  Ends that move onto a plane are flagged in
+// pair_block (kSolveIn / kSolveOut, with the chord guess in the pair record)
+// and solved by the clip fix-up kernel before stage 3.
+constexpr int kMaxCutPlanes = IVV_MAX_CUT_PLANES;
+constexpr int kSolveIn = 1 << 30, kSolveOut = 1 << 29, kBlockMask = (1 << 29) - 1;
+template <typename R>
+struct ClipArgs {
+  int on;                       // any plane active
+  R near;                       // > 0: near plane distance along f
+  R f[3];                       // view direction
+  int n_cut;
+  R cut[kMaxCutPlanes][4];      // (n, w): n.g + w > 0 is cut away
+  DevCamera<R> cam;             // the pixels' rays
+};
+
+template <typename R>
+void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                       typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
+                       const int* n_active, DevStats* st, int num_sms, cudaStream_t s);
+
 template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs,
-                 int* active, int* n_active, float4* out_rgba_zero, Dbl4* out_rgba_zero64, DevStats* st,
+                 int* active, int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, DevStats* st,
                  cudaStream_t s);
 
 struct IntegrateArgs {

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
   const R tail_eps = R(1e-12) * R(V.diag);
   const int ns = T.s;
   unsigned long long c_rhs = 0, c_steps = 0, c_samp = 0, c_fp64 = 0;
+  float max_dp = 0.f;
 
   int pix = -1;           // -1: needs a pixel; -2: queue drained
   int q = 0, np = 0, stage = 0, j = 0, nsamp = 0, nlast = 0;
@@ -148,7 +149,10 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
         const R s0 = R(j - 1) * ds;
         composite_interval<R>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rho, s1 - s0, acc);
       }
-      if (STATS) ++c_samp;
+      if (STATS) {
+        ++c_samp;
+        max_dp = fmaxf(max_dp, pixel_error<R>(cam, phi, pix % cam.w, pix / cam.w));
+      }
       rho_prev = rho;
       if (acc.a >= early || j >= nlast) {
         fresh = true;                  // pair (or pixel) done
@@ -188,11 +192,13 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
       c_rhs += __shfl_down_sync(0xffffffffu, c_rhs, o2);
       c_steps += __shfl_down_sync(0xffffffffu, c_steps, o2);
       c_samp += __shfl_down_sync(0xffffffffu, c_samp, o2);
+      max_dp = fmaxf(max_dp, __shfl_down_sync(0xffffffffu, max_dp, o2));
     }
     if (lane == 0) {
       atomicAdd(&st->rhs_evals, c_rhs);
       atomicAdd(&st->rk_steps, c_steps);
       atomicAdd(&st->samples, c_samp);
+      atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
     }
   }
 }

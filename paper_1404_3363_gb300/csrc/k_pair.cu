@@ -54,6 +54,187 @@ __device__ __forceinline__ int pair_pixel(size_t pix, size_t stride, R tau_dup,
   return np;
 }
 
+// pair_pixel with the cutting and near-clip planes (§5.5) of `cl`, for the
+// pixel (xw, yw) of cl.cam's window: records in front of the near plane are
+// dropped; a block whose nearest remaining record is an exit gets an entry on
+// the near plane; every pair is clipped to the kept side of each cutting
+// plane (empty pairs dropped); moved ends carry a chord guess and a solve
+// flag in pair_block.
+template <typename R>
+__device__ __forceinline__ int pair_pixel_clip(size_t pix, size_t stride, R tau_dup,
+                                               const typename Vec4T<R>::type* __restrict__ frag_tp,
+                                               const unsigned* __restrict__ frag_meta,
+                                               const int* __restrict__ frag_count,
+                                               typename Vec4T<R>::type* __restrict__ pair_in,
+                                               typename Vec4T<R>::type* __restrict__ pair_out,
+                                               int* __restrict__ pair_block, int* __restrict__ pair_count,
+                                               int max_pairs, float4* zero_out, unsigned& um, unsigned& pov,
+                                               const ClipArgs<R>& cl, int xw, int yw) {
+  typedef typename Vec4T<R>::type V4;
+  R o[3], d[3];
+  make_ray<R>(cl.cam, cl.cam.x0 + xw, cl.cam.y0 + yw, o, d);
+  R t_near = R(0);
+  if (cl.near > R(0)) t_near = cl.near / (d[0] * cl.f[0] + d[1] * cl.f[1] + d[2] * cl.f[2]);
+  int n0 = frag_count[pix];
+  n0 = n0 < kMaxFrags ? n0 : kMaxFrags;
+  R t[kMaxFrags], pp[kMaxFrags][3];
+  unsigned m[kMaxFrags];
+  int n = 0;
+  for (int i = 0; i < n0; ++i) {
+    const V4 f = frag_tp[(size_t)i * stride + pix];
+    if (cl.near > R(0) && f.x < t_near) continue;
+    t[n] = f.x;
+    pp[n][0] = f.y;
+    pp[n][1] = f.z;
+    pp[n][2] = f.w;
+    m[n] = frag_meta[(size_t)i * stride + pix];
+    ++n;
+  }
+  unsigned synth = 0;                  // bit i: record i is an entry on the near plane
+  if (cl.near > R(0)) {
+    const int nr = n;
+    for (int i = 0; i < nr && n < kMaxFrags; ++i) {
+      if (m[i] & 1u) continue;         // entries need no partner
+      bool nearest = true;
+      for (int k = 0; k < nr; ++k)
+        if ((m[k] >> 4) == (m[i] >> 4) && (t[k] < t[i] || (t[k] == t[i] && k < i))) nearest = false;
+      if (!nearest) continue;
+      t[n] = t_near;
+      pp[n][0] = pp[n][1] = pp[n][2] = R(0);
+      m[n] = (m[i] & ~15u) | 1u;
+      synth |= 1u << n;
+      ++n;
+    }
+  }
+  int in_idx[kMaxPairs], out_idx[kMaxPairs];
+  const int np = pair_fragments<R>(n, t, m, pp, tau_dup, max_pairs, in_idx, out_idx, um, pov);
+  int kept = 0;
+  for (int q = 0; q < np; ++q) {
+    const int a = in_idx[q], b = out_idx[q];
+    R t0 = t[a], t1 = t[b];
+    for (int k = 0; k < cl.n_cut; ++k) {
+      const R fo = cl.cut[k][0] * o[0] + cl.cut[k][1] * o[1] + cl.cut[k][2] * o[2] + cl.cut[k][3];
+      const R fd = cl.cut[k][0] * d[0] + cl.cut[k][1] * d[1] + cl.cut[k][2] * d[2];
+      if (fd == R(0)) {
+        if (fo > R(0)) t1 = t0 - R(1);
+        continue;
+      }
+      const R tc = -fo / fd;
+      if (fd > R(0)) t1 = tc < t1 ? tc : t1;
+      else t0 = tc > t0 ? tc : t0;
+    }
+    if (!(t1 > t0)) continue;
+    const bool s_in = (synth >> a) & 1u;
+    const bool new_in = s_in || t0 > t[a], new_out = t1 < t[b];
+    const R len = t[b] - t[a];
+    R gi[3], go[3];
+    const R w0 = len > R(0) ? (t0 - t[a]) / len : R(0), w1 = len > R(0) ? (t1 - t[a]) / len : R(1);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      gi[r] = s_in ? pp[b][r] : (new_in ? pp[a][r] + w0 * (pp[b][r] - pp[a][r]) : pp[a][r]);
+      go[r] = new_out ? (s_in ? pp[b][r] : pp[a][r] + w1 * (pp[b][r] - pp[a][r])) : pp[b][r];
+    }
+    const size_t o2 = (size_t)kept * stride + pix;
+    V4 ri, ro;
+    ri.x = t0; ri.y = gi[0]; ri.z = gi[1]; ri.w = gi[2];
+    ro.x = t1; ro.y = go[0]; ro.z = go[1]; ro.w = go[2];
+    pair_in[o2] = ri;
+    pair_out[o2] = ro;
+    pair_block[o2] = (int)(m[a] >> 4) | (new_in ? kSolveIn : 0) | (new_out ? kSolveOut : 0);
+    ++kept;
+  }
+  pair_count[pix] = kept;
+  if (kept == 0 && zero_out) *zero_out = make_float4(0.f, 0.f, 0.f, 0.f);
+  return kept;
+}
+
+// Newton for the world point g in block B from p (line search on |F|, p
+// clamped to [0,1]^3, §5.1); true when |phi(p) - g| <= tol.
+template <int P, typename R>
+__device__ __forceinline__ bool clip_newton(const DevVolume& V, const BlockInfo& B, const R g[3], R p[3], R tol) {
+  R phi[3], J[3][3], rc, F[3];
+  eval_block<P, R, false>(V, B, p, phi, J, rc);
+  for (int r = 0; r < 3; ++r) F[r] = phi[r] - g[r];
+  R nF = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+  for (int it = 0; it < 50; ++it) {
+    if (nF <= tol) return true;
+    R rhs[3] = {-F[0], -F[1], -F[2]}, dx[3];
+    solve3<R>(J, rhs, dx);
+    R lam = R(1);
+    bool moved = false;
+    for (int ls = 0; ls < 12 && !moved; ++ls, lam *= R(0.5)) {
+      R q[3], Jq[3][3], Fq[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const R v = p[r] + lam * dx[r];
+        q[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
+      }
+      eval_block<P, R, false>(V, B, q, phi, Jq, rc);
+      for (int r = 0; r < 3; ++r) Fq[r] = phi[r] - g[r];
+      const R nq = sqrt(Fq[0] * Fq[0] + Fq[1] * Fq[1] + Fq[2] * Fq[2]);
+      if (nq < nF) {
+        moved = true;
+        nF = nq;
+        for (int r = 0; r < 3; ++r) {
+          p[r] = q[r];
+          F[r] = Fq[r];
+          for (int k = 0; k < 3; ++k) J[r][k] = Jq[r][k];
+        }
+      }
+    }
+    if (!moved) break;
+  }
+  return nF <= tol;
+}
+
+// The clip fix-up: one thread per active pixel solves the flagged ends of
+// its pairs; a pair whose end does not invert inside its block gets zero
+// length (skipped by stage 3).
+template <int P, typename R>
+__global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> cam, int npix,
+                                                     typename Vec4T<R>::type* __restrict__ pair_in,
+                                                     typename Vec4T<R>::type* __restrict__ pair_out,
+                                                     int* __restrict__ pair_block, const int* __restrict__ pair_count,
+                                                     const int* __restrict__ active,
+                                                     const int* __restrict__ n_active, DevStats* __restrict__ st) {
+  typedef typename Vec4T<R>::type V4;
+  const int nact = *n_active;
+  const R tol = sizeof(R) == 4 ? R(1e-6) * R(V.diag) : R(1e-12) * R(V.diag);
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    R o[3], d[3];
+    make_ray<R>(cam, cam.x0 + pix % cam.w, cam.y0 + pix / cam.w, o, d);
+    for (int q = 0; q < np; ++q) {
+      const size_t slot = (size_t)q * npix + pix;
+      const int bf = pair_block[slot];
+      if (!(bf & (kSolveIn | kSolveOut))) continue;
+      const int blk = bf & kBlockMask;
+      const BlockInfo B = V.blocks[blk];
+      bool ok = true;
+      for (int e = 0; e < 2 && ok; ++e) {
+        if (!(bf & (e == 0 ? kSolveIn : kSolveOut))) continue;
+        V4 rec = e == 0 ? pair_in[slot] : pair_out[slot];
+        R g[3], pq[3] = {R(rec.y), R(rec.z), R(rec.w)};
+        for (int r = 0; r < 3; ++r) g[r] = o[r] + R(rec.x) * d[r];
+        const R tol_g = tol + R(sizeof(R) == 4 ? 2e-7 : 1e-15) *
+                                  (fabs(g[0]) > fabs(g[1]) ? (fabs(g[0]) > fabs(g[2]) ? fabs(g[0]) : fabs(g[2]))
+                                                           : (fabs(g[1]) > fabs(g[2]) ? fabs(g[1]) : fabs(g[2])));
+        ok = clip_newton<P, R>(V, B, g, pq, tol_g);
+        rec.y = pq[0]; rec.z = pq[1]; rec.w = pq[2];
+        if (e == 0) pair_in[slot] = rec; else pair_out[slot] = rec;
+      }
+      if (!ok) {
+        V4 ro = pair_out[slot];
+        ro.x = pair_in[slot].x;          // zero length: dropped by stage 3
+        pair_out[slot] = ro;
+        atomicAdd(&st->unmatched, 1ull);
+      }
+      pair_block[slot] = blk;
+    }
+  }
+}
+
 // Warp-aggregated append of the active pixels to the integrator's queue and
 // the counters that every render keeps.
 __device__ __forceinline__ void pair_epilogue(int pix, int np, unsigned um, unsigned pov, int* __restrict__ active,
@@ -99,16 +280,22 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                                                typename Vec4T<R>::type* __restrict__ pair_out,
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
-                                               float4* __restrict__ out_rgba, DevStats* __restrict__ st) {
+                                               float4* __restrict__ out_rgba, ClipArgs<R> clip,
+                                               DevStats* __restrict__ st) {
   const int tiles_x = (w + 15) / 16;
   int x, y;
   tile_pixel(blockIdx.x % tiles_x, blockIdx.x / tiles_x, x, y);
   const int pix = y * w + x;
   int np = 0;
   unsigned um = 0, pov = 0;
-  if (x < w && pix < npix)
-    np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
-                       pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
+  if (x < w && pix < npix) {
+    if (clip.on)
+      np = pair_pixel_clip<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
+                              pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov, clip, x, y);
+    else
+      np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
+                         pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
+  }
   pair_epilogue(pix, np, um, pov, active, n_active, st);
 }
 
@@ -144,14 +331,15 @@ template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
-                 int* n_active, float4* out_rgba_zero, Dbl4* /*unused*/, DevStats* st, cudaStream_t s) {
+                 int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, DevStats* st, cudaStream_t s) {
   (void)V;
   if (npix <= 0) return;
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
   if (w <= 0) return;
   const int h = npix / w;
   k4_pair<R><<<((w + 15) / 16) * ((h + 15) / 16), 256, 0, s>>>(w, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
-                                                pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, st);
+                                                pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero,
+                                                clip, st);
 }
 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
@@ -162,11 +350,33 @@ void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4*
                                              pair_block, pair_count, active, n_active, st);
 }
 
-template void launch_pair<float>(const DevVolume&, int, int, float, const float4*, const unsigned*, const int*, float4*,
-                                 float4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*, cudaStream_t);
-template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*, const unsigned*, const int*,
-                                  Dbl4*, Dbl4*, int*, int*, int, int*, int*, float4*, Dbl4*, DevStats*,
+template void launch_pair<float>(const DevVolume&, int, int, float, const float4*, const unsigned*, const int*,
+                                 float4*, float4*, int*, int*, int, int*, int*, float4*, const ClipArgs<float>&,
+                                 DevStats*, cudaStream_t);
+template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*, const unsigned*, const int*, Dbl4*,
+                                  Dbl4*, int*, int*, int, int*, int*, float4*, const ClipArgs<double>&, DevStats*,
                                   cudaStream_t);
+
+template <typename R>
+void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                       typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
+                       const int* n_active, DevStats* st, int num_sms, cudaStream_t s) {
+  if (npix <= 0) return;
+  int grid = num_sms * 8;
+  const int useful = (npix + 127) / 128;
+  grid = grid < useful ? grid : useful;
+  if (V.P == 2)
+    k4_clip_solve<2, R><<<grid, 128, 0, s>>>(V, cam, npix, pair_in, pair_out, pair_block, pair_count, active,
+                                             n_active, st);
+  else
+    k4_clip_solve<3, R><<<grid, 128, 0, s>>>(V, cam, npix, pair_in, pair_out, pair_block, pair_count, active,
+                                             n_active, st);
+}
+
+template void launch_clip_solve<float>(const DevVolume&, const DevCamera<float>&, int, float4*, float4*, int*,
+                                       const int*, const int*, const int*, DevStats*, int, cudaStream_t);
+template void launch_clip_solve<double>(const DevVolume&, const DevCamera<double>&, int, Dbl4*, Dbl4*, int*,
+                                        const int*, const int*, const int*, DevStats*, int, cudaStream_t);
 
 }  // namespace ivv
 

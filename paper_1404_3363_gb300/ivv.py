@@ -57,7 +57,8 @@ class RenderParams(C.Structure):
                 ("c", C.c_double), ("early_alpha", C.c_double), ("use_mlp_guess", C.c_int),
                 ("precision", C.c_int), ("flags", C.c_int), ("x0", C.c_int), ("y0", C.c_int),
                 ("full_width", C.c_int), ("full_height", C.c_int), ("method", C.c_int), ("rf_tol", C.c_double),
-                ("rk_method", C.c_int)]
+                ("rk_method", C.c_int), ("near_clip", C.c_double), ("n_cut_planes", C.c_int),
+                ("cut_planes", (C.c_double * 4) * 4)]
 
 
 class GuessTrainParams(C.Structure):
@@ -184,6 +185,14 @@ def params_struct(p=None, flags=0, window=None) -> RenderParams:
     q.method = getattr(p, "method", 0) if p else 0
     q.rf_tol = getattr(p, "rf_tol", 0.05) if p else 0.05
     q.rk_method = getattr(p, "rk_method", 0) if p else 0
+    q.near_clip = getattr(p, "near_clip", 0.0) if p else 0.0
+    planes = list(getattr(p, "cut_planes", ())) if p else []
+    if len(planes) > 4:
+        raise IvvError(1, "at most 4 cutting planes")
+    q.n_cut_planes = len(planes)
+    for k, pl in enumerate(planes):
+        for c in range(4):
+            q.cut_planes[k][c] = float(pl[c])
     q.flags = flags
     if window is not None:
         q.x0, q.y0, q.full_width, q.full_height = window

@@ -99,3 +99,18 @@ def test_fixed_step_argument_errors(ivv):
         prm = dataclasses.replace(sc.params, **bad)
         with pytest.raises(ivv.IvvError, match=msg):
             vol.render(sc.camera, prm, 16, 16)
+
+
+def test_fixed_step_pixel_accuracy_follows_the_order(ivv):
+    """Delta P (Eq. 5) of the samples: Euler's drift off the ray exceeds
+    RK4's by orders of magnitude on the twisted bar."""
+    sc = scenes.config(1, width=96, height=54)
+    dp = {}
+    for method in (1, 4):
+        sc.params.rk_method = method
+        vol = ivv.volume_for(sc)
+        vol.reset_stats()
+        vol.render(sc.camera, sc.params, sc.width, sc.height, flags=ivv.FLAG_STATS)
+        dp[method] = vol.stats()["max_delta_p"]
+    assert dp[1] > 0 and dp[4] >= 0
+    assert dp[1] > 20 * dp[4], dp

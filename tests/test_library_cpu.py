@@ -103,8 +103,8 @@ def _header_struct_fields(name):
         decl = decl.strip()
         if not decl:
             continue
-        # declarator names: identifiers followed by an optional [n] and a comma or the end
-        names = re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])?\s*(?:,|$)", decl)
+        # declarator names: identifiers followed by optional [n] suffixes and a comma or the end
+        names = re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])*\s*(?:,|$)", decl)
         out += [n for n in names if n not in ("const", "double", "float", "int", "unsigned", "long", "void")]
     return out
 
