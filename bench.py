@@ -29,6 +29,8 @@ METRIC = "Mpixels/s & ms/frame at 1920x1080 vs plain FP32, at <=1e-3 max RGBA er
 UNIT = "Mpixels/s"
 WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x1080 perspective, FP32"
 
+RK_NAMES = {1: "Euler (RK1)", 2: "midpoint (RK2)", 3: "Kutta-3 (RK3)", 4: "RK4", 5: "RK4 3/8", 6: "Fehlberg-5 (RKF)"}
+
 # --workload: the default is the headline frame above; the others are the
 # remaining workloads of the method, each printed as its own line.
 WORKLOADS = {
@@ -254,6 +256,9 @@ def run_ours(args):
     cfg, prec, workload = WORKLOADS[args.workload]
     sc = scenes.config(cfg)
     sc.params.precision = prec
+    if args.rk_method:
+        sc.params.rk_method = args.rk_method
+        workload += ", fixed-step %s (one step per sample interval)" % RK_NAMES[args.rk_method]
     W, H = sc.width, sc.height
     stream = torch.cuda.current_stream()
     vol = ivv.volume_for(sc)
@@ -517,6 +522,8 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="batch64: keep the first N requests (0: all)")
     ap.add_argument("--only-volume", type=int, default=None, help="batch64: keep the requests of one volume")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default launch shapes")
+    ap.add_argument("--rk-method", type=int, default=0, choices=range(7),
+                    help="single-frame workloads: 0 BS3(2) with error control, 1-6 the fixed-step family")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -87,7 +87,7 @@ void free_volume(ivv_volume* v) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : v->ev)
     if (e) cudaEventDestroy(e);
-  void* g[] = {v->d_theta, v->d_adam_m, v->d_adam_v, v->d_theta16, v->d_norms, v->rf_buf};
+  void* g[] = {v->d_theta, v->d_adam_m, v->d_adam_v, v->d_theta16, v->d_norms, v->rf_buf, v->ode_buf};
   for (void* p : g)
     if (p) cudaFree(p);
   delete v;
@@ -354,8 +354,20 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   return IVV_OK;
 }
 
+// Sample-list capacity per pixel of the split integration: the pairs of a
+// ray lie in disjoint blocks inside the control-point box, so their lengths
+// add up to at most its diagonal; each pair adds at most two partial samples.
+constexpr double kSplitMaxBytes = 16.0 * (1ull << 30);
+size_t split_bound(const ivv_volume* v, const ivv_render_params& p) {
+  return (size_t)std::ceil(v->hv.diag / p.ds) + 2 * ivv::kMaxPairs + 2;
+}
+double split_bytes(const ivv_volume* v, const ivv_render_params& p, size_t npix) {
+  return (double)split_bound(v, p) * (double)npix * (double)sizeof(float4);
+}
+
 ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width, int height,
-                       float* out, void* workspace, size_t workspace_bytes, cudaStream_t s) {
+                       float* out, void* workspace, size_t workspace_bytes, cudaStream_t s,
+                       bool ws_is_scratch = false) {
   if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
   if (!out) return fail(IVV_ERR_INVALID_ARG, "out_rgba is NULL");
   if (((uintptr_t)out) % 16) return fail(IVV_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned");
@@ -436,7 +448,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,
                           stats, v->num_sms, s);
     ivv::launch_rf_composite(tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act, counters, off,
-                             (int)npix, (float)p.ds, tail_eps, total, sg, srho, (float4*)out, v->d_stats, stats,
+                             (int)npix, (float)p.ds, tail_eps, total, srho, (float4*)out, v->d_stats, stats,
                              v->num_sms, s);
     if (p.flags & IVV_FLAG_TIMING) {
       IVV_CUDA(cudaEventRecord(v->ev[4], s));
@@ -476,6 +488,45 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                              (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
                              (float4*)out, v->d_stats, v->num_sms, s);
+  } else if (split_bytes(v, p, npix) <= kSplitMaxBytes && !ws_is_scratch) {
+    // split integration: sample lists (count, scan), integrator writing the
+    // sample points, scalar at every sample, per-pixel compositing
+    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    const ivv::DevCamera<float> c32 = dev_camera<float>(F);
+    const size_t bound = split_bound(v, p), cap = bound * npix;
+    st = ensure_own(&v->ode_buf, &v->ode_bytes, split_bytes(v, p, npix), s);
+    if (st != IVV_OK) return st;
+    const float4* pin = (const float4*)(ws + L.pair_in);
+    const float4* pout = (const float4*)(ws + L.pair_out);
+    const int* pblk = (const int*)(ws + L.pair_block);
+    const int* pcnt = (const int*)(ws + L.pair_count);
+    const int* act = (const int*)(ws + L.active);
+    int* counters = (int*)(ws + L.counters);
+    int* cnt = (int*)(ws + L.frag_count);             // fragment lists are dead after stage 2
+    int* off = (int*)(ws + L.frag_meta);
+    int* sums = off + npix;
+    const float tail_eps = 1e-12f * (float)v->hv.diag;  // as the integrator computes it
+    ivv::SplitArgs sa;
+    sa.off = off;
+    sa.sp = (float4*)v->ode_buf;
+    sa.spix = nullptr;
+    sa.cap = (int)cap;
+    ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms, s);
+    ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+    if (V.P == 2) {
+      ivv::launch_integrate_split_p<2>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                       counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
+      ivv::launch_shade_composite_p<2>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act,
+                                       counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out, stats,
+                                       v->d_stats, v->num_sms, s);
+    } else {
+      ivv::launch_integrate_split_p<3>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                       counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
+      ivv::launch_shade_composite_p<3>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act,
+                                       counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out, stats,
+                                       v->d_stats, v->num_sms, s);
+    }
   } else {
     st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;
@@ -746,7 +797,8 @@ ivv_status ivv_render_noalloc(ivv_volume* v, const ivv_camera* cam, const ivv_re
   void* scratch = nullptr;
   ivv_status st = noalloc_scratch(&scratch);
   if (st != IVV_OK) return st;
-  return render_impl(v, cam, params, width, height, out_rgba, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
+  return render_impl(v, cam, params, width, height, out_rgba, scratch, kNoAllocScratchBytes, (cudaStream_t)stream,
+                     true);
 }
 
 ivv_status ivv_render_pairs(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params, int width,

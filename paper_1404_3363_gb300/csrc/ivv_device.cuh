@@ -530,7 +530,29 @@ void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_
                       DevStats* st, bool stats, int num_sms, cudaStream_t s);
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
-                         float tail_eps, int cap, const float4* sg, const float* srho, float4* out, DevStats* st,
+                         float tail_eps, int cap, const float* srho, float4* out, DevStats* st,
                          bool stats, int num_sms, cudaStream_t s);
+
+// Split ODE integration (FP32 / MIXED, one frame): K5 with SPLIT writes every
+// sample's parameter point (x, y, z, block as int bits) at its offset in the
+// per-pixel sample list (rf_count / rf_scan); k_shade_composite evaluates the
+// scalar at the samples and composites, one thread per pixel.
+struct SplitArgs {
+  const int* off;      // [active items] first sample of each pixel
+  float4* sp;          // [cap] sample points
+  int* spix;           // unused (kept NULL)
+  int cap;
+};
+template <int P>
+void launch_integrate_split_p(const DevVolume& V, const DevCamera<float>& cam, const IntegrateArgs& a,
+                              const SplitArgs& sa, bool mixed, bool stats, const float4* pin, const float4* pout,
+                              const int* pblk, const int* pcnt, const int* active, const int* n_active,
+                              int* queue_head, DevStats* st, int num_sms, cudaStream_t s);
+template <int P>
+void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, int K, float early,
+                              const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
+                              const int* active, const int* n_active, const int* off, int npix, float ds,
+                              float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st, int num_sms,
+                              cudaStream_t s);
 
 }  // namespace ivv

@@ -133,6 +133,17 @@ __device__ __forceinline__ float pixel_error(const DevCamera<RC>& cam, const R p
   return 2.f * (float)fmax(fabs(sx - RC(cam.x0 + xw)), fabs(sy - RC(cam.y0 + yw)));
 }
 
+// SPLIT: sample slot k of the pixel's list <- (x, block); the pixel for the
+// statistics pass.
+template <typename R>
+__device__ __forceinline__ void split_write(const SplitArgs& sa, int& k, const R x[3], int blk, int pix) {
+  if (k < sa.cap) {
+    sa.sp[k] = make_float4((float)x[0], (float)x[1], (float)x[2], __int_as_float(blk));
+    if (sa.spix) sa.spix[k] = pix;
+  }
+  ++k;
+}
+
 // One lane's position in the integration of its current pixel.
 //   stage 0: start of a pair (evaluate W and rho at p_in);
 //   stages 1..3: the three new right-hand sides of a Bogacki-Shampine step
@@ -145,9 +156,14 @@ __device__ __forceinline__ float pixel_error(const DevCamera<RC>& cam, const R p
 // lane looks up its pixel's request when it takes the pixel and from then on
 // uses that request's camera, sample distance, transfer function slot and
 // image; the block table of the batch's pool carries each block's scalar mode.
-template <int P, typename R, bool MIXED, bool STATS, bool BATCH = false>
+//
+// SPLIT: the lane writes each sample's parameter point (dense output between
+// step ends) to its pixel's sample list instead of evaluating the scalar and
+// compositing; k_shade and rf_composite finish the pixel.  A step then costs
+// only its three right-hand sides.
+template <int P, typename R, bool MIXED, bool STATS, bool BATCH = false, bool SPLIT = false>
 __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
-                                                       BatchArgs ba,
+                                                       BatchArgs ba, SplitArgs sa,
                                                        const typename Vec4T<R>::type* __restrict__ pair_in,
                                                        const typename Vec4T<R>::type* __restrict__ pair_out,
                                                        const int* __restrict__ pair_block,
@@ -159,7 +175,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
   __shared__ unsigned char s_seg[kTfTable];
-  if constexpr (!BATCH) {
+  if constexpr (!BATCH && !SPLIT) {
     for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
       s_r[i] = tf.r[i];
       s_rgba[i] = tf.rgba[i];
@@ -183,6 +199,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   R hmin = R(1e-7) * ds;
   R hmax = R(args.max_step_samples) * ds;
   int rq = 0;             // BATCH: request of the lane's pixel
+  int kidx = 0, blk = 0;  // SPLIT: next sample slot of the pixel, block of the pair
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
   float max_dp = 0.f;
 
@@ -219,6 +236,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
           } else {
             const int xw = pix % cam.w, yw = pix / cam.w;
             make_ray<R>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
+            if constexpr (SPLIT) kidx = __ldg(sa.off + item);
           }
           acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
           np = __ldg(pair_count + pix);
@@ -243,6 +261,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         L = R(po.x) - R(pi.x);
         if (!(L > R(0))) continue;
         B = V.blocks[__ldg(pair_block + slot)];
+        if constexpr (SPLIT) blk = __ldg(pair_block + slot);
 #pragma unroll
         for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pi.x) * d[r];
         p[0] = R(pi.y); p[1] = R(pi.z); p[2] = R(pi.w);
@@ -259,7 +278,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         const float4 res = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
         if constexpr (BATCH)
           ba.req[rq].out[pix - __ldg(ba.pix0 + rq)] = res;
-        else
+        else if constexpr (!SPLIT)
           out[pix] = res;
         pix = -1;
         live = false;
@@ -294,7 +313,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     }
     // ---- the one right-hand side of this iteration (converged across lanes)
     R W[3], rho, phi[3];
-    rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
+    rhs_eval<P, R, MIXED, !SPLIT>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
     if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
@@ -302,7 +321,11 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     if (stage == 0) {
       k1[0] = W[0]; k1[1] = W[1]; k1[2] = W[2];
       rho_prev = rho;
-      if (STATS) ++c_samp;
+      if constexpr (SPLIT) {
+        split_write(sa, kidx, x, blk, pix);          // sample s_0 = 0: the entry point
+      } else if (STATS) {
+        ++c_samp;
+      }
     } else if (stage == 1) {
       k2[0] = W[0]; k2[1] = W[1]; k2[2] = W[2];
     } else if (stage == 2) {
@@ -339,7 +362,40 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
         h = hh * fac;
         if (capped) {
+          if constexpr (SPLIT)
+            for (; j <= nlast; ++j) split_write(sa, kidx, p, blk, pix);   // keep the list complete
           stage = 0;
+          continue;
+        }
+        if constexpr (SPLIT) {
+          // the samples inside (s0, s]: dense output, or the step end itself
+          for (; j <= nlast; ++j) {
+            const R s_t = (j <= nsamp) ? R(j) * ds : L;
+            if (s_t > s) break;
+            R xs[3];
+            if (s_t < s) {
+              const R th = (s_t - s0) / hh;
+              const R t2 = th * th, t3 = t2 * th;
+              const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + th;
+              const R h01 = R(3) * t2 - R(2) * t3, h11 = t3 - t2;
+#pragma unroll
+              for (int r = 0; r < 3; ++r) {
+                const R v = h00 * p0[r] + h10 * hh * k0[r] + h01 * p[r] + h11 * hh * k1[r];
+                xs[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
+              }
+            } else {
+              xs[0] = p[0]; xs[1] = p[1]; xs[2] = p[2];
+            }
+            split_write(sa, kidx, xs, blk, pix);
+          }
+          if (j > nlast) {
+            stage = 0;       // pair done
+            continue;
+          }
+          const R rem = L - s;
+          hh = h < hmax ? h : hmax;
+          hh = hh < rem ? hh : rem;
+          stage = 1;
           continue;
         }
         stage = 4;           // visit the samples inside (s0, s]
@@ -472,8 +528,224 @@ void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, con
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
   BatchArgs none{};
-  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, pin, pout, pblk, pcnt, active, n_active,
-                                                         queue_head, out, st);
+  SplitArgs nos{};
+  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, nos, pin, pout, pblk, pcnt, active,
+                                                         n_active, queue_head, out, st);
+}
+
+// ---- split integration: sample shading
+// The scalar field alone at parameter point p of block B (control-point
+// scalars): one contraction of the 64 scalar coefficients.
+template <int P>
+__device__ __forceinline__ float eval_rho_cp(const DevVolume& V, const BlockInfo& B, const float p[3]) {
+  constexpr int N = P + 1;
+  float loc[3];
+  int e[3];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    float x = p[dd];
+    x = x < 0.f ? 0.f : (x > 1.f ? 1.f : x);
+    if ((B.uniform >> dd) & 1) {
+      const float xs = x * (float)B.nseg[dd];
+      int k = (int)xs;
+      k = k < B.nseg[dd] - 1 ? k : B.nseg[dd] - 1;
+      e[dd] = k;
+      loc[dd] = xs - (float)k;
+    } else {
+      float sc;
+      e[dd] = locate<float>(V.brk32 + B.brk_off[dd], B.nseg[dd], x, loc[dd], sc);
+    }
+  }
+  const size_t base = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]) * (N * N * N);
+  float bu[N], bv[N], bw[N];
+  bernstein_v<P, float>(loc[0], bu);
+  bernstein_v<P, float>(loc[1], bv);
+  bernstein_v<P, float>(loc[2], bw);
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float si = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float sj = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k) sj += bw[k] * __ldg(V.elem32 + base + (i * N + j) * N + k).w;
+      si += bv[j] * sj;
+    }
+    s += bu[i] * si;
+  }
+  return s;
+}
+
+// det J with the cofactor expansion of solve3 (same rounding as the fused
+// integrator's scalar).
+__device__ __forceinline__ float det_cofactor(const float J[3][3]) {
+  const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  return J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+}
+
+// Shading and compositing of the split integration: one thread per active
+// pixel walks its sample list in front-to-back order (pairs in order, s_j =
+// j ds with the last interval partial), evaluates the scalar at each sample
+// point (control points, det J or Eq. 23) and composites every interval with
+// K sub-samples (Alg. 1), stopping at early_alpha.  Neighbouring lanes are
+// neighbouring pixels at the same sample index, so their control-point loads
+// hit the same elements.  With statistics also Delta P (Eq. 5) per sample.
+template <int P, bool STATS>
+__global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<float> cam, DevTF tf, int K,
+                                                         float early, const float4* __restrict__ pair_in,
+                                                         const float4* __restrict__ pair_out,
+                                                         const int* __restrict__ pair_block,
+                                                         const int* __restrict__ pair_count,
+                                                         const int* __restrict__ active,
+                                                         const int* __restrict__ n_active, const int* __restrict__ off,
+                                                         int npix, float ds, float tail_eps, int cap,
+                                                         const float4* __restrict__ sp, float4* __restrict__ out,
+                                                         DevStats* __restrict__ st) {
+  __shared__ float s_r[256];
+  __shared__ float4 s_rgba[256];
+  __shared__ unsigned char s_seg[kTfTable];
+  for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
+    s_r[i] = tf.r[i];
+    s_rgba[i] = tf.rgba[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
+    const float x = (float)i / (float)kTfTable;
+    int k = 0;
+    while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
+    s_seg[i] = (unsigned char)k;
+  }
+  __syncthreads();
+  const int nact = *n_active;
+  unsigned long long c_samp = 0;
+  float max_dp = 0.f;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    int k = off[item];
+    Acc<float> acc;
+    acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;
+    bool done = false;
+    for (int q = 0; q < np && !done; ++q) {
+      const size_t slot = (size_t)q * npix + pix;
+      const float4 pi = pair_in[slot], po = pair_out[slot];
+      const float L = po.x - pi.x;
+      if (!(L > 0.f)) continue;
+      const BlockInfo B = V.blocks[pair_block[slot]];
+      const float fl = floorf(L / ds);
+      const int nsamp = (int)fl;
+      const int nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
+      float rho_prev = 0.f, s_prev = 0.f;
+      for (int j = 0; j <= nlast; ++j, ++k) {
+        if (k >= cap) {
+          done = true;
+          break;
+        }
+        const float4 r = sp[k];
+        const float p[3] = {r.x, r.y, r.z};
+        float rho;
+        if (!STATS && V.mode == IVV_SCALAR_CP) {
+          rho = eval_rho_cp<P>(V, B, p);
+        } else {
+          float phi[3], J[3][3], rc;
+          if (V.mode == IVV_SCALAR_CP)
+            eval_block<P, float, true>(V, B, p, phi, J, rc);
+          else
+            eval_block<P, float, false>(V, B, p, phi, J, rc);
+          if (V.mode == IVV_SCALAR_CP) {
+            rho = rc;
+          } else {
+            const float det = det_cofactor(J);
+            if (V.mode == IVV_SCALAR_DETJ) {
+              rho = det;
+            } else {
+              float f = 0.f;
+#pragma unroll
+              for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) f += J[a][b] * J[a][b];
+              rho = det / sqrtf(f);
+            }
+          }
+          if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cam, phi, pix % cam.w, pix / cam.w));
+        }
+        const float s = j <= nsamp ? (float)j * ds : L;
+        if (STATS) ++c_samp;
+        if (j > 0) {
+          composite_interval<float>(s_r, s_rgba, s_seg, tf, K, rho_prev, rho, s - s_prev, acc);
+          if (acc.a >= early) {
+            done = true;
+            break;
+          }
+        }
+        rho_prev = rho;
+        s_prev = s;
+      }
+    }
+    out[pix] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      c_samp += __shfl_down_sync(0xffffffffu, c_samp, o2);
+      max_dp = fmaxf(max_dp, __shfl_down_sync(0xffffffffu, max_dp, o2));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&st->samples, c_samp);
+      atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
+    }
+  }
+}
+
+template <int P, bool MIXED, bool STATS>
+void launch_k5_split(const DevVolume& V, const DevCamera<float>& cam, const IntegrateArgs& a, const SplitArgs& sa,
+                     const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
+                     const int* n_active, int* queue_head, DevStats* st, int num_sms, cudaStream_t s) {
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k5_integrate<P, float, MIXED, STATS, false, true>,
+                                                  128, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  int grid = num_sms * blocks_per_sm;
+  const int max_useful = (a.npix + 127) / 128;
+  if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
+  BatchArgs none{};
+  DevTF tf{};
+  k5_integrate<P, float, MIXED, STATS, false, true><<<grid, 128, 0, s>>>(V, cam, tf, a, none, sa, pin, pout, pblk,
+                                                                         pcnt, active, n_active, queue_head,
+                                                                         nullptr, st);
+}
+
+template <int P>
+void launch_integrate_split_p(const DevVolume& V, const DevCamera<float>& cam, const IntegrateArgs& a,
+                              const SplitArgs& sa, bool mixed, bool stats, const float4* pin, const float4* pout,
+                              const int* pblk, const int* pcnt, const int* active, const int* n_active,
+                              int* queue_head, DevStats* st, int num_sms, cudaStream_t s) {
+#define IVV_K5S(MM, SS)   launch_k5_split<P, MM, SS>(V, cam, a, sa, pin, pout, pblk, pcnt, active, n_active, queue_head, st, num_sms, s)
+  if (mixed) { if (stats) IVV_K5S(true, true); else IVV_K5S(true, false); }
+  else { if (stats) IVV_K5S(false, true); else IVV_K5S(false, false); }
+#undef IVV_K5S
+}
+
+template <int P>
+void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, int K, float early,
+                              const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
+                              const int* active, const int* n_active, const int* off, int npix, float ds,
+                              float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st, int num_sms,
+                              cudaStream_t s) {
+  int grid = num_sms * 8;
+  const int useful = (npix + 127) / 128;
+  grid = grid < useful ? grid : (useful > 0 ? useful : 1);
+  if (stats)
+    k_shade_composite<P, true><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active,
+                                                     off, npix, ds, tail_eps, sa.cap, sa.sp, out, st);
+  else
+    k_shade_composite<P, false><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active,
+                                                      off, npix, ds, tail_eps, sa.cap, sa.sp, out, st);
 }
 
 template <int P>

@@ -12,8 +12,9 @@ void launch_kb5(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a,
                 int* queue_head, DevStats* st, int grid, cudaStream_t s) {
   DevCamera<float> cam{};
   DevTF tf{};
-  k5_integrate<P, float, MIXED, STATS, true><<<grid, 128, 0, s>>>(V, cam, tf, a, ba, pin, pout, pblk, pcnt, active,
-                                                                  n_active, queue_head, nullptr, st);
+  SplitArgs nos{};
+  k5_integrate<P, float, MIXED, STATS, true><<<grid, 128, 0, s>>>(V, cam, tf, a, ba, nos, pin, pout, pblk, pcnt,
+                                                                  active, n_active, queue_head, nullptr, st);
 }
 
 template <int P, bool MIXED, bool STATS>

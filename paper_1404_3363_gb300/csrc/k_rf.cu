@@ -15,7 +15,8 @@
 //                      sample's depth (the paper's pixel-accuracy criterion);
 //                      the scalar at the converged point
 //   R5 rf_composite -- per pixel, Alg. 1 with supersampling over its samples
-//                      in front-to-back order, early termination
+//                      in front-to-back order, early termination (also the
+//                      compositing pass of the split ODE integrator)
 #include <cuda_runtime.h>
 
 #include "ivv_device.cuh"
@@ -286,7 +287,7 @@ __global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __res
                                const float4* __restrict__ pair_out, const int* __restrict__ pair_block,
                                const int* __restrict__ pair_count, const int* __restrict__ active,
                                const int* __restrict__ n_active, const int* __restrict__ off, int npix, float ds,
-                               float tail_eps, int cap, const float4* __restrict__ sg, const float* __restrict__ srho,
+                               float tail_eps, int cap, const float* __restrict__ srho,
                                float4* __restrict__ out, DevStats* __restrict__ st, bool stats) {
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
@@ -321,7 +322,7 @@ __global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __res
           break;
         }
         const float rho = srho[k];
-        const float s = sg[k].w;
+        const float s = j <= v.nsamp ? (float)j * ds : v.L;
         ++c_samp;
         if (j > 0 && !done) {
           const float invK = 1.f / (float)K;
@@ -403,10 +404,10 @@ void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_
 
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
-                         float tail_eps, int cap, const float4* sg, const float* srho, float4* out, DevStats* st,
+                         float tail_eps, int cap, const float* srho, float4* out, DevStats* st,
                          bool stats, int num_sms, cudaStream_t s) {
   k_rf_composite<<<num_sms * 8, 128, 0, s>>>(tf, K, early, pin, pout, pblk, pcnt, active, n_active, off, npix, ds,
-                                             tail_eps, cap, sg, srho, out, st, stats);
+                                             tail_eps, cap, srho, out, st, stats);
 }
 
 }  // namespace ivv

@@ -54,4 +54,7 @@ struct ivv_volume {
   // RF sample buffers (grown on demand)
   void* rf_buf = nullptr;
   size_t rf_bytes = 0;
+  // sample lists of the split ODE integration (grown on demand)
+  void* ode_buf = nullptr;
+  size_t ode_bytes = 0;
 };
