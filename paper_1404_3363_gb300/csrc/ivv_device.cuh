@@ -146,8 +146,17 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
                                                const float dbv[P + 1], const float bw[P + 1],
                                                const float dbw[P + 1], float f[3], float fu[3], float fv[3],
                                                float fw[3], float& rho);
+template <int P>
+__device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp, const float bu[P + 1],
+                                                   const float dbu[P + 1], const float bv[P + 1],
+                                                   const float dbv[P + 1], const float bw[P + 1],
+                                                   const float dbw[P + 1], float f[3], float fu[3], float fv[3],
+                                                   float fw[3]);
 
-template <int P, typename R, bool WANT_RHO>
+// XYZ selects the contraction without the scalar channel (fewer paired
+// multiply-adds, same results; the integrator keeps the plain form, for which
+// the compiler allocates its registers better).
+template <int P, typename R, bool WANT_RHO, bool XYZ = false>
 __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& B, const R p[3], R phi[3],
                                            R J[3][3], R& rho) {
   constexpr int N = P + 1;
@@ -178,7 +187,10 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
   R f[3] = {0, 0, 0}, fu[3] = {0, 0, 0}, fv[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
   R s = 0;
   if constexpr (sizeof(R) == 4) {
-    contract_f32x2<P, WANT_RHO>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw, s);
+    if constexpr (XYZ && !WANT_RHO)
+      contract_f32x2_xyz<P>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw);
+    else
+      contract_f32x2<P, WANT_RHO>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw, s);
   } else {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -279,6 +291,58 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
   fv[0] = fvxy.x; fv[1] = fvxy.y; fv[2] = fvzr.x;
   fw[0] = fwxy.x; fw[1] = fwxy.y; fw[2] = fwzr.x;
   rho = fzr.y;
+}
+
+// The same contraction without the scalar channel: the pairs are (x, y) of
+// the value and of each derivative, and the z channel travels paired with
+// itself under two different weights ((b, db) or (b_u, b_u) on two partial
+// sums).  Every output is the same chain of fused multiply-adds in the same
+// order as above, so phi and J agree bit for bit; the w contraction of a
+// cubic point takes 192 paired multiply-adds instead of 256.
+template <int P>
+__device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp, const float bu[P + 1],
+                                                   const float dbu[P + 1], const float bv[P + 1],
+                                                   const float dbv[P + 1], const float bw[P + 1],
+                                                   const float dbw[P + 1], float f[3], float fu[3], float fv[3],
+                                                   float fw[3]) {
+  constexpr int N = P + 1;
+  const float2 z2 = make_float2(0.f, 0.f);
+  // (f, fu).z and (fv, fw).z share pairs
+  float2 fxy = z2, fuxy = z2, fvxy = z2, fwxy = z2, f_fu_z = z2, fv_fw_z = z2;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    float2 s00xy = z2, s01xy = z2, s10xy = z2, s00_s01_z = z2;
+    float s10z = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float2 t0xy = z2, t1xy = z2, t01z = z2;   // t01z = (t0.z, t1.z)
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float4 c = __ldg(cp + (i * N + j) * N + k);
+        const float2 cxy = make_float2(c.x, c.y), czz = make_float2(c.z, c.z);
+        t0xy = __ffma2_rn(make_float2(bw[k], bw[k]), cxy, t0xy);
+        t1xy = __ffma2_rn(make_float2(dbw[k], dbw[k]), cxy, t1xy);
+        t01z = __ffma2_rn(make_float2(bw[k], dbw[k]), czz, t01z);
+      }
+      const float2 b = make_float2(bv[j], bv[j]), db = make_float2(dbv[j], dbv[j]);
+      s00xy = __ffma2_rn(b, t0xy, s00xy);
+      s01xy = __ffma2_rn(db, t0xy, s01xy);
+      s10xy = __ffma2_rn(b, t1xy, s10xy);
+      s00_s01_z = __ffma2_rn(make_float2(bv[j], dbv[j]), make_float2(t01z.x, t01z.x), s00_s01_z);
+      s10z = __fmaf_rn(bv[j], t01z.y, s10z);
+    }
+    const float2 b = make_float2(bu[i], bu[i]), db = make_float2(dbu[i], dbu[i]);
+    fxy = __ffma2_rn(b, s00xy, fxy);
+    fuxy = __ffma2_rn(db, s00xy, fuxy);
+    fvxy = __ffma2_rn(b, s01xy, fvxy);
+    fwxy = __ffma2_rn(b, s10xy, fwxy);
+    f_fu_z = __ffma2_rn(make_float2(bu[i], dbu[i]), make_float2(s00_s01_z.x, s00_s01_z.x), f_fu_z);
+    fv_fw_z = __ffma2_rn(b, make_float2(s00_s01_z.y, s10z), fv_fw_z);
+  }
+  f[0] = fxy.x; f[1] = fxy.y; f[2] = f_fu_z.x;
+  fu[0] = fuxy.x; fu[1] = fuxy.y; fu[2] = f_fu_z.y;
+  fv[0] = fvxy.x; fv[1] = fvxy.y; fv[2] = fv_fw_z.x;
+  fw[0] = fwxy.x; fw[1] = fwxy.y; fw[2] = fv_fw_z.y;
 }
 
 template <typename R>

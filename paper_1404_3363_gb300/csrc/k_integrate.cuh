@@ -91,37 +91,58 @@ template <> __device__ __forceinline__ double fast_exp<double>(double x) { retur
 // [r_0, r_{n-1}]; when both interval ends fall into the same piece, the K
 // sub-sample colours are the same linear interpolation of the two end
 // colours, so two TF lookups serve all K sub-samples.
-template <typename R>
-__device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const unsigned char* s_seg,
-                                                   const DevTF& tf, int K, R rho0, R rho1, R dsi, Acc<R>& acc) {
-  const R invK = R(1) / R(K);
+// KC > 0: K is the compile-time constant KC (loop unrolled, the piece test
+// hoisted); KC = 0: K at run time.  Both round identically.
+template <typename R, int KC>
+__device__ __forceinline__ void composite_interval_k(const float* s_r, const float4* s_rgba,
+                                                     const unsigned char* s_seg, const DevTF& tf, int K, R rho0,
+                                                     R rho1, R dsi, Acc<R>& acc) {
+  const int nk = KC > 0 ? KC : K;
+  const R invK = KC > 0 ? R(1.0 / KC) : R(1) / R(K);
   const R dr = rho1 - rho0;
   const R tau_scale = R(tf.sigma) * dsi * invK;
   const R x0 = (rho0 - R(tf.lo)) * R(tf.inv_range), x1 = (rho1 - R(tf.lo)) * R(tf.inv_range);
   int g0, g1;
   const float4 c0 = tf_eval_seg(s_r, s_rgba, s_seg, tf.n, (float)x0, g0);
   const float4 c1 = tf_eval_seg(s_r, s_rgba, s_seg, tf.n, (float)x1, g1);
-  const bool same = g0 == g1;
-  for (int k = 0; k < K; ++k) {
-    const R fk = (R(k) + R(0.5)) * invK;
-    float4 c;
-    if (same) {
-      const float f = (float)fk;
-      c = make_float4(c0.x + f * (c1.x - c0.x), c0.y + f * (c1.y - c0.y), c0.z + f * (c1.z - c0.z),
-                      c0.w + f * (c1.w - c0.w));
-    } else {
+  if (g0 == g1) {
+    const float4 dc = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
+#pragma unroll
+    for (int k = 0; k < nk; ++k) {
+      const float f = (float)((R(k) + R(0.5)) * invK);
+      const float4 c = make_float4(c0.x + f * dc.x, c0.y + f * dc.y, c0.z + f * dc.z, c0.w + f * dc.w);
+      const R T = fast_exp<R>(-tau_scale * R(c.w));
+      const R w = (R(1) - T) * (R(1) - acc.a);
+      acc.C[0] += w * R(c.x);
+      acc.C[1] += w * R(c.y);
+      acc.C[2] += w * R(c.z);
+      acc.a += w;
+    }
+  } else {
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+      const R fk = (R(k) + R(0.5)) * invK;
       const R rk = rho0 + fk * dr;
       R x = (rk - R(tf.lo)) * R(tf.inv_range);
       x = x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
-      c = tf_eval(s_r, s_rgba, s_seg, tf.n, (float)x);
+      const float4 c = tf_eval(s_r, s_rgba, s_seg, tf.n, (float)x);
+      const R T = fast_exp<R>(-tau_scale * R(c.w));
+      const R w = (R(1) - T) * (R(1) - acc.a);
+      acc.C[0] += w * R(c.x);
+      acc.C[1] += w * R(c.y);
+      acc.C[2] += w * R(c.z);
+      acc.a += w;
     }
-    const R T = fast_exp<R>(-tau_scale * R(c.w));
-    const R w = (R(1) - T) * (R(1) - acc.a);
-    acc.C[0] += w * R(c.x);
-    acc.C[1] += w * R(c.y);
-    acc.C[2] += w * R(c.z);
-    acc.a += w;
   }
+}
+
+template <typename R>
+__device__ __forceinline__ void composite_interval(const float* s_r, const float4* s_rgba, const unsigned char* s_seg,
+                                                   const DevTF& tf, int K, R rho0, R rho1, R dsi, Acc<R>& acc) {
+  if (K == 4)
+    composite_interval_k<R, 4>(s_r, s_rgba, s_seg, tf, K, rho0, rho1, dsi, acc);
+  else
+    composite_interval_k<R, 0>(s_r, s_rgba, s_seg, tf, K, rho0, rho1, dsi, acc);
 }
 
 // Pixel-accuracy error Delta P (Eq. 5) of the world point phi for pixel
@@ -654,7 +675,7 @@ __global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<
           if (V.mode == IVV_SCALAR_CP)
             eval_block<P, float, true>(V, B, p, phi, J, rc);
           else
-            eval_block<P, float, false>(V, B, p, phi, J, rc);
+            eval_block<P, float, false, true>(V, B, p, phi, J, rc);
           if (V.mode == IVV_SCALAR_CP) {
             rho = rc;
           } else {
