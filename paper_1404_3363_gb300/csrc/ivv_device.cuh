@@ -140,6 +140,26 @@ template <> struct ElemPtr<double> {
 // field at parameter point p of block `blk`.  Sum-factorised: for each i the
 // (j,k) slab is contracted along w (value and w-derivative), then along v,
 // then the u contraction accumulates -- 576 FMA for P = 3.
+// One row of N control points (fixed i, j) of a cubic element.  For N = 4
+// the row is two 256-bit loads: every element starts at a multiple of 64
+// control points in an allocation aligned to 256 bytes, so rows and their
+// halves are 32-byte aligned.
+__device__ __forceinline__ void ldg_cp2(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+template <int N>
+__device__ __forceinline__ void ldg_row(const float4* __restrict__ p, float4 c[N]) {
+  if constexpr (N == 4) {
+    ldg_cp2(p, c[0], c[1]);
+    ldg_cp2(p + 2, c[2], c[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) c[k] = __ldg(p + k);
+  }
+}
+
 template <int P, bool WANT_RHO>
 __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
                                                const float dbu[P + 1], const float bv[P + 1],
@@ -258,9 +278,11 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       float2 t0xy = z2, t0zr = z2, t1xy = z2, t1zr = z2;
+      float4 row[N];
+      ldg_row<N>(cp + (i * N + j) * N, row);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const float4 c = __ldg(cp + (i * N + j) * N + k);
+        const float4 c = row[k];
         const float2 cxy = make_float2(c.x, c.y), czr = make_float2(c.z, c.w);
         const float2 b = make_float2(bw[k], bw[k]), db = make_float2(dbw[k], dbw[k]);
         t0xy = __ffma2_rn(b, cxy, t0xy);
@@ -316,9 +338,11 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       float2 t0xy = z2, t1xy = z2, t01z = z2;   // t01z = (t0.z, t1.z)
+      float4 row[N];
+      ldg_row<N>(cp + (i * N + j) * N, row);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const float4 c = __ldg(cp + (i * N + j) * N + k);
+        const float4 c = row[k];
         const float2 cxy = make_float2(c.x, c.y), czz = make_float2(c.z, c.z);
         t0xy = __ffma2_rn(make_float2(bw[k], bw[k]), cxy, t0xy);
         t1xy = __ffma2_rn(make_float2(dbw[k], dbw[k]), cxy, t1xy);
