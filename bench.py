@@ -53,6 +53,9 @@ WORKLOADS = {
 F_RHS = 1283      # one W(p): 576-FMA sum-factorised phi+J, Bernstein basis, V, 3x3 adjugate solve
 F_STEP = 70       # stage combinations, clamps and error norm of one BS3(2) step attempt
 F_SAMPLE = 150    # K=4 supersampled TF lookups + Alg. 1 updates + Eq. 23 per sample
+# scalar at a sample evaluated on its own (shading pass of the split integration)
+F_RHO_J = 1220    # det J or Eq. 23: 564-FMA sum-factorised J, Bernstein basis, det, Frobenius norm
+F_RHO_CP = 200    # scalar control points: 84-FMA contraction and the value basis
 # ray/patch intersection (K2)
 F_HULL = 260      # per (pixel, patch) item: control points into the ray frame (16 x 6 FMA), hull, Jacobian sign
 F_NEWTON = 230    # one 2-D Newton iteration on a bicubic patch (value, 2 partials, 2x2 solve)
@@ -270,7 +273,8 @@ def run_ours(args):
     vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS)
     st = vol.stats()
     flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
-                + st["samples"] * F_SAMPLE)
+                + st["samples"] * F_SAMPLE
+                + st["rho_evals"] * (F_RHO_CP if sc.scalar_mode == scenes.SCALAR_CP else F_RHO_J))
     flops_k2 = st["isect_items"] * F_HULL + st["isect_newton"] * F_NEWTON + st["fragments"] * F_FRAG
 
     # parity spot check of this frame against the oracle (untimed)
@@ -371,7 +375,8 @@ def run_ours(args):
             "roofline": roofs[0],
             "roofline_kernels": roofs,
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
-                                        "fragments", "isect_items", "isect_split", "isect_tests", "isect_newton")},
+                                        "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
+                                        "isect_newton")},
             "max_delta_p": st["max_delta_p"],
             "parity_max_rgba_err_sampled": max_err,
             "clocks": clocks,
@@ -500,7 +505,8 @@ def run_batch(args):
                          "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
                          "flops_per_launch": flops_k5, "ms_per_launch": k5_ms},
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
-                                        "fragments", "isect_items", "isect_split", "isect_tests", "isect_newton")},
+                                        "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
+                                        "isect_newton")},
             "parity_max_rgba_err_sampled": max_err,
             "clocks": clocks,
         }

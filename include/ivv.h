@@ -212,6 +212,7 @@ typedef struct {
   unsigned long long rf_unconverged;  /* RF: samples that missed the tolerance  */
   unsigned long long isect_items;   /* (pixel, patch) candidates after the box tests */
   unsigned long long isect_split;   /* candidates that needed the subdivision search */
+  unsigned long long rho_evals;     /* samples whose scalar was evaluated on its own (shading pass) */
   double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
 } ivv_stats;
 

@@ -510,7 +510,6 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     ivv::SplitArgs sa;
     sa.off = off;
     sa.sp = (float4*)v->ode_buf;
-    sa.spix = nullptr;
     sa.cap = (int)cap;
     ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms, s);
     ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
@@ -1096,6 +1095,7 @@ void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->rf_unconverged = d.rf_unconverged;
   out->isect_items = d.isect_items;
   out->isect_split = d.isect_split;
+  out->rho_evals = d.rho_evals;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;

@@ -60,7 +60,7 @@ struct DevTF {
 struct DevStats {
   unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
       isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap, rf_newton_iters,
-      rf_unconverged, isect_items, isect_split;
+      rf_unconverged, isect_items, isect_split, rho_evals;
   unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
   unsigned int pad;
 };
@@ -136,10 +136,6 @@ template <> struct ElemPtr<double> {
   }
 };
 
-// phi, J (J[r][c] = d phi_r / d p_c) and optionally the scalar control-point
-// field at parameter point p of block `blk`.  Sum-factorised: for each i the
-// (j,k) slab is contracted along w (value and w-derivative), then along v,
-// then the u contraction accumulates -- 576 FMA for P = 3.
 // One row of N control points (fixed i, j) of a cubic element.  For N = 4
 // the row is two 256-bit loads: every element starts at a multiple of 64
 // control points in an allocation aligned to 256 bytes, so rows and their
@@ -160,6 +156,7 @@ __device__ __forceinline__ void ldg_row(const float4* __restrict__ p, float4 c[N
   }
 }
 
+// The paired contractions of eval_block (defined below).
 template <int P, bool WANT_RHO>
 __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
                                                const float dbu[P + 1], const float bv[P + 1],
@@ -173,6 +170,10 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
                                                    const float dbw[P + 1], float f[3], float fu[3], float fv[3],
                                                    float fw[3]);
 
+// phi, J (J[r][c] = d phi_r / d p_c) and optionally the scalar control-point
+// field at parameter point p of block `blk`.  Sum-factorised: for each i the
+// (j,k) slab is contracted along w (value and w-derivative), then along v,
+// then the u contraction accumulates -- 576 FMA for P = 3.
 // XYZ selects the contraction without the scalar channel (fewer paired
 // multiply-adds, same results; the integrator keeps the plain form, for which
 // the compiler allocates its registers better).
@@ -621,14 +622,13 @@ void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin,
                          float tail_eps, int cap, const float* srho, float4* out, DevStats* st,
                          bool stats, int num_sms, cudaStream_t s);
 
-// Split ODE integration (FP32 / MIXED, one frame): K5 with SPLIT writes every
-// sample's parameter point (x, y, z, block as int bits) at its offset in the
-// per-pixel sample list (rf_count / rf_scan); k_shade_composite evaluates the
-// scalar at the samples and composites, one thread per pixel.
+// Split ODE integration (FP32 / MIXED, one frame): the trace kernel K5t
+// writes every sample's parameter point (x, y, z, block as int bits) at its
+// offset in the per-pixel sample list (rf_count / rf_scan); k_shade_composite
+// evaluates the scalar at the samples and composites, one thread per pixel.
 struct SplitArgs {
   const int* off;      // [active items] first sample of each pixel
   float4* sp;          // [cap] sample points
-  int* spix;           // unused (kept NULL)
   int cap;
 };
 template <int P>

@@ -77,6 +77,33 @@ template <typename R> __device__ __forceinline__ R last_end(R s, R hh, R L) {
   return e >= L ? L : e;
 }
 
+// Bogacki-Shampine 3(2) arithmetic shared by the fused integrator and the
+// trace kernel (k_trace.cuh), written as explicit fused multiply-adds so both
+// kernels round alike and take the same steps.
+template <typename R> __device__ __forceinline__ R fmar(R a, R b, R c);   // a b + c
+template <> __device__ __forceinline__ float fmar<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fmar<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+// stage points q2 = p + hh/2 k1, q3 = p + 3hh/4 k2
+template <typename R> __device__ __forceinline__ R bs3_q2(R p, R hh, R k1) { return fmar(R(0.5) * hh, k1, p); }
+template <typename R> __device__ __forceinline__ R bs3_q3(R p, R hh, R k2) { return fmar(R(0.75) * hh, k2, p); }
+// third-order solution p + hh (2/9 k1 + 1/3 k2 + 4/9 k3)
+template <typename R> __device__ __forceinline__ R bs3_pn(R p, R hh, R k1, R k2, R k3) {
+  return fmar(hh, fmar(R(4.0 / 9.0), k3, fmar(R(1.0 / 3.0), k2, R(2.0 / 9.0) * k1)), p);
+}
+// error combination without the k4 term, and the local error with it
+template <typename R> __device__ __forceinline__ R bs3_e3(R k1, R k2, R k3) {
+  return fmar(R(1.0 / 9.0), k3, fmar(R(1.0 / 12.0), k2, R(-5.0 / 72.0) * k1));
+}
+template <typename R> __device__ __forceinline__ R bs3_err(R hh, R e3, R k4) { return hh * fmar(R(-1.0 / 8.0), k4, e3); }
+// cubic Hermite dense output at th in [0, 1] of a step of length hh from
+// (p0, k0) to (p1, k1)
+template <typename R> __device__ __forceinline__ R hermite(R th, R hh, R p0, R k0, R p1, R k1) {
+  const R t2 = th * th, t3 = t2 * th;
+  const R h00 = fmar(R(2), t3, fmar(R(-3), t2, R(1))), h10 = fmar(R(-2), t2, t3 + th);
+  const R h01 = fmar(R(-2), t3, R(3) * t2), h11 = t3 - t2;
+  return fmar(h11 * hh, k1, fmar(h01, p1, fmar(h10 * hh, k0, h00 * p0)));
+}
+
 template <typename R> __device__ __forceinline__ R pow_third(R x);
 template <> __device__ __forceinline__ float pow_third<float>(float x) { return exp2f(__log2f(x) * (1.f / 3.f)); }
 template <> __device__ __forceinline__ double pow_third<double>(double x) { return cbrt(x); }
@@ -154,17 +181,6 @@ __device__ __forceinline__ float pixel_error(const DevCamera<RC>& cam, const R p
   return 2.f * (float)fmax(fabs(sx - RC(cam.x0 + xw)), fabs(sy - RC(cam.y0 + yw)));
 }
 
-// SPLIT: sample slot k of the pixel's list <- (x, block); the pixel for the
-// statistics pass.
-template <typename R>
-__device__ __forceinline__ void split_write(const SplitArgs& sa, int& k, const R x[3], int blk, int pix) {
-  if (k < sa.cap) {
-    sa.sp[k] = make_float4((float)x[0], (float)x[1], (float)x[2], __int_as_float(blk));
-    if (sa.spix) sa.spix[k] = pix;
-  }
-  ++k;
-}
-
 // One lane's position in the integration of its current pixel.
 //   stage 0: start of a pair (evaluate W and rho at p_in);
 //   stages 1..3: the three new right-hand sides of a Bogacki-Shampine step
@@ -178,13 +194,11 @@ __device__ __forceinline__ void split_write(const SplitArgs& sa, int& k, const R
 // uses that request's camera, sample distance, transfer function slot and
 // image; the block table of the batch's pool carries each block's scalar mode.
 //
-// SPLIT: the lane writes each sample's parameter point (dense output between
-// step ends) to its pixel's sample list instead of evaluating the scalar and
-// compositing; k_shade and rf_composite finish the pixel.  A step then costs
-// only its three right-hand sides.
-template <int P, typename R, bool MIXED, bool STATS, bool BATCH = false, bool SPLIT = false>
+// The split form of stage 3 (sample points first, shading after) is the
+// trace kernel of k_trace.cuh.
+template <int P, typename R, bool MIXED, bool STATS, bool BATCH = false>
 __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R> cam, DevTF tf, IntegrateArgs args,
-                                                       BatchArgs ba, SplitArgs sa,
+                                                       BatchArgs ba,
                                                        const typename Vec4T<R>::type* __restrict__ pair_in,
                                                        const typename Vec4T<R>::type* __restrict__ pair_out,
                                                        const int* __restrict__ pair_block,
@@ -196,7 +210,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   __shared__ float s_r[256];
   __shared__ float4 s_rgba[256];
   __shared__ unsigned char s_seg[kTfTable];
-  if constexpr (!BATCH && !SPLIT) {
+  if constexpr (!BATCH) {
     for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
       s_r[i] = tf.r[i];
       s_rgba[i] = tf.rgba[i];
@@ -220,7 +234,6 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   R hmin = R(1e-7) * ds;
   R hmax = R(args.max_step_samples) * ds;
   int rq = 0;             // BATCH: request of the lane's pixel
-  int kidx = 0, blk = 0;  // SPLIT: next sample slot of the pixel, block of the pair
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_samp = 0, c_fp64 = 0, c_cap = 0;
   float max_dp = 0.f;
 
@@ -257,7 +270,6 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
           } else {
             const int xw = pix % cam.w, yw = pix / cam.w;
             make_ray<R>(cam, cam.x0 + xw, cam.y0 + yw, o, d);
-            if constexpr (SPLIT) kidx = __ldg(sa.off + item);
           }
           acc.C[0] = acc.C[1] = acc.C[2] = acc.a = R(0);
           np = __ldg(pair_count + pix);
@@ -282,7 +294,6 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         L = R(po.x) - R(pi.x);
         if (!(L > R(0))) continue;
         B = V.blocks[__ldg(pair_block + slot)];
-        if constexpr (SPLIT) blk = __ldg(pair_block + slot);
 #pragma unroll
         for (int r = 0; r < 3; ++r) g_in[r] = o[r] + R(pi.x) * d[r];
         p[0] = R(pi.y); p[1] = R(pi.z); p[2] = R(pi.w);
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         const float4 res = make_float4((float)acc.C[0], (float)acc.C[1], (float)acc.C[2], (float)acc.a);
         if constexpr (BATCH)
           ba.req[rq].out[pix - __ldg(ba.pix0 + rq)] = res;
-        else if constexpr (!SPLIT)
+        else
           out[pix] = res;
         pix = -1;
         live = false;
@@ -311,21 +322,18 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
       } else if (stage == 1) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = p[r] + R(0.5) * hh * k1[r];
+        for (int r = 0; r < 3; ++r) x[r] = bs3_q2<R>(p[r], hh, k1[r]);
       } else if (stage == 2) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = p[r] + R(0.75) * hh * k2[r];
+        for (int r = 0; r < 3; ++r) x[r] = bs3_q3<R>(p[r], hh, k2[r]);
       } else if (stage == 3) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) x[r] = pn[r];
       } else {
         // cubic Hermite dense output on the accepted step [s0, s] (length hh)
         const R th = ((j <= nsamp ? R(j) * ds : L) - s0) / hh;
-        const R t2 = th * th, t3 = t2 * th;
-        const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + th;
-        const R h01 = R(3) * t2 - R(2) * t3, h11 = t3 - t2;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = h00 * p0[r] + h10 * hh * k0[r] + h01 * p[r] + h11 * hh * k1[r];
+        for (int r = 0; r < 3; ++r) x[r] = hermite<R>(th, hh, p0[r], k0[r], p[r], k1[r]);
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = x[r] < R(0) ? R(0) : (x[r] > R(1) ? R(1) : x[r]);
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     }
     // ---- the one right-hand side of this iteration (converged across lanes)
     R W[3], rho, phi[3];
-    rhs_eval<P, R, MIXED, !SPLIT>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
+    rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
     if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
@@ -342,23 +350,19 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     if (stage == 0) {
       k1[0] = W[0]; k1[1] = W[1]; k1[2] = W[2];
       rho_prev = rho;
-      if constexpr (SPLIT) {
-        split_write(sa, kidx, x, blk, pix);          // sample s_0 = 0: the entry point
-      } else if (STATS) {
-        ++c_samp;
-      }
+      if (STATS) ++c_samp;
     } else if (stage == 1) {
       k2[0] = W[0]; k2[1] = W[1]; k2[2] = W[2];
     } else if (stage == 2) {
       k3[0] = W[0]; k3[1] = W[1]; k3[2] = W[2];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
-        pn[r] = p[r] + hh * (R(2.0 / 9.0) * k1[r] + R(1.0 / 3.0) * k2[r] + R(4.0 / 9.0) * k3[r]);
+        pn[r] = bs3_pn<R>(p[r], hh, k1[r], k2[r], k3[r]);
     } else if (stage == 3) {
       R err = R(0);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const R e = hh * (R(-5.0 / 72.0) * k1[r] + R(1.0 / 12.0) * k2[r] + R(1.0 / 9.0) * k3[r] - R(1.0 / 8.0) * W[r]);
+        const R e = bs3_err<R>(hh, bs3_e3<R>(k1[r], k2[r], k3[r]), W[r]);
         const R ae = fabs(e);
         err = ae > err ? ae : err;
       }
@@ -383,40 +387,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         fac = fac < R(0.2) ? R(0.2) : (fac > R(5) ? R(5) : fac);
         h = hh * fac;
         if (capped) {
-          if constexpr (SPLIT)
-            for (; j <= nlast; ++j) split_write(sa, kidx, p, blk, pix);   // keep the list complete
           stage = 0;
-          continue;
-        }
-        if constexpr (SPLIT) {
-          // the samples inside (s0, s]: dense output, or the step end itself
-          for (; j <= nlast; ++j) {
-            const R s_t = (j <= nsamp) ? R(j) * ds : L;
-            if (s_t > s) break;
-            R xs[3];
-            if (s_t < s) {
-              const R th = (s_t - s0) / hh;
-              const R t2 = th * th, t3 = t2 * th;
-              const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + th;
-              const R h01 = R(3) * t2 - R(2) * t3, h11 = t3 - t2;
-#pragma unroll
-              for (int r = 0; r < 3; ++r) {
-                const R v = h00 * p0[r] + h10 * hh * k0[r] + h01 * p[r] + h11 * hh * k1[r];
-                xs[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
-              }
-            } else {
-              xs[0] = p[0]; xs[1] = p[1]; xs[2] = p[2];
-            }
-            split_write(sa, kidx, xs, blk, pix);
-          }
-          if (j > nlast) {
-            stage = 0;       // pair done
-            continue;
-          }
-          const R rem = L - s;
-          hh = h < hmax ? h : hmax;
-          hh = hh < rem ? hh : rem;
-          stage = 1;
           continue;
         }
         stage = 4;           // visit the samples inside (s0, s]
@@ -549,8 +520,7 @@ void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, con
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
   BatchArgs none{};
-  SplitArgs nos{};
-  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, nos, pin, pout, pblk, pcnt, active,
+  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, pin, pout, pblk, pcnt, active,
                                                          n_active, queue_head, out, st);
 }
 
@@ -641,7 +611,7 @@ __global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<
   }
   __syncthreads();
   const int nact = *n_active;
-  unsigned long long c_samp = 0;
+  unsigned long long c_samp = 0, c_rho = 0;
   float max_dp = 0.f;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
     const int pix = active[item];
@@ -694,7 +664,10 @@ __global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<
           if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cam, phi, pix % cam.w, pix / cam.w));
         }
         const float s = j <= nsamp ? (float)j * ds : L;
-        if (STATS) ++c_samp;
+        if (STATS) {
+          ++c_samp;
+          ++c_rho;
+        }
         if (j > 0) {
           composite_interval<float>(s_r, s_rgba, s_seg, tf, K, rho_prev, rho, s - s_prev, acc);
           if (acc.a >= early) {
@@ -712,44 +685,15 @@ __global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
       c_samp += __shfl_down_sync(0xffffffffu, c_samp, o2);
+      c_rho += __shfl_down_sync(0xffffffffu, c_rho, o2);
       max_dp = fmaxf(max_dp, __shfl_down_sync(0xffffffffu, max_dp, o2));
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&st->samples, c_samp);
+      atomicAdd(&st->rho_evals, c_rho);
       atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
     }
   }
-}
-
-template <int P, bool MIXED, bool STATS>
-void launch_k5_split(const DevVolume& V, const DevCamera<float>& cam, const IntegrateArgs& a, const SplitArgs& sa,
-                     const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
-                     const int* n_active, int* queue_head, DevStats* st, int num_sms, cudaStream_t s) {
-  static int blocks_per_sm = -1;
-  if (blocks_per_sm < 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k5_integrate<P, float, MIXED, STATS, false, true>,
-                                                  128, 0);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
-  int grid = num_sms * blocks_per_sm;
-  const int max_useful = (a.npix + 127) / 128;
-  if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
-  BatchArgs none{};
-  DevTF tf{};
-  k5_integrate<P, float, MIXED, STATS, false, true><<<grid, 128, 0, s>>>(V, cam, tf, a, none, sa, pin, pout, pblk,
-                                                                         pcnt, active, n_active, queue_head,
-                                                                         nullptr, st);
-}
-
-template <int P>
-void launch_integrate_split_p(const DevVolume& V, const DevCamera<float>& cam, const IntegrateArgs& a,
-                              const SplitArgs& sa, bool mixed, bool stats, const float4* pin, const float4* pout,
-                              const int* pblk, const int* pcnt, const int* active, const int* n_active,
-                              int* queue_head, DevStats* st, int num_sms, cudaStream_t s) {
-#define IVV_K5S(MM, SS)   launch_k5_split<P, MM, SS>(V, cam, a, sa, pin, pout, pblk, pcnt, active, n_active, queue_head, st, num_sms, s)
-  if (mixed) { if (stats) IVV_K5S(true, true); else IVV_K5S(true, false); }
-  else { if (stats) IVV_K5S(false, true); else IVV_K5S(false, false); }
-#undef IVV_K5S
 }
 
 template <int P>

@@ -12,8 +12,7 @@ void launch_kb5(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a,
                 int* queue_head, DevStats* st, int grid, cudaStream_t s) {
   DevCamera<float> cam{};
   DevTF tf{};
-  SplitArgs nos{};
-  k5_integrate<P, float, MIXED, STATS, true><<<grid, 128, 0, s>>>(V, cam, tf, a, ba, nos, pin, pout, pblk, pcnt,
+  k5_integrate<P, float, MIXED, STATS, true><<<grid, 128, 0, s>>>(V, cam, tf, a, ba, pin, pout, pblk, pcnt,
                                                                   active, n_active, queue_head, nullptr, st);
 }
 

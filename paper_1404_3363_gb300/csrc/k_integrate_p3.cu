@@ -1,5 +1,7 @@
-// Degree-3 instantiations of the ray integrator (K5); see k_integrate.cuh.
+// Degree-3 instantiations of the ray integrator (K5, K5t and the shading
+// pass); see k_integrate.cuh and k_trace.cuh.
 #include "k_integrate.cuh"
+#include "k_trace.cuh"
 
 namespace ivv {
 template void launch_integrate_p<3>(const DevVolume&, const DevCamera<float>*, const DevCamera<double>*,

@@ -83,7 +83,7 @@ class Stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in (
         "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
         "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap",
-        "rf_newton_iters", "rf_unconverged", "isect_items", "isect_split")] + \
+        "rf_newton_iters", "rf_unconverged", "isect_items", "isect_split", "rho_evals")] + \
         [("max_delta_p", C.c_double)]
 
     def as_dict(self):
