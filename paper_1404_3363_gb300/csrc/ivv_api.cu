@@ -357,7 +357,12 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
 // Sample-list capacity per pixel of the split integration: the pairs of a
 // ray lie in disjoint blocks inside the control-point box, so their lengths
 // add up to at most its diagonal; each pair adds at most two partial samples.
-constexpr double kSplitMaxBytes = 16.0 * (1ull << 30);
+// Up to kSplitBoundBytes the sample list is sized by this bound (no host
+// round trip); above it the render reads the exact sample total back first
+// (not inside a stream capture), and above kSplitMaxBytes of samples it keeps
+// the fused integrator.
+constexpr double kSplitBoundBytes = 4.0 * (1ull << 30);
+constexpr double kSplitMaxBytes = 64.0 * (1ull << 30);
 size_t split_bound(const ivv_volume* v, const ivv_render_params& p) {
   return (size_t)std::ceil(v->hv.diag / p.ds) + 2 * ivv::kMaxPairs + 2;
 }
@@ -488,58 +493,70 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                              (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
                              (float4*)out, v->d_stats, v->num_sms, s);
-  } else if (split_bytes(v, p, npix) <= kSplitMaxBytes && !ws_is_scratch) {
-    // split integration: sample lists (count, scan), integrator writing the
-    // sample points, scalar at every sample, per-pixel compositing
+  } else {
     st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     const ivv::DevCamera<float> c32 = dev_camera<float>(F);
-    const size_t bound = split_bound(v, p), cap = bound * npix;
-    st = ensure_own(&v->ode_buf, &v->ode_bytes, split_bytes(v, p, npix), s);
-    if (st != IVV_OK) return st;
     const float4* pin = (const float4*)(ws + L.pair_in);
     const float4* pout = (const float4*)(ws + L.pair_out);
     const int* pblk = (const int*)(ws + L.pair_block);
     const int* pcnt = (const int*)(ws + L.pair_count);
     const int* act = (const int*)(ws + L.active);
     int* counters = (int*)(ws + L.counters);
+    // split integration: sample lists (count, scan), trace kernel writing the
+    // sample points, scalar at every sample and per-pixel compositing
+    const bool by_bound = split_bytes(v, p, npix) <= kSplitBoundBytes;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    bool split = !ws_is_scratch && (by_bound || !capturing);
+    size_t cap = 0;
     int* cnt = (int*)(ws + L.frag_count);             // fragment lists are dead after stage 2
     int* off = (int*)(ws + L.frag_meta);
     int* sums = off + npix;
     const float tail_eps = 1e-12f * (float)v->hv.diag;  // as the integrator computes it
-    ivv::SplitArgs sa;
-    sa.off = off;
-    sa.sp = (float4*)v->ode_buf;
-    sa.cap = (int)cap;
-    ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms, s);
-    ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
-    if (V.P == 2) {
-      ivv::launch_integrate_split_p<2>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
-                                       counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
-      ivv::launch_shade_composite_p<2>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act,
-                                       counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out, stats,
-                                       v->d_stats, v->num_sms, s);
-    } else {
-      ivv::launch_integrate_split_p<3>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
-                                       counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
-      ivv::launch_shade_composite_p<3>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act,
-                                       counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out, stats,
-                                       v->d_stats, v->num_sms, s);
+    if (split) {
+      ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms,
+                           s);
+      ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+      if (by_bound) {
+        cap = split_bound(v, p) * npix;
+      } else {
+        int total = 0;
+        IVV_CUDA(cudaMemcpyAsync(&total, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IVV_CUDA(cudaStreamSynchronize(s));
+        cap = (size_t)std::max(total, 1);
+        split = (double)cap * sizeof(float4) <= kSplitMaxBytes;
+      }
     }
-  } else {
-    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
-    if (st != IVV_OK) return st;
-    ivv::DevCamera<float> c32 = dev_camera<float>(F);
-    if (V.P == 2)
-      ivv::launch_integrate_p<2>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
-                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
-                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
-    else
-      ivv::launch_integrate_p<3>(V, &c32, nullptr, tf, a, mixed, stats, ws + L.pair_in, ws + L.pair_out,
-                                 (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
-                                 (const int*)(ws + L.active), (const int*)(ws + L.counters),
-                                 (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
+    if (split) {
+      st = ensure_own(&v->ode_buf, &v->ode_bytes, cap * sizeof(float4), s);
+      if (st != IVV_OK) return st;
+      ivv::SplitArgs sa;
+      sa.off = off;
+      sa.sp = (float4*)v->ode_buf;
+      sa.cap = (int)cap;
+      if (V.P == 2) {
+        ivv::launch_integrate_split_p<2>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                         counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
+        ivv::launch_shade_composite_p<2>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt,
+                                         act, counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out,
+                                         stats, v->d_stats, v->num_sms, s);
+      } else {
+        ivv::launch_integrate_split_p<3>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                         counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
+        ivv::launch_shade_composite_p<3>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt,
+                                         act, counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out,
+                                         stats, v->d_stats, v->num_sms, s);
+      }
+    } else {
+      ivv::DevCamera<float> cf = c32;
+      if (V.P == 2)
+        ivv::launch_integrate_p<2>(V, &cf, nullptr, tf, a, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                   counters + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
+      else
+        ivv::launch_integrate_p<3>(V, &cf, nullptr, tf, a, mixed, stats, pin, pout, pblk, pcnt, act, counters,
+                                   counters + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
+    }
   }
   if (p.flags & IVV_FLAG_TIMING) {
     IVV_CUDA(cudaEventRecord(v->ev[4], s));
