@@ -48,18 +48,47 @@ WORKLOADS = {
                          "{256,512,768,1024}^2, seeded cameras and TFs, FP32, one CUDA graph"),
 }
 
-# Algorithmic FP32 flops per unit (cubic elements):
-# integrator (K5)
-F_RHS = 1283      # one W(p): 576-FMA sum-factorised phi+J, Bernstein basis, V, 3x3 adjugate solve
-F_STEP = 70       # stage combinations, clamps and error norm of one BS3(2) step attempt
-F_SAMPLE = 150    # K=4 supersampled TF lookups + Alg. 1 updates + Eq. 23 per sample
-# scalar at a sample evaluated on its own (shading pass of the split integration)
-F_RHO_J = 1220    # det J or Eq. 23: 564-FMA sum-factorised J, Bernstein basis, det, Frobenius norm
-F_RHO_CP = 200    # scalar control points: 84-FMA contraction and the value basis
-# ray/patch intersection (K2)
-F_HULL = 260      # per (pixel, patch) item: control points into the ray frame (16 x 6 FMA), hull, Jacobian sign
-F_NEWTON = 230    # one 2-D Newton iteration on a bicubic patch (value, 2 partials, 2x2 solve)
-F_FRAG = 220      # 3-D point, partials and facing of a root
+# Algorithmic FP32 flops per unit for Bezier degree P (N = P + 1 control
+# points per direction; the cubic figures in brackets).
+# integrator (K5 / K5t)
+def flop_model(P):
+    N = P + 1
+    return {
+        # one W(p): sum-factorised phi + J (6N^3 + 9N^2 + 12N FMA [576]), Bernstein
+        # basis, V and the 3x3 adjugate solve (131) [1283]
+        "rhs": 2 * (6 * N ** 3 + 9 * N ** 2 + 12 * N) + 131,
+        # stage combinations, clamps and error norm of one BS3(2) step attempt [70]
+        "step": 70,
+        # K=4 supersampled TF lookups + Alg. 1 updates per sample [150]
+        "sample": 150,
+        # scalar at a sample evaluated on its own (shading pass of the split
+        # integration): det J or Eq. 23 from J alone (6N^3 + 9N^2 + 9N FMA [564]),
+        # basis, det and Frobenius norm [1220]; or the scalar control points
+        # (N^3 + N^2 + N FMA [84]) and the value basis [200]
+        "rho_j": 2 * (6 * N ** 3 + 9 * N ** 2 + 9 * N) + 92,
+        "rho_cp": 2 * (N ** 3 + N ** 2 + N) + 32,
+        # ray/patch intersection (K2): per (pixel, patch) item the N^2 control
+        # points into the ray frame (6 FMA each), hull and Jacobian-sign test [260];
+        # one 2-D Newton iteration (value, 2 partials: 4N^2 + 6N FMA, 2x2 solve) [230];
+        # per fragment the 3-D point, partials and facing [220]
+        "hull": 12 * N * N + 68,
+        "newton": 2 * (4 * N * N + 6 * N) + 54,
+        "frag": round(220 * (6 * N * N + 9 * N) / 132),
+    }
+
+
+def scene_degree(blocks):
+    """The common Bezier degree the library raises a volume's blocks to."""
+    return max(max(b.degree) for b in blocks)
+
+
+def k5_flops(st, F, scalar_cp):
+    return (st["rhs_evals"] * F["rhs"] + (st["rk_steps"] + st["rk_rejects"]) * F["step"]
+            + st["samples"] * F["sample"] + st["rho_evals"] * (F["rho_cp"] if scalar_cp else F["rho_j"]))
+
+
+def k2_flops(st, F):
+    return st["isect_items"] * F["hull"] + st["isect_newton"] * F["newton"] + st["fragments"] * F["frag"]
 
 
 def _env_int(name, default):
@@ -272,10 +301,9 @@ def run_ours(args):
     vol.reset_stats()
     vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS)
     st = vol.stats()
-    flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
-                + st["samples"] * F_SAMPLE
-                + st["rho_evals"] * (F_RHO_CP if sc.scalar_mode == scenes.SCALAR_CP else F_RHO_J))
-    flops_k2 = st["isect_items"] * F_HULL + st["isect_newton"] * F_NEWTON + st["fragments"] * F_FRAG
+    F = flop_model(scene_degree(sc.blocks))
+    flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP)
+    flops_k2 = k2_flops(st, F)
 
     # parity spot check of this frame against the oracle (untimed)
     max_err = None
@@ -424,8 +452,10 @@ def run_batch(args):
     b.reset_stats()
     b.render(flags=ivv.FLAG_STATS)
     st = b.stats()
-    flops_k5 = (st["rhs_evals"] * F_RHS + (st["rk_steps"] + st["rk_rejects"]) * F_STEP
-                + st["samples"] * F_SAMPLE)
+    # the batch pool's volumes share one degree; the batch integrator composites
+    # inside K5, so rho_evals is 0 there
+    F = flop_model(scene_degree(vols[0].blocks))
+    flops_k5 = k5_flops(st, F, False)
     b.render(flags=ivv.FLAG_TIMING)
     stages = b.stage_times()
 

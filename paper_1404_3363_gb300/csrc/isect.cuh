@@ -205,11 +205,13 @@ template <> struct RootEps<double> {
 };
 
 // Damped Newton on the planar map of patch q (local parameters) from (a,b).
+// lo / hi: the iterate is abandoned once it leaves [lo, hi]^2; max_it: the
+// iteration budget.
 template <int P, typename R>
-IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
+IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters, R lo = R(-0.5), R hi = R(1.5), int max_it = 16) {
   constexpr int N = P + 1;
 #pragma unroll 1
-  for (int it = 0; it < 16; ++it) {
+  for (int it = 0; it < max_it; ++it) {
     R ba[N], dba[N], bb[N], dbb[N];
     bern_hd<P, R>(a, ba, dba);
     bern_hd<P, R>(b, bb, dbb);
@@ -236,7 +238,7 @@ IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
     if (mx > R(0.5)) { da *= R(0.5) / mx; db *= R(0.5) / mx; }
     a += da;
     b += db;
-    if (a < R(-0.5) || a > R(1.5) || b < R(-0.5) || b > R(1.5)) return false;
+    if (a < lo || a > hi || b < lo || b > hi) return false;
     if (fabs(da) + fabs(db) < RootEps<R>::step) return true;
   }
   return false;
@@ -244,6 +246,13 @@ IVV_HD bool newton2(const Patch2<P, R>& q, R& a, R& b, int& iters) {
 
 constexpr int kMaxPatchRoots = 4;
 constexpr int kSplitDepth = 8;
+// Newton inside a certified box of the subdivision search: a root of the box
+// lies within it, so an iterate that leaves the box by a quarter of its size,
+// or a budget of 10 iterations without convergence, only means the box is
+// split again (its halves are nearly bilinear).
+template <typename R> IVV_HD constexpr R kBoxNewtonLo() { return R(-0.25); }
+template <typename R> IVV_HD constexpr R kBoxNewtonHi() { return R(1.25); }
+constexpr int kBoxNewtonIters = 10;
 
 // Starting point for Newton on patch q: the zero of the bilinear map through
 // its four corners (which lie on the patch), c00 + a e + b f + a b g = 0 with
@@ -382,7 +391,8 @@ __host__ __device__ __noinline__ int patch_roots_split(const Patch2<P, R>* q0p, 
       // Newton from the centre; if it fails or converges to a root outside
       // this piece, look for the piece's root in smaller pieces
       R a = R(0.5), b = R(0.5);
-      split = !(newton2<P, R>(q, a, b, iters) && accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
+      split = !(newton2<P, R>(q, a, b, iters, kBoxNewtonLo<R>(), kBoxNewtonHi<R>(), kBoxNewtonIters) &&
+                accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
     } else if (nd.depth >= kSplitDepth) {
       // smallest piece, not certified: Newton from the centre and the four
       // quarter points, keeping every distinct root inside the piece

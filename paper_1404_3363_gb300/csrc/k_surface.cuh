@@ -285,7 +285,8 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
       bool split = true;
       if (fixed_jacobian_sign<P, R>(q)) {
         R a = R(0.5), b = R(0.5);
-        split = !(newton2<P, R>(q, a, b, iters) && gather_root<R>(nd, a, b, sm));
+        split = !(newton2<P, R>(q, a, b, iters, kBoxNewtonLo<R>(), kBoxNewtonHi<R>(), kBoxNewtonIters) &&
+                  gather_root<R>(nd, a, b, sm));
       } else if (nd.depth >= kSplitDepth) {
 #pragma unroll 1
         for (int s0 = 0; s0 < 5; ++s0) {
