@@ -591,11 +591,15 @@ IVV_HD void refine_hit_fp64(const V4* cp, const double org[3], const double o[3]
     const double c20 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
     const double c21 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
     const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    const double x0 = (c00 * F[0] + c10 * F[1] + c20 * F[2]) / det;
-    const double x1 = (c01 * F[0] + c11 * F[1] + c21 * F[2]) / det;
-    const double x2 = (c02 * F[0] + c12 * F[1] + c22 * F[2]) / det;
+    const double inv = 1.0 / det;
+    const double x0 = (c00 * F[0] + c10 * F[1] + c20 * F[2]) * inv;
+    const double x1 = (c01 * F[0] + c11 * F[1] + c21 * F[2]) * inv;
+    const double x2 = (c02 * F[0] + c12 * F[1] + c22 * F[2]) * inv;
     if (!(fabs(x0) < 0.5 && fabs(x1) < 0.5)) break;
     a += x0; b += x1; t += x2;
+    // Newton converges quadratically from the FP32 root: after an update
+    // below 1e-12 the next one is below FP64 resolution
+    if (fabs(x0) + fabs(x1) < 1e-12) break;
   }
 }
 
