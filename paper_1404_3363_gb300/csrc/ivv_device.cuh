@@ -156,6 +156,17 @@ __device__ __forceinline__ void ldg_row(const float4* __restrict__ p, float4 c[N
   }
 }
 
+// a[i] for an index the compiler keeps at run time (the outer loop of the
+// contractions is not unrolled): a select chain on registers, so the basis
+// arrays stay in registers instead of a local-memory stack copy.
+template <int N>
+__device__ __forceinline__ float pick(const float a[N], int i) {
+  float v = a[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k) v = (i == k) ? a[k] : v;
+  return v;
+}
+
 // The paired contractions of eval_block (defined below).
 template <int P, bool WANT_RHO>
 __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
@@ -299,7 +310,8 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
       s10xy = __ffma2_rn(b, t1xy, s10xy);
       s10zr = __ffma2_rn(b, t1zr, s10zr);
     }
-    const float2 b = make_float2(bu[i], bu[i]), db = make_float2(dbu[i], dbu[i]);
+    const float bui = pick<N>(bu, i), dbui = pick<N>(dbu, i);
+    const float2 b = make_float2(bui, bui), db = make_float2(dbui, dbui);
     fxy = __ffma2_rn(b, s00xy, fxy);
     fzr = __ffma2_rn(b, s00zr, fzr);
     fuxy = __ffma2_rn(db, s00xy, fuxy);
@@ -356,12 +368,13 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
       s00_s01_z = __ffma2_rn(make_float2(bv[j], dbv[j]), make_float2(t01z.x, t01z.x), s00_s01_z);
       s10z = __fmaf_rn(bv[j], t01z.y, s10z);
     }
-    const float2 b = make_float2(bu[i], bu[i]), db = make_float2(dbu[i], dbu[i]);
+    const float bui = pick<N>(bu, i), dbui = pick<N>(dbu, i);
+    const float2 b = make_float2(bui, bui), db = make_float2(dbui, dbui);
     fxy = __ffma2_rn(b, s00xy, fxy);
     fuxy = __ffma2_rn(db, s00xy, fuxy);
     fvxy = __ffma2_rn(b, s01xy, fvxy);
     fwxy = __ffma2_rn(b, s10xy, fwxy);
-    f_fu_z = __ffma2_rn(make_float2(bu[i], dbu[i]), make_float2(s00_s01_z.x, s00_s01_z.x), f_fu_z);
+    f_fu_z = __ffma2_rn(make_float2(bui, dbui), make_float2(s00_s01_z.x, s00_s01_z.x), f_fu_z);
     fv_fw_z = __ffma2_rn(b, make_float2(s00_s01_z.y, s10z), fv_fw_z);
   }
   f[0] = fxy.x; f[1] = fxy.y; f[2] = f_fu_z.x;
