@@ -175,13 +175,16 @@ def _peaks():
         return {}
 
 
-def _ncu_traffic(kernel):
+def _ncu_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu counters, or
-    None if its sources changed since the capture."""
+    None if they were taken on another workload or its sources changed since
+    the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_counters.json")) as f:
             rec = json.load(f)[kernel]
+        if rec.get("workload") != workload:
+            return None
         m = hashlib.sha256()
         for name in rec["src_files"]:
             with open(os.path.join(ROOT, "paper_1404_3363_gb300", "csrc", name), "rb") as f:
@@ -373,10 +376,11 @@ def run_ours(args):
     def roof(kernel, flops, ms):
         achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
         return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32 if peak_fp32 else None, "traffic": _ncu_traffic(kernel),
+                "frac": achieved / peak_fp32 if peak_fp32 else None,
+                "traffic": _ncu_traffic(kernel, args.workload),
                 "peak_note": peak_note, "flops_per_launch": flops, "ms_per_launch": ms}
 
-    roofs = sorted([roof("k2_intersect", flops_k2, k2_ms), roof("k5_integrate", flops_k5, k5_ms)],
+    roofs = sorted([roof("k2_intersect", flops_k2, k2_ms), roof("stage3_integrate", flops_k5, k5_ms)],
                    key=lambda r: -r["ms_per_launch"])
 
     cpu_base = None
