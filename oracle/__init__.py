@@ -13,8 +13,10 @@ Functions follow the paper (Fuchs & Hjelmervik, TVCG 2015):
   render         the whole per-pixel path, per-sample RF (method 0),
                  RKF45 on the pulled-back ODE of §5.2 (method 1) or one step
                  per sample interval of the fixed-step RK family of §5.3
-                 (FIXED_* methods)
-  table1         §5.3 Table 1 harness (fixed-step RK family / RF)
+                 (FIXED_* methods) or of implicit Euler (IMPLICIT_EULER)
+  table1         §5.3 Table 1 harness (fixed-step RK family / RF / implicit
+                 Euler)
+  eval2          second partials (the Hessian used by implicit Euler)
 Cutting and near-clip planes (§5.5) act on the depth-sorted intersections
 before compositing (render with params.near_clip / params.cut_planes).
 """
@@ -36,6 +38,9 @@ METHOD_RF = 0
 METHOD_RKF45 = 1
 FIXED_EULER, FIXED_MIDPOINT, FIXED_KUTTA3, FIXED_RK4, FIXED_RK4_38, FIXED_FEHLBERG5 = 11, 12, 13, 14, 15, 16
 FIXED_ORDER = {11: 1, 12: 2, 13: 3, 14: 4, 15: 4, 16: 5}
+# implicit Euler of §5.3 (one step per sample interval, Newton with the exact
+# Jacobian of G)
+IMPLICIT_EULER = 17
 
 c_double_p = C.POINTER(C.c_double)
 
@@ -105,6 +110,8 @@ def lib():
                                  C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  c_double_p, C.POINTER(PixelStats)]
         L.orc_table1.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, c_double_p]
+        L.orc_table1_ex.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, c_double_p, C.POINTER(C.c_long)]
+        L.orc_eval2.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, c_double_p, c_double_p, c_double_p]
         _LIB = L
     return _LIB
 
@@ -175,6 +182,16 @@ class OracleVolume:
         rho = np.zeros(n)
         lib().orc_eval(self.h, block, n, _dp(p), _dp(phi), _dp(J), _dp(rho))
         return phi, J, rho
+
+    def eval2(self, block, p):
+        """phi, J and the Hessian H[n][r][a][b] = d^2 phi_r / dp_a dp_b."""
+        p = _f64(np.atleast_2d(p))
+        n = p.shape[0]
+        phi = np.zeros((n, 3))
+        J = np.zeros((n, 3, 3))
+        H = np.zeros((n, 3, 3, 3))
+        lib().orc_eval2(self.h, block, n, _dp(p), _dp(phi), _dp(J), _dp(H))
+        return phi, J, H
 
     def basis(self, block, direction, x, n_cp):
         x = _f64(np.atleast_1d(x))
@@ -316,3 +333,10 @@ def table1(method, ds, c=1.0, rf_tol=1e-14):
     e = C.c_double()
     lib().orc_table1(int(method), float(ds), float(c), float(rf_tol), C.byref(e))
     return e.value
+
+
+def table1_irk1(ds, c=100.0):
+    """Table 1's implicit Euler row: (error, steps, Newton iterations)."""
+    e, it = C.c_double(), C.c_long()
+    steps = lib().orc_table1_ex(8, float(ds), float(c), 1e-14, C.byref(e), C.byref(it))
+    return e.value, steps, it.value

@@ -149,6 +149,55 @@ struct Basis1D {
   }
 };
 
+// N, N' and N'' of one knot vector at x: the derivative formula of Eq. 1's
+// B-splines applied twice,
+//   N'_{i,q} = q/(t_{i+q}-t_i) N_{i,q-1} - q/(t_{i+q+1}-t_{i+1}) N_{i+1,q-1},
+// once to the degree p-1 functions (giving N'_{.,p}) and once to the
+// derivatives of the degree p-1 functions (giving N''_{.,p}).
+void basis_eval2(const Basis1D& B, double x, std::vector<double>& N, std::vector<double>& dN,
+                 std::vector<double>& ddN) {
+  const std::vector<double>& t = B.t;
+  const int p = B.p, n = B.n, m = (int)t.size() - 1;
+  if (x < t[0]) x = t[0];
+  if (x > t[m]) x = t[m];
+  std::vector<std::vector<double>> Nq(p + 1);      // Nq[q][i] = N_{i,q}(x)
+  Nq[0].assign(m, 0.0);
+  int last_span = -1;
+  for (int i = 0; i < m; ++i) if (t[i] < t[i + 1]) last_span = i;
+  for (int i = 0; i < m; ++i) if (t[i] <= x && x < t[i + 1]) Nq[0][i] = 1.0;
+  if (x == t[m]) Nq[0][last_span] = 1.0;
+  for (int q = 1; q <= p; ++q) {
+    Nq[q].assign(m - q, 0.0);
+    for (int i = 0; i < m - q; ++i) {
+      double a = 0, b = 0;
+      const double d1 = t[i + q] - t[i], d2 = t[i + q + 1] - t[i + 1];
+      if (d1 > 0) a = (x - t[i]) / d1 * Nq[q - 1][i];
+      if (d2 > 0) b = (t[i + q + 1] - x) / d2 * Nq[q - 1][i + 1];
+      Nq[q][i] = a + b;
+    }
+  }
+  // derivative of the degree-q functions from the degree-(q-1) values v
+  auto deriv = [&](int q, const std::vector<double>& v, int count) {
+    std::vector<double> out(count, 0.0);
+    for (int i = 0; i < count; ++i) {
+      const double d1 = t[i + q] - t[i], d2 = t[i + q + 1] - t[i + 1];
+      double w = 0;
+      if (d1 > 0) w += q / d1 * v[i];
+      if (d2 > 0 && i + 1 < (int)v.size()) w -= q / d2 * v[i + 1];
+      out[i] = w;
+    }
+    return out;
+  };
+  N.assign(Nq[p].begin(), Nq[p].begin() + n);
+  dN.assign(n, 0.0);
+  ddN.assign(n, 0.0);
+  if (p >= 1) dN = deriv(p, Nq[p - 1], n);
+  if (p >= 2) {
+    const std::vector<double> dprev = deriv(p - 1, Nq[p - 2], m - p + 1);   // N'_{i,p-1}
+    ddN = deriv(p, dprev, n);
+  }
+}
+
 struct Block {
   Basis1D B[3];
   std::vector<double> geom;    // [nw][nv][nu][3]
@@ -186,6 +235,46 @@ void block_eval(const Block& b, const double p[3], double phi[3], double J[3][3]
     }
   }
   if (rho) *rho = s;
+}
+
+// phi, J and the Hessian H[r][a][b] = d^2 phi_r / dp_a dp_b at p.
+void block_eval2(const Block& b, const double p[3], double phi[3], double J[3][3], double H[3][3][3]) {
+  std::vector<double> N[3], dN[3], ddN[3];
+  for (int d = 0; d < 3; ++d) basis_eval2(b.B[d], p[d], N[d], dN[d], ddN[d]);
+  const int nu = b.B[0].n, nv = b.B[1].n, nw = b.B[2].n;
+  for (int r = 0; r < 3; ++r) {
+    phi[r] = 0;
+    for (int a = 0; a < 3; ++a) {
+      J[r][a] = 0;
+      for (int c = 0; c < 3; ++c) H[r][a][c] = 0;
+    }
+  }
+  for (int k = 0; k < nw; ++k)
+    for (int j = 0; j < nv; ++j)
+      for (int i = 0; i < nu; ++i) {
+        // value, first and second derivative of each factor
+        const double u[3] = {N[0][i], dN[0][i], ddN[0][i]};
+        const double v[3] = {N[1][j], dN[1][j], ddN[1][j]};
+        const double w[3] = {N[2][k], dN[2][k], ddN[2][k]};
+        if (u[0] == 0 && u[1] == 0 && u[2] == 0) continue;
+        if (v[0] == 0 && v[1] == 0 && v[2] == 0) continue;
+        if (w[0] == 0 && w[1] == 0 && w[2] == 0) continue;
+        const double* cp = &b.geom[3 * (((size_t)k * nv + j) * nu + i)];
+        // derivative orders (ou, ov, ow) of d^2/dp_a dp_b: a, b in {0,1,2}
+        for (int r = 0; r < 3; ++r) {
+          phi[r] += u[0] * v[0] * w[0] * cp[r];
+          J[r][0] += u[1] * v[0] * w[0] * cp[r];
+          J[r][1] += u[0] * v[1] * w[0] * cp[r];
+          J[r][2] += u[0] * v[0] * w[1] * cp[r];
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+              int o[3] = {0, 0, 0};
+              ++o[a];
+              ++o[c];
+              H[r][a][c] += u[o[0]] * v[o[1]] * w[o[2]] * cp[r];
+            }
+        }
+      }
 }
 
 enum { MODE_CP = 0, MODE_DETJ = 1, MODE_QUALITY = 2 };
@@ -626,6 +715,64 @@ bool ode_rhs(const Block& b, const double p[3], const double g_in[3], const doub
   return qr_solve3(J, Vv, W);
 }
 
+// One implicit Euler step of §5.3: p_next = p + h W(p_next), solved for the
+// increment z = p_next - p by Newton on G(z) = z - h W(p + z) with the exact
+// Jacobian of G from differentiating J_phi G = J_phi z - h V(phi):
+//   J_phi(x) J_G(z) = H_phi(x)[z - G(z)] + (I - h J_V) J_phi(x),  x = p + z,
+// J_V = c (d d^T - I) (V(g) = d + c [(g_in - g) - <g_in - g, d> d]), and
+// H_phi(x)[v]_{ij} = sum_k d^2 phi_i / dx_j dx_k v_k.  A Newton step then
+// solves (J_phi J_G) dz = -J_phi G.  z starts at 0, so the first iteration
+// evaluates the map at p itself; the evaluation point is clamped to [0,1]^3
+// (§5.4) and the iteration stops once |dz|_inf <= tol (or after max_it).
+// ev(x, phi, J, H) evaluates the map.  Returns the iterations, -1 if a
+// linear system is singular.
+template <class Eval>
+int irk1_step(Eval ev, const double p[3], double h, const double g_in[3], const double d[3], double c,
+              double tol, int max_it, double pn[3]) {
+  double z[3] = {0, 0, 0};
+  int it = 0;
+  for (; it < max_it; ++it) {
+    double x[3];
+    for (int r = 0; r < 3; ++r) x[r] = std::min(std::max(p[r] + z[r], 0.0), 1.0);
+    double phi[3], J[3][3], H[3][3][3];
+    ev(x, phi, J, H);
+    double e[3] = {g_in[0] - phi[0], g_in[1] - phi[1], g_in[2] - phi[2]};
+    const double ed = dot3(e, d);
+    double Vv[3], W[3];
+    for (int r = 0; r < 3; ++r) Vv[r] = d[r] + c * (e[r] - ed * d[r]);
+    if (!qr_solve3(J, Vv, W)) return -1;
+    double G[3], v[3];
+    for (int r = 0; r < 3; ++r) {
+      v[r] = h * W[r];                  // z - G(z)
+      G[r] = z[r] - v[r];
+    }
+    // M = H[v] + (I - h J_V) J,  (I - h J_V) = (1 + h c) I - h c d d^T
+    double M[3][3], JG[3];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) {
+        double hv = 0;
+        for (int k = 0; k < 3; ++k) hv += H[i][j][k] * v[k];
+        double aj = 0;
+        for (int k = 0; k < 3; ++k) {
+          const double A = (i == k ? 1.0 + h * c : 0.0) - h * c * d[i] * d[k];
+          aj += A * J[k][j];
+        }
+        M[i][j] = hv + aj;
+      }
+      JG[i] = -(J[i][0] * G[0] + J[i][1] * G[1] + J[i][2] * G[2]);
+    }
+    double dz[3];
+    if (!qr_solve3(M, JG, dz)) return -1;
+    for (int r = 0; r < 3; ++r) z[r] += dz[r];
+    if (std::max(std::fabs(dz[0]), std::max(std::fabs(dz[1]), std::fabs(dz[2]))) <= tol) {
+      ++it;
+      break;
+    }
+  }
+  for (int r = 0; r < 3; ++r) pn[r] = std::min(std::max(p[r] + z[r], 0.0), 1.0);
+  return it;
+}
+
 // Runge-Kutta-Fehlberg 4(5) coefficients (Fehlberg 1969), 5th-order solution
 // propagated, as the paper's "RKF".
 const double F45_c[6] = {0, 1.0/4, 3.0/8, 12.0/13, 1.0, 1.0/2};
@@ -706,7 +853,8 @@ void composite_interval(const TF& tf, int K, double early, double rho0, double r
 
 struct Params {
   double ds; int K; double c; double early;
-  int method;          // 0 = RF per sample, 1 = RKF45 ODE, 10 + k = fixed-step tableau k (one step per interval)
+  int method;          // 0 = RF per sample, 1 = RKF45 ODE, 10 + k = fixed-step tableau k (one step per interval),
+                       // 17 = implicit Euler (one step per interval)
   double newton_tol;   // relative to diag
   double rk_tol;
   double near_clip;    // > 0: near plane at this distance along the view direction
@@ -774,6 +922,19 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
           for (int st2 = 0; st2 < T.s; ++st2) acc2 += hh * T.b[st2] * k[st2][r];
           p[r] = std::min(std::max(acc2, 0.0), 1.0);
         }
+        ++st.rk_steps;
+      }
+    } else if (P.method == 17) {
+      // one implicit Euler step (§5.3) from s_{j-1} to s_j
+      const double hh = s[j] - s[j - 1];
+      double pn[3];
+      auto ev = [&](const double x[3], double phi[3], double J[3][3], double H[3][3][3]) {
+        block_eval2(b, x, phi, J, H);
+      };
+      if (irk1_step(ev, p, hh, g_in, d, P.c, 1e-13, 50, pn) < 0) {
+        ++st.newton_fail;
+      } else {
+        for (int r = 0; r < 3; ++r) p[r] = pn[r];
         ++st.rk_steps;
       }
     } else {
@@ -932,6 +1093,16 @@ void t1_map(const double p[3], double phi[3], double J[3][3]) {
   J[2][0] = 0; J[2][1] = 0; J[2][2] = 1;
 }
 
+// Second derivatives of the analytic map: only d^2 phi_1 / dx^2 is non-zero.
+void t1_map2(const double p[3], double phi[3], double J[3][3], double H[3][3][3]) {
+  t1_map(p, phi, J);
+  for (int r = 0; r < 3; ++r)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) H[r][a][b] = 0;
+  const double x = p[0], w = 10 * M_PI;
+  H[1][0][0] = -0.6 * w * std::cos(w * x) - 0.3 * (1 - x) * w * w * std::sin(w * x);
+}
+
 void t1_rhs(const double p[3], const double g_in[3], const double d[3], double c, double W[3]) {
   double phi[3], J[3][3];
   t1_map(p, phi, J);
@@ -1085,6 +1256,25 @@ int orc_eval(void* v, int block, int n, const double* p, double* phi, double* J,
 }
 
 // 1-D basis values/derivatives of one direction of one block (for pins).
+// phi [n][3], J [n][3][3] and the Hessian H [n][3][3][3] (H[r][a][b] =
+// d^2 phi_r / dp_a dp_b) at n points of a block.
+int orc_eval2(void* v, int block, int n, const double* p, double* phi, double* J, double* H) {
+  Volume* V = (Volume*)v;
+  if (block < 0 || block >= (int)V->blocks.size()) return -1;
+  for (int i = 0; i < n; ++i) {
+    double f[3], Jm[3][3], Hm[3][3][3];
+    block_eval2(V->blocks[block], p + 3 * i, f, Jm, Hm);
+    for (int r = 0; r < 3; ++r) {
+      phi[3 * i + r] = f[r];
+      for (int a = 0; a < 3; ++a) {
+        J[9 * i + 3 * r + a] = Jm[r][a];
+        for (int b = 0; b < 3; ++b) H[27 * i + 9 * r + 3 * a + b] = Hm[r][a][b];
+      }
+    }
+  }
+  return 0;
+}
+
 int orc_basis(void* v, int block, int dir, int n, const double* x, double* N, double* dN) {
   Volume* V = (Volume*)v;
   const Basis1D& B = V->blocks[block].B[dir];
@@ -1247,10 +1437,17 @@ int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* 
 
 // Table 1 of §5.3: error of a fixed-step method on the analytic map.
 // method: 1 Euler, 2 midpoint, 3 Kutta-3, 4 RK4, 5 RK4 3/8, 6 RKF (5th order
-// weights), 7 RF with stopping tolerance rf_tol on ||F||.
+// weights), 7 RF with stopping tolerance rf_tol on ||F||, 8 implicit Euler.
 // The ray is sampled every ds in G arc length from g_in to g_out (last step
 // partial).  err = max_i distance of phi(p_i) to the ray.
+int orc_table1_ex(int method, double ds, double c, double rf_tol, double* err, long* newton_iters);
 int orc_table1(int method, double ds, double c, double rf_tol, double* err) {
+  return orc_table1_ex(method, ds, c, rf_tol, err, nullptr);
+}
+
+// As orc_table1; newton_iters (if not NULL) receives the Newton iterations
+// of the implicit Euler steps (method 8).
+int orc_table1_ex(int method, double ds, double c, double rf_tol, double* err, long* newton_iters) {
   const double p_in[3] = {0.0, 0.3, 0.5}, p_out[3] = {1.0, 0.7, 0.5};
   double g_in[3], g_out[3], J[3][3];
   t1_map(p_in, g_in, J);
@@ -1270,6 +1467,7 @@ int orc_table1(int method, double ds, double c, double rf_tol, double* err) {
   double e = dist(p);
   double s = 0;
   int steps = 0;
+  if (newton_iters) *newton_iters = 0;
   if (method >= 1 && method <= 6) {
     Tableau T = tableau(method);
     while (s < L - 1e-14 && steps < 10000000) {
@@ -1289,6 +1487,18 @@ int orc_table1(int method, double ds, double c, double rf_tol, double* err) {
         for (int st = 0; st < T.s; ++st) acc += h * T.b[st] * k[st][r];
         p[r] = acc;
       }
+      s += h;
+      ++steps;
+      e = std::max(e, dist(p));
+    }
+  } else if (method == 8) {
+    while (s < L - 1e-14 && steps < 10000000) {
+      const double h = std::min(ds, L - s);
+      double pn[3];
+      const int it = irk1_step(t1_map2, p, h, g_in, d, c, 1e-13, 50, pn);
+      if (it < 0) return -1;
+      if (newton_iters) *newton_iters += it;
+      for (int r = 0; r < 3; ++r) p[r] = pn[r];
       s += h;
       ++steps;
       e = std::max(e, dist(p));
