@@ -29,7 +29,8 @@ METRIC = "Mpixels/s & ms/frame at 1920x1080 vs plain FP32, at <=1e-3 max RGBA er
 UNIT = "Mpixels/s"
 WORKLOAD = "twisted bar, 1 cubic block 8x8x32 cp, quality scalar (Eq. 23), 1920x1080 perspective, FP32"
 
-RK_NAMES = {1: "Euler (RK1)", 2: "midpoint (RK2)", 3: "Kutta-3 (RK3)", 4: "RK4", 5: "RK4 3/8", 6: "Fehlberg-5 (RKF)"}
+RK_NAMES = {1: "Euler (RK1)", 2: "midpoint (RK2)", 3: "Kutta-3 (RK3)", 4: "RK4", 5: "RK4 3/8", 6: "Fehlberg-5 (RKF)",
+            7: "implicit Euler (IRK1)"}
 
 # --workload: the default is the headline frame above; the others are the
 # remaining workloads of the method, each printed as its own line.
@@ -67,6 +68,10 @@ def flop_model(P):
         # (N^3 + N^2 + N FMA [84]) and the value basis [200]
         "rho_j": 2 * (6 * N ** 3 + 9 * N ** 2 + 9 * N) + 92,
         "rho_cp": 2 * (N ** 3 + N ** 2 + N) + 32,
+        # one implicit Euler Newton iteration: phi, J and the Hessian
+        # (9N^3 + 18N^2 + 30N FMA [984]), second-derivative basis, V and the
+        # solve for W, the Jacobian of G and its solve [2218]
+        "irk": 2 * (9 * N ** 3 + 18 * N ** 2 + 30 * N) + 250,
         # ray/patch intersection (K2): per (pixel, patch) item the N^2 control
         # points into the ray frame (6 FMA each), hull and Jacobian-sign test [260];
         # one 2-D Newton iteration (value, 2 partials: 4N^2 + 6N FMA, 2x2 solve) [230];
@@ -82,8 +87,10 @@ def scene_degree(blocks):
     return max(max(b.degree) for b in blocks)
 
 
-def k5_flops(st, F, scalar_cp):
-    return (st["rhs_evals"] * F["rhs"] + (st["rk_steps"] + st["rk_rejects"]) * F["step"]
+def k5_flops(st, F, scalar_cp, implicit=False):
+    # implicit Euler counts one map evaluation per Newton iteration in rhs_evals
+    return (st["rhs_evals"] * (F["irk"] if implicit else F["rhs"])
+            + (st["rk_steps"] + st["rk_rejects"]) * F["step"]
             + st["samples"] * F["sample"] + st["rho_evals"] * (F["rho_cp"] if scalar_cp else F["rho_j"]))
 
 
@@ -294,6 +301,9 @@ def run_ours(args):
     if args.rk_method:
         sc.params.rk_method = args.rk_method
         workload += ", fixed-step %s (one step per sample interval)" % RK_NAMES[args.rk_method]
+    if args.c is not None:
+        sc.params.c = args.c
+        workload += ", c = %g" % args.c
     W, H = sc.width, sc.height
     stream = torch.cuda.current_stream()
     vol = ivv.volume_for(sc)
@@ -305,7 +315,7 @@ def run_ours(args):
     vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS)
     st = vol.stats()
     F = flop_model(scene_degree(sc.blocks))
-    flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP)
+    flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP, implicit=args.rk_method == 7)
     flops_k2 = k2_flops(st, F)
 
     # parity spot check of this frame against the oracle (untimed)
@@ -562,8 +572,11 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="batch64: keep the first N requests (0: all)")
     ap.add_argument("--only-volume", type=int, default=None, help="batch64: keep the requests of one volume")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default launch shapes")
-    ap.add_argument("--rk-method", type=int, default=0, choices=range(7),
-                    help="single-frame workloads: 0 BS3(2) with error control, 1-6 the fixed-step family")
+    ap.add_argument("--rk-method", type=int, default=0, choices=range(8),
+                    help="single-frame workloads: 0 BS3(2) with error control, 1-6 the explicit fixed-step "
+                         "family, 7 implicit Euler")
+    ap.add_argument("--c", type=float, default=None, help="single-frame workloads: the pull-back constant c "
+                                                           "of the ray field (Eq. 10; default 1)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -174,7 +174,10 @@ enum {
   IVV_RK_KUTTA3 = 3,    /* fixed step: Kutta's third-order method (RK3)         */
   IVV_RK_RK4 = 4,       /* fixed step: classic fourth-order Runge-Kutta (RK4)   */
   IVV_RK_RK4_38 = 5,    /* fixed step: Kutta's 3/8 rule (RK4 3/8)               */
-  IVV_RK_FEHLBERG5 = 6  /* fixed step: Fehlberg's pair, fifth-order weights (RKF) */
+  IVV_RK_FEHLBERG5 = 6, /* fixed step: Fehlberg's pair, fifth-order weights (RKF) */
+  IVV_RK_IMPLICIT_EULER = 7  /* fixed step: implicit Euler (IRK1), Newton with the
+                                exact Jacobian of §5.3 (spline Hessian); use with
+                                a large c (the paper's c = 100) */
 };
 
 /* Preimage methods of stage 3 (§5): */

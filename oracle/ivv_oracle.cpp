@@ -153,19 +153,25 @@ struct Basis1D {
 // B-splines applied twice,
 //   N'_{i,q} = q/(t_{i+q}-t_i) N_{i,q-1} - q/(t_{i+q+1}-t_{i+1}) N_{i+1,q-1},
 // once to the degree p-1 functions (giving N'_{.,p}) and once to the
-// derivatives of the degree p-1 functions (giving N''_{.,p}).
+// derivatives of the degree p-1 functions (giving N''_{.,p}).  Outside
+// [t_0, t_end] the polynomials of the first or last non-empty span are
+// continued (the recursion is polynomial in x), which is what the implicit
+// Euler Newton iteration evaluates when an iterate leaves the parameter box.
 void basis_eval2(const Basis1D& B, double x, std::vector<double>& N, std::vector<double>& dN,
                  std::vector<double>& ddN) {
   const std::vector<double>& t = B.t;
   const int p = B.p, n = B.n, m = (int)t.size() - 1;
-  if (x < t[0]) x = t[0];
-  if (x > t[m]) x = t[m];
   std::vector<std::vector<double>> Nq(p + 1);      // Nq[q][i] = N_{i,q}(x)
   Nq[0].assign(m, 0.0);
-  int last_span = -1;
-  for (int i = 0; i < m; ++i) if (t[i] < t[i + 1]) last_span = i;
+  int first_span = -1, last_span = -1;
+  for (int i = 0; i < m; ++i)
+    if (t[i] < t[i + 1]) {
+      if (first_span < 0) first_span = i;
+      last_span = i;
+    }
   for (int i = 0; i < m; ++i) if (t[i] <= x && x < t[i + 1]) Nq[0][i] = 1.0;
-  if (x == t[m]) Nq[0][last_span] = 1.0;
+  if (x >= t[m]) Nq[0][last_span] = 1.0;
+  if (x < t[0]) Nq[0][first_span] = 1.0;
   for (int q = 1; q <= p; ++q) {
     Nq[q].assign(m - q, 0.0);
     for (int i = 0; i < m - q; ++i) {
@@ -237,7 +243,8 @@ void block_eval(const Block& b, const double p[3], double phi[3], double J[3][3]
   if (rho) *rho = s;
 }
 
-// phi, J and the Hessian H[r][a][b] = d^2 phi_r / dp_a dp_b at p.
+// phi, J and the Hessian H[r][a][b] = d^2 phi_r / dp_a dp_b at p (p may lie
+// outside [0,1]^3: the boundary elements' polynomials are continued).
 void block_eval2(const Block& b, const double p[3], double phi[3], double J[3][3], double H[3][3][3]) {
   std::vector<double> N[3], dN[3], ddN[3];
   for (int d = 0; d < 3; ++d) basis_eval2(b.B[d], p[d], N[d], dN[d], ddN[d]);
@@ -722,30 +729,38 @@ bool ode_rhs(const Block& b, const double p[3], const double g_in[3], const doub
 // J_V = c (d d^T - I) (V(g) = d + c [(g_in - g) - <g_in - g, d> d]), and
 // H_phi(x)[v]_{ij} = sum_k d^2 phi_i / dx_j dx_k v_k.  A Newton step then
 // solves (J_phi J_G) dz = -J_phi G.  z starts at 0, so the first iteration
-// evaluates the map at p itself; the evaluation point is clamped to [0,1]^3
-// (§5.4) and the iteration stops once |dz|_inf <= tol (or after max_it).
-// ev(x, phi, J, H) evaluates the map.  Returns the iterations, -1 if a
-// linear system is singular.
+// evaluates the map at p itself.  Iterates may leave the parameter box (the
+// map's boundary polynomials are continued there, so G stays smooth); the
+// iteration stops once |dz|_inf <= tol and the new point p + z is clamped to
+// [0,1]^3 (§5.4: the ray is followed along the boundary).  If Newton does not
+// converge within max_it iterations (or meets a singular system: the map is
+// degenerate near the ray), the step falls back to the clamped explicit
+// Euler step p + h W(p) from the first iteration's evaluation.
+// ev(x, phi, J, H) evaluates the map.  Returns the iterations, or -1 if the
+// step fell back.
 template <class Eval>
 int irk1_step(Eval ev, const double p[3], double h, const double g_in[3], const double d[3], double c,
               double tol, int max_it, double pn[3]) {
-  double z[3] = {0, 0, 0};
+  double z[3] = {0, 0, 0}, v0[3] = {0, 0, 0};
+  bool conv = false;
   int it = 0;
   for (; it < max_it; ++it) {
     double x[3];
-    for (int r = 0; r < 3; ++r) x[r] = std::min(std::max(p[r] + z[r], 0.0), 1.0);
+    for (int r = 0; r < 3; ++r) x[r] = p[r] + z[r];
     double phi[3], J[3][3], H[3][3][3];
     ev(x, phi, J, H);
     double e[3] = {g_in[0] - phi[0], g_in[1] - phi[1], g_in[2] - phi[2]};
     const double ed = dot3(e, d);
     double Vv[3], W[3];
     for (int r = 0; r < 3; ++r) Vv[r] = d[r] + c * (e[r] - ed * d[r]);
-    if (!qr_solve3(J, Vv, W)) return -1;
+    if (!qr_solve3(J, Vv, W)) break;
     double G[3], v[3];
     for (int r = 0; r < 3; ++r) {
       v[r] = h * W[r];                  // z - G(z)
       G[r] = z[r] - v[r];
     }
+    if (it == 0)
+      for (int r = 0; r < 3; ++r) v0[r] = v[r];
     // M = H[v] + (I - h J_V) J,  (I - h J_V) = (1 + h c) I - h c d d^T
     double M[3][3], JG[3];
     for (int i = 0; i < 3; ++i) {
@@ -762,15 +777,16 @@ int irk1_step(Eval ev, const double p[3], double h, const double g_in[3], const 
       JG[i] = -(J[i][0] * G[0] + J[i][1] * G[1] + J[i][2] * G[2]);
     }
     double dz[3];
-    if (!qr_solve3(M, JG, dz)) return -1;
+    if (!qr_solve3(M, JG, dz)) break;
     for (int r = 0; r < 3; ++r) z[r] += dz[r];
     if (std::max(std::fabs(dz[0]), std::max(std::fabs(dz[1]), std::fabs(dz[2]))) <= tol) {
       ++it;
+      conv = true;
       break;
     }
   }
-  for (int r = 0; r < 3; ++r) pn[r] = std::min(std::max(p[r] + z[r], 0.0), 1.0);
-  return it;
+  for (int r = 0; r < 3; ++r) pn[r] = std::min(std::max(p[r] + (conv ? z[r] : v0[r]), 0.0), 1.0);
+  return conv ? it : -1;
 }
 
 // Runge-Kutta-Fehlberg 4(5) coefficients (Fehlberg 1969), 5th-order solution
@@ -931,12 +947,11 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
       auto ev = [&](const double x[3], double phi[3], double J[3][3], double H[3][3][3]) {
         block_eval2(b, x, phi, J, H);
       };
-      if (irk1_step(ev, p, hh, g_in, d, P.c, 1e-13, 50, pn) < 0) {
-        ++st.newton_fail;
-      } else {
-        for (int r = 0; r < 3; ++r) p[r] = pn[r];
-        ++st.rk_steps;
-      }
+      // Newton to |dz| <= 2e-6 (quadratic convergence leaves an error far
+      // below that), at most 12 iterations, as the GPU integrator
+      if (irk1_step(ev, p, hh, g_in, d, P.c, 2e-6, 12, pn) < 0) ++st.newton_fail;
+      for (int r = 0; r < 3; ++r) p[r] = pn[r];
+      ++st.rk_steps;
     } else {
       // integrate the pulled-back ODE from s_{j-1} to s_j with RKF45
       double sc = s[j - 1];

@@ -223,7 +223,7 @@ ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_ren
     return fail(IVV_ERR_INVALID_ARG, "initial guesses apply to the RF method");
   if (p.method == IVV_METHOD_RF && p.precision != IVV_PREC_FP32)
     return fail(IVV_ERR_UNSUPPORTED, "the RF method runs in FP32 precision");
-  if (p.rk_method < IVV_RK_BS32 || p.rk_method > IVV_RK_FEHLBERG5) return fail(IVV_ERR_INVALID_ARG, "bad rk_method");
+  if (p.rk_method < IVV_RK_BS32 || p.rk_method > IVV_RK_IMPLICIT_EULER) return fail(IVV_ERR_INVALID_ARG, "bad rk_method");
   if (p.rk_method != IVV_RK_BS32 && p.method != IVV_METHOD_ODE)
     return fail(IVV_ERR_INVALID_ARG, "rk_method applies to the ODE method");
   if (p.rk_method != IVV_RK_BS32 && p.precision == IVV_PREC_FP64)
@@ -476,6 +476,22 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                                  (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
                                  (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
+  } else if (p.rk_method == IVV_RK_IMPLICIT_EULER) {
+    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    if (st != IVV_OK) return st;
+    const ivv::DevCamera<float> c32 = dev_camera<float>(F);
+    const float4* pin = (const float4*)(ws + L.pair_in);
+    const float4* pout = (const float4*)(ws + L.pair_out);
+    if (V.P == 2)
+      ivv::launch_irk1_p<2>(V, c32, tf, a, mixed, stats, pin, pout, (const int*)(ws + L.pair_block),
+                            (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                            (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
+                            (float4*)out, v->d_stats, v->num_sms, s);
+    else
+      ivv::launch_irk1_p<3>(V, c32, tf, a, mixed, stats, pin, pout, (const int*)(ws + L.pair_block),
+                            (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                            (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
+                            (float4*)out, v->d_stats, v->num_sms, s);
   } else if (p.rk_method != IVV_RK_BS32) {
     st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
     if (st != IVV_OK) return st;

@@ -614,6 +614,12 @@ void launch_fixed_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF
                     const RkTableau& T, bool mixed, bool stats, const float4* pin, const float4* pout,
                     const int* pblk, const int* pcnt, const int* active, const int* n_active, int* queue_head,
                     float4* out, DevStats* st, int num_sms, cudaStream_t s);
+// Implicit Euler (k_irk1.cuh).
+template <int P>
+void launch_irk1_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, const IntegrateArgs& a,
+                   bool mixed, bool stats, const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
+                   const int* active, const int* n_active, int* queue_head, float4* out, DevStats* st, int num_sms,
+                   cudaStream_t s);
 
 void launch_eval_points(const DevVolume& V, int block, int n, const float* p, float* phi, float* jac,
                         float* rho, cudaStream_t s);

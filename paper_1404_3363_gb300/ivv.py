@@ -24,8 +24,9 @@ STATUS_NAMES = {0: "IVV_OK", 1: "IVV_ERR_INVALID_ARG", 2: "IVV_ERR_CUDA", 3: "IV
 FLAG_STATS = 1
 FLAG_TIMING = 2
 GUESS_PARAMS = 4611
-# ODE integrators (rk_method): error-controlled BS3(2) and the fixed-step family
-RK_BS32, RK_EULER, RK_MIDPOINT, RK_KUTTA3, RK_RK4, RK_RK4_38, RK_FEHLBERG5 = range(7)
+# ODE integrators (rk_method): error-controlled BS3(2), the explicit fixed-step
+# family and implicit Euler
+RK_BS32, RK_EULER, RK_MIDPOINT, RK_KUTTA3, RK_RK4, RK_RK4_38, RK_FEHLBERG5, RK_IMPLICIT_EULER = range(8)
 STAGES = ("project", "intersect", "pair", "integrate")
 
 c_double_p = C.POINTER(C.c_double)

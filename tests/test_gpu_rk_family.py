@@ -94,7 +94,7 @@ def test_fixed_step_counters(ivv, method):
 def test_fixed_step_argument_errors(ivv):
     sc = scenes.config(0, width=16, height=16)
     vol = ivv.volume_for(sc)
-    for bad, msg in [(dict(rk_method=7), "rk_method"), (dict(rk_method=4, method=1, precision=scenes.PRECISION_FP32), "ODE method"),
+    for bad, msg in [(dict(rk_method=8), "rk_method"), (dict(rk_method=4, method=1, precision=scenes.PRECISION_FP32), "ODE method"),
                      (dict(rk_method=4, precision=scenes.PRECISION_FP64), "FP32 or MIXED")]:
         prm = dataclasses.replace(sc.params, **bad)
         with pytest.raises(ivv.IvvError, match=msg):
