@@ -105,6 +105,30 @@ def test_full_size_sampled_pixels(ivv):
         assert np.abs(ref).max() <= TOL_RGBA
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_4k_backstep_sampled_pixels(ivv, prec):
+    """3840x2160 backward-facing step (the frame whose sample list is sized
+    from the exact scanned total, read back once): sampled pixels against the
+    oracle computed one by one, and the split path's counters."""
+    sc = scenes.config(4)
+    sc.params.precision = prec
+    vol, img = _gpu_image(ivv, sc)
+    vol.reset_stats()
+    vol.render(sc.camera, sc.params, sc.width, sc.height, flags=ivv.FLAG_STATS)
+    st = vol.stats()
+    assert st["rho_evals"] == st["samples"] > 10_000_000          # the split integration ran
+    assert st["abuf_overflow"] == 0 and st["pair_overflow"] == 0 and st["step_cap"] == 0
+    cov = np.argwhere(img[..., 3] > 0)
+    rng = np.random.default_rng(52 + prec)
+    pick = cov[rng.choice(len(cov), 64, replace=False)]
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    worst = 0.0
+    for y, x in pick:
+        ref = oracle.render(sc, ov, window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
+        worst = max(worst, np.abs(img[y, x] - ref).max())
+    assert worst <= TOL_RGBA, worst
+
+
 def test_window_equals_crop_and_is_deterministic(ivv):
     sc = scenes.config(1, width=200, height=120)
     vol = ivv.volume_for(sc)
