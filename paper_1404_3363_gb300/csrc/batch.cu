@@ -227,6 +227,7 @@ ivv::DevVolume pool_volume(const ivv_batch* b) {
   V.elem32 = b->d_elem32;
   V.elem64 = nullptr;
   V.org32 = b->d_org32;
+  V.rho32 = nullptr;
   V.org64 = nullptr;
   V.face32 = b->d_face32;
   V.face64 = b->d_face64;

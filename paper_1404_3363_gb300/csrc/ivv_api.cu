@@ -80,7 +80,7 @@ namespace {
 
 void free_volume(ivv_volume* v) {
   if (!v) return;
-  void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_org64,
+  void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_rho32, v->d_org64,
                   v->d_count, v->d_face32, v->d_face64,
                   v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
   for (void* p : ptrs)
@@ -117,6 +117,7 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   V.elem32 = v->d_elem32;
   V.elem64 = v->d_elem64;
   V.org32 = v->d_org32;
+  V.rho32 = v->d_rho32;
   V.org64 = v->d_org64;
   V.face32 = v->d_face32;
   V.face64 = v->d_face64;
@@ -636,12 +637,16 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
                             (float)hv.elem[4 * i + 3]);
   for (size_t i = 0; i < face32.size(); ++i)
     face32[i] = make_float4((float)hv.face_cp[4 * i], (float)hv.face_cp[4 * i + 1], (float)hv.face_cp[4 * i + 2], 0.f);
+  const size_t nnn = (size_t)(hv.P + 1) * (hv.P + 1) * (hv.P + 1), rs = (size_t)ivv::rho_stride32(hv.P);
+  std::vector<float> rho32((size_t)hv.n_elems() * rs, 0.f);
+  for (size_t i = 0; i < hv.elem.size() / 4; ++i) rho32[(i / nnn) * rs + i % nnn] = (float)hv.elem[4 * i + 3];
   if ((st = upload(&v->d_blocks, hv.blocks.data(), hv.blocks.size(), s)) != IVV_OK ||
       (st = upload(&v->d_brk32, brk32.data(), brk32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_brk64, hv.brk.data(), hv.brk.size(), s)) != IVV_OK ||
       (st = upload(&v->d_elem32, elem32.data(), elem32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_elem64, (const ivv::Dbl4*)hv.elem.data(), hv.elem.size() / 4, s)) != IVV_OK ||
       (st = upload(&v->d_org32, org32.data(), org32.size(), s)) != IVV_OK ||
+      (st = upload(&v->d_rho32, rho32.data(), rho32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_org64, (const ivv::Dbl4*)hv.elem_org.data(), hv.elem_org.size() / 4, s)) != IVV_OK ||
       (st = upload(&v->d_face32, face32.data(), face32.size(), s)) != IVV_OK ||
       (st = upload(&v->d_face64, (const ivv::Dbl4*)hv.face_cp.data(), hv.face_cp.size() / 4, s)) != IVV_OK ||

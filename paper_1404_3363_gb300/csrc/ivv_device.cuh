@@ -41,6 +41,7 @@ struct DevVolume {
   const float4* elem32;
   const Dbl4* elem64;
   const float4* org32;
+  const float* rho32;     // scalar control points alone, rho_stride32(P) per element (NULL in batches)
   const Dbl4* org64;
   const float4* face32;
   const Dbl4* face64;

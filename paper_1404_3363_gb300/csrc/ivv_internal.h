@@ -37,6 +37,11 @@ struct FaceMeta64 {
   double org[3];
 };
 
+// Floats per element in the scalar-only array: (P+1)^3 scalar control points
+// padded to a multiple of 8, so every element is 32-byte aligned and is read
+// with 256-bit loads (64 for cubic, 32 for quadratic elements).
+constexpr int rho_stride32(int P) { return ((P + 1) * (P + 1) * (P + 1) + 7) & ~7; }
+
 struct BlockInfo {
   int nseg[3];
   int brk_off[3];     // offsets into the breakpoint arrays

@@ -525,11 +525,21 @@ void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, con
 }
 
 // ---- split integration: sample shading
+// Eight consecutive floats with one 256-bit read-only load (32-byte aligned).
+__device__ __forceinline__ void ldg_f8(const float* p, float v[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+
 // The scalar field alone at parameter point p of block B (control-point
-// scalars): one contraction of the 64 scalar coefficients.
+// scalars): one contraction of the (P+1)^3 scalar coefficients, read from the
+// scalar-only array with 256-bit loads (8 per cubic element, 4 per quadratic
+// element), summed in the order of the integrator's fused contraction.
 template <int P>
 __device__ __forceinline__ float eval_rho_cp(const DevVolume& V, const BlockInfo& B, const float p[3]) {
   constexpr int N = P + 1;
+  constexpr int NNN = N * N * N;
   float loc[3];
   int e[3];
 #pragma unroll
@@ -547,23 +557,46 @@ __device__ __forceinline__ float eval_rho_cp(const DevVolume& V, const BlockInfo
       e[dd] = locate<float>(V.brk32 + B.brk_off[dd], B.nseg[dd], x, loc[dd], sc);
     }
   }
-  const size_t base = (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]) * (N * N * N);
+  const float* cp = V.rho32 + (size_t)(B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0]) * rho_stride32(P);
   float bu[N], bv[N], bw[N];
   bernstein_v<P, float>(loc[0], bu);
   bernstein_v<P, float>(loc[1], bv);
   bernstein_v<P, float>(loc[2], bw);
+  static_assert(NNN <= rho_stride32(P), "padded scalar element");
   float s = 0.f;
+  if constexpr (P == 3) {
+    // one i-slab (16 scalars, two loads) at a time
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      float c[16];
+      ldg_f8(cp + 16 * i, c);
+      ldg_f8(cp + 16 * i + 8, c + 8);
+      float si = 0.f;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float si = 0.f;
+      for (int j = 0; j < N; ++j) {
+        float sj = 0.f;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float sj = 0.f;
-#pragma unroll
-      for (int k = 0; k < N; ++k) sj += bw[k] * __ldg(V.elem32 + base + (i * N + j) * N + k).w;
-      si += bv[j] * sj;
+        for (int k = 0; k < N; ++k) sj += bw[k] * c[j * N + k];
+        si += bv[j] * sj;
+      }
+      s += pick<N>(bu, i) * si;
     }
-    s += bu[i] * si;
+  } else {
+    float c[rho_stride32(P)];
+#pragma unroll
+    for (int q = 0; q < rho_stride32(P) / 8; ++q) ldg_f8(cp + 8 * q, c + 8 * q);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float si = 0.f;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float sj = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) sj += bw[k] * c[(i * N + j) * N + k];
+        si += bv[j] * sj;
+      }
+      s += bu[i] * si;
+    }
   }
   return s;
 }
@@ -584,8 +617,10 @@ __device__ __forceinline__ float det_cofactor(const float J[3][3]) {
 // K sub-samples (Alg. 1), stopping at early_alpha.  Neighbouring lanes are
 // neighbouring pixels at the same sample index, so their control-point loads
 // hit the same elements.  With statistics also Delta P (Eq. 5) per sample.
-template <int P, bool STATS>
-__global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<float> cam, DevTF tf, int K,
+// CP: the volume's scalar is its control-point field (a separate instance, so
+// the det J / Eq. 23 instance keeps its own register allocation).
+template <int P, bool STATS, bool CP>
+__global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCamera<float> cam, DevTF tf, int K,
                                                          float early, const float4* __restrict__ pair_in,
                                                          const float4* __restrict__ pair_out,
                                                          const int* __restrict__ pair_block,
@@ -638,7 +673,7 @@ __global__ void __launch_bounds__(128) k_shade_composite(DevVolume V, DevCamera<
         const float4 r = sp[k];
         const float p[3] = {r.x, r.y, r.z};
         float rho;
-        if (!STATS && V.mode == IVV_SCALAR_CP) {
+        if (!STATS && CP) {
           rho = eval_rho_cp<P>(V, B, p);
         } else {
           float phi[3], J[3][3], rc;
@@ -705,12 +740,13 @@ void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, c
   int grid = num_sms * 8;
   const int useful = (npix + 127) / 128;
   grid = grid < useful ? grid : (useful > 0 ? useful : 1);
-  if (stats)
-    k_shade_composite<P, true><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active,
-                                                     off, npix, ds, tail_eps, sa.cap, sa.sp, out, st);
-  else
-    k_shade_composite<P, false><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active,
-                                                      off, npix, ds, tail_eps, sa.cap, sa.sp, out, st);
+  const bool cp = V.mode == IVV_SCALAR_CP;
+#define IVV_SHADE(SS, CC)                                                                                   \
+  k_shade_composite<P, SS, CC><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active, \
+                                                    off, npix, ds, tail_eps, sa.cap, sa.sp, out, st)
+  if (stats) { if (cp) IVV_SHADE(true, true); else IVV_SHADE(true, false); }
+  else { if (cp) IVV_SHADE(false, true); else IVV_SHADE(false, false); }
+#undef IVV_SHADE
 }
 
 template <int P>

@@ -22,6 +22,7 @@ struct ivv_volume {
   float4* d_elem32 = nullptr;
   ivv::Dbl4* d_elem64 = nullptr;
   float4* d_org32 = nullptr;
+  float* d_rho32 = nullptr;
   ivv::Dbl4* d_org64 = nullptr;
   float4* d_face32 = nullptr;
   ivv::Dbl4* d_face64 = nullptr;
