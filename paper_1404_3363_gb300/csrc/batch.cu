@@ -120,6 +120,10 @@ struct ivv_batch {
   // workspace
   BatchLayout L{};
   char* ws = nullptr;
+  // sample buffer of the split integration (sp_cap samples; NULL: fused K5)
+  float4* d_sp = nullptr;
+  long long sp_cap = 0;
+  bool sp_sized = false;
   // launch shapes, graph, timing
   ivv_batch_tuning tune{8, 4, 4, 8};
   int k5_max_ctas[2] = {1, 1};              // occupancy limit without / with statistics
@@ -145,7 +149,7 @@ void free_batch(ivv_batch* b) {
   drop_graph(b);
   void* ptrs[] = {b->d_blocks, b->d_brk32, b->d_brk64, b->d_elem32, b->d_org32, b->d_face32, b->d_face64,
                   b->d_faces, b->d_faces64, b->d_req, b->d_pix0, b->d_tile0[0], b->d_tile0[1], b->d_tile0[2],
-                  b->d_tile0[3], b->d_tf, b->d_stats, b->ws};
+                  b->d_tile0[3], b->d_tf, b->d_stats, b->ws, b->d_sp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : b->ev)
@@ -248,8 +252,9 @@ ivv::BatchArgs batch_args(const ivv_batch* b) {
   return a;
 }
 
-// Every stage of one batch render on stream s.
-ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
+// Every stage of one batch render on stream s.  measure: stop after the
+// sample counts and their scan (the total lands in counters[2]).
+ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s, bool measure = false) {
   const ivv::DevVolume V = pool_volume(b);
   const ivv::BatchArgs ba = batch_args(b);
   const BatchLayout& L = b->L;
@@ -280,6 +285,17 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
                          (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), (int*)(ws + L.active),
                          (int*)(ws + L.counters), b->d_stats, s);
   if (timing) IVV_BCUDA(cudaEventRecord(b->ev[3], s));
+  int* counters = (int*)(ws + L.counters);
+  int* cnt = (int*)(ws + L.frag_count);            // fragment lists are dead after stage 2
+  int* off = (int*)(ws + L.frag_meta);
+  if (measure) {
+    ivv::launch_batch_count(ba, (const float4*)(ws + L.pair_in), (const float4*)(ws + L.pair_out),
+                            (const int*)(ws + L.pair_count), (const int*)(ws + L.active), counters, npix, cnt,
+                            b->num_sms, s);
+    ivv::launch_rf_scan(cnt, counters, npix, off, off + npix, 0x7fffffff, counters + 2, s);
+    IVV_BCUDA(cudaGetLastError());
+    return IVV_OK;
+  }
   ivv::IntegrateArgs a;
   a.rk_tol = (float)b->p.rk_tol;
   a.ds = 0.f;                        // per request
@@ -292,15 +308,47 @@ ivv_status enqueue(ivv_batch* b, bool stats, bool timing, cudaStream_t s) {
   const int cps = std::min(b->tune.k5_ctas_per_sm, b->k5_max_ctas[stats ? 1 : 0]);
   int grid = b->num_sms * std::max(cps, 1);
   grid = std::min(grid, std::max(1, (npix + 127) / 128));
-  ivv::launch_batch_integrate(V, ba, a, mixed, stats, (const float4*)(ws + L.pair_in),
-                              (const float4*)(ws + L.pair_out), (const int*)(ws + L.pair_block),
-                              (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
-                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff, b->d_stats, grid, s);
+  if (b->d_sp)
+    ivv::launch_batch_split(V, ba, a, mixed, stats, (const float4*)(ws + L.pair_in), (const float4*)(ws + L.pair_out),
+                            (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                            (const int*)(ws + L.active), counters, off, cnt, off + npix, b->d_sp, (int)b->sp_cap,
+                            (int*)(ws + L.slow), grid, b->num_sms, b->d_stats, s);
+  else
+    ivv::launch_batch_integrate(V, ba, a, mixed, stats, (const float4*)(ws + L.pair_in),
+                                (const float4*)(ws + L.pair_out), (const int*)(ws + L.pair_block),
+                                (const int*)(ws + L.pair_count), (const int*)(ws + L.active), counters,
+                                counters + ivv::kQueueHeadOff, b->d_stats, grid, s);
   if (timing) {
     IVV_BCUDA(cudaEventRecord(b->ev[4], s));
     b->timed = true;
   }
   IVV_BCUDA(cudaGetLastError());
+  return IVV_OK;
+}
+
+// The split integration's sample buffer, sized once from the samples of the
+// batch as it is (stages 1-2 and the counts run eagerly on s; the samples of
+// later camera changes may differ: pixels beyond the buffer are rendered by
+// the fused integrator).  Without room for it, stage 3 stays fused.
+ivv_status ensure_samples(ivv_batch* b, cudaStream_t s) {
+  if (b->sp_sized) return IVV_OK;
+  ivv::DevStats saved;                 // the measuring pass leaves the statistics as they were
+  IVV_BCUDA(cudaMemcpyAsync(&saved, b->d_stats, sizeof(saved), cudaMemcpyDeviceToHost, s));
+  const ivv_status st = enqueue(b, false, false, s, true);
+  if (st != IVV_OK) return st;
+  int total = 0;
+  IVV_BCUDA(cudaMemcpyAsync(&total, (int*)(b->ws + b->L.counters) + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  IVV_BCUDA(cudaMemcpyAsync(b->d_stats, &saved, sizeof(saved), cudaMemcpyHostToDevice, s));
+  IVV_BCUDA(cudaStreamSynchronize(s));
+  const long long cap = std::min<long long>((long long)total + total / 4 + 4096, 0x7fffffffll);
+  if (cudaMalloc((void**)&b->d_sp, sizeof(float4) * (size_t)cap) == cudaSuccess) {
+    b->sp_cap = cap;
+  } else {
+    cudaGetLastError();
+    b->d_sp = nullptr;
+    b->sp_cap = 0;
+  }
+  b->sp_sized = true;
   return IVV_OK;
 }
 
@@ -522,6 +570,8 @@ ivv_status ivv_batch_render(ivv_batch* b, int flags, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   b->last_stream = s;
   const bool stats = (flags & IVV_FLAG_STATS) != 0, timing = (flags & IVV_FLAG_TIMING) != 0;
+  const ivv_status sst = ensure_samples(b, s);
+  if (sst != IVV_OK) return sst;
   if (stats || timing) return enqueue(b, stats, timing, s);
   if (!b->exec) {
     const ivv_status st = capture(b);
@@ -579,6 +629,10 @@ ivv_status ivv_batch_autotune(ivv_batch* b, int reps, ivv_batch_tuning* best, fl
     return IVV_OK;
   };
   drop_graph(b);
+  {
+    const ivv_status sst = ensure_samples(b, s);
+    if (sst != IVV_OK) return sst;
+  }
   ivv_batch_tuning cur = b->tune, win = cur;
   float best_t = 1e30f;
   for (int k = 0; k < kNumWarpShapes; ++k) {     // K2a warp tile by the surface stage

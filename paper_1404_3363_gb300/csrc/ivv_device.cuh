@@ -500,14 +500,17 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
   return make_float4(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z), a.w + t * (b.w - a.w));
 }
 
-// Counters block of a render: [0] active pixels, [2] RF sample total, [3]
+// Counters block of a render: [0] active pixels, [2] sample total, [3]
 // spare, [4] stage-1 items, [5] their hand-out head, [6] deferred items, [7]
-// their hand-out head; the integrator's queue head at kQueueHeadOff.
+// their hand-out head, [8] and [9] the batch's overflow list and its queue
+// head; the integrator's queue head at kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
 constexpr int kItemCounter = 4;
 constexpr int kItemHead = 5;         // next stage-1 item to hand out (K2b)
 constexpr int kSlowCounter = 6;      // items deferred to the subdivision search
 constexpr int kSlowHead = 7;         // next deferred item to hand out (K2c)
+constexpr int kOverflowCounter = 8;  // batch: pixels beyond the sample buffer
+constexpr int kOverflowHead = 9;     // batch: the fused integrator's queue head over them
 constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
@@ -600,6 +603,16 @@ void launch_batch_integrate(const DevVolume& V, const BatchArgs& ba, const Integ
                             const int* active, const int* n_active, int* queue_head, DevStats* st, int grid,
                             cudaStream_t s);
 int batch_integrate_max_ctas_per_sm(int P, bool mixed, bool stats);
+// Split stage 3 of a batch (k_integrate_batch.cu): counts into cnt, their
+// scan into off (sums: scan scratch), trace and shading into the sample
+// buffer sp of cap samples, the fused integrator over the pixels that do not
+// fit (list: npix ints of scratch).  counters: the render's counters block.
+void launch_batch_count(const BatchArgs& ba, const float4* pin, const float4* pout, const int* pcnt, const int* active,
+                        const int* n_active, int npix, int* cnt, int num_sms, cudaStream_t s);
+void launch_batch_split(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a, bool mixed, bool stats,
+                        const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
+                        int* counters, int* off, int* cnt, int* sums, float4* sp, int cap, int* list, int grid,
+                        int num_sms, DevStats* st, cudaStream_t s);
 
 // Explicit Runge-Kutta tableau of the fixed-step integrators, at most
 // kRkStagesMax stages (a strictly lower triangular).

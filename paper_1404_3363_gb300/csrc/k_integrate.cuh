@@ -619,9 +619,14 @@ __device__ __forceinline__ float det_cofactor(const float J[3][3]) {
 // hit the same elements.  With statistics also Delta P (Eq. 5) per sample.
 // CP: the volume's scalar is its control-point field (a separate instance, so
 // the det J / Eq. 23 instance keeps its own register allocation).
-template <int P, bool STATS, bool CP>
+// BATCH: pixels of every request of a batch; each takes its request's camera,
+// sample distance, transfer-function slot and output image, and each block's
+// scalar mode (CP unused); a pixel whose sample list does not fit the list
+// (off + cnt > cap) is left to the fused integrator.
+template <int P, bool STATS, bool CP, bool BATCH = false>
 __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCamera<float> cam, DevTF tf, int K,
-                                                         float early, const float4* __restrict__ pair_in,
+                                                         float early, BatchArgs ba, const int* __restrict__ cnt,
+                                                         const float4* __restrict__ pair_in,
                                                          const float4* __restrict__ pair_out,
                                                          const int* __restrict__ pair_block,
                                                          const int* __restrict__ pair_count,
@@ -630,21 +635,23 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
                                                          int npix, float ds, float tail_eps, int cap,
                                                          const float4* __restrict__ sp, float4* __restrict__ out,
                                                          DevStats* __restrict__ st) {
-  __shared__ float s_r[256];
-  __shared__ float4 s_rgba[256];
-  __shared__ unsigned char s_seg[kTfTable];
-  for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
-    s_r[i] = tf.r[i];
-    s_rgba[i] = tf.rgba[i];
+  __shared__ float s_r[BATCH ? 1 : 256];
+  __shared__ float4 s_rgba[BATCH ? 1 : 256];
+  __shared__ unsigned char s_seg[BATCH ? 1 : kTfTable];
+  if constexpr (!BATCH) {
+    for (int i = threadIdx.x; i < tf.n; i += blockDim.x) {
+      s_r[i] = tf.r[i];
+      s_rgba[i] = tf.rgba[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
+      const float x = (float)i / (float)kTfTable;
+      int k = 0;
+      while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
+      s_seg[i] = (unsigned char)k;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTfTable; i += blockDim.x) {
-    const float x = (float)i / (float)kTfTable;
-    int k = 0;
-    while (k < tf.n - 2 && s_r[k + 1] <= x) ++k;
-    s_seg[i] = (unsigned char)k;
-  }
-  __syncthreads();
   const int nact = *n_active;
   unsigned long long c_samp = 0, c_rho = 0;
   float max_dp = 0.f;
@@ -652,6 +659,31 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     const int pix = active[item];
     const int np = pair_count[pix];
     int k = off[item];
+    const float* tr = s_r;
+    const float4* trgba = s_rgba;
+    const unsigned char* tseg = s_seg;
+    DevTF t2 = tf;
+    DevCamera<float> cm = cam;
+    int loc = pix;          // the pixel's index in its image (and in dst)
+    float4* dst = out;
+    if constexpr (BATCH) {
+      if (k + __ldg(cnt + item) > cap) continue;       // rendered by the fused integrator
+      const int rq = batch_request(ba, pix);
+      const DevRequest& rr = ba.req[rq];
+      const DevTFSlot& ts = ba.tf[rq];
+      tr = ts.r;
+      trgba = ts.rgba;
+      tseg = ts.seg;
+      t2.n = ts.n;
+      t2.sigma = ts.sigma;
+      t2.lo = ts.lo;
+      t2.inv_range = ts.inv_range;
+      ds = rr.ds;
+      tail_eps = 1e-12f * rr.diag;
+      loc = pix - __ldg(ba.pix0 + rq);
+      dst = rr.out;
+      if (STATS) cm = rr.cam;
+    }
     Acc<float> acc;
     acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;
     bool done = false;
@@ -673,19 +705,20 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
         const float4 r = sp[k];
         const float p[3] = {r.x, r.y, r.z};
         float rho;
-        if (!STATS && CP) {
+        const int mode = BATCH ? B.mode : V.mode;
+        if (!STATS && !BATCH && CP) {
           rho = eval_rho_cp<P>(V, B, p);
         } else {
           float phi[3], J[3][3], rc;
-          if (V.mode == IVV_SCALAR_CP)
+          if (mode == IVV_SCALAR_CP)
             eval_block<P, float, true>(V, B, p, phi, J, rc);
           else
             eval_block<P, float, false, true>(V, B, p, phi, J, rc);
-          if (V.mode == IVV_SCALAR_CP) {
+          if (mode == IVV_SCALAR_CP) {
             rho = rc;
           } else {
             const float det = det_cofactor(J);
-            if (V.mode == IVV_SCALAR_DETJ) {
+            if (mode == IVV_SCALAR_DETJ) {
               rho = det;
             } else {
               float f = 0.f;
@@ -696,7 +729,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
               rho = det / sqrtf(f);
             }
           }
-          if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cam, phi, pix % cam.w, pix / cam.w));
+          if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cm, phi, loc % cm.w, loc / cm.w));
         }
         const float s = j <= nsamp ? (float)j * ds : L;
         if (STATS) {
@@ -704,7 +737,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
           ++c_rho;
         }
         if (j > 0) {
-          composite_interval<float>(s_r, s_rgba, s_seg, tf, K, rho_prev, rho, s - s_prev, acc);
+          composite_interval<float>(tr, trgba, tseg, t2, K, rho_prev, rho, s - s_prev, acc);
           if (acc.a >= early) {
             done = true;
             break;
@@ -714,7 +747,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
         s_prev = s;
       }
     }
-    out[pix] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
+    dst[loc] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
   }
   if (STATS) {
 #pragma unroll
@@ -742,8 +775,9 @@ void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, c
   grid = grid < useful ? grid : (useful > 0 ? useful : 1);
   const bool cp = V.mode == IVV_SCALAR_CP;
 #define IVV_SHADE(SS, CC)                                                                                   \
-  k_shade_composite<P, SS, CC><<<grid, 128, 0, s>>>(V, cam, tf, K, early, pin, pout, pblk, pcnt, active, n_active, \
-                                                    off, npix, ds, tail_eps, sa.cap, sa.sp, out, st)
+  k_shade_composite<P, SS, CC><<<grid, 128, 0, s>>>(V, cam, tf, K, early, BatchArgs{}, nullptr, pin, pout, pblk,  \
+                                                    pcnt, active, n_active, off, npix, ds, tail_eps, sa.cap, sa.sp, \
+                                                    out, st)
   if (stats) { if (cp) IVV_SHADE(true, true); else IVV_SHADE(true, false); }
   else { if (cp) IVV_SHADE(false, true); else IVV_SHADE(false, false); }
 #undef IVV_SHADE

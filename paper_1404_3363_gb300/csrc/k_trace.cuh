@@ -14,14 +14,21 @@
 // error combination -- after the second, so k2 and k3 are never live
 // together.  The dense output of an accepted step is written before p and k1
 // move to the step end, so the previous step needs no copy.
+//
+// BATCH: the queue holds pixels of every request of a batch; a lane looks up
+// its pixel's request (camera, sample distance, volume diagonal) when it
+// takes the pixel.  A pixel whose sample list would end beyond the list's
+// capacity (off + cnt > cap) is skipped here and in the shading pass; the
+// batch renders such pixels with the fused integrator.
 #pragma once
 
 #include "k_integrate.cuh"
 
 namespace ivv {
 
-template <int P, bool MIXED, bool STATS>
-__global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float> cam, IntegrateArgs args,
+template <int P, bool MIXED, bool STATS, bool BATCH = false>
+__global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float> cam, IntegrateArgs args, BatchArgs ba,
+                                                   const int* __restrict__ cnt,
                                                    const float4* __restrict__ pair_in,
                                                    const float4* __restrict__ pair_out,
                                                    const int* __restrict__ pair_block,
@@ -33,10 +40,12 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
   const int nact = *n_active;
   if (nact == 0) return;
   const int npix = args.npix;
-  const float tol = args.rk_tol, cc = args.c, ds = args.ds;
-  const float tail_eps = 1e-12f * V.diag;
-  const float hmin = 1e-7f * ds;
-  const float hmax = (float)args.max_step_samples * ds;
+  const float tol = args.rk_tol, cc = args.c;
+  float ds = args.ds;
+  float tail_eps = 1e-12f * V.diag;
+  float hmin = 1e-7f * ds;
+  float hmax = (float)args.max_step_samples * ds;
+  int rq = 0;             // BATCH: request of the lane's pixel
   unsigned long long c_rhs = 0, c_steps = 0, c_rej = 0, c_fp64 = 0, c_cap = 0;
 
   int pix = -1;           // -1: needs a pixel; -2: queue drained
@@ -60,12 +69,24 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
           np = __ldg(pair_count + pix);
           q = -1;
           stage = 0;
+          if constexpr (BATCH) {
+            if (kidx + __ldg(cnt + item) > cap) {
+              pix = -1;                  // beyond the sample list: the fused integrator's
+            } else {
+              rq = batch_request(ba, pix);
+              const DevRequest& rr = ba.req[rq];
+              ds = rr.ds;
+              tail_eps = 1e-12f * rr.diag;
+              hmin = 1e-7f * ds;
+              hmax = (float)args.max_step_samples * ds;
+            }
+          }
         } else {
           pix = -2;
         }
       }
     }
-    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) break;
+    if (__ballot_sync(0xffffffffu, pix != -2) == 0) break;   // every lane found the queue drained
 
     bool live = pix >= 0;
     if (live && stage == 0) {
@@ -80,7 +101,13 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
         blk = __ldg(pair_block + slot);
         B = V.blocks[blk];
         float o[3];
-        make_ray<float>(cam, cam.x0 + pix % cam.w, cam.y0 + pix / cam.w, o, d);
+        if constexpr (BATCH) {
+          const DevCamera<float>& cm = ba.req[rq].cam;
+          const int loc = pix - __ldg(ba.pix0 + rq);
+          make_ray<float>(cm, cm.x0 + loc % cm.w, cm.y0 + loc / cm.w, o, d);
+        } else {
+          make_ray<float>(cam, cam.x0 + pix % cam.w, cam.y0 + pix / cam.w, o, d);
+        }
 #pragma unroll
         for (int r = 0; r < 3; ++r) g_in[r] = o[r] + pi.x * d[r];
         p[0] = pi.y; p[1] = pi.z; p[2] = pi.w;
@@ -228,8 +255,8 @@ void launch_k5_trace(const DevVolume& V, const DevCamera<float>& cam, const Inte
   int grid = num_sms * blocks_per_sm;
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
-  k5_trace<P, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, a, pin, pout, pblk, pcnt, active, n_active, queue_head,
-                                                 sa.off, sa.sp, sa.cap, st);
+  k5_trace<P, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, a, BatchArgs{}, nullptr, pin, pout, pblk, pcnt, active,
+                                                 n_active, queue_head, sa.off, sa.sp, sa.cap, st);
 }
 
 template <int P>

@@ -164,6 +164,36 @@ def test_graph_replay_eager_and_camera_update(ivv, pool):
         assert torch.equal(outs[k], keep[k])
 
 
+def test_camera_change_beyond_the_sample_buffer(ivv, pool):
+    """The split integration's sample buffer is sized by the first render;
+    zooming every camera in afterwards multiplies the samples, and the pixels
+    that no longer fit are rendered by the fused integrator: the images still
+    match the oracle, and the zoomed-out cameras render as before."""
+    vols, reqs, gpu, orc = pool
+    small = _small(reqs, SIZES, 4)
+    b = _batch(ivv, gpu, small)
+    first = [o.clone() for o in b.render()]
+    torch.cuda.synchronize()
+    zoomed = []
+    for i, q in enumerate(small):
+        c = q.camera
+        eye = tuple(np.asarray(c.target) + (np.asarray(c.eye) - np.asarray(c.target)) / 3.0)
+        cam = dataclasses.replace(c, eye=eye, ortho_height=c.ortho_height / 3.0)
+        zoomed.append(cam)
+        b.set_camera(i, cam)
+    outs = b.render()
+    torch.cuda.synchronize()
+    for i, q in enumerate(small):
+        ref = oracle.render(dataclasses.replace(_scene(vols, q), camera=zoomed[i]), orc[q.volume])
+        assert np.abs(_np(outs[i]) - ref).max() <= TOL_RGBA, i
+    for i, q in enumerate(small):
+        b.set_camera(i, q.camera)
+    again = b.render()
+    torch.cuda.synchronize()
+    for x, y in zip(first, again):
+        assert torch.equal(x, y)
+
+
 def test_autotune_picks_a_valid_shape(ivv, pool):
     vols, reqs, gpu, orc = pool
     small = _small(reqs, [(128, 96), (96, 128)], 6)
