@@ -546,7 +546,7 @@ def run_batch(args):
             "gpu_launches": 4 * args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_batch": e2e_ms, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": npix * 16},
-            "roofline": {"bound": "alu", "kernel": "k5_integrate (batched)", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "stage3_integrate (batched)", "achieved": achieved,
                          "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
                          "flops_per_launch": flops_k5, "ms_per_launch": k5_ms},
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
