@@ -451,9 +451,13 @@ typedef struct {
 } ivv_batch_tuning;
 
 /* Build a batch of n requests (1..IVV_BATCH_MAX_REQUESTS) rendered with the
- * shared parameters `params` (NULL: defaults; method ODE, precision FP32 or
- * MIXED, no window; ds <= 0 gives each request its volume's diag/128).
- * Uploads the pool and the request table on `stream` and synchronises it. */
+ * shared parameters `params` (NULL: defaults; method ODE with rk_method
+ * IVV_RK_BS32, precision FP32 or MIXED, no window, no cutting or near-clip
+ * planes; ds <= 0 gives each request its volume's diag/128; anything else is
+ * IVV_ERR_UNSUPPORTED).  Uploads the pool and the request table on `stream`
+ * and synchronises it.  The first render also sizes the batch's sample
+ * buffer (one eager pass of stages 1-2 and a read-back of the sample total,
+ * synchronising `stream` once). */
 ivv_status ivv_batch_create(const ivv_request* requests, int n, const ivv_render_params* params, void* stream,
                             ivv_batch** out);
 

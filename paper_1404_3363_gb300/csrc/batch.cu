@@ -402,6 +402,8 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
     return bfail(IVV_ERR_INVALID_ARG, "batches render whole images (no window)");
   if (p.near_clip > 0 || p.n_cut_planes > 0)
     return bfail(IVV_ERR_UNSUPPORTED, "batches render without cutting or near-clip planes");
+  if (p.rk_method != IVV_RK_BS32)
+    return bfail(IVV_ERR_UNSUPPORTED, "batches integrate with the error-controlled BS3(2) pair (rk_method 0)");
   p.flags = 0;
 
   ivv_batch* b = new ivv_batch();

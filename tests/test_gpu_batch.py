@@ -243,6 +243,9 @@ def test_batch_argument_errors(ivv, pool):
         ivv.Batch([item], scenes.RenderParams(method=1))
     with pytest.raises(ivv.IvvError, match="FP32 or MIXED"):
         ivv.Batch([item], scenes.RenderParams(precision=scenes.PRECISION_FP64))
+    for rk in (1, 7):
+        with pytest.raises(ivv.IvvError, match="BS3"):
+            ivv.Batch([item], scenes.RenderParams(rk_method=rk))
     big = scenes.TransferFunction(np.linspace(0, 1, 65).astype(np.float32),
                                   np.full((65, 4), 0.5, np.float32), 4.0)
     with pytest.raises(ivv.IvvError, match="tf_n"):
