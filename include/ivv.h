@@ -244,15 +244,21 @@ ivv_status ivv_set_transfer_function(ivv_volume* vol, int n_knots, const float* 
 ivv_status ivv_get_scalar_range(const ivv_volume* vol, double* lo, double* hi);
 
 /* Bytes of device workspace ivv_render needs for a width x height window at
- * the given precision (fragment lists, pair lists, queues, counters). */
+ * the given precision (fragment lists, pair lists, queues, counters).
+ * Windows are limited to 2^27 pixels (IVV_ERR_INVALID_ARG beyond). */
 ivv_status ivv_workspace_size(const ivv_volume* vol, int width, int height, int precision,
                               size_t* bytes);
 
-/* Render a width x height window into out_rgba (device, caller-owned,
- * [height][width][4] float32).  workspace: device buffer of at least
- * ivv_workspace_size bytes, 256-byte aligned; NULL makes the library use a
- * buffer it owns (grown with cudaMalloc outside of any stream capture).
- * All work is enqueued on `stream`; nothing is synchronised. */
+/* Render a width x height window (at most 2^27 pixels) into out_rgba
+ * (device, caller-owned, [height][width][4] float32).  workspace: device
+ * buffer of at least ivv_workspace_size bytes, 256-byte aligned; NULL makes
+ * the library use a buffer it owns (grown with cudaMalloc outside of any
+ * stream capture).  The FP32 / MIXED ODE method also keeps a sample buffer
+ * per volume (16 bytes per sample, grown with cudaMalloc).  All work is
+ * enqueued on `stream` and nothing is synchronised, except that a window
+ * whose sample bound exceeds 4 GiB (e.g. 3840x2160 at ds = diag/128) reads
+ * its sample total back once (synchronising `stream`; under a stream
+ * capture such a window takes the fused integrator instead). */
 ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
                       int width, int height, float* out_rgba, void* workspace,
                       size_t workspace_bytes, void* stream);

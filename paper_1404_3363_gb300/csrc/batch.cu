@@ -336,12 +336,12 @@ ivv_status ensure_samples(ivv_batch* b, cudaStream_t s) {
   IVV_BCUDA(cudaMemcpyAsync(&saved, b->d_stats, sizeof(saved), cudaMemcpyDeviceToHost, s));
   const ivv_status st = enqueue(b, false, false, s, true);
   if (st != IVV_OK) return st;
-  int total = 0;
-  IVV_BCUDA(cudaMemcpyAsync(&total, (int*)(b->ws + b->L.counters) + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int total[2] = {0, 0};               // the sample total and its excess over INT_MAX
+  IVV_BCUDA(cudaMemcpyAsync(total, (int*)(b->ws + b->L.counters) + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   IVV_BCUDA(cudaMemcpyAsync(b->d_stats, &saved, sizeof(saved), cudaMemcpyHostToDevice, s));
   IVV_BCUDA(cudaStreamSynchronize(s));
-  const long long cap = std::min<long long>((long long)total + total / 4 + 4096, 0x7fffffffll);
-  if (cudaMalloc((void**)&b->d_sp, sizeof(float4) * (size_t)cap) == cudaSuccess) {
+  const long long cap = std::min<long long>((long long)total[0] + total[0] / 4 + 4096, 0x7fffffffll);
+  if (total[1] == 0 && cudaMalloc((void**)&b->d_sp, sizeof(float4) * (size_t)cap) == cudaSuccess) {
     b->sp_cap = cap;
   } else {
     cudaGetLastError();

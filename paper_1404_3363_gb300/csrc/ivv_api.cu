@@ -127,6 +127,9 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   return V;
 }
 
+// Largest window of one render: pixel, item and slot indices stay in int.
+constexpr long long kMaxWindowPixels = 1ll << 27;
+
 struct Frame {
   double eye[3], f[3], r[3], u[3], sx, sy;
   int ortho, W, H, x0, y0, w, h;
@@ -135,6 +138,8 @@ struct Frame {
 ivv_status make_frame(const ivv_camera* c, const ivv_render_params& p, int width, int height, Frame& F) {
   if (!c) return fail(IVV_ERR_INVALID_ARG, "camera is NULL");
   if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  if ((long long)width * height > kMaxWindowPixels)
+    return fail(IVV_ERR_INVALID_ARG, "window larger than 2^27 pixels");
   F.W = p.full_width > 0 ? p.full_width : width;
   F.H = p.full_height > 0 ? p.full_height : height;
   F.x0 = p.x0;
@@ -538,11 +543,11 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
       if (by_bound) {
         cap = split_bound(v, p) * npix;
       } else {
-        int total = 0;
-        IVV_CUDA(cudaMemcpyAsync(&total, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int total[2] = {0, 0};          // the sample total and its excess over INT_MAX
+        IVV_CUDA(cudaMemcpyAsync(total, counters + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         IVV_CUDA(cudaStreamSynchronize(s));
-        cap = (size_t)std::max(total, 1);
-        split = (double)cap * sizeof(float4) <= kSplitMaxBytes;
+        cap = (size_t)std::max(total[0], 1);
+        split = total[1] == 0 && (double)cap * sizeof(float4) <= kSplitMaxBytes;
       }
     }
     if (split) {
@@ -759,6 +764,8 @@ ivv_status ivv_get_scalar_range(const ivv_volume* v, double* lo, double* hi) {
 ivv_status ivv_workspace_size(const ivv_volume* v, int width, int height, int precision, size_t* bytes) {
   if (!v || !bytes) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
   if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  if ((long long)width * height > kMaxWindowPixels)
+    return fail(IVV_ERR_INVALID_ARG, "window larger than 2^27 pixels");
   const bool fp64 = precision == IVV_PREC_FP64;
   *bytes = layout(v->hv.n_faces(), (size_t)width * height, fp64 ? sizeof(ivv::Dbl4) : sizeof(float4)).total;
   return IVV_OK;

@@ -653,6 +653,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     __syncthreads();
   }
   const int nact = *n_active;
+  const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
   unsigned long long c_samp = 0, c_rho = 0;
   float max_dp = 0.f;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     int loc = pix;          // the pixel's index in its image (and in dst)
     float4* dst = out;
     if constexpr (BATCH) {
-      if (k + __ldg(cnt + item) > cap) continue;       // rendered by the fused integrator
+      if (excess || k < 0 || k + __ldg(cnt + item) > cap) continue;   // rendered by the fused integrator
       const int rq = batch_request(ba, pix);
       const DevRequest& rr = ba.req[rq];
       const DevTFSlot& ts = ba.tf[rq];

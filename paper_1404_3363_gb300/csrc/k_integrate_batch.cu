@@ -45,13 +45,17 @@ __global__ void kb_count(BatchArgs ba, const float4* __restrict__ pair_in, const
   }
 }
 
-// Active pixels whose sample list would end beyond cap, for the fused integrator.
+// Active pixels whose sample list would end beyond cap (all of them when the
+// scanned total did not fit an int: n_active[3] > 0), for the fused integrator.
 __global__ void kb_overflow(const int* __restrict__ active, const int* __restrict__ n_active,
                             const int* __restrict__ off, const int* __restrict__ cnt, int cap, int* __restrict__ list,
                             int* __restrict__ n_list) {
   const int nact = *n_active;
-  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x)
-    if (__ldg(off + item) + __ldg(cnt + item) > cap) list[atomicAdd(n_list, 1)] = __ldg(active + item);
+  const bool excess = n_active[3] > 0;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int o = __ldg(off + item);
+    if (excess || o < 0 || o + __ldg(cnt + item) > cap) list[atomicAdd(n_list, 1)] = __ldg(active + item);
+  }
 }
 
 template <int P, bool MIXED, bool STATS>

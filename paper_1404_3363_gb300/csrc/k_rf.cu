@@ -98,11 +98,13 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_local(const int* __restrict
   if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = incl;
 }
 
-// exclusive scan of the CTA sums (one CTA, chunks of kScanBlock) and total
+// exclusive scan of the CTA sums (one CTA, chunks of kScanBlock) and total;
+// the running total is kept in 64 bits, so a total beyond cap (at most
+// INT_MAX) is reported as cap with the excess in total[1]
 __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* __restrict__ sums, const int* __restrict__ n_ptr,
                                                           int cap, int* __restrict__ total) {
   __shared__ int warp_tot[kScanBlock / 32];
-  __shared__ int carry;
+  __shared__ long long carry;
   const int n = (*n_ptr + kScanBlock - 1) / kScanBlock;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0;
@@ -129,14 +131,19 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* __restrict__ sums
     }
     __syncthreads();
     const int incl = v + (warp > 0 ? warp_tot[warp - 1] : 0);
-    const int c = carry;
-    if (i < n) sums[i] = c + incl - x;
+    const long long c = carry;
+    if (i < n) sums[i] = (int)(c + incl - x);
     __syncthreads();
     if (threadIdx.x == kScanBlock - 1) carry = c + incl;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry < cap ? carry : cap;
-  if (threadIdx.x == 0 && carry > cap) total[1] = carry - cap;   // overflow count
+  if (threadIdx.x == 0) {
+    *total = carry < (long long)cap ? (int)carry : cap;
+    if (carry > (long long)cap) {                                  // overflow count
+      const long long ex = carry - cap;
+      total[1] = ex < 0x7fffffffll ? (int)ex : 0x7fffffff;
+    }
+  }
 }
 
 __global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ n_ptr, const int* __restrict__ sums) {

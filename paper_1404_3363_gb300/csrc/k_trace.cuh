@@ -18,7 +18,8 @@
 // BATCH: the queue holds pixels of every request of a batch; a lane looks up
 // its pixel's request (camera, sample distance, volume diagonal) when it
 // takes the pixel.  A pixel whose sample list would end beyond the list's
-// capacity (off + cnt > cap) is skipped here and in the shading pass; the
+// capacity (off + cnt > cap), and every pixel when the scanned total did not
+// fit an int (n_active[3] > 0), is skipped here and in the shading pass; the
 // batch renders such pixels with the fused integrator.
 #pragma once
 
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   if (nact == 0) return;
+  const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
   const int npix = args.npix;
   const float tol = args.rk_tol, cc = args.c;
   float ds = args.ds;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
           q = -1;
           stage = 0;
           if constexpr (BATCH) {
-            if (kidx + __ldg(cnt + item) > cap) {
+            if (excess || kidx < 0 || kidx + __ldg(cnt + item) > cap) {
               pix = -1;                  // beyond the sample list: the fused integrator's
             } else {
               rq = batch_request(ba, pix);

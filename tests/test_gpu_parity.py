@@ -221,3 +221,13 @@ def test_render_to_host_and_errors(ivv):
     bad = scenes.Camera(False, sc.camera.eye, sc.camera.eye, sc.camera.up)
     with pytest.raises(ivv.IvvError):
         vol.render(bad, sc.params, 40, 30)
+    # windows beyond 2^27 pixels are refused before any allocation
+    import ctypes as C
+    L = ivv.load()
+    cam = ivv.camera_struct(sc.camera)
+    prm = ivv.params_struct(sc.params, 0, None)
+    need = C.c_size_t()
+    assert L.ivv_workspace_size(vol.h, 20000, 20000, 0, C.byref(need)) == 1
+    assert L.ivv_render(vol.h, C.byref(cam), C.byref(prm), 20000, 20000, C.c_void_p(dev.data_ptr()), None, 0,
+                        None) == 1
+    assert "2^27" in L.ivv_last_error().decode()
