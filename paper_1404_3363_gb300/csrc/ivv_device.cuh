@@ -18,10 +18,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "ivv_internal.h"
 #include "isect.cuh"
 
 namespace ivv {
+
+// Programmatic dependent launch: a kernel launched by launch_pdl may become
+// resident while its predecessor on the stream finishes (hiding the launch
+// gap between dependent kernels).  Every such kernel calls pdl_wait(), which
+// returns once the predecessor grid has completed and its writes are visible,
+// unconditionally and before it reads or writes any buffer another kernel of
+// the frame touches; so a grid completes only after all earlier ones did.
+// Launch errors land in cudaGetLastError as for <<<>>>.  pdl_wait() returns
+// at once in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 
 // ------------------------------------------------------------- parameters
 // 32-byte aligned four-double vector (x, y, z, w).

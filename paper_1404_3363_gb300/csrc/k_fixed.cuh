@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
     s_seg[i] = (unsigned char)k;
   }
   __syncthreads();
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   if (nact == 0) return;
@@ -222,8 +223,8 @@ void launch_fixed_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
 #define IVV_K5F(MM, SS) \
-  k5_fixed<P, float, MM, SS><<<grid, 128, 0, s>>>(V, cam, tf, a, T, pin, pout, pblk, pcnt, active, n_active, \
-                                                   queue_head, out, st)
+  launch_pdl(k5_fixed<P, float, MM, SS>, dim3(grid), dim3(128), s, V, cam, tf, a, T, pin, pout, pblk, pcnt, \
+             active, n_active, queue_head, out, st)
   if (mixed) { if (stats) IVV_K5F(true, true); else IVV_K5F(true, false); }
   else { if (stats) IVV_K5F(false, true); else IVV_K5F(false, false); }
 #undef IVV_K5F

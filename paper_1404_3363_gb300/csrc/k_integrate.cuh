@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
     }
     __syncthreads();
   }
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   if (nact == 0) return;
@@ -520,8 +521,8 @@ void launch_k5(const DevVolume& V, const DevCamera<R>& cam, const DevTF& tf, con
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
   BatchArgs none{};
-  k5_integrate<P, R, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, tf, a, none, pin, pout, pblk, pcnt, active,
-                                                         n_active, queue_head, out, st);
+  launch_pdl(k5_integrate<P, R, MIXED, STATS>, dim3(grid), dim3(128), s, V, cam, tf, a, none, pin, pout, pblk, pcnt,
+             active, n_active, queue_head, out, st);
 }
 
 // ---- split integration: sample shading
@@ -652,6 +653,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     }
     __syncthreads();
   }
+  pdl_wait();                                       // (the TF above is the volume's, not a predecessor's)
   const int nact = *n_active;
   const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
   unsigned long long c_samp = 0, c_rho = 0;
@@ -776,9 +778,9 @@ void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, c
   grid = grid < useful ? grid : (useful > 0 ? useful : 1);
   const bool cp = V.mode == IVV_SCALAR_CP;
 #define IVV_SHADE(SS, CC)                                                                                   \
-  k_shade_composite<P, SS, CC><<<grid, 128, 0, s>>>(V, cam, tf, K, early, BatchArgs{}, nullptr, pin, pout, pblk,  \
-                                                    pcnt, active, n_active, off, npix, ds, tail_eps, sa.cap, sa.sp, \
-                                                    out, st)
+  launch_pdl(k_shade_composite<P, SS, CC>, dim3(grid), dim3(128), s, V, cam, tf, K, early, BatchArgs{},              \
+             (const int*)nullptr, pin, pout, pblk, pcnt, active, n_active, off, npix, ds, tail_eps, sa.cap, sa.sp, out, \
+             st)
   if (stats) { if (cp) IVV_SHADE(true, true); else IVV_SHADE(true, false); }
   else { if (cp) IVV_SHADE(false, true); else IVV_SHADE(false, false); }
 #undef IVV_SHADE

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
     s_seg[i] = (unsigned char)k;
   }
   __syncthreads();
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   if (nact == 0) return;
@@ -419,7 +420,8 @@ void launch_irk1_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF&
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
 #define IVV_K5I(MM, SS) \
-  k5_irk1<P, MM, SS><<<grid, 128, 0, s>>>(V, cam, tf, a, pin, pout, pblk, pcnt, active, n_active, queue_head, out, st)
+  launch_pdl(k5_irk1<P, MM, SS>, dim3(grid), dim3(128), s, V, cam, tf, a, pin, pout, pblk, pcnt, active, n_active, \
+             queue_head, out, st)
   if (mixed) { if (stats) IVV_K5I(true, true); else IVV_K5I(true, false); }
   else { if (stats) IVV_K5I(false, true); else IVV_K5I(false, false); }
 #undef IVV_K5I

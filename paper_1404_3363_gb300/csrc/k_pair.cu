@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
                                                      const int* __restrict__ active,
                                                      const int* __restrict__ n_active, DevStats* __restrict__ st) {
   typedef typename Vec4T<R>::type V4;
+  pdl_wait();
   const int nact = *n_active;
   const R tol = sizeof(R) == 4 ? R(1e-6) * R(V.diag) : R(1e-12) * R(V.diag);
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
                                                float4* __restrict__ out_rgba, ClipArgs<R> clip,
                                                DevStats* __restrict__ st) {
+  pdl_wait();
   const int tiles_x = (w + 15) / 16;
   int x, y;
   tile_pixel(blockIdx.x % tiles_x, blockIdx.x / tiles_x, x, y);
@@ -337,9 +339,9 @@ void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
   if (w <= 0) return;
   const int h = npix / w;
-  k4_pair<R><<<((w + 15) / 16) * ((h + 15) / 16), 256, 0, s>>>(w, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out,
-                                                pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero,
-                                                clip, st);
+  launch_pdl(k4_pair<R>, dim3(((w + 15) / 16) * ((h + 15) / 16)), dim3(256), s, w, npix, tau, frag_tp, frag_meta,
+             frag_count, pair_in, pair_out, pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, clip,
+             st);
 }
 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
@@ -366,11 +368,11 @@ void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, ty
   const int useful = (npix + 127) / 128;
   grid = grid < useful ? grid : useful;
   if (V.P == 2)
-    k4_clip_solve<2, R><<<grid, 128, 0, s>>>(V, cam, npix, pair_in, pair_out, pair_block, pair_count, active,
-                                             n_active, st);
+    launch_pdl(k4_clip_solve<2, R>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block,
+               pair_count, active, n_active, st);
   else
-    k4_clip_solve<3, R><<<grid, 128, 0, s>>>(V, cam, npix, pair_in, pair_out, pair_block, pair_count, active,
-                                             n_active, st);
+    launch_pdl(k4_clip_solve<3, R>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block,
+               pair_count, active, n_active, st);
 }
 
 template void launch_clip_solve<float>(const DevVolume&, const DevCamera<float>&, int, float4*, float4*, int*,

@@ -53,6 +53,7 @@ __global__ void k_rf_count(const float4* __restrict__ pair_in, const float4* __r
                            const int* __restrict__ pair_block, const int* __restrict__ pair_count,
                            const int* __restrict__ active, const int* __restrict__ n_active, int npix, float ds,
                            float tail_eps, int* __restrict__ cnt) {
+  pdl_wait();
   const int nact = *n_active;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
     const int pix = active[item];
@@ -70,6 +71,7 @@ __global__ void k_rf_count(const float4* __restrict__ pair_in, const float4* __r
 __global__ void __launch_bounds__(kScanBlock) k_scan_local(const int* __restrict__ in, const int* __restrict__ n_ptr,
                                                            int* __restrict__ out, int* __restrict__ sums) {
   __shared__ int warp_tot[kScanBlock / 32];
+  pdl_wait();
   const int n = *n_ptr;
   const int i = blockIdx.x * kScanBlock + threadIdx.x;
   if (blockIdx.x * kScanBlock >= n) return;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* __restrict__ sums
                                                           int cap, int* __restrict__ total) {
   __shared__ int warp_tot[kScanBlock / 32];
   __shared__ long long carry;
+  pdl_wait();
   const int n = (*n_ptr + kScanBlock - 1) / kScanBlock;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* __restrict__ sums
 }
 
 __global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ n_ptr, const int* __restrict__ sums) {
+  pdl_wait();
   const int n = *n_ptr;
   const int i = blockIdx.x * kScanBlock + threadIdx.x;
   if (i < n) out[i] += sums[blockIdx.x];
@@ -158,6 +162,7 @@ __global__ void k_rf_expand(DevCamera<float> cam, const float4* __restrict__ pai
                             const int* __restrict__ n_active, const int* __restrict__ off, int npix, float ds,
                             float tail_eps, int guess, int cap, float4* __restrict__ sg, int* __restrict__ sblk,
                             float4* __restrict__ sp) {
+  pdl_wait();
   const int nact = *n_active;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
     const int pix = active[item];
@@ -197,6 +202,7 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
                                                    const int* __restrict__ sblk, const float4* __restrict__ sp,
                                                    float* __restrict__ srho, float4* __restrict__ p_out,
                                                    int* __restrict__ it_out, DevStats* __restrict__ st) {
+  pdl_wait();
   const int n = *n_ptr;
   unsigned long long c_it = 0, c_ev = 0, c_fail = 0;
   // half width of a pixel per unit depth (perspective) or absolute (ortho)
@@ -311,6 +317,7 @@ __global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __res
     s_seg[i] = (unsigned char)k;
   }
   __syncthreads();
+  pdl_wait();
   const int nact = *n_active;
   unsigned long long c_samp = 0;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
@@ -376,23 +383,24 @@ void launch_fill_center(float4* p, int n, cudaStream_t s) {
 
 void launch_rf_count(const float4* pin, const float4* pout, const int* pblk, const int* pcnt, const int* active,
                      const int* n_active, int npix, float ds, float tail_eps, int* cnt, int num_sms, cudaStream_t s) {
-  k_rf_count<<<num_sms * 8, 256, 0, s>>>(pin, pout, pblk, pcnt, active, n_active, npix, ds, tail_eps, cnt);
+  launch_pdl(k_rf_count, dim3(num_sms * 8), dim3(256), s, pin, pout, pblk, pcnt, active, n_active, npix, ds, tail_eps,
+             cnt);
 }
 
 void launch_rf_scan(const int* cnt, const int* n_active, int npix, int* off, int* sums, int cap, int* total,
                     cudaStream_t s) {
   const int blocks = (npix + kScanBlock - 1) / kScanBlock;
-  k_scan_local<<<blocks, kScanBlock, 0, s>>>(cnt, n_active, off, sums);
-  k_scan_sums<<<1, kScanBlock, 0, s>>>(sums, n_active, cap, total);
-  k_scan_add<<<blocks, kScanBlock, 0, s>>>(off, n_active, sums);
+  launch_pdl(k_scan_local, dim3(blocks), dim3(kScanBlock), s, cnt, n_active, off, sums);
+  launch_pdl(k_scan_sums, dim3(1), dim3(kScanBlock), s, sums, n_active, cap, total);
+  launch_pdl(k_scan_add, dim3(blocks), dim3(kScanBlock), s, off, n_active, (const int*)sums);
 }
 
 void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const float4* pout, const int* pblk,
                       const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                       float tail_eps, int guess, int cap, float4* sg, int* sblk, float4* sp, int num_sms,
                       cudaStream_t s) {
-  k_rf_expand<<<num_sms * 8, 256, 0, s>>>(cam, pin, pout, pblk, pcnt, active, n_active, off, npix, ds, tail_eps,
-                                          guess, cap, sg, sblk, sp);
+  launch_pdl(k_rf_expand, dim3(num_sms * 8), dim3(256), s, cam, pin, pout, pblk, pcnt, active, n_active, off, npix, ds,
+             tail_eps, guess, cap, sg, sblk, sp);
 }
 
 void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
@@ -400,7 +408,8 @@ void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_
                       DevStats* st, bool stats, int num_sms, cudaStream_t s) {
   const int grid = num_sms * 16;
 #define IVV_RFN(PP, SS) \
-  k_rf_newton<PP, SS><<<grid, 128, 0, s>>>(V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, p_out, it_out, st)
+  launch_pdl(k_rf_newton<PP, SS>, dim3(grid), dim3(128), s, V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, p_out, \
+             it_out, st)
   if (V.P == 2) {
     if (stats) IVV_RFN(2, true); else IVV_RFN(2, false);
   } else {
@@ -413,8 +422,8 @@ void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                          float tail_eps, int cap, const float* srho, float4* out, DevStats* st,
                          bool stats, int num_sms, cudaStream_t s) {
-  k_rf_composite<<<num_sms * 8, 128, 0, s>>>(tf, K, early, pin, pout, pblk, pcnt, active, n_active, off, npix, ds,
-                                             tail_eps, cap, srho, out, st, stats);
+  launch_pdl(k_rf_composite, dim3(num_sms * 8), dim3(128), s, tf, K, early, pin, pout, pblk, pcnt, active, n_active,
+             off, npix, ds, tail_eps, cap, srho, out, st, stats);
 }
 
 }  // namespace ivv

@@ -25,6 +25,7 @@ constexpr int kRootsThreads = 128;
 template <int P>
 __global__ void k0_face_project(DevVolume V, DevCamera<float> cam, int4* __restrict__ boxes,
                                 int4* __restrict__ gboxes) {
+  pdl_wait();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   project_faces<P>(V, cam, f, V.n_faces, 0, V.diag, boxes, gboxes);
 }
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(32 * kCullWarps) k2a_cull(DevVolume V, DevCame
                                                             const int4* __restrict__ gboxes, int2* __restrict__ items,
                                                             int cap, int* __restrict__ n_items,
                                                             int* __restrict__ frag_count, DevStats* __restrict__ st) {
+  pdl_wait();
   const int tiles_x = (cam.w + 7) / 8;
   const int tiles = tiles_x * ((cam.h + 3) / 4);
   const int t = blockIdx.x * kCullWarps + (threadIdx.x >> 5);
@@ -54,6 +56,7 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCa
                                                               unsigned* __restrict__ frag_meta,
                                                               int* __restrict__ frag_count,
                                                               DevStats* __restrict__ st) {
+  pdl_wait();
   const int n = min(n_items[0], cap);
   const size_t stride = (size_t)cam.w * cam.h;
   unsigned long long c_tests = 0, c_fp64 = 0, c_frag = 0;
@@ -90,6 +93,7 @@ __global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamer
                                                            int* __restrict__ frag_count, DevStats* __restrict__ st) {
   __shared__ SplitSmem<R> s_split[kRootsThreads / 32];
   SplitSmem<R>& sm = s_split[threadIdx.x >> 5];
+  pdl_wait();
   const int n = min(n_items[kSlowCounter - kItemCounter], cap);
   if (n > warp_max) return;
   const size_t stride = (size_t)cam.w * cam.h;
@@ -123,6 +127,7 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2c_thread(DevVolume V, DevC
                                                                unsigned* __restrict__ frag_meta,
                                                                int* __restrict__ frag_count,
                                                                DevStats* __restrict__ st) {
+  pdl_wait();
   const int n = min(n_items[kSlowCounter - kItemCounter], cap);
   if (n <= warp_max) return;
   const size_t stride = (size_t)cam.w * cam.h;
@@ -156,12 +161,14 @@ void launch_k2b(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<dou
     for (int& x : per_sm) x = x < 1 ? 1 : x;
   }
   const int warp_max = kSplitWaves * num_sms * per_sm[1] * (kRootsThreads / 32);
-  k2b_roots<P, R, MIXED, STATS><<<num_sms * per_sm[0], kRootsThreads, 0, s>>>(
-      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
-  k2c_split<P, R, MIXED, STATS><<<num_sms * per_sm[1], kRootsThreads, 0, s>>>(
-      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
-  k2c_thread<P, R, MIXED, STATS><<<num_sms * per_sm[2], kRootsThreads, 0, s>>>(
-      V, cam, cam64, w.items, w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
+  launch_pdl(k2b_roots<P, R, MIXED, STATS>, dim3(num_sms * per_sm[0]), dim3(kRootsThreads), s, V, cam, cam64,
+             w.items, w.slow, w.n_items, w.cap, (V4*)w.frag_tp, w.frag_meta, w.frag_count, st);
+  launch_pdl(k2c_split<P, R, MIXED, STATS>, dim3(num_sms * per_sm[1]), dim3(kRootsThreads), s, V, cam, cam64,
+             (const int2*)w.items, (const int*)w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta,
+             w.frag_count, st);
+  launch_pdl(k2c_thread<P, R, MIXED, STATS>, dim3(num_sms * per_sm[2]), dim3(kRootsThreads), s, V, cam, cam64,
+             (const int2*)w.items, (const int*)w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta,
+             w.frag_count, st);
 }
 
 }  // namespace
@@ -170,9 +177,9 @@ void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* 
                          cudaStream_t s) {
   if (V.n_faces <= 0) return;
   if (V.P == 2)
-    k0_face_project<2><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes, gboxes);
+    launch_pdl(k0_face_project<2>, dim3((V.n_faces + 127) / 128), dim3(128), s, V, cam, boxes, gboxes);
   else
-    k0_face_project<3><<<(V.n_faces + 127) / 128, 128, 0, s>>>(V, cam, boxes, gboxes);
+    launch_pdl(k0_face_project<3>, dim3((V.n_faces + 127) / 128), dim3(128), s, V, cam, boxes, gboxes);
 }
 
 template <typename R>
@@ -180,8 +187,8 @@ void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCame
                       bool stats, const SurfaceWs& w, DevStats* st, int num_sms, cudaStream_t s) {
   const int tiles = ((cam.w + 7) / 8) * ((cam.h + 3) / 4);
   if (tiles <= 0) return;
-  k2a_cull<R><<<(tiles + kCullWarps - 1) / kCullWarps, 32 * kCullWarps, 0, s>>>(
-      V, cam, w.boxes, w.gboxes, w.items, w.cap, w.n_items, w.frag_count, st);
+  launch_pdl(k2a_cull<R>, dim3((tiles + kCullWarps - 1) / kCullWarps), dim3(32 * kCullWarps), s, V, cam,
+             (const int4*)w.boxes, (const int4*)w.gboxes, w.items, w.cap, w.n_items, w.frag_count, st);
 #define IVV_K2B(PP, MM, SS) launch_k2b<PP, R, MM, SS>(V, cam, cam64, w, st, num_sms, s)
   if constexpr (sizeof(R) == 4) {
     if (V.P == 2) {

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
                                                    int* __restrict__ queue_head, const int* __restrict__ off,
                                                    float4* __restrict__ sp, int cap, DevStats* __restrict__ st) {
   const int lane = threadIdx.x & 31;
+  pdl_wait();
   const int nact = *n_active;
   if (nact == 0) return;
   const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
@@ -257,8 +258,8 @@ void launch_k5_trace(const DevVolume& V, const DevCamera<float>& cam, const Inte
   int grid = num_sms * blocks_per_sm;
   const int max_useful = (a.npix + 127) / 128;
   if (grid > max_useful) grid = max_useful > 0 ? max_useful : 1;
-  k5_trace<P, MIXED, STATS><<<grid, 128, 0, s>>>(V, cam, a, BatchArgs{}, nullptr, pin, pout, pblk, pcnt, active,
-                                                 n_active, queue_head, sa.off, sa.sp, sa.cap, st);
+  launch_pdl(k5_trace<P, MIXED, STATS>, dim3(grid), dim3(128), s, V, cam, a, BatchArgs{}, (const int*)nullptr, pin,
+             pout, pblk, pcnt, active, n_active, queue_head, sa.off, sa.sp, sa.cap, st);
 }
 
 template <int P>
