@@ -35,6 +35,40 @@ namespace ivv {
 // at once in a kernel launched the ordinary way.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The integrators' pixel queue (the active list, consumed through one
+// global counter): lanes that finished their pixel take new ones.  While
+// plenty of the queue remains a warp takes 32 consecutive items at a time and
+// refills its lanes from them, so a warp's lanes stay within one compact
+// screen tile and their rays visit the same elements (control points stay in
+// L1); within 64 items per warp of the end it takes exactly what its lanes
+// need, so no warp holds back work that idle warps could do.
+struct WarpQueue {
+  int next, end, bulk_until;   // warp-uniform: untaken items [next, end) of the warp's chunk
+  __device__ __forceinline__ explicit WarpQueue(int nact)
+      : next(0), end(0), bulk_until(nact - 64 * (int)(gridDim.x * (blockDim.x >> 5))) {}
+  // Every lane calls it with need = ballot(lane wants an item); returns the
+  // item of each asking lane (consecutive in lane order).
+  __device__ __forceinline__ int take(unsigned need, int lane, int* queue_head) {
+    const int nneed = __popc(need);
+    const int rank = __popc(need & ((1u << lane) - 1u));
+    const int avail = end - next;
+    if (avail >= nneed) {
+      const int item = next + rank;
+      next += nneed;
+      return item;
+    }
+    const int count = end < bulk_until ? 32 : nneed - avail;
+    int base = 0;
+    const int leader = __ffs(need) - 1;
+    if (lane == leader) base = atomicAdd(queue_head, count);
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const int item = rank < avail ? next + rank : base + (rank - avail);
+    next = base + (nneed - avail);
+    end = base + count;
+    return item;
+  }
+};
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
   cudaLaunchAttribute attr[1];

@@ -63,15 +63,12 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
   bool fresh = true;      // next stage-0 evaluation starts a pair
   Acc<R> acc;
 
+  WarpQueue wq(nact);
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
     if (need) {
-      int base = 0;
-      const int leader = __ffs(need) - 1;
-      if (lane == leader) base = atomicAdd(queue_head, __popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int item = wq.take(need, lane, queue_head);
       if (pix == -1) {
-        const int item = base + __popc(need & ((1u << lane) - 1u));
         if (item < nact) {
           pix = __ldg(active + item);
           const int xw = pix % cam.w, yw = pix / cam.w;

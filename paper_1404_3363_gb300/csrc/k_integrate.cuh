@@ -246,16 +246,13 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0, rho_end = 0, s0 = 0;
   Acc<R> acc;
 
+  WarpQueue wq(nact);
   for (;;) {
     // ---- refill lanes that finished their pixel
     const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
     if (need) {
-      int base = 0;
-      const int leader = __ffs(need) - 1;
-      if (lane == leader) base = atomicAdd(queue_head, __popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int item = wq.take(need, lane, queue_head);
       if (pix == -1) {
-        const int item = base + __popc(need & ((1u << lane) - 1u));
         if (item < nact) {
           pix = __ldg(active + item);
           if constexpr (BATCH) {

@@ -214,15 +214,12 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
   float h = 0.f, L = 0.f, rho_prev = 0.f;
   Acc<float> acc;
 
+  WarpQueue wq(nact);
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
     if (need) {
-      int base = 0;
-      const int leader = __ffs(need) - 1;
-      if (lane == leader) base = atomicAdd(queue_head, __popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int item = wq.take(need, lane, queue_head);
       if (pix == -1) {
-        const int item = base + __popc(need & ((1u << lane) - 1u));
         if (item < nact) {
           pix = __ldg(active + item);
           acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;

@@ -215,15 +215,15 @@ __device__ __forceinline__ bool roots_item(const DevVolume& V, const DevCamera<d
 
 // ---- K2c: subdivision search of one item by a whole warp, level by level.
 // The parameter boxes of patch_roots_split (isect.cuh) are visited in
-// breadth-first order, starting from a 4 x 4 grid of the patch (its first
-// four levels in one): at each level every lane takes boxes of the level,
+// breadth-first order, starting from an 8 x 8 grid of the patch (its first
+// six levels in one): at each level every lane takes boxes of the level,
 // drops those whose hull misses the origin, solves certified boxes by Newton
 // from their centre (a root outside the box splits it further), runs the
 // multi-start Newton on uncertified boxes at the deepest level and splits
 // the rest along the longer control polygon.  Roots are gathered in shared
 // memory and merged by lane 0 (duplicates within the merge distance).
 constexpr int kBfsCap = 128;         // boxes per level
-constexpr int kSplitGrid = 4;        // first level of the warp search: a grid of boxes (1: the whole patch)
+constexpr int kSplitGrid = 8;        // first level of the warp search: a grid of boxes (1: the whole patch)
 constexpr int kSplitWaves = 4;       // warp-per-item search while the items fit this many waves
 constexpr int kRootCap = 16;         // gathered roots before merging
 
@@ -269,10 +269,10 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
   // the uncertified patch is split into a kSplitGrid x kSplitGrid grid of
   // boxes at once (one level of the warp search instead of 2 log2 kSplitGrid)
   constexpr int G = kSplitGrid;
-  if (lane < G * G) {
-    const int ia = lane % G, ib = lane / G;
+  for (int k = lane; k < G * G; k += 32) {
+    const int ia = k % G, ib = k / G;
     const R w = R(1) / R(G);
-    sm.box[0][lane] = SplitBox<R>{R(ia) * w, R(ia + 1) * w, R(ib) * w, R(ib + 1) * w, G == 1 ? 0 : 2 * (31 - __clz(G))};
+    sm.box[0][k] = SplitBox<R>{R(ia) * w, R(ia + 1) * w, R(ib) * w, R(ib + 1) * w, G == 1 ? 0 : 2 * (31 - __clz(G))};
   }
   if (lane == 0) {
     sm.n[0] = G * G;

@@ -57,15 +57,12 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
   float d[3], g_in[3], p[3], k1[3], ka[3], kb[3];
   float s = 0.f, h = 0.f, hh = 0.f, L = 0.f;
 
+  WarpQueue wq(nact);
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
     if (need) {
-      int base = 0;
-      const int leader = __ffs(need) - 1;
-      if (lane == leader) base = atomicAdd(queue_head, __popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int item = wq.take(need, lane, queue_head);
       if (pix == -1) {
-        const int item = base + __popc(need & ((1u << lane) - 1u));
         if (item < nact) {
           pix = __ldg(active + item);
           kidx = __ldg(off + item);
