@@ -561,14 +561,14 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
         ivv::launch_integrate_split_p<2>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
                                          counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
         ivv::launch_shade_composite_p<2>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt,
-                                         act, counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out,
-                                         stats, v->d_stats, v->num_sms, s);
+                                         act, counters, counters + ivv::kShadeHead, off, (int)npix, (float)p.ds,
+                                         tail_eps, sa, (float4*)out, stats, v->d_stats, v->num_sms, s);
       } else {
         ivv::launch_integrate_split_p<3>(V, c32, a, sa, mixed, stats, pin, pout, pblk, pcnt, act, counters,
                                          counters + ivv::kQueueHeadOff, v->d_stats, v->num_sms, s);
         ivv::launch_shade_composite_p<3>(V, c32, tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt,
-                                         act, counters, off, (int)npix, (float)p.ds, tail_eps, sa, (float4*)out,
-                                         stats, v->d_stats, v->num_sms, s);
+                                         act, counters, counters + ivv::kShadeHead, off, (int)npix, (float)p.ds,
+                                         tail_eps, sa, (float4*)out, stats, v->d_stats, v->num_sms, s);
       }
     } else {
       ivv::DevCamera<float> cf = c32;

@@ -565,7 +565,8 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
 // Counters block of a render: [0] active pixels, [2] sample total, [3]
 // spare, [4] stage-1 items, [5] their hand-out head, [6] deferred items, [7]
 // their hand-out head, [8] and [9] the batch's overflow list and its queue
-// head; the integrator's queue head at kQueueHeadOff.
+// head, [10] the shading pass's queue head; the integrator's queue head at
+// kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
 constexpr int kItemCounter = 4;
 constexpr int kItemHead = 5;         // next stage-1 item to hand out (K2b)
@@ -573,6 +574,7 @@ constexpr int kSlowCounter = 6;      // items deferred to the subdivision search
 constexpr int kSlowHead = 7;         // next deferred item to hand out (K2c)
 constexpr int kOverflowCounter = 8;  // batch: pixels beyond the sample buffer
 constexpr int kOverflowHead = 9;     // batch: the fused integrator's queue head over them
+constexpr int kShadeHead = 10;       // the shading pass's queue head (split integration)
 constexpr int kCountersBytes = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg_float(unsigned int* addr, float v) {
@@ -734,8 +736,8 @@ void launch_integrate_split_p(const DevVolume& V, const DevCamera<float>& cam, c
 template <int P>
 void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, int K, float early,
                               const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
-                              const int* active, const int* n_active, const int* off, int npix, float ds,
-                              float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st, int num_sms,
-                              cudaStream_t s);
+                              const int* active, const int* n_active, int* queue_head, const int* off, int npix,
+                              float ds, float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st,
+                              int num_sms, cudaStream_t s);
 
 }  // namespace ivv

@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
         live = false;
       }
     }
+    if (!live) continue;                             // idle lanes issue no loads
     // ---- the evaluation point of this lane
     R x[3];
-    if (live && stage > 0) {
+    if (stage > 0) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         R sum = R(0);
@@ -124,14 +125,11 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
         const R v = p[r] + h * sum;
         x[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
       }
-    } else if (live) {
-      x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
     } else {
-      x[0] = x[1] = x[2] = R(0.5);
+      x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
     }
     R W[3], rho, phi[3];
     rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
-    if (!live) continue;
     if (STATS) ++c_rhs;
 #pragma unroll
     for (int m = 0; m < kRkStagesMax; ++m)

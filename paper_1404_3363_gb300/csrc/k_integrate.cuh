@@ -314,8 +314,9 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
         live = false;
       }
     }
+    if (!live) continue;                             // idle lanes issue no loads
     R x[3];
-    if (live) {
+    {
       if (stage == 0) {
         x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
       } else if (stage == 1) {
@@ -335,13 +336,10 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = x[r] < R(0) ? R(0) : (x[r] > R(1) ? R(1) : x[r]);
-    } else {
-      x[0] = x[1] = x[2] = R(0.5);
     }
-    // ---- the one right-hand side of this iteration (converged across lanes)
+    // ---- the one right-hand side of this iteration
     R W[3], rho, phi[3];
     rhs_eval<P, R, MIXED, true>(V, B, x, g_in, d, cc, BATCH ? B.mode : V.mode, W, rho, phi, c_fp64);
-    if (!live) continue;
     if (STATS) ++c_rhs;
     // ---- advance the lane's state
     bool sample = false;        // rho / phi belong to sample s_j
@@ -608,13 +606,19 @@ __device__ __forceinline__ float det_cofactor(const float J[3][3]) {
   return J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
 }
 
-// Shading and compositing of the split integration: one thread per active
-// pixel walks its sample list in front-to-back order (pairs in order, s_j =
-// j ds with the last interval partial), evaluates the scalar at each sample
-// point (control points, det J or Eq. 23) and composites every interval with
-// K sub-samples (Alg. 1), stopping at early_alpha.  Neighbouring lanes are
-// neighbouring pixels at the same sample index, so their control-point loads
-// hit the same elements.  With statistics also Delta P (Eq. 5) per sample.
+// Shading and compositing of the split integration: every active pixel's
+// sample list is walked front to back (pairs in order, s_j = j ds with the
+// last interval partial); the scalar is evaluated at each sample point
+// (control points, det J or Eq. 23) and every interval is composited with K
+// sub-samples (Alg. 1), stopping at early_alpha.  One sample per lane and
+// loop iteration over the flattened (pair, sample) sequence, so lanes whose
+// pixels cross pair boundaries at different samples stay converged; lanes
+// whose pixel is finished sit out (no loads) until the whole warp is idle,
+// and the warp then takes 32 consecutive queue items at once, from a chunk
+// of 128 shared by the block's warps while the queue is long: the pixels of
+// a block are neighbours that start together, so their control-point loads
+// hit the same elements in L1.  With statistics also Delta P (Eq. 5) per
+// sample.
 // CP: the volume's scalar is its control-point field (a separate instance, so
 // the det J / Eq. 23 instance keeps its own register allocation).
 // BATCH: pixels of every request of a batch; each takes its request's camera,
@@ -629,10 +633,10 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
                                                          const int* __restrict__ pair_block,
                                                          const int* __restrict__ pair_count,
                                                          const int* __restrict__ active,
-                                                         const int* __restrict__ n_active, const int* __restrict__ off,
-                                                         int npix, float ds, float tail_eps, int cap,
-                                                         const float4* __restrict__ sp, float4* __restrict__ out,
-                                                         DevStats* __restrict__ st) {
+                                                         const int* __restrict__ n_active, int* __restrict__ queue_head,
+                                                         const int* __restrict__ off, int npix, float ds,
+                                                         float tail_eps, int cap, const float4* __restrict__ sp,
+                                                         float4* __restrict__ out, DevStats* __restrict__ st) {
   __shared__ float s_r[BATCH ? 1 : 256];
   __shared__ float4 s_rgba[BATCH ? 1 : 256];
   __shared__ unsigned char s_seg[BATCH ? 1 : kTfTable];
@@ -651,103 +655,186 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     __syncthreads();
   }
   pdl_wait();                                       // (the TF above is the volume's, not a predecessor's)
+  const int lane = threadIdx.x & 31;
   const int nact = *n_active;
+  if (nact == 0) return;
+  // the block's chunk of 128 queue items (base << 32 | items handed out),
+  // handed to its warps 32 at a time while the queue is long
+  __shared__ unsigned long long s_chunk;
+  const int blk_until = nact - 2 * 128 * (int)gridDim.x;
+  if (threadIdx.x == 0)
+    s_chunk = blk_until > 0 ? ((unsigned long long)(unsigned)atomicAdd(queue_head, 128) << 32) : 128ull;
+  __syncthreads();
   const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
   unsigned long long c_samp = 0, c_rho = 0;
   float max_dp = 0.f;
-  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
-    const int pix = active[item];
-    const int np = pair_count[pix];
-    int k = off[item];
-    const float* tr = s_r;
-    const float4* trgba = s_rgba;
-    const unsigned char* tseg = s_seg;
-    DevTF t2 = tf;
-    DevCamera<float> cm = cam;
-    int loc = pix;          // the pixel's index in its image (and in dst)
-    float4* dst = out;
-    if constexpr (BATCH) {
-      if (excess || k < 0 || k + __ldg(cnt + item) > cap) continue;   // rendered by the fused integrator
-      const int rq = batch_request(ba, pix);
-      const DevRequest& rr = ba.req[rq];
-      const DevTFSlot& ts = ba.tf[rq];
-      tr = ts.r;
-      trgba = ts.rgba;
-      tseg = ts.seg;
-      t2.n = ts.n;
-      t2.sigma = ts.sigma;
-      t2.lo = ts.lo;
-      t2.inv_range = ts.inv_range;
-      ds = rr.ds;
-      tail_eps = 1e-12f * rr.diag;
-      loc = pix - __ldg(ba.pix0 + rq);
-      dst = rr.out;
-      if (STATS) cm = rr.cam;
-    }
-    Acc<float> acc;
-    acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;
-    bool done = false;
-    for (int q = 0; q < np && !done; ++q) {
-      const size_t slot = (size_t)q * npix + pix;
-      const float4 pi = pair_in[slot], po = pair_out[slot];
-      const float L = po.x - pi.x;
-      if (!(L > 0.f)) continue;
-      const BlockInfo B = V.blocks[pair_block[slot]];
-      const float fl = floorf(L / ds);
-      const int nsamp = (int)fl;
-      const int nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
-      float rho_prev = 0.f, s_prev = 0.f;
-      for (int j = 0; j <= nlast; ++j, ++k) {
-        if (k >= cap) {
-          done = true;
-          break;
-        }
-        const float4 r = sp[k];
-        const float p[3] = {r.x, r.y, r.z};
-        float rho;
-        const int mode = BATCH ? B.mode : V.mode;
-        if (!STATS && !BATCH && CP) {
-          rho = eval_rho_cp<P>(V, B, p);
-        } else {
-          float phi[3], J[3][3], rc;
-          if (mode == IVV_SCALAR_CP)
-            eval_block<P, float, true>(V, B, p, phi, J, rc);
-          else
-            eval_block<P, float, false, true>(V, B, p, phi, J, rc);
-          if (mode == IVV_SCALAR_CP) {
-            rho = rc;
+
+  // lane state: the pixel (-1: needs one, -2: queue drained), its pair q of
+  // np, the sample j of the pair (nlast: its last), k: the sample's index in
+  // the list
+  int pix = -1, q = 0, np = 0, j = 1, nsamp = 0, nlast = 0, k = 0;
+  float L = 0.f, rho_prev = 0.f, s_prev = 0.f;
+  Acc<float> acc;
+  acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;
+  BlockInfo B = V.blocks[0];
+  const float* tr = s_r;
+  const float4* trgba = s_rgba;
+  const unsigned char* tseg = s_seg;
+  DevTF t2 = tf;
+  DevCamera<float> cm = cam;
+  int loc = 0;            // the pixel's index in its image (and in dst)
+  float4* dst = out;
+
+  int wnext = 0, wend = 0;     // the warp's untaken items [wnext, wend)
+  unsigned drained = 0;        // lanes that found the queue empty (warp-uniform)
+  for (;;) {
+    // a warp refills only once all its lanes are idle: the new pixels are
+    // neighbours and start together, so their loads stay coherent
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {
+      if (drained == 0xffffffffu) break;
+      const unsigned need = ~drained;
+      const int nneed = __popc(need);
+      const int rank = __popc(need & ((1u << lane) - 1u));
+      const int avail = wend - wnext;
+      int item;
+      if (avail >= nneed) {
+        item = wnext + rank;
+        wnext += nneed;
+      } else {
+        int wb = 0;
+        const int leader = __ffs(need) - 1;
+        if (lane == leader) {
+          const unsigned long long old = atomicAdd(&s_chunk, 32ull);
+          const unsigned taken = (unsigned)old;
+          const int base = (int)(old >> 32);
+          if (taken < 128u) {
+            wb = base + (int)taken;
+          } else if (taken == 128u && base + 128 < blk_until) {
+            wb = atomicAdd(queue_head, 128);
+            atomicExch(&s_chunk, ((unsigned long long)(unsigned)wb << 32) | 32ull);
           } else {
-            const float det = det_cofactor(J);
-            if (mode == IVV_SCALAR_DETJ) {
-              rho = det;
+            wb = atomicAdd(queue_head, 32);
+          }
+        }
+        wb = __shfl_sync(0xffffffffu, wb, leader);
+        item = rank < avail ? wnext + rank : wb + (rank - avail);
+        wnext = wb + (nneed - avail);
+        wend = wb + 32;
+      }
+      if (pix == -1) {
+        if (item < nact) {
+          pix = __ldg(active + item);
+          k = __ldg(off + item);
+          np = __ldg(pair_count + pix);
+          q = -1;
+          j = 1;
+          nlast = 0;                                // no pair yet: take the first
+          acc.C[0] = acc.C[1] = acc.C[2] = acc.a = 0.f;
+          loc = pix;
+          if constexpr (BATCH) {
+            if (excess || k < 0 || k + __ldg(cnt + item) > cap) {
+              pix = -1;                             // rendered by the fused integrator
             } else {
-              float f = 0.f;
-#pragma unroll
-              for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) f += J[a][b] * J[a][b];
-              rho = det / sqrtf(f);
+              const int rq = batch_request(ba, pix);
+              const DevRequest& rr = ba.req[rq];
+              const DevTFSlot& ts = ba.tf[rq];
+              tr = ts.r;
+              trgba = ts.rgba;
+              tseg = ts.seg;
+              t2.n = ts.n;
+              t2.sigma = ts.sigma;
+              t2.lo = ts.lo;
+              t2.inv_range = ts.inv_range;
+              ds = rr.ds;
+              tail_eps = 1e-12f * rr.diag;
+              loc = pix - __ldg(ba.pix0 + rq);
+              dst = rr.out;
+              if (STATS) cm = rr.cam;
             }
           }
-          if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cm, phi, loc % cm.w, loc / cm.w));
+        } else {
+          pix = -2;
         }
-        const float s = j <= nsamp ? (float)j * ds : L;
-        if (STATS) {
-          ++c_samp;
-          ++c_rho;
+      }
+      drained |= __ballot_sync(0xffffffffu, pix == -2);
+    }
+
+    bool live = pix >= 0;
+    if (live && j > nlast) {
+      // the next pair with a positive length, or the end of the pixel
+      bool found = false;
+      while (!found && ++q < np) {
+        const size_t slot = (size_t)q * npix + pix;
+        const float4 pi = pair_in[slot], po = pair_out[slot];
+        L = po.x - pi.x;
+        if (!(L > 0.f)) continue;
+        B = V.blocks[__ldg(pair_block + slot)];
+        const float fl = floorf(L / ds);
+        nsamp = (int)fl;
+        nlast = nsamp + ((L - fl * ds > tail_eps) ? 1 : 0);
+        j = 0;
+        rho_prev = 0.f;
+        s_prev = 0.f;
+        found = true;
+      }
+      if (!found) live = false;
+    }
+    if (live && k >= cap) live = false;              // beyond the sample list: the pixel ends here
+    if (pix >= 0 && !live) {
+      dst[loc] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
+      pix = -1;
+    }
+    if (!live) continue;                             // idle lanes issue no loads
+    // ---- the scalar at this lane's sample
+    float p[3];
+    {
+      const float4 r = sp[k];
+      p[0] = r.x; p[1] = r.y; p[2] = r.z;
+    }
+    float rho;
+    const int mode = BATCH ? B.mode : V.mode;
+    if (!STATS && !BATCH && CP) {
+      rho = eval_rho_cp<P>(V, B, p);
+    } else {
+      float phi[3], J[3][3], rc;
+      if (mode == IVV_SCALAR_CP)
+        eval_block<P, float, true>(V, B, p, phi, J, rc);
+      else
+        eval_block<P, float, false, true>(V, B, p, phi, J, rc);
+      if (mode == IVV_SCALAR_CP) {
+        rho = rc;
+      } else {
+        const float det = det_cofactor(J);
+        if (mode == IVV_SCALAR_DETJ) {
+          rho = det;
+        } else {
+          float f = 0.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) f += J[a][b] * J[a][b];
+          rho = det / sqrtf(f);
         }
-        if (j > 0) {
-          composite_interval<float>(tr, trgba, tseg, t2, K, rho_prev, rho, s - s_prev, acc);
-          if (acc.a >= early) {
-            done = true;
-            break;
-          }
-        }
-        rho_prev = rho;
-        s_prev = s;
+      }
+      if (STATS) max_dp = fmaxf(max_dp, pixel_error<float>(cm, phi, loc % cm.w, loc / cm.w));
+    }
+    const float s = j <= nsamp ? (float)j * ds : L;
+    if (STATS) {
+      ++c_samp;
+      ++c_rho;
+    }
+    if (j > 0) {
+      composite_interval<float>(tr, trgba, tseg, t2, K, rho_prev, rho, s - s_prev, acc);
+      if (acc.a >= early) {
+        dst[loc] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
+        pix = -1;
+        continue;
       }
     }
-    dst[loc] = make_float4(acc.C[0], acc.C[1], acc.C[2], acc.a);
+    rho_prev = rho;
+    s_prev = s;
+    ++j;
+    ++k;
   }
   if (STATS) {
 #pragma unroll
@@ -756,7 +843,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
       c_rho += __shfl_down_sync(0xffffffffu, c_rho, o2);
       max_dp = fmaxf(max_dp, __shfl_down_sync(0xffffffffu, max_dp, o2));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       atomicAdd(&st->samples, c_samp);
       atomicAdd(&st->rho_evals, c_rho);
       atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
@@ -767,17 +854,27 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
 template <int P>
 void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, const DevTF& tf, int K, float early,
                               const float4* pin, const float4* pout, const int* pblk, const int* pcnt,
-                              const int* active, const int* n_active, const int* off, int npix, float ds,
-                              float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st, int num_sms,
-                              cudaStream_t s) {
-  int grid = num_sms * 8;
+                              const int* active, const int* n_active, int* queue_head, const int* off, int npix,
+                              float ds, float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st,
+                              int num_sms, cudaStream_t s) {
+  static int per_sm[4] = {-1, -1, -1, -1};
+  const bool cp = V.mode == IVV_SCALAR_CP;
+  const int v = (stats ? 2 : 0) + (cp ? 1 : 0);
+  if (per_sm[v] < 0) {
+    int n = 1;
+    if (v == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, false, false>, 128, 0);
+    if (v == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, false, true>, 128, 0);
+    if (v == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, true, false>, 128, 0);
+    if (v == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, true, true>, 128, 0);
+    per_sm[v] = n < 1 ? 1 : n;
+  }
+  int grid = num_sms * per_sm[v];                   // persistent: the lanes refill from the queue
   const int useful = (npix + 127) / 128;
   grid = grid < useful ? grid : (useful > 0 ? useful : 1);
-  const bool cp = V.mode == IVV_SCALAR_CP;
 #define IVV_SHADE(SS, CC)                                                                                   \
   launch_pdl(k_shade_composite<P, SS, CC>, dim3(grid), dim3(128), s, V, cam, tf, K, early, BatchArgs{},              \
-             (const int*)nullptr, pin, pout, pblk, pcnt, active, n_active, off, npix, ds, tail_eps, sa.cap, sa.sp, out, \
-             st)
+             (const int*)nullptr, pin, pout, pblk, pcnt, active, n_active, queue_head, off, npix, ds, tail_eps, sa.cap, \
+             sa.sp, out, st)
   if (stats) { if (cp) IVV_SHADE(true, true); else IVV_SHADE(true, false); }
   else { if (cp) IVV_SHADE(false, true); else IVV_SHADE(false, false); }
 #undef IVV_SHADE

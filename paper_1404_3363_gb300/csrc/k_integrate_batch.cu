@@ -70,13 +70,21 @@ void launch_kb5t(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a
 template <int P, bool STATS>
 void launch_kbshade(const DevVolume& V, const BatchArgs& ba, const IntegrateArgs& a, const float4* pin,
                     const float4* pout, const int* pblk, const int* pcnt, const int* active, const int* n_active,
-                    const int* off, const int* cnt, const float4* sp, int cap, DevStats* st, int grid,
-                    cudaStream_t s) {
+                    int* queue_head, const int* off, const int* cnt, const float4* sp, int cap, DevStats* st,
+                    int num_sms, cudaStream_t s) {
   DevCamera<float> cam{};
   DevTF tf{};
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shade_composite<P, STATS, false, true>, 128, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  int grid = num_sms * per_sm;                      // persistent: the lanes refill from the queue
+  const int useful = (a.npix + 127) / 128;
+  grid = grid < useful ? grid : (useful > 0 ? useful : 1);
   k_shade_composite<P, STATS, false, true><<<grid, 128, 0, s>>>(V, cam, tf, a.K, a.early_alpha, ba, cnt, pin, pout,
-                                                                 pblk, pcnt, active, n_active, off, a.npix, 0.f, 0.f,
-                                                                 cap, sp, nullptr, st);
+                                                                 pblk, pcnt, active, n_active, queue_head, off,
+                                                                 a.npix, 0.f, 0.f, cap, sp, nullptr, st);
 }
 
 template <int P, bool MIXED, bool STATS>
@@ -120,12 +128,11 @@ void launch_batch_split(const DevVolume& V, const BatchArgs& ba, const Integrate
   launch_rf_scan(cnt, counters, npix, off, sums, 0x7fffffff, counters + 2, s);
   int* qhead = counters + kQueueHeadOff;
   int* n_list = counters + kOverflowCounter;
-  int sgrid = num_sms * 8;
-  sgrid = sgrid < (npix + 127) / 128 ? sgrid : ((npix + 127) / 128 > 0 ? (npix + 127) / 128 : 1);
 #define IVV_KB5T(PP, MM, SS) \
   launch_kb5t<PP, MM, SS>(V, ba, a, pin, pout, pblk, pcnt, active, counters, qhead, off, cnt, sp, cap, st, grid, s)
 #define IVV_KBS(PP, SS) \
-  launch_kbshade<PP, SS>(V, ba, a, pin, pout, pblk, pcnt, active, counters, off, cnt, sp, cap, st, sgrid, s)
+  launch_kbshade<PP, SS>(V, ba, a, pin, pout, pblk, pcnt, active, counters, counters + kShadeHead, off, cnt, sp, cap, \
+                         st, num_sms, s)
   if (V.P == 2) {
     if (mixed) { if (stats) IVV_KB5T(2, true, true); else IVV_KB5T(2, true, false); }
     else { if (stats) IVV_KB5T(2, false, true); else IVV_KB5T(2, false, false); }

@@ -13,6 +13,6 @@ template void launch_integrate_split_p<2>(const DevVolume&, const DevCamera<floa
                                            const int*, const int*, const int*, int*, DevStats*, int, cudaStream_t);
 template void launch_shade_composite_p<2>(const DevVolume&, const DevCamera<float>&, const DevTF&, int, float,
                                            const float4*, const float4*, const int*, const int*, const int*,
-                                           const int*, const int*, int, float, float, const SplitArgs&, float4*, bool,
+                                           const int*, int*, const int*, int, float, float, const SplitArgs&, float4*, bool,
                                            DevStats*, int, cudaStream_t);
 }  // namespace ivv

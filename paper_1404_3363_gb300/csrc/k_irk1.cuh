@@ -263,13 +263,13 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
         live = false;
       }
     }
+    if (!live) continue;                             // idle lanes issue no loads
     // ---- this iteration's evaluation point x = p + z (may leave the box)
     float x[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) x[r] = live ? p[r] + z[r] : 0.5f;
+    for (int r = 0; r < 3; ++r) x[r] = p[r] + z[r];
     float phi[3], J[3][3], H[3][3][3], rc;
     eval_block_h<P>(V, B, x, phi, J, H, rc);
-    if (!live) continue;
     if (STATS) ++c_eval;
     if (it == 0) {
       // x is the sample point p_j: its scalar, and the interval ending there

@@ -125,24 +125,22 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
         live = false;
       }
     }
+    // idle lanes (pixel done, queue drained) sit out the evaluation: they
+    // would only add control-point loads of their own to the warp's
+    if (!live) continue;
     // ---- this iteration's evaluation point
     float x[3];
-    if (live) {
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        float v;
-        if (stage == 0) v = p[r];
-        else if (stage == 1) v = bs3_q2<float>(p[r], hh, k1[r]);
-        else if (stage == 2) v = bs3_q3<float>(p[r], hh, ka[r]);
-        else v = ka[r];                                   // pn
-        x[r] = v < 0.f ? 0.f : (v > 1.f ? 1.f : v);
-      }
-    } else {
-      x[0] = x[1] = x[2] = 0.5f;
+    for (int r = 0; r < 3; ++r) {
+      float v;
+      if (stage == 0) v = p[r];
+      else if (stage == 1) v = bs3_q2<float>(p[r], hh, k1[r]);
+      else if (stage == 2) v = bs3_q3<float>(p[r], hh, ka[r]);
+      else v = ka[r];                                   // pn
+      x[r] = v < 0.f ? 0.f : (v > 1.f ? 1.f : v);
     }
     float W[3], rho, phi[3];
     rhs_eval<P, float, MIXED, false>(V, B, x, g_in, d, cc, V.mode, W, rho, phi, c_fp64);
-    if (!live) continue;
     if (STATS) ++c_rhs;
     if (stage == 0) {
       k1[0] = W[0]; k1[1] = W[1]; k1[2] = W[2];
