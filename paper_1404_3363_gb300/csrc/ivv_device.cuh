@@ -36,36 +36,56 @@ namespace ivv {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // The integrators' pixel queue (the active list, consumed through one
-// global counter): lanes that finished their pixel take new ones.  While
-// plenty of the queue remains a warp takes 32 consecutive items at a time and
-// refills its lanes from them, so a warp's lanes stay within one compact
-// screen tile and their rays visit the same elements (control points stay in
-// L1); within 64 items per warp of the end it takes exactly what its lanes
-// need, so no warp holds back work that idle warps could do.
+// global counter).  A warp takes new pixels only once all its lanes are
+// idle, one consecutive item per lane: its lanes then trace neighbouring
+// pixels that start together, so their rays run through the same elements
+// and their control-point loads coalesce (a lane whose pixel ends early sits
+// out, issuing no loads, until its warp refills).  With a block chunk in
+// shared memory, a warp's 32 items are cut from 128 consecutive items that
+// the block's warps share while the queue is long, so the pixels in flight
+// on a block are neighbours too.
 struct WarpQueue {
-  int next, end, bulk_until;   // warp-uniform: untaken items [next, end) of the warp's chunk
-  __device__ __forceinline__ explicit WarpQueue(int nact)
-      : next(0), end(0), bulk_until(nact - 64 * (int)(gridDim.x * (blockDim.x >> 5))) {}
-  // Every lane calls it with need = ballot(lane wants an item); returns the
-  // item of each asking lane (consecutive in lane order).
-  __device__ __forceinline__ int take(unsigned need, int lane, int* queue_head) {
+  unsigned drained;             // lanes that found the queue empty (warp-uniform)
+  int blk_until;                // block chunks while their base is below this
+  unsigned long long* chunk;    // the block's chunk (base << 32 | items handed out), or null
+  // With a block chunk every thread of the block constructs it (it
+  // synchronises the block).
+  __device__ __forceinline__ WarpQueue(int nact, int* queue_head, unsigned long long* s_chunk)
+      : drained(0u), blk_until(nact - 2 * 128 * (int)gridDim.x), chunk(s_chunk) {
+    if (chunk != nullptr) {
+      if (threadIdx.x == 0)
+        *chunk = blk_until > 0 ? ((unsigned long long)(unsigned)atomicAdd(queue_head, 128) << 32) : 128ull;
+      __syncthreads();
+    }
+  }
+  __device__ __forceinline__ bool done() const { return drained == 0xffffffffu; }
+  // Every lane of an idle warp calls it; returns the item of each lane that
+  // is not drained (the caller marks lanes whose item is past the end).
+  __device__ __forceinline__ int take(int lane, int* queue_head) {
+    const unsigned need = ~drained;
     const int nneed = __popc(need);
     const int rank = __popc(need & ((1u << lane) - 1u));
-    const int avail = end - next;
-    if (avail >= nneed) {
-      const int item = next + rank;
-      next += nneed;
-      return item;
-    }
-    const int count = end < bulk_until ? 32 : nneed - avail;
     int base = 0;
     const int leader = __ffs(need) - 1;
-    if (lane == leader) base = atomicAdd(queue_head, count);
+    if (lane == leader) {
+      if (chunk != nullptr && nneed == 32) {
+        const unsigned long long old = atomicAdd(chunk, 32ull);
+        const unsigned taken = (unsigned)old;
+        const int cb = (int)(old >> 32);
+        if (taken < 128u) {
+          base = cb + (int)taken;
+        } else if (taken == 128u && cb + 128 < blk_until) {
+          base = atomicAdd(queue_head, 128);                // a fresh chunk; its first 32 are ours
+          atomicExch(chunk, ((unsigned long long)(unsigned)base << 32) | 32ull);
+        } else {
+          base = atomicAdd(queue_head, 32);
+        }
+      } else {
+        base = atomicAdd(queue_head, nneed);
+      }
+    }
     base = __shfl_sync(0xffffffffu, base, leader);
-    const int item = rank < avail ? next + rank : base + (rank - avail);
-    next = base + (nneed - avail);
-    end = base + count;
-    return item;
+    return base + rank;
   }
 };
 

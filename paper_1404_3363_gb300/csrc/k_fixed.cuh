@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
   bool fresh = true;      // next stage-0 evaluation starts a pair
   Acc<R> acc;
 
-  WarpQueue wq(nact);
+  WarpQueue wq(nact, queue_head, nullptr);
   for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
-    if (need) {
-      const int item = wq.take(need, lane, queue_head);
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {     // the whole warp is idle: refill
+      if (wq.done()) break;
+      const int item = wq.take(lane, queue_head);
       if (pix == -1) {
         if (item < nact) {
           pix = __ldg(active + item);
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(128, 4) k5_fixed(DevVolume V, DevCamera<R> cam
           pix = -2;
         }
       }
+      wq.drained |= __ballot_sync(0xffffffffu, pix == -2);
     }
-    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) break;
 
     bool live = pix >= 0;
     if (live && fresh) {

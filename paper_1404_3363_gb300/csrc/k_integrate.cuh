@@ -246,12 +246,11 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
   R s = 0, s_last = 0, h = 0, hh = 0, L = 0, rho_prev = 0, rho_end = 0, s0 = 0;
   Acc<R> acc;
 
-  WarpQueue wq(nact);
+  WarpQueue wq(nact, queue_head, nullptr);
   for (;;) {
-    // ---- refill lanes that finished their pixel
-    const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
-    if (need) {
-      const int item = wq.take(need, lane, queue_head);
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {     // the whole warp is idle: refill
+      if (wq.done()) break;
+      const int item = wq.take(lane, queue_head);
       if (pix == -1) {
         if (item < nact) {
           pix = __ldg(active + item);
@@ -277,8 +276,8 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
           pix = -2;                    // the queue is drained
         }
       }
+      wq.drained |= __ballot_sync(0xffffffffu, pix == -2);
     }
-    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) break;
 
     // ---- choose this lane's evaluation point
     bool live = pix >= 0;
@@ -658,13 +657,8 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
   const int lane = threadIdx.x & 31;
   const int nact = *n_active;
   if (nact == 0) return;
-  // the block's chunk of 128 queue items (base << 32 | items handed out),
-  // handed to its warps 32 at a time while the queue is long
   __shared__ unsigned long long s_chunk;
-  const int blk_until = nact - 2 * 128 * (int)gridDim.x;
-  if (threadIdx.x == 0)
-    s_chunk = blk_until > 0 ? ((unsigned long long)(unsigned)atomicAdd(queue_head, 128) << 32) : 128ull;
-  __syncthreads();
+  WarpQueue wq(nact, queue_head, &s_chunk);
   const bool excess = BATCH && n_active[3] > 0;     // the sample offsets overflowed
   unsigned long long c_samp = 0, c_rho = 0;
   float max_dp = 0.f;
@@ -685,42 +679,10 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
   int loc = 0;            // the pixel's index in its image (and in dst)
   float4* dst = out;
 
-  int wnext = 0, wend = 0;     // the warp's untaken items [wnext, wend)
-  unsigned drained = 0;        // lanes that found the queue empty (warp-uniform)
   for (;;) {
-    // a warp refills only once all its lanes are idle: the new pixels are
-    // neighbours and start together, so their loads stay coherent
-    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {
-      if (drained == 0xffffffffu) break;
-      const unsigned need = ~drained;
-      const int nneed = __popc(need);
-      const int rank = __popc(need & ((1u << lane) - 1u));
-      const int avail = wend - wnext;
-      int item;
-      if (avail >= nneed) {
-        item = wnext + rank;
-        wnext += nneed;
-      } else {
-        int wb = 0;
-        const int leader = __ffs(need) - 1;
-        if (lane == leader) {
-          const unsigned long long old = atomicAdd(&s_chunk, 32ull);
-          const unsigned taken = (unsigned)old;
-          const int base = (int)(old >> 32);
-          if (taken < 128u) {
-            wb = base + (int)taken;
-          } else if (taken == 128u && base + 128 < blk_until) {
-            wb = atomicAdd(queue_head, 128);
-            atomicExch(&s_chunk, ((unsigned long long)(unsigned)wb << 32) | 32ull);
-          } else {
-            wb = atomicAdd(queue_head, 32);
-          }
-        }
-        wb = __shfl_sync(0xffffffffu, wb, leader);
-        item = rank < avail ? wnext + rank : wb + (rank - avail);
-        wnext = wb + (nneed - avail);
-        wend = wb + 32;
-      }
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {     // the whole warp is idle: refill
+      if (wq.done()) break;
+      const int item = wq.take(lane, queue_head);
       if (pix == -1) {
         if (item < nact) {
           pix = __ldg(active + item);
@@ -756,7 +718,7 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
           pix = -2;
         }
       }
-      drained |= __ballot_sync(0xffffffffu, pix == -2);
+      wq.drained |= __ballot_sync(0xffffffffu, pix == -2);
     }
 
     bool live = pix >= 0;

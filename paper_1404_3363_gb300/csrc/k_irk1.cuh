@@ -214,11 +214,11 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
   float h = 0.f, L = 0.f, rho_prev = 0.f;
   Acc<float> acc;
 
-  WarpQueue wq(nact);
+  WarpQueue wq(nact, queue_head, nullptr);
   for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
-    if (need) {
-      const int item = wq.take(need, lane, queue_head);
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {     // the whole warp is idle: refill
+      if (wq.done()) break;
+      const int item = wq.take(lane, queue_head);
       if (pix == -1) {
         if (item < nact) {
           pix = __ldg(active + item);
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
           pix = -2;
         }
       }
+      wq.drained |= __ballot_sync(0xffffffffu, pix == -2);
     }
-    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) break;
 
     bool live = pix >= 0;
     if (live && fresh) {

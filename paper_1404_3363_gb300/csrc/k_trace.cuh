@@ -57,11 +57,11 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
   float d[3], g_in[3], p[3], k1[3], ka[3], kb[3];
   float s = 0.f, h = 0.f, hh = 0.f, L = 0.f;
 
-  WarpQueue wq(nact);
+  WarpQueue wq(nact, queue_head, nullptr);
   for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, pix == -1);
-    if (need) {
-      const int item = wq.take(need, lane, queue_head);
+    if (__ballot_sync(0xffffffffu, pix >= 0) == 0) {     // the whole warp is idle: refill
+      if (wq.done()) break;
+      const int item = wq.take(lane, queue_head);
       if (pix == -1) {
         if (item < nact) {
           pix = __ldg(active + item);
@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
           pix = -2;
         }
       }
+      wq.drained |= __ballot_sync(0xffffffffu, pix == -2);
     }
-    if (__ballot_sync(0xffffffffu, pix != -2) == 0) break;   // every lane found the queue drained
 
     bool live = pix >= 0;
     if (live && stage == 0) {
