@@ -236,17 +236,33 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
   }
 }
 
-// Warp-aggregated append of the active pixels to the integrator's queue and
-// the counters that every render keeps.
+// Block-aggregated append of the active pixels to the integrator's queue
+// (every thread of the 256-thread block of one 16 x 16 tile calls it): the
+// tile's active pixels land contiguously, warp tile after warp tile, so the
+// 32 consecutive queue items an integrator warp takes are neighbours even
+// where the tile is only partly covered.  Also the counters that every
+// render keeps.
 __device__ __forceinline__ void pair_epilogue(int pix, int np, unsigned um, unsigned pov, int* __restrict__ active,
                                               int* __restrict__ n_active, DevStats* __restrict__ st) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int s_warp[8];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = np > 0;
   const unsigned bal = __ballot_sync(0xffffffffu, act);
-  int base = 0;
-  if (lane == 0 && bal) base = atomicAdd(n_active, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (act) active[base + __popc(bal & ((1u << lane) - 1u))] = pix;
+  if (lane == 0) s_warp[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = s_warp[k];
+      s_warp[k] = tot;
+      tot += c;
+    }
+    s_base = tot > 0 ? atomicAdd(n_active, tot) : 0;
+  }
+  __syncthreads();
+  if (act) active[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = pix;
   unsigned long long cu = um, cp = pov, cr = act ? 1 : 0, cpairs = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
