@@ -49,7 +49,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
   size_t boxes, gboxes, items, slow, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
-      counters, total;
+      tile_flag, counters, total;
 };
 
 WsLayout layout(int n_faces, size_t npix, size_t v4) {
@@ -68,6 +68,8 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
   L.pair_block = take(sizeof(int) * ivv::kMaxPairs * npix);
   L.pair_count = take(sizeof(int) * npix);
   L.active = take(sizeof(int) * npix);
+  // one flag per 16 x 16 tile: ceil(w/16) ceil(h/16) <= npix/256 + (w+h)/16 + 1 <= npix/8 + 3
+  L.tile_flag = take(sizeof(int) * (npix / 8 + 64));
   L.counters = take(ivv::kCountersBytes);
   L.total = o;
   return L;
@@ -333,6 +335,9 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   sw.frag_tp = ws + L.frag_tp;
   sw.frag_meta = (unsigned*)(ws + L.frag_meta);
   sw.frag_count = (int*)(ws + L.frag_count);
+  sw.tile_flag = (int*)(ws + L.tile_flag);
+  sw.pair_count = (int*)(ws + L.pair_count);
+  sw.zero_out = out_zero;
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[0], s));
   ivv::launch_face_project(V, dev_camera<float>(F), sw.boxes, sw.gboxes, s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[1], s));
@@ -350,7 +355,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   ivv::launch_pair<R>(V, F.w, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                       (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
-                      (int*)(ws + L.counters), out_zero, clip, v->d_stats, s);
+                      (int*)(ws + L.counters), out_zero, clip, sw.tile_flag, v->d_stats, s);
   if (clip.on)
     ivv::launch_clip_solve<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                               (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),

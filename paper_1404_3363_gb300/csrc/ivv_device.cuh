@@ -620,6 +620,13 @@ struct SurfaceWs {
   void* frag_tp;
   unsigned* frag_meta;
   int* frag_count;
+  // single frames: a flag per 16 x 16 tile, set where a warp tile has
+  // candidate patches (K4 processes flagged tiles only and clears their
+  // flags); the warp tiles without candidates get pair_count 0 and, if
+  // zero_out is set, a zero pixel from the cull.  Null: no tile skipping.
+  int* tile_flag = nullptr;
+  int* pair_count = nullptr;
+  float4* zero_out = nullptr;
 };
 
 void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* boxes, int4* gboxes, cudaStream_t s);
@@ -653,8 +660,8 @@ template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs,
-                 int* active, int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, DevStats* st,
-                 cudaStream_t s);
+                 int* active, int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, int* tile_flag,
+                 DevStats* st, cudaStream_t s);
 
 struct IntegrateArgs {
   float rk_tol, ds, c, early_alpha;

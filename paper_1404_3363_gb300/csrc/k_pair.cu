@@ -298,8 +298,11 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
                                                float4* __restrict__ out_rgba, ClipArgs<R> clip,
-                                               DevStats* __restrict__ st) {
+                                               int* __restrict__ tile_flag, DevStats* __restrict__ st) {
   pdl_wait();
+  // a tile none of whose warp tiles had a candidate patch was finished by
+  // the cull (pair counts and zero pixels): nothing to do
+  if (tile_flag != nullptr && tile_flag[blockIdx.x] == 0) return;
   const int tiles_x = (w + 15) / 16;
   int x, y;
   tile_pixel(blockIdx.x % tiles_x, blockIdx.x / tiles_x, x, y);
@@ -315,6 +318,9 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                          pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
   }
   pair_epilogue(pix, np, um, pov, active, n_active, st);
+  // every thread read the flag before the epilogue's barriers: clear it for
+  // the next frame
+  if (tile_flag != nullptr && threadIdx.x == 0) tile_flag[blockIdx.x] = 0;
 }
 
 // Batched form: pixel `pix` of the batch's pixel space belongs to request
@@ -349,7 +355,8 @@ template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
-                 int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, DevStats* st, cudaStream_t s) {
+                 int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, int* tile_flag, DevStats* st,
+                 cudaStream_t s) {
   (void)V;
   if (npix <= 0) return;
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
@@ -357,7 +364,7 @@ void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename
   const int h = npix / w;
   launch_pdl(k4_pair<R>, dim3(((w + 15) / 16) * ((h + 15) / 16)), dim3(256), s, w, npix, tau, frag_tp, frag_meta,
              frag_count, pair_in, pair_out, pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, clip,
-             st);
+             tile_flag, st);
 }
 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
@@ -370,10 +377,10 @@ void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4*
 
 template void launch_pair<float>(const DevVolume&, int, int, float, const float4*, const unsigned*, const int*,
                                  float4*, float4*, int*, int*, int, int*, int*, float4*, const ClipArgs<float>&,
-                                 DevStats*, cudaStream_t);
+                                 int*, DevStats*, cudaStream_t);
 template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*, const unsigned*, const int*, Dbl4*,
-                                  Dbl4*, int*, int*, int, int*, int*, float4*, const ClipArgs<double>&, DevStats*,
-                                  cudaStream_t);
+                                  Dbl4*, int*, int*, int, int*, int*, float4*, const ClipArgs<double>&, int*,
+                                  DevStats*, cudaStream_t);
 
 template <typename R>
 void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,

@@ -35,14 +35,31 @@ __global__ void __launch_bounds__(32 * kCullWarps) k2a_cull(DevVolume V, DevCame
                                                             const int4* __restrict__ boxes,
                                                             const int4* __restrict__ gboxes, int2* __restrict__ items,
                                                             int cap, int* __restrict__ n_items,
-                                                            int* __restrict__ frag_count, DevStats* __restrict__ st) {
+                                                            int* __restrict__ frag_count, int* __restrict__ tile_flag,
+                                                            int* __restrict__ pair_count,
+                                                            float4* __restrict__ zero_out, DevStats* __restrict__ st) {
   pdl_wait();
   const int tiles_x = (cam.w + 7) / 8;
   const int tiles = tiles_x * ((cam.h + 3) / 4);
   const int t = blockIdx.x * kCullWarps + (threadIdx.x >> 5);
   if (t >= tiles) return;                      // whole warps
-  cull_warp_tile<R, 8, 4>(V, cam, t % tiles_x, t / tiles_x, 0, V.n_faces, boxes, gboxes, V.diag, 0, 0, items, cap,
-                          n_items, frag_count, st);
+  const int tx = t % tiles_x, ty = t / tiles_x;
+  const bool any = cull_warp_tile<R, 8, 4>(V, cam, tx, ty, 0, V.n_faces, boxes, gboxes, V.diag, 0, 0, items, cap,
+                                           n_items, frag_count, st);
+  if (tile_flag == nullptr) return;
+  const int lane = threadIdx.x & 31;
+  if (any) {
+    // the 16 x 16 tile of K4 that holds this 8 x 4 warp tile
+    if (lane == 0) tile_flag[(ty >> 2) * ((cam.w + 15) >> 4) + (tx >> 1)] = 1;
+  } else {
+    // no candidate: no fragments, no pairs, a zero pixel (K4 may skip it)
+    const int xw = tx * 8 + (lane & 7), yw = ty * 4 + (lane >> 3);
+    if (xw < cam.w && yw < cam.h) {
+      const int pix = yw * cam.w + xw;
+      pair_count[pix] = 0;
+      if (zero_out) zero_out[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
 }
 
 // K2b: every item on the certified fast path, the others deferred to the
@@ -188,7 +205,8 @@ void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCame
   const int tiles = ((cam.w + 7) / 8) * ((cam.h + 3) / 4);
   if (tiles <= 0) return;
   launch_pdl(k2a_cull<R>, dim3((tiles + kCullWarps - 1) / kCullWarps), dim3(32 * kCullWarps), s, V, cam,
-             (const int4*)w.boxes, (const int4*)w.gboxes, w.items, w.cap, w.n_items, w.frag_count, st);
+             (const int4*)w.boxes, (const int4*)w.gboxes, w.items, w.cap, w.n_items, w.frag_count, w.tile_flag,
+             w.pair_count, w.zero_out, st);
 #define IVV_K2B(PP, MM, SS) launch_k2b<PP, R, MM, SS>(V, cam, cam64, w, st, num_sms, s)
   if constexpr (sizeof(R) == 4) {
     if (V.P == 2) {

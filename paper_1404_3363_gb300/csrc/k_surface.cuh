@@ -78,9 +78,10 @@ __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const Dev
 // group boxes for this camera in boxes / gboxes).  Items carry the pixel's
 // index pix0 + yw * cam.w + xw and tag | (the patch's index in V) (batches
 // put the request into the high bits of tag).  Zeroes the fragment counters
-// of the tile's pixels.
+// of the tile's pixels; returns whether the tile has any candidate (the same
+// on every lane).
 template <typename R, int TW, int TH>
-__device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCamera<R>& cam, int tx, int ty, int face0,
+__device__ __forceinline__ bool cull_warp_tile(const DevVolume& V, const DevCamera<R>& cam, int tx, int ty, int face0,
                                                int nface, const int4* __restrict__ boxes,
                                                const int4* __restrict__ gboxes, float diag, int pix0, int tag,
                                                int2* __restrict__ items, int cap, int* __restrict__ n_items,
@@ -101,6 +102,7 @@ __device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCame
   const R pad = R(1e-6) * R(diag);
   const int ngroups = (nface + kGroup - 1) / kGroup;
   unsigned dropped = 0;
+  bool any = false;
   for (int g0 = 0; g0 < ngroups; g0 += 32) {
     const int g = g0 + lane;
     const bool ghit = g < ngroups && box_meets(__ldg(gboxes + g), rx0, ry0, rx1, ry1);
@@ -125,6 +127,7 @@ __device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCame
         }
         const unsigned pm = __ballot_sync(0xffffffffu, pass);
         if (pm) {
+          any = true;
           int base = 0;
           if (lane == 0) base = atomicAdd(n_items, __popc(pm));
           base = __shfl_sync(0xffffffffu, base, 0);
@@ -140,6 +143,7 @@ __device__ __forceinline__ void cull_warp_tile(const DevVolume& V, const DevCame
     }
   }
   if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
+  return any;
 }
 
 // K2b body: item (pixel, patch) with the pixel's ray (o, d) for pixel
