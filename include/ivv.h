@@ -292,6 +292,22 @@ ivv_status ivv_render_noalloc(ivv_volume* vol, const ivv_camera* cam, const ivv_
 ivv_status ivv_render_to_host(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
                               int width, int height, float* out_rgba_host, void* stream);
 
+/* As ivv_render_to_host, without waiting: the frame is rendered on `stream`
+ * into one of two library-owned device images (used in turn) and copied to
+ * out_rgba_host (pinned host memory, [height][width][4] float32) on a
+ * library stream once the render is done, so the copy of one frame runs
+ * while the next one renders.  out_rgba_host must not be read or reused
+ * before ivv_render_to_host_wait returns; a frame's image is rendered only
+ * after the copy that last used the same device image has finished.  Errors
+ * as ivv_render (IVV_ERR_WORKSPACE: growing an image inside a stream
+ * capture). */
+ivv_status ivv_render_to_host_async(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
+                                    int width, int height, float* out_rgba_host, void* stream);
+
+/* Blocks until every copy queued by ivv_render_to_host_async on this volume
+ * has reached the host. */
+ivv_status ivv_render_to_host_wait(ivv_volume* vol);
+
 /* Stages 1-2 only (§4.1, §4.2): the per-pixel entry/exit pairs in
  * front-to-back order.  Device outputs, caller-owned:
  *   pair_count [height*width] int32,

@@ -82,6 +82,15 @@ namespace {
 
 void free_volume(ivv_volume* v) {
   if (!v) return;
+  if (v->copy_stream) {
+    cudaStreamSynchronize(v->copy_stream);
+    cudaStreamDestroy(v->copy_stream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (v->own_out2[k]) cudaFree(v->own_out2[k]);
+    if (v->ev_rendered[k]) cudaEventDestroy(v->ev_rendered[k]);
+    if (v->ev_copied[k]) cudaEventDestroy(v->ev_copied[k]);
+  }
   void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_rho32, v->d_org64,
                   v->d_count, v->d_face32, v->d_face64,
                   v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
@@ -793,6 +802,45 @@ ivv_status ivv_render_to_host(ivv_volume* v, const ivv_camera* cam, const ivv_re
   if (st != IVV_OK) return st;
   IVV_CUDA(cudaMemcpyAsync(out_host, v->own_out, bytes, cudaMemcpyDeviceToHost, s));
   IVV_CUDA(cudaStreamSynchronize(s));
+  return IVV_OK;
+}
+
+ivv_status ivv_render_to_host_async(ivv_volume* v, const ivv_camera* cam, const ivv_render_params* params,
+                                    int width, int height, float* out_host, void* stream) {
+  if (!v || !out_host) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
+  const size_t bytes = sizeof(float4) * (size_t)width * height;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!v->copy_stream) {
+    IVV_CUDA(cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      IVV_CUDA(cudaEventCreateWithFlags(&v->ev_rendered[k], cudaEventDisableTiming));
+      IVV_CUDA(cudaEventCreateWithFlags(&v->ev_copied[k], cudaEventDisableTiming));
+      IVV_CUDA(cudaEventRecord(v->ev_copied[k], v->copy_stream));
+    }
+  }
+  const int slot = v->next_slot;
+  if (v->own_out2_bytes[slot] < bytes) {
+    // the slot's earlier copy must be done before its image is reallocated
+    IVV_CUDA(cudaStreamSynchronize(v->copy_stream));
+    ivv_status st = ensure_own((void**)&v->own_out2[slot], &v->own_out2_bytes[slot], bytes, s);
+    if (st != IVV_OK) return st;
+  }
+  // the slot's image is overwritten only after its previous copy finished
+  IVV_CUDA(cudaStreamWaitEvent(s, v->ev_copied[slot], 0));
+  ivv_status st = render_impl(v, cam, params, width, height, v->own_out2[slot], nullptr, 0, s);
+  if (st != IVV_OK) return st;
+  IVV_CUDA(cudaEventRecord(v->ev_rendered[slot], s));
+  IVV_CUDA(cudaStreamWaitEvent(v->copy_stream, v->ev_rendered[slot], 0));
+  IVV_CUDA(cudaMemcpyAsync(out_host, v->own_out2[slot], bytes, cudaMemcpyDeviceToHost, v->copy_stream));
+  IVV_CUDA(cudaEventRecord(v->ev_copied[slot], v->copy_stream));
+  v->next_slot = slot ^ 1;
+  return IVV_OK;
+}
+
+ivv_status ivv_render_to_host_wait(ivv_volume* v) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "NULL argument");
+  if (v->copy_stream) IVV_CUDA(cudaStreamSynchronize(v->copy_stream));
   return IVV_OK;
 }
 

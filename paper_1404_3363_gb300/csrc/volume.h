@@ -41,6 +41,13 @@ struct ivv_volume {
   size_t own_ws_bytes = 0;
   float* own_out = nullptr;
   size_t own_out_bytes = 0;
+  // ivv_render_to_host_async: two device images used in turn, each copied
+  // to the host on copy_stream once its render is done
+  float* own_out2[2] = {nullptr, nullptr};
+  size_t own_out2_bytes[2] = {0, 0};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rendered[2] = {}, ev_copied[2] = {};
+  int next_slot = 0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[IVV_N_STAGES + 1] = {};
   bool timed = false;

@@ -118,6 +118,9 @@ def load(path: str = LIB_PATH):
     L.ivv_render.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp,
                              C.c_size_t, vp]
     L.ivv_render_to_host.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp]
+    L.ivv_render_to_host_async.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp,
+                                           vp]
+    L.ivv_render_to_host_wait.argtypes = [vp]
     L.ivv_render_noalloc.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, vp, vp]
     L.ivv_render_pairs.argtypes = [vp, C.POINTER(Camera), C.POINTER(RenderParams), C.c_int, C.c_int, C.c_int,
                                    vp, vp, vp, vp, C.c_size_t, vp]
@@ -343,6 +346,21 @@ class Volume:
         _check(load().ivv_render_to_host(self.h, C.byref(cam), C.byref(prm), width, height, C.c_void_p(ptr),
                                          C.c_void_p(_stream_ptr(stream))))
         return out_host
+
+    def render_to_host_async(self, camera, params, width, height, out_host, stream=None, flags=0):
+        """Queue a render whose image is copied into pinned host memory (a
+        pinned tensor or numpy array) while later frames render; the image is
+        valid after wait_host()."""
+        prm = params_struct(params, flags)
+        cam = camera_struct(camera)
+        ptr = out_host.ctypes.data if isinstance(out_host, np.ndarray) else out_host.data_ptr()
+        _check(load().ivv_render_to_host_async(self.h, C.byref(cam), C.byref(prm), width, height, C.c_void_p(ptr),
+                                               C.c_void_p(_stream_ptr(stream))))
+        return out_host
+
+    def wait_host(self):
+        """Block until every image queued by render_to_host_async is on the host."""
+        _check(load().ivv_render_to_host_wait(self.h))
 
     def render_pairs(self, camera, params, width, height, max_pairs=16, stream=None, flags=0):
         """Stages 1-2: per-pixel entry/exit pairs (counts [H*W], pairs [M][H*W][8], blocks [M][H*W])."""

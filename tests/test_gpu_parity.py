@@ -204,6 +204,33 @@ def test_stats_and_timing(ivv):
     assert set(t) == {"project", "intersect", "pair", "integrate"} and all(v >= 0 for v in t.values())
 
 
+def test_render_to_host_async_pipeline(ivv):
+    """Frames queued with render_to_host_async (each copy overlapping the next
+    render, two device images used in turn, grown when the window grows)
+    equal the blocking render_to_host frame by frame once wait_host returns."""
+    import dataclasses
+    sc = scenes.config(1, width=96, height=64)
+    vol = ivv.volume_for(sc)
+    cams = [sc.camera, dataclasses.replace(sc.camera, eye=tuple(1.1 * e for e in sc.camera.eye))]
+    sizes = [(96, 64), (96, 64), (128, 80), (96, 64), (128, 80), (128, 80)]
+    refs = []
+    for i, (w, h) in enumerate(sizes):
+        ref = np.zeros((h, w, 4), np.float32)
+        vol.render_to_host(cams[i % 2], sc.params, w, h, ref)
+        refs.append(ref)
+    outs = []
+    for i, (w, h) in enumerate(sizes):
+        out = torch.full((h, w, 4), float("nan"), dtype=torch.float32).pin_memory()
+        vol.render_to_host_async(cams[i % 2], sc.params, w, h, out)
+        outs.append(out)
+    vol.wait_host()
+    for i, (ref, out) in enumerate(zip(refs, outs)):
+        got = out.numpy()
+        assert not np.isnan(got).any(), i
+        assert np.abs(got - ref).max() <= 1e-5, i
+    assert max(r[..., 3].max() for r in refs) > 0.05
+
+
 def test_render_to_host_and_errors(ivv):
     sc = scenes.config(0, width=40, height=30)
     sc.params.precision = 0
