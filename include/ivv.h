@@ -132,7 +132,7 @@ typedef struct {
  *              of the pixel at the sample's depth (the paper stops at the
  *              pixel frustum, rf_tol = 1) [0.05]
  * rk_method    IVV_RK_* integrator of the ODE method [IVV_RK_BS32]; the
- *              fixed-step family (§5.3) takes one step per sample interval
+ *              fixed-step family (§5.2-5.3) takes one step per sample interval
  *              (rk_tol unused) and runs in FP32 or MIXED precision
  * near_clip    > 0: near plane at this distance from the eye along the view
  *              direction (§5.5): intersections in front of it are dropped
@@ -176,7 +176,7 @@ enum {
   IVV_RK_RK4_38 = 5,    /* fixed step: Kutta's 3/8 rule (RK4 3/8)               */
   IVV_RK_FEHLBERG5 = 6, /* fixed step: Fehlberg's pair, fifth-order weights (RKF) */
   IVV_RK_IMPLICIT_EULER = 7  /* fixed step: implicit Euler (IRK1), Newton with the
-                                exact Jacobian of §5.3 (spline Hessian); use with
+                                exact Jacobian of §5.2 (spline Hessian); use with
                                 a large c (the paper's c = 100) */
 };
 

@@ -12,7 +12,7 @@ Functions follow the paper (Fuchs & Hjelmervik, TVCG 2015):
   composite      §3.2.1 Alg. 1 with supersampling
   render         the whole per-pixel path, per-sample RF (method 0),
                  RKF45 on the pulled-back ODE of §5.2 (method 1) or one step
-                 per sample interval of the fixed-step RK family of §5.3
+                 per sample interval of the fixed-step RK family of §5.2-5.3
                  (FIXED_* methods) or of implicit Euler (IMPLICIT_EULER)
   table1         §5.3 Table 1 harness (fixed-step RK family / RF / implicit
                  Euler)
@@ -33,12 +33,12 @@ from . import build as _build
 _LIB = None
 
 # render methods: per-sample root finding, RKF45 with error control, and the
-# fixed-step explicit RK family of §5.3 (one step per sample interval)
+# fixed-step explicit RK family of §5.2-5.3 (one step per sample interval)
 METHOD_RF = 0
 METHOD_RKF45 = 1
 FIXED_EULER, FIXED_MIDPOINT, FIXED_KUTTA3, FIXED_RK4, FIXED_RK4_38, FIXED_FEHLBERG5 = 11, 12, 13, 14, 15, 16
 FIXED_ORDER = {11: 1, 12: 2, 13: 3, 14: 4, 15: 4, 16: 5}
-# implicit Euler of §5.3 (one step per sample interval, Newton with the exact
+# implicit Euler of §5.2 (one step per sample interval, Newton with the exact
 # Jacobian of G)
 IMPLICIT_EULER = 17
 

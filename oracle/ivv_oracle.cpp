@@ -722,7 +722,7 @@ bool ode_rhs(const Block& b, const double p[3], const double g_in[3], const doub
   return qr_solve3(J, Vv, W);
 }
 
-// One implicit Euler step of §5.3: p_next = p + h W(p_next), solved for the
+// One implicit Euler step of §5.2: p_next = p + h W(p_next), solved for the
 // increment z = p_next - p by Newton on G(z) = z - h W(p + z) with the exact
 // Jacobian of G from differentiating J_phi G = J_phi z - h V(phi):
 //   J_phi(x) J_G(z) = H_phi(x)[z - G(z)] + (I - h J_V) J_phi(x),  x = p + z,
@@ -941,7 +941,7 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
         ++st.rk_steps;
       }
     } else if (P.method == 17) {
-      // one implicit Euler step (§5.3) from s_{j-1} to s_j
+      // one implicit Euler step (§5.2) from s_{j-1} to s_j
       const double hh = s[j] - s[j - 1];
       double pn[3];
       auto ev = [&](const double x[3], double phi[3], double J[3][3], double H[3][3][3]) {

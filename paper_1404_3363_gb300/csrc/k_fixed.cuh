@@ -1,4 +1,4 @@
-// Stage 3 with the paper's fixed-step explicit Runge-Kutta family (§5.3:
+// Stage 3 with the paper's fixed-step explicit Runge-Kutta family (§5.2-5.3:
 // Euler, midpoint, Kutta's third-order method, classic RK4, the 3/8 rule and
 // Fehlberg's fifth-order weights): one step of the tableau per sample
 // interval [s_{j-1}, s_j] of the pulled-back ODE p' = W(p) (§5.2), stage

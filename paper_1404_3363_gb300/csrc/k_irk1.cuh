@@ -1,4 +1,4 @@
-// Stage 3 with the paper's implicit Euler method (§5.3): one step per sample
+// Stage 3 with the paper's implicit Euler method (§5.2): one step per sample
 // interval [s_j, s_{j+1}] of the pulled-back ODE p' = W(p) (§5.2),
 //     p_{j+1} = p_j + h W(p_{j+1}),   h = s_{j+1} - s_j,
 // solved for the increment z = p_{j+1} - p_j by Newton on

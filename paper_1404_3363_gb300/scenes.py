@@ -93,7 +93,7 @@ class RenderParams:
     use_mlp_guess: int = 0
     method: int = 0            # 0: ODE (§5.2), 1: per-sample root finding (§5.1)
     rf_tol: float = 0.05       # RF stop: fraction of the pixel half width
-    rk_method: int = 0         # 0: BS3(2) with error control; 1-6: fixed-step family of §5.3
+    rk_method: int = 0         # 0: BS3(2) with error control; 1-6: fixed-step family of §5.2-5.3
     near_clip: float = 0.0     # > 0: near plane at this distance along the view direction (§5.5)
     cut_planes: tuple = ()     # up to 4 (n_x, n_y, n_z, w): points with n.g + w > 0 are cut away (§5.5)
 

@@ -1,4 +1,4 @@
-"""Implicit Euler of §5.3 on the GPU (rk_method 7: one step per sample
+"""Implicit Euler of §5.2 on the GPU (rk_method 7: one step per sample
 interval, Newton on G(z) = z - ds W(p + z) with the exact Jacobian from the
 spline Hessian), against the oracle taking the same steps in FP64 (max
 |dRGBA| <= 1e-3), through the C ABI."""

@@ -1,4 +1,4 @@
-"""The fixed-step RK family of §5.3 on the GPU (rk_method 1-6: Euler,
+"""The fixed-step RK family of §5.2-5.3 on the GPU (rk_method 1-6: Euler,
 midpoint, Kutta-3, RK4, RK4 3/8, Fehlberg's fifth-order weights), one step
 per sample interval, against the oracle taking the same steps in FP64
 (max |dRGBA| <= 1e-3), through the C ABI."""

@@ -1,4 +1,4 @@
-"""Oracle pins of the implicit Euler method of §5.3 (one step per sample
+"""Oracle pins of the implicit Euler method of §5.2 (one step per sample
 interval; Newton on G(z) = z - ds W(p + z) with the exact Jacobian of G,
 which needs the second partials of the spline map).
 

@@ -1,4 +1,4 @@
-"""Oracle pins of the fixed-step explicit RK family of §5.3 in the render
+"""Oracle pins of the fixed-step explicit RK family of §5.2-5.3 in the render
 path (one step of the tableau per sample interval, stage points clamped to
 the parameter box as in §5.4).
 
