@@ -238,31 +238,52 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
 
 // Block-aggregated append of the active pixels to the integrator's queue
 // (every thread of the 256-thread block of one 16 x 16 tile calls it): the
-// tile's active pixels land contiguously, warp tile after warp tile, so the
-// 32 consecutive queue items an integrator warp takes are neighbours even
-// where the tile is only partly covered.  Also the counters that every
-// render keeps.
-__device__ __forceinline__ void pair_epilogue(int pix, int np, unsigned um, unsigned pov, int* __restrict__ active,
-                                              int* __restrict__ n_active, DevStats* __restrict__ st) {
-  __shared__ int s_warp[8];
+// tile's active pixels land contiguously, so the 32 consecutive queue items
+// an integrator warp takes are neighbours even where the tile is only partly
+// covered.  Within the tile they are grouped by path length len (8 bands
+// relative to the tile's longest, longest first; warp tile order within a
+// band), so that the pixels of one warp take similar times: the integrators
+// refill a warp only when all its lanes are idle.  Also the counters that
+// every render keeps.
+__device__ __forceinline__ void pair_epilogue(int pix, int np, float len, unsigned um, unsigned pov,
+                                              int* __restrict__ active, int* __restrict__ n_active,
+                                              DevStats* __restrict__ st) {
+  constexpr int kBands = 8;
+  __shared__ int s_cnt[kBands][8];    // [band][warp]: active pixels, then their offsets
+  __shared__ unsigned s_max;
   __shared__ int s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = np > 0;
-  const unsigned bal = __ballot_sync(0xffffffffu, act);
-  if (lane == 0) s_warp[warp] = __popc(bal);
+  const float key = act && len > 0.f ? len : 0.f;
+  unsigned wmax = __float_as_uint(key);           // non-negative floats order as their bits
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if (threadIdx.x == 0) s_max = 0u;
+  __syncthreads();
+  if (lane == 0) atomicMax(&s_max, wmax);
+  __syncthreads();
+  const float kmax = __uint_as_float(s_max);
+  const int band = kmax > 0.f ? min(kBands - 1, (int)((float)kBands * (key / kmax))) : 0;
+  unsigned my_band_mask = 0u;
+#pragma unroll
+  for (int b = 0; b < kBands; ++b) {
+    const unsigned m = __ballot_sync(0xffffffffu, act && band == b);
+    if (band == b) my_band_mask = m;
+    if (lane == 0) s_cnt[b][warp] = __popc(m);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int tot = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int c = s_warp[k];
-      s_warp[k] = tot;
-      tot += c;
-    }
+    for (int b = kBands - 1; b >= 0; --b)         // longest band first
+      for (int w = 0; w < 8; ++w) {
+        const int c = s_cnt[b][w];
+        s_cnt[b][w] = tot;
+        tot += c;
+      }
     s_base = tot > 0 ? atomicAdd(n_active, tot) : 0;
   }
   __syncthreads();
-  if (act) active[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = pix;
+  if (act) active[s_base + s_cnt[band][warp] + __popc(my_band_mask & ((1u << lane) - 1u))] = pix;
   unsigned long long cu = um, cp = pov, cr = act ? 1 : 0, cpairs = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -317,7 +338,12 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
       np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
                          pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
   }
-  pair_epilogue(pix, np, um, pov, active, n_active, st);
+  float len = 0.f;                                  // the pixel's path length through the volume
+  for (int q = 0; q < np; ++q) {
+    const size_t o = (size_t)q * npix + pix;
+    len += (float)(pair_out[o].x - pair_in[o].x);
+  }
+  pair_epilogue(pix, np, len, um, pov, active, n_active, st);
   // every thread read the flag before the epilogue's barriers: clear it for
   // the next frame
   if (tile_flag != nullptr && threadIdx.x == 0) tile_flag[blockIdx.x] = 0;
@@ -346,7 +372,7 @@ __global__ void __launch_bounds__(256) kb4_pair(BatchArgs ba, int npix, const fl
     np = pair_pixel<float>(pix, npix, tau, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
                            pair_count, kMaxPairs, q.out + (pix - __ldg(ba.pix0 + rq)), um, pov);
   }
-  pair_epilogue(pix, np, um, pov, active, n_active, st);
+  pair_epilogue(pix, np, 0.f, um, pov, active, n_active, st);
 }
 
 }  // namespace
