@@ -135,6 +135,20 @@ def test_batch_entry_points_reject_null_arguments(lib):
     lib.ivv_batch_destroy(None)
 
 
+def test_render_entry_points_reject_null_arguments(lib):
+    """The single-frame render calls, the pipelined host read-back among
+    them, validate their arguments before any CUDA call."""
+    import ctypes as C
+    cam = ivv.Camera()
+    prm = ivv.RenderParams()
+    host = (C.c_float * 16)()
+    assert lib.ivv_render_to_host(None, C.byref(cam), C.byref(prm), 2, 2, host, None) == 1
+    assert lib.ivv_render_to_host_async(None, C.byref(cam), C.byref(prm), 2, 2, host, None) == 1
+    assert lib.ivv_render_to_host_async(None, C.byref(cam), C.byref(prm), 2, 2, None, None) == 1
+    assert lib.ivv_render_to_host_wait(None) == 1
+    assert b"NULL" in lib.ivv_last_error()
+
+
 def _grazing_cos(ov, o, d, block, q):
     """|cos| between the ray and the face normal at parameter point q."""
     q = np.asarray(q)
