@@ -216,7 +216,8 @@ def _ncu_traffic(kernel, workload):
 
 def cpu_oracle_sample(scene, target_s=12.0, max_stride=64, label="1920x1080 frame"):
     """Oracle Mpix/s on evenly spaced rows of the frame (rows at stride s,
-    halving s until one sample takes >= target_s / 3)."""
+    halving s until one sample takes >= target_s / 3).  Returns the
+    cpu_baseline record and the rendered rows {y: float64 [W][4]}."""
     import oracle
     vol = oracle.OracleVolume(scene.blocks, scene.scalar_mode)
     W, H = scene.width, scene.height
@@ -225,18 +226,88 @@ def cpu_oracle_sample(scene, target_s=12.0, max_stride=64, label="1920x1080 fram
     cores = os.cpu_count() or 1
     while True:
         rows = list(range(stride // 2, H, stride))
+        got = {}
         t0 = time.perf_counter()
         for y in rows:
-            oracle.render(scene, vol, window=(0, W, y, y + 1), n_threads=cores)
+            got[y] = oracle.render(scene, vol, window=(0, W, y, y + 1), n_threads=cores)[0]
         dt = time.perf_counter() - t0
-        best = (len(rows) * W, dt, stride, len(rows))
+        best = (len(rows) * W, dt, stride, len(rows), got)
         if dt >= target_s / 3 or stride == 1:
             break
         stride //= 2
-    px, dt, stride, nrows = best
+    px, dt, stride, nrows, got = best
     return {"value": px / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d rows at stride %d of the %s (%d pixels), FP64 per-sample Newton, "
-                      "%.2f s" % (nrows, stride, label, px, dt)}
+                      "%.2f s" % (nrows, stride, label, px, dt)}, got
+
+
+def image_parity(img, rows):
+    """Max |dRGBA| of the device image against the oracle's rows."""
+    import numpy as np
+    err = 0.0
+    for y, ref in rows.items():
+        err = max(err, float(np.abs(img[y].astype(np.float64) - ref).max()))
+    return {"max_rgba_err": err, "pixels": len(rows) * img.shape[1], "rows": len(rows),
+            "tolerance": 1e-3, "ok": err <= 1e-3}
+
+
+def pair_parity(vol, sc, rows):
+    """Entry/exit points (stage 1-2 result) of the frame's rows against the
+    oracle's FP64 intersections: parameter-space error per image, over all
+    hits and over the hits at least 0.2 away from grazing (|cos| of the ray
+    and the face normal), and pixels whose pair count differs."""
+    import numpy as np
+    import oracle
+    W, H = sc.width, sc.height
+    cores = os.cpu_count() or 1
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    ys = sorted(rows)
+    if len(ys) == H:
+        co, po, bo = ov.window_pairs(sc.camera, W, H, n_threads=cores)
+    else:
+        parts = [ov.window_pairs(sc.camera, W, H, window=(0, W, y, y + 1), n_threads=cores) for y in ys]
+        co = np.concatenate([q[0] for q in parts])
+        po = np.concatenate([q[1] for q in parts], axis=1)
+        bo = np.concatenate([q[2] for q in parts], axis=1)
+    cap = max(1, int(co.max()))
+    cg, pg, bg = vol.render_pairs(sc.camera, sc.params, W, H, max_pairs=cap)
+    sel = (np.array(ys)[:, None] * W + np.arange(W)[None, :]).reshape(-1)
+    cg = cg.cpu().numpy()[sel]
+    pg = pg.cpu().numpy()[:, sel].astype(np.float64)
+    bg = bg.cpu().numpy()[:, sel]
+    same = cg == co
+    worst, worst_ng, worst_t, n_hits, n_graze, blk_bad = 0.0, 0.0, 0.0, 0, 0, 0
+    for k in range(cap):
+        m = same & (co > k)
+        if not m.any():
+            continue
+        blk_bad += int((bg[k][m] != bo[k][m]).sum())
+        for a, b in ((0, 3), (4, 7)):
+            got, ref = pg[k][m][:, a:b], po[k][m][:, a:b]
+            e = np.abs(got - ref).max(axis=1)
+            worst_t = max(worst_t, float(np.abs(pg[k][m][:, b] - po[k][m][:, b]).max()))
+            cosg = np.ones(len(ref))
+            for blk in np.unique(bo[k][m]):
+                q = bo[k][m] == blk
+                phi, J, _ = ov.eval(int(blk), ref[q])
+                face = np.argmin(np.minimum(np.abs(ref[q]), np.abs(ref[q] - 1)), axis=1)
+                nrm = np.linalg.inv(J)[np.arange(int(q.sum())), face]          # face normal: row of J^-1
+                if sc.camera.ortho:
+                    d = np.broadcast_to(np.asarray(sc.camera.target, float) - np.asarray(sc.camera.eye, float),
+                                        phi.shape)
+                else:
+                    d = phi - np.asarray(sc.camera.eye, float)                 # the ray passes the eye
+                cosg[q] = np.abs((nrm * d).sum(1)) / (np.linalg.norm(nrm, axis=1) * np.linalg.norm(d, axis=1))
+            worst = max(worst, float(e.max()))
+            ng = cosg >= 0.2
+            if ng.any():
+                worst_ng = max(worst_ng, float(e[ng].max()))
+            n_hits += len(e)
+            n_graze += int((~ng).sum())
+    return {"pixels": int(len(sel)), "hits": n_hits, "grazing_hits": n_graze,
+            "max_param_err": worst, "max_param_err_non_grazing": worst_ng, "max_t_err": worst_t,
+            "count_mismatch_pixels": int((~same).sum()), "block_mismatch": blk_bad,
+            "bound": 1e-5}
 
 
 def aggregate_ranks(ms_local, pixels_per_rank, dist=None, device=None):
@@ -331,20 +402,6 @@ def run_ours(args):
     flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP, implicit=args.rk_method == 7)
     flops_k2 = k2_flops(st, F)
 
-    # parity spot check of this frame against the oracle (untimed)
-    max_err = None
-    if rank == 0 and not args.no_parity:
-        import oracle
-        img = out.cpu().numpy().astype(np.float64)
-        ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
-        cov = np.argwhere(img[..., 3] > 0)
-        rng = np.random.default_rng(7)
-        pick = cov[rng.choice(len(cov), min(48, len(cov)), replace=False)] if len(cov) else []
-        max_err = 0.0
-        for y, x in pick:
-            ref = oracle.render(sc, ov, window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
-            max_err = max(max_err, float(np.abs(img[y, x] - ref).max()))
-
     def frame(flags=0):
         vol.render(sc.camera, sc.params, W, H, out=out, flags=flags)
 
@@ -425,9 +482,21 @@ def run_ours(args):
     roofs = sorted([roof("k2_intersect", flops_k2, k2_ms), roof("stage3_integrate", flops_k5, k5_ms)],
                    key=lambda r: -r["ms_per_launch"])
 
-    cpu_base = None
+    cpu_base, rows = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = cpu_oracle_sample(sc, label="%dx%d frame" % (W, H))
+        cpu_base, rows = cpu_oracle_sample(sc, label="%dx%d frame" % (W, H))
+
+    # parity of this frame against the oracle (untimed): every pixel of the
+    # rows the CPU baseline rendered (the whole frame where it reached stride
+    # 1), and the entry/exit points of the same pixels
+    parity = pair_err = None
+    if rank == 0 and not args.no_parity:
+        if rows is None:
+            _, rows = cpu_oracle_sample(sc, target_s=6.0, max_stride=32, label="%dx%d frame" % (W, H))
+        vol.render(sc.camera, sc.params, W, H, out=out)
+        torch.cuda.synchronize()
+        parity = image_parity(out.cpu().numpy(), rows)
+        pair_err = pair_parity(vol, sc, rows)
 
     if rank == 0:
         import ctypes
@@ -455,7 +524,8 @@ def run_ours(args):
                                         "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
                                         "isect_newton")},
             "max_delta_p": st["max_delta_p"],
-            "parity_max_rgba_err_sampled": max_err,
+            "parity": parity,
+            "entry_exit_parity": pair_err,
             "clocks": clocks,
         }
         if cpu_base:
@@ -509,25 +579,27 @@ def run_batch(args):
     b.render(flags=ivv.FLAG_TIMING)
     stages = b.stage_times()
 
-    max_err = None
+    parity = None
     if rank == 0 and not args.no_parity:
         import oracle
         b.render()
         torch.cuda.synchronize()
         orc = [oracle.OracleVolume(v.blocks, v.scalar_mode) for v in vols]
-        rng = np.random.default_rng(7)
-        max_err = 0.0
-        for q, out in list(zip(reqs, b.outputs))[::4]:
+        max_err, px = 0.0, 0
+        for q, out in zip(reqs, b.outputs):
             img = out.cpu().numpy()
-            cov = np.argwhere(img[..., 3] > 0)
+            cov = np.flatnonzero(img[..., 3].max(axis=1) > 0)
             if not len(cov):
                 continue
-            y, x = cov[rng.integers(len(cov))]
+            y = int(cov[len(cov) // 2])                 # the middle covered row, every pixel of it
             sc = vols[q.volume]
             sc = type(sc)(sc.name, sc.blocks, sc.scalar_mode, q.tf, q.camera, q.width, q.height,
                           scenes.RenderParams())
-            ref = oracle.render(sc, orc[q.volume], window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
-            max_err = max(max_err, float(np.abs(img[y, x].astype(np.float64) - ref).max()))
+            ref = oracle.render(sc, orc[q.volume], window=(0, q.width, y, y + 1))[0]
+            max_err = max(max_err, float(np.abs(img[y].astype(np.float64) - ref).max()))
+            px += q.width
+        parity = {"max_rgba_err": max_err, "pixels": px, "rows": len(reqs),
+                  "sample": "the middle covered row of every request", "tolerance": 1e-3, "ok": max_err <= 1e-3}
 
     for _ in range(args.warmup):
         b.render()
@@ -587,7 +659,8 @@ def run_batch(args):
             "work": {k: st[k] for k in ("rays", "pairs", "samples", "rk_steps", "rk_rejects", "rhs_evals",
                                         "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
                                         "isect_newton")},
-            "parity_max_rgba_err_sampled": max_err,
+            "parity": parity,
+            "entry_exit_parity": pair_err,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -118,14 +118,20 @@ typedef struct {
  *              (§3.2.1 supersampling) [4]
  * c            weight of the perpendicular field V_perp (Eq. 10) [1]
  * early_alpha  stop a pixel once alpha_dst >= early_alpha [1 - 1e-4]
- * use_mlp_guess IVV_GUESS_* initial guess of the RF method; must be
- *              IVV_GUESS_CENTER (0) with the ODE method [0]
+ * use_mlp_guess IVV_GUESS_* initial guess [0].  RF method: the Newton start
+ *              of every sample.  Both methods: IVV_GUESS_MLP starts the
+ *              stage-2 Newton solves that have no chord context -- entries
+ *              on the near plane and entries moved off a singular face
+ *              (§5.4) -- from the block's trained network (tensor-core
+ *              inference on the list of those entries), falling back to the
+ *              plain starts when Newton from it fails.  IVV_GUESS_CHORD is
+ *              for the RF method only.
  * precision    IVV_PREC_* [FP32]
  * flags        IVV_FLAG_* [0]
  * x0, y0, full_width, full_height
  *              render the window [x0, x0+width) x [y0, y0+height) of a
  *              full_width x full_height image (0 = the window is the image)
- * method       IVV_METHOD_* [ODE]; RF supports FP32 precision only, reads
+ * method       IVV_METHOD_* [ODE]; RF runs in FP32 or MIXED precision, reads
  *              back the sample count (one stream synchronisation) and keeps
  *              its sample buffers (40 bytes per sample) in library memory
  * rf_tol       RF stopping rule: ||phi(p) - g|| <= rf_tol times the half width
@@ -138,6 +144,8 @@ typedef struct {
  *              direction (§5.5): intersections in front of it are dropped
  *              and a block whose nearest remaining intersection is an exit
  *              (the plane cuts through the block) is entered on the plane [0]
+ *              (its parameter point by Newton from the exit point, or from
+ *              the learned guess)
  * n_cut_planes, cut_planes
  *              up to IVV_MAX_CUT_PLANES cutting planes (§5.5), plane k as
  *              (n_x, n_y, n_z, w): the part of the volume with n.g + w > 0 is
@@ -216,6 +224,8 @@ typedef struct {
   unsigned long long isect_items;   /* (pixel, patch) candidates after the box tests */
   unsigned long long isect_split;   /* candidates that needed the subdivision search */
   unsigned long long rho_evals;     /* samples whose scalar was evaluated on its own (shading pass) */
+  unsigned long long entry_shrinks; /* entries with a singular Jacobian moved into the block (§5.4, Eq. 22) */
+  unsigned long long entry_newton;  /* Newton iterations of the stage-2 fix-up solves (§5.4, §5.5) */
   double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
 } ivv_stats;
 
@@ -274,14 +284,17 @@ ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_p
  * with up to 16384 face patches; every GPU that loads the library keeps that
  * array until the process exits.  Larger windows return IVV_ERR_WORKSPACE
  * with the required size in ivv_last_error(); use ivv_render for them.
+ * Only the ODE method is rendered here (every rk_method and precision, with
+ * the fused integrators, which need no sample buffer); the RF method sizes
+ * its sample buffers from a read-back and returns IVV_ERR_UNSUPPORTED.
  * The volume (created earlier) and out_rgba (device, caller-owned,
- * [height][width][4] float32) are the caller's.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  All calls share
- * the one array, whose contents persist between calls (everything a frame
- * needs zeroed is cleared by the frame itself), so calls that overlap on the
- * GPU -- on different streams or from different threads -- race: serialise
- * them. */
+ * [height][width][4] float32) are the caller's.  Every call looks up the
+ * array's address in the current device's context (cudaGetSymbolAddress);
+ * the first call on a device may load the library's device code, so make it
+ * before any stream capture.  All calls share the one array, whose contents
+ * persist between calls (everything a frame needs zeroed is cleared by the
+ * frame itself), so calls that overlap on the GPU -- on different streams or
+ * from different threads -- race: serialise them. */
 #define IVV_NOALLOC_SCRATCH_BYTES (12u << 20)
 ivv_status ivv_render_noalloc(ivv_volume* vol, const ivv_camera* cam, const ivv_render_params* params,
                               int width, int height, float* out_rgba, void* stream);
@@ -407,6 +420,44 @@ ivv_status ivv_guess_loss_grad(ivv_volume* vol, int block, int n, const float* x
 /* Host copies of one block's parameters and normalisation (c[3], inv_h[3]). */
 ivv_status ivv_get_guess_weights(ivv_volume* vol, int block, float* params, float* c, float* inv_h);
 ivv_status ivv_set_guess_weights(ivv_volume* vol, int block, const float* params);
+
+/* Capacities and iteration caps of a volume's renders (not in the paper:
+ * the paper's linked-list A-buffer and shaders state none).  Pass NULL to
+ * ivv_set_limits for the defaults in brackets; smaller values exist to
+ * exercise the overflow and cap paths (a frame never faults on them: what
+ * does not fit is dropped and counted).
+ * max_frags        fragment slots per pixel, 1..32 [32]; hits beyond them
+ *                  are dropped (ivv_stats.abuf_overflow)
+ * max_pairs        entry/exit pair slots per pixel, 1..16 [16]; pairs beyond
+ *                  them are dropped (ivv_stats.pair_overflow)
+ * items_per_pixel  capacity of the (pixel, face patch) candidate list of
+ *                  stage 1, per pixel of the window, 1..16 [16]; candidates
+ *                  beyond it are dropped (ivv_stats.abuf_overflow)
+ * max_rk_steps     RK steps per entry/exit pair of the error-controlled
+ *                  integrator, >= 1 [200000]; a pair that reaches it ends
+ *                  at its exit point (ivv_stats.step_cap)
+ * max_newton       Newton iterations per sample of the RF method and per point
+ *                  of ivv_invert_points, 1..64 [16]; a sample that misses
+ *                  its tolerance is counted (ivv_stats.rf_unconverged) */
+typedef struct {
+  int max_frags;
+  int max_pairs;
+  int items_per_pixel;
+  int max_rk_steps;
+  int max_newton;
+} ivv_limits;
+
+ivv_status ivv_set_limits(ivv_volume* vol, const ivv_limits* limits);
+ivv_status ivv_get_limits(const ivv_volume* vol, ivv_limits* limits);
+
+/* Status of the renders since the last ivv_check_frame (or ivv_reset_stats):
+ * synchronises the stream of the last render and reads the overflow and cap
+ * counters that every render keeps.  Returns IVV_ERR_ABUF_OVERFLOW if any
+ * fragment, pair or stage-1 candidate was dropped, else IVV_ERR_NONCONVERGED
+ * if an entry/exit pair hit the RK step cap or an RF sample missed its
+ * tolerance, else IVV_OK; ivv_last_error() names the counts.  The images
+ * stay valid: only the pixels concerned lack the dropped parts. */
+ivv_status ivv_check_frame(ivv_volume* vol);
 
 /* Counters (see ivv_stats); synchronises the stream of the last render. */
 ivv_status ivv_get_stats(ivv_volume* vol, ivv_stats* out);

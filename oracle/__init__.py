@@ -80,7 +80,7 @@ class Pair(C.Structure):
 
 class PixelStats(C.Structure):
     _fields_ = [("npairs", C.c_int), ("unmatched", C.c_int), ("newton_fail", C.c_int),
-                ("nsamples", C.c_int), ("rk_steps", C.c_int)]
+                ("nsamples", C.c_int), ("rk_steps", C.c_int), ("shrunk", C.c_int)]
 
 
 def lib():
@@ -112,6 +112,10 @@ def lib():
         L.orc_table1.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, c_double_p]
         L.orc_table1_ex.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, c_double_p, C.POINTER(C.c_long)]
         L.orc_eval2.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, c_double_p, c_double_p, c_double_p]
+        L.orc_window_pairs.argtypes = [C.c_void_p, C.POINTER(_Camera), C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), c_double_p,
+                                       C.POINTER(C.c_int)]
+        L.orc_t1_irk1_step.argtypes = [c_double_p, C.c_double, C.c_double, C.c_double, C.c_int, c_double_p]
         _LIB = L
     return _LIB
 
@@ -221,6 +225,22 @@ class OracleVolume:
         n = lib().orc_pixel_pairs(self.h, C.byref(c), W, H, x, y, cap, out, C.byref(um))
         return [out[i] for i in range(min(n, cap))], um.value
 
+    def window_pairs(self, cam, W, H, window=None, cap=16, n_threads=None):
+        """Entry/exit pairs of every pixel of a window (x0, x1, y0, y1) of a
+        W x H image: (count [h*w], pairs [cap][h*w][8] as (p_in, t_in, p_out,
+        t_out), block [cap][h*w]), the layout of the library's pair export."""
+        x0, x1, y0, y1 = window if window is not None else (0, W, 0, H)
+        npx = (x1 - x0) * (y1 - y0)
+        cnt = np.zeros(npx, np.int32)
+        pairs = np.full((cap, npx, 8), np.nan)
+        blk = np.full((cap, npx), -1, np.int32)
+        c = camera_struct(cam)
+        nt = n_threads if n_threads is not None else (os.cpu_count() or 1)
+        lib().orc_window_pairs(self.h, C.byref(c), W, H, x0, x1, y0, y1, nt, cap,
+                               cnt.ctypes.data_as(C.POINTER(C.c_int)), _dp(pairs),
+                               blk.ctypes.data_as(C.POINTER(C.c_int)))
+        return cnt, pairs, blk
+
     def invert(self, block, g, p0, tol=1e-13, maxit=50):
         g, p0 = _f64(g), _f64(p0)
         p = np.zeros(3)
@@ -323,8 +343,8 @@ def render(scene, vol=None, method=0, window=None, n_threads=None, stats=False,
     lib().orc_render(vol.h, C.byref(t), C.byref(c), C.byref(prm), W, H, x0, x1, y0, y1, nt,
                      _dp(out), st)
     if stats:
-        arr = np.array([[s.npairs, s.unmatched, s.newton_fail, s.nsamples, s.rk_steps] for s in st],
-                       dtype=np.int64).reshape(y1 - y0, x1 - x0, 5)
+        arr = np.array([[s.npairs, s.unmatched, s.newton_fail, s.nsamples, s.rk_steps, s.shrunk] for s in st],
+                       dtype=np.int64).reshape(y1 - y0, x1 - x0, 6)
         return out, arr
     return out
 
@@ -333,6 +353,15 @@ def table1(method, ds, c=1.0, rf_tol=1e-14):
     e = C.c_double()
     lib().orc_table1(int(method), float(ds), float(c), float(rf_tol), C.byref(e))
     return e.value
+
+
+def t1_irk1_step(p, h, c=100.0, tol=1e-13, max_it=50):
+    """One implicit Euler step on the Table 1 harness's analytic map:
+    (new point, Newton iterations or -1 for the boundary step of §5.4)."""
+    p = _f64(p)
+    pn = np.zeros(3)
+    it = lib().orc_t1_irk1_step(_dp(p), float(h), float(c), float(tol), int(max_it), _dp(pn))
+    return pn, it
 
 
 def table1_irk1(ds, c=100.0):

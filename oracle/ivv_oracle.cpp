@@ -208,7 +208,7 @@ struct Block {
   Basis1D B[3];
   std::vector<double> geom;    // [nw][nv][nu][3]
   std::vector<double> scal;    // [nw][nv][nu] or empty
-  double mean_abs_det = 1.0;
+  double mean_abs_det = 1.0;   // mean of |det J| over [0,1]^3 (the block's volume in G)
 };
 
 // phi, J (J[r][c] = d phi_r / d p_c) and scalar (cp mode) at p in [0,1]^3.
@@ -732,12 +732,15 @@ bool ode_rhs(const Block& b, const double p[3], const double g_in[3], const doub
 // evaluates the map at p itself.  Iterates may leave the parameter box (the
 // map's boundary polynomials are continued there, so G stays smooth); the
 // iteration stops once |dz|_inf <= tol and the new point p + z is clamped to
-// [0,1]^3 (§5.4: the ray is followed along the boundary).  If Newton does not
-// converge within max_it iterations (or meets a singular system: the map is
-// degenerate near the ray), the step falls back to the clamped explicit
-// Euler step p + h W(p) from the first iteration's evaluation.
-// ev(x, phi, J, H) evaluates the map.  Returns the iterations, or -1 if the
-// step fell back.
+// [0,1]^3 (§5.4: the ray is followed along the boundary).  §5.4 also names
+// the case in which Newton does not converge because it keeps trying to
+// leave the block, and answers it by stepping along the boundary of the
+// parameter domain: if Newton does not converge within max_it iterations
+// (or meets a singular system: the map is degenerate near the ray), the step
+// is the explicit Euler step p + h W(p) from the first iteration's
+// evaluation, clamped to [0,1]^3 (a step that moves along the boundary where
+// W points out of the box).  ev(x, phi, J, H) evaluates the map.  Returns the
+// iterations, or -1 if the step took the boundary step.
 template <class Eval>
 int irk1_step(Eval ev, const double p[3], double h, const double g_in[3], const double d[3], double c,
               double tol, int max_it, double pn[3]) {
@@ -881,7 +884,7 @@ struct Params {
 struct Tableau { int s; double a[6][6]; double b[6]; };
 Tableau tableau(int method);
 
-struct PixelStats { int npairs = 0, unmatched = 0, newton_fail = 0, nsamples = 0, rk_steps = 0; };
+struct PixelStats { int npairs = 0, unmatched = 0, newton_fail = 0, nsamples = 0, rk_steps = 0, shrunk = 0; };
 
 // Samples s_j = j ds (j = 0..floor(L/ds)) plus L when it lies more than
 // 1e-12 diag beyond the last one.
@@ -947,9 +950,10 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
       auto ev = [&](const double x[3], double phi[3], double J[3][3], double H[3][3][3]) {
         block_eval2(b, x, phi, J, H);
       };
-      // Newton to |dz| <= 2e-6 (quadratic convergence leaves an error far
-      // below that), at most 12 iterations, as the GPU integrator
-      if (irk1_step(ev, p, hh, g_in, d, P.c, 2e-6, 12, pn) < 0) ++st.newton_fail;
+      // G(z) = 0 solved to |dz|_inf <= 1e-13 (parameter space), at most 50
+      // Newton iterations; a step that does not converge takes the §5.4
+      // boundary step and is counted
+      if (irk1_step(ev, p, hh, g_in, d, P.c, 1e-13, 50, pn) < 0) ++st.newton_fail;
       for (int r = 0; r < 3; ++r) p[r] = pn[r];
       ++st.rk_steps;
     } else {
@@ -1077,6 +1081,76 @@ std::vector<Pair> clip_pairs(const Volume& V, const Params& P, const Camera& cam
   return out;
 }
 
+// Mean of |det J| over the parameter box, i.e. the integral of |det J| over
+// [0,1]^3: 5-point Gauss-Legendre in every knot span of every direction
+// (exact for the polynomial det J of a block up to degree 3 per direction).
+double mean_abs_det(const Block& b) {
+  const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+  const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                        0.2369268850561891};
+  std::vector<double> br[3];
+  for (int k = 0; k < 3; ++k) br[k] = breakpoints(b.B[k]);
+  double sum = 0;
+  for (size_t i = 0; i + 1 < br[0].size(); ++i)
+    for (size_t j = 0; j + 1 < br[1].size(); ++j)
+      for (size_t k = 0; k + 1 < br[2].size(); ++k) {
+        const double h[3] = {br[0][i + 1] - br[0][i], br[1][j + 1] - br[1][j], br[2][k + 1] - br[2][k]};
+        for (int a = 0; a < 5; ++a)
+          for (int c = 0; c < 5; ++c)
+            for (int e = 0; e < 5; ++e) {
+              const double p[3] = {br[0][i] + 0.5 * h[0] * (gx[a] + 1), br[1][j] + 0.5 * h[1] * (gx[c] + 1),
+                                   br[2][k] + 0.5 * h[2] * (gx[e] + 1)};
+              double phi[3], J[3][3];
+              block_eval(b, p, phi, J, nullptr);
+              sum += gw[a] * gw[c] * gw[e] * 0.125 * h[0] * h[1] * h[2] * std::fabs(det3(J));
+            }
+      }
+  return sum;
+}
+
+// §5.4, singular Jacobian at the entry point (Eq. 22): where |det J(p_in)|
+// is below tau_det = 1e-6 times the block's mean |det J|, neither Newton nor
+// the ODE's linear system can start at the entry, so the block is "shrunk":
+// the entry moves a distance delta = 1e-4 diag along the ray,
+// g~_in = g_in + delta d (reading: the paper adds the step to the entry in
+// G, so its direction is the ray's), and p~_in solves phi(p) = g~_in by
+// Newton (§5.1) started at x_0 = p_in + eps (p_out - p_in) / |p_out - p_in|
+// with eps = 1e-4 (Eq. 22).  A pair no longer than delta, or whose new
+// entry does not invert inside its block, is dropped.  Returns the pairs;
+// *shrunk counts the moved entries, *dropped the dropped pairs.
+std::vector<Pair> shrink_singular_entries(const Volume& V, const double o[3], const double d[3], double newton_tol,
+                                          const std::vector<Pair>& in, int* shrunk, int* dropped) {
+  std::vector<Pair> out;
+  const double delta = 1e-4 * V.diag, eps = 1e-4;
+  for (Pair pr : in) {
+    const Block& b = V.blocks[pr.block];
+    double phi[3], J[3][3];
+    block_eval(b, pr.p_in, phi, J, nullptr);
+    if (!(std::fabs(det3(J)) < 1e-6 * b.mean_abs_det)) {
+      out.push_back(pr);
+      continue;
+    }
+    if (shrunk) ++*shrunk;
+    if (!(pr.t_out - pr.t_in > delta)) {
+      if (dropped) ++*dropped;
+      continue;
+    }
+    double dir[3] = {pr.p_out[0] - pr.p_in[0], pr.p_out[1] - pr.p_in[1], pr.p_out[2] - pr.p_in[2]};
+    const double nd = norm3(dir);
+    double x0[3], g[3], q[3];
+    for (int r = 0; r < 3; ++r) x0[r] = pr.p_in[r] + (nd > 0 ? eps * dir[r] / nd : 0.0);
+    pr.t_in += delta;
+    for (int r = 0; r < 3; ++r) g[r] = o[r] + pr.t_in * d[r];
+    if (invert_point(b, g, x0, newton_tol * V.diag, 100, q) < 0) {
+      if (dropped) ++*dropped;
+      continue;
+    }
+    for (int r = 0; r < 3; ++r) pr.p_in[r] = q[r];
+    out.push_back(pr);
+  }
+  return out;
+}
+
 void render_pixel(const Volume& V, const TF& tf, const Params& P, const Camera& cam, int W, int H,
                   int x, int y, double out[4], PixelStats& st) {
   double o[3], d[3];
@@ -1085,6 +1159,7 @@ void render_pixel(const Volume& V, const TF& tf, const Params& P, const Camera& 
   int um = 0;
   std::vector<Pair> pairs = (P.near_clip > 0 || P.n_cut > 0) ? clip_pairs(V, P, cam, o, d, hits, &um)
                                                               : pair_hits(hits, &um);
+  pairs = shrink_singular_entries(V, o, d, P.newton_tol, pairs, &st.shrunk, &um);
   st.npairs = (int)pairs.size();
   st.unmatched = um;
   Accum acc;
@@ -1189,7 +1264,7 @@ typedef struct {
 
 typedef struct { double t; double p[3]; int block, face, front; } orc_hit;
 typedef struct { int block; double t_in, t_out; double p_in[3], p_out[3]; } orc_pair;
-typedef struct { int npairs, unmatched, newton_fail, nsamples, rk_steps; } orc_pixel_stats;
+typedef struct { int npairs, unmatched, newton_fail, nsamples, rk_steps, shrunk; } orc_pixel_stats;
 
 void* orc_volume_create(const orc_block_desc* blocks, int n_blocks, int mode, char* err, int errlen) {
   auto fail = [&](const char* m) -> void* {
@@ -1231,6 +1306,7 @@ void* orc_volume_create(const orc_block_desc* blocks, int n_blocks, int mode, ch
   }
   double dg[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
   V->diag = norm3(dg);
+  for (Block& b : V->blocks) b.mean_abs_det = mean_abs_det(b);
   // pieces of the 6 faces of every block
   for (int bi = 0; bi < n_blocks; ++bi) {
     const Block& b = V->blocks[bi];
@@ -1360,7 +1436,7 @@ int orc_pixel_pairs(void* v, const orc_camera* c, int W, int H, int x, int y, in
   double o[3], d[3];
   orc_ray(c, W, H, x, y, o, d);
   std::vector<Hit> h = ray_hits(*(Volume*)v, o, d);
-  std::vector<Pair> p = pair_hits(h, unmatched);
+  std::vector<Pair> p = shrink_singular_entries(*(Volume*)v, o, d, 1e-13, pair_hits(h, unmatched), nullptr, unmatched);
   for (int i = 0; i < (int)p.size() && i < cap; ++i) {
     out[i].block = p[i].block; out[i].t_in = p[i].t_in; out[i].t_out = p[i].t_out;
     for (int r = 0; r < 3; ++r) { out[i].p_in[r] = p[i].p_in[r]; out[i].p_out[r] = p[i].p_out[r]; }
@@ -1435,7 +1511,50 @@ int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* 
         if (stats) {
           orc_pixel_stats& s = stats[q];
           s.npairs = st.npairs; s.unmatched = st.unmatched; s.newton_fail = st.newton_fail;
-          s.nsamples = st.nsamples; s.rk_steps = st.rk_steps;
+          s.nsamples = st.nsamples; s.rk_steps = st.rk_steps; s.shrunk = st.shrunk;
+        }
+      }
+    }
+  };
+  if (n_threads <= 1) {
+    work();
+  } else {
+    std::vector<std::thread> th;
+    for (int i = 0; i < n_threads; ++i) th.emplace_back(work);
+    for (auto& x : th) x.join();
+  }
+  return 0;
+}
+
+// Entry/exit pairs (§4.1 intersections, Alg. 2, singular entries moved as
+// §5.4 says) of the pixels [x0,x1) x [y0,y1) of a W x H image, without
+// cutting planes: count[q], and for slot k
+// < cap pairs[(k * npx + q) * 8 + (p_in[3], t_in, p_out[3], t_out)] and
+// block[k * npx + q], q = (y - y0)(x1 - x0) + (x - x0).  Multithreaded as
+// orc_render.  Returns 0.
+int orc_window_pairs(void* v, const orc_camera* c, int W, int H, int x0, int x1, int y0, int y1, int n_threads,
+                     int cap, int* count, double* pairs, int* block) {
+  const Volume* V = (const Volume*)v;
+  const int w = x1 - x0, h = y1 - y0;
+  const long npx = (long)w * h;
+  std::atomic<long> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const long c0 = next.fetch_add(16);
+      if (c0 >= npx) break;
+      for (long q = c0; q < c0 + 16 && q < npx; ++q) {
+        double o[3], d[3];
+        orc_ray(c, W, H, x0 + (int)(q % w), y0 + (int)(q / w), o, d);
+        int um = 0;
+        std::vector<Pair> pr = shrink_singular_entries(*V, o, d, 1e-13, pair_hits(ray_hits(*V, o, d), &um),
+                                                       nullptr, &um);
+        count[q] = (int)pr.size();
+        for (int k = 0; k < (int)pr.size() && k < cap; ++k) {
+          double* e = pairs + ((size_t)k * npx + q) * 8;
+          for (int r = 0; r < 3; ++r) { e[r] = pr[k].p_in[r]; e[4 + r] = pr[k].p_out[r]; }
+          e[3] = pr[k].t_in;
+          e[7] = pr[k].t_out;
+          block[(size_t)k * npx + q] = pr[k].block;
         }
       }
     }
@@ -1458,6 +1577,21 @@ int orc_render(void* v, const orc_tf* t, const orc_camera* c, const orc_params* 
 int orc_table1_ex(int method, double ds, double c, double rf_tol, double* err, long* newton_iters);
 int orc_table1(int method, double ds, double c, double rf_tol, double* err) {
   return orc_table1_ex(method, ds, c, rf_tol, err, nullptr);
+}
+
+// One implicit Euler step on the analytic map of the Table 1 harness from p
+// with step h, Newton capped at max_it iterations to |dz| <= tol; g_in and d
+// are the harness's.  pn receives the new point; returns irk1_step's value
+// (-1: the §5.4 boundary step was taken).  For pinning that step directly.
+int orc_t1_irk1_step(const double* p, double h, double c, double tol, int max_it, double* pn) {
+  const double p_in[3] = {0.0, 0.3, 0.5}, p_out[3] = {1.0, 0.7, 0.5};
+  double g_in[3], g_out[3], J[3][3];
+  t1_map(p_in, g_in, J);
+  t1_map(p_out, g_out, J);
+  double d[3] = {g_out[0] - g_in[0], g_out[1] - g_in[1], g_out[2] - g_in[2]};
+  const double L = norm3(d);
+  for (int r = 0; r < 3; ++r) d[r] /= L;
+  return irk1_step(t1_map2, p, h, g_in, d, c, tol, max_it, pn);
 }
 
 // As orc_table1; newton_iters (if not NULL) receives the Newton iterations

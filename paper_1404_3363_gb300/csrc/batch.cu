@@ -238,6 +238,8 @@ ivv::DevVolume pool_volume(const ivv_batch* b) {
   V.faces = b->d_faces;
   V.faces64 = b->d_faces64;
   V.diag = 0.f;
+  V.max_frags = ivv::kMaxFrags;
+  V.max_newton = 16;
   return V;
 }
 
@@ -390,6 +392,8 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
     if (req[i].width <= 0 || req[i].height <= 0) return bfail(IVV_ERR_INVALID_ARG, "request size must be positive");
     if (req[i].volume->hv.P != req[0].volume->hv.P)
       return bfail(IVV_ERR_UNSUPPORTED, "the volumes of a batch must share one common degree P");
+    if (req[i].volume->hv.any_singular)
+      return bfail(IVV_ERR_UNSUPPORTED, "batches take volumes without singular faces (render those with ivv_render)");
   }
   // shared parameters (diag 1: ds is resolved per request below)
   ivv_render_params p;

@@ -81,7 +81,7 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
           nr = patch_roots<P, R>(pq, hull_pad, ra, rb, iters);
         }
         for (int k = 0; k < nr; ++k) {
-          R a = clamp01r(ra[k]), b2 = clamp01r(rb[k]);
+          const R a = ra[k], b2 = rb[k];     // within the acceptance tolerance of the patch
           R t, pp[3], cosang;
           bool front;
           if constexpr (sizeof(R) == 8)
@@ -89,16 +89,14 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
           else
             make_fragment<P, R, float4>(&face32[(size_t)f * NN], org, m, pa0, pa1, pb0, pb1, o, d, a, b2, t, front, pp,
                                         cosang);
-          if (sizeof(R) == 4 && mixed && cosang < R(0.2)) {
+          if (sizeof(R) == 4 && mixed && cosang < R(kPolishCos)) {
             double a64 = a, b64 = b2, t64 = t, o64[3], d64[3];
             make_ray<double>(c64, px, py, o64, d64);
             refine_hit_fp64<P, Dbl4>(&face64[(size_t)f * NN], m64.org, o64, d64, a64, b64, t64);
-            a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
-            b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
             t = R(t64);
             const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-            pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
-            pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+            pp[ad] = R(std::fmin(std::fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+            pp[bd] = R(std::fmin(std::fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
           }
           if (!(t > R(0)) || n >= kMaxFrags) continue;
           tt[n] = t;

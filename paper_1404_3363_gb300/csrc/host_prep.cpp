@@ -327,6 +327,7 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
     }
     B.elem_off = hv.n_elems();
     B.tau_det = 0.f;
+    B.sing_faces = 0;
     B.uniform = 0;
     B.mode = mode;
     for (int k = 0; k < 3; ++k) {
@@ -466,8 +467,54 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
                 sum += dj;
                 ++cnt;
               }
-    hv.mean_abs_det[b] = sum / cnt;
+    (void)sum;
+    (void)cnt;
+    // mean |det J| over [0,1]^3 (the block's volume in G): 5-point
+    // Gauss-Legendre per knot span and direction, exact for det J
+    static const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                                 0.9061798459386640};
+    static const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                                 0.2369268850561891};
+    double vol = 0;
+    for (int ew = 0; ew < B.nseg[2]; ++ew)
+      for (int ev = 0; ev < B.nseg[1]; ++ev)
+        for (int eu = 0; eu < B.nseg[0]; ++eu) {
+          const double h[3] = {bu[eu + 1] - bu[eu], bv[ev + 1] - bv[ev], bw[ew + 1] - bw[ew]};
+          for (int a = 0; a < 5; ++a)
+            for (int c = 0; c < 5; ++c)
+              for (int e = 0; e < 5; ++e) {
+                double p[3] = {bu[eu] + 0.5 * h[0] * (gx[a] + 1), bv[ev] + 0.5 * h[1] * (gx[c] + 1),
+                               bw[ew] + 0.5 * h[2] * (gx[e] + 1)};
+                double phi[3], J[3][3];
+                host_eval(hv, b, p, phi, J, nullptr);
+                vol += gw[a] * gw[c] * gw[e] * 0.125 * h[0] * h[1] * h[2] * std::fabs(det3(J));
+              }
+        }
+    hv.mean_abs_det[b] = vol;
     B.tau_det = (float)(1e-6 * hv.mean_abs_det[b]);
+    // faces on which det J comes within 1e-2 of the mean (9 x 9 points per
+    // face element, edges included): entries there may need §5.4's shrink,
+    // whose threshold is 1e-6 of the mean
+    B.sing_faces = 0;
+    const double* br[3] = {bu, bv, bw};
+    for (int f = 0; f < 6; ++f) {
+      const int nd = f >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+      double mn = 1e300;
+      for (int sa = 0; sa < B.nseg[ad]; ++sa)
+        for (int sb = 0; sb < B.nseg[bd]; ++sb)
+          for (int i = 0; i <= 8; ++i)
+            for (int j = 0; j <= 8; ++j) {
+              double p[3];
+              p[nd] = (f & 1) ? 1.0 : 0.0;
+              p[ad] = br[ad][sa] + (br[ad][sa + 1] - br[ad][sa]) * i / 8.0;
+              p[bd] = br[bd][sb] + (br[bd][sb + 1] - br[bd][sb]) * j / 8.0;
+              double phi[3], J[3][3];
+              host_eval(hv, b, p, phi, J, nullptr);
+              mn = std::min(mn, std::fabs(det3(J)));
+            }
+      if (mn < 1e-2 * hv.mean_abs_det[b]) B.sing_faces |= 1 << f;
+    }
+    if (B.sing_faces) hv.any_singular = true;
   }
 
   // default scalar range

@@ -297,11 +297,19 @@ IVV_HD void bilinear_start(const Patch2<P, R>& q, R& a, R& b) {
 // patch, and not a duplicate of a root already found.
 // Returns false if (a,b) lies outside the sub-patch (the caller then looks
 // for the sub-patch's own root in smaller pieces).
+// With in_box = false (the uncertified smallest pieces of the subdivision
+// search, which may hold two roots on either side of a fold of the
+// projected patch) a root anywhere inside the patch is kept: Newton from the
+// piece's starts may reach the second root of the fold just beyond the
+// piece, and the neighbouring piece's starts may all reach the first one.
+// Copies of one root found from several pieces are merged here and, as
+// fragments of equal facing, by the depth sort.
 template <typename R>
-IVV_HD bool accept_root(R a, R b, R a0, R a1, R b0, R b1, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& nr) {
+IVV_HD bool accept_root(R a, R b, R a0, R a1, R b0, R b1, R ra[kMaxPatchRoots], R rb[kMaxPatchRoots], int& nr,
+                        bool in_box = true) {
   const R wa = a1 - a0, wb = b1 - b0;
   const R ea = RootEps<R>::accept / wa, eb = RootEps<R>::accept / wb;
-  if (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb) return false;
+  if (in_box && (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb)) return false;
   const R ga = a0 + a * wa, gb = b0 + b * wb;
   const R e = RootEps<R>::accept;
   if (ga < -e || ga > R(1) + e || gb < -e || gb > R(1) + e) return true;
@@ -399,7 +407,7 @@ __host__ __device__ __noinline__ int patch_roots_split(const Patch2<P, R>* q0p, 
       for (int s0 = 0; s0 < 5; ++s0) {
         R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
         R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
-        if (newton2<P, R>(q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr);
+        if (newton2<P, R>(q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr, false);
       }
       split = false;
     }
@@ -550,6 +558,10 @@ IVV_HD bool ray_obb(const R o[3], const R d[3], const FaceMeta& m, R pad) {
 }
 
 // Fragment of a root (a,b) of face `m`: depth t, facing, block parameter point.
+// (a,b) may lie outside the patch by the root acceptance tolerance (a root on
+// the seam of two patches, found by both): the patch polynomial is evaluated
+// there as it is, and only the block parameter point is clamped to [0,1]^3,
+// so both copies of a seam root carry the same accurate point.
 template <int P, typename R, typename V4>
 IVV_HD void make_fragment(const V4* cp, const R org[3], const FaceMeta& m, const R pa0, const R pa1, const R pb0,
                           const R pb1, const R o[3], const R d[3], R a, R b, R& t, bool& front, R pp[3], R& cosang) {
@@ -564,9 +576,15 @@ IVV_HD void make_fragment(const V4* cp, const R org[3], const FaceMeta& m, const
   front = (m.face & 1) ? (dn < R(0)) : (dn > R(0));
   const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
   pp[nd] = (m.face & 1) ? R(1) : R(0);
-  pp[ad] = pa0 + a * (pa1 - pa0);
-  pp[bd] = pb0 + b * (pb1 - pb0);
+  pp[ad] = clamp01r(pa0 + a * (pa1 - pa0));
+  pp[bd] = clamp01r(pb0 + b * (pb1 - pb0));
 }
+
+// Mixed precision: hits where |cos| of the ray and the face normal is below
+// this get the FP64 polish.  An FP32 hit is accurate to about 4e-6 / |cos|
+// in the block parameters (positions of magnitude ~10 carry ~1e-6 of
+// rounding), so 0.35 keeps every hit within 1e-5.
+constexpr float kPolishCos = 0.35f;
 
 // FP64 polish of a hit near a silhouette: Newton on S(a,b) - o - t d = 0
 // with the FP64 face patch (control points relative to org).
@@ -635,13 +653,24 @@ IVV_HD int pair_fragments(int n, const R* t, const unsigned* m, const R (*pp)[3]
     }
     ord[j] = (unsigned char)i;
   }
+  // duplicates: of two copies of one hit (a seam of two patches or an edge
+  // of two faces, both within the root acceptance tolerance) keep the one
+  // with fewer parameter coordinates on the block boundary -- the copy from
+  // the face that holds the hit, not the one clamped onto the edge
+  auto on_bound = [](const R* p) {
+    return (int)(p[0] == R(0) || p[0] == R(1)) + (int)(p[1] == R(0) || p[1] == R(1)) +
+           (int)(p[2] == R(0) || p[2] == R(1));
+  };
   unsigned used = 0;
   for (int i = 0; i < n; ++i) {
     const int a = ord[i];
     for (int j = 0; j < i; ++j) {
       const int b = ord[j];
       if (!((used >> j) & 1u) && (m[a] >> 4) == (m[b] >> 4) && (m[a] & 1u) == (m[b] & 1u) && t[a] - t[b] <= tau_dup) {
-        used |= 1u << i;
+        if (on_bound(pp[a]) < on_bound(pp[b]))
+          used |= 1u << j;
+        else
+          used |= 1u << i;
         break;
       }
     }

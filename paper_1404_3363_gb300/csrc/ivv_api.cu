@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "ivv_device.cuh"
@@ -135,6 +134,8 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   V.faces = v->d_faces;
   V.faces64 = v->d_faces64;
   V.diag = (float)v->hv.diag;
+  V.max_frags = v->lim_frags;
+  V.max_newton = v->lim_newton;
   return V;
 }
 
@@ -236,10 +237,10 @@ ivv_status resolve_params_diag(double diag, const ivv_render_params* in, ivv_ren
   if (p.method != IVV_METHOD_ODE && p.method != IVV_METHOD_RF) return fail(IVV_ERR_INVALID_ARG, "bad method");
   if (p.use_mlp_guess < IVV_GUESS_CENTER || p.use_mlp_guess > IVV_GUESS_CHORD)
     return fail(IVV_ERR_INVALID_ARG, "bad initial-guess mode");
-  if (p.method == IVV_METHOD_ODE && p.use_mlp_guess != IVV_GUESS_CENTER)
-    return fail(IVV_ERR_INVALID_ARG, "initial guesses apply to the RF method");
-  if (p.method == IVV_METHOD_RF && p.precision != IVV_PREC_FP32)
-    return fail(IVV_ERR_UNSUPPORTED, "the RF method runs in FP32 precision");
+  if (p.method == IVV_METHOD_ODE && p.use_mlp_guess == IVV_GUESS_CHORD)
+    return fail(IVV_ERR_INVALID_ARG, "the chord guess applies to the RF method");
+  if (p.method == IVV_METHOD_RF && p.precision == IVV_PREC_FP64)
+    return fail(IVV_ERR_UNSUPPORTED, "the RF method runs in FP32 or MIXED precision");
   if (p.rk_method < IVV_RK_BS32 || p.rk_method > IVV_RK_IMPLICIT_EULER) return fail(IVV_ERR_INVALID_ARG, "bad rk_method");
   if (p.rk_method != IVV_RK_BS32 && p.method != IVV_METHOD_ODE)
     return fail(IVV_ERR_INVALID_ARG, "rk_method applies to the ODE method");
@@ -339,7 +340,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   sw.gboxes = (int4*)(ws + L.gboxes);
   sw.items = (int2*)(ws + L.items);
   sw.slow = (int*)(ws + L.slow);
-  sw.cap = (int)std::min<size_t>((size_t)ivv::kItemsPerPixel * npix, 0x7fffffff);
+  sw.cap = (int)std::min<size_t>((size_t)v->lim_items * npix, 0x7fffffff);
   sw.n_items = (int*)(ws + L.counters) + ivv::kItemCounter;
   sw.frag_tp = ws + L.frag_tp;
   sw.frag_meta = (unsigned*)(ws + L.frag_meta);
@@ -365,10 +366,35 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                       (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
                       (int*)(ws + L.counters), out_zero, clip, sw.tile_flag, v->d_stats, s);
-  if (clip.on)
+  // fix-up solves of stage 2: ends moved onto cutting or near-clip planes
+  // (§5.5) and entries with a singular Jacobian (§5.4), the entries without
+  // chord context from the learned guess when it is asked for
+  const bool learned = p.use_mlp_guess == IVV_GUESS_MLP && v->guess_ready && (clip.on || v->hv.any_singular);
+  if (learned) {
+    ivv::GuessList gl;
+    gl.g = (float4*)(ws + L.frag_tp);                 // the fragment lists are dead after K4
+    gl.p = gl.g + (size_t)ivv::kMaxPairs * npix;
+    gl.gidx = (int*)(ws + L.frag_meta);
+    gl.blk = gl.gidx + (size_t)ivv::kMaxPairs * npix;
+    gl.n = (int*)(ws + L.counters) + ivv::kGuessCounter;
+    ivv::launch_guess_mark<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
+                              (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                              (const int*)(ws + L.counters), v->hv.any_singular, mixed, gl, v->d_stats, v->num_sms,
+                              s);
+    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, gl.g, gl.blk, gl.n, 0, gl.p, v->num_sms, s);
     ivv::launch_clip_solve<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                               (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
-                              (const int*)(ws + L.counters), v->d_stats, v->num_sms, s);
+                              (const int*)(ws + L.counters), mixed, &gl, v->d_stats, v->num_sms, s);
+  } else if (clip.on) {
+    ivv::launch_clip_solve<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
+                              (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
+                              (const int*)(ws + L.counters), mixed, nullptr, v->d_stats, v->num_sms, s);
+  }
+  if (v->hv.any_singular)
+    ivv::launch_entry_fix<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
+                             (const int*)(ws + L.pair_block), (const int*)(ws + L.pair_count),
+                             (const int*)(ws + L.active), (const int*)(ws + L.counters), mixed, v->d_stats, v->num_sms,
+                             s);
   if (timing) IVV_CUDA(cudaEventRecord(v->ev[3], s));
   IVV_CUDA(cudaGetLastError());
   return IVV_OK;
@@ -430,15 +456,15 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
   a.c = (float)p.c;
   a.early_alpha = (float)p.early_alpha;
   a.K = p.supersample_k;
-  a.max_steps = 200000;
+  a.max_steps = v->lim_rk_steps;
   a.max_step_samples = 8;
   a.npix = (int)npix;
   const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
   const bool mixed = p.precision == IVV_PREC_MIXED;
+  if (p.use_mlp_guess == IVV_GUESS_MLP && !v->guess_ready)
+    return fail(IVV_ERR_INVALID_ARG, "IVV_GUESS_MLP needs ivv_train_guess or ivv_set_guess_weights first");
   if (p.method == IVV_METHOD_RF) {
-    if (p.use_mlp_guess == IVV_GUESS_MLP && !v->guess_ready)
-      return fail(IVV_ERR_INVALID_ARG, "IVV_GUESS_MLP needs ivv_train_guess or ivv_set_guess_weights first");
-    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     const float4* pin = (const float4*)(ws + L.pair_in);
     const float4* pout = (const float4*)(ws + L.pair_out);
@@ -471,7 +497,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
       ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->num_sms, s);
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,
-                          stats, v->num_sms, s);
+                          stats, mixed, v->num_sms, s);
     ivv::launch_rf_composite(tf, p.supersample_k, (float)p.early_alpha, pin, pout, pblk, pcnt, act, counters, off,
                              (int)npix, (float)p.ds, tail_eps, total, srho, (float4*)out, v->d_stats, stats,
                              v->num_sms, s);
@@ -483,7 +509,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     return IVV_OK;
   }
   if (fp64) {
-    st = run_surface_pairs<double>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    st = run_surface_pairs<double>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     ivv::DevCamera<double> c64 = dev_camera<double>(F);
     if (V.P == 2)
@@ -497,7 +523,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                                  (const int*)(ws + L.active), (const int*)(ws + L.counters),
                                  (int*)(ws + L.counters) + ivv::kQueueHeadOff, (float4*)out, v->d_stats, v->num_sms, s);
   } else if (p.rk_method == IVV_RK_IMPLICIT_EULER) {
-    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     const ivv::DevCamera<float> c32 = dev_camera<float>(F);
     const float4* pin = (const float4*)(ws + L.pair_in);
@@ -513,7 +539,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                             (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
                             (float4*)out, v->d_stats, v->num_sms, s);
   } else if (p.rk_method != IVV_RK_BS32) {
-    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     const ivv::DevCamera<float> c32 = dev_camera<float>(F);
     const ivv::RkTableau T = rk_tableau(p.rk_method);
@@ -530,7 +556,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
                              (float4*)out, v->d_stats, v->num_sms, s);
   } else {
-    st = run_surface_pairs<float>(v, F, p, ws, L, ivv::kMaxPairs, (float4*)out, s);
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
     if (st != IVV_OK) return st;
     const ivv::DevCamera<float> c32 = dev_camera<float>(F);
     const float4* pin = (const float4*)(ws + L.pair_in);
@@ -856,24 +882,17 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;   // 12 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  In host code
-// the array's name only stands for it, so the address is looked up once per
-// device (with that device current) and cached.
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name only stands for it, so the address is looked up
+// with that device current.  The lookup is repeated on every call (it is a
+// table read once the module is loaded): a cached address would outlive a
+// cudaDeviceReset or a re-created primary context.  The first call on a
+// device may load the library's device code, so it belongs before any stream
+// capture.
 ivv_status noalloc_scratch(void** out) {
-  int dev = 0;
-  IVV_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(IVV_ERR_UNSUPPORTED, "device index too large for the scratch table");
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    IVV_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* ptr = nullptr;
+  IVV_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  *out = ptr;
   return IVV_OK;
 }
 
@@ -886,6 +905,9 @@ ivv_status ivv_render_noalloc(ivv_volume* v, const ivv_camera* cam, const ivv_re
   if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
   if (width <= 0 || height <= 0) return fail(IVV_ERR_INVALID_ARG, "width and height must be positive");
   const int precision = params ? params->precision : IVV_PREC_FP32;
+  if (params && params->method == IVV_METHOD_RF)
+    return fail(IVV_ERR_UNSUPPORTED, "ivv_render_noalloc renders with the ODE method only (the RF method sizes its "
+                                     "sample buffers from a read-back and allocates them)");
   const size_t need = layout(v->hv.n_faces(), (size_t)width * height,
                              precision == IVV_PREC_FP64 ? sizeof(ivv::Dbl4) : sizeof(float4)).total;
   if (need > kNoAllocScratchBytes)
@@ -923,7 +945,7 @@ ivv_status ivv_render_pairs(ivv_volume* v, const ivv_camera* cam, const ivv_rend
     ws = (char*)v->own_ws;
   }
   v->last_stream = s;
-  const int mp = std::min(max_pairs, ivv::kMaxPairs);
+  const int mp = std::min(max_pairs, v->lim_pairs);
   st = run_surface_pairs<float>(v, F, p, ws, L, mp, nullptr, s);
   if (st != IVV_OK) return st;
   ivv::launch_export_pairs((int)npix, max_pairs, false, ws + L.pair_in, ws + L.pair_out,
@@ -1064,7 +1086,7 @@ ivv_status ivv_invert_points(ivv_volume* v, int n, const float* g, const int* bl
   cam.H = 1;
   cam.ortho = 1;
   ivv::launch_rf_newton(dev_volume(v), cam, 0.f, tol, v->d_count, (const float4*)g, block_of, (const float4*)p_out,
-                        nullptr, (float4*)p_out, iters, v->d_stats, false, v->num_sms, s);
+                        nullptr, (float4*)p_out, iters, v->d_stats, false, false, v->num_sms, s);
   IVV_CUDA(cudaGetLastError());
   return IVV_OK;
 }
@@ -1194,6 +1216,8 @@ void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->isect_items = d.isect_items;
   out->isect_split = d.isect_split;
   out->rho_evals = d.rho_evals;
+  out->entry_shrinks = d.entry_shrinks;
+  out->entry_newton = d.entry_newton;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;
@@ -1206,6 +1230,55 @@ ivv_status ivv_reset_stats(ivv_volume* v) {
   if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
   IVV_CUDA(cudaMemsetAsync(v->d_stats, 0, sizeof(ivv::DevStats), v->last_stream));
   IVV_CUDA(cudaStreamSynchronize(v->last_stream));
+  v->seen_overflow = v->seen_cap = 0;
+  return IVV_OK;
+}
+
+ivv_status ivv_set_limits(ivv_volume* v, const ivv_limits* in) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  ivv_limits l = {ivv::kMaxFrags, ivv::kMaxPairs, ivv::kItemsPerPixel, 200000, 16};
+  if (in) l = *in;
+  if (l.max_frags < 1 || l.max_frags > ivv::kMaxFrags) return fail(IVV_ERR_INVALID_ARG, "max_frags must be in 1..32");
+  if (l.max_pairs < 1 || l.max_pairs > ivv::kMaxPairs) return fail(IVV_ERR_INVALID_ARG, "max_pairs must be in 1..16");
+  if (l.items_per_pixel < 1 || l.items_per_pixel > ivv::kItemsPerPixel)
+    return fail(IVV_ERR_INVALID_ARG, "items_per_pixel must be in 1..16");
+  if (l.max_rk_steps < 1) return fail(IVV_ERR_INVALID_ARG, "max_rk_steps must be >= 1");
+  if (l.max_newton < 1 || l.max_newton > 64) return fail(IVV_ERR_INVALID_ARG, "max_newton must be in 1..64");
+  v->lim_frags = l.max_frags;
+  v->lim_pairs = l.max_pairs;
+  v->lim_items = l.items_per_pixel;
+  v->lim_rk_steps = l.max_rk_steps;
+  v->lim_newton = l.max_newton;
+  return IVV_OK;
+}
+
+ivv_status ivv_get_limits(const ivv_volume* v, ivv_limits* out) {
+  if (!v || !out) return fail(IVV_ERR_INVALID_ARG, "volume or output is NULL");
+  out->max_frags = v->lim_frags;
+  out->max_pairs = v->lim_pairs;
+  out->items_per_pixel = v->lim_items;
+  out->max_rk_steps = v->lim_rk_steps;
+  out->max_newton = v->lim_newton;
+  return IVV_OK;
+}
+
+ivv_status ivv_check_frame(ivv_volume* v) {
+  if (!v) return fail(IVV_ERR_INVALID_ARG, "volume is NULL");
+  IVV_CUDA(cudaStreamSynchronize(v->last_stream));
+  ivv::DevStats d;
+  IVV_CUDA(cudaMemcpy(&d, v->d_stats, sizeof(d), cudaMemcpyDeviceToHost));
+  const unsigned long long ov = d.abuf_overflow + d.pair_overflow, cap = d.step_cap + d.rf_unconverged;
+  const unsigned long long new_ov = ov - std::min(ov, v->seen_overflow), new_cap = cap - std::min(cap, v->seen_cap);
+  v->seen_overflow = ov;
+  v->seen_cap = cap;
+  if (new_ov)
+    return fail(IVV_ERR_ABUF_OVERFLOW, std::to_string(new_ov) + " fragments, candidates or pairs dropped (" +
+                                           std::to_string(d.abuf_overflow) + " fragment/candidate and " +
+                                           std::to_string(d.pair_overflow) + " pair drops since the last reset)");
+  if (new_cap)
+    return fail(IVV_ERR_NONCONVERGED, std::to_string(new_cap) + " capped iterations (" + std::to_string(d.step_cap) +
+                                          " pairs at the RK step cap, " + std::to_string(d.rf_unconverged) +
+                                          " RF samples off tolerance since the last reset)");
   return IVV_OK;
 }
 

@@ -130,6 +130,8 @@ struct DevVolume {
   const FaceMeta* faces;
   const FaceMeta64* faces64;
   float diag;
+  int max_frags;          // fragment slots in use per pixel (<= kMaxFrags)
+  int max_newton;         // Newton iterations of a per-point inversion (RF method, point location)
 };
 
 struct DevTF {
@@ -143,7 +145,7 @@ struct DevTF {
 struct DevStats {
   unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
       isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap, rf_newton_iters,
-      rf_unconverged, isect_items, isect_split, rho_evals;
+      rf_unconverged, isect_items, isect_split, rho_evals, entry_shrinks, entry_newton;
   unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
   unsigned int pad;
 };
@@ -640,7 +642,12 @@ void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCame
 // pair_block (kSolveIn / kSolveOut, with the chord guess in the pair record)
 // and solved by the clip fix-up kernel before stage 3.
 constexpr int kMaxCutPlanes = IVV_MAX_CUT_PLANES;
-constexpr int kSolveIn = 1 << 30, kSolveOut = 1 << 29, kBlockMask = (1 << 29) - 1;
+// kGuessIn marks an entry without chord context (an entry on the near plane
+// or a moved singular entry), whose Newton may start from the learned guess;
+// kShrunk an entry moved by §5.4's singular-entry rule.
+constexpr int kSolveIn = 1 << 30, kSolveOut = 1 << 29, kGuessIn = 1 << 28, kShrunk = 1 << 27,
+              kBlockMask = (1 << 27) - 1;
+constexpr int kGuessCounter = 11;    // counters slot: entries in the learned-guess list
 template <typename R>
 struct ClipArgs {
   int on;                       // any plane active
@@ -651,10 +658,37 @@ struct ClipArgs {
   DevCamera<R> cam;             // the pixels' rays
 };
 
+// Learned initial guesses of the fix-up solves: entries flagged kGuessIn are
+// listed (world point, block) for the guess network; guess_p receives its
+// parameter guesses, gidx [kMaxPairs][npix] the list index of each slot.
+struct GuessList {
+  float4* g;        // [n] world points (x, y, z, 0)
+  int* blk;         // [n] blocks
+  float4* p;        // [n] parameter guesses
+  int* gidx;        // [kMaxPairs][npix]
+  int* n;           // list length (device counter)
+};
+
 template <typename R>
 void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
                        typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
-                       const int* n_active, DevStats* st, int num_sms, cudaStream_t s);
+                       const int* n_active, bool mixed, const GuessList* guess, DevStats* st, int num_sms,
+                       cudaStream_t s);
+
+// Lists the entries that take the learned guess (kGuessIn), first moving the
+// singular entries of flagged blocks (§5.4) when `singular` is set.
+template <typename R>
+void launch_guess_mark(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                       typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
+                       const int* n_active, bool singular, bool mixed, const GuessList& guess, DevStats* st,
+                       int num_sms, cudaStream_t s);
+
+// §5.4 (Eq. 22): entries with a singular Jacobian, in blocks with a flagged
+// face, move along the ray and get a new parameter point (k_pair.cu).
+template <typename R>
+void launch_entry_fix(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                      typename Vec4T<R>::type* pair_out, const int* pair_block, const int* pair_count,
+                      const int* active, const int* n_active, bool mixed, DevStats* st, int num_sms, cudaStream_t s);
 
 template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
@@ -740,7 +774,7 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
                       cudaStream_t s);
 void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
                       const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
-                      DevStats* st, bool stats, int num_sms, cudaStream_t s);
+                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s);
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                          float tail_eps, int cap, const float* srho, float4* out, DevStats* st,

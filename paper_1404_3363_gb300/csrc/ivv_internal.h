@@ -49,6 +49,7 @@ struct BlockInfo {
   float tau_det;      // |det J| below which MIXED precision solves in FP64
   int uniform;        // bit d set: breakpoints of direction d are i / nseg[d]
   int mode;           // IVV_SCALAR_* of the block's volume
+  int sing_faces;     // bit f set: det J comes close to 0 on face f (singular entries possible, §5.4)
 };
 
 // Host image of a prepared volume (see host_prep.cpp).
@@ -64,6 +65,7 @@ struct HostVolume {
   std::vector<FaceMeta> faces;
   std::vector<FaceMeta64> faces64;
   std::vector<double> mean_abs_det;
+  bool any_singular = false;       // some block has a face where det J comes close to 0
   double diag = 1.0;               // diagonal of the control-point bbox
   double def_lo = 0.0, def_hi = 1.0;   // default scalar range
   int n_elems() const { return (int)(elem.size() / (4 * (size_t)(P + 1) * (P + 1) * (P + 1))); }

@@ -364,10 +364,8 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
       ++steps;
       const bool capped = steps >= args.max_steps;
       if (err <= tol || hh <= hmin || capped) {
-        if (STATS) {
-          ++c_steps;
-          if (capped) ++c_cap;
-        }
+        if (STATS) ++c_steps;
+        if (capped) ++c_cap;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
           p0[r] = p[r];
@@ -498,6 +496,8 @@ __global__ void __launch_bounds__(128, 4) k5_integrate(DevVolume V, DevCamera<R>
       atomicAdd(&st->step_cap, c_cap);
       atomic_max_nonneg_float(&st->max_delta_p_bits, max_dp);
     }
+  } else if (c_cap) {
+    atomicAdd(&st->step_cap, c_cap);               // a cap counter: kept by every render
   }
 }
 

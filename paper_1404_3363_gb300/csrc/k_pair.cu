@@ -27,10 +27,10 @@ __device__ __forceinline__ int pair_pixel(size_t pix, size_t stride, R tau_dup,
                                           typename Vec4T<R>::type* __restrict__ pair_in,
                                           typename Vec4T<R>::type* __restrict__ pair_out, int* __restrict__ pair_block,
                                           int* __restrict__ pair_count, int max_pairs, float4* zero_out,
-                                          unsigned& um, unsigned& pov) {
+                                          unsigned& um, unsigned& pov, int max_frags = kMaxFrags) {
   typedef typename Vec4T<R>::type V4;
   int n = frag_count[pix];
-  n = n < kMaxFrags ? n : kMaxFrags;
+  n = n < max_frags ? n : max_frags;
   R t[kMaxFrags], pp[kMaxFrags][3];
   unsigned m[kMaxFrags];
   for (int i = 0; i < n; ++i) {
@@ -69,14 +69,14 @@ __device__ __forceinline__ int pair_pixel_clip(size_t pix, size_t stride, R tau_
                                                typename Vec4T<R>::type* __restrict__ pair_out,
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, float4* zero_out, unsigned& um, unsigned& pov,
-                                               const ClipArgs<R>& cl, int xw, int yw) {
+                                               const ClipArgs<R>& cl, int xw, int yw, int max_frags) {
   typedef typename Vec4T<R>::type V4;
   R o[3], d[3];
   make_ray<R>(cl.cam, cl.cam.x0 + xw, cl.cam.y0 + yw, o, d);
   R t_near = R(0);
   if (cl.near > R(0)) t_near = cl.near / (d[0] * cl.f[0] + d[1] * cl.f[1] + d[2] * cl.f[2]);
   int n0 = frag_count[pix];
-  n0 = n0 < kMaxFrags ? n0 : kMaxFrags;
+  n0 = n0 < max_frags ? n0 : max_frags;
   R t[kMaxFrags], pp[kMaxFrags][3];
   unsigned m[kMaxFrags];
   int n = 0;
@@ -140,7 +140,7 @@ __device__ __forceinline__ int pair_pixel_clip(size_t pix, size_t stride, R tau_
     ro.x = t1; ro.y = go[0]; ro.z = go[1]; ro.w = go[2];
     pair_in[o2] = ri;
     pair_out[o2] = ro;
-    pair_block[o2] = (int)(m[a] >> 4) | (new_in ? kSolveIn : 0) | (new_out ? kSolveOut : 0);
+    pair_block[o2] = (int)(m[a] >> 4) | (new_in ? kSolveIn : 0) | (new_out ? kSolveOut : 0) | (s_in ? kGuessIn : 0);
     ++kept;
   }
   pair_count[pix] = kept;
@@ -149,17 +149,33 @@ __device__ __forceinline__ int pair_pixel_clip(size_t pix, size_t stride, R tau_
 }
 
 // Newton for the world point g in block B from p (line search on |F|, p
-// clamped to [0,1]^3, §5.1); true when |phi(p) - g| <= tol.
-template <int P, typename R>
-__device__ __forceinline__ bool clip_newton(const DevVolume& V, const BlockInfo& B, const R g[3], R p[3], R tol) {
+// clamped to [0,1]^3, §5.1); true when |phi(p) - g| <= tol.  MIXED: the 3x3
+// solve switches to FP64 where |det J| < tau_det (counted in n64); iters
+// accumulates the iterations.
+template <int P, typename R, bool MIXED>
+__device__ __forceinline__ bool clip_newton(const DevVolume& V, const BlockInfo& B, const R g[3], R p[3], R tol,
+                                            unsigned long long& iters, unsigned long long& n64) {
   R phi[3], J[3][3], rc, F[3];
   eval_block<P, R, false>(V, B, p, phi, J, rc);
   for (int r = 0; r < 3; ++r) F[r] = phi[r] - g[r];
   R nF = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
   for (int it = 0; it < 50; ++it) {
     if (nF <= tol) return true;
+    ++iters;
     R rhs[3] = {-F[0], -F[1], -F[2]}, dx[3];
-    solve3<R>(J, rhs, dx);
+    const R det = solve3<R>(J, rhs, dx);
+    if constexpr (MIXED) {
+      if (fabs(det) < R(B.tau_det)) {
+        double Jd[3][3], bd[3], xd[3];
+        for (int r = 0; r < 3; ++r) {
+          bd[r] = rhs[r];
+          for (int k = 0; k < 3; ++k) Jd[r][k] = J[r][k];
+        }
+        solve3<double>(Jd, bd, xd);
+        for (int r = 0; r < 3; ++r) dx[r] = R(xd[r]);
+        ++n64;
+      }
+    }
     R lam = R(1);
     bool moved = false;
     for (int ls = 0; ls < 12 && !moved; ++ls, lam *= R(0.5)) {
@@ -187,20 +203,35 @@ __device__ __forceinline__ bool clip_newton(const DevVolume& V, const BlockInfo&
   return nF <= tol;
 }
 
+// Newton tolerance of the fix-up solves at world point g: 1e-6 diag (FP32)
+// or 1e-12 diag (FP64), plus the rounding of g itself.
+template <typename R>
+__device__ __forceinline__ R fixup_tol(const R g[3], float diag) {
+  const R tol = sizeof(R) == 4 ? R(1e-6) * R(diag) : R(1e-12) * R(diag);
+  const R m = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+  return tol + R(sizeof(R) == 4 ? 2e-7 : 1e-15) * m;
+}
+
 // The clip fix-up: one thread per active pixel solves the flagged ends of
 // its pairs; a pair whose end does not invert inside its block gets zero
-// length (skipped by stage 3).
-template <int P, typename R>
+// length (skipped by stage 3).  Newton starts: an entry listed for the
+// learned guess (kGuessIn, guess != NULL) first from the network's guess; then
+// from the guess in the pair record (the chord of the segment's ends, the
+// exit point for an entry on the near plane, Eq. 22's x_0 for a moved
+// singular entry); a moved singular entry (kShrunk) also from the centre of
+// the parameter box and from its exit point.
+template <int P, typename R, bool MIXED>
 __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> cam, int npix,
                                                      typename Vec4T<R>::type* __restrict__ pair_in,
                                                      typename Vec4T<R>::type* __restrict__ pair_out,
                                                      int* __restrict__ pair_block, const int* __restrict__ pair_count,
                                                      const int* __restrict__ active,
-                                                     const int* __restrict__ n_active, DevStats* __restrict__ st) {
+                                                     const int* __restrict__ n_active, const float4* __restrict__ gp,
+                                                     const int* __restrict__ gidx, DevStats* __restrict__ st) {
   typedef typename Vec4T<R>::type V4;
   pdl_wait();
   const int nact = *n_active;
-  const R tol = sizeof(R) == 4 ? R(1e-6) * R(V.diag) : R(1e-12) * R(V.diag);
+  unsigned long long c_it = 0, c_64 = 0;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
     const int pix = active[item];
     const int np = pair_count[pix];
@@ -209,19 +240,37 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
     for (int q = 0; q < np; ++q) {
       const size_t slot = (size_t)q * npix + pix;
       const int bf = pair_block[slot];
-      if (!(bf & (kSolveIn | kSolveOut))) continue;
       const int blk = bf & kBlockMask;
+      if (!(bf & (kSolveIn | kSolveOut))) {
+        if (bf != blk) pair_block[slot] = blk;
+        continue;
+      }
       const BlockInfo B = V.blocks[blk];
       bool ok = true;
       for (int e = 0; e < 2 && ok; ++e) {
         if (!(bf & (e == 0 ? kSolveIn : kSolveOut))) continue;
         V4 rec = e == 0 ? pair_in[slot] : pair_out[slot];
-        R g[3], pq[3] = {R(rec.y), R(rec.z), R(rec.w)};
+        const V4 other = e == 0 ? pair_out[slot] : pair_in[slot];
+        R g[3], pq[3];
         for (int r = 0; r < 3; ++r) g[r] = o[r] + R(rec.x) * d[r];
-        const R tol_g = tol + R(sizeof(R) == 4 ? 2e-7 : 1e-15) *
-                                  (fabs(g[0]) > fabs(g[1]) ? (fabs(g[0]) > fabs(g[2]) ? fabs(g[0]) : fabs(g[2]))
-                                                           : (fabs(g[1]) > fabs(g[2]) ? fabs(g[1]) : fabs(g[2])));
-        ok = clip_newton<P, R>(V, B, g, pq, tol_g);
+        const R tol_g = fixup_tol<R>(g, V.diag);
+        const bool learned = e == 0 && (bf & kGuessIn) && gp != nullptr;
+        const int n_starts = (e == 0 && (bf & kShrunk)) ? 4 : 2;
+        ok = false;
+        for (int k = learned ? 0 : 1; k < n_starts && !ok; ++k) {
+          if (k == 0) {
+            const float4 h = gp[gidx[slot]];
+            pq[0] = R(h.x); pq[1] = R(h.y); pq[2] = R(h.z);
+          } else if (k == 1) {
+            pq[0] = R(rec.y); pq[1] = R(rec.z); pq[2] = R(rec.w);
+          } else if (k == 2) {
+            pq[0] = pq[1] = pq[2] = R(0.5);
+          } else {
+            pq[0] = R(other.y); pq[1] = R(other.z); pq[2] = R(other.w);
+          }
+          for (int r = 0; r < 3; ++r) pq[r] = pq[r] < R(0) ? R(0) : (pq[r] > R(1) ? R(1) : pq[r]);
+          ok = clip_newton<P, R, MIXED>(V, B, g, pq, tol_g, c_it, c_64);
+        }
         rec.y = pq[0]; rec.z = pq[1]; rec.w = pq[2];
         if (e == 0) pair_in[slot] = rec; else pair_out[slot] = rec;
       }
@@ -234,6 +283,167 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
       pair_block[slot] = blk;
     }
   }
+  if (c_it) atomicAdd(&st->entry_newton, c_it);
+  if (c_64) atomicAdd(&st->fp64_solves, c_64);
+}
+
+// det J at the entry of one pair (FP64 arithmetic on the FP32 Jacobian in
+// mixed precision, as the FP64 solves).
+template <int P, typename R, bool MIXED>
+__device__ __forceinline__ double entry_det(const DevVolume& V, const BlockInfo& B, const R p[3]) {
+  R phi[3], J[3][3], rc;
+  eval_block<P, R, false>(V, B, p, phi, J, rc);
+  if (MIXED || sizeof(R) == 8)
+    return (double)J[0][0] * ((double)J[1][1] * J[2][2] - (double)J[1][2] * J[2][1]) -
+           (double)J[0][1] * ((double)J[1][0] * J[2][2] - (double)J[1][2] * J[2][0]) +
+           (double)J[0][2] * ((double)J[1][0] * J[2][1] - (double)J[1][1] * J[2][0]);
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// Learned-guess listing (before the clip fix-up): with `singular`, the
+// entries of flagged blocks whose det J is below tau_det move delta along
+// the ray as §5.4 says (x_0 of Eq. 22 in the pair record, kSolveIn |
+// kGuessIn | kShrunk); every kGuessIn entry is then appended to the list
+// (world point and block) for the guess network.
+template <int P, typename R, bool MIXED>
+__global__ void __launch_bounds__(128) k4_guess_mark(DevVolume V, DevCamera<R> cam, int npix,
+                                                     typename Vec4T<R>::type* __restrict__ pair_in,
+                                                     typename Vec4T<R>::type* __restrict__ pair_out,
+                                                     int* __restrict__ pair_block, const int* __restrict__ pair_count,
+                                                     const int* __restrict__ active,
+                                                     const int* __restrict__ n_active, int singular, GuessList gl,
+                                                     DevStats* __restrict__ st) {
+  typedef typename Vec4T<R>::type V4;
+  pdl_wait();
+  const int nact = *n_active;
+  const R delta = R(1e-4) * R(V.diag), eps = R(1e-4);
+  unsigned long long c_shrink = 0, c_drop = 0;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    R o[3], d[3];
+    make_ray<R>(cam, cam.x0 + pix % cam.w, cam.y0 + pix / cam.w, o, d);
+    for (int q = 0; q < np; ++q) {
+      const size_t slot = (size_t)q * npix + pix;
+      int bf = pair_block[slot];
+      const BlockInfo B = V.blocks[bf & kBlockMask];
+      V4 in = pair_in[slot];
+      const V4 out = pair_out[slot];
+      if (singular && B.sing_faces && !(bf & kSolveIn) && out.x > in.x) {
+        const R p[3] = {R(in.y), R(in.z), R(in.w)};
+        if (fabs(entry_det<P, R, MIXED>(V, B, p)) < (double)B.tau_det) {
+          ++c_shrink;
+          if (!(R(out.x) - R(in.x) > delta)) {
+            V4 ro = out;
+            ro.x = in.x;                                 // zero length: dropped by stage 3
+            pair_out[slot] = ro;
+            ++c_drop;
+          } else {
+            R dir[3] = {R(out.y) - p[0], R(out.z) - p[1], R(out.w) - p[2]};
+            const R nd = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+            in.x = R(in.x) + delta;
+            const R x0[3] = {p[0] + (nd > R(0) ? eps * dir[0] / nd : R(0)),
+                             p[1] + (nd > R(0) ? eps * dir[1] / nd : R(0)),
+                             p[2] + (nd > R(0) ? eps * dir[2] / nd : R(0))};
+            in.y = x0[0]; in.z = x0[1]; in.w = x0[2];
+            pair_in[slot] = in;
+            bf |= kSolveIn | kGuessIn | kShrunk;
+          }
+        }
+      }
+      if (bf & kGuessIn) {
+        const int k = atomicAdd(gl.n, 1);
+        const R t = R(in.x);
+        gl.g[k] = make_float4(float(o[0] + t * d[0]), float(o[1] + t * d[1]), float(o[2] + t * d[2]), 0.f);
+        gl.blk[k] = bf & kBlockMask;
+        gl.gidx[slot] = k;
+      }
+      pair_block[slot] = bf;
+    }
+  }
+  if (c_shrink) atomicAdd(&st->entry_shrinks, c_shrink);
+  if (c_drop) atomicAdd(&st->unmatched, c_drop);
+}
+
+// §5.4, singular Jacobian at the entry point (Eq. 22): for the pairs of
+// blocks with a face flagged at creation (det J comes close to 0 there),
+// det J is evaluated at the entry; below tau_det (1e-6 of the block's mean
+// |det J|) neither Newton nor the ODE's linear system can start there, so the
+// block is "shrunk": the entry moves delta = 1e-4 diag along the ray and its
+// parameter point is found by Newton from x_0 = p_in + eps (p_out - p_in) /
+// |p_out - p_in|, eps = 1e-4 (Eq. 22).  A pair not longer than delta, or
+// whose new entry does not invert inside the block, gets zero length
+// (stage 3 skips it).  One thread per active pixel.
+template <int P, typename R, bool MIXED>
+__global__ void __launch_bounds__(128) k4_entry_fix(DevVolume V, DevCamera<R> cam, int npix,
+                                                    typename Vec4T<R>::type* __restrict__ pair_in,
+                                                    typename Vec4T<R>::type* __restrict__ pair_out,
+                                                    const int* __restrict__ pair_block,
+                                                    const int* __restrict__ pair_count,
+                                                    const int* __restrict__ active, const int* __restrict__ n_active,
+                                                    DevStats* __restrict__ st) {
+  typedef typename Vec4T<R>::type V4;
+  pdl_wait();
+  const int nact = *n_active;
+  const R delta = R(1e-4) * R(V.diag), eps = R(1e-4);
+  unsigned long long c_shrink = 0, c_it = 0, c_64 = 0, c_drop = 0;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nact; item += gridDim.x * blockDim.x) {
+    const int pix = active[item];
+    const int np = pair_count[pix];
+    R o[3], d[3];
+    make_ray<R>(cam, cam.x0 + pix % cam.w, cam.y0 + pix / cam.w, o, d);
+    for (int q = 0; q < np; ++q) {
+      const size_t slot = (size_t)q * npix + pix;
+      const BlockInfo B = V.blocks[pair_block[slot] & kBlockMask];
+      if (!B.sing_faces) continue;
+      V4 in = pair_in[slot];
+      const V4 out = pair_out[slot];
+      if (!(out.x > in.x)) continue;                     // already empty
+      const R p[3] = {R(in.y), R(in.z), R(in.w)};
+      if (!(fabs(entry_det<P, R, MIXED>(V, B, p)) < (double)B.tau_det)) continue;
+      ++c_shrink;
+      bool ok = R(out.x) - R(in.x) > delta;
+      if (ok) {
+        R dir[3] = {R(out.y) - p[0], R(out.z) - p[1], R(out.w) - p[2]};
+        const R nd = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        R x[3], g[3];
+        const R t_in = R(in.x) + delta;
+        for (int r = 0; r < 3; ++r) g[r] = o[r] + t_in * d[r];
+        // Newton from Eq. 22's x_0; where the map degenerates faster than
+        // linearly toward the face, Newton from x_0 overshoots out of the
+        // block and its line search cannot recover: then from the centre of
+        // the parameter box, then from the exit point (the root is unique)
+        const R tol_g = fixup_tol<R>(g, V.diag);
+        const R p_out[3] = {R(out.y), R(out.z), R(out.w)};
+        ok = false;
+        for (int k = 0; k < 3 && !ok; ++k) {
+          for (int r = 0; r < 3; ++r) {
+            const R v = k == 0 ? p[r] + (nd > R(0) ? eps * dir[r] / nd : R(0)) : (k == 1 ? R(0.5) : p_out[r]);
+            x[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
+          }
+          ok = clip_newton<P, R, MIXED>(V, B, g, x, tol_g, c_it, c_64);
+        }
+        if (ok) {
+          in.x = t_in;
+          in.y = x[0];
+          in.z = x[1];
+          in.w = x[2];
+          pair_in[slot] = in;
+        }
+      }
+      if (!ok) {
+        V4 ro = out;
+        ro.x = in.x;                                     // zero length: dropped by stage 3
+        pair_out[slot] = ro;
+        ++c_drop;
+      }
+    }
+  }
+  if (c_shrink) atomicAdd(&st->entry_shrinks, c_shrink);
+  if (c_it) atomicAdd(&st->entry_newton, c_it);
+  if (c_64) atomicAdd(&st->fp64_solves, c_64);
+  if (c_drop) atomicAdd(&st->unmatched, c_drop);
 }
 
 // Block-aggregated append of the active pixels to the integrator's queue
@@ -254,7 +464,7 @@ __device__ __forceinline__ void pair_epilogue(int pix, int np, float len, unsign
   __shared__ int s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = np > 0;
-  const float key = act && len > 0.f ? len : 0.f;
+  const float key = act && isfinite(len) && len > 0.f ? len : 0.f;   // a non-finite length goes to band 0
   unsigned wmax = __float_as_uint(key);           // non-negative floats order as their bits
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -263,7 +473,7 @@ __device__ __forceinline__ void pair_epilogue(int pix, int np, float len, unsign
   if (lane == 0) atomicMax(&s_max, wmax);
   __syncthreads();
   const float kmax = __uint_as_float(s_max);
-  const int band = kmax > 0.f ? min(kBands - 1, (int)((float)kBands * (key / kmax))) : 0;
+  const int band = kmax > 0.f ? max(0, min(kBands - 1, (int)((float)kBands * (key / kmax)))) : 0;
   unsigned my_band_mask = 0u;
 #pragma unroll
   for (int b = 0; b < kBands; ++b) {
@@ -319,7 +529,8 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
                                                float4* __restrict__ out_rgba, ClipArgs<R> clip,
-                                               int* __restrict__ tile_flag, DevStats* __restrict__ st) {
+                                               int* __restrict__ tile_flag, int max_frags,
+                                               DevStats* __restrict__ st) {
   pdl_wait();
   // a tile none of whose warp tiles had a candidate patch was finished by
   // the cull (pair counts and zero pixels): nothing to do
@@ -333,10 +544,11 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
   if (x < w && pix < npix) {
     if (clip.on)
       np = pair_pixel_clip<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
-                              pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov, clip, x, y);
+                              pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov, clip, x, y,
+                              max_frags);
     else
       np = pair_pixel<R>(pix, npix, tau_dup, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block,
-                         pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov);
+                         pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov, max_frags);
   }
   float len = 0.f;                                  // the pixel's path length through the volume
   for (int q = 0; q < np; ++q) {
@@ -383,14 +595,13 @@ void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
                  int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, int* tile_flag, DevStats* st,
                  cudaStream_t s) {
-  (void)V;
   if (npix <= 0) return;
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
   if (w <= 0) return;
   const int h = npix / w;
   launch_pdl(k4_pair<R>, dim3(((w + 15) / 16) * ((h + 15) / 16)), dim3(256), s, w, npix, tau, frag_tp, frag_meta,
              frag_count, pair_in, pair_out, pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, clip,
-             tile_flag, st);
+             tile_flag, V.max_frags, st);
 }
 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
@@ -411,23 +622,86 @@ template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*
 template <typename R>
 void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
                        typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
-                       const int* n_active, DevStats* st, int num_sms, cudaStream_t s) {
+                       const int* n_active, bool mixed, const GuessList* guess, DevStats* st, int num_sms,
+                       cudaStream_t s) {
   if (npix <= 0) return;
   int grid = num_sms * 8;
   const int useful = (npix + 127) / 128;
   grid = grid < useful ? grid : useful;
-  if (V.P == 2)
-    launch_pdl(k4_clip_solve<2, R>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block,
-               pair_count, active, n_active, st);
-  else
-    launch_pdl(k4_clip_solve<3, R>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block,
-               pair_count, active, n_active, st);
+  const float4* gp = guess ? guess->p : nullptr;
+  const int* gidx = guess ? guess->gidx : nullptr;
+#define IVV_CLIP(PP, MM)                                                                                        \
+  launch_pdl(k4_clip_solve<PP, R, MM>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block, \
+             pair_count, active, n_active, gp, gidx, st)
+  const bool m = mixed && sizeof(R) == 4;
+  if (V.P == 2) {
+    if (m) IVV_CLIP(2, true); else IVV_CLIP(2, false);
+  } else {
+    if (m) IVV_CLIP(3, true); else IVV_CLIP(3, false);
+  }
+#undef IVV_CLIP
 }
 
 template void launch_clip_solve<float>(const DevVolume&, const DevCamera<float>&, int, float4*, float4*, int*,
-                                       const int*, const int*, const int*, DevStats*, int, cudaStream_t);
+                                       const int*, const int*, const int*, bool, const GuessList*, DevStats*, int,
+                                       cudaStream_t);
 template void launch_clip_solve<double>(const DevVolume&, const DevCamera<double>&, int, Dbl4*, Dbl4*, int*,
-                                        const int*, const int*, const int*, DevStats*, int, cudaStream_t);
+                                        const int*, const int*, const int*, bool, const GuessList*, DevStats*, int,
+                                        cudaStream_t);
+
+template <typename R>
+void launch_guess_mark(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                       typename Vec4T<R>::type* pair_out, int* pair_block, const int* pair_count, const int* active,
+                       const int* n_active, bool singular, bool mixed, const GuessList& guess, DevStats* st,
+                       int num_sms, cudaStream_t s) {
+  if (npix <= 0) return;
+  int grid = num_sms * 8;
+  const int useful = (npix + 127) / 128;
+  grid = grid < useful ? grid : useful;
+  const int sg = singular ? 1 : 0;
+#define IVV_MARK(PP, MM)                                                                                        \
+  launch_pdl(k4_guess_mark<PP, R, MM>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block, \
+             pair_count, active, n_active, sg, guess, st)
+  const bool m = mixed && sizeof(R) == 4;
+  if (V.P == 2) {
+    if (m) IVV_MARK(2, true); else IVV_MARK(2, false);
+  } else {
+    if (m) IVV_MARK(3, true); else IVV_MARK(3, false);
+  }
+#undef IVV_MARK
+}
+
+template void launch_guess_mark<float>(const DevVolume&, const DevCamera<float>&, int, float4*, float4*, int*,
+                                       const int*, const int*, const int*, bool, bool, const GuessList&, DevStats*,
+                                       int, cudaStream_t);
+template void launch_guess_mark<double>(const DevVolume&, const DevCamera<double>&, int, Dbl4*, Dbl4*, int*,
+                                        const int*, const int*, const int*, bool, bool, const GuessList&, DevStats*,
+                                        int, cudaStream_t);
+
+template <typename R>
+void launch_entry_fix(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
+                      typename Vec4T<R>::type* pair_out, const int* pair_block, const int* pair_count,
+                      const int* active, const int* n_active, bool mixed, DevStats* st, int num_sms, cudaStream_t s) {
+  if (npix <= 0) return;
+  int grid = num_sms * 8;
+  const int useful = (npix + 127) / 128;
+  grid = grid < useful ? grid : useful;
+#define IVV_FIX(PP, MM)                                                                                          \
+  launch_pdl(k4_entry_fix<PP, R, MM>, dim3(grid), dim3(128), s, V, cam, npix, pair_in, pair_out, pair_block,   \
+             pair_count, active, n_active, st)
+  const bool m = mixed && sizeof(R) == 4;
+  if (V.P == 2) {
+    if (m) IVV_FIX(2, true); else IVV_FIX(2, false);
+  } else {
+    if (m) IVV_FIX(3, true); else IVV_FIX(3, false);
+  }
+#undef IVV_FIX
+}
+
+template void launch_entry_fix<float>(const DevVolume&, const DevCamera<float>&, int, float4*, float4*, const int*,
+                                      const int*, const int*, const int*, bool, DevStats*, int, cudaStream_t);
+template void launch_entry_fix<double>(const DevVolume&, const DevCamera<double>&, int, Dbl4*, Dbl4*, const int*,
+                                       const int*, const int*, const int*, bool, DevStats*, int, cudaStream_t);
 
 }  // namespace ivv
 

@@ -196,7 +196,8 @@ __global__ void k_rf_expand(DevCamera<float> cam, const float4* __restrict__ pai
 
 // abs_tol > 0: fixed stopping tolerance (point location); otherwise the
 // pixel-accuracy rule of the camera.  p_out / it_out are optional.
-template <int P, bool STATS>
+// MIXED: the 3x3 Newton solve switches to FP64 where |det J| < tau_det.
+template <int P, bool STATS, bool MIXED>
 __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float> cam, float rf_tol, float abs_tol,
                                                    const int* __restrict__ n_ptr, const float4* __restrict__ sg,
                                                    const int* __restrict__ sblk, const float4* __restrict__ sp,
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
                                                    int* __restrict__ it_out, DevStats* __restrict__ st) {
   pdl_wait();
   const int n = *n_ptr;
-  unsigned long long c_it = 0, c_ev = 0, c_fail = 0;
+  unsigned long long c_it = 0, c_ev = 0, c_fail = 0, c_64 = 0;
   // half width of a pixel per unit depth (perspective) or absolute (ortho)
   const float px_half = cam.sy / (float)cam.H;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -230,10 +231,25 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
     float F[3] = {phi[0] - g[0], phi[1] - g[1], phi[2] - g[2]};
     float nF = sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
     int it = 0;
-    for (; it < 16 && nF > tol; ++it) {
+    for (; it < V.max_newton && nF > tol; ++it) {
       float dx[3];
       const float rhs[3] = {-F[0], -F[1], -F[2]};
-      solve3<float>(J, rhs, dx);
+      const float det = solve3<float>(J, rhs, dx);
+      if constexpr (MIXED) {
+        if (fabsf(det) < B.tau_det) {
+          double Jd[3][3], bd[3], xd[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            bd[r] = rhs[r];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Jd[r][c] = J[r][c];
+          }
+          solve3<double>(Jd, bd, xd);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) dx[r] = (float)xd[r];
+          ++c_64;
+        }
+      }
       float lam = 1.f;
       bool moved = false;
       for (int ls = 0; ls < 6; ++ls) {
@@ -261,10 +277,8 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
       }
       if (!moved) break;
     }
-    if (STATS) {
-      c_it += it;
-      if (nF > tol) ++c_fail;
-    }
+    if (STATS) c_it += it;
+    if (nF > tol) ++c_fail;
     if (p_out) p_out[i] = make_float4(p[0], p[1], p[2], nF);
     if (it_out) it_out[i] = nF <= tol ? it : -1 - it;
     float rho = rc;
@@ -293,7 +307,10 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
       atomicAdd(&st->rhs_evals, c_ev);
       atomicAdd(&st->rf_unconverged, c_fail);
     }
+  } else if (c_fail) {
+    atomicAdd(&st->rf_unconverged, c_fail);       // a cap counter: kept by every render
   }
+  if (MIXED && c_64) atomicAdd(&st->fp64_solves, c_64);
 }
 
 __global__ void k_rf_composite(DevTF tf, int K, float early, const float4* __restrict__ pair_in,
@@ -405,15 +422,17 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
 
 void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
                       const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
-                      DevStats* st, bool stats, int num_sms, cudaStream_t s) {
+                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s) {
   const int grid = num_sms * 16;
-#define IVV_RFN(PP, SS) \
-  launch_pdl(k_rf_newton<PP, SS>, dim3(grid), dim3(128), s, V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, p_out, \
-             it_out, st)
+#define IVV_RFN(PP, SS, MM) \
+  launch_pdl(k_rf_newton<PP, SS, MM>, dim3(grid), dim3(128), s, V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, \
+             p_out, it_out, st)
   if (V.P == 2) {
-    if (stats) IVV_RFN(2, true); else IVV_RFN(2, false);
+    if (mixed) { if (stats) IVV_RFN(2, true, true); else IVV_RFN(2, false, true); }
+    else { if (stats) IVV_RFN(2, true, false); else IVV_RFN(2, false, false); }
   } else {
-    if (stats) IVV_RFN(3, true); else IVV_RFN(3, false);
+    if (mixed) { if (stats) IVV_RFN(3, true, true); else IVV_RFN(3, false, true); }
+    else { if (stats) IVV_RFN(3, true, false); else IVV_RFN(3, false, false); }
   }
 #undef IVV_RFN
 }

@@ -184,27 +184,25 @@ __device__ __forceinline__ bool roots_item(const DevVolume& V, const DevCamera<d
   if (!patch_roots_fast<P, R>(pq, ra, rb, nr, c_newton)) return false;
   const int face = m.face, block = m.block;
   for (int k = 0; k < nr; ++k) {
-    R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
+    const R a = ra[k], b = rb[k];          // within the acceptance tolerance of the patch
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
     if constexpr (MIXED) {
-      if (cosang < R(0.2)) {
+      if (cosang < R(kPolishCos)) {
         double a64 = a, b64 = b, t64 = t;
         refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
-        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
         t = R(t64);
         const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
         const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
-        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
         if (STATS) ++c_fp64;
       }
     }
     if (!(t > R(0))) continue;
     const int slot = atomicAdd(frag_count + pix, 1);
-    if (slot < kMaxFrags) {
+    if (slot < V.max_frags) {
       V4 rec;
       rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
       frag_tp[(size_t)slot * stride + pix] = rec;
@@ -246,12 +244,14 @@ struct SplitSmem {
 };
 
 // Root (a, b) local to box nd: kept if inside the box (tolerance scaled to
-// its size) and the patch; returns false if outside the box.
+// its size) and the patch; returns false if outside the box.  in_box =
+// false (uncertified smallest boxes) keeps a root anywhere in the patch, as
+// accept_root (isect.cuh) does.
 template <typename R>
-__device__ __forceinline__ bool gather_root(const SplitBox<R>& nd, R a, R b, SplitSmem<R>& sm) {
+__device__ __forceinline__ bool gather_root(const SplitBox<R>& nd, R a, R b, SplitSmem<R>& sm, bool in_box = true) {
   const R wa = nd.a1 - nd.a0, wb = nd.b1 - nd.b0;
   const R ea = RootEps<R>::accept / wa, eb = RootEps<R>::accept / wb;
-  if (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb) return false;
+  if (in_box && (a < -ea || a > R(1) + ea || b < -eb || b > R(1) + eb)) return false;
   const R ga = nd.a0 + a * wa, gb = nd.b0 + b * wb;
   const R e = RootEps<R>::accept;
   if (ga < -e || ga > R(1) + e || gb < -e || gb > R(1) + e) return true;
@@ -305,7 +305,7 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
         for (int s0 = 0; s0 < 5; ++s0) {
           R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
           R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
-          if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm);
+          if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm, false);
         }
         split = false;
       }
@@ -393,28 +393,26 @@ __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCam
   const int nr = split_roots_warp<P, R>(pq, pad, sm, c_newton, dropped);
   const int lane = threadIdx.x & 31;
   if (lane < nr) {
-    R a = clamp01r(sm.ra[lane]), b = clamp01r(sm.rb[lane]);
+    const R a = sm.ra[lane], b = sm.rb[lane];   // within the acceptance tolerance of the patch
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
     const int face = m.face, block = m.block;
     if constexpr (MIXED) {
-      if (cosang < R(0.2)) {
+      if (cosang < R(kPolishCos)) {
         double a64 = a, b64 = b, t64 = t;
         refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
-        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
         t = R(t64);
         const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
         const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
-        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
         if (STATS) ++c_fp64;
       }
     }
     if (t > R(0)) {
       const int slot = atomicAdd(frag_count + pix, 1);
-      if (slot < kMaxFrags) {
+      if (slot < V.max_frags) {
         V4 rec;
         rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
         frag_tp[(size_t)slot * stride + pix] = rec;
@@ -461,27 +459,25 @@ __device__ __forceinline__ void split_item_thread(const DevVolume& V, const DevC
   const int nr = patch_roots_split<P, R>(&pq, pad, ra, rb, c_newton);
   const int face = m.face, block = m.block;
   for (int k = 0; k < nr; ++k) {
-    R a = clamp01r(ra[k]), b = clamp01r(rb[k]);
+    const R a = ra[k], b = rb[k];          // within the acceptance tolerance of the patch
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
     if constexpr (MIXED) {
-      if (cosang < R(0.2)) {
+      if (cosang < R(kPolishCos)) {
         double a64 = a, b64 = b, t64 = t;
         refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        a64 = a64 < 0.0 ? 0.0 : (a64 > 1.0 ? 1.0 : a64);
-        b64 = b64 < 0.0 ? 0.0 : (b64 > 1.0 ? 1.0 : b64);
         t = R(t64);
         const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
         const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(m64.a0 + a64 * (m64.a1 - m64.a0));
-        pp[bd] = R(m64.b0 + b64 * (m64.b1 - m64.b0));
+        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
         if (STATS) ++c_fp64;
       }
     }
     if (!(t > R(0))) continue;
     const int slot = atomicAdd(frag_count + pix, 1);
-    if (slot < kMaxFrags) {
+    if (slot < V.max_frags) {
       V4 rec;
       rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
       frag_tp[(size_t)slot * stride + pix] = rec;

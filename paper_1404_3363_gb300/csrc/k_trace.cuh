@@ -170,10 +170,8 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
       ++steps;
       const bool capped = steps >= args.max_steps;
       if (err <= tol || hh <= hmin || capped) {
-        if (STATS) {
-          ++c_steps;
-          if (capped) ++c_cap;
-        }
+        if (STATS) ++c_steps;
+        if (capped) ++c_cap;
         const float s1 = last_end(s, hh, L);
         // samples inside (s, s1]: cubic Hermite through (p, k1) and (x, W)
         for (; j <= nlast; ++j) {
@@ -238,6 +236,8 @@ __global__ void __launch_bounds__(128, 4) k5_trace(DevVolume V, DevCamera<float>
       atomicAdd(&st->rk_rejects, c_rej);
       atomicAdd(&st->step_cap, c_cap);
     }
+  } else if (c_cap) {
+    atomicAdd(&st->step_cap, c_cap);               // a cap counter: kept by every render
   }
 }
 

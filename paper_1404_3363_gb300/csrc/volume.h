@@ -65,4 +65,9 @@ struct ivv_volume {
   // sample lists of the split ODE integration (grown on demand)
   void* ode_buf = nullptr;
   size_t ode_bytes = 0;
+  // capacities and iteration caps of the render (ivv_set_limits)
+  int lim_frags = ivv::kMaxFrags, lim_pairs = ivv::kMaxPairs, lim_items = ivv::kItemsPerPixel;
+  int lim_rk_steps = 200000, lim_newton = 16;
+  // overflow and cap counters already reported by ivv_check_frame
+  unsigned long long seen_overflow = 0, seen_cap = 0;
 };

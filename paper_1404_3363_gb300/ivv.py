@@ -62,6 +62,11 @@ class RenderParams(C.Structure):
                 ("cut_planes", (C.c_double * 4) * 4)]
 
 
+class Limits(C.Structure):
+    _fields_ = [("max_frags", C.c_int), ("max_pairs", C.c_int), ("items_per_pixel", C.c_int),
+                ("max_rk_steps", C.c_int), ("max_newton", C.c_int)]
+
+
 class GuessTrainParams(C.Structure):
     _fields_ = [("samples_per_block", C.c_int), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
                 ("seed", C.c_ulonglong)]
@@ -84,7 +89,8 @@ class Stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in (
         "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
         "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap",
-        "rf_newton_iters", "rf_unconverged", "isect_items", "isect_split", "rho_evals")] + \
+        "rf_newton_iters", "rf_unconverged", "isect_items", "isect_split", "rho_evals", "entry_shrinks",
+        "entry_newton")] + \
         [("max_delta_p", C.c_double)]
 
     def as_dict(self):
@@ -138,6 +144,9 @@ def load(path: str = LIB_PATH):
     L.ivv_set_guess_weights.argtypes = [vp, C.c_int, c_float_p]
     L.ivv_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.ivv_reset_stats.argtypes = [vp]
+    L.ivv_set_limits.argtypes = [vp, C.POINTER(Limits)]
+    L.ivv_get_limits.argtypes = [vp, C.POINTER(Limits)]
+    L.ivv_check_frame.argtypes = [vp]
     L.ivv_volume_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
     L.ivv_destroy_volume.argtypes = [vp]
     L.ivv_destroy_volume.restype = None
@@ -456,6 +465,29 @@ class Volume:
         s = Stats()
         _check(load().ivv_get_stats(self.h, C.byref(s)))
         return s.as_dict()
+
+    def set_limits(self, **kw):
+        """Capacities and caps (ivv_limits); unnamed fields keep their value;
+        no arguments restores the defaults."""
+        if not kw:
+            _check(load().ivv_set_limits(self.h, None))
+            return
+        lim = Limits()
+        _check(load().ivv_get_limits(self.h, C.byref(lim)))
+        for k, v in kw.items():
+            setattr(lim, k, int(v))
+        _check(load().ivv_set_limits(self.h, C.byref(lim)))
+
+    def limits(self):
+        lim = Limits()
+        _check(load().ivv_get_limits(self.h, C.byref(lim)))
+        return {n: getattr(lim, n) for n, _ in Limits._fields_}
+
+    def check_frame(self):
+        """(status, message) of the renders since the last check: IVV_OK,
+        IVV_ERR_ABUF_OVERFLOW or IVV_ERR_NONCONVERGED."""
+        st = load().ivv_check_frame(self.h)
+        return st, load().ivv_last_error().decode(errors="replace") if st != IVV_OK else ""
 
     def reset_stats(self):
         _check(load().ivv_reset_stats(self.h))

@@ -382,6 +382,47 @@ def backstep(seed: int = 12349, width: int = 3840, height: int = 2160,
     return Scene("backstep", blocks, SCALAR_CP, tf, cam, width, height, params)
 
 
+def degenerate_cube(seed: int = 12350, width: int = 256, height: int = 256, precision: int = PRECISION_FP32,
+                    twist: float = 0.5 * math.pi, jitter: float = 0.02, scalar=None, direction=(0.35, 0.25, 0.9),
+                    ortho: bool = True) -> Scene:
+    """Cubic Bezier element (4x4x4 cp) of the unit cube, twisted by `twist`
+    about the axis x=y=0.5, whose three upper control-point layers coincide
+    (the top layer repeated, as a designer's collapsed layers): z(w) =
+    1 - (1 - w)^3, so d phi / d w and det J vanish on the whole top face w = 1
+    (a singular Jacobian on the boundary, §5.4).  Jitter U(-jitter, jitter)
+    per control point of the bottom layer and of the (shared) top layer;
+    scalar control points U(0,1) (or the constant `scalar`); 8-knot TF,
+    sigma = 4; camera looking down along -direction so that rays enter
+    through the top face."""
+    rng = np.random.default_rng(seed)
+    kn = np.array([0, 0, 0, 0, 1, 1, 1, 1], dtype=np.float64)
+    g = np.linspace(0, 1, 4)
+    P = _grid(g, g, g)
+    P[..., 2] = np.where(P[..., 2] > 0, 1.0, 0.0)           # layers k = 1, 2, 3 at z = 1
+    th = twist * P[..., 2]
+    x, y = P[..., 0] - 0.5, P[..., 1] - 0.5
+    cp = np.stack([0.5 + x * np.cos(th) - y * np.sin(th),
+                   0.5 + x * np.sin(th) + y * np.cos(th),
+                   P[..., 2]], axis=-1)
+    jit = rng.uniform(-jitter, jitter, (2, 4, 4, 3))
+    cp[0] += jit[0]
+    cp[1:] += jit[1][None]                                   # the top layers stay coincident
+    scal = np.full((4, 4, 4), float(scalar)) if scalar is not None else rng.uniform(0, 1, (4, 4, 4))
+    blk = Block((3, 3, 3), [kn.copy(), kn.copy(), kn.copy()], cp, scal)
+    tf = _random_tf(rng, 8, 4.0)
+    pts = cp.reshape(-1, 3)
+    lo, hi = pts.min(0), pts.max(0)
+    centre, diag = 0.5 * (lo + hi), float(np.linalg.norm(hi - lo))
+    dvec = _unit(direction)
+    up = np.array([0.0, 1.0, 0.0]) if abs(dvec[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    if ortho:
+        cam = Camera(True, tuple(centre + 3 * diag * dvec), tuple(centre), tuple(up), ortho_height=1.1 * diag)
+    else:
+        cam = Camera(False, tuple(centre + 2.2 * diag * dvec), tuple(centre), tuple(up), fovy_deg=35.0)
+    params = RenderParams(rk_tol=1e-5, ds=_default_ds([blk]), precision=precision)
+    return Scene("degenerate_cube", [blk], SCALAR_CP, tf, cam, width, height, params)
+
+
 CONFIG_BUILDERS = {0: twisted_cube, 1: twisted_bar, 2: bent_beam, 4: backstep}
 
 

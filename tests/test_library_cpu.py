@@ -146,6 +146,9 @@ def test_render_entry_points_reject_null_arguments(lib):
     assert lib.ivv_render_to_host_async(None, C.byref(cam), C.byref(prm), 2, 2, host, None) == 1
     assert lib.ivv_render_to_host_async(None, C.byref(cam), C.byref(prm), 2, 2, None, None) == 1
     assert lib.ivv_render_to_host_wait(None) == 1
+    assert lib.ivv_check_frame(None) == 1
+    assert lib.ivv_set_limits(None, None) == 1
+    assert lib.ivv_get_limits(None, None) == 1
     assert b"NULL" in lib.ivv_last_error()
 
 

@@ -103,3 +103,65 @@ def test_implicit_euler_first_order_on_the_twisted_bar():
     slopes = np.log2(errs[:-1] / errs[1:])
     assert errs[0] > 1e-9
     assert np.all(np.abs(slopes - 1.0) < 0.35), (errs, slopes)
+
+
+def _t1_map(p):
+    """The Table 1 harness's analytic map phi(x,y,z) = (2x, y + 0.3 (1-x) sin(10 pi x), z), its Jacobian."""
+    x, y, z = p
+    s, c = np.sin(10 * np.pi * x), np.cos(10 * np.pi * x)
+    phi = np.array([2 * x, y + 0.3 * (1 - x) * s, z])
+    J = np.array([[2.0, 0, 0], [-0.3 * s + 3 * np.pi * (1 - x) * c, 1, 0], [0, 0, 1]])
+    return phi, J
+
+
+def _t1_ray():
+    g_in, _ = _t1_map(np.array([0.0, 0.3, 0.5]))
+    g_out, _ = _t1_map(np.array([1.0, 0.7, 0.5]))
+    d = g_out - g_in
+    return g_in, d / np.linalg.norm(d)
+
+
+def _t1_W(p, c):
+    g_in, d = _t1_ray()
+    phi, J = _t1_map(p)
+    e = g_in - phi
+    return np.linalg.solve(J, d + c * (e - (e @ d) * d))
+
+
+def test_implicit_step_solves_g_to_rounding():
+    """A converged step satisfies z = h W(p + z) (the definition of implicit
+    Euler, §5.2) to rounding, with the field evaluated independently here."""
+    p = np.array([0.31, 0.42, 0.5])
+    for h, c in ((0.02, 1.0), (0.02, 100.0), (0.005, 100.0)):
+        pn, it = oracle.t1_irk1_step(p, h, c)
+        assert 0 < it <= 6, it
+        np.testing.assert_allclose(pn - p, h * _t1_W(pn, c), atol=1e-13)
+
+
+def test_non_converged_step_takes_the_boundary_step():
+    """§5.4's answer to a Newton iteration that does not converge: the step
+    follows the boundary of the parameter box.  With the iteration cap at one
+    Newton step the oracle takes the explicit Euler step from p, clamped to
+    [0,1]^3; next to the exit face x = 1, where the field points out of the
+    box, the step slides along that face."""
+    c, h = 100.0, 0.05
+    for p in (np.array([0.31, 0.42, 0.5]), np.array([0.998, 0.69, 0.5])):
+        pn, it = oracle.t1_irk1_step(p, h, c, max_it=1)
+        assert it == -1
+        np.testing.assert_allclose(pn, np.clip(p + h * _t1_W(p, c), 0, 1), atol=1e-14)
+    p = np.array([0.998, 0.69, 0.5])
+    pn, _ = oracle.t1_irk1_step(p, h, c, max_it=1)
+    assert (p + h * _t1_W(p, c))[0] > 1 and pn[0] == 1.0 and abs(pn[1] - p[1]) > 1e-3
+
+
+@pytest.mark.parametrize("cfg,c", [(1, 100.0), (2, 100.0)])
+def test_implicit_euler_render_converges_on_every_step(cfg, c):
+    """The render path solves G(z) = 0 to 1e-13 on every step of the bar and
+    the beam (no step takes the boundary step) and matches the root-finding
+    image to first-order accuracy."""
+    sc = scenes.config(cfg, width=48, height=27)
+    sc.params.c = c
+    vol = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    img, st = oracle.render(sc, vol, method=oracle.IMPLICIT_EULER, stats=True)
+    assert st[..., 4].sum() > 1000
+    assert st[..., 2].sum() == 0, st[..., 2].sum()
