@@ -49,6 +49,30 @@ WORKLOADS = {
                          "{256,512,768,1024}^2, seeded cameras and TFs, FP32, one CUDA graph"),
 }
 
+# Workloads of the learned initial guess: (base workload, render-parameter
+# overrides, label).  The guess network (3-64-64-3 per block) is trained on
+# the device before the timed frames (2^20 forward-map samples per block,
+# untimed, reported as train_s).  RF: every sample's Newton starts from the
+# guess named; rf_tol 1e-3 of the pixel half width (image parity, not only
+# pixel accuracy).
+LEARNED_WORKLOADS = {
+    "beam1080-rf-learned-mixed": ("beam1080", {"method": 1, "use_mlp_guess": 1, "rf_tol": 1e-3},
+                                  "root finding per sample (5.1) from the learned guess, mixed precision"),
+    "beam1080-rf-chord-fp32": ("beam1080-fp32", {"method": 1, "use_mlp_guess": 2, "rf_tol": 1e-3},
+                               "root finding per sample (5.1) from the chord guess, FP32"),
+    "bar1080-rf-learned-mixed": ("bar1080", {"precision": 1, "method": 1, "use_mlp_guess": 1, "rf_tol": 1e-3},
+                                 "root finding per sample (5.1) from the learned guess, mixed precision"),
+    "bar1080-rf-chord-fp32": ("bar1080", {"method": 1, "use_mlp_guess": 2, "rf_tol": 1e-3},
+                              "root finding per sample (5.1) from the chord guess, FP32"),
+    "backstep4k-rf-learned-mixed": ("backstep4k", {"method": 1, "use_mlp_guess": 1, "rf_tol": 1e-3},
+                                    "root finding per sample (5.1) from the learned guess, mixed precision"),
+    "backstep4k-rf-chord-fp32": ("backstep4k-fp32", {"method": 1, "use_mlp_guess": 2, "rf_tol": 1e-3},
+                                 "root finding per sample (5.1) from the chord guess, FP32"),
+    "beam1080-learned-mixed": ("beam1080", {"use_mlp_guess": 1},
+                               "ODE method with the learned guess for stage-2 entries without chord context "
+                               "(none on this view: the guess network is idle)"),
+}
+
 # Algorithmic FP32 flops per unit for Bezier degree P (N = P + 1 control
 # points per direction; the cubic figures in brackets).
 # integrator (K5 / K5t)
@@ -58,7 +82,14 @@ WORKLOADS = {
 # FP64 integrator and the fixed-step / implicit ones replace the last six by
 # one kernel.  A batch replays the same stages for every request at once,
 # plus the overflow list and its fused integrator.
-def kernels_per_frame(prec, rk_method):
+def kernels_per_frame(prec, rk_method, method=0, guess=0):
+    """Kernels one frame launches: stages 1-2 (K0, K2a, K2b, both K2c forms,
+    K4) and stage 3 -- the split integration (sample counts, three scan
+    passes, K5t, shading), one fused integrator (FP64, fixed-step, implicit
+    Euler), or the RF chain (counts, three scan passes, expansion, Newton,
+    compositing, plus the guess network's inference with the learned guess)."""
+    if method == 1:
+        return 6 + 7 + (1 if guess == 1 else 0)
     return 12 if prec != 2 and not rk_method else 7
 
 
@@ -310,6 +341,14 @@ def pair_parity(vol, sc, rows):
             "bound": 1e-5}
 
 
+def tile_rows(height, rank, world):
+    """Band of rows (y0, h) of a frame split over `world` ranks (--split
+    rows): contiguous bands, the first height % world ranks one row taller."""
+    base, extra = divmod(height, world)
+    y0 = rank * base + min(rank, extra)
+    return y0, base + (1 if rank < extra else 0)
+
+
 def aggregate_ranks(ms_local, pixels_per_rank, dist=None, device=None):
     """Whole-job Mpixels/s: every rank renders its own frame (replicas, weak
     scaling); the job time is the slowest rank's.  Returns (value, ms_max)."""
@@ -379,9 +418,19 @@ def run_ours(args):
     libbuild.build()
     from paper_1404_3363_gb300 import ivv, scenes
 
-    cfg, prec, workload = WORKLOADS[args.workload]
+    overrides, train = {}, False
+    if args.workload in LEARNED_WORKLOADS:
+        base, overrides, label = LEARNED_WORKLOADS[args.workload]
+        cfg, prec, workload = WORKLOADS[base]
+        workload = workload + ", " + label
+        train = overrides.get("use_mlp_guess") == 1
+    else:
+        cfg, prec, workload = WORKLOADS[args.workload]
     sc = scenes.config(cfg)
     sc.params.precision = prec
+    for k, v in overrides.items():
+        setattr(sc.params, k, v)
+    prec = sc.params.precision
     if args.rk_method:
         sc.params.rk_method = args.rk_method
         workload += ", fixed-step %s (one step per sample interval)" % RK_NAMES[args.rk_method]
@@ -389,21 +438,33 @@ def run_ours(args):
         sc.params.c = args.c
         workload += ", c = %g" % args.c
     W, H = sc.width, sc.height
+    FW, FH = W, H                     # the full frame
+    window = None
+    if args.split == "rows" and world > 1:
+        # strong scaling: each rank renders its band of rows of the one frame
+        y0, H = tile_rows(FH, rank, world)
+        window = (0, y0, FW, FH)
     stream = torch.cuda.current_stream()
     vol = ivv.volume_for(sc)
+    train_s = None
+    if train:
+        t0 = time.perf_counter()
+        train_loss = vol.train_guess(samples_per_block=1 << 20, epochs=8, batch=4096, lr=3e-3, seed=1)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     # untimed instrumented replay: algorithmic work counts of this exact frame
     vol.reset_stats()
-    vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS)
+    vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS, window=window)
     st = vol.stats()
     F = flop_model(scene_degree(sc.blocks))
     flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP, implicit=args.rk_method == 7)
     flops_k2 = k2_flops(st, F)
 
     def frame(flags=0):
-        vol.render(sc.camera, sc.params, W, H, out=out, flags=flags)
+        vol.render(sc.camera, sc.params, W, H, out=out, flags=flags, window=window)
 
     for _ in range(args.warmup):
         frame()
@@ -437,7 +498,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    value, ms = aggregate_ranks(ms, W * H, dist, "cuda")
+    px_rank = W * H if window is None else FW * FH / world      # rows: the ranks share one frame
+    value, ms = aggregate_ranks(ms, px_rank, dist, "cuda")
     if dist:
         dist.barrier()
     k5_ms = stage_sum["integrate"] / args.steps
@@ -449,21 +511,21 @@ def run_ours(args):
     # inside the timed region; the blocking ivv_render_to_host is timed too)
     hosts = [torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     for i in range(2):
-        vol.render_to_host(sc.camera, sc.params, W, H, hosts[i])
-        vol.render_to_host_async(sc.camera, sc.params, W, H, hosts[i])
+        vol.render_to_host(sc.camera, sc.params, W, H, hosts[i], window=window)
+        vol.render_to_host_async(sc.camera, sc.params, W, H, hosts[i], window=window)
     vol.wait_host()
     e2e_n = max(3, args.steps)
     t0 = time.perf_counter()
     for i in range(e2e_n):
-        vol.render_to_host_async(sc.camera, sc.params, W, H, hosts[i % 2])
+        vol.render_to_host_async(sc.camera, sc.params, W, H, hosts[i % 2], window=window)
     vol.wait_host()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_n
-    e2e_value, e2e_ms = aggregate_ranks(e2e_ms, W * H, dist, "cuda")
+    e2e_value, e2e_ms = aggregate_ranks(e2e_ms, px_rank, dist, "cuda")
     t0 = time.perf_counter()
     for i in range(e2e_n):
-        vol.render_to_host(sc.camera, sc.params, W, H, hosts[i % 2])
+        vol.render_to_host(sc.camera, sc.params, W, H, hosts[i % 2], window=window)
     e2e_sync_ms = (time.perf_counter() - t0) * 1e3 / e2e_n
-    e2e_sync_value, e2e_sync_ms = aggregate_ranks(e2e_sync_ms, W * H, dist, "cuda")
+    e2e_sync_value, e2e_sync_ms = aggregate_ranks(e2e_sync_ms, px_rank, dist, "cuda")
 
     props = torch.cuda.get_device_properties(local)
     peaks = _peaks()
@@ -502,15 +564,18 @@ def run_ours(args):
         import ctypes
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if window is not None else "weak",
             "vs_baseline": None, "dtype": {0: "f32", 1: "f32+f64", 2: "f64"}[prec], "data": "synthetic",
-            "config": {"workload": workload, "width": W, "height": H, "rk_tol": sc.params.rk_tol,
+            "config": {"workload": workload, "width": FW, "height": FH, "rk_tol": sc.params.rk_tol,
                        "ds": sc.params.ds, "supersample_k": sc.params.supersample_k,
                        "l2": "flushed between steps (512 MiB write outside the timed events)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": ("row bands of one frame" if window is not None else "replicas")
+                       if world > 1 else "single"},
             "stages_ms": {k: v / args.steps for k, v in stage_sum.items()},
             "wall_s_timed_loop": t_wall,
-            "gpu_launches": kernels_per_frame(prec, args.rk_method) * args.steps,
+            "gpu_launches": kernels_per_frame(prec, args.rk_method, sc.params.method, sc.params.use_mlp_guess)
+                            * args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "ms_per_frame": e2e_ms,
                     "api": "ivv_render_to_host_async + ivv_render_to_host_wait (copies overlap the next render)",
@@ -524,6 +589,7 @@ def run_ours(args):
                                         "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
                                         "isect_newton")},
             "max_delta_p": st["max_delta_p"],
+            "guess_training_s": train_s,
             "parity": parity,
             "entry_exit_parity": pair_err,
             "clocks": clocks,
@@ -677,10 +743,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--ref-stride", type=int, default=96)
-    ap.add_argument("--workload", default="bar1080", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bar1080", choices=sorted(WORKLOADS) + sorted(LEARNED_WORKLOADS))
     ap.add_argument("--requests", type=int, default=0, help="batch64: keep the first N requests (0: all)")
     ap.add_argument("--only-volume", type=int, default=None, help="batch64: keep the requests of one volume")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default launch shapes")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "rows"],
+                    help="N > 1: every rank renders its own frame (replicas, weak scaling) or a band of rows of "
+                         "one frame (strong scaling)")
     ap.add_argument("--rk-method", type=int, default=0, choices=range(8),
                     help="single-frame workloads: 0 BS3(2) with error control, 1-6 the explicit fixed-step "
                          "family, 7 implicit Euler")

@@ -115,6 +115,8 @@ def lib():
         L.orc_window_pairs.argtypes = [C.c_void_p, C.POINTER(_Camera), C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), c_double_p,
                                        C.POINTER(C.c_int)]
+        L.orc_walk_into_block.argtypes = [C.c_void_p, C.c_int, c_double_p, c_double_p, C.c_double, C.c_double,
+                                          c_double_p, c_double_p, c_double_p, c_double_p]
         L.orc_t1_irk1_step.argtypes = [c_double_p, C.c_double, C.c_double, C.c_double, C.c_int, c_double_p]
         _LIB = L
     return _LIB
@@ -240,6 +242,16 @@ class OracleVolume:
                                cnt.ctypes.data_as(C.POINTER(C.c_int)), _dp(pairs),
                                blk.ctypes.data_as(C.POINTER(C.c_int)))
         return cnt, pairs, blk
+
+    def walk_into_block(self, block, o, d, t0, t1, p0, p1):
+        """First point of the ray segment [t0, t1] inside the block (§5.4's
+        walk along the ray): (t, p) or None."""
+        o, d, p0, p1 = _f64(o), _f64(d), _f64(p0), _f64(p1)
+        t = C.c_double()
+        p = np.zeros(3)
+        ok = lib().orc_walk_into_block(self.h, block, _dp(o), _dp(d), float(t0), float(t1), _dp(p0), _dp(p1),
+                                       C.byref(t), _dp(p))
+        return (t.value, p) if ok else None
 
     def invert(self, block, g, p0, tol=1e-13, maxit=50):
         g, p0 = _f64(g), _f64(p0)

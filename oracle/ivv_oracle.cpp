@@ -1108,6 +1108,47 @@ double mean_abs_det(const Block& b) {
   return sum;
 }
 
+// §5.4's first case: where the ray is outside the block just behind an entry
+// (an entry that only touches the block's boundary, so that the moved entry
+// point has no preimage in the block), the entry steps along the ray until
+// the ray is inside the block again: 16 probes t0 + k (t1 - t0) / 16 with
+// Newton from the chord guesses, then 50 bisections between the last probe
+// outside and the first inside.  Returns false if no probe is inside.
+bool walk_into_block(const Block& b, const double o[3], const double d[3], double t0, double t1,
+                     const double p0[3], const double p1[3], double tol, double* t_new, double p_new[3]) {
+  double t_lo = t0, t_hi = 0, p_hi[3], g[3], x[3];
+  bool found = false;
+  for (int k = 1; k <= 16 && !found; ++k) {
+    const double tk = t0 + (t1 - t0) * k / 16.0;
+    double x0[3];
+    for (int r = 0; r < 3; ++r) {
+      x0[r] = p0[r] + (p1[r] - p0[r]) * k / 16.0;
+      g[r] = o[r] + tk * d[r];
+    }
+    if (invert_point(b, g, x0, tol, 100, x) >= 0) {
+      found = true;
+      t_hi = tk;
+      for (int r = 0; r < 3; ++r) p_hi[r] = x[r];
+    } else {
+      t_lo = tk;
+    }
+  }
+  if (!found) return false;
+  for (int it = 0; it < 50; ++it) {
+    const double tm = 0.5 * (t_lo + t_hi);
+    for (int r = 0; r < 3; ++r) g[r] = o[r] + tm * d[r];
+    if (invert_point(b, g, p_hi, tol, 100, x) >= 0) {
+      t_hi = tm;
+      for (int r = 0; r < 3; ++r) p_hi[r] = x[r];
+    } else {
+      t_lo = tm;
+    }
+  }
+  *t_new = t_hi;
+  for (int r = 0; r < 3; ++r) p_new[r] = p_hi[r];
+  return true;
+}
+
 // §5.4, singular Jacobian at the entry point (Eq. 22): where |det J(p_in)|
 // is below tau_det = 1e-6 times the block's mean |det J|, neither Newton nor
 // the ODE's linear system can start at the entry, so the block is "shrunk":
@@ -1115,8 +1156,10 @@ double mean_abs_det(const Block& b) {
 // g~_in = g_in + delta d (reading: the paper adds the step to the entry in
 // G, so its direction is the ray's), and p~_in solves phi(p) = g~_in by
 // Newton (§5.1) started at x_0 = p_in + eps (p_out - p_in) / |p_out - p_in|
-// with eps = 1e-4 (Eq. 22).  A pair no longer than delta, or whose new
-// entry does not invert inside its block, is dropped.  Returns the pairs;
+// with eps = 1e-4 (Eq. 22).  If the moved entry has no preimage in the block
+// (the entry only touched its boundary), the entry walks along the ray into
+// the block (walk_into_block).  A pair no longer than delta, or that never
+// enters its block, is dropped.  Returns the pairs;
 // *shrunk counts the moved entries, *dropped the dropped pairs.
 std::vector<Pair> shrink_singular_entries(const Volume& V, const double o[3], const double d[3], double newton_tol,
                                           const std::vector<Pair>& in, int* shrunk, int* dropped) {
@@ -1141,7 +1184,8 @@ std::vector<Pair> shrink_singular_entries(const Volume& V, const double o[3], co
     for (int r = 0; r < 3; ++r) x0[r] = pr.p_in[r] + (nd > 0 ? eps * dir[r] / nd : 0.0);
     pr.t_in += delta;
     for (int r = 0; r < 3; ++r) g[r] = o[r] + pr.t_in * d[r];
-    if (invert_point(b, g, x0, newton_tol * V.diag, 100, q) < 0) {
+    if (invert_point(b, g, x0, newton_tol * V.diag, 100, q) < 0 &&
+        !walk_into_block(b, o, d, pr.t_in, pr.t_out, pr.p_in, pr.p_out, newton_tol * V.diag, &pr.t_in, q)) {
       if (dropped) ++*dropped;
       continue;
     }
@@ -1442,6 +1486,14 @@ int orc_pixel_pairs(void* v, const orc_camera* c, int W, int H, int x, int y, in
     for (int r = 0; r < 3; ++r) { out[i].p_in[r] = p[i].p_in[r]; out[i].p_out[r] = p[i].p_out[r]; }
   }
   return (int)p.size();
+}
+
+// The walk of §5.4's first case on one ray segment (test hook): returns 1
+// and the first point of [t0, t1] inside the block, or 0.
+int orc_walk_into_block(void* v, int block, const double* o, const double* d, double t0, double t1, const double* p0,
+                        const double* p1, double* t_new, double* p_new) {
+  const Volume* V = (const Volume*)v;
+  return walk_into_block(V->blocks[block], o, d, t0, t1, p0, p1, 1e-13 * V->diag, t_new, p_new) ? 1 : 0;
 }
 
 int orc_invert(void* v, int block, const double* g, const double* p0, double tol, int maxit, double* p) {

@@ -212,6 +212,52 @@ __device__ __forceinline__ R fixup_tol(const R g[3], float diag) {
   return tol + R(sizeof(R) == 4 ? 2e-7 : 1e-15) * m;
 }
 
+// §5.4's first case: where the ray is outside the block just behind an entry
+// (an entry that only touched the block's boundary, so that the moved entry
+// point has no preimage in the block), the entry steps along the ray until
+// the ray is inside the block again: 16 probes t0 + k (t1 - t0) / 16 with
+// Newton from the chord guesses, then 24 bisections between the last probe
+// outside and the first inside.  Returns false if no probe is inside.
+template <int P, typename R, bool MIXED>
+__device__ bool walk_into_block(const DevVolume& V, const BlockInfo& B, const R o[3], const R d[3], R t0,
+                                             R t1, const R p0[3], const R p1[3], R& t_new, R p_new[3],
+                                             unsigned long long& iters, unsigned long long& n64) {
+  R t_lo = t0, t_hi = t1, p_hi[3], g[3], x[3];
+  bool found = false;
+  for (int k = 1; k <= 16 && !found; ++k) {
+    const R tk = t0 + (t1 - t0) * R(k) / R(16);
+    for (int r = 0; r < 3; ++r) {
+      const R v = p0[r] + (p1[r] - p0[r]) * R(k) / R(16);
+      x[r] = v < R(0) ? R(0) : (v > R(1) ? R(1) : v);
+      g[r] = o[r] + tk * d[r];
+    }
+    if (clip_newton<P, R, MIXED>(V, B, g, x, fixup_tol<R>(g, V.diag), iters, n64)) {
+      found = true;
+      t_hi = tk;
+      for (int r = 0; r < 3; ++r) p_hi[r] = x[r];
+    } else {
+      t_lo = tk;
+    }
+  }
+  if (!found) return false;
+  for (int it = 0; it < 24; ++it) {
+    const R tm = R(0.5) * (t_lo + t_hi);
+    for (int r = 0; r < 3; ++r) {
+      x[r] = p_hi[r];
+      g[r] = o[r] + tm * d[r];
+    }
+    if (clip_newton<P, R, MIXED>(V, B, g, x, fixup_tol<R>(g, V.diag), iters, n64)) {
+      t_hi = tm;
+      for (int r = 0; r < 3; ++r) p_hi[r] = x[r];
+    } else {
+      t_lo = tm;
+    }
+  }
+  t_new = t_hi;
+  for (int r = 0; r < 3; ++r) p_new[r] = p_hi[r];
+  return true;
+}
+
 // The clip fix-up: one thread per active pixel solves the flagged ends of
 // its pairs; a pair whose end does not invert inside its block gets zero
 // length (skipped by stage 3).  Newton starts: an entry listed for the
@@ -270,6 +316,13 @@ __global__ void __launch_bounds__(128) k4_clip_solve(DevVolume V, DevCamera<R> c
           }
           for (int r = 0; r < 3; ++r) pq[r] = pq[r] < R(0) ? R(0) : (pq[r] > R(1) ? R(1) : pq[r]);
           ok = clip_newton<P, R, MIXED>(V, B, g, pq, tol_g, c_it, c_64);
+        }
+        if (!ok && e == 0 && (bf & kShrunk)) {
+          // a moved singular entry without a preimage: walk into the block
+          R t_new, p0[3] = {R(rec.y), R(rec.z), R(rec.w)};
+          const R p1[3] = {R(other.y), R(other.z), R(other.w)};
+          ok = walk_into_block<P, R, MIXED>(V, B, o, d, R(rec.x), R(other.x), p0, p1, t_new, pq, c_it, c_64);
+          if (ok) rec.x = t_new;
         }
         rec.y = pq[0]; rec.z = pq[1]; rec.w = pq[2];
         if (e == 0) pair_in[slot] = rec; else pair_out[slot] = rec;
@@ -424,8 +477,10 @@ __global__ void __launch_bounds__(128) k4_entry_fix(DevVolume V, DevCamera<R> ca
           }
           ok = clip_newton<P, R, MIXED>(V, B, g, x, tol_g, c_it, c_64);
         }
+        R t_new = t_in;
+        if (!ok) ok = walk_into_block<P, R, MIXED>(V, B, o, d, t_in, R(out.x), p, p_out, t_new, x, c_it, c_64);
         if (ok) {
-          in.x = t_in;
+          in.x = t_new;
           in.y = x[0];
           in.z = x[1];
           in.w = x[2];

@@ -347,20 +347,20 @@ class Volume:
                                          C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
         return out
 
-    def render_to_host(self, camera, params, width, height, out_host, stream=None, flags=0):
+    def render_to_host(self, camera, params, width, height, out_host, stream=None, flags=0, window=None):
         """Render and copy into host memory (numpy float32 [H][W][4] or a pinned tensor)."""
-        prm = params_struct(params, flags)
+        prm = params_struct(params, flags, window)
         cam = camera_struct(camera)
         ptr = out_host.ctypes.data if isinstance(out_host, np.ndarray) else out_host.data_ptr()
         _check(load().ivv_render_to_host(self.h, C.byref(cam), C.byref(prm), width, height, C.c_void_p(ptr),
                                          C.c_void_p(_stream_ptr(stream))))
         return out_host
 
-    def render_to_host_async(self, camera, params, width, height, out_host, stream=None, flags=0):
+    def render_to_host_async(self, camera, params, width, height, out_host, stream=None, flags=0, window=None):
         """Queue a render whose image is copied into pinned host memory (a
         pinned tensor or numpy array) while later frames render; the image is
         valid after wait_host()."""
-        prm = params_struct(params, flags)
+        prm = params_struct(params, flags, window)
         cam = camera_struct(camera)
         ptr = out_host.ctypes.data if isinstance(out_host, np.ndarray) else out_host.data_ptr()
         _check(load().ivv_render_to_host_async(self.h, C.byref(cam), C.byref(prm), width, height, C.c_void_p(ptr),

@@ -89,3 +89,25 @@ def test_twisted_degenerate_cube_renders():
     assert np.isfinite(img).all()
     assert st[..., 5].sum() > 200 and st[..., 2].sum() == 0
     assert img[..., 3].max() > 0.3
+
+
+def test_walk_into_the_block_finds_the_boundary():
+    """§5.4's walk along the ray: from a point above the flat degenerate cube
+    (outside the block) toward a point inside, the first point inside is where
+    the ray crosses the top face z = 1 (closed form), with its parameter
+    point on the face w = 1."""
+    sc = _flat_cube()
+    vol = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    o = np.array([0.3, 0.6, 3.0])
+    d = np.array([0.2, -0.1, -1.0])
+    d /= np.linalg.norm(d)
+    t_top = (3.0 - 1.0) / -d[2]
+    t0, t1 = t_top - 0.3, t_top + 0.5
+    got = vol.walk_into_block(0, o, d, t0, t1, [0.5, 0.5, 1.0], [0.5, 0.5, 0.5])
+    assert got is not None
+    t, p = got
+    assert abs(t - t_top) < 1e-12
+    g = o + t * d
+    np.testing.assert_allclose(p[:2], g[:2], atol=1e-9)
+    assert abs(p[2] - 1.0) < 1e-4                   # w = 1 - (1 - z)^(1/3) is steep at the face
+    assert vol.walk_into_block(0, o, d, t0, t_top - 0.1, [0.5, 0.5, 1.0], [0.5, 0.5, 0.9]) is None
