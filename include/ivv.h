@@ -226,6 +226,7 @@ typedef struct {
   unsigned long long rho_evals;     /* samples whose scalar was evaluated on its own (shading pass) */
   unsigned long long entry_shrinks; /* entries with a singular Jacobian moved into the block (§5.4, Eq. 22) */
   unsigned long long entry_newton;  /* Newton iterations of the stage-2 fix-up solves (§5.4, §5.5) */
+  unsigned long long async_timeouts; /* bounded waits for tensor-core work that gave up (a device fault) */
   double max_delta_p;               /* max pixel-accuracy error Delta P (Eq. 5) */
 } ivv_stats;
 
@@ -452,7 +453,8 @@ ivv_status ivv_get_limits(const ivv_volume* vol, ivv_limits* limits);
 
 /* Status of the renders since the last ivv_check_frame (or ivv_reset_stats):
  * synchronises the stream of the last render and reads the overflow and cap
- * counters that every render keeps.  Returns IVV_ERR_ABUF_OVERFLOW if any
+ * counters that every render keeps.  Returns IVV_ERR_CUDA if a bounded
+ * wait for tensor-core work gave up, else IVV_ERR_ABUF_OVERFLOW if any
  * fragment, pair or stage-1 candidate was dropped, else IVV_ERR_NONCONVERGED
  * if an entry/exit pair hit the RK step cap or an RF sample missed its
  * tolerance, else IVV_OK; ivv_last_error() names the counts.  The images

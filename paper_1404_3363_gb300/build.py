@@ -22,7 +22,7 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I", INCLUDE]
 
 CU_SOURCES = ["ivv_api.cu", "k_surface.cu", "k_pair.cu", "k_integrate_p2.cu", "k_integrate_p3.cu",
-              "k_eval.cu", "host_debug.cu", "k_mlp.cu", "k_rf.cu", "batch.cu", "k_batch.cu",
+              "k_eval.cu", "host_debug.cu", "k_mlp.cu", "k_mlp_tc.cu", "k_rf.cu", "batch.cu", "k_batch.cu",
               "k_integrate_batch.cu", "k_fixed_p2.cu", "k_fixed_p3.cu"]
 CXX_SOURCES = ["host_prep.cpp"]
 

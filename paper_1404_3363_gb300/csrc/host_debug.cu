@@ -92,7 +92,7 @@ ivv_status host_pairs(const ivv::HostVolume& hv, const ivv::DevCamera<float>& c3
           if (sizeof(R) == 4 && mixed && cosang < R(kPolishCos)) {
             double a64 = a, b64 = b2, t64 = t, o64[3], d64[3];
             make_ray<double>(c64, px, py, o64, d64);
-            refine_hit_fp64<P, Dbl4>(&face64[(size_t)f * NN], m64.org, o64, d64, a64, b64, t64);
+            refine_hit_mixed<P>(&face64[(size_t)f * NN], &face32[(size_t)f * NN], m64.org, o64, d64, a64, b64, t64);
             t = R(t64);
             const int nd = m.face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
             pp[ad] = R(std::fmin(std::fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));

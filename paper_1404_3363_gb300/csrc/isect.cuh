@@ -586,38 +586,67 @@ IVV_HD void make_fragment(const V4* cp, const R org[3], const FaceMeta& m, const
 // rounding), so 0.35 keeps every hit within 1e-5.
 constexpr float kPolishCos = 0.35f;
 
-// FP64 polish of a hit near a silhouette: Newton on S(a,b) - o - t d = 0
-// with the FP64 face patch (control points relative to org).
-template <int P, typename V4>
-IVV_HD void refine_hit_fp64(const V4* cp, const double org[3], const double o[3], const double d[3], double& a,
-                            double& b, double& t) {
+// Patch value S(a,b) relative to the patch origin (no partials).
+template <int P, typename R, typename V4>
+IVV_HD void patch_value3_rel(const V4* cp, R a, R b, R S[3]) {
+  constexpr int N = P + 1;
+  R ba[N], dba[N], bb[N], dbb[N];
+  bern_hd<P, R>(a, ba, dba);
+  bern_hd<P, R>(b, bb, dbb);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) S[r] = R(0);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    R t0[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const V4 c = cp[j * N + i];
+      t0[0] += ba[i] * R(c.x); t0[1] += ba[i] * R(c.y); t0[2] += ba[i] * R(c.z);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) S[r] += bb[j] * t0[r];
+  }
+}
+
+// Mixed-precision polish of a hit near a silhouette: Newton on
+// S(a,b) - o - t d = 0 whose residual is evaluated in FP64 (the FP64 face
+// patch cp64, control points relative to org64) while the Jacobian
+// [S_a S_b -d] and the 3x3 solve stay in FP32 (the FP32 patch cp32): the
+// classic refinement by an accurate residual.  Each step shrinks the error by
+// about |cos|^-1 times the FP32 rounding, so a few steps reach the FP64 root;
+// the FP64 work is the patch value alone.
+template <int P, typename V4D>
+IVV_HD void refine_hit_mixed(const V4D* cp64, const float4* cp32, const double org[3], const double o[3],
+                             const double d[3], double& a, double& b, double& t) {
   for (int it = 0; it < 4; ++it) {
-    double S[3], Sa[3], Sb[3];
-    patch_eval3_rel<P, double, V4>(cp, a, b, S, Sa, Sb);
-    double F[3];
-    for (int r = 0; r < 3; ++r) F[r] = -((org[r] - o[r]) + S[r] - t * d[r]);
-    // solve [Sa Sb -d] x = F by Cramer
-    const double A[3][3] = {{Sa[0], Sb[0], -d[0]}, {Sa[1], Sb[1], -d[1]}, {Sa[2], Sb[2], -d[2]}};
-    const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
-    const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
-    const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
-    const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
-    if (det == 0.0) break;
-    const double c10 = A[0][2] * A[2][1] - A[0][1] * A[2][2];
-    const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
-    const double c12 = A[0][1] * A[2][0] - A[0][0] * A[2][1];
-    const double c20 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-    const double c21 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
-    const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    const double inv = 1.0 / det;
-    const double x0 = (c00 * F[0] + c10 * F[1] + c20 * F[2]) * inv;
-    const double x1 = (c01 * F[0] + c11 * F[1] + c21 * F[2]) * inv;
-    const double x2 = (c02 * F[0] + c12 * F[1] + c22 * F[2]) * inv;
-    if (!(fabs(x0) < 0.5 && fabs(x1) < 0.5)) break;
+    double S[3];
+    patch_value3_rel<P, double, V4D>(cp64, a, b, S);
+    float F[3];
+    for (int r = 0; r < 3; ++r) F[r] = (float)(-((org[r] - o[r]) + S[r] - t * d[r]));
+    float S32[3], Sa[3], Sb[3];
+    patch_eval3_rel<P, float, float4>(cp32, (float)a, (float)b, S32, Sa, Sb);
+    const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+    const float A[3][3] = {{Sa[0], Sb[0], -df[0]}, {Sa[1], Sb[1], -df[1]}, {Sa[2], Sb[2], -df[2]}};
+    const float c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    const float c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    const float c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    const float det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+    if (det == 0.f) break;
+    const float c10 = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    const float c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    const float c12 = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    const float c20 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    const float c21 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    const float c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    const float inv = 1.f / det;
+    const float x0 = (c00 * F[0] + c10 * F[1] + c20 * F[2]) * inv;
+    const float x1 = (c01 * F[0] + c11 * F[1] + c21 * F[2]) * inv;
+    const float x2 = (c02 * F[0] + c12 * F[1] + c22 * F[2]) * inv;
+    if (!(fabsf(x0) < 0.5f && fabsf(x1) < 0.5f)) break;
     a += x0; b += x1; t += x2;
-    // Newton converges quadratically from the FP32 root: after an update
-    // below 1e-12 the next one is below FP64 resolution
-    if (fabs(x0) + fabs(x1) < 1e-12) break;
+    // the fragment keeps FP32 parameters: corrections below 1e-9 of the
+    // patch are beyond what it stores
+    if (fabsf(x0) + fabsf(x1) < 1e-9f) break;
   }
 }
 

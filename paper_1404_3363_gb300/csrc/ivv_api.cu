@@ -48,8 +48,12 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
   size_t boxes, gboxes, items, slow, frag_tp, frag_meta, frag_count, pair_in, pair_out, pair_block, pair_count, active,
-      tile_flag, counters, total;
+      tile_flag, polish, counters, total;
 };
+
+// Grazing hits per frame whose FP64 polish (mixed precision) runs in its own
+// pass: one per pixel of the window (beyond it, hits are polished inline).
+size_t polish_cap(size_t npix) { return std::max<size_t>(npix, 1024); }
 
 WsLayout layout(int n_faces, size_t npix, size_t v4) {
   WsLayout L;
@@ -69,6 +73,7 @@ WsLayout layout(int n_faces, size_t npix, size_t v4) {
   L.active = take(sizeof(int) * npix);
   // one flag per 16 x 16 tile: ceil(w/16) ceil(h/16) <= npix/256 + (w+h)/16 + 1 <= npix/8 + 3
   L.tile_flag = take(sizeof(int) * (npix / 8 + 64));
+  L.polish = take(2 * sizeof(float4) * polish_cap(npix));
   L.counters = take(ivv::kCountersBytes);
   L.total = o;
   return L;
@@ -136,6 +141,9 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   V.diag = (float)v->hv.diag;
   V.max_frags = v->lim_frags;
   V.max_newton = v->lim_newton;
+  V.polish = nullptr;
+  V.polish_cap = 0;
+  V.n_polish = nullptr;
   return V;
 }
 
@@ -329,10 +337,15 @@ template <typename R>
 ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_params& p, char* ws, const WsLayout& L,
                              int max_pairs, float4* out_zero, cudaStream_t s) {
   typedef typename ivv::Vec4T<R>::type V4;
-  const ivv::DevVolume V = dev_volume(v);
+  ivv::DevVolume V = dev_volume(v);
   const int npix = F.w * F.h;
   const bool stats = (p.flags & IVV_FLAG_STATS) != 0;
   const bool mixed = p.precision == IVV_PREC_MIXED;
+  if (mixed && sizeof(R) == 4) {
+    V.polish = (float4*)(ws + L.polish);
+    V.polish_cap = (int)std::min<size_t>(polish_cap((size_t)npix), 0x7fffffff);
+    V.n_polish = (int*)(ws + L.counters) + ivv::kPolishCounter;
+  }
   const bool timing = (p.flags & IVV_FLAG_TIMING) != 0;
   IVV_CUDA(cudaMemsetAsync(ws + L.counters, 0, ivv::kCountersBytes, s));
   ivv::SurfaceWs sw;
@@ -381,7 +394,7 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
                               (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
                               (const int*)(ws + L.counters), v->hv.any_singular, mixed, gl, v->d_stats, v->num_sms,
                               s);
-    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, gl.g, gl.blk, gl.n, 0, gl.p, v->num_sms, s);
+    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, gl.g, gl.blk, gl.n, 0, gl.p, v->d_stats, v->num_sms, s);
     ivv::launch_clip_solve<R>(V, clip.cam, npix, (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                               (int*)(ws + L.pair_block), (const int*)(ws + L.pair_count), (const int*)(ws + L.active),
                               (const int*)(ws + L.counters), mixed, &gl, v->d_stats, v->num_sms, s);
@@ -494,7 +507,7 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     ivv::launch_rf_expand(c32, pin, pout, pblk, pcnt, act, counters, off, (int)npix, (float)p.ds, tail_eps,
                           p.use_mlp_guess, total, sg, sblk, sp, v->num_sms, s);
     if (p.use_mlp_guess == IVV_GUESS_MLP)
-      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->num_sms, s);
+      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s);
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,
                           stats, mixed, v->num_sms, s);
@@ -1062,8 +1075,8 @@ ivv_status ivv_guess_points(ivv_volume* v, int n, const float* g, const int* blo
   if (!v->guess_ready) return fail(IVV_ERR_INVALID_ARG, "the guess network is neither trained nor set");
   if (((uintptr_t)g) % 16 || ((uintptr_t)p_out) % 16) return fail(IVV_ERR_INVALID_ARG, "g and p_out must be 16-byte aligned");
   if (n == 0) return IVV_OK;
-  ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->num_sms,
-                        (cudaStream_t)stream);
+  ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->d_stats,
+                        v->num_sms, (cudaStream_t)stream);
   IVV_CUDA(cudaGetLastError());
   return IVV_OK;
 }
@@ -1079,7 +1092,8 @@ ivv_status ivv_invert_points(ivv_volume* v, int n, const float* g, const int* bl
   cudaStream_t s = (cudaStream_t)stream;
   IVV_CUDA(cudaMemcpyAsync(v->d_count, &n, sizeof(int), cudaMemcpyHostToDevice, s));
   if (guess == IVV_GUESS_MLP)
-    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out, v->num_sms, s);
+    ivv::launch_mlp_infer(v->d_theta16, v->d_norms, (const float4*)g, block_of, nullptr, n, (float4*)p_out,
+                          v->d_stats, v->num_sms, s);
   else
     ivv::launch_fill_center((float4*)p_out, n, s);
   ivv::DevCamera<float> cam{};
@@ -1218,6 +1232,7 @@ void stats_to_public(const DevStats& d, ivv_stats* out) {
   out->rho_evals = d.rho_evals;
   out->entry_shrinks = d.entry_shrinks;
   out->entry_newton = d.entry_newton;
+  out->async_timeouts = d.async_timeouts;
   float f;
   std::memcpy(&f, &d.max_delta_p_bits, sizeof(f));
   out->max_delta_p = f;
@@ -1267,6 +1282,8 @@ ivv_status ivv_check_frame(ivv_volume* v) {
   IVV_CUDA(cudaStreamSynchronize(v->last_stream));
   ivv::DevStats d;
   IVV_CUDA(cudaMemcpy(&d, v->d_stats, sizeof(d), cudaMemcpyDeviceToHost));
+  if (d.async_timeouts)
+    return fail(IVV_ERR_CUDA, std::to_string(d.async_timeouts) + " bounded waits for the tensor cores gave up");
   const unsigned long long ov = d.abuf_overflow + d.pair_overflow, cap = d.step_cap + d.rf_unconverged;
   const unsigned long long new_ov = ov - std::min(ov, v->seen_overflow), new_cap = cap - std::min(cap, v->seen_cap);
   v->seen_overflow = ov;

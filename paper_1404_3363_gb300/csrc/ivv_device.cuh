@@ -132,6 +132,11 @@ struct DevVolume {
   float diag;
   int max_frags;          // fragment slots in use per pixel (<= kMaxFrags)
   int max_newton;         // Newton iterations of a per-point inversion (RF method, point location)
+  // per frame, mixed precision: the list of grazing hits whose FP64 polish
+  // is deferred to its own pass (two float4 per hit), or null (inline polish)
+  float4* polish;
+  int polish_cap;
+  int* n_polish;
 };
 
 struct DevTF {
@@ -145,7 +150,7 @@ struct DevTF {
 struct DevStats {
   unsigned long long rays, pairs, fragments, samples, rk_steps, rk_rejects, rhs_evals,
       isect_newton, isect_tests, fp64_solves, abuf_overflow, pair_overflow, unmatched, step_cap, rf_newton_iters,
-      rf_unconverged, isect_items, isect_split, rho_evals, entry_shrinks, entry_newton;
+      rf_unconverged, isect_items, isect_split, rho_evals, entry_shrinks, entry_newton, async_timeouts;
   unsigned int max_delta_p_bits;   // float bits of max Delta P (non-negative: int order)
   unsigned int pad;
 };
@@ -587,8 +592,9 @@ __device__ __forceinline__ float4 tf_eval_seg(const float* __restrict__ r, const
 // Counters block of a render: [0] active pixels, [2] sample total, [3]
 // spare, [4] stage-1 items, [5] their hand-out head, [6] deferred items, [7]
 // their hand-out head, [8] and [9] the batch's overflow list and its queue
-// head, [10] the shading pass's queue head; the integrator's queue head at
-// kQueueHeadOff.
+// head, [10] the shading pass's queue head, [11] the learned-guess list of
+// stage 2, [12] the FP64 polish list of stage 1; the integrator's queue head
+// at kQueueHeadOff.
 constexpr int kQueueHeadOff = 1;
 constexpr int kItemCounter = 4;
 constexpr int kItemHead = 5;         // next stage-1 item to hand out (K2b)
@@ -636,6 +642,7 @@ void launch_face_project(const DevVolume& V, const DevCamera<float>& cam, int4* 
 template <typename R>
 void launch_intersect(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, bool mixed,
                       bool stats, const SurfaceWs& w, DevStats* st, int num_sms, cudaStream_t s);
+constexpr int kPolishCounter = 12;   // counters slot: grazing hits listed for the FP64 polish pass
 
 // Cutting and near-clip planes (§5.5) applied by K4 to the depth-sorted
 // intersections of each pixel.  Ends that move onto a plane are flagged in

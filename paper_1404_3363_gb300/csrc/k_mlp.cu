@@ -226,160 +226,6 @@ __global__ void k_mlp_to_half(const float* __restrict__ theta, __half* __restric
   if (i < n) theta16[i] = __float2half_rn(theta[i]);
 }
 
-// ----------------------------------------------------------- inference
-__device__ __forceinline__ unsigned pack_half2(float a, float b) {
-  const __half2 h = __floats2half2_rn(a, b);
-  return *reinterpret_cast<const unsigned*>(&h);
-}
-
-__device__ __forceinline__ void mma16816(float c[4], const unsigned a[4], const unsigned b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int kInferWarps = 4;
-
-// p_hat for n points.  xs [n] float4: normalised input (x, y, z) and the
-// block index in w (as a float); only points of `block` are written when
-// block >= 0, all when the tile is uniform in its block (see caller).
-__global__ void __launch_bounds__(32 * kInferWarps) k_mlp_infer(const __half* __restrict__ theta16_all,
-                                                                const MlpNorm* __restrict__ norms,
-                                                                const float4* __restrict__ g, const int* __restrict__ gblk,
-                                                                const int* __restrict__ n_ptr, int n_static,
-                                                                float4* __restrict__ p_out) {
-  const int lane = threadIdx.x & 31;
-  const int grp = lane >> 2, tq = lane & 3;
-  const int n = n_ptr ? *n_ptr : n_static;
-  const int warp_global = blockIdx.x * kInferWarps + (threadIdx.x >> 5);
-  const int warps_total = gridDim.x * kInferWarps;
-  for (int tile = warp_global; tile * 16 < n; tile += warps_total) {
-    const int r0 = tile * 16 + grp, r1 = r0 + 8;
-    const int b0 = r0 < n ? __ldg(gblk + r0) : -1;
-    const int b1 = r1 < n ? __ldg(gblk + r1) : -1;
-    // the blocks present in this tile, handled one at a time
-    int todo_b = __shfl_sync(0xffffffffu, b0 >= 0 ? b0 : b1, 0);
-    unsigned pending = 0;
-    {
-      const bool mine = (b0 >= 0) || (b1 >= 0);
-      pending = __ballot_sync(0xffffffffu, mine);
-    }
-    bool done0 = b0 < 0, done1 = b1 < 0;
-    for (int guard = 0; guard < 32 && pending; ++guard) {
-      // pick the first unfinished block in the tile
-      const unsigned want = __ballot_sync(0xffffffffu, !done0 || !done1);
-      if (!want) break;
-      const int src = __ffs(want) - 1;
-      todo_b = __shfl_sync(0xffffffffu, !done0 ? b0 : b1, src);
-      const __half* th = theta16_all + (size_t)todo_b * kMlpStride;
-      const MlpNorm nm = norms[todo_b];
-      float x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
-      if (r0 < n) {
-        const float4 a = g[r0];
-        x0[0] = (a.x - nm.c[0]) * nm.inv_h[0]; x0[1] = (a.y - nm.c[1]) * nm.inv_h[1];
-        x0[2] = (a.z - nm.c[2]) * nm.inv_h[2];
-      }
-      if (r1 < n) {
-        const float4 a = g[r1];
-        x1[0] = (a.x - nm.c[0]) * nm.inv_h[0]; x1[1] = (a.y - nm.c[1]) * nm.inv_h[1];
-        x1[2] = (a.z - nm.c[2]) * nm.inv_h[2];
-      }
-      // layer 1 on the FP32 pipe, written as A fragments of layer 2 (K = 64)
-      unsigned A[4][4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const int c = 16 * s + 8 * half + 2 * tq;
-          float h[2][2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int col = c + e;
-            const float w0 = __half2float(th[kOffW1 + 3 * col]), w1 = __half2float(th[kOffW1 + 3 * col + 1]);
-            const float w2 = __half2float(th[kOffW1 + 3 * col + 2]), bb = __half2float(th[kOffB1 + col]);
-            const float z0 = bb + w0 * x0[0] + w1 * x0[1] + w2 * x0[2];
-            const float z1 = bb + w0 * x1[0] + w1 * x1[1] + w2 * x1[2];
-            h[0][e] = z0 > 0.f ? z0 : 0.f;
-            h[1][e] = z1 > 0.f ? z1 : 0.f;
-          }
-          A[s][2 * half] = pack_half2(h[0][0], h[0][1]);      // row grp
-          A[s][2 * half + 1] = pack_half2(h[1][0], h[1][1]);  // row grp + 8
-        }
-      }
-      // layer 2: [16 x 64] x W2^T -> [16 x 64], 8 n-tiles x 4 k-steps
-      float C[8][4];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int col = 8 * t + 2 * tq;
-        const float bb0 = __half2float(th[kOffB2 + col]), bb1 = __half2float(th[kOffB2 + col + 1]);
-        C[t][0] = bb0; C[t][1] = bb1; C[t][2] = bb0; C[t][3] = bb1;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          // B(k, n) = W2[n][k]; n = 8t + grp, k = 16s + 2tq (+1), +8
-          const __half* wr = th + kOffW2 + (8 * t + grp) * kMlpH + 16 * s + 2 * tq;
-          unsigned b[2];
-          b[0] = *reinterpret_cast<const unsigned*>(wr);
-          b[1] = *reinterpret_cast<const unsigned*>(wr + 8);
-          // A fragment register order: {row g k0-7, row g+8 k0-7, row g k8-15, row g+8 k8-15}
-          const unsigned a[4] = {A[s][0], A[s][1], A[s][2], A[s][3]};
-          mma16816(C[t], a, b);
-        }
-      }
-      // ReLU and repack as A fragments of layer 3
-      unsigned A3[4][4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const float* lo = C[2 * s];
-        const float* hi = C[2 * s + 1];
-        A3[s][0] = pack_half2(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
-        A3[s][1] = pack_half2(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
-        A3[s][2] = pack_half2(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
-        A3[s][3] = pack_half2(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
-      }
-      // layer 3: [16 x 64] x W3^T (3 outputs padded to 8)
-      float D[4];
-      {
-        const int col = 2 * tq;
-        D[0] = col < 3 ? __half2float(th[kOffB3 + col]) : 0.f;
-        D[1] = col + 1 < 3 ? __half2float(th[kOffB3 + col + 1]) : 0.f;
-        D[2] = D[0];
-        D[3] = D[1];
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        unsigned b[2] = {0u, 0u};
-        if (grp < 3) {
-          const __half* wr = th + kOffW3 + grp * kMlpH + 16 * s + 2 * tq;
-          b[0] = *reinterpret_cast<const unsigned*>(wr);
-          b[1] = *reinterpret_cast<const unsigned*>(wr + 8);
-        }
-        mma16816(D, A3[s], b);
-      }
-      // outputs: lanes tq = 0 hold columns 0,1; tq = 1 holds column 2
-      const bool w0 = !done0 && b0 == todo_b, w1 = !done1 && b1 == todo_b;
-      float o0[3], o1[3];
-      // gather (col0, col1) from tq=0 and col2 from tq=1 of the same group
-      const float c00 = __shfl_sync(0xffffffffu, D[0], (lane & ~3) | 0);
-      const float c01 = __shfl_sync(0xffffffffu, D[1], (lane & ~3) | 0);
-      const float c02 = __shfl_sync(0xffffffffu, D[0], (lane & ~3) | 1);
-      const float c10 = __shfl_sync(0xffffffffu, D[2], (lane & ~3) | 0);
-      const float c11 = __shfl_sync(0xffffffffu, D[3], (lane & ~3) | 0);
-      const float c12 = __shfl_sync(0xffffffffu, D[2], (lane & ~3) | 1);
-      o0[0] = c00; o0[1] = c01; o0[2] = c02;
-      o1[0] = c10; o1[1] = c11; o1[2] = c12;
-      if (tq == 0) {
-        if (w0 && r0 < n) p_out[r0] = make_float4(o0[0], o0[1], o0[2], 0.f);
-        if (w1 && r1 < n) p_out[r1] = make_float4(o1[0], o1[1], o1[2], 0.f);
-      }
-      if (w0) done0 = true;
-      if (w1) done1 = true;
-      pending = __ballot_sync(0xffffffffu, !done0 || !done1);
-    }
-  }
-}
-
 }  // namespace
 
 void launch_mlp_samples(const DevVolume& V, const MlpNorm& norm, int block, int S, unsigned long long seed,
@@ -425,16 +271,5 @@ void launch_mlp_to_half(const float* theta, __half* theta16, int n, cudaStream_t
   k_mlp_to_half<<<(n + 255) / 256, 256, 0, s>>>(theta, theta16, n);
 }
 
-void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
-                      int n_static, float4* p_out, int num_sms, cudaStream_t s) {
-  int grid = num_sms * 8;
-  if (!n_ptr) {
-    const int tiles = (n_static + 15) / 16;
-    const int need = (tiles + kInferWarps - 1) / kInferWarps;
-    grid = need < grid ? need : grid;
-    if (grid < 1) grid = 1;
-  }
-  k_mlp_infer<<<grid, 32 * kInferWarps, 0, s>>>(theta16, norms, g, gblk, n_ptr, n_static, p_out);
-}
 
 }  // namespace ivv

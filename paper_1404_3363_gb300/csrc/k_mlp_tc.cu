@@ -1,0 +1,280 @@
+// K6 inference of the learned initial guess on the 5th-generation tensor
+// cores: per block a 3-64-64-3 perceptron (ReLU), FP16 weights, FP32
+// accumulation.  One CTA of 128 threads takes a contiguous run of tiles of
+// 128 listed points (one thread per point = one row of the MMA):
+//   layer 1 (3 -> 64) on the FP32 pipe, its ReLU output rounded to FP16 and
+//     stored as the A operand in shared memory;
+//   layer 2 (64 -> 64) as one tcgen05.mma M = 128, N = 64, K = 64 (four
+//     K = 16 steps) issued by one thread, A and B (W2, K-major) read from
+//     shared memory through matrix descriptors, the FP32 accumulator in
+//     tensor memory (64 columns, allocated once per CTA);
+//   layer 3 (64 -> 3) on the FP32 pipe from the accumulator row (tcgen05.ld),
+//     its input rounded to FP16 as the weights' precision.
+// A tile whose points lie in several blocks runs one pass per block, each
+// with that block's weights (staged in shared memory when the block
+// changes); rows of other blocks ride along and are not written.  The MMA's
+// completion is awaited on an mbarrier with a bounded spin: a wait that gives
+// up counts in DevStats::async_timeouts and the CTA writes no further points.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "ivv_device.cuh"
+#include "mlp.cuh"
+
+namespace ivv {
+namespace {
+
+constexpr int kTcRows = 128;               // points per tile = M of the MMA = threads per CTA
+constexpr unsigned kTmemCols = 64;         // accumulator: 128 lanes x 64 FP32 columns
+constexpr long long kWaitSpins = 1ll << 22;
+
+// Shared-memory operands in the K-major layout without swizzling: 8 x 8
+// "core matrices" (8 rows of 16 bytes, 128 contiguous bytes); along K the
+// core matrices of an 8-row group follow each other (leading byte offset
+// 128), and the 8-row groups are 8 core matrices apart (stride byte offset
+// 1024, K = 64 halves).
+__device__ __forceinline__ int core_off(int row, int k) {
+  return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+struct __align__(1024) TcSmem {
+  __half a[kTcRows * kMlpH];       // layer-2 A operand (16 KB)
+  __half b[kMlpH * kMlpH];         // W2 of the loaded block (8 KB), B operand
+  float w1[kMlpH * 3], b1[kMlpH], b2[kMlpH], w3[3 * kMlpH], b3[4];
+  float nc[3], ninv[3];            // input normalisation of the loaded block
+  unsigned long long mbar;
+  unsigned tmem;
+  int block;                       // block whose weights are loaded (-1: none)
+  int next;                        // the tile's next block to run
+  int err;
+};
+
+// Matrix descriptor of a shared-memory operand starting at p (no swizzle).
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);     // start address
+  d |= (uint64_t)(128u >> 4) << 16;                // leading byte offset: next core matrix along K
+  d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                          // descriptor version of tcgen05
+  return d;                                        // base offset 0, layout: no swizzle
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kMlpH >> 3) << 17) |
+                            ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tmem_alloc(unsigned* dst) {       // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(kTmemCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr) {    // the allocating warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(unsigned d, uint64_t a, uint64_t b, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* mbar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// 16 consecutive FP32 columns of this thread's accumulator row.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait for the phase `parity` of the MMA barrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity) {
+  for (long long i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __restrict__ theta16_all,
+                                                         const MlpNorm* __restrict__ norms,
+                                                         const float4* __restrict__ g, const int* __restrict__ gblk,
+                                                         const int* __restrict__ n_ptr, int n_static,
+                                                         float4* __restrict__ p_out, DevStats* __restrict__ st) {
+  __shared__ TcSmem sm;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tmem_alloc(&sm.tmem);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sm.block = -1;
+    sm.err = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = sm.tmem;
+  const int n = n_ptr ? *n_ptr : n_static;
+  unsigned phase = 0;
+  // each CTA takes a contiguous run of tiles: neighbouring list entries
+  // mostly share a block, so the staged weights are reused
+  const int tiles = (n + kTcRows - 1) / kTcRows;
+  const int per_cta = (tiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int tile0 = blockIdx.x * per_cta, tile1 = min(tiles, tile0 + per_cta);
+  for (int tile = tile0; tile < tile1; ++tile) {
+    const int item = tile * kTcRows + tid;
+    const int myb = item < n ? __ldg(gblk + item) : -1;
+    float4 gi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (item < n) gi = __ldg(g + item);
+    bool done = myb < 0;
+    for (int pass = 0; pass < kTcRows; ++pass) {
+      // the smallest block of the tile not yet done
+      if (tid == 0) sm.next = INT_MAX;
+      __syncthreads();
+      if (!done) atomicMin(&sm.next, myb);
+      __syncthreads();
+      const int bsel = sm.next;
+      if (bsel == INT_MAX || sm.err) break;
+      if (sm.block != bsel) {
+        const __half* th = theta16_all + (size_t)bsel * kMlpStride;
+        for (int c = tid; c < kMlpH * (kMlpH / 8); c += kTcRows) {
+          const int nrow = c / (kMlpH / 8), kc = c % (kMlpH / 8);
+          const uint4 v = *reinterpret_cast<const uint4*>(th + kOffW2 + nrow * kMlpH + kc * 8);
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b) + core_off(nrow, kc * 8)) = v;
+        }
+        for (int i = tid; i < kMlpH * 3; i += kTcRows) {
+          sm.w1[i] = __half2float(th[kOffW1 + i]);
+          sm.w3[i] = __half2float(th[kOffW3 + i]);
+        }
+        if (tid < kMlpH) {
+          sm.b1[tid] = __half2float(th[kOffB1 + tid]);
+          sm.b2[tid] = __half2float(th[kOffB2 + tid]);
+        }
+        if (tid < 3) {
+          sm.b3[tid] = __half2float(th[kOffB3 + tid]);
+          sm.nc[tid] = norms[bsel].c[tid];
+          sm.ninv[tid] = norms[bsel].inv_h[tid];
+        }
+        __syncthreads();
+        if (tid == 0) sm.block = bsel;
+      }
+      // layer 1 of this row (zero for rows of other blocks), the A row
+      const bool mine = !done && myb == bsel;
+      const float x0 = (gi.x - sm.nc[0]) * sm.ninv[0], x1 = (gi.y - sm.nc[1]) * sm.ninv[1],
+                  x2 = (gi.z - sm.nc[2]) * sm.ninv[2];
+#pragma unroll
+      for (int kc = 0; kc < kMlpH / 8; ++kc) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = kc * 8 + e;
+          const float z = sm.b1[k] + sm.w1[3 * k] * x0 + sm.w1[3 * k + 1] * x1 + sm.w1[3 * k + 2] * x2;
+          h[e] = __float2half_rn(mine ? fmaxf(z, 0.f) : 0.f);
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off(tid, kc * 8)) =
+            *reinterpret_cast<const uint4*>(h);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the A rows, for the tensor cores
+      tc_fence_before();
+      __syncthreads();
+      // layer 2: one thread issues the four K = 16 steps and commits
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int s = 0; s < kMlpH / 16; ++s)
+          tc_mma(tmem, smem_desc(reinterpret_cast<const char*>(sm.a) + 256 * s),
+                 smem_desc(reinterpret_cast<const char*>(sm.b) + 256 * s), s > 0);
+        tc_commit(&sm.mbar);
+      }
+      const bool ok = mbar_wait(&sm.mbar, phase);
+      phase ^= 1u;
+      if (!ok) atomicOr(&sm.err, 1);
+      __syncthreads();
+      if (sm.err) break;
+      tc_fence_after();
+      // layer 3 from this thread's accumulator row (TMEM lane = row)
+      float out[3] = {sm.b3[0], sm.b3[1], sm.b3[2]};
+#pragma unroll
+      for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int col = c0 + e;
+          const float h2 = __half2float(__float2half_rn(fmaxf(v[e] + sm.b2[col], 0.f)));
+          out[0] += sm.w3[col] * h2;
+          out[1] += sm.w3[kMlpH + col] * h2;
+          out[2] += sm.w3[2 * kMlpH + col] * h2;
+        }
+      }
+      if (mine) {
+        p_out[item] = make_float4(out[0], out[1], out[2], 0.f);
+        done = true;
+      }
+      tc_fence_before();
+      __syncthreads();                  // the accumulator and the A rows are free again
+    }
+    if (sm.err) break;
+  }
+  __syncthreads();
+  if (sm.err) {
+    // an MMA that did not complete in time: wait once more (bounded) before
+    // its tensor memory is released
+    if (tid == 0) {
+      mbar_wait(&sm.mbar, phase ^ 1u);
+      atomicAdd(&st->async_timeouts, 1ull);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem);
+  }
+}
+
+}  // namespace
+
+void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
+                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s) {
+  int grid = num_sms * 8;         // 8 CTAs of 27 KB shared memory and 64 TMEM columns fill an SM
+  if (!n_ptr) {
+    const int tiles = (n_static + kTcRows - 1) / kTcRows;
+    grid = tiles < grid ? tiles : grid;
+    if (grid < 1) return;
+  }
+  k_mlp_infer_tc<<<grid, kTcRows, 0, s>>>(theta16, norms, g, gblk, n_ptr, n_static, p_out, st);
+}
+
+}  // namespace ivv

@@ -96,8 +96,10 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCa
 }
 
 // K2c: the deferred items' subdivision search.  With at most `warp_max`
-// deferred items (they fit a few waves of warps) each gets a whole warp
-// (split_item_warp, short latency); with more, one thread each
+// deferred items (they fit a few waves of warps) each gets a whole CTA of
+// kRootsThreads / 32 warps (split_item_warp with NW warps: every level of
+// the breadth-first search takes about one box's time, so an item's latency
+// -- which sets the kernel's time -- is shortest); with more, one thread each
 // (k2c_thread, throughput).  Both kernels are launched; the one whose case
 // does not hold returns at once.
 template <int P, typename R, bool MIXED, bool STATS>
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamer
                                                            typename Vec4T<R>::type* __restrict__ frag_tp,
                                                            unsigned* __restrict__ frag_meta,
                                                            int* __restrict__ frag_count, DevStats* __restrict__ st) {
-  __shared__ SplitSmem<R> s_split[kRootsThreads / 32];
-  SplitSmem<R>& sm = s_split[threadIdx.x >> 5];
+  __shared__ SplitSmem<R> sm;
+  __shared__ int s_k;
   pdl_wait();
   const int n = min(n_items[kSlowCounter - kItemCounter], cap);
   if (n > warp_max) return;
@@ -118,17 +120,19 @@ __global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamer
   int c_newton = 0;
   unsigned dropped = 0;
   for (;;) {
-    int k = 0;
-    if ((threadIdx.x & 31) == 0) k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
-    k = __shfl_sync(0xffffffffu, k, 0);
+    if (threadIdx.x == 0) s_k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();                                 // s_k read by all before the next item's hand-out
     if (k >= n) break;
     const int2 it = __ldg(items + __ldg(slow + k));
     const int xw = it.x % cam.w, yw = it.x / cam.w;
     const int px = cam.x0 + xw, py = cam.y0 + yw;
     R o[3], d[3];
     make_ray<R>(cam, px, py, o, d);
-    split_item_warp<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
-                                        frag_count, st, sm, c_newton, c_fp64, c_frag, dropped);
+    split_item_warp<P, R, MIXED, STATS, kRootsThreads / 32>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride,
+                                                            frag_tp, frag_meta, frag_count, st, sm, c_newton, c_fp64,
+                                                            c_frag, dropped);
   }
   if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
   roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
@@ -166,6 +170,18 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2c_thread(DevVolume V, DevC
   roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
 }
 
+// K2p: the deferred FP64 polish of the grazing hits listed by K2b / K2c
+// (mixed precision), one thread per hit.
+template <int P, bool STATS>
+__global__ void __launch_bounds__(128) k2p_polish(DevVolume V, DevCamera<double> cam64, float4* __restrict__ frag_tp,
+                                                  DevStats* __restrict__ st) {
+  pdl_wait();
+  const int n = min(*V.n_polish, V.polish_cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    polish_hit<P>(V, cam64, k, frag_tp);
+  if (STATS && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->fp64_solves, (unsigned long long)n);
+}
+
 template <int P, typename R, bool MIXED, bool STATS>
 void launch_k2b(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<double>& cam64, const SurfaceWs& w,
                 DevStats* st, int num_sms, cudaStream_t s) {
@@ -186,6 +202,10 @@ void launch_k2b(const DevVolume& V, const DevCamera<R>& cam, const DevCamera<dou
   launch_pdl(k2c_thread<P, R, MIXED, STATS>, dim3(num_sms * per_sm[2]), dim3(kRootsThreads), s, V, cam, cam64,
              (const int2*)w.items, (const int*)w.slow, w.n_items, w.cap, warp_max, (V4*)w.frag_tp, w.frag_meta,
              w.frag_count, st);
+  if constexpr (MIXED && sizeof(R) == 4) {
+    if (V.polish != nullptr)
+      launch_pdl(k2p_polish<P, STATS>, dim3(num_sms * 4), dim3(128), s, V, cam64, (float4*)w.frag_tp, st);
+  }
 }
 
 }  // namespace

@@ -63,14 +63,62 @@ __device__ __forceinline__ void project_faces(const DevVolume& V, const DevCamer
     gboxes[f / kGroup] = x0 <= x1 ? make_int4(x0, y0, x1, y1) : make_int4(1, 1, 0, 0);
 }
 
-// FP64 polish of a grazing hit (mixed precision), kept out of line.
+// Polish of a grazing hit with an FP64 residual (mixed precision), kept out
+// of line.
 template <int P>
 __device__ __noinline__ void refine_fp64(const DevVolume& V, int face, const DevCamera<double>& cam64, int px, int py,
                                          double& a, double& b, double& t) {
   const FaceMeta64 m = V.faces64[face];
   double o[3], d[3];
   make_ray<double>(cam64, px, py, o, d);
-  refine_hit_fp64<P, Dbl4>(V.face64 + (size_t)face * (P + 1) * (P + 1), m.org, o, d, a, b, t);
+  refine_hit_mixed<P>(V.face64 + (size_t)face * (P + 1) * (P + 1), V.face32 + (size_t)face * (P + 1) * (P + 1), m.org,
+                      o, d, a, b, t);
+}
+
+// Stores the fragment of root (a, b) of face patch fi (FP32 depth t and
+// block point pp) in the pixel's next slot.  Mixed precision: a hit within
+// |cos| < kPolishCos of grazing gets the FP64 polish -- listed for the polish
+// pass (k2p_polish) where the frame has a list with room, so that the FP64
+// work runs on full warps, else here.
+template <int P, typename R, bool MIXED, bool STATS>
+__device__ __forceinline__ void emit_fragment(const DevVolume& V, const DevCamera<double>& cam64, int fi, int face,
+                                              int block, int px, int py, int pix, size_t stride, R a, R b, R t,
+                                              R pp[3], bool front, R cosang,
+                                              typename Vec4T<R>::type* __restrict__ frag_tp,
+                                              unsigned* __restrict__ frag_meta, int* __restrict__ frag_count,
+                                              DevStats* __restrict__ st, unsigned long long& c_fp64,
+                                              unsigned long long& c_frag) {
+  typedef typename Vec4T<R>::type V4;
+  if (!(t > R(0))) return;
+  const int slot = atomicAdd(frag_count + pix, 1);
+  if (slot >= V.max_frags) {
+    atomicAdd(&st->abuf_overflow, 1ull);
+    return;
+  }
+  if constexpr (MIXED) {
+    if (cosang < R(kPolishCos)) {
+      int k = V.polish_cap;
+      if (V.polish != nullptr) k = atomicAdd(V.n_polish, 1);
+      if (k < V.polish_cap) {
+        V.polish[2 * (size_t)k] = make_float4(__int_as_float(pix), __int_as_float(slot), __int_as_float(fi), 0.f);
+        V.polish[2 * (size_t)k + 1] = make_float4(float(a), float(b), float(t), 0.f);
+      } else {
+        double a64 = a, b64 = b, t64 = t;
+        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+        t = R(t64);
+        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+        const FaceMeta64 m64 = V.faces64[fi];
+        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
+        if (STATS) ++c_fp64;
+      }
+    }
+  }
+  V4 rec;
+  rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
+  frag_tp[(size_t)slot * stride + pix] = rec;
+  frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
+  if (STATS) ++c_frag;
 }
 
 // K2a body: tile (tx, ty) of TW x TH = 32 pixels of the window of cam, one
@@ -188,31 +236,32 @@ __device__ __forceinline__ bool roots_item(const DevVolume& V, const DevCamera<d
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
-    if constexpr (MIXED) {
-      if (cosang < R(kPolishCos)) {
-        double a64 = a, b64 = b, t64 = t;
-        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        t = R(t64);
-        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-        const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
-        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
-        if (STATS) ++c_fp64;
-      }
-    }
-    if (!(t > R(0))) continue;
-    const int slot = atomicAdd(frag_count + pix, 1);
-    if (slot < V.max_frags) {
-      V4 rec;
-      rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
-      frag_tp[(size_t)slot * stride + pix] = rec;
-      frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
-      if (STATS) ++c_frag;
-    } else {
-      atomicAdd(&st->abuf_overflow, 1ull);
-    }
+    emit_fragment<P, R, MIXED, STATS>(V, cam64, fi, face, block, px, py, pix, stride, a, b, t, pp, front, cosang,
+                                      frag_tp, frag_meta, frag_count, st, c_fp64, c_frag);
   }
   return true;
+}
+
+// K2p body: the FP64 polish of listed grazing hit k (mixed precision): Newton
+// on the FP64 face patch from the FP32 root, then the fragment's depth and
+// block point are rewritten in its slot.
+template <int P>
+__device__ __forceinline__ void polish_hit(const DevVolume& V, const DevCamera<double>& cam64, int k,
+                                           float4* __restrict__ frag_tp) {
+  const float4 e0 = V.polish[2 * (size_t)k], e1 = V.polish[2 * (size_t)k + 1];
+  const int pix = __float_as_int(e0.x), slot = __float_as_int(e0.y), fi = __float_as_int(e0.z);
+  const size_t stride = (size_t)cam64.w * cam64.h;
+  const int px = cam64.x0 + pix % cam64.w, py = cam64.y0 + pix / cam64.w;
+  double a64 = e1.x, b64 = e1.y, t64 = e1.z;
+  refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
+  const int face = V.faces[fi].face;
+  const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
+  const FaceMeta64 m64 = V.faces64[fi];
+  float pp[3];
+  pp[nd] = (face & 1) ? 1.f : 0.f;
+  pp[ad] = float(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
+  pp[bd] = float(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
+  frag_tp[(size_t)slot * stride + pix] = make_float4(float(t64), pp[0], pp[1], pp[2]);
 }
 
 // ---- K2c: subdivision search of one item by a whole warp, level by level.
@@ -263,17 +312,25 @@ __device__ __forceinline__ bool gather_root(const SplitBox<R>& nd, R a, R b, Spl
   return true;
 }
 
-// All lanes of the warp call it; returns the merged roots in sm.ra/rb[0..n)
-// (n <= kMaxPatchRoots, the same on every lane).
-template <int P, typename R>
+// NW = 1: all lanes of the warp call it; NW > 1: all NW * 32 threads of the
+// CTA (one item per CTA: each level's boxes spread over more lanes, so a
+// level takes about one box's time).  Returns the merged roots in
+// sm.ra/rb[0..n) (n <= kMaxPatchRoots, the same on every thread).
+template <int NW>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NW == 1) group_sync<NW>(); else __syncthreads();
+}
+
+template <int P, typename R, int NW = 1>
 __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, SplitSmem<R>& sm, int& iters,
                                                 unsigned& dropped) {
   constexpr int N = P + 1;
-  const int lane = threadIdx.x & 31;
+  constexpr int NL = 32 * NW;                       // lanes of the group
+  const int lane = NW == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   // the uncertified patch is split into a kSplitGrid x kSplitGrid grid of
   // boxes at once (one level of the warp search instead of 2 log2 kSplitGrid)
   constexpr int G = kSplitGrid;
-  for (int k = lane; k < G * G; k += 32) {
+  for (int k = lane; k < G * G; k += NL) {
     const int ia = k % G, ib = k / G;
     const R w = R(1) / R(G);
     sm.box[0][k] = SplitBox<R>{R(ia) * w, R(ia + 1) * w, R(ib) * w, R(ib + 1) * w, G == 1 ? 0 : 2 * (31 - __clz(G))};
@@ -283,14 +340,14 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     sm.n[1] = 0;
     sm.nr = 0;
   }
-  __syncwarp();
+  group_sync<NW>();
   int cur = 0;
 #pragma unroll 1
   for (int level = 0; level <= kSplitDepth; ++level) {
     const int n = min(sm.n[cur], kBfsCap);
     if (n == 0) break;
 #pragma unroll 1
-    for (int k = lane; k < n; k += 32) {
+    for (int k = lane; k < n; k += NL) {
       const SplitBox<R> nd = sm.box[cur][k];
       Patch2<P, R> q;
       sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
@@ -335,9 +392,9 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
         ++dropped;
       }
     }
-    __syncwarp();
+    group_sync<NW>();
     if (lane == 0) sm.n[cur] = 0;
-    __syncwarp();
+    group_sync<NW>();
     cur ^= 1;
   }
   // merge duplicates (lane 0), keep at most kMaxPatchRoots
@@ -356,13 +413,14 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     }
     sm.nr = kept;
   }
-  __syncwarp();
+  group_sync<NW>();
   return sm.nr;
 }
 
-// K2c body for one deferred item (all lanes of the warp, same item): the
-// warp search, then one lane per root writes its fragment.
-template <int P, typename R, bool MIXED, bool STATS>
+// K2c body for one deferred item (all lanes of the warp, or of the CTA with
+// NW warps, on the same item): the subdivision search, then one lane per
+// root writes its fragment.
+template <int P, typename R, bool MIXED, bool STATS, int NW = 1>
 __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
                                                 int px, int py, const R o[3], const R d[3], float diag, size_t stride,
                                                 typename Vec4T<R>::type* __restrict__ frag_tp,
@@ -390,40 +448,17 @@ __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCam
   }
   Patch2<P, R> pq;
   project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
-  const int nr = split_roots_warp<P, R>(pq, pad, sm, c_newton, dropped);
-  const int lane = threadIdx.x & 31;
+  const int nr = split_roots_warp<P, R, NW>(pq, pad, sm, c_newton, dropped);
+  const int lane = NW == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   if (lane < nr) {
     const R a = sm.ra[lane], b = sm.rb[lane];   // within the acceptance tolerance of the patch
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
-    const int face = m.face, block = m.block;
-    if constexpr (MIXED) {
-      if (cosang < R(kPolishCos)) {
-        double a64 = a, b64 = b, t64 = t;
-        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        t = R(t64);
-        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-        const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
-        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
-        if (STATS) ++c_fp64;
-      }
-    }
-    if (t > R(0)) {
-      const int slot = atomicAdd(frag_count + pix, 1);
-      if (slot < V.max_frags) {
-        V4 rec;
-        rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
-        frag_tp[(size_t)slot * stride + pix] = rec;
-        frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
-        if (STATS) ++c_frag;
-      } else {
-        atomicAdd(&st->abuf_overflow, 1ull);
-      }
-    }
+    emit_fragment<P, R, MIXED, STATS>(V, cam64, fi, m.face, m.block, px, py, pix, stride, a, b, t, pp, front, cosang,
+                                      frag_tp, frag_meta, frag_count, st, c_fp64, c_frag);
   }
-  __syncwarp();
+  group_sync<NW>();
 }
 
 // K2c body, one thread per deferred item (many deferred items): the
@@ -463,29 +498,8 @@ __device__ __forceinline__ void split_item_thread(const DevVolume& V, const DevC
     R t, pp[3], cosang;
     bool front;
     make_fragment<P, R, V4>(cp, org, m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
-    if constexpr (MIXED) {
-      if (cosang < R(kPolishCos)) {
-        double a64 = a, b64 = b, t64 = t;
-        refine_fp64<P>(V, fi, cam64, px, py, a64, b64, t64);
-        t = R(t64);
-        const int nd = face >> 1, ad = (nd + 1) % 3, bd = (nd + 2) % 3;
-        const FaceMeta64 m64 = V.faces64[fi];
-        pp[ad] = R(fmin(fmax(m64.a0 + a64 * (m64.a1 - m64.a0), 0.0), 1.0));
-        pp[bd] = R(fmin(fmax(m64.b0 + b64 * (m64.b1 - m64.b0), 0.0), 1.0));
-        if (STATS) ++c_fp64;
-      }
-    }
-    if (!(t > R(0))) continue;
-    const int slot = atomicAdd(frag_count + pix, 1);
-    if (slot < V.max_frags) {
-      V4 rec;
-      rec.x = t; rec.y = pp[0]; rec.z = pp[1]; rec.w = pp[2];
-      frag_tp[(size_t)slot * stride + pix] = rec;
-      frag_meta[(size_t)slot * stride + pix] = ((unsigned)block << 4) | ((unsigned)face << 1) | (front ? 1u : 0u);
-      if (STATS) ++c_frag;
-    } else {
-      atomicAdd(&st->abuf_overflow, 1ull);
-    }
+    emit_fragment<P, R, MIXED, STATS>(V, cam64, fi, face, block, px, py, pix, stride, a, b, t, pp, front, cosang,
+                                      frag_tp, frag_meta, frag_count, st, c_fp64, c_frag);
   }
 }
 

@@ -41,7 +41,9 @@ void launch_mlp_reduce(const float* partial, const float* partial_loss, int npar
 void launch_mlp_adam(float* theta, float* m, float* v, const float* grad, float lr, int step, __half* theta16,
                      cudaStream_t s);
 void launch_mlp_to_half(const float* theta, __half* theta16, int n, cudaStream_t s);
+// Tensor-core inference (k_mlp_tc.cu): p_out[i] = network of block gblk[i]
+// at world point g[i], for i < *n_ptr (or n_static when n_ptr is null).
 void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
-                      int n_static, float4* p_out, int num_sms, cudaStream_t s);
+                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s);
 
 }  // namespace ivv

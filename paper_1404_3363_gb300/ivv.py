@@ -90,7 +90,7 @@ class Stats(C.Structure):
         "rays", "pairs", "fragments", "samples", "rk_steps", "rk_rejects", "rhs_evals", "isect_newton",
         "isect_tests", "fp64_solves", "abuf_overflow", "pair_overflow", "unmatched", "step_cap",
         "rf_newton_iters", "rf_unconverged", "isect_items", "isect_split", "rho_evals", "entry_shrinks",
-        "entry_newton")] + \
+        "entry_newton", "async_timeouts")] + \
         [("max_delta_p", C.c_double)]
 
     def as_dict(self):
