@@ -96,10 +96,8 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2b_roots(DevVolume V, DevCa
 }
 
 // K2c: the deferred items' subdivision search.  With at most `warp_max`
-// deferred items (they fit a few waves of warps) each gets a whole CTA of
-// kRootsThreads / 32 warps (split_item_warp with NW warps: every level of
-// the breadth-first search takes about one box's time, so an item's latency
-// -- which sets the kernel's time -- is shortest); with more, one thread each
+// deferred items (they fit a few waves of warps) each gets a whole warp
+// (split_item_warp, short latency); with more, one thread each
 // (k2c_thread, throughput).  Both kernels are launched; the one whose case
 // does not hold returns at once.
 template <int P, typename R, bool MIXED, bool STATS>
@@ -110,8 +108,8 @@ __global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamer
                                                            typename Vec4T<R>::type* __restrict__ frag_tp,
                                                            unsigned* __restrict__ frag_meta,
                                                            int* __restrict__ frag_count, DevStats* __restrict__ st) {
-  __shared__ SplitSmem<R> sm;
-  __shared__ int s_k;
+  __shared__ SplitSmem<R> s_split[kRootsThreads / 32];
+  SplitSmem<R>& sm = s_split[threadIdx.x >> 5];
   pdl_wait();
   const int n = min(n_items[kSlowCounter - kItemCounter], cap);
   if (n > warp_max) return;
@@ -120,19 +118,17 @@ __global__ void __launch_bounds__(kRootsThreads) k2c_split(DevVolume V, DevCamer
   int c_newton = 0;
   unsigned dropped = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
-    __syncthreads();
-    const int k = s_k;
-    __syncthreads();                                 // s_k read by all before the next item's hand-out
+    int k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(n_items + (kSlowHead - kItemCounter), 1);
+    k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= n) break;
     const int2 it = __ldg(items + __ldg(slow + k));
     const int xw = it.x % cam.w, yw = it.x / cam.w;
     const int px = cam.x0 + xw, py = cam.y0 + yw;
     R o[3], d[3];
     make_ray<R>(cam, px, py, o, d);
-    split_item_warp<P, R, MIXED, STATS, kRootsThreads / 32>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride,
-                                                            frag_tp, frag_meta, frag_count, st, sm, c_newton, c_fp64,
-                                                            c_frag, dropped);
+    split_item_warp<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
+                                        frag_count, st, sm, c_newton, c_fp64, c_frag, dropped);
   }
   if (dropped) atomicAdd(&st->abuf_overflow, (unsigned long long)dropped);
   roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);

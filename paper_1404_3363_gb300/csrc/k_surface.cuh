@@ -312,25 +312,17 @@ __device__ __forceinline__ bool gather_root(const SplitBox<R>& nd, R a, R b, Spl
   return true;
 }
 
-// NW = 1: all lanes of the warp call it; NW > 1: all NW * 32 threads of the
-// CTA (one item per CTA: each level's boxes spread over more lanes, so a
-// level takes about one box's time).  Returns the merged roots in
-// sm.ra/rb[0..n) (n <= kMaxPatchRoots, the same on every thread).
-template <int NW>
-__device__ __forceinline__ void group_sync() {
-  if constexpr (NW == 1) group_sync<NW>(); else __syncthreads();
-}
-
-template <int P, typename R, int NW = 1>
+// All lanes of the warp call it; returns the merged roots in sm.ra/rb[0..n)
+// (n <= kMaxPatchRoots, the same on every lane).
+template <int P, typename R>
 __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, SplitSmem<R>& sm, int& iters,
                                                 unsigned& dropped) {
   constexpr int N = P + 1;
-  constexpr int NL = 32 * NW;                       // lanes of the group
-  const int lane = NW == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  const int lane = threadIdx.x & 31;
   // the uncertified patch is split into a kSplitGrid x kSplitGrid grid of
   // boxes at once (one level of the warp search instead of 2 log2 kSplitGrid)
   constexpr int G = kSplitGrid;
-  for (int k = lane; k < G * G; k += NL) {
+  for (int k = lane; k < G * G; k += 32) {
     const int ia = k % G, ib = k / G;
     const R w = R(1) / R(G);
     sm.box[0][k] = SplitBox<R>{R(ia) * w, R(ia + 1) * w, R(ib) * w, R(ib + 1) * w, G == 1 ? 0 : 2 * (31 - __clz(G))};
@@ -340,14 +332,14 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     sm.n[1] = 0;
     sm.nr = 0;
   }
-  group_sync<NW>();
+  __syncwarp();
   int cur = 0;
 #pragma unroll 1
   for (int level = 0; level <= kSplitDepth; ++level) {
     const int n = min(sm.n[cur], kBfsCap);
     if (n == 0) break;
 #pragma unroll 1
-    for (int k = lane; k < n; k += NL) {
+    for (int k = lane; k < n; k += 32) {
       const SplitBox<R> nd = sm.box[cur][k];
       Patch2<P, R> q;
       sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
@@ -392,9 +384,9 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
         ++dropped;
       }
     }
-    group_sync<NW>();
+    __syncwarp();
     if (lane == 0) sm.n[cur] = 0;
-    group_sync<NW>();
+    __syncwarp();
     cur ^= 1;
   }
   // merge duplicates (lane 0), keep at most kMaxPatchRoots
@@ -413,14 +405,13 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     }
     sm.nr = kept;
   }
-  group_sync<NW>();
+  __syncwarp();
   return sm.nr;
 }
 
-// K2c body for one deferred item (all lanes of the warp, or of the CTA with
-// NW warps, on the same item): the subdivision search, then one lane per
-// root writes its fragment.
-template <int P, typename R, bool MIXED, bool STATS, int NW = 1>
+// K2c body for one deferred item (all lanes of the warp, same item): the
+// warp search, then one lane per root writes its fragment.
+template <int P, typename R, bool MIXED, bool STATS>
 __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCamera<double>& cam64, int pix, int fi,
                                                 int px, int py, const R o[3], const R d[3], float diag, size_t stride,
                                                 typename Vec4T<R>::type* __restrict__ frag_tp,
@@ -448,8 +439,8 @@ __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCam
   }
   Patch2<P, R> pq;
   project_patch<P, R, V4>(cp, org, o, e1, e2, pq);
-  const int nr = split_roots_warp<P, R, NW>(pq, pad, sm, c_newton, dropped);
-  const int lane = NW == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  const int nr = split_roots_warp<P, R>(pq, pad, sm, c_newton, dropped);
+  const int lane = threadIdx.x & 31;
   if (lane < nr) {
     const R a = sm.ra[lane], b = sm.rb[lane];   // within the acceptance tolerance of the patch
     R t, pp[3], cosang;
@@ -458,7 +449,7 @@ __device__ __forceinline__ void split_item_warp(const DevVolume& V, const DevCam
     emit_fragment<P, R, MIXED, STATS>(V, cam64, fi, m.face, m.block, px, py, pix, stride, a, b, t, pp, front, cosang,
                                       frag_tp, frag_meta, frag_count, st, c_fp64, c_frag);
   }
-  group_sync<NW>();
+  __syncwarp();
 }
 
 // K2c body, one thread per deferred item (many deferred items): the
