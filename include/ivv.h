@@ -133,7 +133,7 @@ typedef struct {
  *              full_width x full_height image (0 = the window is the image)
  * method       IVV_METHOD_* [ODE]; RF runs in FP32 or MIXED precision, reads
  *              back the sample count (one stream synchronisation) and keeps
- *              its sample buffers (40 bytes per sample) in library memory
+ *              its sample buffers (44 bytes per sample) in library memory
  * rf_tol       RF stopping rule: ||phi(p) - g|| <= rf_tol times the half width
  *              of the pixel at the sample's depth (the paper stops at the
  *              pixel frustum, rf_tol = 1) [0.05]

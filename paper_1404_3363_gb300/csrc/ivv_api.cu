@@ -494,20 +494,28 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     int total = 0;
     IVV_CUDA(cudaMemcpyAsync(&total, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     IVV_CUDA(cudaStreamSynchronize(s));
-    const size_t per = 2 * sizeof(float4) + sizeof(int) + sizeof(float);
+    // per sample: world point, guess, block, scalar, and the block-sorted
+    // order of the learned guess's inference; then the sort's histogram
+    const size_t per = 2 * sizeof(float4) + 3 * sizeof(int);
     const size_t cap_n = (size_t)std::max(total, 1);
-    st = ensure_own(&v->rf_buf, &v->rf_bytes, cap_n * per + 1024, s);
+    const int nb = v->hv.n_blocks;
+    st = ensure_own(&v->rf_buf, &v->rf_bytes, cap_n * per + sizeof(int) * (nb + 1) + 1024, s);
     if (st != IVV_OK) return st;
     char* rb = (char*)v->rf_buf;
     float4* sg = (float4*)rb;
     float4* sp = sg + cap_n;
     int* sblk = (int*)(sp + cap_n);
     float* srho = (float*)(sblk + cap_n);
+    int* sperm = (int*)(srho + cap_n);
+    int* shist = sperm + cap_n;
     ivv::DevCamera<float> c32 = dev_camera<float>(F);
     ivv::launch_rf_expand(c32, pin, pout, pblk, pcnt, act, counters, off, (int)npix, (float)p.ds, tail_eps,
                           p.use_mlp_guess, total, sg, sblk, sp, v->num_sms, s);
-    if (p.use_mlp_guess == IVV_GUESS_MLP)
-      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s);
+    if (p.use_mlp_guess == IVV_GUESS_MLP) {
+      if (nb > 1) ivv::launch_block_sort(sblk, counters + 2, nb, shist, sperm, v->num_sms, s);
+      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s,
+                            nb > 1 ? sperm : nullptr);
+    }
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,
                           stats, mixed, v->num_sms, s);

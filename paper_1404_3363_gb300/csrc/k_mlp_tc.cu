@@ -43,7 +43,9 @@ __device__ __forceinline__ int core_off(int row, int k) {
 struct __align__(1024) TcSmem {
   __half a[kTcRows * kMlpH];       // layer-2 A operand (16 KB)
   __half b[kMlpH * kMlpH];         // W2 of the loaded block (8 KB), B operand
-  float w1[kMlpH * 3], b1[kMlpH], b2[kMlpH], w3[3 * kMlpH], b3[4];
+  float4 w1b[kMlpH];               // layer 1: (W1[k][0..2], b1[k]) per hidden unit k
+  float4 w3b[kMlpH];               // layer 3: (W3[0..2][c], b2[c]) per hidden unit c
+  float b3[4];
   float nc[3], ninv[3];            // input normalisation of the loaded block
   unsigned long long mbar;
   unsigned tmem;
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
                                                          const MlpNorm* __restrict__ norms,
                                                          const float4* __restrict__ g, const int* __restrict__ gblk,
                                                          const int* __restrict__ n_ptr, int n_static,
-                                                         float4* __restrict__ p_out, DevStats* __restrict__ st) {
+                                                         const int* __restrict__ perm, float4* __restrict__ p_out,
+                                                         DevStats* __restrict__ st) {
   __shared__ TcSmem sm;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) tmem_alloc(&sm.tmem);
@@ -154,7 +157,8 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
   const int per_cta = (tiles + (int)gridDim.x - 1) / (int)gridDim.x;
   const int tile0 = blockIdx.x * per_cta, tile1 = min(tiles, tile0 + per_cta);
   for (int tile = tile0; tile < tile1; ++tile) {
-    const int item = tile * kTcRows + tid;
+    int item = tile * kTcRows + tid;                // the list entry of this row
+    if (perm != nullptr && item < n) item = __ldg(perm + item);
     const int myb = item < n ? __ldg(gblk + item) : -1;
     float4 gi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (item < n) gi = __ldg(g + item);
@@ -174,13 +178,11 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
           const uint4 v = *reinterpret_cast<const uint4*>(th + kOffW2 + nrow * kMlpH + kc * 8);
           *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b) + core_off(nrow, kc * 8)) = v;
         }
-        for (int i = tid; i < kMlpH * 3; i += kTcRows) {
-          sm.w1[i] = __half2float(th[kOffW1 + i]);
-          sm.w3[i] = __half2float(th[kOffW3 + i]);
-        }
         if (tid < kMlpH) {
-          sm.b1[tid] = __half2float(th[kOffB1 + tid]);
-          sm.b2[tid] = __half2float(th[kOffB2 + tid]);
+          sm.w1b[tid] = make_float4(__half2float(th[kOffW1 + 3 * tid]), __half2float(th[kOffW1 + 3 * tid + 1]),
+                                    __half2float(th[kOffW1 + 3 * tid + 2]), __half2float(th[kOffB1 + tid]));
+          sm.w3b[tid] = make_float4(__half2float(th[kOffW3 + tid]), __half2float(th[kOffW3 + kMlpH + tid]),
+                                    __half2float(th[kOffW3 + 2 * kMlpH + tid]), __half2float(th[kOffB2 + tid]));
         }
         if (tid < 3) {
           sm.b3[tid] = __half2float(th[kOffB3 + tid]);
@@ -199,8 +201,8 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
         __align__(16) __half h[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int k = kc * 8 + e;
-          const float z = sm.b1[k] + sm.w1[3 * k] * x0 + sm.w1[3 * k + 1] * x1 + sm.w1[3 * k + 2] * x2;
+          const float4 w = sm.w1b[kc * 8 + e];
+          const float z = w.w + w.x * x0 + w.y * x1 + w.z * x2;
           h[e] = __float2half_rn(mine ? fmaxf(z, 0.f) : 0.f);
         }
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off(tid, kc * 8)) =
@@ -232,11 +234,11 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
         tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int col = c0 + e;
-          const float h2 = __half2float(__float2half_rn(fmaxf(v[e] + sm.b2[col], 0.f)));
-          out[0] += sm.w3[col] * h2;
-          out[1] += sm.w3[kMlpH + col] * h2;
-          out[2] += sm.w3[2 * kMlpH + col] * h2;
+          const float4 w = sm.w3b[c0 + e];
+          const float h2 = __half2float(__float2half_rn(fmaxf(v[e] + w.w, 0.f)));
+          out[0] += w.x * h2;
+          out[1] += w.y * h2;
+          out[2] += w.z * h2;
         }
       }
       if (mine) {
@@ -264,17 +266,83 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
   }
 }
 
+
+// Counting sort of list entries by block (the guess list of the RF method):
+// perm lists the entries block after block, so the inference's tiles hold
+// one block each and run one pass.  Atomics are aggregated per warp over the
+// lanes of one block.  hist: [n_blocks + 1] ints (zeroed by the caller).
+__global__ void k_sort_hist(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int* __restrict__ hist) {
+  const int n = *n_ptr;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    const int b = i < n ? __ldg(gblk + i) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(hist + b, __popc(peers));
+  }
+}
+
+__global__ void k_sort_scan(int* __restrict__ hist, int n_blocks) {
+  __shared__ int s_sum[1024];
+  // exclusive scan of hist[0..n_blocks) in place by one CTA: per-thread runs,
+  // then a scan of the run totals
+  const int per = (n_blocks + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(n_blocks, b0 + per);
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += hist[b];
+  s_sum[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (unsigned t = 0; t < blockDim.x; ++t) {
+      const int v = s_sum[t];
+      s_sum[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  int acc = s_sum[threadIdx.x];
+  for (int b = b0; b < b1; ++b) {
+    const int v = hist[b];
+    hist[b] = acc;
+    acc += v;
+  }
+}
+
+__global__ void k_sort_scatter(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int* __restrict__ cursor,
+                               int* __restrict__ perm) {
+  const int n = *n_ptr;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    const int b = i < n ? __ldg(gblk + i) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    int at = 0;
+    if (b >= 0 && lane == leader) at = atomicAdd(cursor + b, __popc(peers));
+    at = __shfl_sync(0xffffffffu, at, leader);
+    if (b >= 0) perm[at + __popc(peers & ((1u << lane) - 1u))] = i;
+  }
+}
+
 }  // namespace
 
+void launch_block_sort(const int* gblk, const int* n_ptr, int n_blocks, int* hist, int* perm, int num_sms,
+                       cudaStream_t s) {
+  cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)(n_blocks + 1), s);
+  k_sort_hist<<<num_sms * 8, 256, 0, s>>>(gblk, n_ptr, hist);
+  k_sort_scan<<<1, 1024, 0, s>>>(hist, n_blocks);
+  k_sort_scatter<<<num_sms * 8, 256, 0, s>>>(gblk, n_ptr, hist, perm);
+}
+
 void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
-                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s) {
+                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s, const int* perm) {
   int grid = num_sms * 8;         // 8 CTAs of 27 KB shared memory and 64 TMEM columns fill an SM
   if (!n_ptr) {
     const int tiles = (n_static + kTcRows - 1) / kTcRows;
     grid = tiles < grid ? tiles : grid;
     if (grid < 1) return;
   }
-  k_mlp_infer_tc<<<grid, kTcRows, 0, s>>>(theta16, norms, g, gblk, n_ptr, n_static, p_out, st);
+  k_mlp_infer_tc<<<grid, kTcRows, 0, s>>>(theta16, norms, g, gblk, n_ptr, n_static, perm, p_out, st);
 }
 
 }  // namespace ivv

@@ -43,7 +43,14 @@ void launch_mlp_adam(float* theta, float* m, float* v, const float* grad, float 
 void launch_mlp_to_half(const float* theta, __half* theta16, int n, cudaStream_t s);
 // Tensor-core inference (k_mlp_tc.cu): p_out[i] = network of block gblk[i]
 // at world point g[i], for i < *n_ptr (or n_static when n_ptr is null).
+// perm (optional): the order in which the entries are taken (block after
+// block, from launch_block_sort), so that a tile of 128 holds one block.
 void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,
-                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s);
+                      int n_static, float4* p_out, DevStats* st, int num_sms, cudaStream_t s,
+                      const int* perm = nullptr);
+// Counting sort of the n = *n_ptr entries by block into perm [n]; hist:
+// [n_blocks + 1] ints of scratch.
+void launch_block_sort(const int* gblk, const int* n_ptr, int n_blocks, int* hist, int* perm, int num_sms,
+                       cudaStream_t s);
 
 }  // namespace ivv
