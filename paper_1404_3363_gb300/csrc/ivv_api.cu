@@ -512,9 +512,13 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     ivv::launch_rf_expand(c32, pin, pout, pblk, pcnt, act, counters, off, (int)npix, (float)p.ds, tail_eps,
                           p.use_mlp_guess, total, sg, sblk, sp, v->num_sms, s);
     if (p.use_mlp_guess == IVV_GUESS_MLP) {
-      if (nb > 1) ivv::launch_block_sort(sblk, counters + 2, nb, shist, sperm, v->num_sms, s);
+      // with many blocks a tile of consecutive samples spans many of them
+      // (one inference pass each): sort by block first; with few, the
+      // scattered reads of the sorted order cost more than the passes
+      const bool sort = nb >= 8;
+      if (sort) ivv::launch_block_sort(sblk, counters + 2, nb, shist, sperm, v->num_sms, s);
       ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s,
-                            nb > 1 ? sperm : nullptr);
+                            sort ? sperm : nullptr);
     }
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,

@@ -1,20 +1,24 @@
 // K6 inference of the learned initial guess on the 5th-generation tensor
 // cores: per block a 3-64-64-3 perceptron (ReLU), FP16 weights, FP32
 // accumulation.  One CTA of 128 threads takes a contiguous run of tiles of
-// 128 listed points (one thread per point = one row of the MMA):
-//   layer 1 (3 -> 64) on the FP32 pipe, its ReLU output rounded to FP16 and
-//     stored as the A operand in shared memory;
-//   layer 2 (64 -> 64) as one tcgen05.mma M = 128, N = 64, K = 64 (four
-//     K = 16 steps) issued by one thread, A and B (W2, K-major) read from
-//     shared memory through matrix descriptors, the FP32 accumulator in
-//     tensor memory (64 columns, allocated once per CTA);
-//   layer 3 (64 -> 3) on the FP32 pipe from the accumulator row (tcgen05.ld),
-//     its input rounded to FP16 as the weights' precision.
-// A tile whose points lie in several blocks runs one pass per block, each
-// with that block's weights (staged in shared memory when the block
-// changes); rows of other blocks ride along and are not written.  The MMA's
-// completion is awaited on an mbarrier with a bounded spin: a wait that gives
-// up counts in DevStats::async_timeouts and the CTA writes no further points.
+// 128 listed points (one thread per point = one row of the MMAs); each layer
+// is one tcgen05.mma chain (M = 128, issued by one thread, A and B read from
+// shared memory through matrix descriptors, the FP32 accumulator in tensor
+// memory, 64 columns allocated once per CTA):
+//   layer 1 (3 -> 64): A = (x_hi, x_lo, 1) per row, each input split into
+//     two FP16 parts so that the products keep FP32 accuracy, against
+//     B = (W1, W1, b1): K = 16, N = 64;
+//   layer 2 (64 -> 64): A = the ReLU of layer 1 rounded to FP16, B = W2:
+//     K = 64 (four K = 16 steps), N = 64;
+//   layer 3 (64 -> 3): A = the ReLU of layer 2 (+ b2) rounded to FP16,
+//     B = W3 padded to N = 16: K = 64.
+// Between layers every thread reads its accumulator row (tcgen05.ld), applies
+// bias and ReLU, and writes the next A row.  A tile whose points lie in
+// several blocks runs one pass per block with that block's weights (staged
+// in shared memory when the block changes); rows of other blocks ride along
+// and are not written.  Each MMA chain's completion is awaited on an mbarrier
+// with a bounded spin: a wait that gives up counts in
+// DevStats::async_timeouts and the CTA writes no further points.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -34,18 +38,22 @@ constexpr long long kWaitSpins = 1ll << 22;
 // Shared-memory operands in the K-major layout without swizzling: 8 x 8
 // "core matrices" (8 rows of 16 bytes, 128 contiguous bytes); along K the
 // core matrices of an 8-row group follow each other (leading byte offset
-// 128), and the 8-row groups are 8 core matrices apart (stride byte offset
-// 1024, K = 64 halves).
+// 128), and the 8-row groups are K / 8 core matrices apart (stride byte
+// offset 16 K bytes).
+template <int K>
 __device__ __forceinline__ int core_off(int row, int k) {
-  return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+  return (row >> 3) * (16 * K) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
+constexpr int kK1 = 16;                    // layer 1's K: (x_hi, x_lo, 1) padded
+constexpr int kN3 = 16;                    // layer 3's N: 3 outputs padded
 
 struct __align__(1024) TcSmem {
-  __half a[kTcRows * kMlpH];       // layer-2 A operand (16 KB)
-  __half b[kMlpH * kMlpH];         // W2 of the loaded block (8 KB), B operand
-  float4 w1b[kMlpH];               // layer 1: (W1[k][0..2], b1[k]) per hidden unit k
-  float4 w3b[kMlpH];               // layer 3: (W3[0..2][c], b2[c]) per hidden unit c
-  float b3[4];
+  __half a[kTcRows * kMlpH];       // A operand of the current layer (16 KB; layer 1 uses 4 KB)
+  __half b2[kMlpH * kMlpH];        // W2 of the loaded block (8 KB)
+  __half b1[kMlpH * kK1];          // (W1, W1, b1) (2 KB)
+  __half b3[kN3 * kMlpH];          // W3, rows 3..15 zero (2 KB)
+  float bias2[kMlpH];
+  float bias3[4];
   float nc[3], ninv[3];            // input normalisation of the loaded block
   unsigned long long mbar;
   unsigned tmem;
@@ -54,20 +62,22 @@ struct __align__(1024) TcSmem {
   int err;
 };
 
-// Matrix descriptor of a shared-memory operand starting at p (no swizzle).
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+// Matrix descriptor of a shared-memory operand starting at p (no swizzle)
+// whose 8-row groups are sbo bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t sbo) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
   uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);     // start address
   d |= (uint64_t)(128u >> 4) << 16;                // leading byte offset: next core matrix along K
-  d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: next 8-row group
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;     // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;                          // descriptor version of tcgen05
   return d;                                        // base offset 0, layout: no swizzle
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both
-// K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kMlpH >> 3) << 17) |
-                            ((uint32_t)(kTcRows >> 4) << 24);
+// K-major, M = 128 and the given N.
+constexpr uint32_t idesc_f16(int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -85,11 +95,11 @@ __device__ __forceinline__ void tmem_dealloc(unsigned taddr) {    // the allocat
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_mma(unsigned d, uint64_t a, uint64_t b, int accumulate) {
+__device__ __forceinline__ void tc_mma(unsigned d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -130,6 +140,48 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned par
   return false;
 }
 
+// One MMA round of the CTA: every thread has written its A row (generic
+// proxy); thread 0 issues `issue` and commits; all wait (bounded) for the
+// chain.  Returns false (the same on every thread) if a wait gave up.
+template <class Issue>
+__device__ __forceinline__ bool mma_round(TcSmem& sm, unsigned& phase, Issue issue) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the A rows, for the tensor cores
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue();
+    tc_commit(&sm.mbar);
+  }
+  const bool ok = mbar_wait(&sm.mbar, phase);
+  phase ^= 1u;
+  if (!ok) atomicOr(&sm.err, 1);
+  __syncthreads();
+  if (sm.err) return false;
+  tc_fence_after();
+  return true;
+}
+
+// Accumulator row -> bias, ReLU, FP16 -> the next layer's A row (K = 64).
+__device__ __forceinline__ void relu_row_to_a(TcSmem& sm, unsigned taddr_row, const float* bias, int row) {
+#pragma unroll
+  for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    float v[16];
+    tmem_ld16(taddr_row + (unsigned)c0, v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      __align__(16) __half q[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float z = v[8 * h + e] + (bias ? bias[c0 + 8 * h + e] : 0.f);
+        q[e] = __float2half_rn(fmaxf(z, 0.f));
+      }
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off<kMlpH>(row, c0 + 8 * h)) =
+          *reinterpret_cast<const uint4*>(q);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __restrict__ theta16_all,
                                                          const MlpNorm* __restrict__ norms,
                                                          const float4* __restrict__ g, const int* __restrict__ gblk,
@@ -149,6 +201,7 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = sm.tmem;
+  const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);   // this thread's accumulator row (TMEM lane)
   const int n = n_ptr ? *n_ptr : n_static;
   unsigned phase = 0;
   // each CTA takes a contiguous run of tiles: neighbouring list entries
@@ -176,73 +229,88 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
         for (int c = tid; c < kMlpH * (kMlpH / 8); c += kTcRows) {
           const int nrow = c / (kMlpH / 8), kc = c % (kMlpH / 8);
           const uint4 v = *reinterpret_cast<const uint4*>(th + kOffW2 + nrow * kMlpH + kc * 8);
-          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b) + core_off(nrow, kc * 8)) = v;
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b2) + core_off<kMlpH>(nrow, kc * 8)) = v;
         }
         if (tid < kMlpH) {
-          sm.w1b[tid] = make_float4(__half2float(th[kOffW1 + 3 * tid]), __half2float(th[kOffW1 + 3 * tid + 1]),
-                                    __half2float(th[kOffW1 + 3 * tid + 2]), __half2float(th[kOffB1 + tid]));
-          sm.w3b[tid] = make_float4(__half2float(th[kOffW3 + tid]), __half2float(th[kOffW3 + kMlpH + tid]),
-                                    __half2float(th[kOffW3 + 2 * kMlpH + tid]), __half2float(th[kOffB2 + tid]));
+          // (W1, W1, b1) of hidden unit tid: pairs with the row (x_hi, x_lo, 1)
+          __align__(16) __half r[kK1];
+          const __half z = __float2half_rn(0.f);
+#pragma unroll
+          for (int k = 0; k < kK1; ++k) r[k] = z;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) r[k] = r[3 + k] = th[kOffW1 + 3 * tid + k];
+          r[6] = th[kOffB1 + tid];
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b1) + core_off<kK1>(tid, 0)) =
+              *reinterpret_cast<const uint4*>(r);
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b1) + core_off<kK1>(tid, 8)) =
+              *reinterpret_cast<const uint4*>(r + 8);
+          sm.bias2[tid] = __half2float(th[kOffB2 + tid]);
+        }
+        for (int c = tid; c < kN3 * (kMlpH / 8); c += kTcRows) {
+          const int nrow = c / (kMlpH / 8), kc = c % (kMlpH / 8);
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (nrow < 3) v = *reinterpret_cast<const uint4*>(th + kOffW3 + nrow * kMlpH + kc * 8);
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.b3) + core_off<kMlpH>(nrow, kc * 8)) = v;
         }
         if (tid < 3) {
-          sm.b3[tid] = __half2float(th[kOffB3 + tid]);
+          sm.bias3[tid] = __half2float(th[kOffB3 + tid]);
           sm.nc[tid] = norms[bsel].c[tid];
           sm.ninv[tid] = norms[bsel].inv_h[tid];
         }
         __syncthreads();
         if (tid == 0) sm.block = bsel;
       }
-      // layer 1 of this row (zero for rows of other blocks), the A row
       const bool mine = !done && myb == bsel;
-      const float x0 = (gi.x - sm.nc[0]) * sm.ninv[0], x1 = (gi.y - sm.nc[1]) * sm.ninv[1],
-                  x2 = (gi.z - sm.nc[2]) * sm.ninv[2];
+      // layer 1: the row (x_hi, x_lo, 1, 0 ...) of this point (zero for rows
+      // of other blocks)
+      {
+        const float x[3] = {(gi.x - sm.nc[0]) * sm.ninv[0], (gi.y - sm.nc[1]) * sm.ninv[1],
+                            (gi.z - sm.nc[2]) * sm.ninv[2]};
+        __align__(16) __half r[kK1];
+        const __half z = __float2half_rn(0.f);
 #pragma unroll
-      for (int kc = 0; kc < kMlpH / 8; ++kc) {
-        __align__(16) __half h[8];
+        for (int k = 0; k < kK1; ++k) r[k] = z;
+        if (mine) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float4 w = sm.w1b[kc * 8 + e];
-          const float z = w.w + w.x * x0 + w.y * x1 + w.z * x2;
-          h[e] = __float2half_rn(mine ? fmaxf(z, 0.f) : 0.f);
+          for (int k = 0; k < 3; ++k) {
+            const __half hi = __float2half_rn(x[k]);
+            r[k] = hi;
+            r[3 + k] = __float2half_rn(x[k] - __half2float(hi));
+          }
+          r[6] = __float2half_rn(1.f);
         }
-        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off(tid, kc * 8)) =
-            *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off<kK1>(tid, 0)) =
+            *reinterpret_cast<const uint4*>(r);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sm.a) + core_off<kK1>(tid, 8)) =
+            *reinterpret_cast<const uint4*>(r + 8);
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the A rows, for the tensor cores
-      tc_fence_before();
-      __syncthreads();
-      // layer 2: one thread issues the four K = 16 steps and commits
-      if (tid == 0) {
-        tc_fence_after();
+      if (!mma_round(sm, phase, [&] {
+            tc_mma(tmem, smem_desc(sm.a, 16 * kK1), smem_desc(sm.b1, 16 * kK1), idesc_f16(kMlpH), 0);
+          }))
+        break;
+      relu_row_to_a(sm, trow, nullptr, tid);          // h1 (b1 is in the MMA)
+      // layer 2
+      if (!mma_round(sm, phase, [&] {
 #pragma unroll
-        for (int s = 0; s < kMlpH / 16; ++s)
-          tc_mma(tmem, smem_desc(reinterpret_cast<const char*>(sm.a) + 256 * s),
-                 smem_desc(reinterpret_cast<const char*>(sm.b) + 256 * s), s > 0);
-        tc_commit(&sm.mbar);
-      }
-      const bool ok = mbar_wait(&sm.mbar, phase);
-      phase ^= 1u;
-      if (!ok) atomicOr(&sm.err, 1);
-      __syncthreads();
-      if (sm.err) break;
-      tc_fence_after();
-      // layer 3 from this thread's accumulator row (TMEM lane = row)
-      float out[3] = {sm.b3[0], sm.b3[1], sm.b3[2]};
+            for (int k = 0; k < kMlpH / 16; ++k)
+              tc_mma(tmem, smem_desc(reinterpret_cast<const char*>(sm.a) + 256 * k, 16 * kMlpH),
+                     smem_desc(reinterpret_cast<const char*>(sm.b2) + 256 * k, 16 * kMlpH), idesc_f16(kMlpH),
+                     k > 0);
+          }))
+        break;
+      relu_row_to_a(sm, trow, sm.bias2, tid);         // h2
+      // layer 3
+      if (!mma_round(sm, phase, [&] {
 #pragma unroll
-      for (int c0 = 0; c0 < kMlpH; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float4 w = sm.w3b[c0 + e];
-          const float h2 = __half2float(__float2half_rn(fmaxf(v[e] + w.w, 0.f)));
-          out[0] += w.x * h2;
-          out[1] += w.y * h2;
-          out[2] += w.z * h2;
-        }
-      }
+            for (int k = 0; k < kMlpH / 16; ++k)
+              tc_mma(tmem, smem_desc(reinterpret_cast<const char*>(sm.a) + 256 * k, 16 * kMlpH),
+                     smem_desc(reinterpret_cast<const char*>(sm.b3) + 256 * k, 16 * kMlpH), idesc_f16(kN3), k > 0);
+          }))
+        break;
+      float v[16];
+      tmem_ld16(trow, v);
       if (mine) {
-        p_out[item] = make_float4(out[0], out[1], out[2], 0.f);
+        p_out[item] = make_float4(v[0] + sm.bias3[0], v[1] + sm.bias3[1], v[2] + sm.bias3[2], 0.f);
         done = true;
       }
       tc_fence_before();
@@ -252,8 +320,8 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
   }
   __syncthreads();
   if (sm.err) {
-    // an MMA that did not complete in time: wait once more (bounded) before
-    // its tensor memory is released
+    // an MMA chain that did not complete in time: wait once more (bounded)
+    // before its tensor memory is released
     if (tid == 0) {
       mbar_wait(&sm.mbar, phase ^ 1u);
       atomicAdd(&st->async_timeouts, 1ull);
@@ -265,7 +333,6 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
     tmem_dealloc(tmem);
   }
 }
-
 
 // Counting sort of list entries by block (the guess list of the RF method):
 // perm lists the entries block after block, so the inference's tiles hold
