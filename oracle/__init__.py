@@ -7,6 +7,7 @@ the CUDA path; both consume the seeded inputs of
 
 Functions follow the paper (Fuchs & Hjelmervik, TVCG 2015):
   eval           Eq. 1 (Cox-de Boor), first partials, scalar per mode
+                 (control points, det J, Eq. 23, von Mises of §6.2 Eq. 24)
   hits / pairs   §4.1 intersections, §4.2 Alg. 2 pairing
   invert         §5.1 Newton (RF) with QR, clamping and line search
   composite      §3.2.1 Alg. 1 with supersampling
@@ -48,7 +49,7 @@ c_double_p = C.POINTER(C.c_double)
 class _Block(C.Structure):
     _fields_ = [("degree", C.c_int * 3), ("n_cp", C.c_int * 3),
                 ("knots", c_double_p * 3), ("geom_cp", c_double_p),
-                ("scalar_cp", c_double_p)]
+                ("scalar_cp", c_double_p), ("disp_cp", c_double_p)]
 
 
 class _Camera(C.Structure):
@@ -141,7 +142,8 @@ def camera_struct(cam):
 
 
 class OracleVolume:
-    """Oracle copy of a multi-block volume (scalar mode CP / DETJ / QUALITY)."""
+    """Oracle copy of a multi-block volume (scalar mode CP / DETJ / QUALITY /
+    VONMISES, the last from the blocks' displacement control points, §6.2)."""
 
     def __init__(self, blocks, scalar_mode):
         L = lib()
@@ -151,7 +153,8 @@ class OracleVolume:
             kn = [_f64(k) for k in b.knots]
             g = _f64(b.geom_cp)
             s = _f64(b.scalar_cp) if b.scalar_cp is not None else None
-            self._keep += kn + [g] + ([s] if s is not None else [])
+            u = _f64(b.disp_cp) if getattr(b, "disp_cp", None) is not None else None
+            self._keep += kn + [g] + [x for x in (s, u) if x is not None]
             nu, nv, nw = b.n_cp
             for d in range(3):
                 arr[bi].degree[d] = int(b.degree[d])
@@ -159,6 +162,7 @@ class OracleVolume:
             arr[bi].n_cp[0], arr[bi].n_cp[1], arr[bi].n_cp[2] = nu, nv, nw
             arr[bi].geom_cp = _dp(g)
             arr[bi].scalar_cp = _dp(s) if s is not None else c_double_p()
+            arr[bi].disp_cp = _dp(u) if u is not None else c_double_p()
         err = C.create_string_buffer(256)
         h = L.orc_volume_create(arr, len(blocks), int(scalar_mode), err, 256)
         if not h:

@@ -208,6 +208,7 @@ struct Block {
   Basis1D B[3];
   std::vector<double> geom;    // [nw][nv][nu][3]
   std::vector<double> scal;    // [nw][nv][nu] or empty
+  std::vector<double> disp;    // [nw][nv][nu][3] displacement u (§6.2) or empty
   double mean_abs_det = 1.0;   // mean of |det J| over [0,1]^3 (the block's volume in G)
 };
 
@@ -284,10 +285,58 @@ void block_eval2(const Block& b, const double p[3], double phi[3], double J[3][3
       }
 }
 
-enum { MODE_CP = 0, MODE_DETJ = 1, MODE_QUALITY = 2 };
+enum { MODE_CP = 0, MODE_DETJ = 1, MODE_QUALITY = 2, MODE_VONMISES = 3 };
 
-double scalar_of(int mode, const double J[3][3], double rho_cp) {
+// J_u[r][c] = d u_r / d p_c of the displacement spline u: P -> R^3 (§6.2),
+// same knots and basis as the geometry, Cox-de Boor at p.
+void disp_jacobian(const Block& b, const double p[3], double Ju[3][3]) {
+  std::vector<double> N[3], dN[3];
+  for (int d = 0; d < 3; ++d) b.B[d].eval(p[d], N[d], dN[d]);
+  const int nu = b.B[0].n, nv = b.B[1].n, nw = b.B[2].n;
+  for (int r = 0; r < 3; ++r) Ju[r][0] = Ju[r][1] = Ju[r][2] = 0;
+  for (int k = 0; k < nw; ++k)
+    for (int j = 0; j < nv; ++j)
+      for (int i = 0; i < nu; ++i) {
+        const double* c = &b.disp[3 * (((size_t)k * nv + j) * nu + i)];
+        const double wu = dN[0][i] * N[1][j] * N[2][k];
+        const double wv = N[0][i] * dN[1][j] * N[2][k];
+        const double ww = N[0][i] * N[1][j] * dN[2][k];
+        for (int r = 0; r < 3; ++r) {
+          Ju[r][0] += wu * c[r];
+          Ju[r][1] += wv * c[r];
+          Ju[r][2] += ww * c[r];
+        }
+      }
+}
+
+// §6.2 (Eq. 24): the Jacobian of u o phi^-1 at g = phi(p) solves
+// J_phi(p)^T X = J_u(p)^T column by column (QR), the strain tensor is its
+// symmetric part sigma = (X + X^T) / 2, and rho is the von Mises value
+// sqrt(((s11 - s22)^2 + (s22 - s33)^2 + (s33 - s11)^2
+//        + 6 (s12^2 + s23^2 + s31^2)) / 2)
+// (the squares and the root, garbled in the printed equation, restored).
+double von_mises(const Block& b, const double p[3], const double J[3][3]) {
+  double Ju[3][3], JT[3][3], X[3][3];
+  disp_jacobian(b, p, Ju);
+  for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) JT[r][c] = J[c][r];
+  for (int col = 0; col < 3; ++col) {
+    const double rhs[3] = {Ju[col][0], Ju[col][1], Ju[col][2]};   // column col of J_u^T
+    double x[3];
+    qr_solve3(JT, rhs, x);
+    for (int r = 0; r < 3; ++r) X[r][col] = x[r];
+  }
+  double sg[3][3];
+  for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) sg[r][c] = 0.5 * (X[r][c] + X[c][r]);
+  const double d01 = sg[0][0] - sg[1][1], d12 = sg[1][1] - sg[2][2], d20 = sg[2][2] - sg[0][0];
+  const double q = d01 * d01 + d12 * d12 + d20 * d20 +
+                   6.0 * (sg[0][1] * sg[0][1] + sg[1][2] * sg[1][2] + sg[2][0] * sg[2][0]);
+  return std::sqrt(0.5 * q);
+}
+
+// The scalar field rho at p of block b for the volume's mode; J = J_phi(p).
+double scalar_of(const Block& b, int mode, const double p[3], const double J[3][3], double rho_cp) {
   if (mode == MODE_CP) return rho_cp;
+  if (mode == MODE_VONMISES) return von_mises(b, p, J);
   const double dj = det3(J);
   if (mode == MODE_DETJ) return dj;
   double f = 0;                                     // Eq. 23: det J / ||J||_F
@@ -981,7 +1030,7 @@ void render_pair(const Volume& V, const TF& tf, const Params& P, const double o[
     }
     double phi[3], J[3][3], rc;
     block_eval(b, p, phi, J, &rc);
-    const double rho = scalar_of(V.mode, J, rc);
+    const double rho = scalar_of(b, V.mode, p, J, rc);
     if (trace) {
       trace->push_back(s[j]);
       for (int r = 0; r < 3; ++r) trace->push_back(p[r]);
@@ -1285,6 +1334,7 @@ typedef struct {
   const double* knots[3];
   const double* geom_cp;
   const double* scalar_cp;
+  const double* disp_cp;       // [nw][nv][nu][3], the displacement for MODE_VONMISES
 } orc_block_desc;
 
 typedef struct {
@@ -1316,7 +1366,7 @@ void* orc_volume_create(const orc_block_desc* blocks, int n_blocks, int mode, ch
     return nullptr;
   };
   if (!blocks || n_blocks <= 0) return fail("no blocks");
-  if (mode < 0 || mode > 2) return fail("bad scalar mode");
+  if (mode < 0 || mode > 3) return fail("bad scalar mode");
   Volume* V = new Volume();
   V->mode = mode;
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -1341,6 +1391,10 @@ void* orc_volume_create(const orc_block_desc* blocks, int n_blocks, int mode, ch
     if (mode == MODE_CP) {
       if (!d.scalar_cp) { delete V; return fail("scalar mode CP needs scalar control points"); }
       b.scal.assign(d.scalar_cp, d.scalar_cp + ncp);
+    }
+    if (mode == MODE_VONMISES) {
+      if (!d.disp_cp) { delete V; return fail("scalar mode VONMISES needs displacement control points"); }
+      b.disp.assign(d.disp_cp, d.disp_cp + 3 * ncp);
     }
     for (size_t q = 0; q < ncp; ++q) for (int r = 0; r < 3; ++r) {
       lo[r] = std::min(lo[r], b.geom[3 * q + r]);
@@ -1385,7 +1439,7 @@ int orc_eval(void* v, int block, int n, const double* p, double* phi, double* J,
     block_eval(V->blocks[block], p + 3 * i, f, Jm, &rc);
     if (phi) for (int r = 0; r < 3; ++r) phi[3 * i + r] = f[r];
     if (J) for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) J[9 * i + 3 * r + c] = Jm[r][c];
-    if (rho) rho[i] = scalar_of(V->mode, Jm, rc);
+    if (rho) rho[i] = scalar_of(V->blocks[block], V->mode, p + 3 * i, Jm, rc);
   }
   return 0;
 }
@@ -1433,7 +1487,7 @@ int orc_scalar_range(void* v, int n, double* lo, double* hi) {
       for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
         double p[3] = {(i + 0.5) / n, (j + 0.5) / n, (k + 0.5) / n}, f[3], J[3][3], rc;
         block_eval(b, p, f, J, &rc);
-        double s = scalar_of(V->mode, J, rc);
+        double s = scalar_of(b, V->mode, p, J, rc);
         a = std::min(a, s); z = std::max(z, s);
       }
     }

@@ -38,6 +38,7 @@ import numpy as np
 SCALAR_CP = 0       # rho from scalar control points
 SCALAR_DETJ = 1     # rho = det J_phi
 SCALAR_QUALITY = 2  # rho = det J_phi / ||J_phi||_F  (Eq. 23)
+SCALAR_VONMISES = 3  # rho = von Mises value of the strain of a displacement u (§6.2, Eq. 24)
 
 PRECISION_FP32 = 0
 PRECISION_MIXED = 1
@@ -51,6 +52,7 @@ class Block:
     knots: List[np.ndarray]  # 3 float64 arrays, len n_cp[d] + degree[d] + 1
     geom_cp: np.ndarray    # float64 [n_w][n_v][n_u][3], u fastest
     scalar_cp: Optional[np.ndarray] = None  # float64 [n_w][n_v][n_u]
+    disp_cp: Optional[np.ndarray] = None    # float64 [n_w][n_v][n_u][3], displacement u (§6.2)
 
     @property
     def n_cp(self):
@@ -252,13 +254,21 @@ def twisted_bar(seed: int = 12346, width: int = 1920, height: int = 1080,
 
 
 def bent_beam(seed: int = 12347, width: int = 1920, height: int = 1080,
-              precision: int = PRECISION_MIXED) -> Scene:
+              precision: int = PRECISION_MIXED, displacement: bool = False) -> Scene:
     """16 cubic blocks (2x2 cross-section, 4 along) of the beam
     [0,1]^2 x [0,8], each 6x6x12 cp, sharing face control points (C0); the
     global net is jittered by U(-a,a), a = 0.5% of the smallest block edge,
     then bent 60 deg about the y axis along a circular arc.  Scalar: sum of 8
     seeded Gaussians on the unbent beam, quasi-interpolated at Greville
-    points.  The TF leaves r in [0,0.4] transparent."""
+    points.  The TF leaves r in [0,0.4] transparent.
+
+    displacement=True adds a displacement spline per block and renders its
+    von Mises value (§6.2): a cantilever clamped at z = 0 under a tip load
+    along x (Euler-Bernoulli: deflection w(z) = delta (z/L)^2 (3 - z/L) / 2,
+    axial u_z = -(x - 1/2) w'(z), delta = 0.05), plus three seeded
+    sinusoids of amplitude delta/5 per component (generator seed + 1000),
+    taken at the Greville points of the unbent beam and turned with the bend
+    into world axes."""
     rng = np.random.default_rng(seed)
     p = 3
     nb = (2, 2, 4)
@@ -291,6 +301,19 @@ def bent_beam(seed: int = 12347, width: int = 1920, height: int = 1080,
     f = np.zeros(G.shape[:3])
     for k in range(8):
         f += amp[k] * np.exp(-np.sum((G - cen[k]) ** 2, -1) / (2 * sig[k] ** 2))
+    U = None
+    if displacement:
+        drng = np.random.default_rng(seed + 1000)
+        L, delta = ext[2], 0.05
+        zl = G[..., 2] / L
+        w = delta * zl ** 2 * (3.0 - zl) / 2.0
+        dw = delta * 3.0 * zl * (2.0 - zl) / (2.0 * L)
+        loc = np.stack([w, np.zeros_like(w), -(G[..., 0] - 0.5) * dw], -1)
+        for _ in range(3):
+            kv = _random_dir(drng) * drng.uniform(0.5, 2.0)
+            loc += (0.2 * delta * drng.uniform(-1, 1, 3)) * np.sin(G @ kv + drng.uniform(0, 2 * math.pi))[..., None]
+        ct, st_ = np.cos(G[..., 2] / R), np.sin(G[..., 2] / R)
+        U = np.stack([loc[..., 0] * ct - loc[..., 2] * st_, loc[..., 1], loc[..., 0] * st_ + loc[..., 2] * ct], -1)
     blocks = []
     for bw in range(nb[2]):
         for bv in range(nb[1]):
@@ -299,7 +322,8 @@ def bent_beam(seed: int = 12347, width: int = 1920, height: int = 1080,
                 sv = slice(bv * (ncp[1] - 1), bv * (ncp[1] - 1) + ncp[1])
                 sw = slice(bw * (ncp[2] - 1), bw * (ncp[2] - 1) + ncp[2])
                 blocks.append(Block((p, p, p), [k.copy() for k in kn],
-                                    bent[sw, sv, su].copy(), f[sw, sv, su].copy()))
+                                    bent[sw, sv, su].copy(), f[sw, sv, su].copy(),
+                                    U[sw, sv, su].copy() if U is not None else None))
     r = np.concatenate([[0.0, 0.4], np.sort(rng.uniform(0.4, 1.0, 5)), [1.0]])
     rgba = rng.uniform(0, 1, (8, 4))
     rgba[:2, 3] = 0.0
@@ -310,6 +334,8 @@ def bent_beam(seed: int = 12347, width: int = 1920, height: int = 1080,
     cam = _perspective_camera(centre, 14.0, rng.uniform(15, 35),
                               rng.uniform(0, 2 * math.pi), 35.0, up_axis=1)
     params = RenderParams(rk_tol=1e-5, ds=_default_ds(blocks), precision=precision)
+    if displacement:
+        return Scene("loaded_beam", blocks, SCALAR_VONMISES, tf, cam, width, height, params)
     return Scene("bent_beam", blocks, SCALAR_CP, tf, cam, width, height, params)
 
 
