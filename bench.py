@@ -45,6 +45,8 @@ WORKLOADS = {
                          "64-knot TF, 3840x2160, rk_tol 1e-6, mixed precision"),
     "backstep4k-fp32": (4, 0, "backward-facing step, 3 quadratic/cubic blocks 64x16x16 cp, shear-layer scalar, "
                               "64-knot TF, 3840x2160, rk_tol 1e-6, FP32"),
+    "beam1080-vonmises": ("vm", 0, "bent beam, 16 cubic blocks 6x6x12 cp (C0) with a cantilever displacement "
+                                   "spline, von Mises scalar (6.2, Eq. 24), 1920x1080 perspective, FP32"),
     "batch64": (None, 0, "64 requests over the twisted cube, twisted bar and bent beam, sizes uniform over "
                          "{256,512,768,1024}^2, seeded cameras and TFs, FP32, one CUDA graph"),
 }
@@ -112,6 +114,10 @@ def flop_model(P):
         # (N^3 + N^2 + N FMA [84]) and the value basis [200]
         "rho_j": 2 * (6 * N ** 3 + 9 * N ** 2 + 9 * N) + 92,
         "rho_cp": 2 * (N ** 3 + N ** 2 + N) + 32,
+        # von Mises (§6.2): J_phi and J_u at the sample (two contractions of
+        # 6N^3 + 9N^2 + 9N FMA, one basis), the adjugate, J_u adj(J) / det,
+        # the strain's deviatoric sum and its root (130) [2348]
+        "rho_vm": 4 * (6 * N ** 3 + 9 * N ** 2 + 9 * N) + 92 + 130,
         # one implicit Euler Newton iteration: phi, J and the Hessian
         # (9N^3 + 18N^2 + 30N FMA [984]), second-derivative basis, V and the
         # solve for W, the Jacobian of G and its solve [2218]
@@ -131,7 +137,11 @@ def scene_degree(blocks):
     return max(max(b.degree) for b in blocks)
 
 
-def k5_flops_per_unit(st, F, scalar_cp, P):
+def _scalar_kind(mode):
+    return {0: "cp", 3: "vm"}.get(int(mode), "j")
+
+
+def k5_flops_per_unit(st, F, scalar_mode, P):
     """Stage-3 work of the frame priced per unit with the scalar taken as if
     J were at hand at every sample: per RHS F["rhs"] (1283 cubic), per step
     attempt 40, per sample 100 (K = 4 TF lookups, exp and Alg. 1) plus the
@@ -140,15 +150,18 @@ def k5_flops_per_unit(st, F, scalar_cp, P):
     J at each sample instead (rho_evals x F["rho_j"]): that cost of the
     split design is not counted here."""
     N = P + 1
-    rho = 2 * (N ** 3 + N ** 2 + N) if scalar_cp else 40
+    kind = _scalar_kind(scalar_mode)
+    # the scalar with J at hand: control points; det J or Eq. 23 (about 40);
+    # von Mises: the J_u contraction (6N^3 + 9N^2 + 9N FMA) and 130
+    rho = {"cp": 2 * (N ** 3 + N ** 2 + N), "j": 40, "vm": 2 * (6 * N ** 3 + 9 * N ** 2 + 9 * N) + 130}[kind]
     return st["rhs_evals"] * F["rhs"] + (st["rk_steps"] + st["rk_rejects"]) * 40 + st["samples"] * (100 + rho)
 
 
-def k5_flops(st, F, scalar_cp, implicit=False):
+def k5_flops(st, F, scalar_mode, implicit=False):
     # implicit Euler counts one map evaluation per Newton iteration in rhs_evals
     return (st["rhs_evals"] * (F["irk"] if implicit else F["rhs"])
             + (st["rk_steps"] + st["rk_rejects"]) * F["step"]
-            + st["samples"] * F["sample"] + st["rho_evals"] * (F["rho_cp"] if scalar_cp else F["rho_j"]))
+            + st["samples"] * F["sample"] + st["rho_evals"] * F["rho_" + _scalar_kind(scalar_mode)])
 
 
 def k2_flops(st, F):
@@ -439,7 +452,7 @@ def run_ours(args):
         train = overrides.get("use_mlp_guess") == 1
     else:
         cfg, prec, workload = WORKLOADS[args.workload]
-    sc = scenes.config(cfg)
+    sc = scenes.bent_beam(seed=12347, displacement=True) if cfg == "vm" else scenes.config(cfg)
     sc.params.precision = prec
     for k, v in overrides.items():
         setattr(sc.params, k, v)
@@ -476,8 +489,8 @@ def run_ours(args):
     vol.render(sc.camera, sc.params, W, H, out=out, flags=ivv.FLAG_STATS, window=window)
     st = vol.stats()
     F = flop_model(scene_degree(sc.blocks))
-    flops_k5 = k5_flops(st, F, sc.scalar_mode == scenes.SCALAR_CP, implicit=args.rk_method == 7)
-    flops_k5_unit = (k5_flops_per_unit(st, F, sc.scalar_mode == scenes.SCALAR_CP, scene_degree(sc.blocks))
+    flops_k5 = k5_flops(st, F, sc.scalar_mode, implicit=args.rk_method == 7)
+    flops_k5_unit = (k5_flops_per_unit(st, F, sc.scalar_mode, scene_degree(sc.blocks))
                      if args.rk_method != 7 and sc.params.method == 0 else None)
     flops_k2 = k2_flops(st, F)
 
@@ -677,7 +690,7 @@ def run_batch(args):
     # control-point scalars (cube, beam) and Eq. 23 (bar): counted at the
     # control-point cost, a lower bound on the work
     F = flop_model(scene_degree(vols[0].blocks))
-    flops_k5 = k5_flops(st, F, True)
+    flops_k5 = k5_flops(st, F, 0)
     b.render(flags=ivv.FLAG_TIMING)
     stages = b.stage_times()
 
@@ -762,7 +775,6 @@ def run_batch(args):
                                         "rho_evals", "fragments", "isect_items", "isect_split", "isect_tests",
                                         "isect_newton")},
             "parity": parity,
-            "entry_exit_parity": pair_err,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

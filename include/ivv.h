@@ -52,7 +52,9 @@ typedef enum {
 enum {
   IVV_SCALAR_CP = 0,        /* rho from the scalar control points              */
   IVV_SCALAR_DETJ = 1,      /* rho = det J_phi, derived per sample              */
-  IVV_SCALAR_QUALITY = 2    /* rho = det J_phi / ||J_phi||_F  (Eq. 23)          */
+  IVV_SCALAR_QUALITY = 2,   /* rho = det J_phi / ||J_phi||_F  (Eq. 23)          */
+  IVV_SCALAR_VONMISES = 3   /* rho = von Mises value of the strain of the
+                               displacement u (§6.2, Eq. 24), per sample      */
 };
 
 /* Arithmetic of the ray stages: */
@@ -86,13 +88,23 @@ typedef struct ivv_volume ivv_volume;     /* opaque, library-owned */
  *   to [0,1]^3, §5.1 and §5.4).
  * geom_cp: [n_cp[2]][n_cp[1]][n_cp[0]][3] doubles, u fastest.
  * scalar_cp: [n_cp[2]][n_cp[1]][n_cp[0]] doubles; required for IVV_SCALAR_CP,
- *   ignored otherwise. */
+ *   ignored otherwise.
+ * disp_cp: [n_cp[2]][n_cp[1]][n_cp[0]][3] doubles, the control points of the
+ *   displacement field u: P -> R^3 of a structural analysis (§6.2) on the
+ *   block's knots and degrees; required for IVV_SCALAR_VONMISES, ignored
+ *   otherwise.  Per sample the library forms J_u J_phi^-1 (the Jacobian of
+ *   u o phi^-1, whose transpose solves the paper's J_phi^T X = J_u^T), the
+ *   strain tensor sigma = its symmetric part, and
+ *   rho = sqrt(((s11-s22)^2 + (s22-s33)^2 + (s33-s11)^2
+ *               + 6 (s12^2 + s23^2 + s31^2)) / 2).
+ *   Batches (ivv_batch_create) do not take IVV_SCALAR_VONMISES volumes. */
 typedef struct {
   int degree[3];
   int n_cp[3];
   const double* knots[3];
   const double* geom_cp;
   const double* scalar_cp;
+  const double* disp_cp;
 } ivv_block_desc;
 
 /* Pinhole (ortho = 0) or orthographic (ortho = 1) camera.  The ray of pixel

@@ -394,6 +394,8 @@ ivv_status ivv_batch_create(const ivv_request* req, int n, const ivv_render_para
       return bfail(IVV_ERR_UNSUPPORTED, "the volumes of a batch must share one common degree P");
     if (req[i].volume->hv.any_singular)
       return bfail(IVV_ERR_UNSUPPORTED, "batches take volumes without singular faces (render those with ivv_render)");
+    if (req[i].volume->hv.mode == IVV_SCALAR_VONMISES)
+      return bfail(IVV_ERR_UNSUPPORTED, "batches do not take von Mises volumes (render those with ivv_render)");
   }
   // shared parameters (diag 1: ds is resolved per request below)
   ivv_render_params p;

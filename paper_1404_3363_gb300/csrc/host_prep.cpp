@@ -9,6 +9,7 @@
 #include <cstring>
 
 #include "ivv_internal.h"
+#include "strain.h"
 
 namespace ivv {
 namespace {
@@ -184,8 +185,12 @@ void face_obb(const double* cp, int P, const double org[3], FaceMeta& m) {
 
 }  // namespace
 
-void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
-               double* rho_cp) {
+namespace {
+
+// Value and first partials of one field stored as Bezier elements (el, org:
+// the geometry with its scalar channel, or the displacement) at p.
+void eval_elements(const HostVolume& hv, const std::vector<double>& el, const std::vector<double>& eorg, int block,
+                   const double p[3], double f[3], double J[3][3], double* rho_cp) {
   const BlockInfo& B = hv.blocks[block];
   const int P = hv.P, n1 = P + 1;
   int e[3];
@@ -198,13 +203,13 @@ void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3]
     loc[d] = (x - brk[e[d]]) * sc[d];
   }
   const int eid = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
-  const double* C = &hv.elem[(size_t)eid * n1 * n1 * n1 * 4];
-  const double* org = &hv.elem_org[(size_t)eid * 4];
+  const double* C = &el[(size_t)eid * n1 * n1 * n1 * 4];
+  const double* org = &eorg[(size_t)eid * 4];
   double bu[4], dbu[4], bv[4], dbv[4], bw[4], dbw[4];
   bernstein(P, loc[0], bu, dbu);
   bernstein(P, loc[1], bv, dbv);
   bernstein(P, loc[2], bw, dbw);
-  for (int r = 0; r < 3; ++r) { phi[r] = 0; J[r][0] = J[r][1] = J[r][2] = 0; }
+  for (int r = 0; r < 3; ++r) { f[r] = 0; J[r][0] = J[r][1] = J[r][2] = 0; }
   double rho = 0;
   for (int i = 0; i < n1; ++i)
     for (int j = 0; j < n1; ++j)
@@ -212,21 +217,42 @@ void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3]
         const double* c = C + ((i * n1 + j) * n1 + k) * 4;
         const double w0 = bu[i] * bv[j] * bw[k];
         for (int r = 0; r < 3; ++r) {
-          phi[r] += w0 * c[r];
+          f[r] += w0 * c[r];
           J[r][0] += dbu[i] * bv[j] * bw[k] * c[r] * sc[0];
           J[r][1] += bu[i] * dbv[j] * bw[k] * c[r] * sc[1];
           J[r][2] += bu[i] * bv[j] * dbw[k] * c[r] * sc[2];
         }
         rho += w0 * c[3];
       }
-  for (int r = 0; r < 3; ++r) phi[r] += org[r];
+  for (int r = 0; r < 3; ++r) f[r] += org[r];
   if (rho_cp) *rho_cp = rho;
+}
+
+}  // namespace
+
+void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
+               double* rho_cp) {
+  eval_elements(hv, hv.elem, hv.elem_org, block, p, phi, J, rho_cp);
+}
+
+double host_scalar(const HostVolume& hv, int block, const double p[3], const double J[3][3], double rho_cp) {
+  if (hv.mode == IVV_SCALAR_CP) return rho_cp;
+  if (hv.mode == IVV_SCALAR_VONMISES) {
+    double u[3], Ju[3][3];
+    eval_elements(hv, hv.disp, hv.disp_org, block, p, u, Ju, nullptr);
+    return von_mises<double>(J, Ju);
+  }
+  const double dj = det3(J);
+  if (hv.mode == IVV_SCALAR_DETJ) return dj;
+  double f = 0;
+  for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) f += J[r][c] * J[r][c];
+  return dj / std::sqrt(f);
 }
 
 ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, HostVolume& hv,
                           std::string& err) {
   if (!blocks || n_blocks <= 0) { err = "no blocks"; return IVV_ERR_INVALID_ARG; }
-  if (mode < IVV_SCALAR_CP || mode > IVV_SCALAR_QUALITY) { err = "bad scalar mode"; return IVV_ERR_INVALID_ARG; }
+  if (mode < IVV_SCALAR_CP || mode > IVV_SCALAR_VONMISES) { err = "bad scalar mode"; return IVV_ERR_INVALID_ARG; }
   hv = HostVolume();
   hv.mode = mode;
   hv.n_blocks = n_blocks;
@@ -244,7 +270,13 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
     if (mode == IVV_SCALAR_CP && !blocks[b].scalar_cp) {
       err = "IVV_SCALAR_CP needs scalar control points"; return IVV_ERR_INVALID_ARG;
     }
+    if (mode == IVV_SCALAR_VONMISES && !blocks[b].disp_cp) {
+      err = "IVV_SCALAR_VONMISES needs displacement control points"; return IVV_ERR_INVALID_ARG;
+    }
   }
+  // channels carried through the extraction: (x, y, z, rho), plus the
+  // displacement (u_x, u_y, u_z) for the von Mises scalar
+  const int nc = mode == IVV_SCALAR_VONMISES ? 7 : 4;
   hv.P = P;
   const int n1 = P + 1;
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -269,21 +301,26 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
       for (double& x : kn[k]) x = (x - a) / (z - a);
     }
     const int nu = d.n_cp[0], nv = d.n_cp[1], nw = d.n_cp[2];
-    // grid[w][v][u][4] = (x, y, z, rho)
-    std::vector<double> grid((size_t)nu * nv * nw * 4);
+    // grid[w][v][u][nc] = (x, y, z, rho[, u_x, u_y, u_z])
+    std::vector<double> grid((size_t)nu * nv * nw * nc);
     for (size_t q = 0; q < (size_t)nu * nv * nw; ++q) {
       for (int r = 0; r < 3; ++r) {
         const double v = d.geom_cp[3 * q + r];
         if (!std::isfinite(v)) { err = "non-finite control point"; return IVV_ERR_INVALID_ARG; }
-        grid[4 * q + r] = v;
+        grid[nc * q + r] = v;
         lo[r] = std::min(lo[r], v);
         hi[r] = std::max(hi[r], v);
       }
       const double s = (mode == IVV_SCALAR_CP) ? d.scalar_cp[q] : 0.0;
       if (!std::isfinite(s)) { err = "non-finite scalar control point"; return IVV_ERR_INVALID_ARG; }
-      grid[4 * q + 3] = s;
+      grid[nc * q + 3] = s;
       slo = std::min(slo, s);
       shi = std::max(shi, s);
+      for (int r = 0; r < nc - 4; ++r) {
+        const double u = d.disp_cp[3 * q + r];
+        if (!std::isfinite(u)) { err = "non-finite displacement control point"; return IVV_ERR_INVALID_ARG; }
+        grid[nc * q + 4 + r] = u;
+      }
     }
     // extraction along u, then v, then w (tensor product)
     int dims[3] = {nu, nv, nw};
@@ -294,7 +331,7 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
       int oi = 0;
       for (int a = 0; a < 3; ++a) if (a != axis) other[oi++] = a;
       std::vector<double> seg_out;
-      std::vector<double> line(n * 4);
+      std::vector<double> line((size_t)n * nc);
       int nout = -1;
       std::vector<double> next;
       int ndims[3] = {dims[0], dims[1], dims[2]};
@@ -306,15 +343,15 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
             return ((size_t)c[2] * dd[1] + c[1]) * dd[0] + c[0];
           };
           for (int t = 0; t < n; ++t)
-            for (int c = 0; c < 4; ++c) line[t * 4 + c] = grid[index(dims, t, i0, i1) * 4 + c];
-          extract_curve(kn[axis], d.degree[axis], 4, line.data(), n, P, seg_out, brk[axis]);
+            for (int c = 0; c < nc; ++c) line[t * nc + c] = grid[index(dims, t, i0, i1) * nc + c];
+          extract_curve(kn[axis], d.degree[axis], nc, line.data(), n, P, seg_out, brk[axis]);
           if (nout < 0) {
-            nout = (int)(seg_out.size() / 4);
+            nout = (int)(seg_out.size() / nc);
             ndims[axis] = nout;
-            next.assign((size_t)ndims[0] * ndims[1] * ndims[2] * 4, 0.0);
+            next.assign((size_t)ndims[0] * ndims[1] * ndims[2] * nc, 0.0);
           }
           for (int t = 0; t < nout; ++t)
-            for (int c = 0; c < 4; ++c) next[index(ndims, t, i0, i1) * 4 + c] = seg_out[t * 4 + c];
+            for (int c = 0; c < nc; ++c) next[index(ndims, t, i0, i1) * nc + c] = seg_out[t * nc + c];
         }
       grid.swap(next);
       dims[axis] = ndims[axis];
@@ -342,15 +379,23 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
       for (int ev = 0; ev < B.nseg[1]; ++ev)
         for (int eu = 0; eu < B.nseg[0]; ++eu) {
           const size_t g0 = (((size_t)(ew * n1) * dims[1]) + (ev * n1)) * dims[0] + (eu * n1);
-          const double org[3] = {grid[g0 * 4], grid[g0 * 4 + 1], grid[g0 * 4 + 2]};
+          const double org[3] = {grid[g0 * nc], grid[g0 * nc + 1], grid[g0 * nc + 2]};
           for (int c = 0; c < 3; ++c) hv.elem_org.push_back(org[c]);
           hv.elem_org.push_back(0.0);
+          if (nc == 7) {                  // the displacement, relative to its first control point
+            for (int c = 0; c < 3; ++c) hv.disp_org.push_back(grid[g0 * nc + 4 + c]);
+            hv.disp_org.push_back(0.0);
+          }
           for (int i = 0; i < n1; ++i)
             for (int j = 0; j < n1; ++j)
               for (int k = 0; k < n1; ++k) {
                 const size_t g = (((size_t)(ew * n1 + k) * dims[1]) + (ev * n1 + j)) * dims[0] + (eu * n1 + i);
-                for (int c = 0; c < 3; ++c) hv.elem.push_back(grid[g * 4 + c] - org[c]);
-                hv.elem.push_back(grid[g * 4 + 3]);
+                for (int c = 0; c < 3; ++c) hv.elem.push_back(grid[g * nc + c] - org[c]);
+                hv.elem.push_back(grid[g * nc + 3]);
+                if (nc == 7) {
+                  for (int c = 0; c < 3; ++c) hv.disp.push_back(grid[g * nc + 4 + c] - grid[g0 * nc + 4 + c]);
+                  hv.disp.push_back(0.0);
+                }
               }
         }
     hv.blocks.push_back(B);
@@ -530,12 +575,7 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int mode, 
           for (int i = 0; i < n; ++i) {
             double p[3] = {(i + 0.5) / n, (j + 0.5) / n, (k + 0.5) / n}, phi[3], J[3][3];
             host_eval(hv, b, p, phi, J, nullptr);
-            double s = det3(J);
-            if (mode == IVV_SCALAR_QUALITY) {
-              double f = 0;
-              for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) f += J[r][c] * J[r][c];
-              s /= std::sqrt(f);
-            }
+            const double s = host_scalar(hv, b, p, J, 0.0);
             a = std::min(a, s);
             z = std::max(z, s);
           }

@@ -96,7 +96,7 @@ void free_volume(ivv_volume* v) {
     if (v->ev_copied[k]) cudaEventDestroy(v->ev_copied[k]);
   }
   void* ptrs[] = {v->d_blocks, v->d_brk32, v->d_brk64, v->d_elem32, v->d_elem64, v->d_org32, v->d_rho32, v->d_org64,
-                  v->d_count, v->d_face32, v->d_face64,
+                  v->d_disp32, v->d_dorg32, v->d_disp64, v->d_dorg64, v->d_count, v->d_face32, v->d_face64,
                   v->d_faces, v->d_faces64, v->d_tf_r, v->d_tf_rgba, v->d_stats, v->own_ws, v->own_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -134,6 +134,10 @@ ivv::DevVolume dev_volume(const ivv_volume* v) {
   V.org32 = v->d_org32;
   V.rho32 = v->d_rho32;
   V.org64 = v->d_org64;
+  V.disp32 = v->d_disp32;
+  V.dorg32 = v->d_dorg32;
+  V.disp64 = v->d_disp64;
+  V.dorg64 = v->d_dorg64;
   V.face32 = v->d_face32;
   V.face64 = v->d_face64;
   V.faces = v->d_faces;
@@ -730,6 +734,28 @@ ivv_status ivv_create_volume(const ivv_block_desc* blocks, int n_blocks, int sca
     free_volume(v);
     return fail(st, m);
   }
+  if (!hv.disp.empty()) {
+    std::vector<float4> disp32(hv.disp.size() / 4), dorg32(hv.disp_org.size() / 4);
+    for (size_t i = 0; i < disp32.size(); ++i)
+      disp32[i] = make_float4((float)hv.disp[4 * i], (float)hv.disp[4 * i + 1], (float)hv.disp[4 * i + 2], 0.f);
+    for (size_t i = 0; i < dorg32.size(); ++i)
+      dorg32[i] = make_float4((float)hv.disp_org[4 * i], (float)hv.disp_org[4 * i + 1], (float)hv.disp_org[4 * i + 2],
+                              0.f);
+    if ((st = upload(&v->d_disp32, disp32.data(), disp32.size(), s)) != IVV_OK ||
+        (st = upload(&v->d_dorg32, dorg32.data(), dorg32.size(), s)) != IVV_OK ||
+        (st = upload(&v->d_disp64, (const ivv::Dbl4*)hv.disp.data(), hv.disp.size() / 4, s)) != IVV_OK ||
+        (st = upload(&v->d_dorg64, (const ivv::Dbl4*)hv.disp_org.data(), hv.disp_org.size() / 4, s)) != IVV_OK) {
+      std::string m = g_err;
+      free_volume(v);
+      return fail(st, m);
+    }
+    // the host vectors die with this scope: the copies must be done
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      free_volume(v);
+      return cuda_fail(e, "displacement upload");
+    }
+  }
   for (int i = 0; i <= IVV_N_STAGES && e == cudaSuccess; ++i) e = cudaEventCreate(&v->ev[i]);
   if (e != cudaSuccess) {
     free_volume(v);
@@ -1184,20 +1210,7 @@ ivv_status ivv_host_eval(const ivv_block_desc* blocks, int n_blocks, int scalar_
     if (jac)
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) jac[9 * i + 3 * r + c] = J[r][c];
-    if (rho) {
-      double s = rc;
-      if (scalar_mode != IVV_SCALAR_CP) {
-        s = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-        if (scalar_mode == IVV_SCALAR_QUALITY) {
-          double fr = 0;
-          for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) fr += J[r][c] * J[r][c];
-          s /= std::sqrt(fr);
-        }
-      }
-      rho[i] = s;
-    }
+    if (rho) rho[i] = ivv::host_scalar(hv, block, p + 3 * i, J, rc);
   }
   return IVV_OK;
 }

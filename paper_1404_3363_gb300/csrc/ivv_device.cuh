@@ -22,6 +22,7 @@
 
 #include "ivv_internal.h"
 #include "isect.cuh"
+#include "strain.h"
 
 namespace ivv {
 
@@ -125,6 +126,12 @@ struct DevVolume {
   const float4* org32;
   const float* rho32;     // scalar control points alone, rho_stride32(P) per element (NULL in batches)
   const Dbl4* org64;
+  // IVV_SCALAR_VONMISES: the displacement u as Bezier elements with their
+  // origins, the geometry's layout (null in other modes)
+  const float4* disp32;
+  const float4* dorg32;
+  const Dbl4* disp64;
+  const Dbl4* dorg64;
   const float4* face32;
   const Dbl4* face64;
   const FaceMeta* faces;
@@ -497,6 +504,41 @@ __device__ __forceinline__ R solve3(const R J[3][3], const R b[3], R x[3]) {
   x[1] = (c01 * b[0] + c11 * b[1] + c21 * b[2]) * inv;
   x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
   return det;
+}
+
+// J_u(p) of the displacement field (IVV_SCALAR_VONMISES): the geometry's
+// element lookup and contraction, run on the displacement elements.
+template <int P, typename R>
+__device__ __forceinline__ void eval_disp_jac(const DevVolume& V, const BlockInfo& B, const R p[3], R Ju[3][3]) {
+  DevVolume U = V;
+  U.elem32 = V.disp32;
+  U.org32 = V.dorg32;
+  U.elem64 = V.disp64;
+  U.org64 = V.dorg64;
+  R u[3], unused;
+  eval_block<P, R, false, true>(U, B, p, u, Ju, unused);
+}
+
+// The scalar rho at parameter point p for the volume's mode, from
+// J = J_phi(p) and the control-point scalar rc there: rc (IVV_SCALAR_CP),
+// det J, Eq. 23's det J / ||J||_F, or the von Mises value of §6.2.
+template <int P, typename R>
+__device__ __forceinline__ R scalar_at(const DevVolume& V, const BlockInfo& B, int mode, const R p[3],
+                                       const R J[3][3], R rc) {
+  if (mode == IVV_SCALAR_CP) return rc;
+  if (mode == IVV_SCALAR_VONMISES) {
+    R Ju[3][3];
+    eval_disp_jac<P, R>(V, B, p, Ju);
+    return von_mises<R>(J, Ju);
+  }
+  const R det = det3<R>(J);
+  if (mode == IVV_SCALAR_DETJ) return det;
+  R f = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) f += J[a][b] * J[a][b];
+  return det / sqrt(f);
 }
 
 // Piecewise-linear TF (knots in shared memory): colour and extinction weight.

@@ -61,6 +61,8 @@ struct HostVolume {
   std::vector<double> brk;         // concatenated breakpoints (normalised)
   std::vector<double> elem;        // [E][(P+1)^3][4] (x, y, z, rho), i-major, xyz relative to elem_org
   std::vector<double> elem_org;    // [E][4] element origin (first control point), w = 0
+  std::vector<double> disp;        // IVV_SCALAR_VONMISES: [E][(P+1)^3][4] (u_x, u_y, u_z, 0) relative to disp_org
+  std::vector<double> disp_org;    // [E][4] the element's first displacement control point, w = 0
   std::vector<double> face_cp;     // [F][(P+1)^2][4] (x, y, z, 0) relative to the face origin, a fastest
   std::vector<FaceMeta> faces;
   std::vector<FaceMeta64> faces64;
@@ -80,5 +82,9 @@ ivv_status prepare_volume(const ivv_block_desc* blocks, int n_blocks, int scalar
 // (used for the det J check and the default scalar range).
 void host_eval(const HostVolume& hv, int block, const double p[3], double phi[3], double J[3][3],
                double* rho_cp);
+
+// The volume's scalar at p of `block` from J = J_phi(p) and the control-point
+// scalar there (IVV_SCALAR_* of the volume), FP64.
+double host_scalar(const HostVolume& hv, int block, const double p[3], const double J[3][3], double rho_cp);
 
 }  // namespace ivv

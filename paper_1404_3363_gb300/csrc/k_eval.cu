@@ -19,19 +19,7 @@ __global__ void k_eval_points(DevVolume V, int block, int n, const float* __rest
   if (jac)
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c) jac[9 * i + 3 * r + c] = J[r][c];
-  if (rho) {
-    float s = rc;
-    if (V.mode != IVV_SCALAR_CP) {
-      s = det3<float>(J);
-      if (V.mode == IVV_SCALAR_QUALITY) {
-        float fr = 0.f;
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) fr += J[r][c] * J[r][c];
-        s /= sqrtf(fr);
-      }
-    }
-    rho[i] = s;
-  }
+  if (rho) rho[i] = scalar_at<P, float>(V, B, V.mode, q, J, rc);
 }
 
 }  // namespace

@@ -61,12 +61,7 @@ __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B,
     } else if (mode == IVV_SCALAR_DETJ) {
       rho = det;
     } else {
-      R f = 0;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) f += J[r][k] * J[r][k];
-      rho = det / sqrt(f);
+      rho = scalar_at<P, R>(V, B, mode, p, J, rc);
     }
   }
 }
@@ -624,7 +619,9 @@ __device__ __forceinline__ float det_cofactor(const float J[3][3]) {
 // sample distance, transfer-function slot and output image, and each block's
 // scalar mode (CP unused); a pixel whose sample list does not fit the list
 // (off + cnt > cap) is left to the fused integrator.
-template <int P, bool STATS, bool CP, bool BATCH = false>
+// VM: the von Mises scalar of §6.2 (its own instance: the displacement's
+// contraction stays out of the other instances' register allocation).
+template <int P, bool STATS, bool CP, bool BATCH = false, bool VM = false>
 __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCamera<float> cam, DevTF tf, int K,
                                                          float early, BatchArgs ba, const int* __restrict__ cnt,
                                                          const float4* __restrict__ pair_in,
@@ -755,15 +752,20 @@ __global__ void __launch_bounds__(128, 4) k_shade_composite(DevVolume V, DevCame
     }
     float rho;
     const int mode = BATCH ? B.mode : V.mode;
+    // single frames: the launch picks the instance of the volume's mode, so
+    // CP decides at compile time; batches carry each block's mode
+    const bool cp_mode = BATCH ? mode == IVV_SCALAR_CP : CP;
     if (!STATS && !BATCH && CP) {
       rho = eval_rho_cp<P>(V, B, p);
     } else {
       float phi[3], J[3][3], rc;
-      if (mode == IVV_SCALAR_CP)
+      if (cp_mode)
         eval_block<P, float, true>(V, B, p, phi, J, rc);
       else
         eval_block<P, float, false, true>(V, B, p, phi, J, rc);
-      if (mode == IVV_SCALAR_CP) {
+      if constexpr (VM) {
+        rho = scalar_at<P, float>(V, B, IVV_SCALAR_VONMISES, p, J, rc);
+      } else if (cp_mode) {
         rho = rc;
       } else {
         const float det = det_cofactor(J);
@@ -819,26 +821,32 @@ void launch_shade_composite_p(const DevVolume& V, const DevCamera<float>& cam, c
                               const int* active, const int* n_active, int* queue_head, const int* off, int npix,
                               float ds, float tail_eps, const SplitArgs& sa, float4* out, bool stats, DevStats* st,
                               int num_sms, cudaStream_t s) {
-  static int per_sm[4] = {-1, -1, -1, -1};
+  static int per_sm[6] = {-1, -1, -1, -1, -1, -1};
   const bool cp = V.mode == IVV_SCALAR_CP;
-  const int v = (stats ? 2 : 0) + (cp ? 1 : 0);
+  const bool vm = V.mode == IVV_SCALAR_VONMISES;
+  const int v = vm ? 4 + (stats ? 1 : 0) : (stats ? 2 : 0) + (cp ? 1 : 0);
   if (per_sm[v] < 0) {
     int n = 1;
     if (v == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, false, false>, 128, 0);
     if (v == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, false, true>, 128, 0);
     if (v == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, true, false>, 128, 0);
     if (v == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, true, true>, 128, 0);
+    if (v == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, false, false, false, true>, 128, 0);
+    if (v == 5)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shade_composite<P, true, false, false, true>, 128, 0);
     per_sm[v] = n < 1 ? 1 : n;
   }
   int grid = num_sms * per_sm[v];                   // persistent: the lanes refill from the queue
   const int useful = (npix + 127) / 128;
   grid = grid < useful ? grid : (useful > 0 ? useful : 1);
-#define IVV_SHADE(SS, CC)                                                                                   \
-  launch_pdl(k_shade_composite<P, SS, CC>, dim3(grid), dim3(128), s, V, cam, tf, K, early, BatchArgs{},              \
+#define IVV_SHADE(SS, CC, VV)                                                                               \
+  launch_pdl(k_shade_composite<P, SS, CC, false, VV>, dim3(grid), dim3(128), s, V, cam, tf, K, early, BatchArgs{},   \
              (const int*)nullptr, pin, pout, pblk, pcnt, active, n_active, queue_head, off, npix, ds, tail_eps, sa.cap, \
              sa.sp, out, st)
-  if (stats) { if (cp) IVV_SHADE(true, true); else IVV_SHADE(true, false); }
-  else { if (cp) IVV_SHADE(false, true); else IVV_SHADE(false, false); }
+  if (vm) { if (stats) IVV_SHADE(true, false, true); else IVV_SHADE(false, false, true); }
+  else if (stats) { if (cp) IVV_SHADE(true, true, false); else IVV_SHADE(true, false, false); }
+  else { if (cp) IVV_SHADE(false, true, false); else IVV_SHADE(false, false, false); }
 #undef IVV_SHADE
 }
 

@@ -274,23 +274,7 @@ __global__ void __launch_bounds__(128, 3) k5_irk1(DevVolume V, DevCamera<float> 
     if (it == 0) {
       // x is the sample point p_j: its scalar, and the interval ending there
       float rho;
-      if (V.mode == IVV_SCALAR_CP) {
-        rho = rc;
-      } else {
-        const float det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) +
-                          J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
-                          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-        if (V.mode == IVV_SCALAR_DETJ) {
-          rho = det;
-        } else {
-          float f = 0.f;
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) f += J[a][b] * J[a][b];
-          rho = det / sqrtf(f);
-        }
-      }
+      rho = scalar_at<P, float>(V, B, V.mode, x, J, rc);
       if (j > 0) {
         const float s1 = (j <= nsamp) ? (float)j * ds : L;
         composite_interval<float>(s_r, s_rgba, s_seg, tf, args.K, rho_prev, rho, s1 - (float)(j - 1) * ds, acc);

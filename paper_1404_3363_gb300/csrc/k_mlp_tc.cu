@@ -336,15 +336,45 @@ __global__ void __launch_bounds__(kTcRows, 8) k_mlp_infer_tc(const __half* __res
 
 // Counting sort of list entries by block (the guess list of the RF method):
 // perm lists the entries block after block, so the inference's tiles hold
-// one block each and run one pass.  Atomics are aggregated per warp over the
-// lanes of one block.  hist: [n_blocks + 1] ints (zeroed by the caller).
-__global__ void k_sort_hist(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int* __restrict__ hist) {
-  const int n = *n_ptr;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+// one block each and run one pass.  Each CTA takes a contiguous range of the
+// list and counts it in shared memory (atomics aggregated per warp over the
+// lanes of one block); only its per-block totals go to global memory, so a
+// block's global counter sees one atomic per CTA instead of one per warp.
+// hist: [n_blocks + 1] ints (zeroed by the caller).  Volumes with more
+// blocks than kSortSharedBlocks count with global atomics directly.
+constexpr int kSortSharedBlocks = 4096;
+
+__device__ __forceinline__ void cta_range(int n, int& i0, int& i1) {
+  const int per = (((n + (int)gridDim.x - 1) / (int)gridDim.x) + 31) & ~31;
+  i0 = min(n, (int)blockIdx.x * per);
+  i1 = min(n, i0 + per);
+}
+
+// Warp-aggregated count of the entries [i0, i1) into cnt (shared or global).
+__device__ __forceinline__ void count_range(const int* __restrict__ gblk, int i0, int i1, int* cnt) {
+  for (int base = i0; base < i1; base += blockDim.x) {
     const int i = base + (int)threadIdx.x;
-    const int b = i < n ? __ldg(gblk + i) : -1;
+    const int b = i < i1 ? __ldg(gblk + i) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
-    if (b >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(hist + b, __popc(peers));
+    if (b >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(cnt + b, __popc(peers));
+  }
+}
+
+template <bool SHARED>
+__global__ void k_sort_hist(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int n_blocks,
+                            int* __restrict__ hist) {
+  extern __shared__ int s_cnt[];
+  int i0, i1;
+  cta_range(*n_ptr, i0, i1);
+  if constexpr (SHARED) {
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    count_range(gblk, i0, i1, s_cnt);
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x)
+      if (s_cnt[b]) atomicAdd(hist + b, s_cnt[b]);
+  } else {
+    count_range(gblk, i0, i1, hist);
   }
 }
 
@@ -375,17 +405,34 @@ __global__ void k_sort_scan(int* __restrict__ hist, int n_blocks) {
   }
 }
 
-__global__ void k_sort_scatter(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int* __restrict__ cursor,
-                               int* __restrict__ perm) {
-  const int n = *n_ptr;
+// cursor: the scanned histogram, advanced as entries are placed.  SHARED:
+// the CTA counts its range again, claims one run per block from the global
+// cursor, then places its entries inside its runs (shared running offsets).
+template <bool SHARED>
+__global__ void k_sort_scatter(const int* __restrict__ gblk, const int* __restrict__ n_ptr, int n_blocks,
+                               int* __restrict__ cursor, int* __restrict__ perm) {
+  extern __shared__ int s_dyn[];
   const int lane = threadIdx.x & 31;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  int i0, i1;
+  cta_range(*n_ptr, i0, i1);
+  int* off = cursor;
+  if constexpr (SHARED) {
+    int* s_cnt = s_dyn;
+    off = s_dyn + n_blocks;
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    count_range(gblk, i0, i1, s_cnt);
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) off[b] = s_cnt[b] ? atomicAdd(cursor + b, s_cnt[b]) : 0;
+    __syncthreads();
+  }
+  for (int base = i0; base < i1; base += blockDim.x) {
     const int i = base + (int)threadIdx.x;
-    const int b = i < n ? __ldg(gblk + i) : -1;
+    const int b = i < i1 ? __ldg(gblk + i) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(peers) - 1;
     int at = 0;
-    if (b >= 0 && lane == leader) at = atomicAdd(cursor + b, __popc(peers));
+    if (b >= 0 && lane == leader) at = atomicAdd(off + b, __popc(peers));
     at = __shfl_sync(0xffffffffu, at, leader);
     if (b >= 0) perm[at + __popc(peers & ((1u << lane) - 1u))] = i;
   }
@@ -396,9 +443,16 @@ __global__ void k_sort_scatter(const int* __restrict__ gblk, const int* __restri
 void launch_block_sort(const int* gblk, const int* n_ptr, int n_blocks, int* hist, int* perm, int num_sms,
                        cudaStream_t s) {
   cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)(n_blocks + 1), s);
-  k_sort_hist<<<num_sms * 8, 256, 0, s>>>(gblk, n_ptr, hist);
-  k_sort_scan<<<1, 1024, 0, s>>>(hist, n_blocks);
-  k_sort_scatter<<<num_sms * 8, 256, 0, s>>>(gblk, n_ptr, hist, perm);
+  const int grid = num_sms * 8;
+  if (n_blocks <= kSortSharedBlocks) {
+    k_sort_hist<true><<<grid, 256, sizeof(int) * n_blocks, s>>>(gblk, n_ptr, n_blocks, hist);
+    k_sort_scan<<<1, 1024, 0, s>>>(hist, n_blocks);
+    k_sort_scatter<true><<<grid, 256, 2 * sizeof(int) * n_blocks, s>>>(gblk, n_ptr, n_blocks, hist, perm);
+  } else {
+    k_sort_hist<false><<<grid, 256, 0, s>>>(gblk, n_ptr, n_blocks, hist);
+    k_sort_scan<<<1, 1024, 0, s>>>(hist, n_blocks);
+    k_sort_scatter<false><<<grid, 256, 0, s>>>(gblk, n_ptr, n_blocks, hist, perm);
+  }
 }
 
 void launch_mlp_infer(const __half* theta16, const MlpNorm* norms, const float4* g, const int* gblk, const int* n_ptr,

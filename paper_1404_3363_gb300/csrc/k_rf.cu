@@ -281,18 +281,7 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
     if (nF > tol) ++c_fail;
     if (p_out) p_out[i] = make_float4(p[0], p[1], p[2], nF);
     if (it_out) it_out[i] = nF <= tol ? it : -1 - it;
-    float rho = rc;
-    if (V.mode != IVV_SCALAR_CP) {
-      rho = det3<float>(J);
-      if (V.mode == IVV_SCALAR_QUALITY) {
-        float f = 0.f;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) f += J[r][c] * J[r][c];
-        rho /= sqrtf(f);
-      }
-    }
+    const float rho = scalar_at<P, float>(V, B, V.mode, p, J, rc);
     if (srho) srho[i] = rho;
   }
   if (STATS) {

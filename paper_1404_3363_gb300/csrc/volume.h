@@ -24,6 +24,11 @@ struct ivv_volume {
   float4* d_org32 = nullptr;
   float* d_rho32 = nullptr;
   ivv::Dbl4* d_org64 = nullptr;
+  // IVV_SCALAR_VONMISES: displacement elements and origins (null otherwise)
+  float4* d_disp32 = nullptr;
+  float4* d_dorg32 = nullptr;
+  ivv::Dbl4* d_disp64 = nullptr;
+  ivv::Dbl4* d_dorg64 = nullptr;
   float4* d_face32 = nullptr;
   ivv::Dbl4* d_face64 = nullptr;
   ivv::FaceMeta* d_faces = nullptr;

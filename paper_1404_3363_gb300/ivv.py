@@ -41,7 +41,7 @@ class IvvError(RuntimeError):
 
 class BlockDesc(C.Structure):
     _fields_ = [("degree", C.c_int * 3), ("n_cp", C.c_int * 3), ("knots", c_double_p * 3),
-                ("geom_cp", c_double_p), ("scalar_cp", c_double_p)]
+                ("geom_cp", c_double_p), ("scalar_cp", c_double_p), ("disp_cp", c_double_p)]
 
 
 class Camera(C.Structure):
@@ -227,7 +227,8 @@ def block_descs(blocks):
         kn = [_f64(k) for k in b.knots]
         g = _f64(b.geom_cp)
         s = _f64(b.scalar_cp) if b.scalar_cp is not None else None
-        keep += kn + [g] + ([s] if s is not None else [])
+        u = _f64(b.disp_cp) if getattr(b, "disp_cp", None) is not None else None
+        keep += kn + [g] + [x for x in (s, u) if x is not None]
         nu, nv, nw = b.n_cp
         for d in range(3):
             arr[bi].degree[d] = int(b.degree[d])
@@ -235,6 +236,7 @@ def block_descs(blocks):
         arr[bi].n_cp[0], arr[bi].n_cp[1], arr[bi].n_cp[2] = nu, nv, nw
         arr[bi].geom_cp = g.ctypes.data_as(c_double_p)
         arr[bi].scalar_cp = s.ctypes.data_as(c_double_p) if s is not None else c_double_p()
+        arr[bi].disp_cp = u.ctypes.data_as(c_double_p) if u is not None else c_double_p()
     return arr, keep
 
 

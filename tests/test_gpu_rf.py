@@ -96,3 +96,27 @@ def test_learned_guess_gains_over_plain_newton(ivv, cfg):
         res[guess] = (its[ok].mean(), e0.elapsed_time(e1))
     print("workload", cfg, "Newton iterations / ms  centre:", res[ivv.GUESS_CENTER], " learned:", res[ivv.GUESS_MLP])
     assert res[ivv.GUESS_MLP][0] < 0.75 * res[ivv.GUESS_CENTER][0], res
+
+
+@pytest.mark.parametrize("cfg,prec,guess", [(1, 0, 2), (2, 0, 2), (2, 1, 1)],
+                         ids=["bar-chord-fp32", "beam-chord-fp32", "beam-learned-mixed"])
+def test_full_frame_1080p_every_pixel(ivv, cfg, prec, guess):
+    """The benchmark's root-finding frames at 1920x1080 (rf_tol 1e-3 of the
+    pixel half width): the chord guess in FP32, and on the beam the learned
+    guess (trained as the benchmark trains it) with mixed precision; every
+    pixel against the oracle."""
+    sc = scenes.config(cfg)
+    sc.params.precision = prec
+    sc.params.rf_tol = 1e-3
+    vol = ivv.volume_for(sc)
+    if guess == 1:
+        vol.train_guess(samples_per_block=1 << 20, epochs=8, batch=4096, lr=3e-3, seed=1)
+    vol.reset_stats()
+    img = _render(ivv, vol, sc, 1, guess, flags=ivv.FLAG_STATS)
+    st = vol.stats()
+    assert (img[..., 3] > 0).sum() > 10_000
+    assert st["rf_unconverged"] <= 1e-4 * st["samples"], (st["rf_unconverged"], st["samples"])
+    ref = oracle.render(sc)
+    err = np.abs(img - ref)
+    assert err.max() <= TOL_RGBA, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    vol.close()

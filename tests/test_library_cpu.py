@@ -2,6 +2,8 @@
 function include/ivv.h declares; its host preparation (knot insertion,
 degree elevation, face extraction, validation) reproduces the oracle's
 Cox-de Boor evaluation; invalid descriptions are rejected with statuses."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -37,6 +39,27 @@ def test_bezier_extraction_matches_oracle(lib, cfg):
         np.testing.assert_allclose(f1, f2, atol=1e-12)
         np.testing.assert_allclose(J1, J2, atol=1e-10 * np.abs(J2).max())
         np.testing.assert_allclose(r1, r2, atol=1e-12 * max(1.0, np.abs(r2).max()))
+
+
+def test_von_mises_host_path_matches_oracle(lib):
+    """The library's FP64 host path for the von Mises scalar (§6.2): the
+    displacement carried through the Bezier extraction beside the geometry,
+    rho from J_u J_phi^-1, against the oracle's QR solve of the paper's
+    transposed system on the loaded beam."""
+    sc = scenes.bent_beam(width=8, height=8, displacement=True)
+    assert sc.scalar_mode == scenes.SCALAR_VONMISES
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    P = np.random.default_rng(43).uniform(0, 1, (200, 3))
+    for b in (0, 6, 15):
+        f1, J1, r1 = ivv.host_eval(sc.blocks, sc.scalar_mode, b, P)
+        f2, J2, r2 = ov.eval(b, P)
+        np.testing.assert_allclose(f1, f2, atol=1e-12)
+        assert r2.max() > 1e-4
+        np.testing.assert_allclose(r1, r2, rtol=1e-9, atol=1e-13)
+    no_disp = [dataclasses.replace(b, disp_cp=None) for b in sc.blocks]
+    with pytest.raises(ivv.IvvError) as e:
+        ivv.host_eval(no_disp, scenes.SCALAR_VONMISES, 0, P[:1])
+    assert e.value.status == 1
 
 
 def test_degree_elevation_and_mixed_degrees(lib):
@@ -111,7 +134,7 @@ def _header_struct_fields(name):
 
 @pytest.mark.parametrize("cname,pyname", [("ivv_stats", "Stats"), ("ivv_render_params", "RenderParams"),
                                           ("ivv_camera", "Camera"), ("ivv_request", "Request"),
-                                          ("ivv_batch_tuning", "BatchTuning")])
+                                          ("ivv_batch_tuning", "BatchTuning"), ("ivv_block_desc", "BlockDesc")])
 def test_binding_structs_match_header(cname, pyname):
     """ctypes mirrors of the header's structs: same fields in the same order."""
     fields = [n for n, _ in getattr(ivv, pyname)._fields_]
