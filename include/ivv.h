@@ -287,10 +287,9 @@ ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_p
                       size_t workspace_bytes, void* stream);
 
 /* Render a small window without allocating device memory.  For callers that
- * cannot call cudaMalloc at render time: code recording a CUDA graph (device
- * allocation cannot be captured), real-time or plug-in hosts whose memory is
- * owned by a pool or budget of their own, and threads that must not risk the
- * implicit device synchronisation an allocation may cause.  The paper has no
+ * cannot call cudaMalloc at render time: real-time or plug-in hosts whose
+ * memory is owned by a pool or budget of their own, and threads that must not
+ * risk the implicit device synchronisation an allocation may cause.  The paper has no
  * counterpart; this is a deployment variant of ivv_render.
  * The per-frame workspace lives in a file-scope device array of 12 MiB
  * (IVV_NOALLOC_SCRATCH_BYTES), enough for a 64 x 64 window at any precision
@@ -303,8 +302,8 @@ ivv_status ivv_render(ivv_volume* vol, const ivv_camera* cam, const ivv_render_p
  * The volume (created earlier) and out_rgba (device, caller-owned,
  * [height][width][4] float32) are the caller's.  Every call looks up the
  * array's address in the current device's context (cudaGetSymbolAddress);
- * the first call on a device may load the library's device code, so make it
- * before any stream capture.  All calls share the one array, whose contents
+ * the first call on a device may load the library's device code.  All calls
+ * share the one array, whose contents
  * persist between calls (everything a frame needs zeroed is cleared by the
  * frame itself), so calls that overlap on the GPU -- on different streams or
  * from different threads -- race: serialise them. */

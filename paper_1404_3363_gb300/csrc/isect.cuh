@@ -704,6 +704,33 @@ IVV_HD int pair_fragments(int n, const R* t, const unsigned* m, const R (*pp)[3]
       }
     }
   }
+  // a lone hit on a block edge (two or three parameter coordinates on the
+  // block boundary) next to a hit of the same block and the same facing:
+  // the ray touches the edge within the root tolerance on one face while
+  // the other face's copy of the touch falls outside it, so the touch has no
+  // partner of the opposite facing.  Entry and exit alternate along a ray
+  // through a block (its boundary is closed), so of two consecutive hits of
+  // one block with the same facing the edge hit is the spurious one, and a
+  // block's first hit cannot be an exit: such edge hits are dropped before
+  // Alg. 2.
+  for (int i = 0; i < n; ++i) {
+    if ((used >> i) & 1u) continue;
+    const unsigned blk = m[ord[i]] >> 4;
+    int prev = -1;
+    for (int j = i - 1; j >= 0; --j)
+      if (!((used >> j) & 1u) && (m[ord[j]] >> 4) == blk) { prev = j; break; }
+    const bool front = m[ord[i]] & 1u;
+    if (prev < 0) {
+      if (!front && on_bound(pp[ord[i]]) >= 2) used |= 1u << i;
+      continue;
+    }
+    if (((m[ord[prev]] & 1u) != 0) != front) continue;
+    const bool edge_i = on_bound(pp[ord[i]]) >= 2, edge_p = on_bound(pp[ord[prev]]) >= 2;
+    if (edge_p && !edge_i)
+      used |= 1u << prev;
+    else if (edge_i && !edge_p)
+      used |= 1u << i;
+  }
   int np = 0;
   for (;;) {
     int back = -1;

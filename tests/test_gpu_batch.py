@@ -336,3 +336,26 @@ def test_full_batched_workload_sampled(ivv, pool):
             ref = oracle.render(sc, orc[q.volume], window=(x, x + 1, y, y + 1), n_threads=1)[0, 0]
             worst = max(worst, np.abs(img[y, x].astype(np.float64) - ref).max())
     assert worst <= TOL_RGBA, worst
+
+
+def test_full_batched_workload_middle_rows(ivv, pool):
+    """The 64-request workload at its own sizes: the middle covered row of
+    every request, every pixel of it, against the oracle (silhouettes and
+    grazing rays included, where random pixels rarely land)."""
+    vols, reqs, gpu, orc = pool
+    b = _batch(ivv, gpu, reqs)
+    outs = b.render()
+    torch.cuda.synchronize()
+    worst, rows = 0.0, 0
+    for i, (q, out) in enumerate(zip(reqs, outs)):
+        img = out.cpu().numpy()
+        cov = np.flatnonzero(img[..., 3].max(axis=1) > 0)
+        if not len(cov):
+            continue
+        y = int(cov[len(cov) // 2])
+        ref = oracle.render(_scene(vols, q), orc[q.volume], window=(0, q.width, y, y + 1))[0]
+        err = float(np.abs(img[y].astype(np.float64) - ref).max())
+        assert err <= TOL_RGBA, (i, q.volume, q.width, y, err)
+        worst = max(worst, err)
+        rows += 1
+    assert rows > 50

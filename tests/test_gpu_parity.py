@@ -97,6 +97,23 @@ def test_full_frame_1080p_every_pixel(ivv, cfg, prec):
     assert err.max() <= TOL_RGBA, (err.max(), np.unravel_index(err.argmax(), err.shape))
 
 
+def test_full_frame_cube_1024_silhouette_sliver(ivv):
+    """The twisted cube at 1024x1024 from a camera whose view grazes the edge
+    where the top face bends over a side face (a sliver of the block a pixel
+    wide): every pixel against the oracle."""
+    import dataclasses
+    vols, reqs = scenes.batch_requests()
+    q = reqs[37]
+    sc = dataclasses.replace(vols[q.volume], camera=q.camera, tf=q.tf, width=q.width, height=q.height,
+                             params=scenes.RenderParams())
+    for prec in (0, 1):
+        sc.params.precision = prec
+        vol, img = _gpu_image(ivv, sc)
+        ref = oracle.render(sc)
+        err = np.abs(img - ref)
+        assert err.max() <= TOL_RGBA, (prec, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
 @pytest.mark.parametrize("cfg,prec", [(1, 0), (1, 1)])
 def test_full_frame_entry_exit_points(ivv, cfg, prec):
     """Entry/exit parameters of every pixel of the 1080p bar against the
@@ -152,7 +169,9 @@ def test_full_frame_entry_exit_points(ivv, cfg, prec):
 def test_full_size_4k_backstep_every_8th_row(ivv, prec):
     """3840x2160 backward-facing step (the frame whose sample list is sized
     from the exact scanned total, read back once): every pixel of every 8th
-    row against the oracle, and the split path's counters."""
+    row against the oracle -- the rows the benchmark checks, which cross the
+    shear layer where the integration tolerance decides the error -- and the
+    split path's counters."""
     sc = scenes.config(4)
     sc.params.precision = prec
     vol, img = _gpu_image(ivv, sc)
@@ -163,7 +182,7 @@ def test_full_size_4k_backstep_every_8th_row(ivv, prec):
     assert st["abuf_overflow"] == 0 and st["pair_overflow"] == 0 and st["step_cap"] == 0
     ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
     worst = 0.0
-    for y in range(3, sc.height, 8):
+    for y in range(4, sc.height, 8):
         ref = oracle.render(sc, ov, window=(0, sc.width, y, y + 1))[0]
         worst = max(worst, np.abs(img[y] - ref).max())
     assert worst <= TOL_RGBA, worst

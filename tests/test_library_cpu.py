@@ -227,3 +227,32 @@ def test_host_stage12_code_matches_oracle_pairs(lib, cfg, size, prec, tol):
     graze = 0.2 if prec == 0 else -1.0
     checked, worst = compare_pairs(ov, sc, cnt, pairs, blk, tol, graze_cos=graze)
     assert checked > 0.02 * sc.width * sc.height
+
+
+def test_lone_edge_touch_is_not_an_entry(lib):
+    """A ray that passes a block edge within the FP32 root tolerance: one
+    face accepts the touch, the neighbouring face's copy falls outside it.
+    Of two consecutive hits of one block with the same facing the edge hit
+    is dropped before Alg. 2, so the pixels around the sliver where the
+    twisted cube's top face bends over its side face pair as the oracle's
+    exact intersections do (window of the 1024^2 request whose middle row
+    showed the lone touch)."""
+    vols, reqs = scenes.batch_requests()
+    q = reqs[37]
+    sc = dataclasses.replace(vols[q.volume], camera=q.camera, tf=q.tf, width=q.width, height=q.height,
+                             params=scenes.RenderParams())
+    x0, y0, w, h = 263, 484, 16, 16
+    cnt, pairs, blk = ivv.host_render_pairs(sc.blocks, sc.scalar_mode, sc.camera, sc.params, w, h,
+                                            window=(x0, y0, sc.width, sc.height))
+    ov = oracle.OracleVolume(sc.blocks, sc.scalar_mode)
+    touched = 0
+    for j in range(h):
+        for i in range(w):
+            pix = j * w + i
+            rp, um = ov.pixel_pairs(sc.camera, sc.width, sc.height, x0 + i, y0 + j)
+            assert cnt[pix] == len(rp), (x0 + i, y0 + j, cnt[pix], len(rp))
+            for k, p in enumerate(rp):
+                assert abs(pairs[k, pix, 3] - p.t_in) <= 2e-4 and abs(pairs[k, pix, 7] - p.t_out) <= 2e-4, \
+                    (x0 + i, y0 + j, k, pairs[k, pix, [3, 7]], p.t_in, p.t_out)
+            touched += len(rp) > 1
+    assert touched > 10, "the window crosses the sliver"

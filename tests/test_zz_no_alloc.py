@@ -1,9 +1,8 @@
 """ivv_render_noalloc: rendering a small window with no device allocation.
 
-Some callers cannot allocate device memory while they render: a CUDA graph
-being recorded (allocation cannot be captured), hosts whose GPU memory is
-owned by their own pool or budget, and real-time threads that must not risk
-the synchronisation an allocation may bring.  The allocation-free entry point
+Some callers cannot allocate device memory while they render: hosts whose
+GPU memory is owned by their own pool or budget, and real-time threads that
+must not risk the synchronisation an allocation may bring.  The allocation-free entry point
 keeps the frame's workspace in a fixed device array inside the library; its
 image must equal the one ivv_render produces with a caller workspace, on
 consecutive calls (the array keeps the previous call's contents, so anything
