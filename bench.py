@@ -75,29 +75,28 @@ LEARNED_WORKLOADS = {
                                "(none on this view: the guess network is idle)"),
 }
 
-# Algorithmic FP32 flops per unit for Bezier degree P (N = P + 1 control
-# points per direction; the cubic figures in brackets).
-# integrator (K5 / K5t)
-# Kernels of this library that one frame launches.  The split integration
-# (FP32 / MIXED with BS3(2)): K0, K2a, K2b, K2c (warp and thread forms), K4,
-# the sample counts, three scan passes, K5t and the shading pass; the fused
-# FP64 integrator and the fixed-step / implicit ones replace the last six by
-# one kernel.  A batch replays the same stages for every request at once,
-# plus the overflow list and its fused integrator.
-def kernels_per_frame(prec, rk_method, method=0, guess=0):
+
+def kernels_per_frame(prec, rk_method, method=0, guess=0, n_blocks=1):
     """Kernels one frame launches: stages 1-2 (K0, K2a, K2b, both K2c forms,
-    K4) and stage 3 -- the split integration (sample counts, three scan
-    passes, K5t, shading), one fused integrator (FP64, fixed-step, implicit
-    Euler), or the RF chain (counts, three scan passes, expansion, Newton,
-    compositing, plus the guess network's inference with the learned guess)."""
+    K4; mixed precision adds the K2p polish of grazing hits) and stage 3 --
+    the split integration (sample counts, three scan passes, K5t, shading),
+    one fused integrator (FP64, fixed-step, implicit Euler), or the RF chain
+    (counts, three scan passes, expansion, Newton, compositing, plus the
+    guess network's inference with the learned guess, after a three-kernel
+    block sort for volumes of 8 blocks or more)."""
+    n = 6 + (1 if prec == 1 else 0)
     if method == 1:
-        return 6 + 7 + (1 if guess == 1 else 0)
-    return 12 if prec != 2 and not rk_method else 7
+        return n + 7 + ((1 + (3 if n_blocks >= 8 else 0)) if guess == 1 else 0)
+    return n + (6 if prec != 2 and not rk_method else 1)
 
 
+# A batch replays the same stages for every request at once, plus the
+# overflow list and its fused integrator.
 BATCH_KERNELS = 14
 
 
+# Algorithmic FP32 flops per unit for Bezier degree P (N = P + 1 control
+# points per direction; the cubic figures in brackets).
 def flop_model(P):
     N = P + 1
     return {
@@ -629,7 +628,8 @@ def run_ours(args):
                        if world > 1 else "single"},
             "stages_ms": {k: v / args.steps for k, v in stage_sum.items()},
             "wall_s_timed_loop": t_wall,
-            "gpu_launches": kernels_per_frame(prec, args.rk_method, sc.params.method, sc.params.use_mlp_guess)
+            "gpu_launches": kernels_per_frame(prec, args.rk_method, sc.params.method, sc.params.use_mlp_guess,
+                                              len(sc.blocks))
                             * args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "ms_per_frame": e2e_ms,
