@@ -284,13 +284,26 @@ struct SplitBox {
   int depth;
 };
 
+constexpr int kMultiStarts = 5;     // Newton starts on an uncertified box of the deepest level
+constexpr int kDeepCap = 32;        // such boxes per item solved after the levels, a start per lane
+
 template <typename R>
 struct SplitSmem {
   SplitBox<R> box[2][kBfsCap];
+  SplitBox<R> deep[kDeepCap];
   R ra[kRootCap], rb[kRootCap];
   int n[2];
   int nr;
+  int ndeep;
 };
+
+// Start s of the multi-start Newton on an uncertified box: its centre, then
+// the centres of its four quarters.
+template <typename R>
+__device__ __forceinline__ void multi_start(int s0, R& a, R& b) {
+  a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
+  b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
+}
 
 // Root (a, b) local to box nd: kept if inside the box (tolerance scaled to
 // its size) and the patch; returns false if outside the box.  in_box =
@@ -331,6 +344,7 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     sm.n[0] = G * G;
     sm.n[1] = 0;
     sm.nr = 0;
+    sm.ndeep = 0;
   }
   __syncwarp();
   int cur = 0;
@@ -350,11 +364,19 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
         split = !(newton2<P, R>(q, a, b, iters, kBoxNewtonLo<R>(), kBoxNewtonHi<R>(), kBoxNewtonIters) &&
                   gather_root<R>(nd, a, b, sm));
       } else if (nd.depth >= kSplitDepth) {
+        // the multi-start Newton of an uncertified deepest box runs after
+        // the levels with one start per lane (its starts are independent);
+        // boxes beyond the list run their starts here
+        const int at = atomicAdd(&sm.ndeep, 1);
+        if (at < kDeepCap) {
+          sm.deep[at] = nd;
+        } else {
 #pragma unroll 1
-        for (int s0 = 0; s0 < 5; ++s0) {
-          R a = s0 == 0 ? R(0.5) : ((s0 & 1) ? R(0.25) : R(0.75));
-          R b = s0 == 0 ? R(0.5) : ((s0 & 2) ? R(0.25) : R(0.75));
-          if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm, false);
+          for (int s0 = 0; s0 < kMultiStarts; ++s0) {
+            R a, b;
+            multi_start<R>(s0, a, b);
+            if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm, false);
+          }
         }
         split = false;
       }
@@ -389,6 +411,18 @@ __device__ __forceinline__ int split_roots_warp(const Patch2<P, R>& q0, R pad, S
     __syncwarp();
     cur ^= 1;
   }
+  // the deepest uncertified boxes: every (box, start) pair on its own lane
+  const int nd_deep = min(sm.ndeep, kDeepCap);
+#pragma unroll 1
+  for (int k = lane; k < nd_deep * kMultiStarts; k += 32) {
+    const SplitBox<R> nd = sm.deep[k / kMultiStarts];
+    Patch2<P, R> q;
+    sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
+    R a, b;
+    multi_start<R>(k % kMultiStarts, a, b);
+    if (newton2<P, R>(q, a, b, iters)) gather_root<R>(nd, a, b, sm, false);
+  }
+  __syncwarp();
   // merge duplicates (lane 0), keep at most kMaxPatchRoots
   if (lane == 0) {
     const int m = min(sm.nr, kRootCap);
