@@ -77,17 +77,19 @@ LEARNED_WORKLOADS = {
 
 
 def kernels_per_frame(prec, rk_method, method=0, guess=0, n_blocks=1):
-    """Kernels one frame launches: stages 1-2 (K0, K2a, K2b, both K2c forms,
-    K4; mixed precision adds the K2p polish of grazing hits) and stage 3 --
-    the split integration (sample counts, three scan passes, K5t, shading),
-    one fused integrator (FP64, fixed-step, implicit Euler), or the RF chain
-    (counts, three scan passes, expansion, Newton, compositing, plus the
-    guess network's inference with the learned guess, after a three-kernel
-    block sort for volumes of 8 blocks or more)."""
+    """Kernels one frame of the benchmark's workloads launches: stages 1-2
+    (K0, K2a, K2b, both K2c forms, K4, which also counts the sample lists;
+    mixed precision adds the K2p polish of grazing hits) and stage 3 -- the
+    split integration (K5t, shading), one fused integrator (FP64, fixed-step,
+    implicit Euler), or the RF chain (expansion, Newton, compositing, plus
+    the guess network's inference with the learned guess, after a
+    three-kernel block sort for volumes of 8 blocks or more).  Frames with
+    cutting or near planes or singular faces count their samples with four
+    more kernels after the fix-up solves; none of the workloads has them."""
     n = 6 + (1 if prec == 1 else 0)
     if method == 1:
-        return n + 7 + ((1 + (3 if n_blocks >= 8 else 0)) if guess == 1 else 0)
-    return n + (6 if prec != 2 and not rk_method else 1)
+        return n + 3 + ((1 + (3 if n_blocks >= 8 else 0)) if guess == 1 else 0)
+    return n + (2 if prec != 2 and not rk_method else 1)
 
 
 # A batch replays the same stages for every request at once, plus the

@@ -338,8 +338,11 @@ ivv_status ensure_own(void** buf, size_t* have, size_t need, cudaStream_t s) {
 // Stages 1-2 into the workspace.  out_zero receives zero pixels for rays
 // without pairs (may be NULL).
 template <typename R>
+// count (optional): K4 also counts the pixels' samples into the sample
+// lists when no fix-up solve moves a pair end after it; *counted tells.
 ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_params& p, char* ws, const WsLayout& L,
-                             int max_pairs, float4* out_zero, cudaStream_t s) {
+                             int max_pairs, float4* out_zero, cudaStream_t s, const ivv::SampleCount* count = nullptr,
+                             bool* counted = nullptr) {
   typedef typename ivv::Vec4T<R>::type V4;
   ivv::DevVolume V = dev_volume(v);
   const int npix = F.w * F.h;
@@ -379,10 +382,13 @@ ivv_status run_surface_pairs(ivv_volume* v, const Frame& F, const ivv_render_par
   for (int k = 0; k < p.n_cut_planes; ++k)
     for (int c = 0; c < 4; ++c) clip.cut[k][c] = (R)p.cut_planes[k][c];
   clip.cam = dev_camera<R>(F);
+  const bool count_here = count != nullptr && sizeof(R) == 4 && !clip.on && !v->hv.any_singular;
+  if (counted) *counted = count_here;
   ivv::launch_pair<R>(V, F.w, npix, (float)v->hv.diag, (const V4*)(ws + L.frag_tp), (const unsigned*)(ws + L.frag_meta),
                       (const int*)(ws + L.frag_count), (V4*)(ws + L.pair_in), (V4*)(ws + L.pair_out),
                       (int*)(ws + L.pair_block), (int*)(ws + L.pair_count), max_pairs, (int*)(ws + L.active),
-                      (int*)(ws + L.counters), out_zero, clip, sw.tile_flag, v->d_stats, s);
+                      (int*)(ws + L.counters), out_zero, clip, sw.tile_flag, v->d_stats, s,
+                      count_here ? count : nullptr);
   // fix-up solves of stage 2: ends moved onto cutting or near-clip planes
   // (§5.5) and entries with a singular Jacobian (§5.4), the entries without
   // chord context from the learned guess when it is asked for
@@ -481,23 +487,33 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
   if (p.use_mlp_guess == IVV_GUESS_MLP && !v->guess_ready)
     return fail(IVV_ERR_INVALID_ARG, "IVV_GUESS_MLP needs ivv_train_guess or ivv_set_guess_weights first");
   if (p.method == IVV_METHOD_RF) {
-    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
+    int* counters = (int*)(ws + L.counters);
+    const float tail_eps = (float)(1e-12 * v->hv.diag);
+    // sample lists counted by K4 where no fix-up follows it (their arrays in
+    // the stage-1 item list, dead after K2c), else by the count and scan
+    // kernels over the fragment lists, dead after stage 2
+    ivv::SampleCount sc{(float)p.ds, tail_eps, (int*)(ws + L.items), (int*)(ws + L.items) + npix, counters + 2};
+    bool counted = false;
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s, &sc, &counted);
     if (st != IVV_OK) return st;
     const float4* pin = (const float4*)(ws + L.pair_in);
     const float4* pout = (const float4*)(ws + L.pair_out);
     const int* pblk = (const int*)(ws + L.pair_block);
     const int* pcnt = (const int*)(ws + L.pair_count);
     const int* act = (const int*)(ws + L.active);
-    int* counters = (int*)(ws + L.counters);
-    int* cnt = (int*)(ws + L.frag_count);             // fragment lists are dead after stage 2
-    int* off = (int*)(ws + L.frag_meta);
-    int* sums = off + npix;
-    const float tail_eps = (float)(1e-12 * v->hv.diag);
-    ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms, s);
-    ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
-    int total = 0;
-    IVV_CUDA(cudaMemcpyAsync(&total, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* cnt = counted ? sc.cnt : (int*)(ws + L.frag_count);
+    int* off = counted ? sc.off : (int*)(ws + L.frag_meta);
+    int* sums = (int*)(ws + L.frag_meta) + npix;
+    if (!counted) {
+      ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms,
+                           s);
+      ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+    }
+    int totals[2] = {0, 0};
+    IVV_CUDA(cudaMemcpyAsync(totals, counters + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     IVV_CUDA(cudaStreamSynchronize(s));
+    if (totals[1] != 0) return fail(IVV_ERR_UNSUPPORTED, "the frame's sample count exceeds INT_MAX");
+    const int total = totals[0];
     // per sample: world point, guess, block, scalar, and the block-sorted
     // order of the learned guess's inference; then the sort's histogram
     const size_t per = 2 * sizeof(float4) + 3 * sizeof(int);
@@ -585,7 +601,18 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
                              (const int*)(ws + L.counters), (int*)(ws + L.counters) + ivv::kQueueHeadOff,
                              (float4*)out, v->d_stats, v->num_sms, s);
   } else {
-    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s);
+    // split integration: sample lists (counted by K4, or count and scan),
+    // trace kernel writing the sample points, scalar at every sample and
+    // per-pixel compositing
+    const bool by_bound = split_bytes(v, p, npix) <= kSplitBoundBytes;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    bool split = !ws_is_scratch && (by_bound || !capturing);
+    int* counters = (int*)(ws + L.counters);
+    const float tail_eps = 1e-12f * (float)v->hv.diag;  // as the integrator computes it
+    ivv::SampleCount sc{(float)p.ds, tail_eps, (int*)(ws + L.items), (int*)(ws + L.items) + npix, counters + 2};
+    bool counted = false;
+    st = run_surface_pairs<float>(v, F, p, ws, L, v->lim_pairs, (float4*)out, s, split ? &sc : nullptr, &counted);
     if (st != IVV_OK) return st;
     const ivv::DevCamera<float> c32 = dev_camera<float>(F);
     const float4* pin = (const float4*)(ws + L.pair_in);
@@ -593,22 +620,16 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     const int* pblk = (const int*)(ws + L.pair_block);
     const int* pcnt = (const int*)(ws + L.pair_count);
     const int* act = (const int*)(ws + L.active);
-    int* counters = (int*)(ws + L.counters);
-    // split integration: sample lists (count, scan), trace kernel writing the
-    // sample points, scalar at every sample and per-pixel compositing
-    const bool by_bound = split_bytes(v, p, npix) <= kSplitBoundBytes;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool capturing = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
-    bool split = !ws_is_scratch && (by_bound || !capturing);
     size_t cap = 0;
-    int* cnt = (int*)(ws + L.frag_count);             // fragment lists are dead after stage 2
-    int* off = (int*)(ws + L.frag_meta);
-    int* sums = off + npix;
-    const float tail_eps = 1e-12f * (float)v->hv.diag;  // as the integrator computes it
+    int* cnt = counted ? sc.cnt : (int*)(ws + L.frag_count);   // fragment lists are dead after stage 2
+    int* off = counted ? sc.off : (int*)(ws + L.frag_meta);
+    int* sums = (int*)(ws + L.frag_meta) + npix;
     if (split) {
-      ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt, v->num_sms,
-                           s);
-      ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+      if (!counted) {
+        ivv::launch_rf_count(pin, pout, pblk, pcnt, act, counters, (int)npix, (float)p.ds, tail_eps, cnt,
+                             v->num_sms, s);
+        ivv::launch_rf_scan(cnt, counters, (int)npix, off, sums, 0x7fffffff, counters + 2, s);
+      }
       if (by_bound) {
         cap = split_bound(v, p) * npix;
       } else {

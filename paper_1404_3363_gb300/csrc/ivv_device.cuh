@@ -739,12 +739,31 @@ void launch_entry_fix(const DevVolume& V, const DevCamera<R>& cam, int npix, typ
                       typename Vec4T<R>::type* pair_out, const int* pair_block, const int* pair_count,
                       const int* active, const int* n_active, bool mixed, DevStats* st, int num_sms, cudaStream_t s);
 
+// Samples of a pair of length L > 0 at spacing ds: s_j = j ds for j = 0 ..
+// floor(L / ds), plus the exit s = L when the remainder exceeds tail_eps --
+// the rule every integrator and the sample lists follow.
+__device__ __forceinline__ int pair_sample_count(float L, float ds, float tail_eps) {
+  const float fl = floorf(L / ds);
+  return (int)fl + ((L - fl * ds > tail_eps) ? 1 : 0) + 1;
+}
+
+// Sample lists counted by K4 itself (frames without stage-2 fix-ups): each
+// 16 x 16 tile claims one run of the list for its active pixels, in the
+// order of their queue items; off / cnt [active items], total[0] the running
+// total, total[1] set when it passed INT_MAX.  off == nullptr: not counted.
+struct SampleCount {
+  float ds, tail_eps;
+  int* off;
+  int* cnt;
+  int* total;
+};
+
 template <typename R>
 void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename Vec4T<R>::type* frag_tp,
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs,
                  int* active, int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, int* tile_flag,
-                 DevStats* st, cudaStream_t s);
+                 DevStats* st, cudaStream_t s, const SampleCount* count = nullptr);
 
 struct IntegrateArgs {
   float rk_tol, ds, c, early_alpha;

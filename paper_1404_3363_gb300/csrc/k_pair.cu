@@ -512,11 +512,12 @@ __global__ void __launch_bounds__(128) k4_entry_fix(DevVolume V, DevCamera<R> ca
 // every render keeps.
 __device__ __forceinline__ void pair_epilogue(int pix, int np, float len, unsigned um, unsigned pov,
                                               int* __restrict__ active, int* __restrict__ n_active,
-                                              DevStats* __restrict__ st) {
+                                              DevStats* __restrict__ st, int ns = 0,
+                                              const SampleCount* sc = nullptr) {
   constexpr int kBands = 8;
   __shared__ int s_cnt[kBands][8];    // [band][warp]: active pixels, then their offsets
   __shared__ unsigned s_max;
-  __shared__ int s_base;
+  __shared__ int s_base, s_tot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = np > 0;
   const float key = act && isfinite(len) && len > 0.f ? len : 0.f;   // a non-finite length goes to band 0
@@ -546,9 +547,50 @@ __device__ __forceinline__ void pair_epilogue(int pix, int np, float len, unsign
         tot += c;
       }
     s_base = tot > 0 ? atomicAdd(n_active, tot) : 0;
+    s_tot = tot;
   }
   __syncthreads();
-  if (act) active[s_base + s_cnt[band][warp] + __popc(my_band_mask & ((1u << lane) - 1u))] = pix;
+  const int loc = act ? s_cnt[band][warp] + __popc(my_band_mask & ((1u << lane) - 1u)) : 0;
+  if (act) active[s_base + loc] = pix;
+  if (sc != nullptr) {
+    // the tile's run of the sample list: an exclusive scan of its active
+    // pixels' sample counts in queue order, one atomic for the tile
+    __shared__ int s_ns[256];
+    __shared__ int s_wsum[8];
+    __shared__ int s_sbase;
+    const int tot = s_tot;
+    if (act) s_ns[loc] = ns;
+    __syncthreads();
+    const int v = (int)threadIdx.x < tot ? s_ns[threadIdx.x] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int w = 0; w < 8; ++w) {
+        const int c = s_wsum[w];
+        s_wsum[w] = acc;
+        acc += c;
+      }
+      int b = 0;
+      if (acc > 0) {
+        b = atomicAdd(sc->total, acc);
+        if (b < 0 || b > 0x7fffffff - acc) sc->total[1] = 1;     // the list passed INT_MAX
+      }
+      s_sbase = b;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < tot) {
+      const int item = s_base + (int)threadIdx.x;
+      sc->off[item] = s_sbase + s_wsum[warp] + incl - v;
+      sc->cnt[item] = v;
+    }
+  }
   unsigned long long cu = um, cp = pov, cr = act ? 1 : 0, cpairs = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -584,7 +626,7 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                                                int* __restrict__ pair_block, int* __restrict__ pair_count,
                                                int max_pairs, int* __restrict__ active, int* __restrict__ n_active,
                                                float4* __restrict__ out_rgba, ClipArgs<R> clip,
-                                               int* __restrict__ tile_flag, int max_frags,
+                                               int* __restrict__ tile_flag, int max_frags, SampleCount sc,
                                                DevStats* __restrict__ st) {
   pdl_wait();
   // a tile none of whose warp tiles had a candidate patch was finished by
@@ -606,11 +648,14 @@ __global__ void __launch_bounds__(256) k4_pair(int w, int npix, R tau_dup, const
                          pair_count, max_pairs, out_rgba ? out_rgba + pix : nullptr, um, pov, max_frags);
   }
   float len = 0.f;                                  // the pixel's path length through the volume
+  int ns = 0;                                       // its samples (counted here when sc.off is set)
   for (int q = 0; q < np; ++q) {
     const size_t o = (size_t)q * npix + pix;
-    len += (float)(pair_out[o].x - pair_in[o].x);
+    const float L = (float)(pair_out[o].x - pair_in[o].x);
+    len += L;
+    if (sc.off != nullptr && L > 0.f) ns += pair_sample_count(L, sc.ds, sc.tail_eps);
   }
-  pair_epilogue(pix, np, len, um, pov, active, n_active, st);
+  pair_epilogue(pix, np, len, um, pov, active, n_active, st, ns, sc.off != nullptr ? &sc : nullptr);
   // every thread read the flag before the epilogue's barriers: clear it for
   // the next frame
   if (tile_flag != nullptr && threadIdx.x == 0) tile_flag[blockIdx.x] = 0;
@@ -649,14 +694,16 @@ void launch_pair(const DevVolume& V, int w, int npix, float diag, const typename
                  const unsigned* frag_meta, const int* frag_count, typename Vec4T<R>::type* pair_in,
                  typename Vec4T<R>::type* pair_out, int* pair_block, int* pair_count, int max_pairs, int* active,
                  int* n_active, float4* out_rgba_zero, const ClipArgs<R>& clip, int* tile_flag, DevStats* st,
-                 cudaStream_t s) {
+                 cudaStream_t s, const SampleCount* count) {
   if (npix <= 0) return;
   const R tau = sizeof(R) == 4 ? R(1e-5) * R(diag) : R(1e-9) * R(diag);
   if (w <= 0) return;
   const int h = npix / w;
+  SampleCount sc{0.f, 0.f, nullptr, nullptr, nullptr};
+  if (count != nullptr) sc = *count;
   launch_pdl(k4_pair<R>, dim3(((w + 15) / 16) * ((h + 15) / 16)), dim3(256), s, w, npix, tau, frag_tp, frag_meta,
              frag_count, pair_in, pair_out, pair_block, pair_count, max_pairs, active, n_active, out_rgba_zero, clip,
-             tile_flag, V.max_frags, st);
+             tile_flag, V.max_frags, sc, st);
 }
 
 void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4* frag_tp, const unsigned* frag_meta,
@@ -669,10 +716,10 @@ void launch_batch_pair(const BatchArgs& ba, int tiles16, int npix, const float4*
 
 template void launch_pair<float>(const DevVolume&, int, int, float, const float4*, const unsigned*, const int*,
                                  float4*, float4*, int*, int*, int, int*, int*, float4*, const ClipArgs<float>&,
-                                 int*, DevStats*, cudaStream_t);
+                                 int*, DevStats*, cudaStream_t, const SampleCount*);
 template void launch_pair<double>(const DevVolume&, int, int, float, const Dbl4*, const unsigned*, const int*, Dbl4*,
                                   Dbl4*, int*, int*, int, int*, int*, float4*, const ClipArgs<double>&, int*,
-                                  DevStats*, cudaStream_t);
+                                  DevStats*, cudaStream_t, const SampleCount*);
 
 template <typename R>
 void launch_clip_solve(const DevVolume& V, const DevCamera<R>& cam, int npix, typename Vec4T<R>::type* pair_in,
