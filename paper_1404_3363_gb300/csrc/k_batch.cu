@@ -122,22 +122,29 @@ __global__ void __launch_bounds__(kRootsThreads, 4) kb2c_thread(DevVolume V, Bat
   if (n <= warp_max) return;
   unsigned long long c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
+  __shared__ ThreadDeepSmem<P> s_deep[kRootsThreads / 32];
+  ThreadDeepSmem<P>& dm = s_deep[threadIdx.x >> 5];
   for (;;) {
     const int base = take_items(n_items, n, kSlowHead);
     if (base >= n) break;
     const int k = base + (int)(threadIdx.x & 31);
-    if (k >= n) continue;
-    const int2 it = __ldg(items + __ldg(slow + k));
-    const int rq = (int)((unsigned)it.y >> kBatchFaceBits);
-    const int fi = it.y & ((1 << kBatchFaceBits) - 1);
-    const DevRequest& q = ba.req[rq];
-    const int loc = it.x - __ldg(ba.pix0 + rq);
-    const int xw = loc % q.cam.w, yw = loc / q.cam.w;
-    const int px = q.cam.x0 + xw, py = q.cam.y0 + yw;
-    float o[3], d[3];
-    make_ray<float>(q.cam, px, py, o, d);
-    split_item_thread<P, float, MIXED, STATS>(V, q.cam64, it.x, fi, px, py, o, d, q.diag, stride, frag_tp,
-                                              frag_meta, frag_count, st, c_newton, c_fp64, c_frag);
+    const bool have = k < n;
+    int pix = 0, fi = 0, px = 0, py = 0, rq = 0;
+    float o[3] = {0, 0, 0}, d[3] = {0, 0, 1}, diag = 1.f;
+    if (have) {
+      const int2 it = __ldg(items + __ldg(slow + k));
+      rq = (int)((unsigned)it.y >> kBatchFaceBits);
+      fi = it.y & ((1 << kBatchFaceBits) - 1);
+      pix = it.x;
+      const DevRequest& q = ba.req[rq];
+      const int loc = it.x - __ldg(ba.pix0 + rq);
+      px = q.cam.x0 + loc % q.cam.w;
+      py = q.cam.y0 + loc / q.cam.w;
+      diag = q.diag;
+      make_ray<float>(q.cam, px, py, o, d);
+    }
+    split_round_thread<P, MIXED, STATS>(V, ba.req[rq].cam64, have, pix, fi, px, py, o, d, diag, stride, frag_tp,
+                                        frag_meta, frag_count, st, dm, c_newton, c_fp64, c_frag);
   }
   roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
 }

@@ -150,18 +150,40 @@ __global__ void __launch_bounds__(kRootsThreads, 4) k2c_thread(DevVolume V, DevC
   const size_t stride = (size_t)cam.w * cam.h;
   unsigned long long c_fp64 = 0, c_frag = 0;
   int c_newton = 0;
-  for (;;) {
-    const int base = take_items(n_items, n, kSlowHead);
-    if (base >= n) break;
-    const int k = base + (int)(threadIdx.x & 31);
-    if (k >= n) continue;
-    const int2 it = __ldg(items + __ldg(slow + k));
-    const int xw = it.x % cam.w, yw = it.x / cam.w;
-    const int px = cam.x0 + xw, py = cam.y0 + yw;
-    R o[3], d[3];
-    make_ray<R>(cam, px, py, o, d);
-    split_item_thread<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
-                                          frag_count, st, c_newton, c_fp64, c_frag);
+  if constexpr (sizeof(R) == 4) {
+    __shared__ ThreadDeepSmem<P> s_deep[kRootsThreads / 32];
+    ThreadDeepSmem<P>& dm = s_deep[threadIdx.x >> 5];
+    for (;;) {
+      const int base = take_items(n_items, n, kSlowHead);
+      if (base >= n) break;
+      const int k = base + (int)(threadIdx.x & 31);
+      const bool have = k < n;
+      int2 it = make_int2(0, 0);
+      int px = 0, py = 0;
+      R o[3] = {0, 0, 0}, d[3] = {0, 0, 1};
+      if (have) {
+        it = __ldg(items + __ldg(slow + k));
+        px = cam.x0 + it.x % cam.w;
+        py = cam.y0 + it.x / cam.w;
+        make_ray<R>(cam, px, py, o, d);
+      }
+      split_round_thread<P, MIXED, STATS>(V, cam64, have, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp,
+                                          frag_meta, frag_count, st, dm, c_newton, c_fp64, c_frag);
+    }
+  } else {
+    for (;;) {
+      const int base = take_items(n_items, n, kSlowHead);
+      if (base >= n) break;
+      const int k = base + (int)(threadIdx.x & 31);
+      if (k >= n) continue;
+      const int2 it = __ldg(items + __ldg(slow + k));
+      const int xw = it.x % cam.w, yw = it.x / cam.w;
+      const int px = cam.x0 + xw, py = cam.y0 + yw;
+      R o[3], d[3];
+      make_ray<R>(cam, px, py, o, d);
+      split_item_thread<P, R, MIXED, STATS>(V, cam64, it.x, it.y, px, py, o, d, V.diag, stride, frag_tp, frag_meta,
+                                            frag_count, st, c_newton, c_fp64, c_frag);
+    }
   }
   roots_counters<STATS, true>(0, c_newton, c_fp64, c_frag, n, st);
 }

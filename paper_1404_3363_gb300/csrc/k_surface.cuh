@@ -528,6 +528,151 @@ __device__ __forceinline__ void split_item_thread(const DevVolume& V, const DevC
   }
 }
 
+// K2c thread form with the deepest multi-starts shared by the warp: each
+// lane runs the depth-first search of patch_roots_split (isect.cuh) for its
+// own item, but the uncertified boxes of the deepest level -- whose five
+// Newton starts would hold the warp while one lane runs them -- go to a
+// warp list; once every lane's search is done the warp runs the list with
+// one (box, start) pair per lane and hands the roots back to their items.
+constexpr int kWarpDeepCap = 64;      // deferred boxes per warp and round of 32 items
+
+template <int P>
+struct ThreadDeepSmem {
+  Patch2<P, float> q[32];             // each lane's projected patch
+  SplitBox<float> box[kWarpDeepCap];
+  int owner[kWarpDeepCap];
+  float2 root[kWarpDeepCap * kMultiStarts];   // per (box, start): the root in patch coordinates, or NaN
+  int n;
+};
+
+// patch_roots_split with the deepest uncertified boxes deferred to dm
+// (inline once the list is full).
+template <int P>
+__device__ __forceinline__ int split_roots_defer(const Patch2<P, float>& q0, float pad, float* ra, float* rb,
+                                                 int& iters, ThreadDeepSmem<P>& dm, int lane) {
+  typedef float R;
+  constexpr int N = P + 1;
+  SplitBox<R> stack[kSplitDepth + 1];
+  stack[0] = SplitBox<R>{R(0), R(1), R(0), R(1), 0};
+  int sp = 1, nr = 0;
+  while (sp > 0) {
+    const SplitBox<R> nd = stack[--sp];
+    Patch2<P, R> q;
+    sub_patch<P, R>(q0, nd.a0, nd.a1, nd.b0, nd.b1, q);
+    if (!hull_has_origin<P, R>(q, pad)) continue;
+    bool split = true;
+    if (fixed_jacobian_sign<P, R>(q)) {
+      R a = R(0.5), b = R(0.5);
+      split = !(newton2<P, R>(q, a, b, iters, kBoxNewtonLo<R>(), kBoxNewtonHi<R>(), kBoxNewtonIters) &&
+                accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr));
+    } else if (nd.depth >= kSplitDepth) {
+      const int at = atomicAdd(&dm.n, 1);
+      if (at < kWarpDeepCap) {
+        dm.box[at] = nd;
+        dm.owner[at] = lane;
+      } else {
+#pragma unroll 1
+        for (int s0 = 0; s0 < kMultiStarts; ++s0) {
+          R a, b;
+          multi_start<R>(s0, a, b);
+          if (newton2<P, R>(q, a, b, iters)) accept_root<R>(a, b, nd.a0, nd.a1, nd.b0, nd.b1, ra, rb, nr, false);
+        }
+      }
+      split = false;
+    }
+    if (!split || nd.depth >= kSplitDepth || sp + 2 > kSplitDepth + 1) continue;
+    R la = 0, lb = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      la += fabs(q.x[k * N + P] - q.x[k * N]) + fabs(q.y[k * N + P] - q.y[k * N]);
+      lb += fabs(q.x[P * N + k] - q.x[k]) + fabs(q.y[P * N + k] - q.y[k]);
+    }
+    SplitBox<R>& hi = stack[sp];
+    SplitBox<R>& lo = stack[sp + 1];       // lower half is processed next
+    lo = nd;
+    hi = nd;
+    lo.depth = hi.depth = nd.depth + 1;
+    if (la >= lb) {
+      const R m = R(0.5) * (nd.a0 + nd.a1);
+      lo.a1 = m;
+      hi.a0 = m;
+    } else {
+      const R m = R(0.5) * (nd.b0 + nd.b1);
+      lo.b1 = m;
+      hi.b0 = m;
+    }
+    sp += 2;
+  }
+  return nr;
+}
+
+// One round of the thread form (all lanes of the warp call it; lanes with
+// have = false only help with the deferred boxes): the lane's item
+// (pixel pix, face patch fi, ray o + t d of pixel (px, py) of cam64's image),
+// then its fragments.
+template <int P, bool MIXED, bool STATS>
+__device__ __forceinline__ void split_round_thread(const DevVolume& V, const DevCamera<double>& cam64, bool have,
+                                                   int pix, int fi, int px, int py, const float o[3],
+                                                   const float d[3], float diag, size_t stride,
+                                                   float4* __restrict__ frag_tp, unsigned* __restrict__ frag_meta,
+                                                   int* __restrict__ frag_count, DevStats* __restrict__ st,
+                                                   ThreadDeepSmem<P>& dm, int& c_newton,
+                                                   unsigned long long& c_fp64, unsigned long long& c_frag) {
+  typedef float R;
+  constexpr int NN = (P + 1) * (P + 1);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) dm.n = 0;
+  __syncwarp();
+  const R pad = R(1e-6) * R(diag);
+  R ra[kMaxPatchRoots], rb[kMaxPatchRoots];
+  int nr = 0;
+  const FaceMeta* m = nullptr;
+  R org[3] = {0, 0, 0};
+  const float4* cp = nullptr;
+  if (have) {
+    R e1[3], e2[3];
+    ray_frame<R>(d, e1, e2);
+    m = &V.faces[fi];
+    org[0] = m->org[0]; org[1] = m->org[1]; org[2] = m->org[2];
+    cp = V.face32 + (size_t)fi * NN;
+    project_patch<P, R, float4>(cp, org, o, e1, e2, dm.q[lane]);
+    nr = split_roots_defer<P>(dm.q[lane], pad, ra, rb, c_newton, dm, lane);
+  }
+  __syncwarp();
+  const int nd_deep = min(dm.n, kWarpDeepCap);
+#pragma unroll 1
+  for (int k = lane; k < nd_deep * kMultiStarts; k += 32) {
+    const SplitBox<R> nd = dm.box[k / kMultiStarts];
+    Patch2<P, R> q;
+    sub_patch<P, R>(dm.q[dm.owner[k / kMultiStarts]], nd.a0, nd.a1, nd.b0, nd.b1, q);
+    R a, b;
+    multi_start<R>(k % kMultiStarts, a, b);
+    float2 r = make_float2(__int_as_float(0x7fffffff), 0.f);
+    if (newton2<P, R>(q, a, b, c_newton)) r = make_float2(nd.a0 + a * (nd.a1 - nd.a0), nd.b0 + b * (nd.b1 - nd.b0));
+    dm.root[k] = r;
+  }
+  __syncwarp();
+  if (have) {
+    // the item's roots from its deferred boxes, in the order the search
+    // deferred them, merged as the inline search merges (accept_root)
+    for (int k = 0; k < nd_deep * kMultiStarts; ++k) {
+      if (dm.owner[k / kMultiStarts] != lane) continue;
+      const float2 r = dm.root[k];
+      if (r.x == r.x) accept_root<R>(r.x, r.y, R(0), R(1), R(0), R(1), ra, rb, nr, false);
+    }
+    const R pa0 = m->a0, pa1 = m->a1, pb0 = m->b0, pb1 = m->b1;
+    for (int k = 0; k < nr; ++k) {
+      const R a = ra[k], b = rb[k];          // within the acceptance tolerance of the patch
+      R t, pp[3], cosang;
+      bool front;
+      make_fragment<P, R, float4>(cp, org, *m, pa0, pa1, pb0, pb1, o, d, a, b, t, front, pp, cosang);
+      emit_fragment<P, R, MIXED, STATS>(V, cam64, fi, m->face, m->block, px, py, pix, stride, a, b, t, pp, front,
+                                        cosang, frag_tp, frag_meta, frag_count, st, c_fp64, c_frag);
+    }
+  }
+  __syncwarp();
+}
+
 // Appends item i to the list of items that need the subdivision search
 // (count at n_items[kSlowCounter - kItemCounter]).
 __device__ __forceinline__ void defer_item(int i, int* __restrict__ slow, int cap, int* __restrict__ n_items) {
