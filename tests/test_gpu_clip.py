@@ -133,3 +133,25 @@ def test_clip_argument_errors(ivv):
                 dict(cut_planes=((float("nan"), 0.0, 1.0, 0.0),))]:
         with pytest.raises(ivv.IvvError):
             vol.render(sc.camera, dataclasses.replace(sc.params, **bad), 16, 16)
+
+
+@pytest.mark.parametrize("cfg,method", [(1, 0), (2, 0), (2, 1)])
+def test_sample_lists_counted_by_k4_or_after_the_fix_ups(ivv, cfg, method):
+    """Without planes K4 counts each pixel's samples into the sample lists;
+    with a plane the counts run after the fix-up solves.  A near plane just
+    in front of the eye moves no pair end, so both routes see the same pairs
+    and must give the same image, value for value (split ODE integration and
+    per-sample root finding)."""
+    sc = scenes.config(cfg, width=200, height=120)
+    sc.params.method = method
+    if method == 1:
+        sc.params.use_mlp_guess = 2
+        sc.params.rf_tol = 1e-3
+    vol = ivv.volume_for(sc)
+    a = vol.render(sc.camera, sc.params, sc.width, sc.height).clone()
+    near = dataclasses.replace(sc.params, near_clip=1e-4)
+    b = vol.render(sc.camera, near, sc.width, sc.height)
+    torch.cuda.synchronize()
+    assert a[..., 3].max().item() > 0.1
+    assert torch.equal(a, b), (a - b).abs().max().item()
+    vol.close()
