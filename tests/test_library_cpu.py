@@ -3,6 +3,7 @@ function include/ivv.h declares; its host preparation (knot insertion,
 degree elevation, face extraction, validation) reproduces the oracle's
 Cox-de Boor evaluation; invalid descriptions are rejected with statuses."""
 import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -256,3 +257,26 @@ def test_lone_edge_touch_is_not_an_entry(lib):
                     (x0 + i, y0 + j, k, pairs[k, pix, [3, 7]], p.t_in, p.t_out)
             touched += len(rp) > 1
     assert touched > 10, "the window crosses the sliver"
+
+
+def test_batch_transfer_functions_have_bounded_slope():
+    """The request TFs' knots lie at least 1/64 apart (slope <= 64 per unit
+    of normalised scalar); the spread keeps the seeded draws, so the cameras
+    and sizes are those of the plain draw."""
+    vols, reqs = scenes.batch_requests()
+    for q in reqs:
+        r = q.tf.r.astype(np.float64)
+        assert r[0] == 0.0 and r[-1] == 1.0
+        assert np.diff(r).min() >= 1.0 / 64 - 1e-6
+        assert np.all((q.tf.rgba >= 0) & (q.tf.rgba <= 1))
+    # the same stream drawn plainly: the knots are the sorted draws spread
+    # by r -> i/64 + (1 - 7/64) r, the colours are the draws themselves
+    rng = np.random.default_rng(12348)
+    for q in reqs:
+        assert q.volume == int(rng.integers(0, 3))
+        assert q.width == int(rng.choice([256, 512, 768, 1024]))
+        rng.uniform(-1, 1), rng.uniform(0, 2 * math.pi), rng.uniform(30, 45)
+        r = np.sort(rng.uniform(0, 1, 6))
+        rgba = rng.uniform(0, 1, (8, 4))
+        np.testing.assert_allclose(q.tf.r[1:-1], np.arange(1, 7) / 64 + (1 - 7 / 64) * r, atol=1e-7)
+        np.testing.assert_allclose(q.tf.rgba, rgba, atol=1e-7)
