@@ -264,14 +264,15 @@ __device__ __forceinline__ float pick(const float a[N], int i) {
   return v;
 }
 
-// The paired contractions of eval_block (defined below).
-template <int P, bool WANT_RHO>
+// The paired contractions of eval_block (defined below); UI unrolls their
+// outer (u) loop, chosen per kernel by measurement.
+template <int P, bool WANT_RHO, int UI = 1>
 __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
                                                const float dbu[P + 1], const float bv[P + 1],
                                                const float dbv[P + 1], const float bw[P + 1],
                                                const float dbw[P + 1], float f[3], float fu[3], float fv[3],
                                                float fw[3], float& rho);
-template <int P>
+template <int P, int UI = 1>
 __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp, const float bu[P + 1],
                                                    const float dbu[P + 1], const float bv[P + 1],
                                                    const float dbv[P + 1], const float bw[P + 1],
@@ -285,7 +286,7 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
 // XYZ selects the contraction without the scalar channel (fewer paired
 // multiply-adds, same results; the integrator keeps the plain form, for which
 // the compiler allocates its registers better).
-template <int P, typename R, bool WANT_RHO, bool XYZ = false>
+template <int P, typename R, bool WANT_RHO, bool XYZ = false, int UI = 1>
 __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& B, const R p[3], R phi[3],
                                            R J[3][3], R& rho) {
   constexpr int N = P + 1;
@@ -317,9 +318,9 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
   R s = 0;
   if constexpr (sizeof(R) == 4) {
     if constexpr (XYZ && !WANT_RHO)
-      contract_f32x2_xyz<P>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw);
+      contract_f32x2_xyz<P, UI>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw);
     else
-      contract_f32x2<P, WANT_RHO>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw, s);
+      contract_f32x2<P, WANT_RHO, UI>(V.elem32 + base, bu, dbu, bv, dbv, bw, dbw, f, fu, fv, fw, s);
   } else {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -372,7 +373,7 @@ __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& 
 // multiply-adds per instruction): (x, y) and (z, rho) of each control point
 // travel together through the w, v and u contractions; the second lane of the
 // (z, rho) pair of a derivative is not needed and costs nothing.
-template <int P, bool WANT_RHO>
+template <int P, bool WANT_RHO, int UI>
 __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, const float bu[P + 1],
                                                const float dbu[P + 1], const float bv[P + 1],
                                                const float dbv[P + 1], const float bw[P + 1],
@@ -381,7 +382,7 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
   constexpr int N = P + 1;
   const float2 z2 = make_float2(0.f, 0.f);
   float2 fxy = z2, fzr = z2, fuxy = z2, fuzr = z2, fvxy = z2, fvzr = z2, fwxy = z2, fwzr = z2;
-#pragma unroll 1
+#pragma unroll UI
   for (int i = 0; i < N; ++i) {
     float2 s00xy = z2, s00zr = z2, s01xy = z2, s01zr = z2, s10xy = z2, s10zr = z2;
 #pragma unroll
@@ -431,7 +432,7 @@ __device__ __forceinline__ void contract_f32x2(const float4* __restrict__ cp, co
 // sums).  Every output is the same chain of fused multiply-adds in the same
 // order as above, so phi and J agree bit for bit; the w contraction of a
 // cubic point takes 192 paired multiply-adds instead of 256.
-template <int P>
+template <int P, int UI>
 __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp, const float bu[P + 1],
                                                    const float dbu[P + 1], const float bv[P + 1],
                                                    const float dbv[P + 1], const float bw[P + 1],
@@ -441,7 +442,7 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
   const float2 z2 = make_float2(0.f, 0.f);
   // (f, fu).z and (fv, fw).z share pairs
   float2 fxy = z2, fuxy = z2, fvxy = z2, fwxy = z2, f_fu_z = z2, fv_fw_z = z2;
-#pragma unroll 1
+#pragma unroll UI
   for (int i = 0; i < N; ++i) {
     float2 s00xy = z2, s01xy = z2, s10xy = z2, s00_s01_z = z2;
     float s10z = 0.f;
