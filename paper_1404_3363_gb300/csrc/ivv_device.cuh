@@ -284,8 +284,8 @@ __device__ __forceinline__ void contract_f32x2_xyz(const float4* __restrict__ cp
 // (j,k) slab is contracted along w (value and w-derivative), then along v,
 // then the u contraction accumulates -- 576 FMA for P = 3.
 // XYZ selects the contraction without the scalar channel (fewer paired
-// multiply-adds, same results; the integrator keeps the plain form, for which
-// the compiler allocates its registers better).
+// multiply-adds, same results; it pays where the kernel has the registers for
+// it: the shading pass and the single-frame trace kernel of cubic volumes).
 template <int P, typename R, bool WANT_RHO, bool XYZ = false, int UI = 1>
 __device__ __forceinline__ void eval_block(const DevVolume& V, const BlockInfo& B, const R p[3], R phi[3],
                                            R J[3][3], R& rho) {

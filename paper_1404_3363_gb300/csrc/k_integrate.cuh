@@ -24,8 +24,10 @@ namespace ivv {
 
 template <typename R> struct Acc { R C[3]; R a; };
 
-// W(p) = J_phi(p)^-1 V(phi(p)) and, when asked, rho(p) and phi(p).
-template <int P, typename R, bool MIXED, bool WANT_RHO, int UI = 1>
+// W(p) = J_phi(p)^-1 V(phi(p)) and, when asked, rho(p) and phi(p).  UI and
+// XYZ pick the contraction's form (outer-loop unroll; without the scalar
+// channel) where that is the faster one.
+template <int P, typename R, bool MIXED, bool WANT_RHO, int UI = 1, bool XYZ = false>
 __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B, const R p[3], const R g_in[3],
                                          const R d[3], R c, int mode, R W[3], R& rho, R phi[3],
                                          unsigned long long& n_fp64) {
@@ -33,7 +35,7 @@ __device__ __forceinline__ void rhs_eval(const DevVolume& V, const BlockInfo& B,
   if (WANT_RHO && mode == IVV_SCALAR_CP)
     eval_block<P, R, true, false, UI>(V, B, p, phi, J, rc);
   else
-    eval_block<P, R, false, false, UI>(V, B, p, phi, J, rc);
+    eval_block<P, R, false, XYZ, UI>(V, B, p, phi, J, rc);
   R e[3] = {g_in[0] - phi[0], g_in[1] - phi[1], g_in[2] - phi[2]};
   const R ed = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
   R v[3];
