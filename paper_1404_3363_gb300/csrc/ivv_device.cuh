@@ -841,9 +841,13 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
                       const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                       float tail_eps, int guess, int cap, float4* sg, int* sblk, float4* sp, int num_sms,
                       cudaStream_t s);
+// perm (optional): the order in which the samples are solved.
 void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
                       const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
-                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s);
+                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s, const int* perm = nullptr);
+// key[i]: global index of the element holding sample i's start sp[i].
+void launch_rf_elem_key(const DevVolume& V, const int* n_ptr, const int* sblk, const float4* sp, int* key, int num_sms,
+                        cudaStream_t s);
 void launch_rf_composite(const DevTF& tf, int K, float early, const float4* pin, const float4* pout, const int* pblk,
                          const int* pcnt, const int* active, const int* n_active, const int* off, int npix, float ds,
                          float tail_eps, int cap, const float* srho, float4* out, DevStats* st,

@@ -202,13 +202,17 @@ __global__ void __launch_bounds__(128) k_rf_newton(DevVolume V, DevCamera<float>
                                                    const int* __restrict__ n_ptr, const float4* __restrict__ sg,
                                                    const int* __restrict__ sblk, const float4* __restrict__ sp,
                                                    float* __restrict__ srho, float4* __restrict__ p_out,
-                                                   int* __restrict__ it_out, DevStats* __restrict__ st) {
+                                                   int* __restrict__ it_out, const int* __restrict__ perm,
+                                                   DevStats* __restrict__ st) {
   pdl_wait();
   const int n = *n_ptr;
   unsigned long long c_it = 0, c_ev = 0, c_fail = 0, c_64 = 0;
   // half width of a pixel per unit depth (perspective) or absolute (ortho)
   const float px_half = cam.sy / (float)cam.H;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    // perm: the samples in the order of their guesses' elements, so a warp's
+    // control-point loads meet few elements
+    const int i = perm ? __ldg(perm + k) : k;
     const float4 g4 = sg[i];
     const float g[3] = {g4.x, g4.y, g4.z};
     const BlockInfo B = V.blocks[sblk[i]];
@@ -409,13 +413,46 @@ void launch_rf_expand(const DevCamera<float>& cam, const float4* pin, const floa
              tail_eps, guess, cap, sg, sblk, sp);
 }
 
+// Sort key of every sample: the global index of the Bezier element that
+// holds its Newton start.
+__global__ void __launch_bounds__(256) k_rf_elem_key(DevVolume V, const int* __restrict__ n_ptr,
+                                                     const int* __restrict__ sblk, const float4* __restrict__ sp,
+                                                     int* __restrict__ key) {
+  pdl_wait();
+  const int n = *n_ptr;
+  const float* brk = V.brk32;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const BlockInfo B = V.blocks[__ldg(sblk + i)];
+    const float4 p4 = sp[i];
+    const float p[3] = {p4.x, p4.y, p4.z};
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float x = fminf(fmaxf(p[d], 0.f), 1.f);
+      if ((B.uniform >> d) & 1) {
+        const int k = (int)(x * (float)B.nseg[d]);
+        e[d] = k < B.nseg[d] - 1 ? k : B.nseg[d] - 1;
+      } else {
+        float loc, sc;
+        e[d] = locate<float>(brk + B.brk_off[d], B.nseg[d], x, loc, sc);
+      }
+    }
+    key[i] = B.elem_off + (e[2] * B.nseg[1] + e[1]) * B.nseg[0] + e[0];
+  }
+}
+
+void launch_rf_elem_key(const DevVolume& V, const int* n_ptr, const int* sblk, const float4* sp, int* key, int num_sms,
+                        cudaStream_t s) {
+  launch_pdl(k_rf_elem_key, dim3(num_sms * 8), dim3(256), s, V, n_ptr, sblk, sp, key);
+}
+
 void launch_rf_newton(const DevVolume& V, const DevCamera<float>& cam, float rf_tol, float abs_tol, const int* n_ptr,
                       const float4* sg, const int* sblk, const float4* sp, float* srho, float4* p_out, int* it_out,
-                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s) {
+                      DevStats* st, bool stats, bool mixed, int num_sms, cudaStream_t s, const int* perm) {
   const int grid = num_sms * 16;
 #define IVV_RFN(PP, SS, MM) \
   launch_pdl(k_rf_newton<PP, SS, MM>, dim3(grid), dim3(128), s, V, cam, rf_tol, abs_tol, n_ptr, sg, sblk, sp, srho, \
-             p_out, it_out, st)
+             p_out, it_out, perm, st)
   if (V.P == 2) {
     if (mixed) { if (stats) IVV_RFN(2, true, true); else IVV_RFN(2, false, true); }
     else { if (stats) IVV_RFN(2, true, false); else IVV_RFN(2, false, false); }
