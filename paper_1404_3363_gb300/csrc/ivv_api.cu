@@ -542,21 +542,22 @@ ivv_status render_impl(ivv_volume* v, const ivv_camera* cam, const ivv_render_pa
     ivv::DevCamera<float> c32 = dev_camera<float>(F);
     ivv::launch_rf_expand(c32, pin, pout, pblk, pcnt, act, counters, off, (int)npix, (float)p.ds, tail_eps,
                           p.use_mlp_guess, total, sg, sblk, sp, v->num_sms, s);
-    if (p.use_mlp_guess == IVV_GUESS_MLP) {
-      // with many blocks a tile of consecutive samples spans many of them
-      // (one inference pass each): sort by block first; with few, the
-      // scattered reads of the sorted order cost more than the passes
-      const bool sort = nb >= 8;
-      if (sort) ivv::launch_block_sort(sblk, counters + 2, nb, shist, sperm, v->num_sms, s);
-      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s,
-                            sort ? sperm : nullptr);
-    }
-    // Newton in the order of the starts' elements: a warp's control-point
-    // loads then meet one or two elements instead of the several that
-    // consecutive samples of neighbouring rays cross
+    // Newton in the order of the elements of the samples' chord points: a
+    // warp's control-point loads then meet one or two elements instead of
+    // the several that consecutive samples of neighbouring rays cross.  The
+    // element order is also block order, so the inference reads it too.
     if (esort) {
       ivv::launch_rf_elem_key(V, counters + 2, sblk, sp, skey, v->num_sms, s);
       ivv::launch_block_sort(skey, counters + 2, ne, shist, sperm, v->num_sms, s);
+    }
+    if (p.use_mlp_guess == IVV_GUESS_MLP) {
+      // with many blocks a tile of consecutive samples spans many of them
+      // (one inference pass each): read them in block order; with few, the
+      // scattered reads of the sorted order cost more than the passes
+      const bool sort = nb >= 8;
+      if (sort && !esort) ivv::launch_block_sort(sblk, counters + 2, nb, shist, sperm, v->num_sms, s);
+      ivv::launch_mlp_infer(v->d_theta16, v->d_norms, sg, sblk, counters + 2, 0, sp, v->d_stats, v->num_sms, s,
+                            sort ? sperm : nullptr);
     }
     if (p.flags & IVV_FLAG_TIMING) IVV_CUDA(cudaEventRecord(v->ev[3], s));
     ivv::launch_rf_newton(V, c32, (float)p.rf_tol, 0.f, counters + 2, sg, sblk, sp, srho, nullptr, nullptr, v->d_stats,

@@ -181,7 +181,9 @@ __global__ void k_rf_expand(DevCamera<float> cam, const float4* __restrict__ pai
         sg[k] = make_float4(o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2], s);
         sblk[k] = v.blk;
         float p[3];
-        if (guess == 2) {
+        if (guess != 0) {
+          // the chord point (the learned guess's samples carry it until the
+          // inference replaces it: it keys their element sort)
           const float a = s / v.L;
 #pragma unroll
           for (int r = 0; r < 3; ++r) p[r] = v.pin[r] + a * (v.pout[r] - v.pin[r]);
